@@ -1,0 +1,218 @@
+/*
+ * scylla.h -- C ABI of a GB300 (sm_103a) implementation of the hot path of the
+ * Scylla primal heuristic (Mexi, Shamsi, Besancon, Le Bodic, arXiv 2307.03466):
+ * the matrix-free PDHG solve of the LP relaxation that each feasibility-pump
+ * round re-runs after its objective update (Algorithm 1), with fix-and-propagate
+ * (Section 2.3) on the host.
+ *
+ * Problem (Algorithm 1, input; generalised to two-sided rows):
+ *     min c^T x   s.t.   row_lo <= A x <= row_hi,   col_lo <= x <= col_hi,
+ *     x_j integer for is_integer[j] = 1.
+ * The paper's  A x >= b  is the case row_lo = b, row_hi = +INFINITY.
+ *
+ * Conventions for every call:
+ *   - Return value: SCYLLA_OK (0) or a negative SCYLLA_ERR_* code.  Solver
+ *     outcomes (converged, iteration limit, found, ...) are reported in result
+ *     structs, never as error codes.  Nothing aborts or throws across the ABI.
+ *   - scylla_last_error() gives a message for the last failing call on the
+ *     calling thread.
+ *   - Host pointers are caller-owned, read during the call only, and copied.
+ *     Arrays are dense, contiguous, of the stated length.  Pointers documented
+ *     as "device" must point to memory of the device that was current when the
+ *     handle was created.
+ *   - A handle may be used by one host thread at a time.
+ *   - Infinite bounds are IEEE +-INFINITY.  NaN is rejected everywhere.
+ */
+#ifndef SCYLLA_H
+#define SCYLLA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes (return values) ------------------------------------------ */
+#define SCYLLA_OK 0
+#define SCYLLA_ERR_INVALID_ARG (-1) /* malformed input; nothing was changed */
+#define SCYLLA_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define SCYLLA_ERR_OOM (-3)         /* device or host allocation failed */
+#define SCYLLA_ERR_TIMEOUT (-4)     /* a time limit expired inside the call */
+#define SCYLLA_ERR_UNSUPPORTED (-6) /* valid input beyond a documented limit */
+
+/* ---- PDHG solve status (scylla_pdhg_result.status) ------------------------ */
+#define SCYLLA_CONVERGED 0  /* relative KKT error <= tol (Section 2.2) */
+#define SCYLLA_ITER_LIMIT 1 /* k reached the iteration limit (Algorithm 1) */
+#define SCYLLA_STALLED 2    /* rounding of x unchanged over stall_checks checks */
+#define SCYLLA_NUMERICAL 3  /* NaN/Inf met in a step-size or KKT reduction */
+
+/* ---- run status (scylla_run_result.status) -------------------------------- */
+#define SCYLLA_FOUND 0
+#define SCYLLA_NOT_FOUND 1
+
+/* ---- precision of the bulk PDHG iteration --------------------------------- */
+#define SCYLLA_PREC_FP64 0  /* values, vectors and accumulation in FP64 */
+#define SCYLLA_PREC_MIXED 1 /* FP32 SpMVs/vector updates; FP64 KKT, restarts, refinement */
+
+/* CSR matrix with m rows and n columns.  rowptr has m+1 entries, rowptr[0] = 0,
+ * non-decreasing, rowptr[m] = nnz; cols[p] in [0, n), strictly increasing within
+ * each row (no duplicates); vals finite. */
+typedef struct {
+  int64_t m, n, nnz;
+  const int64_t* rowptr;
+  const int32_t* cols;
+  const double* vals;
+} scylla_csr;
+
+/* Parameters.  scylla_default_params() fills the paper's values where the paper
+ * gives them (alpha, eps1, beta, eps_floor: Algorithm 1 and Section 2.2) and
+ * PDLP's customary values for the rules the paper delegates to PDLP
+ * (Section 2.1: step size, restarts, preconditioning). */
+typedef struct {
+  int32_t precision;            /* SCYLLA_PREC_FP64 (default) or SCYLLA_PREC_MIXED */
+  int32_t n_check;              /* attempts between KKT checks (64) */
+  int32_t ruiz_iters;           /* Ruiz equilibration passes (10) */
+  int32_t pock_chambolle;       /* Pock-Chambolle alpha=1 scaling after Ruiz (1) */
+  int32_t adaptive_step;        /* 1: adaptive step size; 0: fixed eta = f/||A~||_F (1) */
+  int32_t restarts;             /* KKT-based restarts to current/average iterate (1) */
+  int32_t primal_weight_update; /* update omega at restarts (1) */
+  int32_t stall_checks;         /* stop when round(x_I) is unchanged for this many checks; 0 = off (0) */
+  int32_t aux_general_integers; /* add l1-distance auxiliary columns/rows for general integers (1) */
+  int32_t use_graph;            /* 1: CUDA graph with device-side loop; 0: direct launches (1) */
+  double fixed_step_factor;     /* f of the fixed-step mode (0.9) */
+  double beta_sufficient;       /* restart if KKT <= 0.2 KKT_last_restart */
+  double beta_necessary;        /* ... or <= 0.8 KKT_last_restart and KKT grew since the last check */
+  double beta_artificial;       /* ... or attempts since restart >= 0.36 attempts */
+  double pw_smoothing;          /* theta of the primal weight update (0.5) */
+  double step_reduction_exp;    /* 0.3 */
+  double step_growth_exp;       /* 0.6 */
+  /* outer loop (scylla_run) */
+  double alpha;                 /* 0.9 (Algorithm 1) */
+  double eps1;                  /* 0.01 (Section 2.2) */
+  double beta;                  /* 0.98 (Section 2.2) */
+  double eps_floor;             /* 1e-8 (Section 2.2) */
+  int64_t max_rounds;           /* pump rounds K (100) */
+  int64_t iter_limit;           /* PDHG attempts per solve inside scylla_run (20000) */
+  int64_t total_iter_cap;       /* PDHG attempts over the whole run (1e9) */
+  int32_t run_stall_checks;     /* stall_checks used by scylla_run's solves (5) */
+  int32_t reserved0;
+  uint64_t seed;                /* perturbation random stream (0) */
+  double time_limit_s;          /* wall-clock limit of scylla_run, <= 0 for none (0) */
+} scylla_params;
+
+typedef struct {
+  int32_t status;        /* SCYLLA_CONVERGED / ITER_LIMIT / STALLED / NUMERICAL */
+  int32_t used_average;  /* 1 if the returned point is the averaged iterate */
+  int64_t iterations;    /* step attempts k of this solve */
+  int64_t accepted, rejected, restarts;
+  double eps_p, eps_d, eps_g, rel_kkt; /* relative residuals of the returned point */
+  double pobj, dobj;     /* primal/dual objective (with the objective offset) */
+  double eta, omega;     /* step size and primal weight after the solve */
+  double seconds;        /* device time of the solve (CUDA events) */
+} scylla_pdhg_result;
+
+typedef struct {
+  int32_t status;           /* SCYLLA_FOUND / SCYLLA_NOT_FOUND */
+  int32_t found_by;         /* 1: rounded LP point (Algorithm 1 first test), 2: fix-and-propagate */
+  int64_t rounds;           /* pump rounds K performed */
+  int64_t total_iterations; /* PDHG attempts over all rounds */
+  int64_t perturbations;    /* rounds in which cycling was detected */
+  double objective;         /* c^T x of the returned point */
+  double seconds, seconds_pdhg, seconds_fixprop;
+} scylla_run_result;
+
+typedef struct scylla_lp scylla_lp; /* opaque; owns all device and host copies */
+
+/* Fill *p with the defaults listed above. */
+void scylla_default_params(scylla_params* p);
+
+/* Validate and copy the MIP, add the auxiliary distance columns (Section 4: the l1
+ * distance on general integers needs auxiliary variables), build the transposed
+ * CSR so that A^T y is a row gather (Algorithm 1, primal step), precondition on
+ * the GPU (Section 2.1: PDLP's diagonal preconditioning), and set the initial
+ * point x = proj_[l,u](0), y = 0 (Algorithm 1, initialisation).
+ *   c, col_lo, col_hi, is_integer: host, length A->n.  row_lo, row_hi: host,
+ *   length A->m.  p: NULL for defaults.  cuda_stream: a cudaStream_t whose prior
+ *   work is ordered before each call of this handle, or NULL.
+ * Errors: INVALID_ARG (see scylla_csr; also lo > hi, NaN, integer column with a
+ * fractional finite bound, is_integer not 0/1), UNSUPPORTED (nnz or a dimension
+ * >= 2^31 - 64), OOM, CUDA.  On error *out is NULL. */
+int scylla_lp_create(const scylla_csr* A, const double* c, const double* row_lo, const double* row_hi,
+                     const double* col_lo, const double* col_hi, const uint8_t* is_integer,
+                     const scylla_params* p, void* cuda_stream, scylla_lp** out);
+
+/* Free every resource of the handle.  NULL is a no-op. */
+void scylla_lp_destroy(scylla_lp* lp);
+
+/* Dimensions of the LP the solver iterates on (original plus auxiliary). */
+int scylla_lp_dims(const scylla_lp* lp, int64_t* m_total, int64_t* n_total, int64_t* nnz_total,
+                   int64_t* n_aux);
+
+/* PDHG on the GPU (Algorithm 1 inner loop; Sections 2.1-2.2) from the handle's
+ * current primal-dual pair (a warm start, Section 2.1), until the relative KKT
+ * error of the current or averaged iterate is <= tol, or k = iter_limit, or the
+ * stall rule fires.  The returned point becomes the handle's current pair.
+ * tol >= 0; iter_limit >= 0.  Errors: INVALID_ARG, CUDA. */
+int scylla_pdhg_solve(scylla_lp* lp, double tol, int64_t iter_limit, scylla_pdhg_result* out);
+
+/* Objective update of Algorithm 1 / Section 2.4 for round K >= 1 around the
+ * integer point xhat (host, length n original; entries on integer columns must be
+ * integral and inside their bounds).  Keeps x, y, eta, omega (warm start).
+ * Errors: INVALID_ARG, CUDA. */
+int scylla_set_objective(scylla_lp* lp, const double* xhat, int32_t K);
+
+/* Current objective c_hat (host, length n_total) and offset, unscaled. */
+int scylla_get_objective(const scylla_lp* lp, double* c_hat, double* offset);
+
+/* The whole heuristic (Algorithm 1): PDHG -> MIP-feasibility test -> fix-and-
+ * propagate -> feasibility test -> cycle handling -> objective update, with the
+ * tolerance schedule of Section 2.2.  x_out (host, length n original) receives the
+ * solution when out->status == SCYLLA_FOUND; every returned point passed
+ * scylla_check_feasible.  Errors: INVALID_ARG, CUDA, TIMEOUT (time limit hit). */
+int scylla_run(scylla_lp* lp, double* x_out, scylla_run_result* out);
+
+/* Current primal point, unscaled: host length n (original columns). */
+int scylla_get_primal(const scylla_lp* lp, double* x);
+/* Current dual point, unscaled: host length m (original rows). */
+int scylla_get_dual(const scylla_lp* lp, double* y);
+/* Same, device pointer of length n (original columns), FP64. */
+int scylla_get_primal_device(const scylla_lp* lp, double* x_device);
+
+/* Full iterate of the solved LP (original plus auxiliary), unscaled, host:
+ * x length n_total, y length m_total; eta, omega may be NULL. */
+int scylla_get_state(const scylla_lp* lp, double* x, double* y, double* eta, double* omega);
+/* Replace the iterate (checkpoint/resume; Section 2.1 notes the PDLP state is the
+ * primal-dual pair).  Same layout as scylla_get_state; eta, omega > 0. */
+int scylla_set_state(scylla_lp* lp, const double* x, const double* y, double eta, double omega);
+
+/* Diagonal scaling A~ = diag(R) A diag(C) found at create: host, R length m_total,
+ * C length n_total. */
+int scylla_get_scaling(const scylla_lp* lp, double* R, double* C);
+
+/* Fix-and-propagate (Section 2.3) on the original MIP, on the host.
+ *   xbar: host, length n.  xhat, dom_lo, dom_hi: host outputs, length n.
+ *   fixed_cols: host output, length n (may be NULL), receives the columns fixed
+ *   by rounding in fixing order; *n_fixed their count (may be NULL).
+ *   ignored_rows: host output, length m (may be NULL), 1 for rows ignored after
+ *   emptying a domain. */
+int scylla_fix_and_propagate(const scylla_lp* lp, const double* xbar, double* xhat, double* dom_lo,
+                             double* dom_hi, int32_t* fixed_cols, int64_t* n_fixed, uint8_t* ignored_rows);
+
+/* Exact MIP-feasibility test of x (host, length n) on the original MIP
+ * (Algorithm 1, both "MIP-feasible" tests): *feasible = 1 or 0. */
+int scylla_check_feasible(const scylla_lp* lp, const double* x, int32_t* feasible);
+
+/* Cycle handling of Section 2.3 on its own.  kind: 1 short cycle, 2 long cycle.
+ * xhat: host in/out, length n; xbar: host, length n; K: round; seed: stream seed.
+ * *flipped (may be NULL) receives the number of changed entries. */
+int scylla_perturb(const scylla_lp* lp, double* xhat, const double* xbar, int32_t kind, int64_t K,
+                   uint64_t seed, int64_t* flipped);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* scylla_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCYLLA_H */

@@ -31,7 +31,7 @@ Readings of what the paper leaves open:
   inside [l_j, u_j] (the other direction when the first one is blocked).  Random
   numbers: SplitMix64 seeded with ``seed XOR K``, uniforms ``(r >> 11) * 2^-53``.
 * Feasibility check: integrality exact; a row whose coefficients, bounds and
-  column values are all integers (below 2^53) is checked in exact integer
+  column values are all integers (below 2^47) is checked in exact integer
   arithmetic; otherwise activities are summed in CSR order with Neumaier
   compensation and compared with tolerance 1e-6 * max(1, |bound|).  Continuous
   column bounds use the same tolerance, integer column bounds are exact.
@@ -202,7 +202,7 @@ def _neumaier(terms):
 
 
 def _is_int_val(v):
-    return math.isfinite(v) and v == math.floor(v) and abs(v) < 2.0 ** 53
+    return math.isfinite(v) and v == math.floor(v) and abs(v) < 2.0 ** 47
 
 
 def check_feasible(rowptr, cols, vals, lo, hi, l, u, is_int, x, tol=1e-6) -> bool:

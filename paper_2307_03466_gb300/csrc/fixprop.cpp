@@ -1,0 +1,366 @@
+// Host side of the Scylla rounding step (arXiv 2307.03466, Section 2.3):
+// fix-and-propagate, the exact MIP-feasibility test used by both success tests of
+// Algorithm 1, and the perturbation used against cycling.
+//
+// Built with -ffp-contract=off so every floating-point operation rounds exactly as
+// written; the fixings and domains are then reproducible bit for bit.
+//
+// Fix-and-propagate: the integer columns are visited in order of increasing
+// distance |xbar_j - round(xbar_j)| (ties by index, round(v) = floor(v + 1/2)); one
+// that propagation has already fixed is skipped, otherwise it is fixed to
+// round(xbar_j) clamped to its domain and propagation runs.  Propagation is
+// activity-based bound tightening with a FIFO queue of rows: a visit recomputes the
+// row's minimum and maximum activity from scratch (finite parts in CSR order,
+// infinite contributions counted) and derives, from the domains at the start of the
+// visit, a bound for every column of the row.  Integer bounds are rounded inward
+// with a 1e-6 tolerance and kept when strictly tighter; continuous bounds are kept
+// when finite and tighter by more than 1e-3 max(1, |old|).  A row whose activity
+// range misses [lo, hi] by more than 1e-9, or whose bounds would empty a domain, is
+// ignored from then on (Section 2.3: constraints that would lead to empty domains are
+// ignored) and changes nothing; otherwise its changes are applied together and the
+// rows of each changed column are queued (ascending, unless queued or ignored).  One
+// propagation stops after 20 m + 1000 row visits.  Finally every column takes its
+// reference value projected onto its domain.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <deque>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "lp_handle.h"
+
+using namespace scylla;
+
+namespace {
+
+const double kInf = std::numeric_limits<double>::infinity();
+
+struct Propagator {
+  const scylla_lp& lp;
+  std::vector<double> dl, du;
+  std::vector<uint8_t> ignored, inq;
+  std::deque<int32_t> queue;
+
+  explicit Propagator(const scylla_lp& h)
+      : lp(h), dl(h.l0), du(h.u0), ignored(h.m0, 0), inq(h.m0, 0) {}
+
+  void push(int32_t i) {
+    if (!inq[i] && !ignored[i]) {
+      inq[i] = 1;
+      queue.push_back(i);
+    }
+  }
+
+  void push_rows_of(int64_t j) {
+    for (int64_t q = lp.colptr0[j]; q < lp.colptr0[j + 1]; ++q) push(lp.colrows0[q]);
+  }
+
+  struct Change {
+    int64_t j;
+    double lb, ub;
+  };
+
+  void visit(int32_t i) {
+    const double lo = lp.lo0[i], hi = lp.hi0[i];
+    if (lo == -kInf && hi == kInf) return;
+    const int64_t p0 = lp.rowptr0[i], p1 = lp.rowptr0[i + 1];
+    double minf = 0.0, maxf = 0.0;
+    int nmin = 0, nmax = 0;
+    for (int64_t p = p0; p < p1; ++p) {
+      const int64_t j = lp.cols0[p];
+      const double a = lp.vals0[p];
+      const double bmin = a > 0 ? dl[j] : du[j];
+      const double bmax = a > 0 ? du[j] : dl[j];
+      if (std::isinf(bmin)) nmin++;
+      else minf += a * bmin;
+      if (std::isinf(bmax)) nmax++;
+      else maxf += a * bmax;
+    }
+    if (nmin == 0 && hi != kInf && minf > hi + 1e-9) {
+      ignored[i] = 1;
+      return;
+    }
+    if (nmax == 0 && lo != -kInf && maxf < lo - 1e-9) {
+      ignored[i] = 1;
+      return;
+    }
+    std::vector<Change> changes;
+    for (int64_t p = p0; p < p1; ++p) {
+      const int64_t j = lp.cols0[p];
+      const double a = lp.vals0[p];
+      const double bmin = a > 0 ? dl[j] : du[j];
+      const double bmax = a > 0 ? du[j] : dl[j];
+      double rmin, rmax;
+      if (std::isinf(bmin)) rmin = (nmin == 1) ? minf : -kInf;
+      else rmin = (nmin == 0) ? (minf - a * bmin) : -kInf;
+      if (std::isinf(bmax)) rmax = (nmax == 1) ? maxf : kInf;
+      else rmax = (nmax == 0) ? (maxf - a * bmax) : kInf;
+      double cand_lb = -kInf, cand_ub = kInf;
+      if (hi != kInf && rmin != -kInf) {
+        const double t = (hi - rmin) / a;
+        if (a > 0) cand_ub = t;
+        else cand_lb = t;
+      }
+      if (lo != -kInf && rmax != kInf) {
+        const double t = (lo - rmax) / a;
+        if (a > 0) cand_lb = t;
+        else cand_ub = t;
+      }
+      const double old_lb = dl[j], old_ub = du[j];
+      double nlb = old_lb, nub = old_ub;
+      if (lp.int0[j]) {
+        if (cand_ub != kInf) {
+          const double v = std::floor(cand_ub + 1e-6);
+          if (v < old_ub) nub = v;
+        }
+        if (cand_lb != -kInf) {
+          const double v = std::ceil(cand_lb - 1e-6);
+          if (v > old_lb) nlb = v;
+        }
+      } else {
+        if (cand_ub != kInf && (old_ub == kInf || cand_ub < old_ub - 1e-3 * std::max(1.0, std::fabs(old_ub))))
+          nub = cand_ub;
+        if (cand_lb != -kInf && (old_lb == -kInf || cand_lb > old_lb + 1e-3 * std::max(1.0, std::fabs(old_lb))))
+          nlb = cand_lb;
+      }
+      if (nlb == old_lb && nub == old_ub) continue;
+      if (nlb > nub + 1e-9) {
+        ignored[i] = 1;
+        return;
+      }
+      changes.push_back({j, nlb, nub});
+    }
+    for (const Change& c : changes) {
+      dl[c.j] = c.lb;
+      du[c.j] = c.ub;
+    }
+    for (const Change& c : changes) push_rows_of(c.j);
+  }
+
+  void run() {
+    const int64_t cap = 20 * lp.m0 + 1000;
+    int64_t visits = 0;
+    while (!queue.empty()) {
+      const int32_t i = queue.front();
+      queue.pop_front();
+      inq[i] = 0;
+      if (ignored[i]) continue;
+      if (visits >= cap) {
+        for (int32_t r : queue) inq[r] = 0;
+        queue.clear();
+        break;
+      }
+      ++visits;
+      visit(i);
+    }
+  }
+};
+
+inline double round_half_up(double v) { return std::floor(v + 0.5); }
+
+bool is_int_value(double v) { return std::isfinite(v) && v == std::floor(v) && std::fabs(v) < 140737488355328.0; }
+
+// Neumaier's compensated sum of a_p x_p in CSR order
+double neumaier_row(const scylla_lp& lp, int64_t i, const double* x) {
+  double s = 0.0, comp = 0.0;
+  for (int64_t p = lp.rowptr0[i]; p < lp.rowptr0[i + 1]; ++p) {
+    const double t = lp.vals0[p] * x[lp.cols0[p]];
+    const double tt = s + t;
+    if (std::fabs(s) >= std::fabs(t)) comp += (s - tt) + t;
+    else comp += (t - tt) + s;
+    s = tt;
+  }
+  return s + comp;
+}
+
+}  // namespace
+
+namespace scylla {
+
+// exact feasibility test (Algorithm 1, "MIP-feasible"): integrality exact; rows with
+// integer coefficients, bounds and column values (|v| < 2^47) in exact 128-bit
+// integer arithmetic; other rows by compensated FP64 sums with tolerance
+// 1e-6 max(1, |bound|); continuous column bounds with the same tolerance.
+bool check_feasible_host(const scylla_lp& lp, const double* x) {
+  const double tol = 1e-6;
+  for (int64_t j = 0; j < lp.n0; ++j) {
+    const double v = x[j];
+    if (!std::isfinite(v)) return false;
+    if (lp.int0[j]) {
+      if (v != std::floor(v) || v < lp.l0[j] || v > lp.u0[j]) return false;
+    } else {
+      if (v < lp.l0[j] - tol * std::max(1.0, std::fabs(lp.l0[j])) ||
+          v > lp.u0[j] + tol * std::max(1.0, std::fabs(lp.u0[j])))
+        return false;
+    }
+  }
+  for (int64_t i = 0; i < lp.m0; ++i) {
+    const double lo = lp.lo0[i], hi = lp.hi0[i];
+    bool exact = (lo == -kInf || is_int_value(lo)) && (hi == kInf || is_int_value(hi));
+    for (int64_t p = lp.rowptr0[i]; exact && p < lp.rowptr0[i + 1]; ++p)
+      exact = is_int_value(lp.vals0[p]) && is_int_value(x[lp.cols0[p]]);
+    if (exact) {
+      __int128 act = 0;
+      for (int64_t p = lp.rowptr0[i]; p < lp.rowptr0[i + 1]; ++p)
+        act += (__int128)(int64_t)lp.vals0[p] * (__int128)(int64_t)x[lp.cols0[p]];
+      if (lo != -kInf && act < (__int128)(int64_t)lo) return false;
+      if (hi != kInf && act > (__int128)(int64_t)hi) return false;
+    } else {
+      const double act = neumaier_row(lp, i, x);
+      if (lo != -kInf && act < lo - tol * std::max(1.0, std::fabs(lo))) return false;
+      if (hi != kInf && act > hi + tol * std::max(1.0, std::fabs(hi))) return false;
+    }
+  }
+  return true;
+}
+
+int fix_and_propagate_host(const scylla_lp& lp, const double* xbar, double* xhat, double* dom_lo, double* dom_hi,
+                           int32_t* fixed_cols, int64_t* n_fixed, uint8_t* ignored_rows) {
+  Propagator pr(lp);
+  for (int32_t i = 0; i < lp.m0; ++i) pr.push(i);
+  pr.run();
+  std::vector<int64_t> order;
+  order.reserve(lp.n_int);
+  std::vector<double> dist(lp.n0, 0.0);
+  for (int64_t j = 0; j < lp.n0; ++j) {
+    if (!lp.int0[j]) continue;
+    order.push_back(j);
+    dist[j] = std::fabs(xbar[j] - round_half_up(xbar[j]));
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    if (dist[a] != dist[b]) return dist[a] < dist[b];
+    return a < b;
+  });
+  int64_t nf = 0;
+  for (int64_t j : order) {
+    if (pr.dl[j] == pr.du[j]) continue;
+    double v = round_half_up(xbar[j]);
+    v = std::min(std::max(v, pr.dl[j]), pr.du[j]);
+    pr.dl[j] = v;
+    pr.du[j] = v;
+    if (fixed_cols) fixed_cols[nf] = int32_t(j);
+    ++nf;
+    pr.push_rows_of(j);
+    pr.run();
+  }
+  for (int64_t j = 0; j < lp.n0; ++j) {
+    xhat[j] = std::min(std::max(xbar[j], pr.dl[j]), pr.du[j]);
+    if (dom_lo) dom_lo[j] = pr.dl[j];
+    if (dom_hi) dom_hi[j] = pr.du[j];
+  }
+  if (n_fixed) *n_fixed = nf;
+  if (ignored_rows) std::memcpy(ignored_rows, pr.ignored.data(), size_t(lp.m0));
+  return SCYLLA_OK;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014)
+struct SplitMix64 {
+  uint64_t s;
+  explicit SplitMix64(uint64_t seed) : s(seed) {}
+  uint64_t next() {
+    s += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return double(next() >> 11) * 0x1.0p-53; }
+};
+
+// one unit toward xbar, or away from it when v already is round(xbar); the other
+// direction when the first leaves [l, u]
+static double flip_value(double v, double xb, double l, double u) {
+  const double r = std::floor(xb + 0.5);
+  double s = xb >= v ? 1.0 : -1.0;
+  if (v == r) s = -s;
+  const double d[2] = {s, -s};
+  for (double dd : d) {
+    const double w = v + dd;
+    if (l <= w && w <= u) return w;
+  }
+  return v;
+}
+
+// Section 2.3 (after Fischetti-Glover-Lodi 2005).  kind 1 (short cycle): flip the TT
+// integer columns with largest |xbar - xhat| > 0, TT ~ U{10..30}; if there is none, or
+// kind 2 (long cycle): flip column j when |xbar_j - xhat_j| + max(rho_j, 0) > 0.5,
+// rho_j ~ U[-0.3, 0.7] drawn in ascending j.  The stream is SplitMix64(seed ^ K).
+int64_t perturb_host(const scylla_lp& lp, double* x, const double* xbar, int kind, int64_t K, uint64_t seed) {
+  SplitMix64 rng(seed ^ uint64_t(K));
+  int64_t flipped = 0;
+  if (kind == 1) {
+    const int64_t TT = 10 + int64_t(std::floor(rng.uniform() * 21.0));
+    std::vector<std::pair<double, int64_t>> cand;
+    for (int64_t j = 0; j < lp.n0; ++j) {
+      if (!lp.int0[j]) continue;
+      const double sv = std::fabs(xbar[j] - x[j]);
+      if (sv > 0) cand.push_back({sv, j});
+    }
+    if (!cand.empty()) {
+      std::stable_sort(cand.begin(), cand.end(), [](const std::pair<double, int64_t>& a,
+                                                   const std::pair<double, int64_t>& b) {
+        if (a.first != b.first) return a.first > b.first;
+        return a.second < b.second;
+      });
+      const int64_t cnt = std::min<int64_t>(TT, int64_t(cand.size()));
+      for (int64_t q = 0; q < cnt; ++q) {
+        const int64_t j = cand[q].second;
+        const double w = flip_value(x[j], xbar[j], lp.l0[j], lp.u0[j]);
+        flipped += (w != x[j]);
+        x[j] = w;
+      }
+      return flipped;
+    }
+  }
+  for (int64_t j = 0; j < lp.n0; ++j) {
+    if (!lp.int0[j]) continue;
+    const double rho = -0.3 + rng.uniform();
+    if (std::fabs(xbar[j] - x[j]) + std::max(rho, 0.0) > 0.5) {
+      const double w = flip_value(x[j], xbar[j], lp.l0[j], lp.u0[j]);
+      flipped += (w != x[j]);
+      x[j] = w;
+    }
+  }
+  return flipped;
+}
+
+}  // namespace scylla
+
+extern "C" int scylla_fix_and_propagate(const scylla_lp* lp, const double* xbar, double* xhat, double* dom_lo,
+                                        double* dom_hi, int32_t* fixed_cols, int64_t* n_fixed,
+                                        uint8_t* ignored_rows) {
+  if (!lp || !xbar || !xhat) {
+    set_error("null argument");
+    return SCYLLA_ERR_INVALID_ARG;
+  }
+  for (int64_t j = 0; j < lp->n0; ++j)
+    if (std::isnan(xbar[j])) {
+      set_error("xbar has NaN at " + std::to_string(j));
+      return SCYLLA_ERR_INVALID_ARG;
+    }
+  return fix_and_propagate_host(*lp, xbar, xhat, dom_lo, dom_hi, fixed_cols, n_fixed, ignored_rows);
+}
+
+extern "C" int scylla_check_feasible(const scylla_lp* lp, const double* x, int32_t* feasible) {
+  if (!lp || !x || !feasible) {
+    set_error("null argument");
+    return SCYLLA_ERR_INVALID_ARG;
+  }
+  *feasible = check_feasible_host(*lp, x) ? 1 : 0;
+  return SCYLLA_OK;
+}
+
+extern "C" int scylla_perturb(const scylla_lp* lp, double* xhat, const double* xbar, int32_t kind, int64_t K,
+                              uint64_t seed, int64_t* flipped) {
+  if (!lp || !xhat || !xbar || (kind != 1 && kind != 2)) {
+    set_error("invalid argument");
+    return SCYLLA_ERR_INVALID_ARG;
+  }
+  const int64_t f = perturb_host(*lp, xhat, xbar, kind, K, seed);
+  if (flipped) *flipped = f;
+  return SCYLLA_OK;
+}

@@ -1,0 +1,176 @@
+// Internal declarations of the GB300 Scylla PDHG library.
+//
+// Layout in HBM (all in the preconditioned space unless noted):
+//   A   : CSR over rows    (rowptr int32[m+1], cols int32[nnz], vals T[nnz] (+FP64 copy))
+//   A^T : CSR over columns (same nonzeros, rows ascending within a column)
+//   warp tiles: contiguous row ranges with <= kTileNnz nonzeros and <= 32 rows,
+//               or a single longer row (processed by one warp).
+//   iterate pools: X[3], Y[3], AX[3] (roles cur/next/avg chosen by indices in the
+//   device control block), ATY[2] (cur/avg), XLR, YLR (last restart point).
+// Arrays that are read with 16-byte vector loads are padded to a multiple of 4
+// elements plus 4, so an aligned vector starting before the end stays in bounds.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "scylla.h"
+
+namespace scylla {
+
+constexpr int kWarpsPerBlock = 8;
+constexpr int kThreads = kWarpsPerBlock * 32;
+constexpr int kTileNnz = 256;  // nonzeros per multi-row warp tile
+constexpr int kTileRows = 32;  // rows per multi-row warp tile (one lane per row)
+constexpr int kVec = 4;        // elements per lane per vector load
+constexpr int kSmemPerWarp = kTileNnz + kTileNnz / 32 + 8;  // skewed product buffer
+
+// per-block partial sums written by each kernel
+constexpr int kNP = 1;    // primal: ||dx||^2
+constexpr int kND = 2;    // dual: ||dy||^2, dy.(A x' - A x)
+constexpr int kNC1 = 10;  // column check: 5 sums x {current, average}
+constexpr int kNC2 = 8;   // row check: 4 sums x {current, average}
+
+// Device control block: every decision of the solve is taken on the device and
+// kept here, so the iteration loop needs no host round trip.
+struct Control {
+  double eta, omega, eta_used, wsum, avg_w, tol;
+  double kkt_lr, kkt_prev;
+  double offset, bnorm, cnorm;
+  double eps_p, eps_d, eps_g, rel_kkt, pobj, dobj;  // of the reported point
+  double beta_s, beta_n, beta_a, theta, exp_red, exp_grow;
+  long long k, iter_limit, k_lr, accepted, rejected, restarts, chunks, max_chunks;
+  unsigned long long hash_accum, last_hash;
+  int same_hash, stall_checks;
+  int ix_cur, ix_next, ix_avg, ia_cur, ia_avg;
+  int aty_valid, copy_lr, done, status, used_avg, initial;
+  int adaptive, restarts_on, pw_update;
+  unsigned int cnt_dual, cnt_c2, cnt_misc;
+};
+
+// Pointers of one LP, passed by value to every kernel.  T is the type of the bulk
+// iteration (double or float); the FP64 members are used by the checks.
+template <typename T>
+struct DevLP {
+  int m, n;
+  const int* a_rowptr;
+  const int* a_cols;
+  const int* a_tiles;
+  int a_ntiles;
+  const T* a_vals;
+  const double* a_vals64;
+  const int* t_rowptr;
+  const int* t_cols;
+  const int* t_tiles;
+  int t_ntiles;
+  const T* t_vals;
+  const double* t_vals64;
+  const T *c, *l, *u, *lo, *hi;
+  const double *c64, *l64, *u64, *lo64, *hi64, *R, *C;
+  const unsigned char* int_mask;
+  T* X[3];
+  T* Y[3];
+  T* AX[3];
+  T* ATY[2];
+  T* XLR;
+  T* YLR;
+  Control* ctl;
+  double *part_p, *part_d, *part_c1, *part_c2;
+  int grid_p, grid_d, grid_c1, grid_c2;
+};
+
+// Buffers of the original (unaugmented) columns used by the objective update and
+// by setup; all device pointers.
+struct DevSetup {
+  int m, n;           // augmented sizes
+  int n_orig, m_orig; // original sizes
+  int nnz;
+  const int* a_rowptr;
+  const int* a_cols;
+  const int* t_rowptr;
+  const int* t_cols;
+  double* a_vals64;  // in: original values; out: scaled values
+  double* t_vals64;
+  float* a_vals32;   // may be null
+  float* t_vals32;
+  double* R;
+  double* C;
+  double* R2;  // ping-pong scratch
+  double* C2;
+  double* red;  // reduction scratch
+  int red_blocks;
+};
+
+// ---- kernel launchers (kernels.cu) -------------------------------------------
+cudaError_t launch_precondition(const DevSetup& s, int ruiz_iters, bool pock_chambolle, cudaStream_t st);
+cudaError_t launch_scale_values(const DevSetup& s, cudaStream_t st);
+// max |a~|, sum a~^2 over the scaled A values -> host
+cudaError_t matrix_norms(const DevSetup& s, cudaStream_t st, double* amax, double* fro2);
+
+struct DevVecs {
+  // unscaled originals (FP64), augmented sizes
+  const double *c, *lo, *hi, *l, *u;
+  // scaled outputs
+  double *c64, *lo64, *hi64, *l64, *u64;
+  float *c32, *lo32, *hi32, *l32, *u32;  // null in FP64 mode
+  const double *R, *C;
+  int m, n;
+};
+cudaError_t launch_scale_vectors(const DevVecs& v, cudaStream_t st);
+
+// Objective update of round K (Section 2.4) on the device.
+struct DevObjective {
+  int n_orig, m_orig, n, m;
+  const double* c_orig;  // original c (n_orig)
+  const double* l_orig;
+  const double* u_orig;
+  const int* kind;       // 0 continuous, 1 integer with u-l = 1, 2 general integer (aux)
+  const int* aux_of;     // aux index t of a general integer column, else -1
+  const double* xhat;    // n_orig
+  double* chat;          // unscaled c_hat (n)
+  double* lo_unscaled;   // unscaled row lower bounds (m); aux rows updated
+  const double* hi_unscaled;
+  const double* R;
+  const double* C;
+  double* c64;
+  double* lo64;
+  float* c32;
+  float* lo32;
+  double* red;
+  int red_blocks;
+  Control* ctl;
+};
+cudaError_t launch_objective_update(const DevObjective& o, double t_scale, double one_minus_aK,
+                                    cudaStream_t st);
+// ||c||, ||b|| (unscaled) and the offset into the control block, without changing c.
+cudaError_t launch_objective_norms(const DevObjective& o, double offset, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_solve_init(const DevLP<T>& d, double tol, long long iter_limit, int stall_checks,
+                              long long max_chunks, cudaStream_t st);
+template <typename T>
+cudaError_t launch_check(const DevLP<T>& d, cudaStream_t st);
+template <typename T>
+cudaError_t launch_slot(const DevLP<T>& d, cudaStream_t st);
+cudaError_t launch_loop_ctl(Control* ctl, cudaGraphConditionalHandle h, cudaStream_t st);
+template <typename T>
+cudaError_t launch_get_x(const DevLP<T>& d, double* out, int count, cudaStream_t st);
+template <typename T>
+cudaError_t launch_get_y(const DevLP<T>& d, double* out, int count, cudaStream_t st);
+template <typename T>
+cudaError_t launch_set_xy(const DevLP<T>& d, const double* x, const double* y, cudaStream_t st);
+template <typename T>
+cudaError_t launch_init_point(const DevLP<T>& d, cudaStream_t st);
+template <typename T>
+int occupancy_grid(int kernel_id, int work_tiles);  // kernel_id: 0 primal, 1 dual, 2 c1, 3 c2
+
+int device_sm_count();
+
+// ---- host helpers -------------------------------------------------------------
+void set_error(const std::string& msg);
+const char* get_error();
+
+}  // namespace scylla

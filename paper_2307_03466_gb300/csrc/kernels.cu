@@ -1,0 +1,1064 @@
+// sm_103a kernels of the PDHG hot path of Scylla (arXiv 2307.03466, Algorithm 1,
+// Sections 2.1-2.2 and 2.4).
+//
+// One PDHG attempt is two launches:
+//   k_primal : (A^T y)_j by a warp-tile gather over the stored transpose, fused with
+//              x'_j = proj_[l,u](x_j + tau_x (A^T y - c)_j)  (Algorithm 1, primal
+//              step), the pending iterate-average update and ||x' - x||^2.
+//   k_dual   : (A x')_i by the same gather over A, fused with the extrapolated dual
+//              step y'_i = prox(y_i + tau_y (b - A(2x' - x))_i)  (Algorithm 1, dual
+//              step), the average update, ||y' - y||^2 and (y'-y).(A x' - A x); its
+//              last block takes the adaptive step-size decision.
+// Every n_check attempts two check launches evaluate the current and the averaged
+// iterate in FP64 (Section 2.2: relative KKT error, termination; PDLP restarts)
+// and refresh the cached products A x and A^T y from FP64 matrix values.
+// All decisions live in the device control block; launches read it and return
+// early once the solve is done, so the loop can run inside one CUDA graph.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace scylla {
+
+// ------------------------------------------------------------------ helpers ---
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void ld4(const int* p, int (&o)[4]) {
+  const int4 t = __ldg(reinterpret_cast<const int4*>(p));
+  o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
+  const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+
+__device__ __forceinline__ int skew(int q) { return q + (q >> 5); }
+
+template <typename T>
+__device__ __forceinline__ T clampv(T v, T lo, T hi) {
+  v = v < lo ? lo : v;
+  return v > hi ? hi : v;
+}
+template <typename T>
+__device__ __forceinline__ T fma_t(T a, T b, T c);
+template <>
+__device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <>
+__device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// running average x_avg <- (1-w) x_avg + w x, in one fixed rounding sequence
+template <typename T>
+__device__ __forceinline__ T blend(T a, T x, T w1, T w) { return fma_t<T>(w1, a, w * x); }
+
+template <typename T>
+__device__ __forceinline__ T pos_inf();
+template <>
+__device__ __forceinline__ double pos_inf<double>() { return __longlong_as_double(0x7ff0000000000000ULL); }
+template <>
+__device__ __forceinline__ float pos_inf<float>() { return __int_as_float(0x7f800000); }
+
+// Dual step of Algorithm 1 for a row with bounds [lo, hi] (the proximal step of
+// the row-bound support function); lo = b, hi = +inf gives max(0, y + s (b - axt)).
+template <typename T>
+__device__ __forceinline__ T dual_prox(T y, T sigma, T axt, T lo, T hi) {
+  const T inf = pos_inf<T>();
+  if (lo > -inf) {
+    const T t = y + sigma * (lo - axt);
+    if (t > T(0)) return t;
+  }
+  if (hi < inf) {
+    const T t = y + sigma * (hi - axt);
+    if (t < T(0)) return t;
+  }
+  return T(0);
+}
+
+// lambda = projection of the reduced cost r onto the sign cone of the column bounds
+__device__ __forceinline__ double rc_proj(double r, double l, double u) {
+  const double inf = pos_inf<double>();
+  const bool lf = l > -inf, uf = u < inf;
+  if (lf && uf) return r;
+  if (lf) return r > 0.0 ? r : 0.0;
+  if (uf) return r < 0.0 ? r : 0.0;
+  return 0.0;
+}
+
+// SplitMix64 output function (Steele, Lea, Flood 2014)
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ unsigned long long round_hash(long long j, double v) {
+  double r = floor(v + 0.5);
+  const double lim = 4611686018427387904.0;  // 2^62
+  r = r < -lim ? -lim : (r > lim ? lim : r);
+  const unsigned long long key =
+      (unsigned long long)j * 0x9E3779B97F4A7C15ULL + (unsigned long long)(long long)r;
+  return mix64(key);
+}
+
+// per-block reduction of N partial sums into part[blockIdx.x * N + k], fixed order
+template <int N>
+__device__ __forceinline__ void block_store_partials(const double (&v)[N], double* __restrict__ part) {
+  __shared__ double sh[kWarpsPerBlock][N];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const double t = warp_sum(v[k]);
+    if (lane == 0) sh[w][k] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < kWarpsPerBlock; ++i) s += sh[i][threadIdx.x];
+    part[blockIdx.x * N + threadIdx.x] = s;
+  }
+}
+
+__device__ __forceinline__ bool is_last_block(unsigned int* counter) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (last) __threadfence();
+  return last != 0;
+}
+
+// sum of N partial vectors over nblocks blocks, by the whole (last) block, fixed order
+template <int N>
+__device__ void reduce_partials(const double* part, int nblocks, double* out_shared) {
+  __shared__ double sh[kWarpsPerBlock];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k = 0; k < N; ++k) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += __ldcg(part + b * N + k);
+    s = warp_sum(s);
+    if (lane == 0) sh[w] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int i = 0; i < kWarpsPerBlock; ++i) t += sh[i];
+      out_shared[k] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------- the SpMV core ---
+// Warp-tile CSR gather: each warp takes tiles round-robin.  A multi-row tile (at
+// most kTileNnz nonzeros, at most 32 rows) is streamed with 16-byte vector loads of
+// column indices and values (aligned down to the vector boundary and masked),
+// products go to a skewed per-warp shared buffer, and lane r sums row r in CSR
+// order.  A single long row is reduced across the warp with shuffles.  The
+// epilogue runs once per row, on one lane.
+template <int NV, typename Acc, typename V, typename Gather, typename Epi>
+__device__ __forceinline__ void spmv_tiles(const int* __restrict__ tiles, int ntiles,
+                                           const int* __restrict__ rowptr, const int* __restrict__ cols,
+                                           const V* __restrict__ vals, Gather& gat, Epi& epi,
+                                           Acc* __restrict__ sm) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int t = gwarp; t < ntiles; t += nwarps) {
+    const int r0 = __ldg(tiles + t), r1 = __ldg(tiles + t + 1);
+    const int p0 = __ldg(rowptr + r0), p1 = __ldg(rowptr + r1);
+    const int base = p0 & ~(kVec - 1);
+    if (r1 - r0 == 1 && p1 - p0 > kTileNnz) {
+      Acc s[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) s[k] = Acc(0);
+      for (int p = base + lane * kVec; p < p1; p += 32 * kVec) {
+        int c[4];
+        V v[4];
+        ld4(cols + p, c);
+        ld4(vals + p, v);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int q = p + e;
+          if (q >= p0 && q < p1) {
+            Acc g[NV];
+            gat(c[e], g);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) s[k] = fma_t<Acc>(Acc(v[e]), g[k], s[k]);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NV; ++k) s[k] = warp_sum(s[k]);
+      if (lane == 0) epi(r0, s);
+    } else {
+      for (int p = base + lane * kVec; p < p1; p += 32 * kVec) {
+        int c[4];
+        V v[4];
+        ld4(cols + p, c);
+        ld4(vals + p, v);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int q = p + e;
+          if (q >= p0 && q < p1) {
+            Acc g[NV];
+            gat(c[e], g);
+            const int o = skew(q - p0);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) sm[k * kSmemPerWarp + o] = Acc(v[e]) * g[k];
+          }
+        }
+      }
+      __syncwarp();
+      if (lane < r1 - r0) {
+        const int row = r0 + lane;
+        const int q0 = __ldg(rowptr + row) - p0, q1 = __ldg(rowptr + row + 1) - p0;
+        Acc s[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[k] = Acc(0);
+        for (int q = q0; q < q1; ++q) {
+          const int o = skew(q);
+#pragma unroll
+          for (int k = 0; k < NV; ++k) s[k] += sm[k * kSmemPerWarp + o];
+        }
+        epi(row, s);
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// ------------------------------------------------------------- step control ---
+// Adaptive step (PDLP): eta_max = (omega ||dx||^2 + ||dy||^2 / omega) / (2 |dy.A dx|);
+// eta' = min((1 - (k+1)^-0.3) eta_max, (1 + (k+1)^-0.6) eta), k the 1-based attempt
+// number; the attempt is accepted when eta <= eta_max.
+__device__ void step_control(Control* c, double dx2, double dy2, double inter) {
+  if (!isfinite(dx2) || !isfinite(dy2) || !isfinite(inter)) {
+    c->done = 1;
+    c->status = SCYLLA_NUMERICAL;
+    return;
+  }
+  const long long k1 = c->k + 1;
+  const double eta = c->eta, om = c->omega;
+  bool accept = true;
+  double eta_next = eta;
+  if (c->adaptive) {
+    const double mv = om * dx2 + dy2 / om;
+    const double eta_max = inter != 0.0 ? mv / (2.0 * fabs(inter)) : pos_inf<double>();
+    const double kk = double(k1 + 1);
+    eta_next = fmin((1.0 - pow(kk, -c->exp_red)) * eta_max, (1.0 + pow(kk, -c->exp_grow)) * eta);
+    accept = eta <= eta_max;
+  }
+  c->k = k1;
+  c->eta_used = eta;
+  c->eta = eta_next;
+  c->copy_lr = 0;
+  if (accept) {
+    const int t = c->ix_cur;
+    c->ix_cur = c->ix_next;
+    c->ix_next = t;
+    c->aty_valid = 0;
+    c->wsum += eta;
+    c->avg_w = eta / c->wsum;
+    c->accepted++;
+  } else {
+    c->aty_valid = 1;
+    c->avg_w = 0.0;
+    c->rejected++;
+  }
+}
+
+// ---------------------------------------------------------------- PDHG slot ---
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_primal(DevLP<T> d) {
+  Control* ctl = d.ctl;
+  if (ctl->done || ctl->k >= ctl->iter_limit) return;
+  __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
+  const int cur = ctl->ix_cur, nxt = ctl->ix_next, avg = ctl->ix_avg;
+  const T tau = T(ctl->eta / ctl->omega);
+  const double wd = ctl->avg_w;
+  const T w = T(wd), w1 = T(1.0 - wd);
+  const bool do_avg = wd > 0.0, copy_lr = ctl->copy_lr != 0, aty_valid = ctl->aty_valid != 0;
+  const T* __restrict__ xc = d.X[cur];
+  T* __restrict__ xn = d.X[nxt];
+  T* __restrict__ xa = d.X[avg];
+  const T* __restrict__ yc = d.Y[cur];
+  T* __restrict__ aty = d.ATY[ctl->ia_cur];
+  T* __restrict__ xlr = d.XLR;
+  const T* __restrict__ cc = d.c;
+  const T* __restrict__ ll = d.l;
+  const T* __restrict__ uu = d.u;
+  double acc[kNP] = {0.0};
+  auto epi = [&](int j, T s) {
+    const T x = xc[j];
+    if (do_avg) xa[j] = blend(xa[j], x, w1, w);
+    if (copy_lr) xlr[j] = x;
+    const T v = clampv<T>(x + tau * (s - cc[j]), ll[j], uu[j]);
+    xn[j] = v;
+    const double dx = double(v) - double(x);
+    acc[0] += dx * dx;
+  };
+  if (aty_valid) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += gridDim.x * blockDim.x) epi(j, aty[j]);
+  } else {
+    auto gat = [&](int i, T(&g)[1]) { g[0] = __ldg(yc + i); };
+    auto epi1 = [&](int j, T(&s)[1]) {
+      aty[j] = s[0];
+      epi(j, s[0]);
+    };
+    spmv_tiles<1, T, T>(d.t_tiles, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals, gat, epi1,
+                        sm + (threadIdx.x >> 5) * kSmemPerWarp);
+  }
+  block_store_partials<kNP>(acc, d.part_p);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_dual(DevLP<T> d) {
+  Control* ctl = d.ctl;
+  if (ctl->done || ctl->k >= ctl->iter_limit) return;
+  __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
+  const int cur = ctl->ix_cur, nxt = ctl->ix_next, avg = ctl->ix_avg;
+  const T sigma = T(ctl->eta * ctl->omega);
+  const double wd = ctl->avg_w;
+  const T w = T(wd), w1 = T(1.0 - wd);
+  const bool do_avg = wd > 0.0, copy_lr = ctl->copy_lr != 0;
+  const T* __restrict__ xn = d.X[nxt];
+  const T* __restrict__ axc = d.AX[cur];
+  T* __restrict__ axn = d.AX[nxt];
+  const T* __restrict__ yc = d.Y[cur];
+  T* __restrict__ yn = d.Y[nxt];
+  T* __restrict__ ya = d.Y[avg];
+  T* __restrict__ ylr = d.YLR;
+  const T* __restrict__ lo = d.lo;
+  const T* __restrict__ hi = d.hi;
+  double acc[kND] = {0.0, 0.0};
+  auto gat = [&](int j, T(&g)[1]) { g[0] = __ldg(xn + j); };
+  auto epi = [&](int i, T(&s)[1]) {
+    const T ax_new = s[0];
+    const T ax = axc[i];
+    const T y = yc[i];
+    if (do_avg) ya[i] = blend(ya[i], y, w1, w);
+    if (copy_lr) ylr[i] = y;
+    const T axt = T(2) * ax_new - ax;
+    const T v = dual_prox<T>(y, sigma, axt, lo[i], hi[i]);
+    yn[i] = v;
+    axn[i] = ax_new;
+    const double dy = double(v) - double(y);
+    acc[0] += dy * dy;
+    acc[1] += dy * (double(ax_new) - double(ax));
+  };
+  spmv_tiles<1, T, T>(d.a_tiles, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals, gat, epi,
+                      sm + (threadIdx.x >> 5) * kSmemPerWarp);
+  block_store_partials<kND>(acc, d.part_d);
+  if (!is_last_block(&ctl->cnt_dual)) return;
+  __shared__ double red[kNP + kND];
+  reduce_partials<kNP>(d.part_p, d.grid_p, red);
+  reduce_partials<kND>(d.part_d, d.grid_d, red + kNP);
+  if (threadIdx.x == 0) {
+    step_control(ctl, red[0], red[1], red[2]);
+    ctl->cnt_dual = 0;
+  }
+}
+
+// ------------------------------------------------------------------ checks ---
+struct Eval {
+  double rp_s2, rd_s2, rp2, rd2, pobj, dobj, dx2, dy2;
+  double eps_p, eps_d, eps_g, rel;
+};
+
+__device__ __forceinline__ double weighted_kkt(const Eval& e, double om) {
+  const double g = e.pobj - e.dobj;
+  return sqrt(om * om * e.rp_s2 + e.rd_s2 / (om * om) + g * g);
+}
+
+__device__ void finish(Control* c, int status, bool out_avg, const Eval& e) {
+  c->done = 1;
+  c->status = status;
+  c->used_avg = out_avg ? 1 : 0;
+  c->eps_p = e.eps_p;
+  c->eps_d = e.eps_d;
+  c->eps_g = e.eps_g;
+  c->rel_kkt = e.rel;
+  c->pobj = e.pobj;
+  c->dobj = e.dobj;
+  if (out_avg) {
+    int t = c->ix_cur;
+    c->ix_cur = c->ix_avg;
+    c->ix_avg = t;
+    t = c->ia_cur;
+    c->ia_cur = c->ia_avg;
+    c->ia_avg = t;
+  }
+}
+
+// Termination (Section 2.2), stalling (Algorithm 1) and restarts (PDLP) from the
+// 18 reduced sums of the two check kernels.
+__device__ void check_control(Control* c, const double* r) {
+  Eval e[2];
+  for (int q = 0; q < 2; ++q) {
+    const double* cs = r + 5 * q;
+    const double* rs = r + kNC1 + 4 * q;
+    e[q].rd_s2 = cs[0];
+    e[q].rd2 = cs[1];
+    e[q].pobj = cs[2] + c->offset;
+    e[q].dobj = (rs[2] + cs[3]) + c->offset;
+    e[q].dx2 = cs[4];
+    e[q].rp_s2 = rs[0];
+    e[q].rp2 = rs[1];
+    e[q].dy2 = rs[3];
+    e[q].eps_p = sqrt(e[q].rp2) / (1.0 + c->bnorm);
+    e[q].eps_d = sqrt(e[q].rd2) / (1.0 + c->cnorm);
+    e[q].eps_g = fabs(e[q].pobj - e[q].dobj) / (1.0 + fabs(e[q].pobj) + fabs(e[q].dobj));
+    e[q].rel = fmax(e[q].eps_p, fmax(e[q].eps_d, e[q].eps_g));
+  }
+  const unsigned long long h = c->hash_accum;
+  c->hash_accum = 0ULL;
+  c->aty_valid = 1;
+  if (c->initial) {
+    c->initial = 0;
+    c->avg_w = 0.0;
+    const double kc = weighted_kkt(e[0], c->omega);
+    c->kkt_lr = kc;
+    c->kkt_prev = kc;
+    c->k_lr = 0;
+    c->copy_lr = 1;
+    c->last_hash = h;
+    c->same_hash = 0;
+    c->eps_p = e[0].eps_p; c->eps_d = e[0].eps_d; c->eps_g = e[0].eps_g;
+    c->rel_kkt = e[0].rel; c->pobj = e[0].pobj; c->dobj = e[0].dobj;
+    if (isnan(e[0].rel)) finish(c, SCYLLA_NUMERICAL, false, e[0]);
+    else if (e[0].rel <= c->tol) finish(c, SCYLLA_CONVERGED, false, e[0]);
+    else if (c->iter_limit <= 0) finish(c, SCYLLA_ITER_LIMIT, false, e[0]);
+    return;
+  }
+  const bool has_avg = c->wsum > 0.0;
+  c->avg_w = 0.0;
+  const bool out_avg = has_avg && e[1].rel < e[0].rel;
+  const Eval& eo = out_avg ? e[1] : e[0];
+  c->eps_p = eo.eps_p; c->eps_d = eo.eps_d; c->eps_g = eo.eps_g;
+  c->rel_kkt = eo.rel; c->pobj = eo.pobj; c->dobj = eo.dobj;
+  if (isnan(e[0].rel)) { finish(c, SCYLLA_NUMERICAL, false, e[0]); return; }
+  if (eo.rel <= c->tol) { finish(c, SCYLLA_CONVERGED, out_avg, eo); return; }
+  if (c->k >= c->iter_limit) { finish(c, SCYLLA_ITER_LIMIT, out_avg, eo); return; }
+  c->same_hash = (h == c->last_hash) ? c->same_hash + 1 : 0;
+  c->last_hash = h;
+  if (c->stall_checks > 0 && c->same_hash >= c->stall_checks) { finish(c, SCYLLA_STALLED, out_avg, eo); return; }
+  if (!c->restarts_on) return;
+  const double om = c->omega;
+  const double kc_cur = weighted_kkt(e[0], om);
+  const bool cand_avg = has_avg && weighted_kkt(e[1], om) < kc_cur;
+  const Eval& ec = cand_avg ? e[1] : e[0];
+  const double kc = weighted_kkt(ec, om);
+  const bool restart = kc <= c->beta_s * c->kkt_lr || (kc <= c->beta_n * c->kkt_lr && kc > c->kkt_prev) ||
+                       double(c->k - c->k_lr) >= c->beta_a * double(c->k);
+  if (!restart) {
+    c->kkt_prev = kc;
+    return;
+  }
+  c->restarts++;
+  if (c->pw_update) {
+    const double ddx = sqrt(ec.dx2), ddy = sqrt(ec.dy2);
+    if (ddx > 1e-10 && ddy > 1e-10)
+      c->omega = exp(c->theta * log(ddy / ddx) + (1.0 - c->theta) * log(om));
+  }
+  if (cand_avg) {
+    int t = c->ix_cur;
+    c->ix_cur = c->ix_avg;
+    c->ix_avg = t;
+    t = c->ia_cur;
+    c->ia_cur = c->ia_avg;
+    c->ia_avg = t;
+  }
+  c->k_lr = c->k;
+  c->wsum = 0.0;
+  c->copy_lr = 1;
+  c->kkt_lr = weighted_kkt(ec, c->omega);
+  c->kkt_prev = c->kkt_lr;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_check_cols(DevLP<T> d) {
+  Control* ctl = d.ctl;
+  if (ctl->done) return;
+  __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];
+  const int cur = ctl->ix_cur, avg = ctl->ix_avg;
+  const double wd = ctl->avg_w;
+  const T w = T(wd), w1 = T(1.0 - wd);
+  const bool do_avg = wd > 0.0;
+  const T* __restrict__ yc = d.Y[cur];
+  const T* __restrict__ ya = d.Y[avg];
+  const T* __restrict__ xc = d.X[cur];
+  T* __restrict__ xa = d.X[avg];
+  T* __restrict__ aty_c = d.ATY[ctl->ia_cur];
+  T* __restrict__ aty_a = d.ATY[ctl->ia_avg];
+  double acc[kNC1];
+#pragma unroll
+  for (int k = 0; k < kNC1; ++k) acc[k] = 0.0;
+  unsigned long long h = 0ULL;
+  auto gat = [&](int i, double(&g)[2]) {
+    const T y = yc[i];
+    T v = ya[i];
+    if (do_avg) v = blend(v, y, w1, w);
+    g[0] = double(y);
+    g[1] = double(v);
+  };
+  auto epi = [&](int j, double(&s)[2]) {
+    const T x = xc[j];
+    T xav = xa[j];
+    if (do_avg) {
+      xav = blend(xav, x, w1, w);
+      xa[j] = xav;
+    }
+    aty_c[j] = T(s[0]);
+    aty_a[j] = T(s[1]);
+    const double Cj = d.C[j], cj = d.c64[j], lj = d.l64[j], uj = d.u64[j], xl = double(d.XLR[j]);
+    const double xs[2] = {double(x), double(xav)};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const double r = cj - s[q];
+      const double lam = rc_proj(r, lj, uj);
+      const double rd = r - lam;
+      acc[5 * q + 0] += rd * rd;
+      const double rdu = rd / Cj;
+      acc[5 * q + 1] += rdu * rdu;
+      acc[5 * q + 2] += cj * xs[q];
+      acc[5 * q + 3] += (lam > 0.0 ? lj * lam : 0.0) - (lam < 0.0 ? uj * (-lam) : 0.0);
+      const double dd = xs[q] - xl;
+      acc[5 * q + 4] += dd * dd;
+    }
+    if (d.int_mask[j]) h += round_hash(j, double(x) * Cj);
+  };
+  spmv_tiles<2, double, double>(d.t_tiles, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals64, gat, epi,
+                                sm + (threadIdx.x >> 5) * 2 * kSmemPerWarp);
+  block_store_partials<kNC1>(acc, d.part_c1);
+  h = warp_sum_u64(h);
+  if ((threadIdx.x & 31) == 0 && h != 0ULL) atomicAdd(&ctl->hash_accum, h);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_check_rows(DevLP<T> d) {
+  Control* ctl = d.ctl;
+  if (ctl->done) return;
+  __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];
+  const int cur = ctl->ix_cur, avg = ctl->ix_avg;
+  const double wd = ctl->avg_w;
+  const T w = T(wd), w1 = T(1.0 - wd);
+  const bool do_avg = wd > 0.0;
+  const T* __restrict__ xc = d.X[cur];
+  const T* __restrict__ xa = d.X[avg];
+  const T* __restrict__ yc = d.Y[cur];
+  T* __restrict__ ya = d.Y[avg];
+  T* __restrict__ ax_c = d.AX[cur];
+  T* __restrict__ ax_a = d.AX[avg];
+  double acc[kNC2];
+#pragma unroll
+  for (int k = 0; k < kNC2; ++k) acc[k] = 0.0;
+  auto gat = [&](int j, double(&g)[2]) {
+    g[0] = double(xc[j]);
+    g[1] = double(xa[j]);
+  };
+  auto epi = [&](int i, double(&s)[2]) {
+    const T y = yc[i];
+    T yav = ya[i];
+    if (do_avg) {
+      yav = blend(yav, y, w1, w);
+      ya[i] = yav;
+    }
+    ax_c[i] = T(s[0]);
+    ax_a[i] = T(s[1]);
+    const double Ri = d.R[i], lo = d.lo64[i], hi = d.hi64[i], yl = double(d.YLR[i]);
+    const double ys[2] = {double(y), double(yav)};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const double rps = s[q] - clampv<double>(s[q], lo, hi);
+      acc[4 * q + 0] += rps * rps;
+      const double rp = rps / Ri;
+      acc[4 * q + 1] += rp * rp;
+      acc[4 * q + 2] += (ys[q] > 0.0 ? lo * ys[q] : 0.0) - (ys[q] < 0.0 ? hi * (-ys[q]) : 0.0);
+      const double dd = ys[q] - yl;
+      acc[4 * q + 3] += dd * dd;
+    }
+  };
+  spmv_tiles<2, double, double>(d.a_tiles, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals64, gat, epi,
+                                sm + (threadIdx.x >> 5) * 2 * kSmemPerWarp);
+  block_store_partials<kNC2>(acc, d.part_c2);
+  if (!is_last_block(&ctl->cnt_c2)) return;
+  __shared__ double red[kNC1 + kNC2];
+  reduce_partials<kNC1>(d.part_c1, d.grid_c1, red);
+  reduce_partials<kNC2>(d.part_c2, d.grid_c2, red + kNC1);
+  if (threadIdx.x == 0) {
+    check_control(ctl, red);
+    ctl->cnt_c2 = 0;
+  }
+}
+
+__global__ void k_loop_ctl(Control* c, cudaGraphConditionalHandle h) {
+  c->chunks++;
+  if (!c->done && c->chunks >= c->max_chunks) {
+    // safety net: the check at the iteration limit ends every solve before this
+    c->done = 1;
+    c->status = SCYLLA_ITER_LIMIT;
+  }
+  cudaGraphSetConditional(h, c->done ? 0u : 1u);
+}
+
+__global__ void k_solve_init(Control* c, double tol, long long iter_limit, int stall_checks,
+                             long long max_chunks) {
+  c->tol = tol;
+  c->iter_limit = iter_limit;
+  c->stall_checks = stall_checks;
+  c->max_chunks = max_chunks;
+  c->k = 0;
+  c->k_lr = 0;
+  c->wsum = 0.0;
+  c->avg_w = 0.0;
+  c->done = 0;
+  c->status = -1;
+  c->used_avg = 0;
+  c->accepted = c->rejected = c->restarts = 0;
+  c->chunks = 0;
+  c->initial = 1;
+  c->aty_valid = 0;
+  c->copy_lr = 0;
+  c->hash_accum = 0ULL;
+  c->same_hash = 0;
+  c->cnt_dual = c->cnt_c2 = c->cnt_misc = 0;
+}
+
+// ------------------------------------------------------------ state access ---
+template <typename T>
+__global__ void k_get_x(DevLP<T> d, double* out, int count) {
+  const T* x = d.X[d.ctl->ix_cur];
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x)
+    out[j] = double(x[j]) * d.C[j];
+}
+template <typename T>
+__global__ void k_get_y(DevLP<T> d, double* out, int count) {
+  const T* y = d.Y[d.ctl->ix_cur];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+    out[i] = double(y[i]) * d.R[i];
+}
+template <typename T>
+__global__ void k_set_xy(DevLP<T> d, const double* x, const double* y) {
+  T* xc = d.X[d.ctl->ix_cur];
+  T* yc = d.Y[d.ctl->ix_cur];
+  const int stride = gridDim.x * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += stride) xc[j] = T(x[j] / d.C[j]);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) yc[i] = T(y[i] / d.R[i]);
+}
+// x = proj_[l,u](0), y = 0 (Algorithm 1 initialisation, x projected onto its box)
+template <typename T>
+__global__ void k_init_point(DevLP<T> d) {
+  T* xc = d.X[d.ctl->ix_cur];
+  T* yc = d.Y[d.ctl->ix_cur];
+  const int stride = gridDim.x * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += stride)
+    xc[j] = T(clampv<double>(0.0, d.l64[j], d.u64[j]));
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) yc[i] = T(0);
+}
+
+// ----------------------------------------------------------- preconditioning ---
+// Ruiz pass: R'_i = R_i / sqrt(max_j (R_i |a_ij|) C_j), C'_j likewise, both from the
+// same (R, C); a zero maximum leaves the multiplier unchanged.
+__global__ void k_ruiz_rows(int m, const int* rowptr, const int* cols, const double* vals, const double* R,
+                            const double* C, double* Rout) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    double mx = 0.0;
+    const double ri = R[i];
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) mx = fmax(mx, (ri * fabs(vals[p])) * C[cols[p]]);
+    Rout[i] = mx > 0.0 ? ri / sqrt(mx) : ri;
+  }
+}
+__global__ void k_ruiz_cols(int n, const int* colptr, const int* rows, const double* vals, const double* R,
+                            const double* C, double* Cout) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double mx = 0.0;
+    const double cj = C[j];
+    for (int p = colptr[j]; p < colptr[j + 1]; ++p) mx = fmax(mx, (R[rows[p]] * fabs(vals[p])) * cj);
+    Cout[j] = mx > 0.0 ? cj / sqrt(mx) : cj;
+  }
+}
+// Pock-Chambolle (alpha = 1): R'_i = R_i / sqrt(sum_j (R_i |a_ij|) C_j), C'_j likewise.
+__global__ void k_pc_rows(int m, const int* rowptr, const int* cols, const double* vals, const double* R,
+                          const double* C, double* Rout) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    const double ri = R[i];
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) s += (ri * fabs(vals[p])) * C[cols[p]];
+    Rout[i] = s > 0.0 ? ri / sqrt(s) : ri;
+  }
+}
+__global__ void k_pc_cols(int n, const int* colptr, const int* rows, const double* vals, const double* R,
+                          const double* C, double* Cout) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    const double cj = C[j];
+    for (int p = colptr[j]; p < colptr[j + 1]; ++p) s += (R[rows[p]] * fabs(vals[p])) * cj;
+    Cout[j] = s > 0.0 ? cj / sqrt(s) : cj;
+  }
+}
+// a~_ij = (a_ij R_i) C_j in both CSR copies, plus FP32 shadows
+__global__ void k_scale_rows(int m, const int* rowptr, const int* cols, double* vals, float* vals32,
+                             const double* R, const double* C) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const double ri = R[i];
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      const double v = (vals[p] * ri) * C[cols[p]];
+      vals[p] = v;
+      if (vals32) vals32[p] = float(v);
+    }
+  }
+}
+__global__ void k_scale_cols(int n, const int* colptr, const int* rows, double* vals, float* vals32,
+                             const double* R, const double* C) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const double cj = C[j];
+    for (int p = colptr[j]; p < colptr[j + 1]; ++p) {
+      const double v = (vals[p] * R[rows[p]]) * cj;
+      vals[p] = v;
+      if (vals32) vals32[p] = float(v);
+    }
+  }
+}
+
+// two-pass reductions for setup: part[b] = (max |v|, sum v^2) over a grid-stride slice
+__global__ void k_norms_partial(const double* v, long long count, double* part) {
+  double mx = 0.0, s = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < count;
+       p += (long long)gridDim.x * blockDim.x) {
+    const double a = v[p];
+    mx = fmax(mx, fabs(a));
+    s += a * a;
+  }
+  __shared__ double smx[kThreads], ss[kThreads];
+  smx[threadIdx.x] = mx;
+  ss[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int t = 0; t < blockDim.x; ++t) {
+      a = fmax(a, smx[t]);
+      b += ss[t];
+    }
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+  }
+}
+
+__global__ void k_scale_vectors(DevVecs v) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.n; j += stride) {
+    const double cj = v.C[j];
+    const double c = v.c[j] * cj, l = v.l[j] / cj, u = v.u[j] / cj;
+    v.c64[j] = c;
+    v.l64[j] = l;
+    v.u64[j] = u;
+    if (v.c32) {
+      v.c32[j] = float(c);
+      v.l32[j] = float(l);
+      v.u32[j] = float(u);
+    }
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.m; i += stride) {
+    const double ri = v.R[i];
+    const double lo = v.lo[i] * ri, hi = v.hi[i] * ri;
+    v.lo64[i] = lo;
+    v.hi64[i] = hi;
+    if (v.lo32) {
+      v.lo32[i] = float(lo);
+      v.hi32[i] = float(hi);
+    }
+  }
+}
+
+// ------------------------------------------------------- objective update ---
+// c_hat_j = alpha^K s c_j + (1 - alpha^K) g_j (Algorithm 1, Section 2.4): g_j = +1
+// when xhat_j = l_j and -1 when xhat_j = u_j on integer columns with u - l = 1; a
+// general integer column keeps alpha^K s c_j and its auxiliary column gets cost
+// (1 - alpha^K) with auxiliary rows d - x >= -xhat_j, d + x >= xhat_j.
+// part[b] = (offset terms, sum c_hat^2) per block.
+__global__ void k_objective_cols(DevObjective o, double t, double om) {
+  double off = 0.0, c2 = 0.0;
+  const double inf = pos_inf<double>();
+  const int stride = gridDim.x * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < o.n; j += stride) {
+    double ch;
+    if (j < o.n_orig) {
+      double g = 0.0;
+      const int kd = o.kind[j];
+      if (kd == 1) {
+        const double xh = o.xhat[j];
+        if (xh == o.l_orig[j]) {
+          g = 1.0;
+          off -= om * o.l_orig[j];
+        } else if (xh == o.u_orig[j]) {
+          g = -1.0;
+          off += om * o.u_orig[j];
+        }
+      } else if (kd == 2) {
+        const int tq = o.aux_of[j];
+        const double xh = o.xhat[j];
+        const int r0 = o.m_orig + 2 * tq;
+        o.lo_unscaled[r0] = -xh;
+        o.lo_unscaled[r0 + 1] = xh;
+        const double l0 = -xh * o.R[r0], l1 = xh * o.R[r0 + 1];
+        o.lo64[r0] = l0;
+        o.lo64[r0 + 1] = l1;
+        if (o.lo32) {
+          o.lo32[r0] = float(l0);
+          o.lo32[r0 + 1] = float(l1);
+        }
+      }
+      ch = __fadd_rn(__dmul_rn(t, o.c_orig[j]), __dmul_rn(om, g));
+    } else {
+      ch = om;
+    }
+    o.chat[j] = ch;
+    const double cs = ch * o.C[j];
+    o.c64[j] = cs;
+    if (o.c32) o.c32[j] = float(cs);
+    c2 += ch * ch;
+  }
+  (void)inf;
+  __shared__ double s0[kThreads], s1[kThreads];
+  s0[threadIdx.x] = off;
+  s1[threadIdx.x] = c2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < blockDim.x; ++q) {
+      a += s0[q];
+      b += s1[q];
+    }
+    o.red[2 * blockIdx.x] = a;
+    o.red[2 * blockIdx.x + 1] = b;
+  }
+}
+
+// sum c_hat^2 only (no change of c_hat), for the norms at create time
+__global__ void k_cnorm_cols(DevObjective o) {
+  double c2 = 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < o.n; j += gridDim.x * blockDim.x) {
+    const double ch = o.chat[j];
+    c2 += ch * ch;
+  }
+  __shared__ double s1[kThreads];
+  s1[threadIdx.x] = c2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int q = 0; q < blockDim.x; ++q) b += s1[q];
+    o.red[2 * blockIdx.x] = 0.0;
+    o.red[2 * blockIdx.x + 1] = b;
+  }
+}
+
+// ||b||^2 over rows (largest finite |lo|, |hi| per row), then the final reduction of
+// both kernels into the control block (single block of this kernel reduces).
+__global__ void k_objective_rows(DevObjective o, double offset_base, int use_offset_terms) {
+  const double inf = pos_inf<double>();
+  double b2 = 0.0;
+  for (int i = threadIdx.x; i < o.m; i += blockDim.x) {
+    const double lo = o.lo_unscaled[i], hi = o.hi_unscaled[i];
+    const double a = lo > -inf ? fabs(lo) : 0.0;
+    const double b = hi < inf ? fabs(hi) : 0.0;
+    const double v = fmax(a, b);
+    b2 += v * v;
+  }
+  __shared__ double sb[kThreads];
+  sb[threadIdx.x] = b2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bb = 0.0, off = 0.0, cc = 0.0;
+    for (int q = 0; q < blockDim.x; ++q) bb += sb[q];
+    for (int q = 0; q < o.red_blocks; ++q) {
+      off += o.red[2 * q];
+      cc += o.red[2 * q + 1];
+    }
+    o.ctl->bnorm = sqrt(bb);
+    o.ctl->cnorm = sqrt(cc);
+    o.ctl->offset = use_offset_terms ? off : offset_base;
+  }
+}
+
+// ----------------------------------------------------------------- launchers ---
+static int g_sms = 0;
+int device_sm_count() {
+  if (g_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 1;
+  }
+  return g_sms;
+}
+
+static int ew_grid(long long count) {
+  long long g = (count + kThreads - 1) / kThreads;
+  const long long cap = 4LL * device_sm_count();
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return int(g);
+}
+
+cudaError_t launch_precondition(const DevSetup& s, int ruiz_iters, bool pock_chambolle, cudaStream_t st) {
+  double* R = s.R;
+  double* C = s.C;
+  double* R2 = s.R2;
+  double* C2 = s.C2;
+  const int gr = ew_grid(s.m), gc = ew_grid(s.n);
+  for (int it = 0; it < ruiz_iters; ++it) {
+    k_ruiz_rows<<<gr, kThreads, 0, st>>>(s.m, s.a_rowptr, s.a_cols, s.a_vals64, R, C, R2);
+    k_ruiz_cols<<<gc, kThreads, 0, st>>>(s.n, s.t_rowptr, s.t_cols, s.t_vals64, R, C, C2);
+    cudaMemcpyAsync(R, R2, sizeof(double) * s.m, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(C, C2, sizeof(double) * s.n, cudaMemcpyDeviceToDevice, st);
+  }
+  if (pock_chambolle) {
+    k_pc_rows<<<gr, kThreads, 0, st>>>(s.m, s.a_rowptr, s.a_cols, s.a_vals64, R, C, R2);
+    k_pc_cols<<<gc, kThreads, 0, st>>>(s.n, s.t_rowptr, s.t_cols, s.t_vals64, R, C, C2);
+    cudaMemcpyAsync(R, R2, sizeof(double) * s.m, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(C, C2, sizeof(double) * s.n, cudaMemcpyDeviceToDevice, st);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_values(const DevSetup& s, cudaStream_t st) {
+  k_scale_rows<<<ew_grid(s.m), kThreads, 0, st>>>(s.m, s.a_rowptr, s.a_cols, s.a_vals64, s.a_vals32, s.R, s.C);
+  k_scale_cols<<<ew_grid(s.n), kThreads, 0, st>>>(s.n, s.t_rowptr, s.t_cols, s.t_vals64, s.t_vals32, s.R, s.C);
+  return cudaGetLastError();
+}
+
+cudaError_t matrix_norms(const DevSetup& s, cudaStream_t st, double* amax, double* fro2) {
+  const int g = s.red_blocks;
+  k_norms_partial<<<g, kThreads, 0, st>>>(s.a_vals64, s.nnz, s.red);
+  std::vector<double> h(2 * g);
+  cudaError_t e = cudaMemcpyAsync(h.data(), s.red, sizeof(double) * 2 * g, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  double a = 0.0, b = 0.0;
+  for (int q = 0; q < g; ++q) {
+    a = fmax(a, h[2 * q]);
+    b += h[2 * q + 1];
+  }
+  *amax = a;
+  *fro2 = b;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_vectors(const DevVecs& v, cudaStream_t st) {
+  k_scale_vectors<<<ew_grid(v.m > v.n ? v.m : v.n), kThreads, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_objective_update(const DevObjective& o, double t_scale, double one_minus_aK,
+                                    cudaStream_t st) {
+  k_objective_cols<<<o.red_blocks, kThreads, 0, st>>>(o, t_scale, one_minus_aK);
+  k_objective_rows<<<1, kThreads, 0, st>>>(o, 0.0, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_objective_norms(const DevObjective& o, double offset, cudaStream_t st) {
+  k_cnorm_cols<<<o.red_blocks, kThreads, 0, st>>>(o);
+  k_objective_rows<<<1, kThreads, 0, st>>>(o, offset, 0);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_solve_init(const DevLP<T>& d, double tol, long long iter_limit, int stall_checks,
+                              long long max_chunks, cudaStream_t st) {
+  k_solve_init<<<1, 1, 0, st>>>(d.ctl, tol, iter_limit, stall_checks, max_chunks);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_check(const DevLP<T>& d, cudaStream_t st) {
+  k_check_cols<T><<<d.grid_c1, kThreads, 0, st>>>(d);
+  k_check_rows<T><<<d.grid_c2, kThreads, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_slot(const DevLP<T>& d, cudaStream_t st) {
+  k_primal<T><<<d.grid_p, kThreads, 0, st>>>(d);
+  k_dual<T><<<d.grid_d, kThreads, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loop_ctl(Control* ctl, cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_loop_ctl<<<1, 1, 0, st>>>(ctl, h);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_get_x(const DevLP<T>& d, double* out, int count, cudaStream_t st) {
+  k_get_x<T><<<ew_grid(count), kThreads, 0, st>>>(d, out, count);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_get_y(const DevLP<T>& d, double* out, int count, cudaStream_t st) {
+  k_get_y<T><<<ew_grid(count), kThreads, 0, st>>>(d, out, count);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_set_xy(const DevLP<T>& d, const double* x, const double* y, cudaStream_t st) {
+  k_set_xy<T><<<ew_grid(d.m > d.n ? d.m : d.n), kThreads, 0, st>>>(d, x, y);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_init_point(const DevLP<T>& d, cudaStream_t st) {
+  k_init_point<T><<<ew_grid(d.m > d.n ? d.m : d.n), kThreads, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+template <typename T>
+int occupancy_grid(int kernel_id, int work_tiles) {
+  int per_sm = 1;
+  cudaError_t e = cudaSuccess;
+  switch (kernel_id) {
+    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_primal<T>, kThreads, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dual<T>, kThreads, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_check_cols<T>, kThreads, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_check_rows<T>, kThreads, 0); break;
+  }
+  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+  long long need = (work_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (need < 1) need = 1;
+  const long long cap = (long long)per_sm * device_sm_count();
+  return int(need < cap ? need : cap);
+}
+
+#define SCYLLA_INSTANTIATE(T)                                                                              \
+  template cudaError_t launch_solve_init<T>(const DevLP<T>&, double, long long, int, long long, cudaStream_t); \
+  template cudaError_t launch_check<T>(const DevLP<T>&, cudaStream_t);                                    \
+  template cudaError_t launch_slot<T>(const DevLP<T>&, cudaStream_t);                                     \
+  template cudaError_t launch_get_x<T>(const DevLP<T>&, double*, int, cudaStream_t);                      \
+  template cudaError_t launch_get_y<T>(const DevLP<T>&, double*, int, cudaStream_t);                      \
+  template cudaError_t launch_set_xy<T>(const DevLP<T>&, const double*, const double*, cudaStream_t);     \
+  template cudaError_t launch_init_point<T>(const DevLP<T>&, cudaStream_t);                               \
+  template int occupancy_grid<T>(int, int);
+
+SCYLLA_INSTANTIATE(double)
+SCYLLA_INSTANTIATE(float)
+
+}  // namespace scylla

@@ -1,0 +1,790 @@
+// Host runtime of the Scylla PDHG library: the C ABI of scylla.h for creating an
+// LP handle, solving, objective updates and state access.  Everything numeric on
+// the PDHG path runs in the kernels of kernels.cu; this file validates input,
+// builds the auxiliary columns, the transposed CSR and the warp tiles, owns the
+// device memory (one arena per handle) and drives the solve as one CUDA graph
+// whose device-side while loop runs until the device control block says done.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "lp_handle.h"
+
+namespace scylla {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+const char* get_error() { return g_err.c_str(); }
+
+}  // namespace scylla
+
+using namespace scylla;
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+      return e_ == cudaErrorMemoryAllocation ? SCYLLA_ERR_OOM : SCYLLA_ERR_CUDA;          \
+    }                                                                                     \
+  } while (0)
+
+#define FAIL(code, msg)       \
+  do {                        \
+    set_error(msg);           \
+    return (code);            \
+  } while (0)
+
+static const double kInf = std::numeric_limits<double>::infinity();
+
+extern "C" void scylla_default_params(scylla_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->precision = SCYLLA_PREC_FP64;
+  p->n_check = 64;
+  p->ruiz_iters = 10;
+  p->pock_chambolle = 1;
+  p->adaptive_step = 1;
+  p->restarts = 1;
+  p->primal_weight_update = 1;
+  p->stall_checks = 0;
+  p->aux_general_integers = 1;
+  p->use_graph = 1;
+  p->fixed_step_factor = 0.9;
+  p->beta_sufficient = 0.2;
+  p->beta_necessary = 0.8;
+  p->beta_artificial = 0.36;
+  p->pw_smoothing = 0.5;
+  p->step_reduction_exp = 0.3;
+  p->step_growth_exp = 0.6;
+  p->alpha = 0.9;
+  p->eps1 = 0.01;
+  p->beta = 0.98;
+  p->eps_floor = 1e-8;
+  p->max_rounds = 100;
+  p->iter_limit = 20000;
+  p->total_iter_cap = 1000000000LL;
+  p->run_stall_checks = 5;
+  p->seed = 0;
+  p->time_limit_s = 0.0;
+}
+
+extern "C" const char* scylla_last_error(void) { return get_error(); }
+
+namespace {
+
+// bump allocator over one cudaMalloc: pass 1 with base == nullptr sizes, pass 2 carves
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += sizeof(T) * (count ? count : 1);
+    return p;
+  }
+};
+
+size_t padded(size_t nnz) { return ((nnz + 3) & ~size_t(3)) + 4; }
+
+// contiguous row ranges of at most kTileNnz nonzeros and kTileRows rows; a longer
+// row is a tile of its own
+std::vector<int> build_tiles(const std::vector<int>& rowptr) {
+  const int m = int(rowptr.size()) - 1;
+  std::vector<int> t;
+  t.reserve(m / 4 + 2);
+  t.push_back(0);
+  int r = 0;
+  while (r < m) {
+    const int len = rowptr[r + 1] - rowptr[r];
+    if (len > kTileNnz) {
+      ++r;
+      t.push_back(r);
+      continue;
+    }
+    int cnt = 0, nz = 0;
+    while (r < m && cnt < kTileRows) {
+      const int l2 = rowptr[r + 1] - rowptr[r];
+      if (nz + l2 > kTileNnz) break;
+      nz += l2;
+      ++r;
+      ++cnt;
+    }
+    t.push_back(r);
+  }
+  return t;
+}
+
+template <typename T>
+void fill_dev(DevLP<T>& d, scylla_lp* lp);
+
+}  // namespace
+
+// --------------------------------------------------------------- validation ---
+static int validate(const scylla_csr* A, const double* c, const double* lo, const double* hi, const double* l,
+                    const double* u, const uint8_t* is_int) {
+  if (!A || !c || !lo || !hi || !l || !u || !is_int) FAIL(SCYLLA_ERR_INVALID_ARG, "null argument");
+  if (A->m < 0 || A->n < 1 || A->nnz < 0) FAIL(SCYLLA_ERR_INVALID_ARG, "need m >= 0, n >= 1, nnz >= 0");
+  const int64_t lim = (int64_t(1) << 31) - 64;
+  if (A->m >= lim / 2 || A->n >= lim / 2 || A->nnz >= lim / 2)
+    FAIL(SCYLLA_ERR_UNSUPPORTED, "dimensions or nnz beyond the 32-bit index range");
+  if (!A->rowptr || (A->nnz > 0 && (!A->cols || !A->vals))) FAIL(SCYLLA_ERR_INVALID_ARG, "null CSR array");
+  if (A->rowptr[0] != 0 || A->rowptr[A->m] != A->nnz) FAIL(SCYLLA_ERR_INVALID_ARG, "rowptr[0] != 0 or rowptr[m] != nnz");
+  for (int64_t i = 0; i < A->m; ++i) {
+    const int64_t p0 = A->rowptr[i], p1 = A->rowptr[i + 1];
+    if (p1 < p0) FAIL(SCYLLA_ERR_INVALID_ARG, "rowptr not non-decreasing at row " + std::to_string(i));
+    for (int64_t p = p0; p < p1; ++p) {
+      const int32_t j = A->cols[p];
+      if (j < 0 || j >= A->n) FAIL(SCYLLA_ERR_INVALID_ARG, "column index out of range in row " + std::to_string(i));
+      if (p > p0 && A->cols[p - 1] >= j)
+        FAIL(SCYLLA_ERR_INVALID_ARG, "column indices not strictly increasing in row " + std::to_string(i));
+      if (!std::isfinite(A->vals[p])) FAIL(SCYLLA_ERR_INVALID_ARG, "non-finite matrix value in row " + std::to_string(i));
+    }
+  }
+  for (int64_t i = 0; i < A->m; ++i) {
+    if (std::isnan(lo[i]) || std::isnan(hi[i]) || lo[i] > hi[i] || lo[i] == kInf || hi[i] == -kInf)
+      FAIL(SCYLLA_ERR_INVALID_ARG, "invalid row bounds at row " + std::to_string(i));
+  }
+  for (int64_t j = 0; j < A->n; ++j) {
+    if (!std::isfinite(c[j])) FAIL(SCYLLA_ERR_INVALID_ARG, "non-finite objective at column " + std::to_string(j));
+    if (std::isnan(l[j]) || std::isnan(u[j]) || l[j] > u[j] || l[j] == kInf || u[j] == -kInf)
+      FAIL(SCYLLA_ERR_INVALID_ARG, "invalid column bounds at column " + std::to_string(j));
+    if (is_int[j] > 1) FAIL(SCYLLA_ERR_INVALID_ARG, "is_integer must be 0 or 1");
+    if (is_int[j] && ((std::isfinite(l[j]) && l[j] != std::floor(l[j])) ||
+                      (std::isfinite(u[j]) && u[j] != std::floor(u[j]))))
+      FAIL(SCYLLA_ERR_INVALID_ARG, "integer column with a fractional bound: " + std::to_string(j));
+  }
+  return SCYLLA_OK;
+}
+
+// ------------------------------------------------------------------ create ---
+static int create_impl(const scylla_csr* A, const double* c, const double* lo, const double* hi, const double* l,
+                       const double* u, const uint8_t* is_int, const scylla_params* pin, void* cuda_stream,
+                       scylla_lp* lp) {
+  lp->p = *pin;
+  if (lp->p.n_check < 1) FAIL(SCYLLA_ERR_INVALID_ARG, "n_check must be >= 1");
+  if (lp->p.precision != SCYLLA_PREC_FP64 && lp->p.precision != SCYLLA_PREC_MIXED)
+    FAIL(SCYLLA_ERR_INVALID_ARG, "unknown precision");
+  CK(cudaGetDevice(&lp->device));
+  lp->user_st = static_cast<cudaStream_t>(cuda_stream);
+  CK(cudaStreamCreateWithFlags(&lp->st, cudaStreamNonBlocking));
+  CK(cudaEventCreate(&lp->ev_user));
+  CK(cudaEventCreate(&lp->ev0));
+  CK(cudaEventCreate(&lp->ev1));
+
+  // ---- host copies of the original MIP
+  const int64_t m0 = A->m, n0 = A->n, nnz0 = A->nnz;
+  lp->m0 = m0;
+  lp->n0 = n0;
+  lp->nnz0 = nnz0;
+  lp->rowptr0.assign(A->rowptr, A->rowptr + m0 + 1);
+  lp->cols0.assign(A->cols, A->cols + nnz0);
+  lp->vals0.assign(A->vals, A->vals + nnz0);
+  lp->c0.assign(c, c + n0);
+  lp->lo0.assign(lo, lo + m0);
+  lp->hi0.assign(hi, hi + m0);
+  lp->l0.assign(l, l + n0);
+  lp->u0.assign(u, u + n0);
+  lp->int0.assign(is_int, is_int + n0);
+  // rows of each column, ascending (for propagation)
+  lp->colptr0.assign(n0 + 1, 0);
+  for (int64_t p = 0; p < nnz0; ++p) lp->colptr0[lp->cols0[p] + 1]++;
+  for (int64_t j = 0; j < n0; ++j) lp->colptr0[j + 1] += lp->colptr0[j];
+  lp->colrows0.assign(nnz0, 0);
+  {
+    std::vector<int64_t> cur(lp->colptr0.begin(), lp->colptr0.end() - 1);
+    for (int64_t i = 0; i < m0; ++i)
+      for (int64_t p = lp->rowptr0[i]; p < lp->rowptr0[i + 1]; ++p) lp->colrows0[cur[lp->cols0[p]]++] = int32_t(i);
+  }
+  lp->c0norm = 0.0;
+  for (int64_t j = 0; j < n0; ++j) lp->c0norm += c[j] * c[j];
+  lp->c0norm = std::sqrt(lp->c0norm);
+  lp->n_int = 0;
+  for (int64_t j = 0; j < n0; ++j) lp->n_int += is_int[j] ? 1 : 0;
+
+  // ---- auxiliary distance columns for general integers
+  lp->kind.assign(n0, 0);
+  lp->aux_of.assign(n0, -1);
+  lp->gen_int.clear();
+  for (int64_t j = 0; j < n0; ++j) {
+    if (!is_int[j]) continue;
+    const bool unit = (u[j] - l[j] == 1.0);
+    if (unit || !lp->p.aux_general_integers) {
+      lp->kind[j] = 1;
+    } else {
+      lp->kind[j] = 2;
+      lp->aux_of[j] = int32_t(lp->gen_int.size());
+      lp->gen_int.push_back(int32_t(j));
+    }
+  }
+  const int64_t na = int64_t(lp->gen_int.size());
+  lp->n_aux = na;
+  const int64_t m = m0 + 2 * na, n = n0 + na, nnz = nnz0 + 4 * na;
+  lp->m = int(m);
+  lp->n = int(n);
+  lp->nnz = int(nnz);
+
+  std::vector<int> rp(m + 1), ci(nnz);
+  std::vector<double> va(nnz);
+  for (int64_t i = 0; i <= m0; ++i) rp[i] = int(lp->rowptr0[i]);
+  for (int64_t p = 0; p < nnz0; ++p) {
+    ci[p] = lp->cols0[p];
+    va[p] = lp->vals0[p];
+  }
+  for (int64_t t = 0; t < na; ++t) {
+    const int j = lp->gen_int[t];
+    const int64_t r0 = m0 + 2 * t, p = nnz0 + 4 * t;
+    ci[p] = j; va[p] = -1.0;
+    ci[p + 1] = int(n0 + t); va[p + 1] = 1.0;
+    ci[p + 2] = j; va[p + 2] = 1.0;
+    ci[p + 3] = int(n0 + t); va[p + 3] = 1.0;
+    rp[r0 + 1] = int(p + 2);
+    rp[r0 + 2] = int(p + 4);
+  }
+  std::vector<double> cA(n), loA(m), hiA(m), lA(n), uA(n);
+  for (int64_t j = 0; j < n0; ++j) { cA[j] = c[j]; lA[j] = l[j]; uA[j] = u[j]; }
+  for (int64_t t = 0; t < na; ++t) {
+    const int j = lp->gen_int[t];
+    cA[n0 + t] = 0.0;
+    lA[n0 + t] = 0.0;
+    uA[n0 + t] = u[j] - l[j];
+  }
+  for (int64_t i = 0; i < m0; ++i) { loA[i] = lo[i]; hiA[i] = hi[i]; }
+  for (int64_t i = m0; i < m; ++i) { loA[i] = -kInf; hiA[i] = kInf; }
+  std::vector<uint8_t> imask(n, 0);
+  for (int64_t j = 0; j < n0; ++j) imask[j] = is_int[j];
+
+  // ---- transpose (counting sort: rows ascending within each column)
+  std::vector<int> tp(n + 1, 0), tr(nnz);
+  std::vector<double> tv(nnz);
+  for (int64_t p = 0; p < nnz; ++p) tp[ci[p] + 1]++;
+  for (int64_t j = 0; j < n; ++j) tp[j + 1] += tp[j];
+  {
+    std::vector<int> cur(tp.begin(), tp.end() - 1);
+    for (int64_t i = 0; i < m; ++i)
+      for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const int q = cur[ci[p]]++;
+        tr[q] = int(i);
+        tv[q] = va[p];
+      }
+  }
+  const std::vector<int> at = build_tiles(rp), tt = build_tiles(tp);
+  lp->a_ntiles = int(at.size()) - 1;
+  lp->t_ntiles = int(tt.size()) - 1;
+
+  // ---- grid sizes and scratch
+  const bool mixed = lp->p.precision == SCYLLA_PREC_MIXED;
+  if (mixed) {
+    lp->grid_p = occupancy_grid<float>(0, lp->t_ntiles);
+    lp->grid_d = occupancy_grid<float>(1, lp->a_ntiles);
+    lp->grid_c1 = occupancy_grid<float>(2, lp->t_ntiles);
+    lp->grid_c2 = occupancy_grid<float>(3, lp->a_ntiles);
+  } else {
+    lp->grid_p = occupancy_grid<double>(0, lp->t_ntiles);
+    lp->grid_d = occupancy_grid<double>(1, lp->a_ntiles);
+    lp->grid_c1 = occupancy_grid<double>(2, lp->t_ntiles);
+    lp->grid_c2 = occupancy_grid<double>(3, lp->a_ntiles);
+  }
+  // the primal kernel also runs the elementwise retry path over n columns
+  lp->red_blocks = std::max(1, std::min(4 * device_sm_count(), int((std::max(m, n) + kThreads - 1) / kThreads)));
+  const size_t vs = mixed ? sizeof(float) : sizeof(double);
+
+  // ---- device arena: pass 1 sizes, pass 2 carves
+  for (int pass = 0; pass < 2; ++pass) {
+    Arena ar;
+    if (pass == 1) {
+      CK(cudaMalloc(&lp->arena, lp->arena_bytes));
+      ar.base = static_cast<char*>(lp->arena);
+    }
+    lp->a_rowptr = ar.take<int>(m + 1);
+    lp->a_cols = ar.take<int>(padded(nnz));
+    lp->a_tiles = ar.take<int>(at.size());
+    lp->t_rowptr = ar.take<int>(n + 1);
+    lp->t_cols = ar.take<int>(padded(nnz));
+    lp->t_tiles = ar.take<int>(tt.size());
+    lp->a_vals64 = ar.take<double>(padded(nnz));
+    lp->t_vals64 = ar.take<double>(padded(nnz));
+    lp->a_vals32 = mixed ? ar.take<float>(padded(nnz)) : nullptr;
+    lp->t_vals32 = mixed ? ar.take<float>(padded(nnz)) : nullptr;
+    lp->c_un = ar.take<double>(n);
+    lp->l_un = ar.take<double>(n);
+    lp->u_un = ar.take<double>(n);
+    lp->lo_un = ar.take<double>(m);
+    lp->hi_un = ar.take<double>(m);
+    lp->c64 = ar.take<double>(n);
+    lp->l64 = ar.take<double>(n);
+    lp->u64 = ar.take<double>(n);
+    lp->lo64 = ar.take<double>(m);
+    lp->hi64 = ar.take<double>(m);
+    lp->c32 = mixed ? ar.take<float>(n) : nullptr;
+    lp->l32 = mixed ? ar.take<float>(n) : nullptr;
+    lp->u32 = mixed ? ar.take<float>(n) : nullptr;
+    lp->lo32 = mixed ? ar.take<float>(m) : nullptr;
+    lp->hi32 = mixed ? ar.take<float>(m) : nullptr;
+    lp->R = ar.take<double>(m);
+    lp->C = ar.take<double>(n);
+    lp->R2 = ar.take<double>(std::max(m, n));
+    lp->C2 = ar.take<double>(std::max(m, n));
+    lp->int_mask = ar.take<uint8_t>(n);
+    lp->c_orig = ar.take<double>(n0);
+    lp->l_orig = ar.take<double>(n0);
+    lp->u_orig = ar.take<double>(n0);
+    lp->xhat_d = ar.take<double>(n0);
+    lp->kind_d = ar.take<int>(n0);
+    lp->aux_of_d = ar.take<int>(n0);
+    for (int k = 0; k < 3; ++k) {
+      lp->X[k] = ar.take<char>(vs * n);
+      lp->Y[k] = ar.take<char>(vs * m);
+      lp->AX[k] = ar.take<char>(vs * m);
+    }
+    for (int k = 0; k < 2; ++k) lp->ATY[k] = ar.take<char>(vs * n);
+    lp->XLR = ar.take<char>(vs * n);
+    lp->YLR = ar.take<char>(vs * m);
+    lp->part_p = ar.take<double>(size_t(kNP) * std::max(lp->grid_p, 1));
+    lp->part_d = ar.take<double>(size_t(kND) * std::max(lp->grid_d, 1));
+    lp->part_c1 = ar.take<double>(size_t(kNC1) * std::max(lp->grid_c1, 1));
+    lp->part_c2 = ar.take<double>(size_t(kNC2) * std::max(lp->grid_c2, 1));
+    lp->red = ar.take<double>(2 * size_t(lp->red_blocks));
+    lp->io_x = ar.take<double>(n);
+    lp->io_y = ar.take<double>(m);
+    lp->ctl = ar.take<Control>(1);
+    if (pass == 0) lp->arena_bytes = ar.off + 256;
+  }
+  cudaStream_t st = lp->st;
+  CK(cudaMemsetAsync(lp->arena, 0, lp->arena_bytes, st));
+  CK(cudaMallocHost(&lp->h_ctl, sizeof(Control)));
+
+  CK(cudaMemcpyAsync(lp->a_rowptr, rp.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->a_cols, ci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->a_tiles, at.data(), sizeof(int) * at.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->t_rowptr, tp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->t_cols, tr.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->t_tiles, tt.data(), sizeof(int) * tt.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->a_vals64, va.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->t_vals64, tv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->c_un, cA.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->l_un, lA.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->u_un, uA.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->lo_un, loA.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->hi_un, hiA.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->int_mask, imask.data(), n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->c_orig, c, sizeof(double) * n0, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->l_orig, l, sizeof(double) * n0, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->u_orig, u, sizeof(double) * n0, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->kind_d, lp->kind.data(), sizeof(int) * n0, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->aux_of_d, lp->aux_of.data(), sizeof(int) * n0, cudaMemcpyHostToDevice, st));
+  {
+    const std::vector<double> ones(std::max(m, n), 1.0);
+    CK(cudaMemcpyAsync(lp->R, ones.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(lp->C, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    // preconditioning (Section 2.1, PDLP's diagonal scaling) and scaled copies
+    DevSetup s{};
+    s.m = int(m); s.n = int(n); s.n_orig = int(n0); s.m_orig = int(m0); s.nnz = int(nnz);
+    s.a_rowptr = lp->a_rowptr; s.a_cols = lp->a_cols; s.t_rowptr = lp->t_rowptr; s.t_cols = lp->t_cols;
+    s.a_vals64 = lp->a_vals64; s.t_vals64 = lp->t_vals64; s.a_vals32 = lp->a_vals32; s.t_vals32 = lp->t_vals32;
+    s.R = lp->R; s.C = lp->C; s.R2 = lp->R2; s.C2 = lp->C2; s.red = lp->red; s.red_blocks = lp->red_blocks;
+    CK(launch_precondition(s, lp->p.ruiz_iters, lp->p.pock_chambolle != 0, st));
+    CK(launch_scale_values(s, st));
+    DevVecs v{};
+    v.c = lp->c_un; v.lo = lp->lo_un; v.hi = lp->hi_un; v.l = lp->l_un; v.u = lp->u_un;
+    v.c64 = lp->c64; v.lo64 = lp->lo64; v.hi64 = lp->hi64; v.l64 = lp->l64; v.u64 = lp->u64;
+    v.c32 = lp->c32; v.lo32 = lp->lo32; v.hi32 = lp->hi32; v.l32 = lp->l32; v.u32 = lp->u32;
+    v.R = lp->R; v.C = lp->C; v.m = int(m); v.n = int(n);
+    CK(launch_scale_vectors(v, st));
+    double amax = 0.0, fro2 = 0.0;
+    CK(matrix_norms(s, st, &amax, &fro2));
+    // initial step size: 1/max|a~| (adaptive) or f/||A~||_F (fixed); primal weight
+    // ||c~|| / ||b~|| on the scaled LP (1 when either is zero)
+    double eta = 1.0;
+    if (lp->p.adaptive_step) eta = amax > 0.0 ? 1.0 / amax : 1.0;
+    else eta = fro2 > 0.0 ? lp->p.fixed_step_factor / std::sqrt(fro2) : 1.0;
+    std::vector<double> hc(n), hlo(m), hhi(m);
+    CK(cudaMemcpyAsync(hc.data(), lp->c64, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hlo.data(), lp->lo64, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hhi.data(), lp->hi64, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double cn = 0.0, qn = 0.0;
+    for (int64_t j = 0; j < n; ++j) cn += hc[j] * hc[j];
+    for (int64_t i = 0; i < m; ++i) {
+      const double a = std::isfinite(hlo[i]) ? std::fabs(hlo[i]) : 0.0;
+      const double b = std::isfinite(hhi[i]) ? std::fabs(hhi[i]) : 0.0;
+      const double q = std::max(a, b);
+      qn += q * q;
+    }
+    cn = std::sqrt(cn);
+    qn = std::sqrt(qn);
+    Control h{};
+    h.eta = eta;
+    h.omega = (cn > 0.0 && qn > 0.0) ? cn / qn : 1.0;
+    h.ix_cur = 0; h.ix_next = 1; h.ix_avg = 2; h.ia_cur = 0; h.ia_avg = 1;
+    h.adaptive = lp->p.adaptive_step ? 1 : 0;
+    h.restarts_on = lp->p.restarts ? 1 : 0;
+    h.pw_update = lp->p.primal_weight_update ? 1 : 0;
+    h.beta_s = lp->p.beta_sufficient; h.beta_n = lp->p.beta_necessary; h.beta_a = lp->p.beta_artificial;
+    h.theta = lp->p.pw_smoothing; h.exp_red = lp->p.step_reduction_exp; h.exp_grow = lp->p.step_growth_exp;
+    h.done = 1;
+    *lp->h_ctl = h;
+    CK(cudaMemcpyAsync(lp->ctl, lp->h_ctl, sizeof(Control), cudaMemcpyHostToDevice, st));
+    // c_hat = c (already in c_un), offset 0; norms of c and of the row bounds
+    const DevObjective o = lp->objective_desc();
+    CK(launch_objective_norms(o, 0.0, st));
+  }
+  if (mixed) {
+    fill_dev<float>(lp->d32, lp);
+    CK(launch_init_point<float>(lp->d32, st));
+  } else {
+    fill_dev<double>(lp->d64, lp);
+    CK(launch_init_point<double>(lp->d64, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return SCYLLA_OK;
+}
+
+namespace {
+template <typename T>
+void fill_dev(DevLP<T>& d, scylla_lp* lp) {
+  const bool mixed = lp->p.precision == SCYLLA_PREC_MIXED;
+  d.m = lp->m;
+  d.n = lp->n;
+  d.a_rowptr = lp->a_rowptr; d.a_cols = lp->a_cols; d.a_tiles = lp->a_tiles; d.a_ntiles = lp->a_ntiles;
+  d.t_rowptr = lp->t_rowptr; d.t_cols = lp->t_cols; d.t_tiles = lp->t_tiles; d.t_ntiles = lp->t_ntiles;
+  d.a_vals64 = lp->a_vals64;
+  d.t_vals64 = lp->t_vals64;
+  if (mixed) {
+    d.a_vals = reinterpret_cast<const T*>(lp->a_vals32);
+    d.t_vals = reinterpret_cast<const T*>(lp->t_vals32);
+    d.c = reinterpret_cast<const T*>(lp->c32);
+    d.l = reinterpret_cast<const T*>(lp->l32);
+    d.u = reinterpret_cast<const T*>(lp->u32);
+    d.lo = reinterpret_cast<const T*>(lp->lo32);
+    d.hi = reinterpret_cast<const T*>(lp->hi32);
+  } else {
+    d.a_vals = reinterpret_cast<const T*>(lp->a_vals64);
+    d.t_vals = reinterpret_cast<const T*>(lp->t_vals64);
+    d.c = reinterpret_cast<const T*>(lp->c64);
+    d.l = reinterpret_cast<const T*>(lp->l64);
+    d.u = reinterpret_cast<const T*>(lp->u64);
+    d.lo = reinterpret_cast<const T*>(lp->lo64);
+    d.hi = reinterpret_cast<const T*>(lp->hi64);
+  }
+  d.c64 = lp->c64; d.l64 = lp->l64; d.u64 = lp->u64; d.lo64 = lp->lo64; d.hi64 = lp->hi64;
+  d.R = lp->R;
+  d.C = lp->C;
+  d.int_mask = lp->int_mask;
+  for (int k = 0; k < 3; ++k) {
+    d.X[k] = reinterpret_cast<T*>(lp->X[k]);
+    d.Y[k] = reinterpret_cast<T*>(lp->Y[k]);
+    d.AX[k] = reinterpret_cast<T*>(lp->AX[k]);
+  }
+  for (int k = 0; k < 2; ++k) d.ATY[k] = reinterpret_cast<T*>(lp->ATY[k]);
+  d.XLR = reinterpret_cast<T*>(lp->XLR);
+  d.YLR = reinterpret_cast<T*>(lp->YLR);
+  d.ctl = lp->ctl;
+  d.part_p = lp->part_p; d.part_d = lp->part_d; d.part_c1 = lp->part_c1; d.part_c2 = lp->part_c2;
+  d.grid_p = lp->grid_p; d.grid_d = lp->grid_d; d.grid_c1 = lp->grid_c1; d.grid_c2 = lp->grid_c2;
+}
+}  // namespace
+
+DevObjective scylla_lp::objective_desc() {
+  DevObjective o{};
+  o.n_orig = int(n0); o.m_orig = int(m0); o.n = n; o.m = m;
+  o.c_orig = c_orig; o.l_orig = l_orig; o.u_orig = u_orig; o.kind = kind_d; o.aux_of = aux_of_d; o.xhat = xhat_d;
+  o.chat = c_un; o.lo_unscaled = lo_un; o.hi_unscaled = hi_un; o.R = R; o.C = C;
+  o.c64 = c64; o.lo64 = lo64; o.c32 = c32; o.lo32 = lo32; o.red = red; o.red_blocks = red_blocks; o.ctl = ctl;
+  return o;
+}
+
+void scylla_lp::release() {
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  exec = nullptr;
+  graph = nullptr;
+  if (arena) cudaFree(arena);
+  arena = nullptr;
+  if (h_ctl) cudaFreeHost(h_ctl);
+  h_ctl = nullptr;
+  if (ev_user) cudaEventDestroy(ev_user);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  ev_user = ev0 = ev1 = nullptr;
+  if (st) cudaStreamDestroy(st);
+  st = nullptr;
+}
+
+extern "C" int scylla_lp_create(const scylla_csr* A, const double* c, const double* row_lo, const double* row_hi,
+                                const double* col_lo, const double* col_hi, const uint8_t* is_integer,
+                                const scylla_params* p, void* cuda_stream, scylla_lp** out) {
+  if (!out) FAIL(SCYLLA_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  int rc = validate(A, c, row_lo, row_hi, col_lo, col_hi, is_integer);
+  if (rc != SCYLLA_OK) return rc;
+  scylla_params dp;
+  scylla_default_params(&dp);
+  scylla_lp* lp = nullptr;
+  try {
+    lp = new scylla_lp();
+    rc = create_impl(A, c, row_lo, row_hi, col_lo, col_hi, is_integer, p ? p : &dp, cuda_stream, lp);
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    rc = SCYLLA_ERR_OOM;
+  } catch (const std::exception& e) {
+    set_error(e.what());
+    rc = SCYLLA_ERR_INVALID_ARG;
+  }
+  if (rc != SCYLLA_OK) {
+    if (lp) {
+      lp->release();
+      delete lp;
+    }
+    return rc;
+  }
+  *out = lp;
+  return SCYLLA_OK;
+}
+
+extern "C" void scylla_lp_destroy(scylla_lp* lp) {
+  if (!lp) return;
+  cudaStreamSynchronize(lp->st);
+  lp->release();
+  delete lp;
+}
+
+extern "C" int scylla_lp_dims(const scylla_lp* lp, int64_t* m_total, int64_t* n_total, int64_t* nnz_total,
+                              int64_t* n_aux) {
+  if (!lp) FAIL(SCYLLA_ERR_INVALID_ARG, "null handle");
+  if (m_total) *m_total = lp->m;
+  if (n_total) *n_total = lp->n;
+  if (nnz_total) *nnz_total = lp->nnz;
+  if (n_aux) *n_aux = lp->n_aux;
+  return SCYLLA_OK;
+}
+
+// -------------------------------------------------------------------- solve ---
+int scylla_lp::order_after_user() {
+  if (user_st) {
+    CK(cudaEventRecord(ev_user, user_st));
+    CK(cudaStreamWaitEvent(st, ev_user, 0));
+  }
+  return SCYLLA_OK;
+}
+
+template <typename T>
+static int build_graph(scylla_lp* lp, const DevLP<T>& d) {
+  cudaStream_t st = lp->st;
+  CK(cudaGraphCreate(&lp->graph, 0));
+  CK(cudaGraphConditionalHandleCreate(&lp->cond, lp->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = lp->cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, lp->graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < lp->p.n_check && e == cudaSuccess; ++s) e = launch_slot<T>(d, st);
+  if (e == cudaSuccess) e = launch_check<T>(d, st);
+  if (e == cudaSuccess) e = launch_loop_ctl(lp->ctl, lp->cond, st);
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(st, &captured);
+  CK(e);
+  CK(e2);
+  CK(cudaGraphInstantiate(&lp->exec, lp->graph, 0));
+  return SCYLLA_OK;
+}
+
+template <typename T>
+static int solve_impl(scylla_lp* lp, const DevLP<T>& d, double tol, int64_t iter_limit, int stall_checks) {
+  cudaStream_t st = lp->st;
+  const long long nchk = lp->p.n_check;
+  const long long max_chunks = (iter_limit + nchk - 1) / nchk + 2;
+  CK(cudaEventRecord(lp->ev0, st));
+  CK(launch_solve_init<T>(d, tol, (long long)iter_limit, stall_checks, max_chunks, st));
+  CK(launch_check<T>(d, st));  // evaluates the start point, caches A x and A^T y
+  if (lp->p.use_graph) {
+    if (!lp->exec) {
+      const int rc = build_graph<T>(lp, d);
+      if (rc != SCYLLA_OK) return rc;
+    }
+    CK(cudaGraphLaunch(lp->exec, st));
+  } else {
+    for (long long ch = 0; ch < max_chunks; ++ch) {
+      CK(cudaMemcpyAsync(lp->h_ctl, lp->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (lp->h_ctl->done) break;
+      for (int s = 0; s < lp->p.n_check; ++s) CK(launch_slot<T>(d, st));
+      CK(launch_check<T>(d, st));
+    }
+  }
+  CK(cudaEventRecord(lp->ev1, st));
+  CK(cudaMemcpyAsync(lp->h_ctl, lp->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return SCYLLA_OK;
+}
+
+int scylla_lp::solve(double tol, int64_t iter_limit, int stall_checks, scylla_pdhg_result* out) {
+  int rc = order_after_user();
+  if (rc != SCYLLA_OK) return rc;
+  rc = (p.precision == SCYLLA_PREC_MIXED) ? solve_impl<float>(this, d32, tol, iter_limit, stall_checks)
+                                          : solve_impl<double>(this, d64, tol, iter_limit, stall_checks);
+  if (rc != SCYLLA_OK) return rc;
+  const Control& h = *h_ctl;
+  if (!h.done) FAIL(SCYLLA_ERR_CUDA, "solve ended without a final check");
+  if (out) {
+    std::memset(out, 0, sizeof(*out));
+    out->status = h.status;
+    out->used_average = h.used_avg;
+    out->iterations = h.k;
+    out->accepted = h.accepted;
+    out->rejected = h.rejected;
+    out->restarts = h.restarts;
+    out->eps_p = h.eps_p;
+    out->eps_d = h.eps_d;
+    out->eps_g = h.eps_g;
+    out->rel_kkt = h.rel_kkt;
+    out->pobj = h.pobj;
+    out->dobj = h.dobj;
+    out->eta = h.eta;
+    out->omega = h.omega;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    out->seconds = ms * 1e-3;
+  }
+  return SCYLLA_OK;
+}
+
+extern "C" int scylla_pdhg_solve(scylla_lp* lp, double tol, int64_t iter_limit, scylla_pdhg_result* out) {
+  if (!lp) FAIL(SCYLLA_ERR_INVALID_ARG, "null handle");
+  if (!(tol >= 0.0)) FAIL(SCYLLA_ERR_INVALID_ARG, "tol must be >= 0");
+  if (iter_limit < 0) FAIL(SCYLLA_ERR_INVALID_ARG, "iter_limit must be >= 0");
+  return lp->solve(tol, iter_limit, lp->p.stall_checks, out);
+}
+
+// ---------------------------------------------------------- objective update ---
+int scylla_lp::set_objective(const double* xhat, int32_t K) {
+  if (!xhat) FAIL(SCYLLA_ERR_INVALID_ARG, "xhat is null");
+  if (K < 1) FAIL(SCYLLA_ERR_INVALID_ARG, "round K must be >= 1");
+  for (int64_t j = 0; j < n0; ++j) {
+    if (!std::isfinite(xhat[j])) FAIL(SCYLLA_ERR_INVALID_ARG, "xhat not finite at " + std::to_string(j));
+    if (int0[j] && (xhat[j] != std::floor(xhat[j]) || xhat[j] < l0[j] || xhat[j] > u0[j]))
+      FAIL(SCYLLA_ERR_INVALID_ARG, "xhat not integral within bounds at integer column " + std::to_string(j));
+  }
+  int rc = order_after_user();
+  if (rc != SCYLLA_OK) return rc;
+  CK(cudaMemcpyAsync(xhat_d, xhat, sizeof(double) * n0, cudaMemcpyHostToDevice, st));
+  const double aK = std::pow(p.alpha, double(K));
+  const double s = c0norm > 0.0 ? std::sqrt(double(n_int)) / c0norm : 0.0;
+  CK(launch_objective_update(objective_desc(), aK * s, 1.0 - aK, st));
+  CK(cudaStreamSynchronize(st));
+  return SCYLLA_OK;
+}
+
+extern "C" int scylla_set_objective(scylla_lp* lp, const double* xhat, int32_t K) {
+  if (!lp) FAIL(SCYLLA_ERR_INVALID_ARG, "null handle");
+  return lp->set_objective(xhat, K);
+}
+
+extern "C" int scylla_get_objective(const scylla_lp* lp, double* c_hat, double* offset) {
+  if (!lp || !c_hat) FAIL(SCYLLA_ERR_INVALID_ARG, "null argument");
+  CK(cudaMemcpyAsync(c_hat, lp->c_un, sizeof(double) * lp->n, cudaMemcpyDeviceToHost, lp->st));
+  CK(cudaMemcpyAsync(lp->h_ctl, lp->ctl, sizeof(Control), cudaMemcpyDeviceToHost, lp->st));
+  CK(cudaStreamSynchronize(lp->st));
+  if (offset) *offset = lp->h_ctl->offset;
+  return SCYLLA_OK;
+}
+
+// ------------------------------------------------------------- state access ---
+int scylla_lp::fetch_x(double* host, int count) {
+  if (p.precision == SCYLLA_PREC_MIXED) CK(launch_get_x<float>(d32, io_x, count, st));
+  else CK(launch_get_x<double>(d64, io_x, count, st));
+  if (host) {
+    CK(cudaMemcpyAsync(host, io_x, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  return SCYLLA_OK;
+}
+
+int scylla_lp::fetch_y(double* host, int count) {
+  if (p.precision == SCYLLA_PREC_MIXED) CK(launch_get_y<float>(d32, io_y, count, st));
+  else CK(launch_get_y<double>(d64, io_y, count, st));
+  CK(cudaMemcpyAsync(host, io_y, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return SCYLLA_OK;
+}
+
+extern "C" int scylla_get_primal(const scylla_lp* lp, double* x) {
+  if (!lp || !x) FAIL(SCYLLA_ERR_INVALID_ARG, "null argument");
+  return const_cast<scylla_lp*>(lp)->fetch_x(x, int(lp->n0));
+}
+
+extern "C" int scylla_get_dual(const scylla_lp* lp, double* y) {
+  if (!lp || (!y && lp->m0 > 0)) FAIL(SCYLLA_ERR_INVALID_ARG, "null argument");
+  if (lp->m0 == 0) return SCYLLA_OK;
+  return const_cast<scylla_lp*>(lp)->fetch_y(y, int(lp->m0));
+}
+
+extern "C" int scylla_get_primal_device(const scylla_lp* lp, double* x_device) {
+  if (!lp || !x_device) FAIL(SCYLLA_ERR_INVALID_ARG, "null argument");
+  scylla_lp* h = const_cast<scylla_lp*>(lp);
+  int rc = h->fetch_x(nullptr, int(lp->n0));
+  if (rc != SCYLLA_OK) return rc;
+  CK(cudaMemcpyAsync(x_device, h->io_x, sizeof(double) * lp->n0, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return SCYLLA_OK;
+}
+
+extern "C" int scylla_get_state(const scylla_lp* lp, double* x, double* y, double* eta, double* omega) {
+  if (!lp || !x || (!y && lp->m > 0)) FAIL(SCYLLA_ERR_INVALID_ARG, "null argument");
+  scylla_lp* h = const_cast<scylla_lp*>(lp);
+  int rc = h->fetch_x(x, lp->n);
+  if (rc != SCYLLA_OK) return rc;
+  if (lp->m > 0) {
+    rc = h->fetch_y(y, lp->m);
+    if (rc != SCYLLA_OK) return rc;
+  }
+  CK(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (eta) *eta = h->h_ctl->eta;
+  if (omega) *omega = h->h_ctl->omega;
+  return SCYLLA_OK;
+}
+
+extern "C" int scylla_set_state(scylla_lp* lp, const double* x, const double* y, double eta, double omega) {
+  if (!lp || !x || (!y && lp->m > 0)) FAIL(SCYLLA_ERR_INVALID_ARG, "null argument");
+  if (!(eta > 0.0) || !(omega > 0.0) || !std::isfinite(eta) || !std::isfinite(omega))
+    FAIL(SCYLLA_ERR_INVALID_ARG, "eta and omega must be positive and finite");
+  for (int j = 0; j < lp->n; ++j)
+    if (!std::isfinite(x[j])) FAIL(SCYLLA_ERR_INVALID_ARG, "x not finite");
+  for (int i = 0; i < lp->m; ++i)
+    if (!std::isfinite(y[i])) FAIL(SCYLLA_ERR_INVALID_ARG, "y not finite");
+  cudaStream_t st = lp->st;
+  CK(cudaMemcpyAsync(lp->io_x, x, sizeof(double) * lp->n, cudaMemcpyHostToDevice, st));
+  if (lp->m > 0) CK(cudaMemcpyAsync(lp->io_y, y, sizeof(double) * lp->m, cudaMemcpyHostToDevice, st));
+  if (lp->p.precision == SCYLLA_PREC_MIXED) CK(launch_set_xy<float>(lp->d32, lp->io_x, lp->io_y, st));
+  else CK(launch_set_xy<double>(lp->d64, lp->io_x, lp->io_y, st));
+  CK(cudaMemcpyAsync(lp->h_ctl, lp->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  lp->h_ctl->eta = eta;
+  lp->h_ctl->omega = omega;
+  CK(cudaMemcpyAsync(lp->ctl, lp->h_ctl, sizeof(Control), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return SCYLLA_OK;
+}
+
+extern "C" int scylla_get_scaling(const scylla_lp* lp, double* R, double* C) {
+  if (!lp || !C || (!R && lp->m > 0)) FAIL(SCYLLA_ERR_INVALID_ARG, "null argument");
+  if (lp->m > 0) CK(cudaMemcpyAsync(R, lp->R, sizeof(double) * lp->m, cudaMemcpyDeviceToHost, lp->st));
+  CK(cudaMemcpyAsync(C, lp->C, sizeof(double) * lp->n, cudaMemcpyDeviceToHost, lp->st));
+  CK(cudaStreamSynchronize(lp->st));
+  return SCYLLA_OK;
+}

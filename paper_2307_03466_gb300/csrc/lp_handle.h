@@ -1,0 +1,75 @@
+// The LP handle behind the opaque scylla_lp of scylla.h (host-side definition).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "internal.h"
+
+struct scylla_lp {
+  scylla_params p{};
+  int device = 0;
+  cudaStream_t st = nullptr;       // the handle's own stream (graphs are captured on it)
+  cudaStream_t user_st = nullptr;  // caller's stream: its prior work is ordered before each call
+  cudaEvent_t ev_user = nullptr, ev0 = nullptr, ev1 = nullptr;
+
+  // original MIP on the host (fix-and-propagate, feasibility test, run loop)
+  int64_t m0 = 0, n0 = 0, nnz0 = 0;
+  std::vector<int64_t> rowptr0;
+  std::vector<int32_t> cols0;
+  std::vector<double> vals0;
+  std::vector<double> c0, lo0, hi0, l0, u0;
+  std::vector<uint8_t> int0;
+  std::vector<int64_t> colptr0;  // transpose structure: rows of each column, ascending
+  std::vector<int32_t> colrows0;
+  double c0norm = 0.0;
+  int64_t n_int = 0;
+  std::vector<int> kind;     // 0 continuous, 1 integer with u - l = 1, 2 general integer
+  std::vector<int> aux_of;   // auxiliary index of a general integer column, else -1
+  std::vector<int32_t> gen_int;
+  int64_t n_aux = 0;
+
+  // LP iterated on the device (original + auxiliary)
+  int m = 0, n = 0, nnz = 0;
+  int a_ntiles = 0, t_ntiles = 0;
+  int grid_p = 1, grid_d = 1, grid_c1 = 1, grid_c2 = 1, red_blocks = 1;
+
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  int *a_rowptr = nullptr, *a_cols = nullptr, *a_tiles = nullptr;
+  int *t_rowptr = nullptr, *t_cols = nullptr, *t_tiles = nullptr;
+  double *a_vals64 = nullptr, *t_vals64 = nullptr;
+  float *a_vals32 = nullptr, *t_vals32 = nullptr;
+  double *c_un = nullptr, *l_un = nullptr, *u_un = nullptr, *lo_un = nullptr, *hi_un = nullptr;
+  double *c64 = nullptr, *l64 = nullptr, *u64 = nullptr, *lo64 = nullptr, *hi64 = nullptr;
+  float *c32 = nullptr, *l32 = nullptr, *u32 = nullptr, *lo32 = nullptr, *hi32 = nullptr;
+  double *R = nullptr, *C = nullptr, *R2 = nullptr, *C2 = nullptr;
+  uint8_t* int_mask = nullptr;
+  double *c_orig = nullptr, *l_orig = nullptr, *u_orig = nullptr, *xhat_d = nullptr;
+  int *kind_d = nullptr, *aux_of_d = nullptr;
+  char* X[3] = {nullptr, nullptr, nullptr};
+  char* Y[3] = {nullptr, nullptr, nullptr};
+  char* AX[3] = {nullptr, nullptr, nullptr};
+  char* ATY[2] = {nullptr, nullptr};
+  char *XLR = nullptr, *YLR = nullptr;
+  double *part_p = nullptr, *part_d = nullptr, *part_c1 = nullptr, *part_c2 = nullptr, *red = nullptr;
+  double *io_x = nullptr, *io_y = nullptr;
+  scylla::Control* ctl = nullptr;
+  scylla::Control* h_ctl = nullptr;  // pinned host mirror
+  scylla::DevLP<double> d64{};
+  scylla::DevLP<float> d32{};
+
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+
+  scylla::DevObjective objective_desc();
+  void release();
+  int order_after_user();
+  int solve(double tol, int64_t iter_limit, int stall_checks, scylla_pdhg_result* out);
+  int set_objective(const double* xhat, int32_t K);
+  int fetch_x(double* host, int count);
+  int fetch_y(double* host, int count);
+};

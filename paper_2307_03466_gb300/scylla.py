@@ -1,0 +1,272 @@
+"""Thin Python binding of the C ABI in ``include/scylla.h`` (ctypes).
+
+Argument marshalling only: every step of the PDHG path runs in the CUDA kernels of
+``libscylla.so`` and the host rounding step in its C++ code.  The names follow the
+C functions (``scylla_lp_create`` -> ``LP(...)``, ``scylla_pdhg_solve`` ->
+``LP.pdhg_solve`` ...).  If the library is missing this module raises at import
+of ``lib()``: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libscylla.so")
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -6
+CONVERGED, ITER_LIMIT, STALLED, NUMERICAL = 0, 1, 2, 3
+FOUND, NOT_FOUND = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+
+
+class ScyllaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"scylla error {code}: {msg}")
+        self.code = code
+
+
+class Csr(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("nnz", C.c_int64),
+                ("rowptr", C.POINTER(C.c_int64)), ("cols", C.POINTER(C.c_int32)),
+                ("vals", C.POINTER(C.c_double))]
+
+
+class Params(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("n_check", C.c_int32), ("ruiz_iters", C.c_int32),
+                ("pock_chambolle", C.c_int32), ("adaptive_step", C.c_int32), ("restarts", C.c_int32),
+                ("primal_weight_update", C.c_int32), ("stall_checks", C.c_int32),
+                ("aux_general_integers", C.c_int32), ("use_graph", C.c_int32),
+                ("fixed_step_factor", C.c_double), ("beta_sufficient", C.c_double),
+                ("beta_necessary", C.c_double), ("beta_artificial", C.c_double), ("pw_smoothing", C.c_double),
+                ("step_reduction_exp", C.c_double), ("step_growth_exp", C.c_double),
+                ("alpha", C.c_double), ("eps1", C.c_double), ("beta", C.c_double), ("eps_floor", C.c_double),
+                ("max_rounds", C.c_int64), ("iter_limit", C.c_int64), ("total_iter_cap", C.c_int64),
+                ("run_stall_checks", C.c_int32), ("reserved0", C.c_int32), ("seed", C.c_uint64),
+                ("time_limit_s", C.c_double)]
+
+
+class PdhgResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("used_average", C.c_int32), ("iterations", C.c_int64),
+                ("accepted", C.c_int64), ("rejected", C.c_int64), ("restarts", C.c_int64),
+                ("eps_p", C.c_double), ("eps_d", C.c_double), ("eps_g", C.c_double), ("rel_kkt", C.c_double),
+                ("pobj", C.c_double), ("dobj", C.c_double), ("eta", C.c_double), ("omega", C.c_double),
+                ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class RunResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("found_by", C.c_int32), ("rounds", C.c_int64),
+                ("total_iterations", C.c_int64), ("perturbations", C.c_int64), ("objective", C.c_double),
+                ("seconds", C.c_double), ("seconds_pdhg", C.c_double), ("seconds_fixprop", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_SIGS = {
+    "scylla_default_params": (None, [C.POINTER(Params)]),
+    "scylla_lp_create": (C.c_int, [C.POINTER(Csr), _D, _D, _D, _D, _D, C.POINTER(C.c_uint8),
+                                   C.POINTER(Params), _P, C.POINTER(_P)]),
+    "scylla_lp_destroy": (None, [_P]),
+    "scylla_lp_dims": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_int64)]),
+    "scylla_pdhg_solve": (C.c_int, [_P, C.c_double, C.c_int64, C.POINTER(PdhgResult)]),
+    "scylla_set_objective": (C.c_int, [_P, _D, C.c_int32]),
+    "scylla_get_objective": (C.c_int, [_P, _D, _D]),
+    "scylla_run": (C.c_int, [_P, _D, C.POINTER(RunResult)]),
+    "scylla_get_primal": (C.c_int, [_P, _D]),
+    "scylla_get_dual": (C.c_int, [_P, _D]),
+    "scylla_get_primal_device": (C.c_int, [_P, C.c_void_p]),
+    "scylla_get_state": (C.c_int, [_P, _D, _D, _D, _D]),
+    "scylla_set_state": (C.c_int, [_P, _D, _D, C.c_double, C.c_double]),
+    "scylla_get_scaling": (C.c_int, [_P, _D, _D]),
+    "scylla_fix_and_propagate": (C.c_int, [_P, _D, _D, _D, _D, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                           C.POINTER(C.c_uint8)]),
+    "scylla_check_feasible": (C.c_int, [_P, _D, C.POINTER(C.c_int32)]),
+    "scylla_perturb": (C.c_int, [_P, _D, _D, C.c_int32, C.c_int64, C.c_uint64, C.POINTER(C.c_int64)]),
+    "scylla_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib(path: str = LIB_PATH) -> C.CDLL:
+    """Load libscylla.so (raises if it was not built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} not built; run python -m paper_2307_03466_gb300.build")
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise ScyllaError(rc, lib().scylla_last_error().decode())
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().scylla_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _f64(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != (n,):
+        raise ValueError(f"expected length {n}, got {a.shape}")
+    return a
+
+
+class LP:
+    """An LP handle (``scylla_lp``).  Inputs are host arrays, copied at create."""
+
+    def __init__(self, rowptr, cols, vals, c, row_lo, row_hi, col_lo, col_hi, is_integer, m: int, n: int,
+                 params: Params | None = None, stream=None):
+        L = lib()
+        self._rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        self._cols = np.ascontiguousarray(cols, dtype=np.int32)
+        self._vals = np.ascontiguousarray(vals, dtype=np.float64)
+        self.m, self.n = int(m), int(n)
+        csr = Csr(self.m, self.n, int(self._rowptr[-1]) if len(self._rowptr) else 0,
+                  self._rowptr.ctypes.data_as(C.POINTER(C.c_int64)),
+                  self._cols.ctypes.data_as(C.POINTER(C.c_int32)), _dp(self._vals))
+        c = _f64(c, n)
+        lo = _f64(row_lo, m)
+        hi = _f64(row_hi, m)
+        l = _f64(col_lo, n)
+        u = _f64(col_hi, n)
+        ii = np.ascontiguousarray(is_integer, dtype=np.uint8)
+        self.params = params if params is not None else default_params()
+        h = _P()
+        st = _P(stream) if stream is not None else None
+        _check(L.scylla_lp_create(C.byref(csr), _dp(c), _dp(lo), _dp(hi), _dp(l), _dp(u),
+                                  ii.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(self.params), st, C.byref(h)))
+        self.h = h
+        mt, nt, zt, na = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        _check(L.scylla_lp_dims(self.h, C.byref(mt), C.byref(nt), C.byref(zt), C.byref(na)))
+        self.m_total, self.n_total, self.nnz_total, self.n_aux = mt.value, nt.value, zt.value, na.value
+
+    @classmethod
+    def from_instance(cls, inst, params: Params | None = None, stream=None) -> "LP":
+        return cls(inst.rowptr, inst.cols, inst.vals, inst.c, inst.lo, inst.hi, inst.l, inst.u, inst.is_int,
+                   inst.m, inst.n, params, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().scylla_lp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def pdhg_solve(self, tol: float, iter_limit: int) -> PdhgResult:
+        r = PdhgResult()
+        _check(lib().scylla_pdhg_solve(self.h, float(tol), int(iter_limit), C.byref(r)))
+        return r
+
+    def set_objective(self, xhat, K: int):
+        x = _f64(xhat, self.n)
+        _check(lib().scylla_set_objective(self.h, _dp(x), int(K)))
+
+    def get_objective(self):
+        c = np.empty(self.n_total)
+        off = C.c_double()
+        _check(lib().scylla_get_objective(self.h, _dp(c), C.byref(off)))
+        return c, off.value
+
+    def run(self):
+        x = np.zeros(self.n)
+        r = RunResult()
+        _check(lib().scylla_run(self.h, _dp(x), C.byref(r)))
+        return r, x
+
+    def primal(self) -> np.ndarray:
+        x = np.empty(self.n)
+        _check(lib().scylla_get_primal(self.h, _dp(x)))
+        return x
+
+    def dual(self) -> np.ndarray:
+        y = np.empty(self.m)
+        _check(lib().scylla_get_dual(self.h, _dp(y) if self.m else None))
+        return y
+
+    def primal_device(self, ptr: int):
+        _check(lib().scylla_get_primal_device(self.h, C.c_void_p(ptr)))
+
+    def get_state(self):
+        x = np.empty(self.n_total)
+        y = np.empty(self.m_total)
+        eta, om = C.c_double(), C.c_double()
+        _check(lib().scylla_get_state(self.h, _dp(x), _dp(y) if self.m_total else None, C.byref(eta), C.byref(om)))
+        return x, y, eta.value, om.value
+
+    def set_state(self, x, y, eta: float, omega: float):
+        x = _f64(x, self.n_total)
+        y = _f64(y, self.m_total)
+        _check(lib().scylla_set_state(self.h, _dp(x), _dp(y) if self.m_total else None, float(eta), float(omega)))
+
+    def scaling(self):
+        R = np.empty(self.m_total)
+        Cc = np.empty(self.n_total)
+        _check(lib().scylla_get_scaling(self.h, _dp(R) if self.m_total else None, _dp(Cc)))
+        return R, Cc
+
+    def fix_and_propagate(self, xbar):
+        xb = _f64(xbar, self.n)
+        xhat = np.empty(self.n)
+        dl = np.empty(self.n)
+        du = np.empty(self.n)
+        fixed = np.empty(self.n, dtype=np.int32)
+        nf = C.c_int64()
+        ign = np.empty(max(self.m, 1), dtype=np.uint8)
+        _check(lib().scylla_fix_and_propagate(self.h, _dp(xb), _dp(xhat), _dp(dl), _dp(du),
+                                              fixed.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(nf),
+                                              ign.ctypes.data_as(C.POINTER(C.c_uint8))))
+        return xhat, dl, du, fixed[: nf.value].astype(np.int64), ign[: self.m].astype(bool)
+
+    def check_feasible(self, x) -> bool:
+        xx = _f64(x, self.n)
+        f = C.c_int32()
+        _check(lib().scylla_check_feasible(self.h, _dp(xx), C.byref(f)))
+        return bool(f.value)
+
+    def perturb(self, xhat, xbar, kind: int, K: int, seed: int):
+        x = _f64(xhat, self.n).copy()
+        xb = _f64(xbar, self.n)
+        fl = C.c_int64()
+        _check(lib().scylla_perturb(self.h, _dp(x), _dp(xb), int(kind), int(K), int(seed), C.byref(fl)))
+        return x, fl.value

@@ -1,0 +1,175 @@
+"""GPU PDHG (through the C ABI) against the FP64 oracle.
+
+The FP64 iterates must agree with the oracle within 1e-9 relative (max abs error
+over max(1, max |oracle|)) after fixed iteration counts, in the fixed-step mode
+(no discrete decisions) and the full adaptive mode (step rejections, restarts,
+primal-weight updates), with the same decision counts.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import pdhg as O
+from tests.gpu_common import INF, gpu_available, long_row_instance, pair, parity_instances, rel_err
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
+
+TOL = 1e-9
+INSTANCES = parity_instances()
+
+
+def compare_after(inst, k, **kw):
+    g, o = pair(inst, **kw)
+    rg = g.pdhg_solve(0.0, k)
+    ro = o.solve(0.0, k)
+    xg, yg, eta_g, om_g = g.get_state()
+    assert rg.status == ro.status == O.ITER_LIMIT
+    assert rg.iterations == ro.iterations == k
+    assert (rg.accepted, rg.rejected, rg.restarts) == (ro.accepted, ro.rejected, ro.restarts)
+    assert bool(rg.used_average) == ro.used_average
+    ex = rel_err(xg, o.primal())
+    ey = rel_err(yg, o.dual())
+    assert ex <= TOL and ey <= TOL, (ex, ey)
+    assert abs(eta_g - o.eta) <= 1e-9 * o.eta and abs(om_g - o.omega) <= 1e-9 * o.omega
+    assert abs(rg.rel_kkt - ro.rel_kkt) <= 1e-9 * max(1.0, ro.rel_kkt)
+    g.close()
+
+
+@pytest.mark.parametrize("name", list(INSTANCES))
+def test_preconditioning_matches_oracle(name):
+    inst = INSTANCES[name]
+    g, o = pair(inst)
+    R, C = g.scaling()
+    assert rel_err(R, o.R) <= 1e-13 and rel_err(C, o.C) <= 1e-13
+    g.close()
+
+
+@pytest.mark.parametrize("name", list(INSTANCES))
+@pytest.mark.parametrize("k", [1, 10, 100, 1000])
+def test_fixed_step_iterates_match_oracle(name, k):
+    compare_after(INSTANCES[name], k, adaptive_step=False, restarts=False)
+
+
+@pytest.mark.parametrize("name", list(INSTANCES))
+@pytest.mark.parametrize("k", [1, 10, 100, 1000])
+def test_adaptive_iterates_match_oracle(name, k):
+    compare_after(INSTANCES[name], k)
+
+
+@pytest.mark.parametrize("k", [1, 63, 64, 65, 200])
+def test_iteration_limits_off_the_check_grid(k):
+    compare_after(INSTANCES["packcover_2kx4k"], k)
+
+
+def test_small_check_interval_and_no_pock_chambolle():
+    compare_after(INSTANCES["long_rows"], 300, n_check=7, pock_chambolle=False, ruiz_iters=3)
+
+
+@pytest.mark.parametrize("name", ["setcover_200x500", "packcover_2kx4k", "knapcover_700"])
+def test_converges_like_oracle(name):
+    inst = INSTANCES[name]
+    g, o = pair(inst)
+    rg = g.pdhg_solve(1e-6, 200000)
+    ro = o.solve(1e-6, 200000)
+    assert rg.status == ro.status == O.CONVERGED
+    assert rg.iterations == ro.iterations
+    assert rel_err(g.primal(), o.primal()[: inst.n]) <= 1e-8
+    assert abs(rg.pobj - ro.pobj) <= 1e-9 * (1 + abs(ro.pobj))
+    g.close()
+
+
+def test_warm_start_second_solve_is_immediate():
+    inst = INSTANCES["setcover_200x500"]
+    g, _ = pair(inst)
+    r1 = g.pdhg_solve(1e-6, 100000)
+    assert r1.status == O.CONVERGED
+    x = g.primal()
+    r2 = g.pdhg_solve(1e-6, 100000)
+    assert r2.iterations == 0 and r2.status == O.CONVERGED
+    np.testing.assert_array_equal(g.primal(), x)
+    g.close()
+
+
+def test_iteration_limit_zero_and_tolerance_zero():
+    inst = INSTANCES["knapcover_700"]
+    g, o = pair(inst)
+    r = g.pdhg_solve(0.0, 0)
+    ro = o.solve(0.0, 0)
+    assert r.iterations == 0 and r.status == O.ITER_LIMIT
+    assert abs(r.rel_kkt - ro.rel_kkt) <= 1e-12 * max(1, ro.rel_kkt)
+    g.close()
+
+
+def test_box_lp_without_rows():
+    import scipy.sparse as sp
+    from paper_2307_03466_gb300 import instances as I
+    rng = np.random.default_rng(2)
+    n = 1000
+    c = rng.normal(size=n)
+    l = rng.uniform(-5, 0, size=n)
+    u = rng.uniform(0, 5, size=n)
+    inst = I.Instance("box", 0, n, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0), c,
+                      np.zeros(0), np.zeros(0), l, u, np.zeros(n, np.uint8))
+    g, _ = pair(inst)
+    r = g.pdhg_solve(1e-10, 100000)
+    assert r.status == O.CONVERGED
+    np.testing.assert_allclose(g.primal(), np.where(c > 0, l, u), atol=1e-8)
+    g.close()
+
+
+def test_graph_and_direct_launch_agree():
+    inst = INSTANCES["packcover_2kx4k"]
+    g1, _ = pair(inst)
+    g2, _ = pair(inst, use_graph=0)
+    r1 = g1.pdhg_solve(1e-5, 5000)
+    r2 = g2.pdhg_solve(1e-5, 5000)
+    assert r1.iterations == r2.iterations
+    np.testing.assert_array_equal(g1.primal(), g2.primal())
+    g1.close()
+    g2.close()
+
+
+def test_state_roundtrip_and_resume():
+    inst = INSTANCES["packcover_2kx4k"]
+    g, _ = pair(inst)
+    g.pdhg_solve(0.0, 200)
+    x, y, eta, om = g.get_state()
+    g.pdhg_solve(0.0, 300)
+    xa = g.primal()
+    h, _ = pair(inst)
+    h.set_state(x, y, eta, om)
+    h.pdhg_solve(0.0, 300)
+    assert rel_err(h.primal(), xa) <= 1e-12
+    g.close()
+    h.close()
+
+
+def test_stall_rule_matches_oracle():
+    inst = INSTANCES["setcover_200x500"]
+    g, o = pair(inst, stall_checks=2)
+    rg = g.pdhg_solve(1e-12, 100000)
+    ro = o.solve(1e-12, 100000)
+    assert rg.status == ro.status
+    assert rg.iterations == ro.iterations
+    g.close()
+
+
+@pytest.mark.parametrize("name", ["setcover_200x500", "packcover_2kx4k", "mcf_small"])
+def test_mixed_precision_reaches_1e4_checked_by_oracle(name):
+    """FP32 bulk iteration with FP64 checks reaches relative KKT <= 1e-4; the oracle
+    re-evaluates the returned point in FP64 and the objective error is bounded."""
+    inst = INSTANCES[name]
+    g, o = pair(inst, precision=1)
+    r = g.pdhg_solve(1e-4, 200000)
+    assert r.status == O.CONVERGED and r.rel_kkt <= 1e-4
+    x, y, _, _ = g.get_state()
+    o.set_state(x, y)
+    ev = o.evaluate(o.x, o.y)
+    assert ev.rel_kkt <= 1.2e-4, ev
+    ref = O.OracleLP(inst.csr(), inst.c, inst.lo, inst.hi, inst.l, inst.u)
+    rr = ref.solve(1e-8, 400000)
+    assert rr.status == O.CONVERGED
+    obj_err = abs(ev.pobj - rr.pobj) / (1 + abs(rr.pobj))
+    assert obj_err <= 1e-2
+    g.close()
