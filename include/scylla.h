@@ -95,7 +95,7 @@ typedef struct {
   int64_t iter_limit;           /* PDHG attempts per solve inside scylla_run (20000) */
   int64_t total_iter_cap;       /* PDHG attempts over the whole run (1e9) */
   int32_t run_stall_checks;     /* stall_checks used by scylla_run's solves (5) */
-  int32_t reserved0;
+  int32_t trace_capacity;       /* attempts recorded by the decision trace of each solve; 0 = off (0) */
   uint64_t seed;                /* perturbation random stream (0) */
   double time_limit_s;          /* wall-clock limit of scylla_run, <= 0 for none (0) */
 } scylla_params;
@@ -185,6 +185,18 @@ int scylla_get_state(const scylla_lp* lp, double* x, double* y, double* eta, dou
  * primal-dual pair).  Same layout as scylla_get_state; eta, omega > 0. */
 int scylla_set_state(scylla_lp* lp, const double* x, const double* y, double eta, double omega);
 
+/* Cold restart: x = proj_[l,u](0), y = 0 (Algorithm 1 initialisation) and the step
+ * size and primal weight chosen at create.  The objective is left as it is. */
+int scylla_reset_state(scylla_lp* lp);
+
+/* Measurement: run `attempts` PDHG attempts from the current pair (no tolerance
+ * test; every n_check attempts the check kernels run as in a solve) as separate
+ * launches on the handle's stream, with CUDA events around each launch, and write
+ * the mean device time in milliseconds of each kernel to ms[0..3]: primal step,
+ * dual step, column check, row check (0 where a kernel did not run).  The pair
+ * moves on by those attempts. */
+int scylla_time_kernels(scylla_lp* lp, int32_t attempts, double* ms);
+
 /* Diagonal scaling A~ = diag(R) A diag(C) found at create: host, R length m_total,
  * C length n_total. */
 int scylla_get_scaling(const scylla_lp* lp, double* R, double* C);
@@ -207,6 +219,16 @@ int scylla_check_feasible(const scylla_lp* lp, const double* x, int32_t* feasibl
  * *flipped (may be NULL) receives the number of changed entries. */
 int scylla_perturb(const scylla_lp* lp, double* xhat, const double* xbar, int32_t kind, int64_t K,
                    uint64_t seed, int64_t* flipped);
+
+/* Decision trace of the last solve (enabled by params.trace_capacity > 0).
+ *   steps: host, 4 * trace_capacity doubles; for attempt k = 1, 2, ... the record
+ *   (eta used, eta_max of the adaptive rule, accepted 0/1, eta for the next
+ *   attempt).  checks: host, 5 * trace_capacity doubles; for every check that
+ *   neither terminated nor was the start-point evaluation, the record (k, restart
+ *   0/1, candidate is the average 0/1, primal weight after the check, weighted KKT
+ *   of the candidate).  *n_steps, *n_checks receive the record counts (capped at
+ *   trace_capacity). */
+int scylla_get_trace(const scylla_lp* lp, double* steps, int64_t* n_steps, double* checks, int64_t* n_checks);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* scylla_last_error(void);

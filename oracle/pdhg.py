@@ -299,8 +299,24 @@ class OracleLP:
         return rounding_hash((x_s[ic] * self.C[ic]) if len(ic) else np.zeros(0), ic)
 
     # -- Algorithm 1 inner loop with PDLP's step size, averaging and restarts ---
-    def solve(self, tol: float, iter_limit: int, trace: bool = False) -> SolveResult:
+    def solve(self, tol: float, iter_limit: int, trace: bool = False, replay=None) -> SolveResult:
+        """PDHG from the current pair until rel-KKT <= tol or k = iter_limit.
+
+        ``trace`` records, per attempt, ("step", k, accept, eta_used, eta_max,
+        eta_next) and, per check that neither starts nor ends the solve,
+        ("check", k, restart, candidate_is_average, omega_after, kkt_candidate) --
+        all as this oracle computes them.  ``replay = (steps, checks)`` takes the
+        scalar decisions from another implementation's trace instead (eta used,
+        accept, eta next per attempt; restart, candidate and omega per check) while
+        still computing and recording its own: adaptive PDHG amplifies rounding
+        differences chaotically, so iterate parity beyond a few attempts is only
+        meaningful along the same decision sequence.
+        """
         p = self.p
+        if replay is not None:
+            trace = True
+            r_steps, r_checks = replay
+        ci = 0
         x, y = self.x, self.y
         eta, omega = self.eta, self.omega
         k = 0
@@ -321,7 +337,10 @@ class OracleLP:
         if ev_c.rel_kkt <= tol:
             status = CONVERGED
         while status is None and k < iter_limit:
+            if replay is not None:
+                eta = float(r_steps[k][0])
             x_new, y_new = self.pdhg_step(x, y, eta, omega)
+            eta_max = INF
             if p.adaptive_step:
                 dx = x_new - x
                 dy = y_new - y
@@ -339,7 +358,10 @@ class OracleLP:
                 eta_used = eta
             k += 1
             if trace:
-                tr.append(("step", k, bool(accept), eta_used))
+                tr.append(("step", k, bool(accept), eta_used, eta_max, eta))
+            if replay is not None:
+                accept = bool(r_steps[k - 1][2] > 0.5)
+                eta = float(r_steps[k - 1][3])
             if accept:
                 accepted += 1
                 x, y = x_new, y_new
@@ -381,21 +403,30 @@ class OracleLP:
             do_restart = (kc <= p.beta_sufficient * kkt_lr
                           or (kc <= p.beta_necessary * kkt_lr and kc > kkt_prev)
                           or (k - k_lr) >= p.beta_artificial * k)
+            omega_new = omega
+            if do_restart and p.primal_weight_update:
+                ddx = float(np.linalg.norm(xc - x_lr))
+                ddy = float(np.linalg.norm(yc - y_lr))
+                if ddx > 1e-10 and ddy > 1e-10:
+                    omega_new = math.exp(p.pw_smoothing * math.log(ddy / ddx)
+                                         + (1.0 - p.pw_smoothing) * math.log(omega))
+            if trace:
+                tr.append(("check", k, bool(do_restart), is_avg, omega_new, kc))
+            if replay is not None:
+                rec = r_checks[ci]
+                ci += 1
+                do_restart = bool(rec[1] > 0.5)
+                is_avg = bool(rec[2] > 0.5)
+                xc, yc, evc = (x_avg, y_avg, ev_a) if is_avg else (x, y, ev_c)
+                omega_new = float(rec[3])
             if do_restart:
                 restarts += 1
-                if p.primal_weight_update:
-                    ddx = float(np.linalg.norm(xc - x_lr))
-                    ddy = float(np.linalg.norm(yc - y_lr))
-                    if ddx > 1e-10 and ddy > 1e-10:
-                        omega = math.exp(p.pw_smoothing * math.log(ddy / ddx)
-                                         + (1.0 - p.pw_smoothing) * math.log(omega))
+                omega = omega_new
                 x, y = xc, yc
                 x_lr, y_lr, k_lr = xc, yc, k
                 wsum = 0.0
                 kkt_lr = evc.weighted_kkt(omega)
                 kkt_prev = kkt_lr
-                if trace:
-                    tr.append(("restart", k, is_avg, omega))
             else:
                 kkt_prev = kc
         if status is None:

@@ -42,7 +42,7 @@ struct Control {
   double offset, bnorm, cnorm;
   double eps_p, eps_d, eps_g, rel_kkt, pobj, dobj;  // of the reported point
   double beta_s, beta_n, beta_a, theta, exp_red, exp_grow;
-  long long k, iter_limit, k_lr, accepted, rejected, restarts, chunks, max_chunks;
+  long long k, iter_limit, k_lr, accepted, rejected, restarts, chunks, max_chunks, n_ctrace;
   unsigned long long hash_accum, last_hash;
   int same_hash, stall_checks;
   int ix_cur, ix_next, ix_avg, ia_cur, ia_avg;
@@ -80,6 +80,9 @@ struct DevLP {
   Control* ctl;
   double *part_p, *part_d, *part_c1, *part_c2;
   int grid_p, grid_d, grid_c1, grid_c2;
+  double* trace_steps;   // 4 doubles per attempt, or null
+  double* trace_checks;  // 5 doubles per check, or null
+  int trace_cap;
 };
 
 // Buffers of the original (unaugmented) columns used by the objective update and
@@ -155,6 +158,15 @@ template <typename T>
 cudaError_t launch_check(const DevLP<T>& d, cudaStream_t st);
 template <typename T>
 cudaError_t launch_slot(const DevLP<T>& d, cudaStream_t st);
+// the two launches of one attempt and of one check, separately (measurement)
+template <typename T>
+cudaError_t launch_primal(const DevLP<T>& d, cudaStream_t st);
+template <typename T>
+cudaError_t launch_dual(const DevLP<T>& d, cudaStream_t st);
+template <typename T>
+cudaError_t launch_check_cols(const DevLP<T>& d, cudaStream_t st);
+template <typename T>
+cudaError_t launch_check_rows(const DevLP<T>& d, cudaStream_t st);
 cudaError_t launch_loop_ctl(Control* ctl, cudaGraphConditionalHandle h, cudaStream_t st);
 template <typename T>
 cudaError_t launch_get_x(const DevLP<T>& d, double* out, int count, cudaStream_t st);

@@ -252,7 +252,7 @@ __device__ __forceinline__ void spmv_tiles(const int* __restrict__ tiles, int nt
 // Adaptive step (PDLP): eta_max = (omega ||dx||^2 + ||dy||^2 / omega) / (2 |dy.A dx|);
 // eta' = min((1 - (k+1)^-0.3) eta_max, (1 + (k+1)^-0.6) eta), k the 1-based attempt
 // number; the attempt is accepted when eta <= eta_max.
-__device__ void step_control(Control* c, double dx2, double dy2, double inter) {
+__device__ void step_control(Control* c, double dx2, double dy2, double inter, double* trace, int cap) {
   if (!isfinite(dx2) || !isfinite(dy2) || !isfinite(inter)) {
     c->done = 1;
     c->status = SCYLLA_NUMERICAL;
@@ -262,12 +262,20 @@ __device__ void step_control(Control* c, double dx2, double dy2, double inter) {
   const double eta = c->eta, om = c->omega;
   bool accept = true;
   double eta_next = eta;
+  double eta_max = pos_inf<double>();
   if (c->adaptive) {
     const double mv = om * dx2 + dy2 / om;
-    const double eta_max = inter != 0.0 ? mv / (2.0 * fabs(inter)) : pos_inf<double>();
+    eta_max = inter != 0.0 ? mv / (2.0 * fabs(inter)) : pos_inf<double>();
     const double kk = double(k1 + 1);
     eta_next = fmin((1.0 - pow(kk, -c->exp_red)) * eta_max, (1.0 + pow(kk, -c->exp_grow)) * eta);
     accept = eta <= eta_max;
+  }
+  if (trace && k1 <= cap) {
+    double* t = trace + 4 * (k1 - 1);
+    t[0] = eta;
+    t[1] = eta_max;
+    t[2] = accept ? 1.0 : 0.0;
+    t[3] = eta_next;
   }
   c->k = k1;
   c->eta_used = eta;
@@ -375,7 +383,7 @@ __global__ void __launch_bounds__(kThreads) k_dual(DevLP<T> d) {
   reduce_partials<kNP>(d.part_p, d.grid_p, red);
   reduce_partials<kND>(d.part_d, d.grid_d, red + kNP);
   if (threadIdx.x == 0) {
-    step_control(ctl, red[0], red[1], red[2]);
+    step_control(ctl, red[0], red[1], red[2], d.trace_steps, d.trace_cap);
     ctl->cnt_dual = 0;
   }
 }
@@ -413,7 +421,7 @@ __device__ void finish(Control* c, int status, bool out_avg, const Eval& e) {
 
 // Termination (Section 2.2), stalling (Algorithm 1) and restarts (PDLP) from the
 // 18 reduced sums of the two check kernels.
-__device__ void check_control(Control* c, const double* r) {
+__device__ void check_control(Control* c, const double* r, double* trace, int cap) {
   Eval e[2];
   for (int q = 0; q < 2; ++q) {
     const double* cs = r + 5 * q;
@@ -471,6 +479,16 @@ __device__ void check_control(Control* c, const double* r) {
   const double kc = weighted_kkt(ec, om);
   const bool restart = kc <= c->beta_s * c->kkt_lr || (kc <= c->beta_n * c->kkt_lr && kc > c->kkt_prev) ||
                        double(c->k - c->k_lr) >= c->beta_a * double(c->k);
+  double* rec = nullptr;
+  if (trace && c->n_ctrace < cap) {
+    rec = trace + 5 * c->n_ctrace;
+    c->n_ctrace++;
+    rec[0] = double(c->k);
+    rec[1] = restart ? 1.0 : 0.0;
+    rec[2] = cand_avg ? 1.0 : 0.0;
+    rec[3] = c->omega;
+    rec[4] = kc;
+  }
   if (!restart) {
     c->kkt_prev = kc;
     return;
@@ -494,6 +512,7 @@ __device__ void check_control(Control* c, const double* r) {
   c->copy_lr = 1;
   c->kkt_lr = weighted_kkt(ec, c->omega);
   c->kkt_prev = c->kkt_lr;
+  if (rec) rec[3] = c->omega;
 }
 
 template <typename T>
@@ -607,7 +626,7 @@ __global__ void __launch_bounds__(kThreads) k_check_rows(DevLP<T> d) {
   reduce_partials<kNC1>(d.part_c1, d.grid_c1, red);
   reduce_partials<kNC2>(d.part_c2, d.grid_c2, red + kNC1);
   if (threadIdx.x == 0) {
-    check_control(ctl, red);
+    check_control(ctl, red, d.trace_checks, d.trace_cap);
     ctl->cnt_c2 = 0;
   }
 }
@@ -637,6 +656,7 @@ __global__ void k_solve_init(Control* c, double tol, long long iter_limit, int s
   c->used_avg = 0;
   c->accepted = c->rejected = c->restarts = 0;
   c->chunks = 0;
+  c->n_ctrace = 0;
   c->initial = 1;
   c->aty_valid = 0;
   c->copy_lr = 0;
@@ -1005,6 +1025,27 @@ cudaError_t launch_slot(const DevLP<T>& d, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_primal(const DevLP<T>& d, cudaStream_t st) {
+  k_primal<T><<<d.grid_p, kThreads, 0, st>>>(d);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_dual(const DevLP<T>& d, cudaStream_t st) {
+  k_dual<T><<<d.grid_d, kThreads, 0, st>>>(d);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_check_cols(const DevLP<T>& d, cudaStream_t st) {
+  k_check_cols<T><<<d.grid_c1, kThreads, 0, st>>>(d);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_check_rows(const DevLP<T>& d, cudaStream_t st) {
+  k_check_rows<T><<<d.grid_c2, kThreads, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_loop_ctl(Control* ctl, cudaGraphConditionalHandle h, cudaStream_t st) {
   k_loop_ctl<<<1, 1, 0, st>>>(ctl, h);
   return cudaGetLastError();
@@ -1052,6 +1093,10 @@ int occupancy_grid(int kernel_id, int work_tiles) {
   template cudaError_t launch_solve_init<T>(const DevLP<T>&, double, long long, int, long long, cudaStream_t); \
   template cudaError_t launch_check<T>(const DevLP<T>&, cudaStream_t);                                    \
   template cudaError_t launch_slot<T>(const DevLP<T>&, cudaStream_t);                                     \
+  template cudaError_t launch_primal<T>(const DevLP<T>&, cudaStream_t);                                   \
+  template cudaError_t launch_dual<T>(const DevLP<T>&, cudaStream_t);                                     \
+  template cudaError_t launch_check_cols<T>(const DevLP<T>&, cudaStream_t);                               \
+  template cudaError_t launch_check_rows<T>(const DevLP<T>&, cudaStream_t);                               \
   template cudaError_t launch_get_x<T>(const DevLP<T>&, double*, int, cudaStream_t);                      \
   template cudaError_t launch_get_y<T>(const DevLP<T>&, double*, int, cudaStream_t);                      \
   template cudaError_t launch_set_xy<T>(const DevLP<T>&, const double*, const double*, cudaStream_t);     \

@@ -73,6 +73,7 @@ extern "C" void scylla_default_params(scylla_params* p) {
   p->iter_limit = 20000;
   p->total_iter_cap = 1000000000LL;
   p->run_stall_checks = 5;
+  p->trace_capacity = 0;
   p->seed = 0;
   p->time_limit_s = 0.0;
 }
@@ -172,6 +173,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
                        scylla_lp* lp) {
   lp->p = *pin;
   if (lp->p.n_check < 1) FAIL(SCYLLA_ERR_INVALID_ARG, "n_check must be >= 1");
+  if (lp->p.trace_capacity < 0) FAIL(SCYLLA_ERR_INVALID_ARG, "trace_capacity must be >= 0");
   if (lp->p.precision != SCYLLA_PREC_FP64 && lp->p.precision != SCYLLA_PREC_MIXED)
     FAIL(SCYLLA_ERR_INVALID_ARG, "unknown precision");
   CK(cudaGetDevice(&lp->device));
@@ -357,6 +359,9 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     lp->io_x = ar.take<double>(n);
     lp->io_y = ar.take<double>(m);
     lp->ctl = ar.take<Control>(1);
+    const size_t tc = size_t(lp->p.trace_capacity);
+    lp->trace_steps = tc ? ar.take<double>(4 * tc) : nullptr;
+    lp->trace_checks = tc ? ar.take<double>(5 * tc) : nullptr;
     if (pass == 0) lp->arena_bytes = ar.off + 256;
   }
   cudaStream_t st = lp->st;
@@ -425,6 +430,8 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     Control h{};
     h.eta = eta;
     h.omega = (cn > 0.0 && qn > 0.0) ? cn / qn : 1.0;
+    lp->eta0 = h.eta;
+    lp->omega0 = h.omega;
     h.ix_cur = 0; h.ix_next = 1; h.ix_avg = 2; h.ia_cur = 0; h.ia_avg = 1;
     h.adaptive = lp->p.adaptive_step ? 1 : 0;
     h.restarts_on = lp->p.restarts ? 1 : 0;
@@ -491,6 +498,9 @@ void fill_dev(DevLP<T>& d, scylla_lp* lp) {
   d.ctl = lp->ctl;
   d.part_p = lp->part_p; d.part_d = lp->part_d; d.part_c1 = lp->part_c1; d.part_c2 = lp->part_c2;
   d.grid_p = lp->grid_p; d.grid_d = lp->grid_d; d.grid_c1 = lp->grid_c1; d.grid_c2 = lp->grid_c2;
+  d.trace_steps = lp->trace_steps;
+  d.trace_checks = lp->trace_checks;
+  d.trace_cap = lp->p.trace_capacity;
 }
 }  // namespace
 
@@ -787,4 +797,87 @@ extern "C" int scylla_get_scaling(const scylla_lp* lp, double* R, double* C) {
   CK(cudaMemcpyAsync(C, lp->C, sizeof(double) * lp->n, cudaMemcpyDeviceToHost, lp->st));
   CK(cudaStreamSynchronize(lp->st));
   return SCYLLA_OK;
+}
+
+extern "C" int scylla_get_trace(const scylla_lp* lp, double* steps, int64_t* n_steps, double* checks,
+                                int64_t* n_checks) {
+  if (!lp) FAIL(SCYLLA_ERR_INVALID_ARG, "null handle");
+  const int64_t cap = lp->p.trace_capacity;
+  scylla_lp* h = const_cast<scylla_lp*>(lp);
+  CK(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  const int64_t ns = std::min<int64_t>(cap, h->h_ctl->k), nc = std::min<int64_t>(cap, h->h_ctl->n_ctrace);
+  if (steps && ns > 0) CK(cudaMemcpy(steps, h->trace_steps, sizeof(double) * 4 * ns, cudaMemcpyDeviceToHost));
+  if (checks && nc > 0) CK(cudaMemcpy(checks, h->trace_checks, sizeof(double) * 5 * nc, cudaMemcpyDeviceToHost));
+  if (n_steps) *n_steps = ns;
+  if (n_checks) *n_checks = nc;
+  return SCYLLA_OK;
+}
+
+extern "C" int scylla_reset_state(scylla_lp* lp) {
+  if (!lp) FAIL(SCYLLA_ERR_INVALID_ARG, "null handle");
+  int rc = lp->order_after_user();
+  if (rc != SCYLLA_OK) return rc;
+  cudaStream_t st = lp->st;
+  if (lp->p.precision == SCYLLA_PREC_MIXED) CK(launch_init_point<float>(lp->d32, st));
+  else CK(launch_init_point<double>(lp->d64, st));
+  CK(cudaMemcpyAsync(lp->h_ctl, lp->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  lp->h_ctl->eta = lp->eta0;
+  lp->h_ctl->omega = lp->omega0;
+  CK(cudaMemcpyAsync(lp->ctl, lp->h_ctl, sizeof(Control), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return SCYLLA_OK;
+}
+
+template <typename T>
+static int time_kernels_impl(scylla_lp* lp, const DevLP<T>& d, int attempts, double* ms) {
+  cudaStream_t st = lp->st;
+  const int nchk = lp->p.n_check;
+  const int nev = 2 * (attempts + 2 * (attempts / nchk + 1)) + 2;
+  std::vector<cudaEvent_t> ev(nev);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  double sum[4] = {0, 0, 0, 0};
+  int cnt[4] = {0, 0, 0, 0};
+  std::vector<int> which;
+  int q = 0;
+  auto timed = [&](int kind, cudaError_t (*fn)(const DevLP<T>&, cudaStream_t)) -> cudaError_t {
+    cudaError_t e = cudaEventRecord(ev[q], st);
+    if (e == cudaSuccess) e = fn(d, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[q + 1], st);
+    which.push_back(kind);
+    q += 2;
+    return e;
+  };
+  cudaError_t e = launch_solve_init<T>(d, 0.0, (long long)attempts + 1, 0, 1LL << 40, st);
+  if (e == cudaSuccess) e = launch_check<T>(d, st);
+  for (int a = 0; a < attempts && e == cudaSuccess; ++a) {
+    e = timed(0, launch_primal<T>);
+    if (e == cudaSuccess) e = timed(1, launch_dual<T>);
+    if (e == cudaSuccess && (a + 1) % nchk == 0) {
+      e = timed(2, launch_check_cols<T>);
+      if (e == cudaSuccess) e = timed(3, launch_check_rows<T>);
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) {
+    for (size_t i = 0; i < which.size(); ++i) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]);
+      sum[which[i]] += t;
+      cnt[which[i]]++;
+    }
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  CK(e);
+  for (int k = 0; k < 4; ++k) ms[k] = cnt[k] ? sum[k] / cnt[k] : 0.0;
+  return SCYLLA_OK;
+}
+
+extern "C" int scylla_time_kernels(scylla_lp* lp, int32_t attempts, double* ms) {
+  if (!lp || !ms || attempts < 1) FAIL(SCYLLA_ERR_INVALID_ARG, "need a handle, ms[4] and attempts >= 1");
+  int rc = lp->order_after_user();
+  if (rc != SCYLLA_OK) return rc;
+  return lp->p.precision == SCYLLA_PREC_MIXED ? time_kernels_impl<float>(lp, lp->d32, attempts, ms)
+                                              : time_kernels_impl<double>(lp, lp->d64, attempts, ms);
 }

@@ -56,10 +56,13 @@ struct scylla_lp {
   char *XLR = nullptr, *YLR = nullptr;
   double *part_p = nullptr, *part_d = nullptr, *part_c1 = nullptr, *part_c2 = nullptr, *red = nullptr;
   double *io_x = nullptr, *io_y = nullptr;
+  double *trace_steps = nullptr, *trace_checks = nullptr;
   scylla::Control* ctl = nullptr;
   scylla::Control* h_ctl = nullptr;  // pinned host mirror
   scylla::DevLP<double> d64{};
   scylla::DevLP<float> d32{};
+
+  double eta0 = 1.0, omega0 = 1.0;  // step size and primal weight chosen at create
 
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;

@@ -44,7 +44,7 @@ class Params(C.Structure):
                 ("step_reduction_exp", C.c_double), ("step_growth_exp", C.c_double),
                 ("alpha", C.c_double), ("eps1", C.c_double), ("beta", C.c_double), ("eps_floor", C.c_double),
                 ("max_rounds", C.c_int64), ("iter_limit", C.c_int64), ("total_iter_cap", C.c_int64),
-                ("run_stall_checks", C.c_int32), ("reserved0", C.c_int32), ("seed", C.c_uint64),
+                ("run_stall_checks", C.c_int32), ("trace_capacity", C.c_int32), ("seed", C.c_uint64),
                 ("time_limit_s", C.c_double)]
 
 
@@ -91,6 +91,9 @@ _SIGS = {
                                            C.POINTER(C.c_uint8)]),
     "scylla_check_feasible": (C.c_int, [_P, _D, C.POINTER(C.c_int32)]),
     "scylla_perturb": (C.c_int, [_P, _D, _D, C.c_int32, C.c_int64, C.c_uint64, C.POINTER(C.c_int64)]),
+    "scylla_get_trace": (C.c_int, [_P, _D, C.POINTER(C.c_int64), _D, C.POINTER(C.c_int64)]),
+    "scylla_reset_state": (C.c_int, [_P]),
+    "scylla_time_kernels": (C.c_int, [_P, C.c_int32, _D]),
     "scylla_last_error": (C.c_char_p, []),
 }
 
@@ -263,6 +266,24 @@ class LP:
         f = C.c_int32()
         _check(lib().scylla_check_feasible(self.h, _dp(xx), C.byref(f)))
         return bool(f.value)
+
+    def reset_state(self):
+        _check(lib().scylla_reset_state(self.h))
+
+    def time_kernels(self, attempts: int):
+        """Mean device ms of (primal, dual, check-cols, check-rows) launches."""
+        ms = np.zeros(4)
+        _check(lib().scylla_time_kernels(self.h, int(attempts), _dp(ms)))
+        return ms
+
+    def trace(self):
+        """(steps (N x 4), checks (M x 5)) of the last solve; see scylla_get_trace."""
+        cap = int(self.params.trace_capacity)
+        st = np.zeros(4 * max(cap, 1))
+        ck = np.zeros(5 * max(cap, 1))
+        ns, nc = C.c_int64(), C.c_int64()
+        _check(lib().scylla_get_trace(self.h, _dp(st), C.byref(ns), _dp(ck), C.byref(nc)))
+        return st[: 4 * ns.value].reshape(-1, 4), ck[: 5 * nc.value].reshape(-1, 5)
 
     def perturb(self, xhat, xbar, kind: int, K: int, seed: int):
         x = _f64(xhat, self.n).copy()
