@@ -303,9 +303,14 @@ class OracleLP:
         """PDHG from the current pair until rel-KKT <= tol or k = iter_limit.
 
         ``trace`` records, per attempt, ("step", k, accept, eta_used, eta_max,
-        eta_next) and, per check that neither starts nor ends the solve,
-        ("check", k, restart, candidate_is_average, omega_after, kkt_candidate) --
-        all as this oracle computes them.  ``replay = (steps, checks)`` takes the
+        eta_next, cond) and, per check that neither starts nor ends the solve,
+        ("check", k, restart, candidate_is_average, omega_after, kkt_candidate,
+        restart_margin, candidate_margin, omega_cond) -- all as this oracle computes
+        them.  ``cond`` is the condition number of the interaction term
+        sum_i |dy_i| (|A| (|x'| + |x|))_i / |dy.A dx| (how much a rounding of A x'
+        or A x moves it); the margins are the relative distances of the candidate's
+        weighted KKT to the restart thresholds and to the other candidate's;
+        ``omega_cond`` is (||x_c|| / ||x_c - x_lr|| + ||y_c|| / ||y_c - y_lr||).  ``replay = (steps, checks)`` takes the
         scalar decisions from another implementation's trace instead (eta used,
         accept, eta next per attempt; restart, candidate and omega per check) while
         still computing and recording its own: adaptive PDHG amplifies rounding
@@ -341,10 +346,14 @@ class OracleLP:
                 eta = float(r_steps[k][0])
             x_new, y_new = self.pdhg_step(x, y, eta, omega)
             eta_max = INF
+            cond = 0.0
             if p.adaptive_step:
                 dx = x_new - x
                 dy = y_new - y
                 interaction = float(dy @ (self.As @ dx))
+                absA = abs(self.As)
+                scale = float(np.abs(dy) @ (absA @ (np.abs(x_new) + np.abs(x))))
+                cond = scale / abs(interaction) if interaction != 0.0 else INF
                 movement = omega * float(dx @ dx) + float(dy @ dy) / omega
                 eta_max = movement / (2.0 * abs(interaction)) if interaction != 0.0 else INF
                 kk = k + 2  # (k+1) with k the 1-based number of this attempt
@@ -358,7 +367,7 @@ class OracleLP:
                 eta_used = eta
             k += 1
             if trace:
-                tr.append(("step", k, bool(accept), eta_used, eta_max, eta))
+                tr.append(("step", k, bool(accept), eta_used, eta_max, eta, cond))
             if replay is not None:
                 accept = bool(r_steps[k - 1][2] > 0.5)
                 eta = float(r_steps[k - 1][3])
@@ -400,18 +409,25 @@ class OracleLP:
             else:
                 xc, yc, evc, is_avg = x, y, ev_c, False
             kc = evc.weighted_kkt(omega)
+            other = ev_c if is_avg else ev_a
+            cand_margin = (abs(other.weighted_kkt(omega) - kc) / kc) if (other is not None and kc > 0) else INF
+            thresholds = [p.beta_sufficient * kkt_lr, p.beta_necessary * kkt_lr, kkt_prev]
+            restart_margin = min(abs(kc - t) / kc for t in thresholds) if kc > 0 else INF
             do_restart = (kc <= p.beta_sufficient * kkt_lr
                           or (kc <= p.beta_necessary * kkt_lr and kc > kkt_prev)
                           or (k - k_lr) >= p.beta_artificial * k)
             omega_new = omega
+            omega_cond = 0.0
             if do_restart and p.primal_weight_update:
                 ddx = float(np.linalg.norm(xc - x_lr))
                 ddy = float(np.linalg.norm(yc - y_lr))
                 if ddx > 1e-10 and ddy > 1e-10:
+                    omega_cond = float(np.linalg.norm(xc)) / ddx + float(np.linalg.norm(yc)) / ddy
                     omega_new = math.exp(p.pw_smoothing * math.log(ddy / ddx)
                                          + (1.0 - p.pw_smoothing) * math.log(omega))
             if trace:
-                tr.append(("check", k, bool(do_restart), is_avg, omega_new, kc))
+                tr.append(("check", k, bool(do_restart), is_avg, omega_new, kc, restart_margin, cand_margin,
+                           omega_cond))
             if replay is not None:
                 rec = r_checks[ci]
                 ci += 1

@@ -849,7 +849,7 @@ __global__ void k_objective_cols(DevObjective o, double t, double om) {
           o.lo32[r0 + 1] = float(l1);
         }
       }
-      ch = __fadd_rn(__dmul_rn(t, o.c_orig[j]), __dmul_rn(om, g));
+      ch = __dadd_rn(__dmul_rn(t, o.c_orig[j]), __dmul_rn(om, g));
     } else {
       ch = om;
     }

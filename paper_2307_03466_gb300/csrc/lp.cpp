@@ -834,7 +834,7 @@ template <typename T>
 static int time_kernels_impl(scylla_lp* lp, const DevLP<T>& d, int attempts, double* ms) {
   cudaStream_t st = lp->st;
   const int nchk = lp->p.n_check;
-  const int nev = 2 * (attempts + 2 * (attempts / nchk + 1)) + 2;
+  const int nev = 4 * (attempts + attempts / nchk + 1);  // two events per timed launch
   std::vector<cudaEvent_t> ev(nev);
   for (auto& e : ev) CK(cudaEventCreate(&e));
   double sum[4] = {0, 0, 0, 0};

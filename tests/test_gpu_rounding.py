@@ -128,7 +128,7 @@ def test_objective_update_then_solve_matches_oracle_pump_lp():
     """The augmented LP after one objective update solves like the oracle's."""
     inst = I.packing_covering(m=150, n=300, per_col=3, seed=13)
     S = lib()
-    g = S.LP.from_instance(inst, S.default_params())
+    g = S.LP.from_instance(inst, S.default_params(trace_capacity=600))
     A = inst.csr()
     aug = P.augment(A, inst.c, inst.lo, inst.hi, inst.l, inst.u, inst.is_int)
     o = O.OracleLP(aug.A, aug.c, aug.lo, aug.hi, aug.l, aug.u, int_cols=np.nonzero(inst.is_int)[0])
@@ -143,10 +143,11 @@ def test_objective_update_then_solve_matches_oracle_pump_lp():
     lo2 = o.lo.copy()
     lo2[aug.m_orig:] = aux_lo
     o.set_row_bounds(lo2, o.hi)
-    x, y, _, _ = g.get_state()
+    x, y, eta, om = g.get_state()
     o.set_state(x, y)
+    o.eta, o.omega = eta, om
     rg = g.pdhg_solve(0.0, 500)
-    ro = o.solve(0.0, 500)
+    ro = o.solve(0.0, 500, replay=g.trace())
     xg, yg, _, _ = g.get_state()
     from tests.gpu_common import rel_err
     assert rel_err(xg, o.primal()) <= 1e-9 and rel_err(yg, o.dual()) <= 1e-9
