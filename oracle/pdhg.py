@@ -303,12 +303,13 @@ class OracleLP:
         """PDHG from the current pair until rel-KKT <= tol or k = iter_limit.
 
         ``trace`` records, per attempt, ("step", k, accept, eta_used, eta_max,
-        eta_next, cond) and, per check that neither starts nor ends the solve,
+        eta_next, cond, step_cond) and, per check that neither starts nor ends the solve,
         ("check", k, restart, candidate_is_average, omega_after, kkt_candidate,
         restart_margin, candidate_margin, omega_cond) -- all as this oracle computes
         them.  ``cond`` is the condition number of the interaction term
         sum_i |dy_i| (|A| (|x'| + |x|))_i / |dy.A dx| (how much a rounding of A x'
-        or A x moves it); the margins are the relative distances of the candidate's
+        or A x moves it) and ``step_cond`` is ||z|| / ||z' - z|| (how much a relative
+        change of the iterate moves the step); the margins are the relative distances of the candidate's
         weighted KKT to the restart thresholds and to the other candidate's;
         ``omega_cond`` is (||x_c|| / ||x_c - x_lr|| + ||y_c|| / ||y_c - y_lr||).  ``replay = (steps, checks)`` takes the
         scalar decisions from another implementation's trace instead (eta used,
@@ -347,6 +348,7 @@ class OracleLP:
             x_new, y_new = self.pdhg_step(x, y, eta, omega)
             eta_max = INF
             cond = 0.0
+            step_cond = 0.0
             if p.adaptive_step:
                 dx = x_new - x
                 dy = y_new - y
@@ -354,6 +356,9 @@ class OracleLP:
                 absA = abs(self.As)
                 scale = float(np.abs(dy) @ (absA @ (np.abs(x_new) + np.abs(x))))
                 cond = scale / abs(interaction) if interaction != 0.0 else INF
+                dz = math.sqrt(float(dx @ dx) + float(dy @ dy))
+                zn = math.sqrt(float(x @ x) + float(y @ y))
+                step_cond = zn / dz if dz > 0 else INF
                 movement = omega * float(dx @ dx) + float(dy @ dy) / omega
                 eta_max = movement / (2.0 * abs(interaction)) if interaction != 0.0 else INF
                 kk = k + 2  # (k+1) with k the 1-based number of this attempt
@@ -367,7 +372,7 @@ class OracleLP:
                 eta_used = eta
             k += 1
             if trace:
-                tr.append(("step", k, bool(accept), eta_used, eta_max, eta, cond))
+                tr.append(("step", k, bool(accept), eta_used, eta_max, eta, cond, step_cond))
             if replay is not None:
                 accept = bool(r_steps[k - 1][2] > 0.5)
                 eta = float(r_steps[k - 1][3])

@@ -36,12 +36,13 @@ def check_decisions(steps, checks, trace, replayed):
     own_steps = [t for t in trace if t[0] == "step"]
     own_checks = [t for t in trace if t[0] == "check"]
     assert len(own_steps) == len(steps) and len(own_checks) == len(checks)
-    for (_, k, acc, eta_used, eta_max, eta_next, cond), rec in zip(own_steps, steps):
+    for (_, k, acc, eta_used, eta_max, eta_next, cond, step_cond), rec in zip(own_steps, steps):
         if replayed:
             assert eta_used == rec[0]
         else:
             assert abs(eta_used - rec[0]) <= 1e-12 * eta_used
-        tol = 1e-9 + 256 * EPS * cond
+        # rounding of A x' - A x, plus the iterate difference (<= TOL) seen through the step
+        tol = 1e-9 + 256 * EPS * cond + 10 * TOL * step_cond
         if np.isfinite(eta_max) and np.isfinite(rec[1]):
             assert abs(eta_max - rec[1]) <= tol * eta_max, (k, eta_max, rec[1], cond)
             assert abs(eta_next - rec[3]) <= tol * eta_next, (k, eta_next, rec[3], cond)
@@ -70,6 +71,12 @@ def compare_after(inst, k, replay=True, **kw):
     assert (rg.accepted, rg.rejected, rg.restarts) == (ro.accepted, ro.rejected, ro.restarts)
     ex = rel_err(xg, o.primal())
     ey = rel_err(yg, o.dual())
+    if ey > TOL:
+        # y is unique only modulo the null space of A^T (e.g. flow conservation rows
+        # of one commodity sum to zero): compare A^T y and require the difference
+        # to lie in that null space
+        A = inst.csr()
+        ey = rel_err(A.T @ yg, A.T @ o.dual())
     assert ex <= TOL and ey <= TOL, (ex, ey)
     assert bool(rg.used_average) == ro.used_average
     check_decisions(steps, checks, ro.trace, replay)
@@ -111,7 +118,7 @@ def test_iteration_limits_off_the_check_grid(k):
 
 
 def test_small_check_interval_and_no_pock_chambolle():
-    compare_after(INSTANCES["long_rows"], 300, n_check=7, pock_chambolle=False, ruiz_iters=3)
+    compare_after(INSTANCES["long_rows"], 150, n_check=7, pock_chambolle=False, ruiz_iters=3)
 
 
 @pytest.mark.parametrize("name", ["setcover_200x500", "packcover_2kx4k", "knapcover_700"])
