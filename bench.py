@@ -212,8 +212,7 @@ def run_ours(args):
         return lp.pdhg_solve(TOL, ITER_CAP)
 
     def launches(res):
-        chunks = max(1, -(-int(res.iterations) // nchk))
-        return 1 + 1 + 2 + chunks * (2 * nchk + 3)  # reset, init, start check, loop body
+        return 1 + int(res.launches)  # the cold reset plus what the solve issued
 
     for _ in range(args.warmup):
         step(mixed)

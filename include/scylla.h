@@ -78,7 +78,9 @@ typedef struct {
   int32_t primal_weight_update; /* update omega at restarts (1) */
   int32_t stall_checks;         /* stop when round(x_I) is unchanged for this many checks; 0 = off (0) */
   int32_t aux_general_integers; /* add l1-distance auxiliary columns/rows for general integers (1) */
-  int32_t use_graph;            /* 1: CUDA graph with device-side loop; 0: direct launches (1) */
+  int32_t use_graph;            /* 1: one CUDA graph per n_check attempts, replayed by a pipelined host
+                                   loop; 2: a single graph with a device-side while loop; 0: direct
+                                   launches (1) */
   double fixed_step_factor;     /* f of the fixed-step mode (0.9) */
   double beta_sufficient;       /* restart if KKT <= 0.2 KKT_last_restart */
   double beta_necessary;        /* ... or <= 0.8 KKT_last_restart and KKT grew since the last check */
@@ -109,6 +111,7 @@ typedef struct {
   double pobj, dobj;     /* primal/dual objective (with the objective offset) */
   double eta, omega;     /* step size and primal weight after the solve */
   double seconds;        /* device time of the solve (CUDA events) */
+  int64_t launches;      /* kernel launches issued, including ones that returned early */
 } scylla_pdhg_result;
 
 typedef struct {

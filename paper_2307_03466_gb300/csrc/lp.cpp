@@ -367,6 +367,9 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   cudaStream_t st = lp->st;
   CK(cudaMemsetAsync(lp->arena, 0, lp->arena_bytes, st));
   CK(cudaMallocHost(&lp->h_ctl, sizeof(Control)));
+  CK(cudaMallocHost(&lp->h_done, 2 * sizeof(int)));
+  CK(cudaEventCreateWithFlags(&lp->ev_chunk[0], cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&lp->ev_chunk[1], cudaEventDisableTiming));
 
   CK(cudaMemcpyAsync(lp->a_rowptr, rp.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->a_cols, ci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, st));
@@ -518,6 +521,16 @@ void scylla_lp::release() {
   if (graph) cudaGraphDestroy(graph);
   exec = nullptr;
   graph = nullptr;
+  if (chunk_exec) cudaGraphExecDestroy(chunk_exec);
+  if (chunk_graph) cudaGraphDestroy(chunk_graph);
+  chunk_exec = nullptr;
+  chunk_graph = nullptr;
+  for (auto& e : ev_chunk) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
+  if (h_done) cudaFreeHost(h_done);
+  h_done = nullptr;
   if (arena) cudaFree(arena);
   arena = nullptr;
   if (h_ctl) cudaFreeHost(h_ctl);
@@ -614,6 +627,22 @@ static int build_graph(scylla_lp* lp, const DevLP<T>& d) {
 }
 
 template <typename T>
+static int build_chunk_graph(scylla_lp* lp, const DevLP<T>& d) {
+  cudaStream_t st = lp->st;
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < lp->p.n_check && e == cudaSuccess; ++s) e = launch_slot<T>(d, st);
+  if (e == cudaSuccess) e = launch_check<T>(d, st);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(st, &g);
+  CK(e);
+  CK(e2);
+  lp->chunk_graph = g;
+  CK(cudaGraphInstantiate(&lp->chunk_exec, g, 0));
+  return SCYLLA_OK;
+}
+
+template <typename T>
 static int solve_impl(scylla_lp* lp, const DevLP<T>& d, double tol, int64_t iter_limit, int stall_checks) {
   cudaStream_t st = lp->st;
   const long long nchk = lp->p.n_check;
@@ -621,12 +650,36 @@ static int solve_impl(scylla_lp* lp, const DevLP<T>& d, double tol, int64_t iter
   CK(cudaEventRecord(lp->ev0, st));
   CK(launch_solve_init<T>(d, tol, (long long)iter_limit, stall_checks, max_chunks, st));
   CK(launch_check<T>(d, st));  // evaluates the start point, caches A x and A^T y
-  if (lp->p.use_graph) {
+  const long long per_chunk = 2LL * nchk + 2;
+  long long launches = 3;
+  if (lp->p.use_graph == 2) {
     if (!lp->exec) {
       const int rc = build_graph<T>(lp, d);
       if (rc != SCYLLA_OK) return rc;
     }
     CK(cudaGraphLaunch(lp->exec, st));
+    launches = -1;  // counted on the device
+  } else if (lp->p.use_graph == 1) {
+    if (!lp->chunk_exec) {
+      const int rc = build_chunk_graph<T>(lp, d);
+      if (rc != SCYLLA_OK) return rc;
+    }
+    // chunk c+1 is queued before the done flag of chunk c is read, so the GPU never
+    // waits for the host; the chunk queued after the last one returns at once
+    auto enqueue = [&](long long c) -> cudaError_t {
+      cudaError_t e = cudaGraphLaunch(lp->chunk_exec, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&lp->h_done[c & 1], &lp->ctl->done, sizeof(int), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaEventRecord(lp->ev_chunk[c & 1], st);
+      launches += per_chunk;
+      return e;
+    };
+    CK(enqueue(0));
+    for (long long c = 0; c < max_chunks; ++c) {
+      if (c + 1 < max_chunks) CK(enqueue(c + 1));
+      CK(cudaEventSynchronize(lp->ev_chunk[c & 1]));
+      if (lp->h_done[c & 1]) break;
+    }
   } else {
     for (long long ch = 0; ch < max_chunks; ++ch) {
       CK(cudaMemcpyAsync(lp->h_ctl, lp->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
@@ -634,8 +687,10 @@ static int solve_impl(scylla_lp* lp, const DevLP<T>& d, double tol, int64_t iter
       if (lp->h_ctl->done) break;
       for (int s = 0; s < lp->p.n_check; ++s) CK(launch_slot<T>(d, st));
       CK(launch_check<T>(d, st));
+      launches += per_chunk;
     }
   }
+  lp->last_launches = launches;
   CK(cudaEventRecord(lp->ev1, st));
   CK(cudaMemcpyAsync(lp->h_ctl, lp->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -669,6 +724,7 @@ int scylla_lp::solve(double tol, int64_t iter_limit, int stall_checks, scylla_pd
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
     out->seconds = ms * 1e-3;
+    out->launches = last_launches >= 0 ? last_launches : 3 + h.chunks * (2LL * p.n_check + 3);
   }
   return SCYLLA_OK;
 }

@@ -64,9 +64,14 @@ struct scylla_lp {
 
   double eta0 = 1.0, omega0 = 1.0;  // step size and primal weight chosen at create
 
-  cudaGraph_t graph = nullptr;
+  cudaGraph_t graph = nullptr;       // device-side while loop (use_graph = 2)
   cudaGraphExec_t exec = nullptr;
   cudaGraphConditionalHandle cond = 0;
+  cudaGraph_t chunk_graph = nullptr;  // n_check attempts + one check (use_graph = 1)
+  cudaGraphExec_t chunk_exec = nullptr;
+  cudaEvent_t ev_chunk[2] = {nullptr, nullptr};
+  int* h_done = nullptr;             // pinned, two slots
+  int64_t last_launches = 0;
 
   scylla::DevObjective objective_desc();
   void release();

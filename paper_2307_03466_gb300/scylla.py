@@ -53,7 +53,7 @@ class PdhgResult(C.Structure):
                 ("accepted", C.c_int64), ("rejected", C.c_int64), ("restarts", C.c_int64),
                 ("eps_p", C.c_double), ("eps_d", C.c_double), ("eps_g", C.c_double), ("rel_kkt", C.c_double),
                 ("pobj", C.c_double), ("dobj", C.c_double), ("eta", C.c_double), ("omega", C.c_double),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("launches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
