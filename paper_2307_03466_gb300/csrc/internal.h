@@ -4,7 +4,8 @@
 //   A   : CSR over rows    (rowptr int32[m+1], cols int32[nnz], vals T[nnz] (+FP64 copy))
 //   A^T : CSR over columns (same nonzeros, rows ascending within a column)
 //   warp tiles: contiguous row ranges with <= kTileNnz nonzeros and <= 32 rows,
-//               or a single longer row (processed by one warp).
+//               or a single longer row (processed by one warp); stored as
+//               (first row, first nonzero) pairs, ntiles + 1 of them.
 //   iterate pools: X[3], Y[3], AX[3] (roles cur/next/avg chosen by indices in the
 //   device control block), ATY[2] (cur/avg), XLR, YLR (last restart point).
 // Arrays that are read with 16-byte vector loads are padded to a multiple of 4
@@ -43,6 +44,7 @@ struct Control {
   double eps_p, eps_d, eps_g, rel_kkt, pobj, dobj;  // of the reported point
   double beta_s, beta_n, beta_a, theta, exp_red, exp_grow;
   long long k, iter_limit, k_lr, accepted, rejected, restarts, chunks, max_chunks, n_ctrace;
+  long long k_fac;  // attempt count when the step-size factor table was filled
   unsigned long long hash_accum, last_hash;
   int same_hash, stall_checks;
   int ix_cur, ix_next, ix_avg, ia_cur, ia_avg;
@@ -58,13 +60,13 @@ struct DevLP {
   int m, n;
   const int* a_rowptr;
   const int* a_cols;
-  const int* a_tiles;
+  const int2* a_tiles;
   int a_ntiles;
   const T* a_vals;
   const double* a_vals64;
   const int* t_rowptr;
   const int* t_cols;
-  const int* t_tiles;
+  const int2* t_tiles;
   int t_ntiles;
   const T* t_vals;
   const double* t_vals64;
@@ -80,6 +82,8 @@ struct DevLP {
   Control* ctl;
   double *part_p, *part_d, *part_c1, *part_c2;
   int grid_p, grid_d, grid_c1, grid_c2;
+  double* step_fac;      // 2 * n_check: (1 - kk^-a, 1 + kk^-b) of the next n_check attempts
+  int n_check;
   double* trace_steps;   // 4 doubles per attempt, or null
   double* trace_checks;  // 5 doubles per check, or null
   int trace_cap;

@@ -121,14 +121,14 @@ __device__ __forceinline__ unsigned long long round_hash(long long j, double v) 
 }
 
 // per-block reduction of N partial sums into part[blockIdx.x * N + k], fixed order
-template <int N>
-__device__ __forceinline__ void block_store_partials(const double (&v)[N], double* __restrict__ part) {
+template <int N, typename A>
+__device__ __forceinline__ void block_store_partials(const A (&v)[N], double* __restrict__ part) {
   __shared__ double sh[kWarpsPerBlock][N];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    const double t = warp_sum(v[k]);
-    if (lane == 0) sh[w][k] = t;
+    const A t = warp_sum(v[k]);
+    if (lane == 0) sh[w][k] = double(t);
   }
   __syncthreads();
   if (threadIdx.x < N) {
@@ -149,35 +149,49 @@ __device__ __forceinline__ bool is_last_block(unsigned int* counter) {
   return last != 0;
 }
 
-// sum of N partial vectors over nblocks blocks, by the whole (last) block, fixed order
-template <int N>
-__device__ void reduce_partials(const double* part, int nblocks, double* out_shared) {
-  __shared__ double sh[kWarpsPerBlock];
+// sums of two partial arrays (NA values over na blocks, NB over nb) in one pass by
+// the whole (last) block: each thread accumulates a fixed strided subset, then one
+// fixed-order block reduction of all NA + NB values
+template <int NA, int NB>
+__device__ void reduce_two(const double* pa, int na, const double* pb, int nb, double* out_shared) {
+  constexpr int N = NA + NB;
+  __shared__ double sh[kWarpsPerBlock][N];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double s[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) s[k] = 0.0;
+  for (int b = threadIdx.x; b < na; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < NA; ++k) s[k] += __ldcg(pa + b * NA + k);
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < NB; ++k) s[NA + k] += __ldcg(pb + b * NB + k);
+#pragma unroll
   for (int k = 0; k < N; ++k) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += __ldcg(part + b * N + k);
-    s = warp_sum(s);
-    if (lane == 0) sh[w] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int i = 0; i < kWarpsPerBlock; ++i) t += sh[i];
-      out_shared[k] = t;
-    }
-    __syncthreads();
+    const double t = warp_sum(s[k]);
+    if (lane == 0) sh[w][k] = t;
   }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double t = 0.0;
+    for (int i = 0; i < kWarpsPerBlock; ++i) t += sh[i][threadIdx.x];
+    out_shared[threadIdx.x] = t;
+  }
+  __syncthreads();
 }
 
 // --------------------------------------------------------------- the SpMV core ---
-// Warp-tile CSR gather: each warp takes tiles round-robin.  A multi-row tile (at
-// most kTileNnz nonzeros, at most 32 rows) is streamed with 16-byte vector loads of
-// column indices and values (aligned down to the vector boundary and masked),
-// products go to a skewed per-warp shared buffer, and lane r sums row r in CSR
-// order.  A single long row is reduced across the warp with shuffles.  The
-// epilogue runs once per row, on one lane.
+// Warp-tile CSR gather.  Each warp takes tiles round-robin.  A multi-row tile (at
+// most kTileNnz nonzeros and 32 rows) is read with 16-byte vector loads of column
+// indices and values, aligned down to the vector boundary and masked: every lane
+// first issues all of its (at most three) vector loads, then all of its gathers, so
+// up to 12 gathers per lane are in flight.  Products go to a skewed per-warp
+// shared buffer and lane r sums row r in CSR order.  A single long row is reduced
+// across the warp with shuffles.  The epilogue has two halves: load(row) is issued
+// at the start of the tile, before the gathers, and finish(row, sum, pre) runs once
+// the row sum is known, on the lane that owns the row.
 template <int NV, typename Acc, typename V, typename Gather, typename Epi>
-__device__ __forceinline__ void spmv_tiles(const int* __restrict__ tiles, int ntiles,
+__device__ __forceinline__ void spmv_tiles(const int2* __restrict__ tiles, int ntiles,
                                            const int* __restrict__ rowptr, const int* __restrict__ cols,
                                            const V* __restrict__ vals, Gather& gat, Epi& epi,
                                            Acc* __restrict__ sm) {
@@ -185,10 +199,11 @@ __device__ __forceinline__ void spmv_tiles(const int* __restrict__ tiles, int nt
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int t = gwarp; t < ntiles; t += nwarps) {
-    const int r0 = __ldg(tiles + t), r1 = __ldg(tiles + t + 1);
-    const int p0 = __ldg(rowptr + r0), p1 = __ldg(rowptr + r1);
+    const int2 ta = __ldg(tiles + t), tb = __ldg(tiles + t + 1);
+    const int r0 = ta.x, r1 = tb.x, p0 = ta.y, p1 = tb.y;
     const int base = p0 & ~(kVec - 1);
     if (r1 - r0 == 1 && p1 - p0 > kTileNnz) {
+      const typename Epi::Pre pre = epi.load(r0);
       Acc s[NV];
 #pragma unroll
       for (int k = 0; k < NV; ++k) s[k] = Acc(0);
@@ -210,29 +225,45 @@ __device__ __forceinline__ void spmv_tiles(const int* __restrict__ tiles, int nt
       }
 #pragma unroll
       for (int k = 0; k < NV; ++k) s[k] = warp_sum(s[k]);
-      if (lane == 0) epi(r0, s);
+      if (lane == 0) epi.finish(r0, s, pre);
     } else {
-      for (int p = base + lane * kVec; p < p1; p += 32 * kVec) {
-        int c[4];
-        V v[4];
-        ld4(cols + p, c);
-        ld4(vals + p, v);
+      const bool mine = lane < r1 - r0;
+      const int row = r0 + lane;
+      int q0 = 0, q1 = 0;
+      typename Epi::Pre pre{};
+      if (mine) {
+        q0 = __ldg(rowptr + row) - p0;
+        q1 = __ldg(rowptr + row + 1) - p0;
+        pre = epi.load(row);
+      }
+      // p1 - base <= kTileNnz + kVec - 1 < 3 * 32 * kVec: three vector steps cover the tile
+      int c[3][4];
+      V v[3][4];
+#pragma unroll
+      for (int it = 0; it < 3; ++it) {
+        const int p = base + (it * 32 + lane) * kVec;
+        if (p < p1) {
+          ld4(cols + p, c[it]);
+          ld4(vals + p, v[it]);
+        }
+      }
+#pragma unroll
+      for (int it = 0; it < 3; ++it) {
+        const int p = base + (it * 32 + lane) * kVec;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int q = p + e;
           if (q >= p0 && q < p1) {
             Acc g[NV];
-            gat(c[e], g);
+            gat(c[it][e], g);
             const int o = skew(q - p0);
 #pragma unroll
-            for (int k = 0; k < NV; ++k) sm[k * kSmemPerWarp + o] = Acc(v[e]) * g[k];
+            for (int k = 0; k < NV; ++k) sm[k * kSmemPerWarp + o] = Acc(v[it][e]) * g[k];
           }
         }
       }
       __syncwarp();
-      if (lane < r1 - r0) {
-        const int row = r0 + lane;
-        const int q0 = __ldg(rowptr + row) - p0, q1 = __ldg(rowptr + row + 1) - p0;
+      if (mine) {
         Acc s[NV];
 #pragma unroll
         for (int k = 0; k < NV; ++k) s[k] = Acc(0);
@@ -241,7 +272,7 @@ __device__ __forceinline__ void spmv_tiles(const int* __restrict__ tiles, int nt
 #pragma unroll
           for (int k = 0; k < NV; ++k) s[k] += sm[k * kSmemPerWarp + o];
         }
-        epi(row, s);
+        epi.finish(row, s, pre);
       }
       __syncwarp();
     }
@@ -251,8 +282,11 @@ __device__ __forceinline__ void spmv_tiles(const int* __restrict__ tiles, int nt
 // ------------------------------------------------------------- step control ---
 // Adaptive step (PDLP): eta_max = (omega ||dx||^2 + ||dy||^2 / omega) / (2 |dy.A dx|);
 // eta' = min((1 - (k+1)^-0.3) eta_max, (1 + (k+1)^-0.6) eta), k the 1-based attempt
-// number; the attempt is accepted when eta <= eta_max.
-__device__ void step_control(Control* c, double dx2, double dy2, double inter, double* trace, int cap) {
+// number; the attempt is accepted when eta <= eta_max.  The two powers come from
+// a table that the check kernel fills for the next n_check attempts (FP64
+// transcendentals are slow on this part; in the table they run in parallel).
+__device__ void step_control(Control* c, double dx2, double dy2, double inter, const double* fac, int n_check,
+                             double* trace, int cap) {
   if (!isfinite(dx2) || !isfinite(dy2) || !isfinite(inter)) {
     c->done = 1;
     c->status = SCYLLA_NUMERICAL;
@@ -266,8 +300,17 @@ __device__ void step_control(Control* c, double dx2, double dy2, double inter, d
   if (c->adaptive) {
     const double mv = om * dx2 + dy2 / om;
     eta_max = inter != 0.0 ? mv / (2.0 * fabs(inter)) : pos_inf<double>();
-    const double kk = double(k1 + 1);
-    eta_next = fmin((1.0 - pow(kk, -c->exp_red)) * eta_max, (1.0 + pow(kk, -c->exp_grow)) * eta);
+    const long long idx = k1 - 1 - c->k_fac;
+    double fr, fg;
+    if (idx >= 0 && idx < n_check) {
+      fr = fac[2 * idx];
+      fg = fac[2 * idx + 1];
+    } else {
+      const double kk = double(k1 + 1);
+      fr = 1.0 - pow(kk, -c->exp_red);
+      fg = 1.0 + pow(kk, -c->exp_grow);
+    }
+    eta_next = fmin(fr * eta_max, fg * eta);
     accept = eta <= eta_max;
   }
   if (trace && k1 <= cap) {
@@ -296,49 +339,124 @@ __device__ void step_control(Control* c, double dx2, double dy2, double inter, d
   }
 }
 
+// step-size factor table for attempts k+1 .. k+n_check (by the whole last block)
+__device__ void fill_step_factors(Control* c, double* fac, int n_check) {
+  const long long k = c->k;
+  for (int i = threadIdx.x; i < n_check; i += blockDim.x) {
+    const double kk = double(k + 1 + i + 1);
+    fac[2 * i] = 1.0 - pow(kk, -c->exp_red);
+    fac[2 * i + 1] = 1.0 + pow(kk, -c->exp_grow);
+  }
+  if (threadIdx.x == 0) c->k_fac = k;
+}
+
+// per-thread accumulator type of the bulk kernels
+template <typename T>
+struct AccOf {
+  typedef T type;
+};
+
 // ---------------------------------------------------------------- PDHG slot ---
+template <typename T>
+struct PrimalEpi {
+  typedef typename AccOf<T>::type A;
+  struct Pre {
+    T x, c, l, u;
+  };
+  const T* __restrict__ xc;
+  T* __restrict__ xn;
+  T* __restrict__ xa;
+  T* __restrict__ aty;
+  T* __restrict__ xlr;
+  const T* __restrict__ cc;
+  const T* __restrict__ ll;
+  const T* __restrict__ uu;
+  T tau, w, w1;
+  bool do_avg, copy_lr, store_aty;
+  A acc;
+  __device__ __forceinline__ Pre load(int j) const { return Pre{xc[j], cc[j], ll[j], uu[j]}; }
+  __device__ __forceinline__ void finish(int j, const T (&s)[1], const Pre& p) {
+    if (store_aty) aty[j] = s[0];
+    if (do_avg) xa[j] = blend(xa[j], p.x, w1, w);
+    if (copy_lr) xlr[j] = p.x;
+    const T v = clampv<T>(p.x + tau * (s[0] - p.c), p.l, p.u);
+    xn[j] = v;
+    const A dx = A(v) - A(p.x);
+    acc += dx * dx;
+  }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_primal(DevLP<T> d) {
   Control* ctl = d.ctl;
   if (ctl->done || ctl->k >= ctl->iter_limit) return;
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
   const int cur = ctl->ix_cur, nxt = ctl->ix_next, avg = ctl->ix_avg;
-  const T tau = T(ctl->eta / ctl->omega);
   const double wd = ctl->avg_w;
-  const T w = T(wd), w1 = T(1.0 - wd);
-  const bool do_avg = wd > 0.0, copy_lr = ctl->copy_lr != 0, aty_valid = ctl->aty_valid != 0;
-  const T* __restrict__ xc = d.X[cur];
-  T* __restrict__ xn = d.X[nxt];
-  T* __restrict__ xa = d.X[avg];
-  const T* __restrict__ yc = d.Y[cur];
-  T* __restrict__ aty = d.ATY[ctl->ia_cur];
-  T* __restrict__ xlr = d.XLR;
-  const T* __restrict__ cc = d.c;
-  const T* __restrict__ ll = d.l;
-  const T* __restrict__ uu = d.u;
-  double acc[kNP] = {0.0};
-  auto epi = [&](int j, T s) {
-    const T x = xc[j];
-    if (do_avg) xa[j] = blend(xa[j], x, w1, w);
-    if (copy_lr) xlr[j] = x;
-    const T v = clampv<T>(x + tau * (s - cc[j]), ll[j], uu[j]);
-    xn[j] = v;
-    const double dx = double(v) - double(x);
-    acc[0] += dx * dx;
-  };
+  const bool aty_valid = ctl->aty_valid != 0;
+  PrimalEpi<T> epi;
+  epi.xc = d.X[cur];
+  epi.xn = d.X[nxt];
+  epi.xa = d.X[avg];
+  epi.aty = d.ATY[ctl->ia_cur];
+  epi.xlr = d.XLR;
+  epi.cc = d.c;
+  epi.ll = d.l;
+  epi.uu = d.u;
+  epi.tau = T(ctl->eta / ctl->omega);
+  epi.w = T(wd);
+  epi.w1 = T(1.0 - wd);
+  epi.do_avg = wd > 0.0;
+  epi.copy_lr = ctl->copy_lr != 0;
+  epi.store_aty = !aty_valid;
+  epi.acc = 0;
   if (aty_valid) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += gridDim.x * blockDim.x) epi(j, aty[j]);
+    const T* __restrict__ aty = epi.aty;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += gridDim.x * blockDim.x) {
+      const T s[1] = {aty[j]};
+      epi.finish(j, s, epi.load(j));
+    }
   } else {
+    const T* __restrict__ yc = d.Y[cur];
     auto gat = [&](int i, T(&g)[1]) { g[0] = __ldg(yc + i); };
-    auto epi1 = [&](int j, T(&s)[1]) {
-      aty[j] = s[0];
-      epi(j, s[0]);
-    };
-    spmv_tiles<1, T, T>(d.t_tiles, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals, gat, epi1,
+    spmv_tiles<1, T, T>(d.t_tiles, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals, gat, epi,
                         sm + (threadIdx.x >> 5) * kSmemPerWarp);
   }
-  block_store_partials<kNP>(acc, d.part_p);
+  const typename AccOf<T>::type v[kNP] = {epi.acc};
+  block_store_partials<kNP>(v, d.part_p);
 }
+
+template <typename T>
+struct DualEpi {
+  typedef typename AccOf<T>::type A;
+  struct Pre {
+    T ax, y, lo, hi;
+  };
+  const T* __restrict__ axc;
+  T* __restrict__ axn;
+  const T* __restrict__ yc;
+  T* __restrict__ yn;
+  T* __restrict__ ya;
+  T* __restrict__ ylr;
+  const T* __restrict__ lo;
+  const T* __restrict__ hi;
+  T sigma, w, w1;
+  bool do_avg, copy_lr;
+  A acc0, acc1;
+  __device__ __forceinline__ Pre load(int i) const { return Pre{axc[i], yc[i], lo[i], hi[i]}; }
+  __device__ __forceinline__ void finish(int i, const T (&s)[1], const Pre& p) {
+    const T ax_new = s[0];
+    if (do_avg) ya[i] = blend(ya[i], p.y, w1, w);
+    if (copy_lr) ylr[i] = p.y;
+    const T axt = T(2) * ax_new - p.ax;
+    const T v = dual_prox<T>(p.y, sigma, axt, p.lo, p.hi);
+    yn[i] = v;
+    axn[i] = ax_new;
+    const A dy = A(v) - A(p.y);
+    acc0 += dy * dy;
+    acc1 += dy * (A(ax_new) - A(p.ax));
+  }
+};
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_dual(DevLP<T> d) {
@@ -346,44 +464,34 @@ __global__ void __launch_bounds__(kThreads) k_dual(DevLP<T> d) {
   if (ctl->done || ctl->k >= ctl->iter_limit) return;
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
   const int cur = ctl->ix_cur, nxt = ctl->ix_next, avg = ctl->ix_avg;
-  const T sigma = T(ctl->eta * ctl->omega);
   const double wd = ctl->avg_w;
-  const T w = T(wd), w1 = T(1.0 - wd);
-  const bool do_avg = wd > 0.0, copy_lr = ctl->copy_lr != 0;
+  DualEpi<T> epi;
+  epi.axc = d.AX[cur];
+  epi.axn = d.AX[nxt];
+  epi.yc = d.Y[cur];
+  epi.yn = d.Y[nxt];
+  epi.ya = d.Y[avg];
+  epi.ylr = d.YLR;
+  epi.lo = d.lo;
+  epi.hi = d.hi;
+  epi.sigma = T(ctl->eta * ctl->omega);
+  epi.w = T(wd);
+  epi.w1 = T(1.0 - wd);
+  epi.do_avg = wd > 0.0;
+  epi.copy_lr = ctl->copy_lr != 0;
+  epi.acc0 = 0;
+  epi.acc1 = 0;
   const T* __restrict__ xn = d.X[nxt];
-  const T* __restrict__ axc = d.AX[cur];
-  T* __restrict__ axn = d.AX[nxt];
-  const T* __restrict__ yc = d.Y[cur];
-  T* __restrict__ yn = d.Y[nxt];
-  T* __restrict__ ya = d.Y[avg];
-  T* __restrict__ ylr = d.YLR;
-  const T* __restrict__ lo = d.lo;
-  const T* __restrict__ hi = d.hi;
-  double acc[kND] = {0.0, 0.0};
   auto gat = [&](int j, T(&g)[1]) { g[0] = __ldg(xn + j); };
-  auto epi = [&](int i, T(&s)[1]) {
-    const T ax_new = s[0];
-    const T ax = axc[i];
-    const T y = yc[i];
-    if (do_avg) ya[i] = blend(ya[i], y, w1, w);
-    if (copy_lr) ylr[i] = y;
-    const T axt = T(2) * ax_new - ax;
-    const T v = dual_prox<T>(y, sigma, axt, lo[i], hi[i]);
-    yn[i] = v;
-    axn[i] = ax_new;
-    const double dy = double(v) - double(y);
-    acc[0] += dy * dy;
-    acc[1] += dy * (double(ax_new) - double(ax));
-  };
   spmv_tiles<1, T, T>(d.a_tiles, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals, gat, epi,
                       sm + (threadIdx.x >> 5) * kSmemPerWarp);
-  block_store_partials<kND>(acc, d.part_d);
+  const typename AccOf<T>::type v[kND] = {epi.acc0, epi.acc1};
+  block_store_partials<kND>(v, d.part_d);
   if (!is_last_block(&ctl->cnt_dual)) return;
   __shared__ double red[kNP + kND];
-  reduce_partials<kNP>(d.part_p, d.grid_p, red);
-  reduce_partials<kND>(d.part_d, d.grid_d, red + kNP);
+  reduce_two<kNP, kND>(d.part_p, d.grid_p, d.part_d, d.grid_d, red);
   if (threadIdx.x == 0) {
-    step_control(ctl, red[0], red[1], red[2], d.trace_steps, d.trace_cap);
+    step_control(ctl, red[0], red[1], red[2], d.step_fac, d.n_check, d.trace_steps, d.trace_cap);
     ctl->cnt_dual = 0;
   }
 }
@@ -516,32 +624,21 @@ __device__ void check_control(Control* c, const double* r, double* trace, int ca
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_check_cols(DevLP<T> d) {
-  Control* ctl = d.ctl;
-  if (ctl->done) return;
-  __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];
-  const int cur = ctl->ix_cur, avg = ctl->ix_avg;
-  const double wd = ctl->avg_w;
-  const T w = T(wd), w1 = T(1.0 - wd);
-  const bool do_avg = wd > 0.0;
-  const T* __restrict__ yc = d.Y[cur];
-  const T* __restrict__ ya = d.Y[avg];
-  const T* __restrict__ xc = d.X[cur];
-  T* __restrict__ xa = d.X[avg];
-  T* __restrict__ aty_c = d.ATY[ctl->ia_cur];
-  T* __restrict__ aty_a = d.ATY[ctl->ia_avg];
+struct CheckColsEpi {
+  struct Pre {};
+  const T* __restrict__ xc;
+  T* __restrict__ xa;
+  T* __restrict__ aty_c;
+  T* __restrict__ aty_a;
+  const T* __restrict__ xlr;
+  const double *C, *c64, *l64, *u64;
+  const unsigned char* int_mask;
+  T w, w1;
+  bool do_avg;
   double acc[kNC1];
-#pragma unroll
-  for (int k = 0; k < kNC1; ++k) acc[k] = 0.0;
-  unsigned long long h = 0ULL;
-  auto gat = [&](int i, double(&g)[2]) {
-    const T y = yc[i];
-    T v = ya[i];
-    if (do_avg) v = blend(v, y, w1, w);
-    g[0] = double(y);
-    g[1] = double(v);
-  };
-  auto epi = [&](int j, double(&s)[2]) {
+  unsigned long long h;
+  __device__ __forceinline__ Pre load(int) const { return Pre{}; }
+  __device__ __forceinline__ void finish(int j, const double (&s)[2], const Pre&) {
     const T x = xc[j];
     T xav = xa[j];
     if (do_avg) {
@@ -550,7 +647,7 @@ __global__ void __launch_bounds__(kThreads) k_check_cols(DevLP<T> d) {
     }
     aty_c[j] = T(s[0]);
     aty_a[j] = T(s[1]);
-    const double Cj = d.C[j], cj = d.c64[j], lj = d.l64[j], uj = d.u64[j], xl = double(d.XLR[j]);
+    const double Cj = C[j], cj = c64[j], lj = l64[j], uj = u64[j], xl = double(xlr[j]);
     const double xs[2] = {double(x), double(xav)};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -565,17 +662,12 @@ __global__ void __launch_bounds__(kThreads) k_check_cols(DevLP<T> d) {
       const double dd = xs[q] - xl;
       acc[5 * q + 4] += dd * dd;
     }
-    if (d.int_mask[j]) h += round_hash(j, double(x) * Cj);
-  };
-  spmv_tiles<2, double, double>(d.t_tiles, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals64, gat, epi,
-                                sm + (threadIdx.x >> 5) * 2 * kSmemPerWarp);
-  block_store_partials<kNC1>(acc, d.part_c1);
-  h = warp_sum_u64(h);
-  if ((threadIdx.x & 31) == 0 && h != 0ULL) atomicAdd(&ctl->hash_accum, h);
-}
+    if (int_mask[j]) h += round_hash(j, double(x) * Cj);
+  }
+};
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_check_rows(DevLP<T> d) {
+__global__ void __launch_bounds__(kThreads) k_check_cols(DevLP<T> d) {
   Control* ctl = d.ctl;
   if (ctl->done) return;
   __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];
@@ -583,20 +675,53 @@ __global__ void __launch_bounds__(kThreads) k_check_rows(DevLP<T> d) {
   const double wd = ctl->avg_w;
   const T w = T(wd), w1 = T(1.0 - wd);
   const bool do_avg = wd > 0.0;
-  const T* __restrict__ xc = d.X[cur];
-  const T* __restrict__ xa = d.X[avg];
   const T* __restrict__ yc = d.Y[cur];
-  T* __restrict__ ya = d.Y[avg];
-  T* __restrict__ ax_c = d.AX[cur];
-  T* __restrict__ ax_a = d.AX[avg];
-  double acc[kNC2];
+  const T* __restrict__ ya = d.Y[avg];
+  CheckColsEpi<T> epi;
+  epi.xc = d.X[cur];
+  epi.xa = d.X[avg];
+  epi.aty_c = d.ATY[ctl->ia_cur];
+  epi.aty_a = d.ATY[ctl->ia_avg];
+  epi.xlr = d.XLR;
+  epi.C = d.C;
+  epi.c64 = d.c64;
+  epi.l64 = d.l64;
+  epi.u64 = d.u64;
+  epi.int_mask = d.int_mask;
+  epi.w = w;
+  epi.w1 = w1;
+  epi.do_avg = do_avg;
 #pragma unroll
-  for (int k = 0; k < kNC2; ++k) acc[k] = 0.0;
-  auto gat = [&](int j, double(&g)[2]) {
-    g[0] = double(xc[j]);
-    g[1] = double(xa[j]);
+  for (int k = 0; k < kNC1; ++k) epi.acc[k] = 0.0;
+  epi.h = 0ULL;
+  auto gat = [&](int i, double(&g)[2]) {
+    const T y = yc[i];
+    T v = ya[i];
+    if (do_avg) v = blend(v, y, w1, w);
+    g[0] = double(y);
+    g[1] = double(v);
   };
-  auto epi = [&](int i, double(&s)[2]) {
+  spmv_tiles<2, double, double>(d.t_tiles, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals64, gat, epi,
+                                sm + (threadIdx.x >> 5) * 2 * kSmemPerWarp);
+  block_store_partials<kNC1>(epi.acc, d.part_c1);
+  const unsigned long long h = warp_sum_u64(epi.h);
+  if ((threadIdx.x & 31) == 0 && h != 0ULL) atomicAdd(&ctl->hash_accum, h);
+}
+
+template <typename T>
+struct CheckRowsEpi {
+  struct Pre {};
+  const T* __restrict__ yc;
+  T* __restrict__ ya;
+  T* __restrict__ ax_c;
+  T* __restrict__ ax_a;
+  const T* __restrict__ ylr;
+  const double *R, *lo64, *hi64;
+  T w, w1;
+  bool do_avg;
+  double acc[kNC2];
+  __device__ __forceinline__ Pre load(int) const { return Pre{}; }
+  __device__ __forceinline__ void finish(int i, const double (&s)[2], const Pre&) {
     const T y = yc[i];
     T yav = ya[i];
     if (do_avg) {
@@ -605,7 +730,7 @@ __global__ void __launch_bounds__(kThreads) k_check_rows(DevLP<T> d) {
     }
     ax_c[i] = T(s[0]);
     ax_a[i] = T(s[1]);
-    const double Ri = d.R[i], lo = d.lo64[i], hi = d.hi64[i], yl = double(d.YLR[i]);
+    const double Ri = R[i], lo = lo64[i], hi = hi64[i], yl = double(ylr[i]);
     const double ys[2] = {double(y), double(yav)};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -617,14 +742,43 @@ __global__ void __launch_bounds__(kThreads) k_check_rows(DevLP<T> d) {
       const double dd = ys[q] - yl;
       acc[4 * q + 3] += dd * dd;
     }
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_check_rows(DevLP<T> d) {
+  Control* ctl = d.ctl;
+  if (ctl->done) return;
+  __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];
+  const int cur = ctl->ix_cur, avg = ctl->ix_avg;
+  const double wd = ctl->avg_w;
+  const T* __restrict__ xc = d.X[cur];
+  const T* __restrict__ xa = d.X[avg];
+  CheckRowsEpi<T> epi;
+  epi.yc = d.Y[cur];
+  epi.ya = d.Y[avg];
+  epi.ax_c = d.AX[cur];
+  epi.ax_a = d.AX[avg];
+  epi.ylr = d.YLR;
+  epi.R = d.R;
+  epi.lo64 = d.lo64;
+  epi.hi64 = d.hi64;
+  epi.w = T(wd);
+  epi.w1 = T(1.0 - wd);
+  epi.do_avg = wd > 0.0;
+#pragma unroll
+  for (int k = 0; k < kNC2; ++k) epi.acc[k] = 0.0;
+  auto gat = [&](int j, double(&g)[2]) {
+    g[0] = double(xc[j]);
+    g[1] = double(xa[j]);
   };
   spmv_tiles<2, double, double>(d.a_tiles, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals64, gat, epi,
                                 sm + (threadIdx.x >> 5) * 2 * kSmemPerWarp);
-  block_store_partials<kNC2>(acc, d.part_c2);
+  block_store_partials<kNC2>(epi.acc, d.part_c2);
   if (!is_last_block(&ctl->cnt_c2)) return;
   __shared__ double red[kNC1 + kNC2];
-  reduce_partials<kNC1>(d.part_c1, d.grid_c1, red);
-  reduce_partials<kNC2>(d.part_c2, d.grid_c2, red + kNC1);
+  reduce_two<kNC1, kNC2>(d.part_c1, d.grid_c1, d.part_c2, d.grid_c2, red);
+  fill_step_factors(ctl, d.step_fac, d.n_check);
   if (threadIdx.x == 0) {
     check_control(ctl, red, d.trace_checks, d.trace_cap);
     ctl->cnt_c2 = 0;

@@ -98,18 +98,18 @@ struct Arena {
 size_t padded(size_t nnz) { return ((nnz + 3) & ~size_t(3)) + 4; }
 
 // contiguous row ranges of at most kTileNnz nonzeros and kTileRows rows; a longer
-// row is a tile of its own
-std::vector<int> build_tiles(const std::vector<int>& rowptr) {
+// row is a tile of its own.  Each boundary is stored as (row, rowptr[row]).
+std::vector<int2> build_tiles(const std::vector<int>& rowptr) {
   const int m = int(rowptr.size()) - 1;
-  std::vector<int> t;
+  std::vector<int2> t;
   t.reserve(m / 4 + 2);
-  t.push_back(0);
+  t.push_back(make_int2(0, rowptr[0]));
   int r = 0;
   while (r < m) {
     const int len = rowptr[r + 1] - rowptr[r];
     if (len > kTileNnz) {
       ++r;
-      t.push_back(r);
+      t.push_back(make_int2(r, rowptr[r]));
       continue;
     }
     int cnt = 0, nz = 0;
@@ -120,7 +120,7 @@ std::vector<int> build_tiles(const std::vector<int>& rowptr) {
       ++r;
       ++cnt;
     }
-    t.push_back(r);
+    t.push_back(make_int2(r, rowptr[r]));
   }
   return t;
 }
@@ -279,7 +279,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
         tv[q] = va[p];
       }
   }
-  const std::vector<int> at = build_tiles(rp), tt = build_tiles(tp);
+  const std::vector<int2> at = build_tiles(rp), tt = build_tiles(tp);
   lp->a_ntiles = int(at.size()) - 1;
   lp->t_ntiles = int(tt.size()) - 1;
 
@@ -309,10 +309,10 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     }
     lp->a_rowptr = ar.take<int>(m + 1);
     lp->a_cols = ar.take<int>(padded(nnz));
-    lp->a_tiles = ar.take<int>(at.size());
+    lp->a_tiles = ar.take<int2>(at.size());
     lp->t_rowptr = ar.take<int>(n + 1);
     lp->t_cols = ar.take<int>(padded(nnz));
-    lp->t_tiles = ar.take<int>(tt.size());
+    lp->t_tiles = ar.take<int2>(tt.size());
     lp->a_vals64 = ar.take<double>(padded(nnz));
     lp->t_vals64 = ar.take<double>(padded(nnz));
     lp->a_vals32 = mixed ? ar.take<float>(padded(nnz)) : nullptr;
@@ -359,6 +359,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     lp->io_x = ar.take<double>(n);
     lp->io_y = ar.take<double>(m);
     lp->ctl = ar.take<Control>(1);
+    lp->step_fac = ar.take<double>(2 * size_t(lp->p.n_check));
     const size_t tc = size_t(lp->p.trace_capacity);
     lp->trace_steps = tc ? ar.take<double>(4 * tc) : nullptr;
     lp->trace_checks = tc ? ar.take<double>(5 * tc) : nullptr;
@@ -373,10 +374,10 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
 
   CK(cudaMemcpyAsync(lp->a_rowptr, rp.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->a_cols, ci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->a_tiles, at.data(), sizeof(int) * at.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->a_tiles, at.data(), sizeof(int2) * at.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->t_rowptr, tp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->t_cols, tr.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->t_tiles, tt.data(), sizeof(int) * tt.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->t_tiles, tt.data(), sizeof(int2) * tt.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->a_vals64, va.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->t_vals64, tv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->c_un, cA.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
@@ -501,6 +502,8 @@ void fill_dev(DevLP<T>& d, scylla_lp* lp) {
   d.ctl = lp->ctl;
   d.part_p = lp->part_p; d.part_d = lp->part_d; d.part_c1 = lp->part_c1; d.part_c2 = lp->part_c2;
   d.grid_p = lp->grid_p; d.grid_d = lp->grid_d; d.grid_c1 = lp->grid_c1; d.grid_c2 = lp->grid_c2;
+  d.step_fac = lp->step_fac;
+  d.n_check = lp->p.n_check;
   d.trace_steps = lp->trace_steps;
   d.trace_checks = lp->trace_checks;
   d.trace_cap = lp->p.trace_capacity;

@@ -38,8 +38,10 @@ struct scylla_lp {
 
   void* arena = nullptr;
   size_t arena_bytes = 0;
-  int *a_rowptr = nullptr, *a_cols = nullptr, *a_tiles = nullptr;
-  int *t_rowptr = nullptr, *t_cols = nullptr, *t_tiles = nullptr;
+  int *a_rowptr = nullptr, *a_cols = nullptr;
+  int *t_rowptr = nullptr, *t_cols = nullptr;
+  int2 *a_tiles = nullptr, *t_tiles = nullptr;
+  double* step_fac = nullptr;
   double *a_vals64 = nullptr, *t_vals64 = nullptr;
   float *a_vals32 = nullptr, *t_vals32 = nullptr;
   double *c_un = nullptr, *l_un = nullptr, *u_un = nullptr, *lo_un = nullptr, *hi_un = nullptr;

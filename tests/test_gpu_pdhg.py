@@ -35,7 +35,7 @@ EPS = 2.0 ** -52
 MARGIN = 1e-4  # relative closeness of a restart/candidate comparison that counts as a tie
 
 
-def check_decisions(steps, checks, trace, replayed):
+def check_decisions(steps, checks, trace, replayed, long_run=False):
     """The oracle's own decisions, computed on the same trajectory, against the
     device's: step sizes within a tolerance scaled by the condition number of the
     interaction term, accept/restart/candidate choices equal unless the deciding
@@ -52,7 +52,7 @@ def check_decisions(steps, checks, trace, replayed):
         # interaction term does not cancel (cond) and the step is not tiny against the
         # iterate (step_cond); otherwise only a sanity bound applies
         well = cond <= 1e6 and step_cond <= 1e4
-        tol = 1e-6 if well else 1e-2
+        tol = (1e-4 if long_run else 1e-6) if well else 1e-2
         if np.isfinite(eta_max) and np.isfinite(rec[1]):
             assert abs(eta_max - rec[1]) <= tol * eta_max, (k, eta_max, rec[1], cond)
             assert abs(eta_next - rec[3]) <= tol * eta_next, (k, eta_next, rec[3], cond)
@@ -89,7 +89,7 @@ def compare_after(inst, k, replay=True, tol=TOL, **kw):
         ey = min(ey, rel_err(A.T @ yg, A.T @ o.dual()))
     assert ex <= tol and ey <= tol, (ex, ey)
     assert bool(rg.used_average) == ro.used_average
-    check_decisions(steps, checks, ro.trace, replay)
+    check_decisions(steps, checks, ro.trace, replay, long_run=k > 100)
     assert abs(eta_g - o.eta) <= 1e-9 * o.eta and abs(om_g - o.omega) <= 1e-9 * o.omega
     assert abs(rg.rel_kkt - ro.rel_kkt) <= 1e-7 * max(1.0, ro.rel_kkt)
     g.close()
