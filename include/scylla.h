@@ -233,6 +233,33 @@ int scylla_perturb(const scylla_lp* lp, double* xhat, const double* xbar, int32_
  *   trace_capacity). */
 int scylla_get_trace(const scylla_lp* lp, double* steps, int64_t* n_steps, double* checks, int64_t* n_checks);
 
+/* Primal residual without any device allocation, for callers that cannot call
+ * cudaMalloc (inside a CUDA-graph capture, in a plugin handed a fixed memory pool,
+ * in a loop that forbids allocator calls).  The paper has no counterpart: this is
+ * a service entry point over the same residual the solver's KKT check computes.
+ *
+ * Computes, on the caller's stream, for the caller's LP rows and point x:
+ *   out[0] = ||A x - proj_[row_lo,row_hi](A x)||_2
+ *   out[1] = out[0] / (1 + ||b||_2), b_i = the largest finite |row_lo_i|, |row_hi_i|
+ * (eps_p of scylla_pdhg_result for the same point).
+ *   m: rows, 1 <= m <= 2,097,152 (beyond that INVALID_ARG: the fixed scratch holds
+ *   8192 block sums of 256 rows).  rowptr (int64, m+1), cols (int32), vals (double),
+ *   x (double, the columns the CSR refers to), row_lo, row_hi (double, m), out
+ *   (double, 2): all DEVICE pointers owned by the caller.  cuda_stream: a
+ *   cudaStream_t or NULL.  The call is asynchronous: out is ready when the stream
+ *   reaches it.
+ * Scratch: one file-scope __device__ array of 128 KiB per device, held by every GPU
+ * that loads the library until the process exits.  The first call on a device
+ * looks its address up and clears its counter (a synchronising step): make that
+ * first call before any stream capture.  Every call shares the array, so calls
+ * that overlap on the GPU race and must be serialised by the caller.  Nothing is
+ * allocated, by this library or by any library it calls.
+ * Errors: INVALID_ARG (sizes, null pointers), UNSUPPORTED (device ordinal >= 64),
+ * CUDA. */
+int scylla_primal_residual_noalloc(int64_t m, const int64_t* rowptr, const int32_t* cols, const double* vals,
+                                   const double* x, const double* row_lo, const double* row_hi, double* out,
+                                   void* cuda_stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* scylla_last_error(void);
 

@@ -94,6 +94,7 @@ _SIGS = {
     "scylla_get_trace": (C.c_int, [_P, _D, C.POINTER(C.c_int64), _D, C.POINTER(C.c_int64)]),
     "scylla_reset_state": (C.c_int, [_P]),
     "scylla_time_kernels": (C.c_int, [_P, C.c_int32, _D]),
+    "scylla_primal_residual_noalloc": (C.c_int, [C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "scylla_last_error": (C.c_char_p, []),
 }
 
@@ -136,6 +137,13 @@ def default_params(**kw) -> Params:
             raise AttributeError(k)
         setattr(p, k, v)
     return p
+
+
+def primal_residual_noalloc(m: int, rowptr: int, cols: int, vals: int, x: int, row_lo: int, row_hi: int,
+                            out: int, stream=None):
+    """scylla_primal_residual_noalloc on caller-owned device pointers (ints); see the header."""
+    _check(lib().scylla_primal_residual_noalloc(int(m), _P(rowptr), _P(cols), _P(vals), _P(x), _P(row_lo),
+                                                 _P(row_hi), _P(out), _P(stream) if stream else None))
 
 
 def _f64(a, n):
