@@ -45,6 +45,7 @@ extern "C" {
 #define SCYLLA_ITER_LIMIT 1 /* k reached the iteration limit (Algorithm 1) */
 #define SCYLLA_STALLED 2    /* rounding of x unchanged over stall_checks checks */
 #define SCYLLA_NUMERICAL 3  /* NaN/Inf met in a step-size or KKT reduction */
+#define SCYLLA_DEVICE_TIMEOUT 4 /* a bounded device-side wait ran out (the call returns SCYLLA_ERR_TIMEOUT) */
 
 /* ---- run status (scylla_run_result.status) -------------------------------- */
 #define SCYLLA_FOUND 0
@@ -78,9 +79,11 @@ typedef struct {
   int32_t primal_weight_update; /* update omega at restarts (1) */
   int32_t stall_checks;         /* stop when round(x_I) is unchanged for this many checks; 0 = off (0) */
   int32_t aux_general_integers; /* add l1-distance auxiliary columns/rows for general integers (1) */
-  int32_t use_graph;            /* 1: one CUDA graph per n_check attempts, replayed by a pipelined host
-                                   loop; 2: a single graph with a device-side while loop; 0: direct
-                                   launches (1) */
+  int32_t use_graph;            /* 3: one persistent cooperative kernel runs the whole solve (grid
+                                   barriers between phases; falls back to 1 where it cannot be
+                                   co-resident); 1: one CUDA graph per n_check attempts, replayed by a
+                                   pipelined host loop; 2: a single graph with a device-side while
+                                   loop; 0: direct launches (3) */
   double fixed_step_factor;     /* f of the fixed-step mode (0.9) */
   double beta_sufficient;       /* restart if KKT <= 0.2 KKT_last_restart */
   double beta_necessary;        /* ... or <= 0.8 KKT_last_restart and KKT grew since the last check */
@@ -100,6 +103,7 @@ typedef struct {
   int32_t trace_capacity;       /* attempts recorded by the decision trace of each solve; 0 = off (0) */
   uint64_t seed;                /* perturbation random stream (0) */
   double time_limit_s;          /* wall-clock limit of scylla_run, <= 0 for none (0) */
+  double device_wait_limit_s;   /* bound of every device-side barrier wait (5) */
 } scylla_params;
 
 typedef struct {

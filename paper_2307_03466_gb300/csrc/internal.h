@@ -24,6 +24,10 @@ namespace scylla {
 
 constexpr int kWarpsPerBlock = 8;
 constexpr int kThreads = kWarpsPerBlock * 32;
+constexpr int kMaxWarps = 32;       // bound of per-warp shared arrays
+constexpr int kPWarps = 16;         // warps per block of the persistent solve kernel
+constexpr int kPThreads = kPWarps * 32;
+constexpr int kMaxNcheckPersistent = 1024;
 constexpr int kTileNnz = 256;  // nonzeros per multi-row warp tile
 constexpr int kTileRows = 32;  // rows per multi-row warp tile (one lane per row)
 constexpr int kVec = 4;        // elements per lane per vector load
@@ -83,6 +87,8 @@ struct DevLP {
   double *part_p, *part_d, *part_c1, *part_c2;
   int grid_p, grid_d, grid_c1, grid_c2;
   double* step_fac;      // 2 * n_check: (1 - kk^-a, 1 + kk^-b) of the next n_check attempts
+  double* pp_part;       // persistent kernel: 24 partial sums per block
+  unsigned long long* p_hash;  // persistent kernel: two rounding-hash slots
   int n_check;
   double* trace_steps;   // 4 doubles per attempt, or null
   double* trace_checks;  // 5 doubles per check, or null
@@ -172,6 +178,13 @@ cudaError_t launch_check_cols(const DevLP<T>& d, cudaStream_t st);
 template <typename T>
 cudaError_t launch_check_rows(const DevLP<T>& d, cudaStream_t st);
 cudaError_t launch_loop_ctl(Control* ctl, cudaGraphConditionalHandle h, cudaStream_t st);
+// persistent cooperative solve: blocks per SM that fit (0 if it cannot run), and the launch
+template <typename T>
+int persistent_blocks_per_sm();
+template <typename T>
+cudaError_t launch_persistent(const DevLP<T>& d, void* grid_bar, int grid, double wait_limit_s, cudaStream_t st);
+constexpr int kPersistentPartials = 24;  // doubles per block in DevLP::pp_part
+constexpr size_t kGridBarBytes = 16;
 template <typename T>
 cudaError_t launch_get_x(const DevLP<T>& d, double* out, int count, cudaStream_t st);
 template <typename T>

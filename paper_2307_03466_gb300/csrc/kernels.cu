@@ -123,8 +123,8 @@ __device__ __forceinline__ unsigned long long round_hash(long long j, double v) 
 // per-block reduction of N partial sums into part[blockIdx.x * N + k], fixed order
 template <int N, typename A>
 __device__ __forceinline__ void block_store_partials(const A (&v)[N], double* __restrict__ part) {
-  __shared__ double sh[kWarpsPerBlock][N];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ double sh[kMaxWarps][N];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     const A t = warp_sum(v[k]);
@@ -133,10 +133,10 @@ __device__ __forceinline__ void block_store_partials(const A (&v)[N], double* __
   __syncthreads();
   if (threadIdx.x < N) {
     double s = 0.0;
-#pragma unroll
-    for (int i = 0; i < kWarpsPerBlock; ++i) s += sh[i][threadIdx.x];
+    for (int i = 0; i < nw; ++i) s += sh[i][threadIdx.x];
     part[blockIdx.x * N + threadIdx.x] = s;
   }
+  __syncthreads();
 }
 
 __device__ __forceinline__ bool is_last_block(unsigned int* counter) {
@@ -155,8 +155,8 @@ __device__ __forceinline__ bool is_last_block(unsigned int* counter) {
 template <int NA, int NB>
 __device__ void reduce_two(const double* pa, int na, const double* pb, int nb, double* out_shared) {
   constexpr int N = NA + NB;
-  __shared__ double sh[kWarpsPerBlock][N];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ double sh[kMaxWarps][N];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double s[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) s[k] = 0.0;
@@ -174,7 +174,7 @@ __device__ void reduce_two(const double* pa, int na, const double* pb, int nb, d
   __syncthreads();
   if (threadIdx.x < N) {
     double t = 0.0;
-    for (int i = 0; i < kWarpsPerBlock; ++i) t += sh[i][threadIdx.x];
+    for (int i = 0; i < nw; ++i) t += sh[i][threadIdx.x];
     out_shared[threadIdx.x] = t;
   }
   __syncthreads();
@@ -356,6 +356,55 @@ struct AccOf {
   typedef T type;
 };
 
+// gathered vectors: read-only path within one launch; L2-coherent loads inside the
+// persistent kernel, where other SMs wrote them earlier in the same launch
+template <bool Coh, typename T>
+__device__ __forceinline__ T gload(const T* p) {
+  if (Coh) return __ldcg(p);
+  return __ldg(p);
+}
+
+// the control values one attempt or check needs, read once per phase
+struct SlotView {
+  int cur, nxt, avg, ia_cur, ia_avg;
+  double eta, omega, avg_w;
+  int copy_lr, aty_valid;
+};
+__device__ __forceinline__ SlotView make_view(const Control* c) {
+  SlotView v;
+  v.cur = c->ix_cur;
+  v.nxt = c->ix_next;
+  v.avg = c->ix_avg;
+  v.ia_cur = c->ia_cur;
+  v.ia_avg = c->ia_avg;
+  v.eta = c->eta;
+  v.omega = c->omega;
+  v.avg_w = c->avg_w;
+  v.copy_lr = c->copy_lr;
+  v.aty_valid = c->aty_valid;
+  return v;
+}
+
+// rows of every tile owned by this warp, without a gather: lane r takes row r of a
+// multi-row tile, lane 0 a long row (the same row-to-warp map as spmv_tiles)
+template <typename T, typename Epi>
+__device__ __forceinline__ void tiles_rows(const int2* __restrict__ tiles, int ntiles, const T* __restrict__ src,
+                                           Epi& epi) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int t = gwarp; t < ntiles; t += nwarps) {
+    const int2 ta = __ldg(tiles + t), tb = __ldg(tiles + t + 1);
+    const int nr = tb.x - ta.x;
+    const bool mine = (nr == 1 && tb.y - ta.y > kTileNnz) ? lane == 0 : lane < nr;
+    if (mine) {
+      const int row = ta.x + lane;
+      const T s[1] = {src[row]};
+      epi.finish(row, s, epi.load(row));
+    }
+  }
+}
+
 // ---------------------------------------------------------------- PDHG slot ---
 template <typename T>
 struct PrimalEpi {
@@ -386,44 +435,35 @@ struct PrimalEpi {
   }
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_primal(DevLP<T> d) {
-  Control* ctl = d.ctl;
-  if (ctl->done || ctl->k >= ctl->iter_limit) return;
-  __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
-  const int cur = ctl->ix_cur, nxt = ctl->ix_next, avg = ctl->ix_avg;
-  const double wd = ctl->avg_w;
-  const bool aty_valid = ctl->aty_valid != 0;
+// primal step of Algorithm 1 over all columns; block partial of ||x' - x||^2 to part
+template <typename T, bool Coh>
+__device__ __forceinline__ void primal_phase(const DevLP<T>& d, const SlotView& v, T* sm, double* part) {
   PrimalEpi<T> epi;
-  epi.xc = d.X[cur];
-  epi.xn = d.X[nxt];
-  epi.xa = d.X[avg];
-  epi.aty = d.ATY[ctl->ia_cur];
+  epi.xc = d.X[v.cur];
+  epi.xn = d.X[v.nxt];
+  epi.xa = d.X[v.avg];
+  epi.aty = d.ATY[v.ia_cur];
   epi.xlr = d.XLR;
   epi.cc = d.c;
   epi.ll = d.l;
   epi.uu = d.u;
-  epi.tau = T(ctl->eta / ctl->omega);
-  epi.w = T(wd);
-  epi.w1 = T(1.0 - wd);
-  epi.do_avg = wd > 0.0;
-  epi.copy_lr = ctl->copy_lr != 0;
-  epi.store_aty = !aty_valid;
+  epi.tau = T(v.eta / v.omega);
+  epi.w = T(v.avg_w);
+  epi.w1 = T(1.0 - v.avg_w);
+  epi.do_avg = v.avg_w > 0.0;
+  epi.copy_lr = v.copy_lr != 0;
+  epi.store_aty = !v.aty_valid;
   epi.acc = 0;
-  if (aty_valid) {
-    const T* __restrict__ aty = epi.aty;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += gridDim.x * blockDim.x) {
-      const T s[1] = {aty[j]};
-      epi.finish(j, s, epi.load(j));
-    }
+  if (v.aty_valid) {
+    tiles_rows<T>(d.t_tiles, d.t_ntiles, epi.aty, epi);  // retry: A^T y is cached
   } else {
-    const T* __restrict__ yc = d.Y[cur];
-    auto gat = [&](int i, T(&g)[1]) { g[0] = __ldg(yc + i); };
+    const T* __restrict__ yc = d.Y[v.cur];
+    auto gat = [&](int i, T(&g)[1]) { g[0] = gload<Coh>(yc + i); };
     spmv_tiles<1, T, T>(d.t_tiles, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals, gat, epi,
                         sm + (threadIdx.x >> 5) * kSmemPerWarp);
   }
-  const typename AccOf<T>::type v[kNP] = {epi.acc};
-  block_store_partials<kNP>(v, d.part_p);
+  const typename AccOf<T>::type acc[kNP] = {epi.acc};
+  block_store_partials<kNP>(acc, part);
 }
 
 template <typename T>
@@ -458,35 +498,48 @@ struct DualEpi {
   }
 };
 
+// extrapolated dual step of Algorithm 1 over all rows; block partials of ||y' - y||^2
+// and (y' - y).(A x' - A x) to part
+template <typename T, bool Coh>
+__device__ __forceinline__ void dual_phase(const DevLP<T>& d, const SlotView& v, T* sm, double* part) {
+  DualEpi<T> epi;
+  epi.axc = d.AX[v.cur];
+  epi.axn = d.AX[v.nxt];
+  epi.yc = d.Y[v.cur];
+  epi.yn = d.Y[v.nxt];
+  epi.ya = d.Y[v.avg];
+  epi.ylr = d.YLR;
+  epi.lo = d.lo;
+  epi.hi = d.hi;
+  epi.sigma = T(v.eta * v.omega);
+  epi.w = T(v.avg_w);
+  epi.w1 = T(1.0 - v.avg_w);
+  epi.do_avg = v.avg_w > 0.0;
+  epi.copy_lr = v.copy_lr != 0;
+  epi.acc0 = 0;
+  epi.acc1 = 0;
+  const T* __restrict__ xn = d.X[v.nxt];
+  auto gat = [&](int j, T(&g)[1]) { g[0] = gload<Coh>(xn + j); };
+  spmv_tiles<1, T, T>(d.a_tiles, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals, gat, epi,
+                      sm + (threadIdx.x >> 5) * kSmemPerWarp);
+  const typename AccOf<T>::type acc[kND] = {epi.acc0, epi.acc1};
+  block_store_partials<kND>(acc, part);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_primal(DevLP<T> d) {
+  Control* ctl = d.ctl;
+  if (ctl->done || ctl->k >= ctl->iter_limit) return;
+  __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
+  primal_phase<T, false>(d, make_view(ctl), sm, d.part_p);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_dual(DevLP<T> d) {
   Control* ctl = d.ctl;
   if (ctl->done || ctl->k >= ctl->iter_limit) return;
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
-  const int cur = ctl->ix_cur, nxt = ctl->ix_next, avg = ctl->ix_avg;
-  const double wd = ctl->avg_w;
-  DualEpi<T> epi;
-  epi.axc = d.AX[cur];
-  epi.axn = d.AX[nxt];
-  epi.yc = d.Y[cur];
-  epi.yn = d.Y[nxt];
-  epi.ya = d.Y[avg];
-  epi.ylr = d.YLR;
-  epi.lo = d.lo;
-  epi.hi = d.hi;
-  epi.sigma = T(ctl->eta * ctl->omega);
-  epi.w = T(wd);
-  epi.w1 = T(1.0 - wd);
-  epi.do_avg = wd > 0.0;
-  epi.copy_lr = ctl->copy_lr != 0;
-  epi.acc0 = 0;
-  epi.acc1 = 0;
-  const T* __restrict__ xn = d.X[nxt];
-  auto gat = [&](int j, T(&g)[1]) { g[0] = __ldg(xn + j); };
-  spmv_tiles<1, T, T>(d.a_tiles, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals, gat, epi,
-                      sm + (threadIdx.x >> 5) * kSmemPerWarp);
-  const typename AccOf<T>::type v[kND] = {epi.acc0, epi.acc1};
-  block_store_partials<kND>(v, d.part_d);
+  dual_phase<T, false>(d, make_view(ctl), sm, d.part_d);
   if (!is_last_block(&ctl->cnt_dual)) return;
   __shared__ double red[kNP + kND];
   reduce_two<kNP, kND>(d.part_p, d.grid_p, d.part_d, d.grid_d, red);
@@ -666,22 +719,22 @@ struct CheckColsEpi {
   }
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_check_cols(DevLP<T> d) {
-  Control* ctl = d.ctl;
-  if (ctl->done) return;
-  __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];
-  const int cur = ctl->ix_cur, avg = ctl->ix_avg;
-  const double wd = ctl->avg_w;
+// FP64 column half of a check (Section 2.2): A^T y of the current and of the
+// averaged dual from FP64 values, reduced costs, dual residuals, objectives, the
+// rounding hash; block partials to part, hash into *hash
+template <typename T, bool Coh>
+__device__ __forceinline__ void check_cols_phase(const DevLP<T>& d, const SlotView& v, double* sm, double* part,
+                                                 unsigned long long* hash) {
+  const double wd = v.avg_w;
   const T w = T(wd), w1 = T(1.0 - wd);
   const bool do_avg = wd > 0.0;
-  const T* __restrict__ yc = d.Y[cur];
-  const T* __restrict__ ya = d.Y[avg];
+  const T* __restrict__ yc = d.Y[v.cur];
+  const T* __restrict__ ya = d.Y[v.avg];
   CheckColsEpi<T> epi;
-  epi.xc = d.X[cur];
-  epi.xa = d.X[avg];
-  epi.aty_c = d.ATY[ctl->ia_cur];
-  epi.aty_a = d.ATY[ctl->ia_avg];
+  epi.xc = d.X[v.cur];
+  epi.xa = d.X[v.avg];
+  epi.aty_c = d.ATY[v.ia_cur];
+  epi.aty_a = d.ATY[v.ia_avg];
   epi.xlr = d.XLR;
   epi.C = d.C;
   epi.c64 = d.c64;
@@ -695,17 +748,17 @@ __global__ void __launch_bounds__(kThreads) k_check_cols(DevLP<T> d) {
   for (int k = 0; k < kNC1; ++k) epi.acc[k] = 0.0;
   epi.h = 0ULL;
   auto gat = [&](int i, double(&g)[2]) {
-    const T y = yc[i];
-    T v = ya[i];
-    if (do_avg) v = blend(v, y, w1, w);
+    const T y = gload<Coh>(yc + i);
+    T av = gload<Coh>(ya + i);
+    if (do_avg) av = blend(av, y, w1, w);
     g[0] = double(y);
-    g[1] = double(v);
+    g[1] = double(av);
   };
   spmv_tiles<2, double, double>(d.t_tiles, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals64, gat, epi,
                                 sm + (threadIdx.x >> 5) * 2 * kSmemPerWarp);
-  block_store_partials<kNC1>(epi.acc, d.part_c1);
+  block_store_partials<kNC1>(epi.acc, part);
   const unsigned long long h = warp_sum_u64(epi.h);
-  if ((threadIdx.x & 31) == 0 && h != 0ULL) atomicAdd(&ctl->hash_accum, h);
+  if ((threadIdx.x & 31) == 0 && h != 0ULL) atomicAdd(hash, h);
 }
 
 template <typename T>
@@ -745,36 +798,49 @@ struct CheckRowsEpi {
   }
 };
 
+// FP64 row half of a check: A x of the current and averaged primal from FP64
+// values (refreshing the cached products), primal residuals, dual objective rows
+template <typename T, bool Coh>
+__device__ __forceinline__ void check_rows_phase(const DevLP<T>& d, const SlotView& v, double* sm, double* part) {
+  const T* __restrict__ xc = d.X[v.cur];
+  const T* __restrict__ xa = d.X[v.avg];
+  CheckRowsEpi<T> epi;
+  epi.yc = d.Y[v.cur];
+  epi.ya = d.Y[v.avg];
+  epi.ax_c = d.AX[v.cur];
+  epi.ax_a = d.AX[v.avg];
+  epi.ylr = d.YLR;
+  epi.R = d.R;
+  epi.lo64 = d.lo64;
+  epi.hi64 = d.hi64;
+  epi.w = T(v.avg_w);
+  epi.w1 = T(1.0 - v.avg_w);
+  epi.do_avg = v.avg_w > 0.0;
+#pragma unroll
+  for (int k = 0; k < kNC2; ++k) epi.acc[k] = 0.0;
+  auto gat = [&](int j, double(&g)[2]) {
+    g[0] = double(gload<Coh>(xc + j));
+    g[1] = double(gload<Coh>(xa + j));
+  };
+  spmv_tiles<2, double, double>(d.a_tiles, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals64, gat, epi,
+                                sm + (threadIdx.x >> 5) * 2 * kSmemPerWarp);
+  block_store_partials<kNC2>(epi.acc, part);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_check_cols(DevLP<T> d) {
+  Control* ctl = d.ctl;
+  if (ctl->done) return;
+  __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];
+  check_cols_phase<T, false>(d, make_view(ctl), sm, d.part_c1, &ctl->hash_accum);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_check_rows(DevLP<T> d) {
   Control* ctl = d.ctl;
   if (ctl->done) return;
   __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];
-  const int cur = ctl->ix_cur, avg = ctl->ix_avg;
-  const double wd = ctl->avg_w;
-  const T* __restrict__ xc = d.X[cur];
-  const T* __restrict__ xa = d.X[avg];
-  CheckRowsEpi<T> epi;
-  epi.yc = d.Y[cur];
-  epi.ya = d.Y[avg];
-  epi.ax_c = d.AX[cur];
-  epi.ax_a = d.AX[avg];
-  epi.ylr = d.YLR;
-  epi.R = d.R;
-  epi.lo64 = d.lo64;
-  epi.hi64 = d.hi64;
-  epi.w = T(wd);
-  epi.w1 = T(1.0 - wd);
-  epi.do_avg = wd > 0.0;
-#pragma unroll
-  for (int k = 0; k < kNC2; ++k) epi.acc[k] = 0.0;
-  auto gat = [&](int j, double(&g)[2]) {
-    g[0] = double(xc[j]);
-    g[1] = double(xa[j]);
-  };
-  spmv_tiles<2, double, double>(d.a_tiles, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals64, gat, epi,
-                                sm + (threadIdx.x >> 5) * 2 * kSmemPerWarp);
-  block_store_partials<kNC2>(epi.acc, d.part_c2);
+  check_rows_phase<T, false>(d, make_view(ctl), sm, d.part_c2);
   if (!is_last_block(&ctl->cnt_c2)) return;
   __shared__ double red[kNC1 + kNC2];
   reduce_two<kNC1, kNC2>(d.part_c1, d.grid_c1, d.part_c2, d.grid_c2, red);
@@ -782,6 +848,133 @@ __global__ void __launch_bounds__(kThreads) k_check_rows(DevLP<T> d) {
   if (threadIdx.x == 0) {
     check_control(ctl, red, d.trace_checks, d.trace_cap);
     ctl->cnt_c2 = 0;
+  }
+}
+
+// ------------------------------------------------------ persistent solve kernel ---
+// The whole solve in one cooperative launch (all blocks co-resident): per attempt a
+// primal phase and a dual phase separated by grid barriers; after the dual barrier
+// every block reduces the block partials itself, in the same fixed order, and so
+// takes the same step-size decision on its own shared copy of the control block
+// (no third barrier, no serial tail).  Checks run as two more phases.  Partials of
+// consecutive attempts alternate between two buffers, so a block that is still
+// reducing attempt s never sees attempt s+1's partials.  Every barrier wait is
+// bounded by a time limit; on expiry the kernel records SCYLLA_DEVICE_TIMEOUT and
+// all blocks return.
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+  int err;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ bool grid_sync(GridBar* b, unsigned long long limit_ns) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned int* vgen = &b->gen;
+    volatile int* verr = &b->err;
+    const unsigned int g = *vgen;
+    __threadfence();
+    if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+      atomicExch(&b->count, 0u);
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*vgen == g) {
+        if (*verr) {
+          ok = 0;
+          break;
+        }
+        if (global_ns() - t0 > limit_ns) {
+          atomicExch(&b->err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    if (*verr) ok = 0;
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPThreads, 1) k_solve_persistent(DevLP<T> d, GridBar* bar,
+                                                                  unsigned long long limit_ns) {
+  extern __shared__ double psm[];  // 2 * kPWarps * kSmemPerWarp doubles
+  __shared__ Control sc;
+  __shared__ double fac[2 * kMaxNcheckPersistent];
+  __shared__ double red[kNC1 + kNC2];
+  const int nb = gridDim.x;
+  double* pp = d.pp_part;  // [2][nb] primal, [2][2nb] dual, [10 nb] cols, [8 nb] rows
+  double* part_p[2] = {pp, pp + nb};
+  double* part_d[2] = {pp + 2 * nb, pp + 4 * nb};
+  double* part_c1 = pp + 6 * nb;
+  double* part_c2 = pp + 16 * nb;
+  unsigned long long* hash = d.p_hash;  // two slots, alternating between checks
+  if (threadIdx.x == 0) sc = *d.ctl;
+  __syncthreads();
+  const bool lead = blockIdx.x == 0;
+  int hslot = 0;
+  bool ok = true;
+  long long since = 0;  // attempts since the last check
+  bool do_check = true;  // the start point is evaluated first
+  while (ok) {
+    if (do_check) {
+      const SlotView v = make_view(&sc);
+      check_cols_phase<T, true>(d, v, psm, part_c1, &hash[hslot]);
+      ok = grid_sync(bar, limit_ns);
+      if (!ok) break;
+      check_rows_phase<T, true>(d, v, psm, part_c2);
+      ok = grid_sync(bar, limit_ns);
+      if (!ok) break;
+      reduce_two<kNC1, kNC2>(part_c1, nb, part_c2, nb, red);
+      fill_step_factors(&sc, fac, d.n_check);
+      if (threadIdx.x == 0) {
+        sc.hash_accum = __ldcg(&hash[hslot]);
+        if (lead) hash[hslot ^ 1] = 0ULL;  // the next check's slot; nobody reads it now
+        check_control(&sc, red, lead ? d.trace_checks : nullptr, d.trace_cap);
+      }
+      __syncthreads();
+      hslot ^= 1;
+      since = 0;
+      do_check = false;
+    }
+    if (sc.done) break;
+    if (sc.k >= sc.iter_limit || since == d.n_check) {
+      do_check = true;
+      continue;
+    }
+    const int par = int(sc.k & 1);
+    const SlotView v = make_view(&sc);
+    primal_phase<T, true>(d, v, reinterpret_cast<T*>(psm), part_p[par]);
+    ok = grid_sync(bar, limit_ns);
+    if (!ok) break;
+    dual_phase<T, true>(d, v, reinterpret_cast<T*>(psm), part_d[par]);
+    ok = grid_sync(bar, limit_ns);
+    if (!ok) break;
+    reduce_two<kNP, kND>(part_p[par], nb, part_d[par], nb, red);
+    if (threadIdx.x == 0) step_control(&sc, red[0], red[1], red[2], fac, d.n_check, lead ? d.trace_steps : nullptr,
+                                       d.trace_cap);
+    __syncthreads();
+    ++since;
+  }
+  if (lead && threadIdx.x == 0) {
+    if (!ok) {
+      sc.done = 1;
+      sc.status = SCYLLA_DEVICE_TIMEOUT;
+    }
+    *d.ctl = sc;
   }
 }
 
@@ -1226,6 +1419,34 @@ cudaError_t launch_init_point(const DevLP<T>& d, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+constexpr size_t kPersistentSmem = sizeof(double) * 2 * kPWarps * kSmemPerWarp;
+
+template <typename T>
+int persistent_blocks_per_sm() {
+  if (cudaFuncSetAttribute(k_solve_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(kPersistentSmem)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_persistent<T>, kPThreads, kPersistentSmem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm;
+}
+
+template <typename T>
+cudaError_t launch_persistent(const DevLP<T>& d, void* grid_bar, int grid, double wait_limit_s, cudaStream_t st) {
+  GridBar* bar = static_cast<GridBar*>(grid_bar);
+  unsigned long long limit_ns = (unsigned long long)(wait_limit_s * 1e9);
+  DevLP<T> dd = d;
+  void* args[] = {&dd, &bar, &limit_ns};
+  return cudaLaunchCooperativeKernel((const void*)k_solve_persistent<T>, dim3(grid), dim3(kPThreads), args,
+                                     kPersistentSmem, st);
+}
+
 template <typename T>
 int occupancy_grid(int kernel_id, int work_tiles) {
   int per_sm = 1;
@@ -1255,7 +1476,9 @@ int occupancy_grid(int kernel_id, int work_tiles) {
   template cudaError_t launch_get_y<T>(const DevLP<T>&, double*, int, cudaStream_t);                      \
   template cudaError_t launch_set_xy<T>(const DevLP<T>&, const double*, const double*, cudaStream_t);     \
   template cudaError_t launch_init_point<T>(const DevLP<T>&, cudaStream_t);                               \
-  template int occupancy_grid<T>(int, int);
+  template int occupancy_grid<T>(int, int);                                                                \
+  template int persistent_blocks_per_sm<T>();                                                             \
+  template cudaError_t launch_persistent<T>(const DevLP<T>&, void*, int, double, cudaStream_t);
 
 SCYLLA_INSTANTIATE(double)
 SCYLLA_INSTANTIATE(float)

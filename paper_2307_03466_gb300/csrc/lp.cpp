@@ -57,7 +57,7 @@ extern "C" void scylla_default_params(scylla_params* p) {
   p->primal_weight_update = 1;
   p->stall_checks = 0;
   p->aux_general_integers = 1;
-  p->use_graph = 1;
+  p->use_graph = 3;
   p->fixed_step_factor = 0.9;
   p->beta_sufficient = 0.2;
   p->beta_necessary = 0.8;
@@ -76,6 +76,7 @@ extern "C" void scylla_default_params(scylla_params* p) {
   p->trace_capacity = 0;
   p->seed = 0;
   p->time_limit_s = 0.0;
+  p->device_wait_limit_s = 5.0;
 }
 
 extern "C" const char* scylla_last_error(void) { return get_error(); }
@@ -174,6 +175,8 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   lp->p = *pin;
   if (lp->p.n_check < 1) FAIL(SCYLLA_ERR_INVALID_ARG, "n_check must be >= 1");
   if (lp->p.trace_capacity < 0) FAIL(SCYLLA_ERR_INVALID_ARG, "trace_capacity must be >= 0");
+  if (lp->p.use_graph < 0 || lp->p.use_graph > 3) FAIL(SCYLLA_ERR_INVALID_ARG, "use_graph must be 0..3");
+  if (!(lp->p.device_wait_limit_s > 0.0)) FAIL(SCYLLA_ERR_INVALID_ARG, "device_wait_limit_s must be > 0");
   if (lp->p.precision != SCYLLA_PREC_FP64 && lp->p.precision != SCYLLA_PREC_MIXED)
     FAIL(SCYLLA_ERR_INVALID_ARG, "unknown precision");
   CK(cudaGetDevice(&lp->device));
@@ -296,6 +299,11 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     lp->grid_c1 = occupancy_grid<double>(2, lp->t_ntiles);
     lp->grid_c2 = occupancy_grid<double>(3, lp->a_ntiles);
   }
+  // persistent cooperative solve: one grid of co-resident blocks, if it fits
+  {
+    const int per_sm = mixed ? persistent_blocks_per_sm<float>() : persistent_blocks_per_sm<double>();
+    lp->p_grid = (per_sm >= 1 && lp->p.n_check <= kMaxNcheckPersistent) ? per_sm * device_sm_count() : 0;
+  }
   // the primal kernel also runs the elementwise retry path over n columns
   lp->red_blocks = std::max(1, std::min(4 * device_sm_count(), int((std::max(m, n) + kThreads - 1) / kThreads)));
   const size_t vs = mixed ? sizeof(float) : sizeof(double);
@@ -360,6 +368,9 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     lp->io_y = ar.take<double>(m);
     lp->ctl = ar.take<Control>(1);
     lp->step_fac = ar.take<double>(2 * size_t(lp->p.n_check));
+    lp->pp_part = ar.take<double>(size_t(kPersistentPartials) * std::max(lp->p_grid, 1));
+    lp->p_hash = ar.take<unsigned long long>(2);
+    lp->grid_bar = ar.take<char>(kGridBarBytes);
     const size_t tc = size_t(lp->p.trace_capacity);
     lp->trace_steps = tc ? ar.take<double>(4 * tc) : nullptr;
     lp->trace_checks = tc ? ar.take<double>(5 * tc) : nullptr;
@@ -503,6 +514,8 @@ void fill_dev(DevLP<T>& d, scylla_lp* lp) {
   d.part_p = lp->part_p; d.part_d = lp->part_d; d.part_c1 = lp->part_c1; d.part_c2 = lp->part_c2;
   d.grid_p = lp->grid_p; d.grid_d = lp->grid_d; d.grid_c1 = lp->grid_c1; d.grid_c2 = lp->grid_c2;
   d.step_fac = lp->step_fac;
+  d.pp_part = lp->pp_part;
+  d.p_hash = lp->p_hash;
   d.n_check = lp->p.n_check;
   d.trace_steps = lp->trace_steps;
   d.trace_checks = lp->trace_checks;
@@ -652,9 +665,21 @@ static int solve_impl(scylla_lp* lp, const DevLP<T>& d, double tol, int64_t iter
   const long long max_chunks = (iter_limit + nchk - 1) / nchk + 2;
   CK(cudaEventRecord(lp->ev0, st));
   CK(launch_solve_init<T>(d, tol, (long long)iter_limit, stall_checks, max_chunks, st));
+  long long launches = 1;
+  if (lp->p.use_graph == 3 && lp->p_grid > 0) {
+    // one cooperative launch evaluates the start point and runs every attempt
+    CK(cudaMemsetAsync(lp->grid_bar, 0, kGridBarBytes, st));
+    CK(cudaMemsetAsync(lp->p_hash, 0, 2 * sizeof(unsigned long long), st));
+    CK(launch_persistent<T>(d, lp->grid_bar, lp->p_grid, lp->p.device_wait_limit_s, st));
+    lp->last_launches = 2;
+    CK(cudaEventRecord(lp->ev1, st));
+    CK(cudaMemcpyAsync(lp->h_ctl, lp->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return SCYLLA_OK;
+  }
   CK(launch_check<T>(d, st));  // evaluates the start point, caches A x and A^T y
   const long long per_chunk = 2LL * nchk + 2;
-  long long launches = 3;
+  launches = 3;
   if (lp->p.use_graph == 2) {
     if (!lp->exec) {
       const int rc = build_graph<T>(lp, d);
@@ -662,7 +687,7 @@ static int solve_impl(scylla_lp* lp, const DevLP<T>& d, double tol, int64_t iter
     }
     CK(cudaGraphLaunch(lp->exec, st));
     launches = -1;  // counted on the device
-  } else if (lp->p.use_graph == 1) {
+  } else if (lp->p.use_graph == 1 || lp->p.use_graph == 3) {
     if (!lp->chunk_exec) {
       const int rc = build_chunk_graph<T>(lp, d);
       if (rc != SCYLLA_OK) return rc;
@@ -708,6 +733,7 @@ int scylla_lp::solve(double tol, int64_t iter_limit, int stall_checks, scylla_pd
   if (rc != SCYLLA_OK) return rc;
   const Control& h = *h_ctl;
   if (!h.done) FAIL(SCYLLA_ERR_CUDA, "solve ended without a final check");
+  if (h.status == SCYLLA_DEVICE_TIMEOUT) FAIL(SCYLLA_ERR_TIMEOUT, "a device-side barrier wait ran out of time");
   if (out) {
     std::memset(out, 0, sizeof(*out));
     out->status = h.status;

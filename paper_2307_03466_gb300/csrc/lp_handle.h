@@ -42,6 +42,10 @@ struct scylla_lp {
   int *t_rowptr = nullptr, *t_cols = nullptr;
   int2 *a_tiles = nullptr, *t_tiles = nullptr;
   double* step_fac = nullptr;
+  double* pp_part = nullptr;
+  unsigned long long* p_hash = nullptr;
+  void* grid_bar = nullptr;
+  int p_grid = 0;  // persistent grid (0: that mode is unavailable)
   double *a_vals64 = nullptr, *t_vals64 = nullptr;
   float *a_vals32 = nullptr, *t_vals32 = nullptr;
   double *c_un = nullptr, *l_un = nullptr, *u_un = nullptr, *lo_un = nullptr, *hi_un = nullptr;

@@ -17,7 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "lib", "libscylla.so")
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -6
-CONVERGED, ITER_LIMIT, STALLED, NUMERICAL = 0, 1, 2, 3
+CONVERGED, ITER_LIMIT, STALLED, NUMERICAL, DEVICE_TIMEOUT = 0, 1, 2, 3, 4
 FOUND, NOT_FOUND = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 
@@ -45,7 +45,7 @@ class Params(C.Structure):
                 ("alpha", C.c_double), ("eps1", C.c_double), ("beta", C.c_double), ("eps_floor", C.c_double),
                 ("max_rounds", C.c_int64), ("iter_limit", C.c_int64), ("total_iter_cap", C.c_int64),
                 ("run_stall_checks", C.c_int32), ("trace_capacity", C.c_int32), ("seed", C.c_uint64),
-                ("time_limit_s", C.c_double)]
+                ("time_limit_s", C.c_double), ("device_wait_limit_s", C.c_double)]
 
 
 class PdhgResult(C.Structure):

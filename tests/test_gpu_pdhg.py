@@ -191,10 +191,11 @@ def test_box_lp_without_rows():
     g.close()
 
 
-@pytest.mark.parametrize("mode", [0, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_launch_modes_agree(mode):
-    """Chunk graphs with a host loop (default), a device-side while loop and plain
-    launches run the same kernels in the same order: identical results."""
+    """The persistent cooperative kernel (default), chunk graphs with a host loop, a
+    device-side while loop and plain launches compute the same attempts with the
+    same per-row arithmetic and reduction orders: identical results."""
     inst = INSTANCES["packcover_2kx4k"]
     g1, _ = pair(inst)
     g2, _ = pair(inst, use_graph=mode)
