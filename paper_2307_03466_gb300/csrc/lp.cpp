@@ -57,7 +57,7 @@ extern "C" void scylla_default_params(scylla_params* p) {
   p->primal_weight_update = 1;
   p->stall_checks = 0;
   p->aux_general_integers = 1;
-  p->use_graph = 3;
+  p->use_graph = 1;
   p->fixed_step_factor = 0.9;
   p->beta_sufficient = 0.2;
   p->beta_necessary = 0.8;
