@@ -104,6 +104,9 @@ typedef struct {
   uint64_t seed;                /* perturbation random stream (0) */
   double time_limit_s;          /* wall-clock limit of scylla_run, <= 0 for none (0) */
   double device_wait_limit_s;   /* bound of every device-side barrier wait (5) */
+  int32_t pdl;                  /* launch the per-attempt kernels with programmatic dependent launch, so
+                                   each one is resident before its predecessor ends (1) */
+  int32_t reserved1;
 } scylla_params;
 
 typedef struct {

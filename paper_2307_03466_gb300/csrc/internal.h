@@ -90,6 +90,7 @@ struct DevLP {
   double* pp_part;       // persistent kernel: 24 partial sums per block
   unsigned long long* p_hash;  // persistent kernel: two rounding-hash slots
   int n_check;
+  int pdl;               // launch the per-attempt kernels with programmatic dependent launch
   double* trace_steps;   // 4 doubles per attempt, or null
   double* trace_checks;  // 5 doubles per check, or null
   int trace_cap;

@@ -350,6 +350,15 @@ __device__ void fill_step_factors(Control* c, double* fac, int n_check) {
   if (threadIdx.x == 0) c->k_fac = k;
 }
 
+// Programmatic dependent launch: each per-attempt kernel is launched while its
+// predecessor still runs; it waits here for the predecessor's completion (and
+// memory) before touching any mutable data, then lets its own successor launch.
+// Without the launch attribute both calls return at once.
+__device__ __forceinline__ void pdl_enter() {
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();
+}
+
 // per-thread accumulator type of the bulk kernels
 template <typename T>
 struct AccOf {
@@ -529,6 +538,7 @@ __device__ __forceinline__ void dual_phase(const DevLP<T>& d, const SlotView& v,
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_primal(DevLP<T> d) {
   Control* ctl = d.ctl;
+  pdl_enter();
   if (ctl->done || ctl->k >= ctl->iter_limit) return;
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
   primal_phase<T, false>(d, make_view(ctl), sm, d.part_p);
@@ -537,6 +547,7 @@ __global__ void __launch_bounds__(kThreads) k_primal(DevLP<T> d) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_dual(DevLP<T> d) {
   Control* ctl = d.ctl;
+  pdl_enter();
   if (ctl->done || ctl->k >= ctl->iter_limit) return;
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
   dual_phase<T, false>(d, make_view(ctl), sm, d.part_d);
@@ -830,6 +841,7 @@ __device__ __forceinline__ void check_rows_phase(const DevLP<T>& d, const SlotVi
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_check_cols(DevLP<T> d) {
   Control* ctl = d.ctl;
+  pdl_enter();
   if (ctl->done) return;
   __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];
   check_cols_phase<T, false>(d, make_view(ctl), sm, d.part_c1, &ctl->hash_accum);
@@ -838,6 +850,7 @@ __global__ void __launch_bounds__(kThreads) k_check_cols(DevLP<T> d) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_check_rows(DevLP<T> d) {
   Control* ctl = d.ctl;
+  pdl_enter();
   if (ctl->done) return;
   __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];
   check_rows_phase<T, false>(d, make_view(ctl), sm, d.part_c2);
@@ -1358,39 +1371,52 @@ cudaError_t launch_solve_init(const DevLP<T>& d, double tol, long long iter_limi
   return cudaGetLastError();
 }
 
+// launch of a per-attempt kernel, with the programmatic-serialization attribute when
+// d.pdl is set (the kernel then overlaps its launch with its predecessor's tail)
+template <typename T>
+static cudaError_t launch_step_kernel(void (*kernel)(DevLP<T>), int grid, const DevLP<T>& d, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = d.pdl ? attr : nullptr;
+  cfg.numAttrs = d.pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, d);
+}
+
 template <typename T>
 cudaError_t launch_check(const DevLP<T>& d, cudaStream_t st) {
-  k_check_cols<T><<<d.grid_c1, kThreads, 0, st>>>(d);
-  k_check_rows<T><<<d.grid_c2, kThreads, 0, st>>>(d);
-  return cudaGetLastError();
+  cudaError_t e = launch_step_kernel<T>(k_check_cols<T>, d.grid_c1, d, st);
+  if (e == cudaSuccess) e = launch_step_kernel<T>(k_check_rows<T>, d.grid_c2, d, st);
+  return e;
 }
 
 template <typename T>
 cudaError_t launch_slot(const DevLP<T>& d, cudaStream_t st) {
-  k_primal<T><<<d.grid_p, kThreads, 0, st>>>(d);
-  k_dual<T><<<d.grid_d, kThreads, 0, st>>>(d);
-  return cudaGetLastError();
+  cudaError_t e = launch_step_kernel<T>(k_primal<T>, d.grid_p, d, st);
+  if (e == cudaSuccess) e = launch_step_kernel<T>(k_dual<T>, d.grid_d, d, st);
+  return e;
 }
 
 template <typename T>
 cudaError_t launch_primal(const DevLP<T>& d, cudaStream_t st) {
-  k_primal<T><<<d.grid_p, kThreads, 0, st>>>(d);
-  return cudaGetLastError();
+  return launch_step_kernel<T>(k_primal<T>, d.grid_p, d, st);
 }
 template <typename T>
 cudaError_t launch_dual(const DevLP<T>& d, cudaStream_t st) {
-  k_dual<T><<<d.grid_d, kThreads, 0, st>>>(d);
-  return cudaGetLastError();
+  return launch_step_kernel<T>(k_dual<T>, d.grid_d, d, st);
 }
 template <typename T>
 cudaError_t launch_check_cols(const DevLP<T>& d, cudaStream_t st) {
-  k_check_cols<T><<<d.grid_c1, kThreads, 0, st>>>(d);
-  return cudaGetLastError();
+  return launch_step_kernel<T>(k_check_cols<T>, d.grid_c1, d, st);
 }
 template <typename T>
 cudaError_t launch_check_rows(const DevLP<T>& d, cudaStream_t st) {
-  k_check_rows<T><<<d.grid_c2, kThreads, 0, st>>>(d);
-  return cudaGetLastError();
+  return launch_step_kernel<T>(k_check_rows<T>, d.grid_c2, d, st);
 }
 
 cudaError_t launch_loop_ctl(Control* ctl, cudaGraphConditionalHandle h, cudaStream_t st) {

@@ -77,6 +77,7 @@ extern "C" void scylla_default_params(scylla_params* p) {
   p->seed = 0;
   p->time_limit_s = 0.0;
   p->device_wait_limit_s = 5.0;
+  p->pdl = 1;
 }
 
 extern "C" const char* scylla_last_error(void) { return get_error(); }
@@ -517,6 +518,7 @@ void fill_dev(DevLP<T>& d, scylla_lp* lp) {
   d.pp_part = lp->pp_part;
   d.p_hash = lp->p_hash;
   d.n_check = lp->p.n_check;
+  d.pdl = lp->p.pdl ? 1 : 0;
   d.trace_steps = lp->trace_steps;
   d.trace_checks = lp->trace_checks;
   d.trace_cap = lp->p.trace_capacity;

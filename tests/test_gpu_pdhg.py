@@ -212,6 +212,21 @@ def test_launch_modes_agree(mode):
     g2.close()
 
 
+def test_programmatic_launch_changes_nothing():
+    """With and without programmatic dependent launch the same kernels run in the same
+    order on the same data: identical results."""
+    inst = INSTANCES["knapcover_700"]
+    g1, _ = pair(inst, pdl=1)
+    g2, _ = pair(inst, pdl=0)
+    r1 = g1.pdhg_solve(1e-6, 20000)
+    r2 = g2.pdhg_solve(1e-6, 20000)
+    assert r1.iterations == r2.iterations and r1.status == r2.status
+    np.testing.assert_array_equal(g1.primal(), g2.primal())
+    np.testing.assert_array_equal(g1.dual(), g2.dual())
+    g1.close()
+    g2.close()
+
+
 @pytest.mark.parametrize("name", ["setcover_200x500", "packcover_2kx4k", "long_rows"])
 def test_persistent_kernel_matches_graph_path(name):
     """The persistent kernel sums block partials over a different grid, so its step
