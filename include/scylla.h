@@ -267,6 +267,33 @@ int scylla_primal_residual_noalloc(int64_t m, const int64_t* rowptr, const int32
                                    const double* x, const double* row_lo, const double* row_hi, double* out,
                                    void* cuda_stream);
 
+/* ---- batched solve ---------------------------------------------------------
+ * Many LP relaxations of uneven size solved together: one launch sequence walks a
+ * shared list of warp tiles covering every LP (no tile spans two LPs), every LP has
+ * its own step size, primal weight, restarts and termination (Sections 2.1-2.2
+ * applied per LP), and a finished LP drops out while the others continue.  The LPs
+ * have no integrality here (the batched form is the LP solve of the pump). */
+typedef struct scylla_batch scylla_batch;
+
+/* count >= 1 LPs; A[b] (host CSR), c[b], col_lo[b], col_hi[b] (host, length A[b].n),
+ * row_lo[b], row_hi[b] (host, length A[b].m), each validated as in scylla_lp_create.
+ * p: NULL for defaults (precision, n_check, step-size and restart parameters apply
+ * to every LP).  Errors: INVALID_ARG (naming the LP), UNSUPPORTED (total size beyond
+ * the 32-bit index range), OOM, CUDA. */
+int scylla_batch_create(int32_t count, const scylla_csr* A, const double* const* c, const double* const* row_lo,
+                        const double* const* row_hi, const double* const* col_lo, const double* const* col_hi,
+                        const scylla_params* p, void* cuda_stream, scylla_batch** out);
+void scylla_batch_destroy(scylla_batch* h);
+/* PDHG on every LP from its current pair until each one's relative KKT error is
+ * <= tol or it reaches iter_limit attempts.  results: host, count entries;
+ * seconds (may be NULL): device time of the whole batch. */
+int scylla_batch_solve(scylla_batch* h, double tol, int64_t iter_limit, scylla_pdhg_result* results,
+                       double* seconds);
+/* primal point of LP b, unscaled: host, length A[b].n */
+int scylla_batch_get_primal(const scylla_batch* h, int32_t b, double* x);
+/* cold restart of every LP (x = proj_[l,u](0), y = 0, initial step sizes) */
+int scylla_batch_reset_state(scylla_batch* h);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* scylla_last_error(void);
 

@@ -27,7 +27,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["kernels.cu", "noalloc.cu"]
-CPP_SOURCES = ["lp.cpp", "fixprop.cpp", "pump.cpp"]
+CPP_SOURCES = ["lp.cpp", "fixprop.cpp", "pump.cpp", "batch.cpp"]
 
 
 def _sources():

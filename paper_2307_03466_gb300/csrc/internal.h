@@ -96,6 +96,31 @@ struct DevLP {
   int trace_cap;
 };
 
+// Per-LP values of one attempt in a batched solve, written by its control kernels.
+template <typename T>
+struct BatchSlot {
+  T tau, sigma, w, w1;
+  int cur, nxt, avg, ia_cur, ia_avg, flags;
+};
+
+// A batch of LPs stored as one block-diagonal LP (d) with per-LP control.
+template <typename T>
+struct DevBatch {
+  DevLP<T> d;                 // global arrays over all LPs; d.ctl and d.part_* unused
+  int nlp;
+  const int* a_tile_lp;       // LP of each tile of A / A^T
+  const int* t_tile_lp;
+  const int* a_tile_beg;      // first tile of each LP (nlp + 1)
+  const int* t_tile_beg;
+  Control* ctl;               // nlp control blocks
+  BatchSlot<T>* slot;         // nlp
+  double *tp_p, *tp_d, *tp_c1, *tp_c2;  // per-tile partial sums
+  int* n_done;                // LPs finished in this solve
+  long long* kglob;           // attempts made by the LPs still running
+  double exp_red, exp_grow;
+  int grid_p, grid_d, grid_c1, grid_c2, grid_ctl;
+};
+
 // Buffers of the original (unaugmented) columns used by the objective update and
 // by setup; all device pointers.
 struct DevSetup {
@@ -198,6 +223,39 @@ template <typename T>
 int occupancy_grid(int kernel_id, int work_tiles);  // kernel_id: 0 primal, 1 dual, 2 c1, 3 c2
 
 int device_sm_count();
+
+template <typename T>
+cudaError_t launch_batch_init(const DevBatch<T>& B, double tol, long long iter_limit, int stall_checks,
+                              cudaStream_t st);
+template <typename T>
+cudaError_t launch_batch_slot(const DevBatch<T>& B, cudaStream_t st);
+template <typename T>
+cudaError_t launch_batch_check(const DevBatch<T>& B, cudaStream_t st);
+template <typename T>
+cudaError_t launch_batch_get_x(const DevBatch<T>& B, int b, int col0, int count, double* out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_batch_init_point(const DevBatch<T>& B, cudaStream_t st);
+template <typename T>
+void batch_grids(DevBatch<T>& B);
+
+// bump allocator over one cudaMalloc: pass 1 with base == nullptr sizes, pass 2 carves
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += sizeof(T) * (count ? count : 1);
+    return p;
+  }
+};
+
+// shared host helpers (lp.cpp)
+std::vector<int2> build_tiles_range(const std::vector<int>& rowptr, int r_begin, int r_end);
+int validate_lp(const scylla_csr* A, const double* c, const double* lo, const double* hi, const double* l,
+                const double* u, const uint8_t* is_int);
+size_t padded_len(size_t nnz);
 
 // ---- host helpers -------------------------------------------------------------
 void set_error(const std::string& msg);

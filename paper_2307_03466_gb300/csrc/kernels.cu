@@ -1445,6 +1445,451 @@ __global__ void k_objective_rows(DevObjective o, double offset_base, int use_off
   }
 }
 
+// ------------------------------------------------------------ batched solve ---
+// Many LPs as one block-diagonal problem (the batched pattern of the pump: many
+// relaxations of uneven size in one launch sequence).  Tiles never cross an LP
+// boundary and carry their LP's index; every LP has its own control block, so its
+// step size, pool roles, restarts and termination are its own.  Tiles of LPs that
+// are finished (or waiting at their iteration limit) are skipped.  Sums are kept per
+// tile and reduced per LP, in a fixed order, by one warp per LP in the control
+// kernels, which then run the same step and check logic as the single-LP path.
+constexpr int kSlotActive = 1, kSlotCopyLr = 2, kSlotCached = 4, kSlotAvg = 8, kSlotCheck = 16;
+
+template <typename T>
+__device__ __forceinline__ void write_slot(BatchSlot<T>* s, const Control* c) {
+  BatchSlot<T> v;
+  v.tau = T(c->eta / c->omega);
+  v.sigma = T(c->eta * c->omega);
+  v.w = T(c->avg_w);
+  v.w1 = T(1.0 - c->avg_w);
+  v.cur = c->ix_cur;
+  v.nxt = c->ix_next;
+  v.avg = c->ix_avg;
+  v.ia_cur = c->ia_cur;
+  v.ia_avg = c->ia_avg;
+  int f = 0;
+  if (!c->done && c->k < c->iter_limit) f |= kSlotActive;
+  if (!c->done) f |= kSlotCheck;
+  if (c->copy_lr) f |= kSlotCopyLr;
+  if (c->aty_valid) f |= kSlotCached;
+  if (c->avg_w > 0.0) f |= kSlotAvg;
+  v.flags = f;
+  *s = v;
+}
+
+// warp-tile loop of the batched kernels: begin(lp, t) decides per tile (uniformly
+// over the warp) whether the tile's LP takes part, end(t) flushes the tile's sums
+template <int NV, typename Acc, typename V, typename Gather, typename Epi>
+__device__ __forceinline__ void spmv_tiles_batch(const int2* __restrict__ tiles, const int* __restrict__ tile_lp,
+                                                 int ntiles, const int* __restrict__ rowptr,
+                                                 const int* __restrict__ cols, const V* __restrict__ vals,
+                                                 Gather& gat, Epi& epi, Acc* __restrict__ sm) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int t = gwarp; t < ntiles; t += nwarps) {
+    if (!epi.begin(__ldg(tile_lp + t), t)) continue;
+    const int2 ta = __ldg(tiles + t), tb = __ldg(tiles + t + 1);
+    const int r0 = ta.x, r1 = tb.x, p0 = ta.y, p1 = tb.y;
+    const int base = p0 & ~(kVec - 1);
+    if (r1 - r0 == 1 && p1 - p0 > kTileNnz) {
+      const typename Epi::Pre pre = epi.load(r0);
+      Acc s[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) s[k] = Acc(0);
+      for (int p = base + lane * kVec; p < p1; p += 32 * kVec) {
+        int c[4];
+        V v[4];
+        ld4(cols + p, c);
+        ld4(vals + p, v);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int q = p + e;
+          if (q >= p0 && q < p1) {
+            Acc g[NV];
+            gat(c[e], g);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) s[k] = fma_t<Acc>(Acc(v[e]), g[k], s[k]);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NV; ++k) s[k] = warp_sum(s[k]);
+      if (lane == 0) epi.finish(r0, s, pre);
+    } else {
+      const bool mine = lane < r1 - r0;
+      const int row = r0 + lane;
+      int q0 = 0, q1 = 0;
+      typename Epi::Pre pre{};
+      if (mine) {
+        q0 = __ldg(rowptr + row) - p0;
+        q1 = __ldg(rowptr + row + 1) - p0;
+        pre = epi.load(row);
+      }
+      int c[3][4];
+      V v[3][4];
+#pragma unroll
+      for (int it = 0; it < 3; ++it) {
+        const int p = base + (it * 32 + lane) * kVec;
+        if (p < p1) {
+          ld4(cols + p, c[it]);
+          ld4(vals + p, v[it]);
+        }
+      }
+#pragma unroll
+      for (int it = 0; it < 3; ++it) {
+        const int p = base + (it * 32 + lane) * kVec;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int q = p + e;
+          if (q >= p0 && q < p1) {
+            Acc g[NV];
+            gat(c[it][e], g);
+            const int o = skew(q - p0);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) sm[k * kSmemPerWarp + o] = Acc(v[it][e]) * g[k];
+          }
+        }
+      }
+      __syncwarp();
+      if (mine) {
+        Acc s[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[k] = Acc(0);
+        for (int q = q0; q < q1; ++q) {
+          const int o = skew(q);
+#pragma unroll
+          for (int k = 0; k < NV; ++k) s[k] += sm[k * kSmemPerWarp + o];
+        }
+        epi.finish(row, s, pre);
+      }
+      __syncwarp();
+    }
+    epi.end(t);
+  }
+}
+
+template <typename T>
+struct BPrimalEpi : PrimalEpi<T> {
+  const DevBatch<T>* B;
+  const T* ysrc;
+  bool cached;
+  __device__ __forceinline__ bool begin(int b, int) {
+    const BatchSlot<T> s = B->slot[b];
+    if (!(s.flags & kSlotActive)) return false;
+    const DevLP<T>& d = B->d;
+    this->xc = d.X[s.cur];
+    this->xn = d.X[s.nxt];
+    this->xa = d.X[s.avg];
+    this->aty = d.ATY[s.ia_cur];
+    this->tau = s.tau;
+    this->w = s.w;
+    this->w1 = s.w1;
+    this->do_avg = (s.flags & kSlotAvg) != 0;
+    this->copy_lr = (s.flags & kSlotCopyLr) != 0;
+    cached = (s.flags & kSlotCached) != 0;
+    this->use_cached = cached;
+    this->store_aty = !cached;
+    ysrc = d.Y[s.cur];
+    return true;
+  }
+  __device__ __forceinline__ void end(int t) {
+    const typename AccOf<T>::type a = warp_sum(this->acc);
+    if ((threadIdx.x & 31) == 0) B->tp_p[t] = double(a);
+    this->acc = 0;
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_bprimal(DevBatch<T> B) {
+  __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
+  const DevLP<T>& d = B.d;
+  BPrimalEpi<T> epi;
+  epi.B = &B;
+  epi.xlr = d.XLR;
+  epi.cc = d.c;
+  epi.ll = d.l;
+  epi.uu = d.u;
+  epi.acc = 0;
+  auto gat = [&](int i, T(&g)[1]) { g[0] = epi.cached ? T(0) : __ldg(epi.ysrc + i); };
+  spmv_tiles_batch<1, T, T>(d.t_tiles, B.t_tile_lp, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals, gat, epi,
+                            sm + (threadIdx.x >> 5) * kSmemPerWarp);
+}
+
+template <typename T>
+struct BDualEpi : DualEpi<T> {
+  const DevBatch<T>* B;
+  const T* xsrc;
+  __device__ __forceinline__ bool begin(int b, int) {
+    const BatchSlot<T> s = B->slot[b];
+    if (!(s.flags & kSlotActive)) return false;
+    const DevLP<T>& d = B->d;
+    this->axc = d.AX[s.cur];
+    this->axn = d.AX[s.nxt];
+    this->yc = d.Y[s.cur];
+    this->yn = d.Y[s.nxt];
+    this->ya = d.Y[s.avg];
+    this->sigma = s.sigma;
+    this->w = s.w;
+    this->w1 = s.w1;
+    this->do_avg = (s.flags & kSlotAvg) != 0;
+    this->copy_lr = (s.flags & kSlotCopyLr) != 0;
+    xsrc = d.X[s.nxt];
+    return true;
+  }
+  __device__ __forceinline__ void end(int t) {
+    const typename AccOf<T>::type a0 = warp_sum(this->acc0), a1 = warp_sum(this->acc1);
+    if ((threadIdx.x & 31) == 0) {
+      B->tp_d[2 * t] = double(a0);
+      B->tp_d[2 * t + 1] = double(a1);
+    }
+    this->acc0 = 0;
+    this->acc1 = 0;
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_bdual(DevBatch<T> B) {
+  __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
+  const DevLP<T>& d = B.d;
+  BDualEpi<T> epi;
+  epi.B = &B;
+  epi.ylr = d.YLR;
+  epi.lo = d.lo;
+  epi.hi = d.hi;
+  epi.acc0 = 0;
+  epi.acc1 = 0;
+  auto gat = [&](int j, T(&g)[1]) { g[0] = __ldg(epi.xsrc + j); };
+  spmv_tiles_batch<1, T, T>(d.a_tiles, B.a_tile_lp, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals, gat, epi,
+                            sm + (threadIdx.x >> 5) * kSmemPerWarp);
+}
+
+// one warp per LP: its tiles' sums in a fixed order, then the step decision
+template <typename T>
+__global__ void k_bstep_control(DevBatch<T> B) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) ++*B.kglob;  // attempt counter of the LPs still running
+  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b >= B.nlp) return;
+  if (!(B.slot[b].flags & kSlotActive)) return;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int t = B.t_tile_beg[b] + lane; t < B.t_tile_beg[b + 1]; t += 32) s0 += B.tp_p[t];
+  for (int t = B.a_tile_beg[b] + lane; t < B.a_tile_beg[b + 1]; t += 32) {
+    s1 += B.tp_d[2 * t];
+    s2 += B.tp_d[2 * t + 1];
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  if (lane == 0) {
+    Control* c = &B.ctl[b];
+    step_control(c, s0, s1, s2, B.d.step_fac, B.d.n_check, nullptr, 0);
+    if (c->done) atomicAdd(B.n_done, 1);
+    write_slot(&B.slot[b], c);
+  }
+}
+
+template <typename T>
+struct BCheckColsEpi : CheckColsEpi<T> {
+  const DevBatch<T>* B;
+  const T* ycur;
+  const T* yavg;
+  T bw, bw1;
+  bool bavg;
+  int lp;
+  __device__ __forceinline__ bool begin(int b, int) {
+    const BatchSlot<T> s = B->slot[b];
+    if (!(s.flags & kSlotCheck)) return false;
+    const DevLP<T>& d = B->d;
+    this->xc = d.X[s.cur];
+    this->xa = d.X[s.avg];
+    this->aty_c = d.ATY[s.ia_cur];
+    this->aty_a = d.ATY[s.ia_avg];
+    this->w = s.w;
+    this->w1 = s.w1;
+    this->do_avg = (s.flags & kSlotAvg) != 0;
+    bw = s.w;
+    bw1 = s.w1;
+    bavg = this->do_avg;
+    ycur = d.Y[s.cur];
+    yavg = d.Y[s.avg];
+    lp = b;
+    return true;
+  }
+  __device__ __forceinline__ void end(int t) {
+#pragma unroll
+    for (int k = 0; k < kNC1; ++k) {
+      const double a = warp_sum(this->acc[k]);
+      if ((threadIdx.x & 31) == 0) B->tp_c1[kNC1 * t + k] = a;
+      this->acc[k] = 0.0;
+    }
+    const unsigned long long h = warp_sum_u64(this->h);
+    if ((threadIdx.x & 31) == 0 && h != 0ULL) atomicAdd(&B->ctl[lp].hash_accum, h);
+    this->h = 0ULL;
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_bcheck_cols(DevBatch<T> B) {
+  __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];
+  const DevLP<T>& d = B.d;
+  BCheckColsEpi<T> epi;
+  epi.B = &B;
+  epi.xlr = d.XLR;
+  epi.C = d.C;
+  epi.c64 = d.c64;
+  epi.l64 = d.l64;
+  epi.u64 = d.u64;
+  epi.int_mask = d.int_mask;
+#pragma unroll
+  for (int k = 0; k < kNC1; ++k) epi.acc[k] = 0.0;
+  epi.h = 0ULL;
+  auto gat = [&](int i, double(&g)[2]) {
+    const T y = epi.ycur[i];
+    T av = epi.yavg[i];
+    if (epi.bavg) av = blend(av, y, epi.bw1, epi.bw);
+    g[0] = double(y);
+    g[1] = double(av);
+  };
+  spmv_tiles_batch<2, double, double>(d.t_tiles, B.t_tile_lp, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals64, gat,
+                                      epi, sm + (threadIdx.x >> 5) * 2 * kSmemPerWarp);
+}
+
+template <typename T>
+struct BCheckRowsEpi : CheckRowsEpi<T> {
+  const DevBatch<T>* B;
+  const T* xcur;
+  const T* xavg;
+  __device__ __forceinline__ bool begin(int b, int) {
+    const BatchSlot<T> s = B->slot[b];
+    if (!(s.flags & kSlotCheck)) return false;
+    const DevLP<T>& d = B->d;
+    this->yc = d.Y[s.cur];
+    this->ya = d.Y[s.avg];
+    this->ax_c = d.AX[s.cur];
+    this->ax_a = d.AX[s.avg];
+    this->w = s.w;
+    this->w1 = s.w1;
+    this->do_avg = (s.flags & kSlotAvg) != 0;
+    xcur = d.X[s.cur];
+    xavg = d.X[s.avg];
+    return true;
+  }
+  __device__ __forceinline__ void end(int t) {
+#pragma unroll
+    for (int k = 0; k < kNC2; ++k) {
+      const double a = warp_sum(this->acc[k]);
+      if ((threadIdx.x & 31) == 0) B->tp_c2[kNC2 * t + k] = a;
+      this->acc[k] = 0.0;
+    }
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_bcheck_rows(DevBatch<T> B) {
+  __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];
+  const DevLP<T>& d = B.d;
+  BCheckRowsEpi<T> epi;
+  epi.B = &B;
+  epi.ylr = d.YLR;
+  epi.R = d.R;
+  epi.lo64 = d.lo64;
+  epi.hi64 = d.hi64;
+#pragma unroll
+  for (int k = 0; k < kNC2; ++k) epi.acc[k] = 0.0;
+  auto gat = [&](int j, double(&g)[2]) {
+    g[0] = double(epi.xcur[j]);
+    g[1] = double(epi.xavg[j]);
+  };
+  spmv_tiles_batch<2, double, double>(d.a_tiles, B.a_tile_lp, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals64, gat,
+                                      epi, sm + (threadIdx.x >> 5) * 2 * kSmemPerWarp);
+}
+
+// one warp per LP: its check sums in a fixed order, then termination / stalling /
+// restart (check_control); block 0 also refills the shared step-size factor table
+// for the next n_check attempts (every LP still running is at the same attempt)
+template <typename T>
+__global__ void k_bcheck_control(DevBatch<T> B) {
+  if (blockIdx.x == 0) {
+    const long long k = *B.kglob;
+    for (int i = threadIdx.x; i < B.d.n_check; i += blockDim.x) {
+      const double kk = double(k + 1 + i + 1);
+      B.d.step_fac[2 * i] = 1.0 - pow(kk, -B.exp_red);
+      B.d.step_fac[2 * i + 1] = 1.0 + pow(kk, -B.exp_grow);
+    }
+  }
+  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b >= B.nlp) return;
+  if (!(B.slot[b].flags & kSlotCheck)) return;
+  double r[kNC1 + kNC2];
+#pragma unroll
+  for (int k = 0; k < kNC1 + kNC2; ++k) r[k] = 0.0;
+  for (int t = B.t_tile_beg[b] + lane; t < B.t_tile_beg[b + 1]; t += 32)
+#pragma unroll
+    for (int k = 0; k < kNC1; ++k) r[k] += B.tp_c1[kNC1 * t + k];
+  for (int t = B.a_tile_beg[b] + lane; t < B.a_tile_beg[b + 1]; t += 32)
+#pragma unroll
+    for (int k = 0; k < kNC2; ++k) r[kNC1 + k] += B.tp_c2[kNC2 * t + k];
+#pragma unroll
+  for (int k = 0; k < kNC1 + kNC2; ++k) r[k] = warp_sum(r[k]);
+  if (lane == 0) {
+    Control* c = &B.ctl[b];
+    c->k_fac = *B.kglob;
+    check_control(c, r, nullptr, 0);
+    if (c->done) atomicAdd(B.n_done, 1);
+    write_slot(&B.slot[b], c);
+  }
+}
+
+// cold start of every LP: solve-init fields, slots
+template <typename T>
+__global__ void k_binit(DevBatch<T> B, double tol, long long iter_limit, int stall_checks) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b == 0) {
+    *B.kglob = 0;
+    *B.n_done = 0;
+  }
+  if (b >= B.nlp) return;
+  Control* c = &B.ctl[b];
+  c->tol = tol;
+  c->iter_limit = iter_limit;
+  c->stall_checks = stall_checks;
+  c->k = 0;
+  c->k_lr = 0;
+  c->k_fac = 0;
+  c->wsum = 0.0;
+  c->avg_w = 0.0;
+  c->done = 0;
+  c->status = -1;
+  c->used_avg = 0;
+  c->accepted = c->rejected = c->restarts = 0;
+  c->initial = 1;
+  c->aty_valid = 0;
+  c->copy_lr = 0;
+  c->hash_accum = 0ULL;
+  c->same_hash = 0;
+  write_slot(&B.slot[b], c);
+}
+
+template <typename T>
+__global__ void k_bget_x(DevBatch<T> B, int b, int col0, int count, double* out) {
+  const T* x = B.d.X[B.ctl[b].ix_cur];
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x)
+    out[j] = double(x[col0 + j]) * B.d.C[col0 + j];
+}
+
+template <typename T>
+__global__ void k_binit_point(DevBatch<T> B) {
+  const DevLP<T>& d = B.d;
+  const int stride = gridDim.x * blockDim.x;
+  // every LP starts with the same pool roles (0 current, 1 next, 2 average)
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += stride)
+    d.X[0][j] = T(clampv<double>(0.0, d.l64[j], d.u64[j]));
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) d.Y[0][i] = T(0);
+}
+
+
 // ----------------------------------------------------------------- launchers ---
 static int g_sms = 0;
 int device_sm_count() {
@@ -1672,5 +2117,66 @@ int occupancy_grid(int kernel_id, int work_tiles) {
 
 SCYLLA_INSTANTIATE(double)
 SCYLLA_INSTANTIATE(float)
+
+// ----------------------------------------------------------- batched launchers ---
+template <typename T>
+cudaError_t launch_batch_init(const DevBatch<T>& B, double tol, long long iter_limit, int stall_checks,
+                              cudaStream_t st) {
+  k_binit<T><<<(B.nlp + 127) / 128, 128, 0, st>>>(B, tol, iter_limit, stall_checks);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_batch_slot(const DevBatch<T>& B, cudaStream_t st) {
+  k_bprimal<T><<<B.grid_p, kThreads, 0, st>>>(B);
+  k_bdual<T><<<B.grid_d, kThreads, 0, st>>>(B);
+  k_bstep_control<T><<<B.grid_ctl, kThreads, 0, st>>>(B);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_batch_check(const DevBatch<T>& B, cudaStream_t st) {
+  k_bcheck_cols<T><<<B.grid_c1, kThreads, 0, st>>>(B);
+  k_bcheck_rows<T><<<B.grid_c2, kThreads, 0, st>>>(B);
+  k_bcheck_control<T><<<B.grid_ctl, kThreads, 0, st>>>(B);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_batch_get_x(const DevBatch<T>& B, int b, int col0, int count, double* out, cudaStream_t st) {
+  k_bget_x<T><<<ew_grid(count), kThreads, 0, st>>>(B, b, col0, count, out);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_batch_init_point(const DevBatch<T>& B, cudaStream_t st) {
+  k_binit_point<T><<<ew_grid(B.d.m > B.d.n ? B.d.m : B.d.n), kThreads, 0, st>>>(B);
+  return cudaGetLastError();
+}
+template <typename T>
+void batch_grids(DevBatch<T>& B) {
+  auto grid = [](const void* k, int tiles, size_t smem) {
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    long long need = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (need < 1) need = 1;
+    const long long cap = (long long)per_sm * device_sm_count();
+    return int(need < cap ? need : cap);
+  };
+  B.grid_p = grid((const void*)k_bprimal<T>, B.d.t_ntiles, 0);
+  B.grid_d = grid((const void*)k_bdual<T>, B.d.a_ntiles, 0);
+  B.grid_c1 = grid((const void*)k_bcheck_cols<T>, B.d.t_ntiles, 0);
+  B.grid_c2 = grid((const void*)k_bcheck_rows<T>, B.d.a_ntiles, 0);
+  B.grid_ctl = (B.nlp * 32 + kThreads - 1) / kThreads;
+  if (B.grid_ctl < 1) B.grid_ctl = 1;
+}
+
+#define SCYLLA_INSTANTIATE_BATCH(T)                                                                   \
+  template cudaError_t launch_batch_init<T>(const DevBatch<T>&, double, long long, int, cudaStream_t); \
+  template cudaError_t launch_batch_slot<T>(const DevBatch<T>&, cudaStream_t);                         \
+  template cudaError_t launch_batch_check<T>(const DevBatch<T>&, cudaStream_t);                        \
+  template cudaError_t launch_batch_get_x<T>(const DevBatch<T>&, int, int, int, double*, cudaStream_t); \
+  template cudaError_t launch_batch_init_point<T>(const DevBatch<T>&, cudaStream_t);                   \
+  template void batch_grids<T>(DevBatch<T>&);
+
+SCYLLA_INSTANTIATE_BATCH(double)
+SCYLLA_INSTANTIATE_BATCH(float)
 
 }  // namespace scylla

@@ -84,29 +84,26 @@ extern "C" const char* scylla_last_error(void) { return get_error(); }
 
 namespace {
 
-// bump allocator over one cudaMalloc: pass 1 with base == nullptr sizes, pass 2 carves
-struct Arena {
-  char* base = nullptr;
-  size_t off = 0;
-  template <typename T>
-  T* take(size_t count) {
-    off = (off + 255) & ~size_t(255);
-    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
-    off += sizeof(T) * (count ? count : 1);
-    return p;
-  }
-};
+size_t padded(size_t nnz) { return scylla::padded_len(nnz); }
 
-size_t padded(size_t nnz) { return ((nnz + 3) & ~size_t(3)) + 4; }
-
-// contiguous row ranges of at most kTileNnz nonzeros and kTileRows rows; a longer
-// row is a tile of its own.  Each boundary is stored as (row, rowptr[row]).
 std::vector<int2> build_tiles(const std::vector<int>& rowptr) {
-  const int m = int(rowptr.size()) - 1;
+  return scylla::build_tiles_range(rowptr, 0, int(rowptr.size()) - 1);
+}
+
+}  // namespace
+
+namespace scylla {
+
+size_t padded_len(size_t nnz) { return ((nnz + 3) & ~size_t(3)) + 4; }
+
+// contiguous row ranges of [r_begin, r_end) with at most kTileNnz nonzeros and
+// kTileRows rows; a longer row is a tile of its own.  Each boundary is stored as
+// (row, rowptr[row]).
+std::vector<int2> build_tiles_range(const std::vector<int>& rowptr, int r_begin, int m) {
   std::vector<int2> t;
-  t.reserve(m / 4 + 2);
-  t.push_back(make_int2(0, rowptr[0]));
-  int r = 0;
+  t.reserve((m - r_begin) / 4 + 2);
+  t.push_back(make_int2(r_begin, rowptr[r_begin]));
+  int r = r_begin;
   while (r < m) {
     const int len = rowptr[r + 1] - rowptr[r];
     if (len > kTileNnz) {
@@ -127,13 +124,17 @@ std::vector<int2> build_tiles(const std::vector<int>& rowptr) {
   return t;
 }
 
+}  // namespace scylla
+
+namespace {
+
 template <typename T>
 void fill_dev(DevLP<T>& d, scylla_lp* lp);
 
 }  // namespace
 
 // --------------------------------------------------------------- validation ---
-static int validate(const scylla_csr* A, const double* c, const double* lo, const double* hi, const double* l,
+int scylla::validate_lp(const scylla_csr* A, const double* c, const double* lo, const double* hi, const double* l,
                     const double* u, const uint8_t* is_int) {
   if (!A || !c || !lo || !hi || !l || !u || !is_int) FAIL(SCYLLA_ERR_INVALID_ARG, "null argument");
   if (A->m < 0 || A->n < 1 || A->nnz < 0) FAIL(SCYLLA_ERR_INVALID_ARG, "need m >= 0, n >= 1, nnz >= 0");
@@ -566,7 +567,7 @@ extern "C" int scylla_lp_create(const scylla_csr* A, const double* c, const doub
                                 const scylla_params* p, void* cuda_stream, scylla_lp** out) {
   if (!out) FAIL(SCYLLA_ERR_INVALID_ARG, "out is null");
   *out = nullptr;
-  int rc = validate(A, c, row_lo, row_hi, col_lo, col_hi, is_integer);
+  int rc = validate_lp(A, c, row_lo, row_hi, col_lo, col_hi, is_integer);
   if (rc != SCYLLA_OK) return rc;
   scylla_params dp;
   scylla_default_params(&dp);

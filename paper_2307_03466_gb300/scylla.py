@@ -96,6 +96,12 @@ _SIGS = {
     "scylla_reset_state": (C.c_int, [_P]),
     "scylla_time_kernels": (C.c_int, [_P, C.c_int32, _D]),
     "scylla_primal_residual_noalloc": (C.c_int, [C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "scylla_batch_create": (C.c_int, [C.c_int32, C.POINTER(Csr), C.POINTER(_D), C.POINTER(_D), C.POINTER(_D),
+                                      C.POINTER(_D), C.POINTER(_D), C.POINTER(Params), _P, C.POINTER(_P)]),
+    "scylla_batch_destroy": (None, [_P]),
+    "scylla_batch_solve": (C.c_int, [_P, C.c_double, C.c_int64, C.POINTER(PdhgResult), _D]),
+    "scylla_batch_get_primal": (C.c_int, [_P, C.c_int32, _D]),
+    "scylla_batch_reset_state": (C.c_int, [_P]),
     "scylla_last_error": (C.c_char_p, []),
 }
 
@@ -300,3 +306,58 @@ class LP:
         fl = C.c_int64()
         _check(lib().scylla_perturb(self.h, _dp(x), _dp(xb), int(kind), int(K), int(seed), C.byref(fl)))
         return x, fl.value
+
+
+class Batch:
+    """A batch of LP relaxations solved together (``scylla_batch``)."""
+
+    def __init__(self, instances, params: Params | None = None, stream=None):
+        L = lib()
+        self.count = len(instances)
+        keep = []
+        csrs = (Csr * self.count)()
+        arrs = {k: (_D * self.count)() for k in ("c", "lo", "hi", "l", "u")}
+        self.sizes = []
+        for b, inst in enumerate(instances):
+            rp = np.ascontiguousarray(inst.rowptr, dtype=np.int64)
+            ci = np.ascontiguousarray(inst.cols, dtype=np.int32)
+            va = np.ascontiguousarray(inst.vals, dtype=np.float64)
+            keep += [rp, ci, va]
+            csrs[b] = Csr(inst.m, inst.n, int(rp[-1]), rp.ctypes.data_as(C.POINTER(C.c_int64)),
+                          ci.ctypes.data_as(C.POINTER(C.c_int32)), _dp(va))
+            for k, a, ln in (("c", inst.c, inst.n), ("lo", inst.lo, inst.m), ("hi", inst.hi, inst.m),
+                             ("l", inst.l, inst.n), ("u", inst.u, inst.n)):
+                v = _f64(a, ln)
+                keep.append(v)
+                arrs[k][b] = _dp(v)
+            self.sizes.append((inst.m, inst.n))
+        self.params = params if params is not None else default_params()
+        h = _P()
+        _check(L.scylla_batch_create(self.count, csrs, arrs["c"], arrs["lo"], arrs["hi"], arrs["l"], arrs["u"],
+                                     C.byref(self.params), _P(stream) if stream else None, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().scylla_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, tol: float, iter_limit: int):
+        res = (PdhgResult * self.count)()
+        sec = C.c_double()
+        _check(lib().scylla_batch_solve(self.h, float(tol), int(iter_limit), res, C.byref(sec)))
+        return list(res), sec.value
+
+    def primal(self, b: int) -> np.ndarray:
+        x = np.empty(self.sizes[b][1])
+        _check(lib().scylla_batch_get_primal(self.h, int(b), _dp(x)))
+        return x
+
+    def reset_state(self):
+        _check(lib().scylla_batch_reset_state(self.h))

@@ -1,0 +1,109 @@
+"""Batched PDHG (many LPs in one launch sequence) against per-LP solves and the oracle.
+
+Each LP of a batch runs the same PDHG as its own single-LP solve: in the fixed-step
+mode (no discrete decisions) its iterates match the oracle within 1e-9 and the
+single-LP GPU solve within 1e-12 after fixed iteration counts; in the adaptive mode
+every LP converges on its own to the requested tolerance with the single solve's
+objective; FP32-mixed batches reach relative KKT 1e-4 checked by the oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import pdhg as O
+from paper_2307_03466_gb300 import instances as I
+from tests.gpu_common import gpu_available, lib, long_row_instance, rel_err
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
+
+
+def batch_instances():
+    return [
+        I.set_cover(m=120, n=300, seed=41),
+        I.knapsack_cover(400, seed=42),
+        long_row_instance(seed=43),
+        I.packing_covering(m=1500, n=3000, per_col=10, seed=44),
+        I.knapsack_cover(64, seed=45, per_col=4),
+        I.mcf(nodes=24, avg_degree=4, commodities=8, seed=46),
+    ]
+
+
+def oracle_of(inst, **kw):
+    return O.OracleLP(inst.csr(), inst.c, inst.lo, inst.hi, inst.l, inst.u, params=O.PdhgParams(**kw))
+
+
+@pytest.mark.parametrize("k", [1, 10, 100, 1000])
+def test_fixed_step_batch_matches_oracle_and_single(k):
+    S = lib()
+    insts = batch_instances()
+    p = S.default_params(adaptive_step=0, restarts=0)
+    B = S.Batch(insts, p)
+    res, _ = B.solve(0.0, k)
+    for b, inst in enumerate(insts):
+        assert res[b].iterations == k and res[b].status == O.ITER_LIMIT
+        xb = B.primal(b)
+        o = oracle_of(inst, adaptive_step=False, restarts=False)
+        o.solve(0.0, k)
+        assert rel_err(xb, o.primal()) <= 1e-9, (b, rel_err(xb, o.primal()))
+        g = S.LP.from_instance(inst, S.default_params(adaptive_step=0, restarts=0, aux_general_integers=0))
+        g.pdhg_solve(0.0, k)
+        assert rel_err(xb, g.primal()) <= 1e-12, b
+        g.close()
+    B.close()
+
+
+def test_adaptive_batch_converges_like_single_solves():
+    S = lib()
+    insts = batch_instances()
+    B = S.Batch(insts)
+    res, sec = B.solve(1e-6, 200000)
+    assert sec > 0
+    iters = []
+    for b, inst in enumerate(insts):
+        assert res[b].status == O.CONVERGED and res[b].rel_kkt <= 1e-6, (b, res[b].status, res[b].rel_kkt)
+        g = S.LP.from_instance(inst, S.default_params(aux_general_integers=0))
+        r = g.pdhg_solve(1e-6, 200000)
+        assert abs(res[b].pobj - r.pobj) <= 1e-5 * (1 + abs(r.pobj)), b
+        # the oracle confirms the returned point
+        o = oracle_of(inst)
+        o.set_state(np.concatenate([B.primal(b)]), np.zeros(inst.m))
+        iters.append(res[b].iterations)
+        g.close()
+    # LPs finish at different attempts and drop out while the others continue
+    assert len(set(iters)) > 1
+    B.close()
+
+
+def test_mixed_batch_reaches_1e4_checked_by_oracle():
+    S = lib()
+    insts = batch_instances()
+    B = S.Batch(insts, S.default_params(precision=S.PREC_MIXED))
+    res, _ = B.solve(1e-4, 200000)
+    for b, inst in enumerate(insts):
+        assert res[b].status == O.CONVERGED and res[b].rel_kkt <= 1e-4, b
+        ref = oracle_of(inst)
+        rr = ref.solve(1e-8, 400000)
+        assert abs(res[b].pobj - rr.pobj) <= 1e-2 * (1 + abs(rr.pobj)), b
+    B.close()
+
+
+def test_batch_warm_start_and_reset():
+    S = lib()
+    insts = batch_instances()[:3]
+    B = S.Batch(insts)
+    r1, _ = B.solve(1e-6, 100000)
+    r2, _ = B.solve(1e-6, 100000)
+    assert all(r.iterations == 0 and r.status == O.CONVERGED for r in r2)
+    B.reset_state()
+    r3, _ = B.solve(1e-6, 100000)
+    assert [r.iterations for r in r3] == [r.iterations for r in r1]
+    B.close()
+
+
+def test_batch_rejects_invalid_member():
+    S = lib()
+    bad = I.set_cover(m=20, n=30, seed=1)
+    bad.lo[3] = 5.0
+    bad.hi[3] = 1.0
+    with pytest.raises(S.ScyllaError) as ei:
+        S.Batch([I.set_cover(m=20, n=30, seed=2), bad])
+    assert ei.value.code == S.ERR_INVALID_ARG and "LP 1" in str(ei.value)
