@@ -470,6 +470,17 @@ __device__ __forceinline__ void pdl_enter() {
   cudaTriggerProgrammaticLaunchCompletion();
 }
 
+// resident blocks per SM the per-attempt kernels are compiled for: FP32 SpMVs are
+// bound by the bytes in flight (more warps), FP64 ones by the FP64 pipe
+template <typename T>
+struct MinBlocks {
+  static constexpr int value = 4;
+};
+template <>
+struct MinBlocks<double> {
+  static constexpr int value = 2;
+};
+
 // per-thread accumulator type of the bulk kernels
 template <typename T>
 struct AccOf {
@@ -662,7 +673,7 @@ __device__ __forceinline__ void dual_phase(const DevLP<T>& d, const SlotView& v,
 // wait for the predecessor kernel (programmatic dependent launch), so that load
 // overlaps the predecessor's tail.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_primal(DevLP<T> d) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_primal(DevLP<T> d) {
   Control* ctl = d.ctl;
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
   PrimalEpi<T> epi;
@@ -696,7 +707,7 @@ __global__ void __launch_bounds__(kThreads) k_primal(DevLP<T> d) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_dual(DevLP<T> d) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_dual(DevLP<T> d) {
   Control* ctl = d.ctl;
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
   DualEpi<T> epi;
@@ -1601,7 +1612,7 @@ struct BPrimalEpi : PrimalEpi<T> {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_bprimal(DevBatch<T> B) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_bprimal(DevBatch<T> B) {
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
   const DevLP<T>& d = B.d;
   BPrimalEpi<T> epi;
@@ -1649,7 +1660,7 @@ struct BDualEpi : DualEpi<T> {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_bdual(DevBatch<T> B) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_bdual(DevBatch<T> B) {
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
   const DevLP<T>& d = B.d;
   BDualEpi<T> epi;
