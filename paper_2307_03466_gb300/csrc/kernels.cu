@@ -279,117 +279,6 @@ __device__ __forceinline__ void spmv_tiles(const int2* __restrict__ tiles, int n
   }
 }
 
-// Same warp-tile gather, for kernels launched with programmatic dependent launch:
-// the immutable part of a warp's next tile (tile bounds, row pointers, column
-// indices, values) is loaded first; for the first tile this happens before
-// prologue(), which waits for the predecessor kernel and sets up the gather and
-// the epilogue from the control block.  prologue() returning false means there is
-// nothing to do (the solve is over); every thread calls it exactly once.
-template <int NV, typename Acc, typename V, typename Gather, typename Epi, typename Prologue>
-__device__ __forceinline__ bool spmv_tiles_pf(const int2* __restrict__ tiles, int ntiles,
-                                              const int* __restrict__ rowptr, const int* __restrict__ cols,
-                                              const V* __restrict__ vals, Gather& gat, Epi& epi,
-                                              Acc* __restrict__ sm, Prologue& prologue) {
-  const int lane = threadIdx.x & 31;
-  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  int r0 = 0, r1 = 0, p0 = 0, p1 = 0, q0 = 0, q1 = 0;
-  bool multi = false;
-  int c[3][4];
-  V v[3][4];
-  auto fetch = [&](int t) {
-    const int2 ta = __ldg(tiles + t), tb = __ldg(tiles + t + 1);
-    r0 = ta.x;
-    r1 = tb.x;
-    p0 = ta.y;
-    p1 = tb.y;
-    multi = !(r1 - r0 == 1 && p1 - p0 > kTileNnz);
-    if (multi) {
-      if (lane < r1 - r0) {
-        q0 = __ldg(rowptr + r0 + lane) - p0;
-        q1 = __ldg(rowptr + r0 + lane + 1) - p0;
-      }
-      const int base = p0 & ~(kVec - 1);
-#pragma unroll
-      for (int it = 0; it < 3; ++it) {
-        const int p = base + (it * 32 + lane) * kVec;
-        if (p < p1) {
-          ld4(cols + p, c[it]);
-          ld4(vals + p, v[it]);
-        }
-      }
-    }
-  };
-  int t = gwarp;
-  if (t < ntiles) fetch(t);
-  if (!prologue()) return false;
-  for (; t < ntiles;) {
-    if (!multi) {
-      const typename Epi::Pre pre = epi.load(r0);
-      const int base = p0 & ~(kVec - 1);
-      Acc s[NV];
-#pragma unroll
-      for (int k = 0; k < NV; ++k) s[k] = Acc(0);
-      for (int p = base + lane * kVec; p < p1; p += 32 * kVec) {
-        int cc[4];
-        V vv[4];
-        ld4(cols + p, cc);
-        ld4(vals + p, vv);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int q = p + e;
-          if (q >= p0 && q < p1) {
-            Acc g[NV];
-            gat(cc[e], g);
-#pragma unroll
-            for (int k = 0; k < NV; ++k) s[k] = fma_t<Acc>(Acc(vv[e]), g[k], s[k]);
-          }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < NV; ++k) s[k] = warp_sum(s[k]);
-      if (lane == 0) epi.finish(r0, s, pre);
-    } else {
-      const bool mine = lane < r1 - r0;
-      const int row = r0 + lane;
-      typename Epi::Pre pre{};
-      if (mine) pre = epi.load(row);
-      const int base = p0 & ~(kVec - 1);
-#pragma unroll
-      for (int it = 0; it < 3; ++it) {
-        const int p = base + (it * 32 + lane) * kVec;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int q = p + e;
-          if (q >= p0 && q < p1) {
-            Acc g[NV];
-            gat(c[it][e], g);
-            const int o = skew(q - p0);
-#pragma unroll
-            for (int k = 0; k < NV; ++k) sm[k * kSmemPerWarp + o] = Acc(v[it][e]) * g[k];
-          }
-        }
-      }
-      __syncwarp();
-      if (mine) {
-        Acc s[NV];
-#pragma unroll
-        for (int k = 0; k < NV; ++k) s[k] = Acc(0);
-        for (int q = q0; q < q1; ++q) {
-          const int o = skew(q);
-#pragma unroll
-          for (int k = 0; k < NV; ++k) s[k] += sm[k * kSmemPerWarp + o];
-        }
-        epi.finish(row, s, pre);
-      }
-      __syncwarp();
-    }
-    t += nwarps;
-    if (t < ntiles) fetch(t);
-  }
-  return true;
-}
-
 // ------------------------------------------------------------- step control ---
 // Adaptive step (PDLP): eta_max = (omega ||dx||^2 + ||dy||^2 / omega) / (2 |dy.A dx|);
 // eta' = min((1 - (k+1)^-0.3) eta_max, (1 + (k+1)^-0.6) eta), k the 1-based attempt
@@ -669,63 +558,24 @@ __device__ __forceinline__ void dual_phase(const DevLP<T>& d, const SlotView& v,
   block_store_partials<kND>(acc, part);
 }
 
-// The per-attempt kernels load the immutable part of their first tile before they
-// wait for the predecessor kernel (programmatic dependent launch), so that load
-// overlaps the predecessor's tail.
+// The per-attempt kernels: with programmatic dependent launch they are resident
+// while their predecessor drains, and wait for it before touching any data.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_primal(DevLP<T> d) {
   Control* ctl = d.ctl;
+  pdl_enter();
+  if (ctl->done || ctl->k >= ctl->iter_limit) return;
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
-  PrimalEpi<T> epi;
-  const T* yc = nullptr;
-  bool cached = false;
-  auto prologue = [&]() -> bool {
-    pdl_enter();
-    if (ctl->done || ctl->k >= ctl->iter_limit) return false;
-    const SlotView v = make_view(ctl);
-    setup_primal(epi, d, v);
-    yc = d.Y[v.cur];
-    cached = v.aty_valid != 0;
-    epi.use_cached = cached;
-    return true;
-  };
-  if (!d.pdl && ctl->aty_valid) {
-    // a retry (rejected step, or the first attempt after a check): A^T y of the
-    // current y is cached, no gather
-    if (!prologue()) return;
-    tiles_rows<T>(d.t_tiles, d.t_ntiles, epi.aty, epi);
-  } else {
-    // with programmatic launch the retry is only known after the wait: the gather
-    // then reads nothing and the epilogue takes the cached A^T y
-    auto gat = [&](int i, T(&g)[1]) { g[0] = cached ? T(0) : __ldg(yc + i); };
-    if (!spmv_tiles_pf<1, T, T>(d.t_tiles, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals, gat, epi,
-                                sm + (threadIdx.x >> 5) * kSmemPerWarp, prologue))
-      return;
-  }
-  const typename AccOf<T>::type acc[kNP] = {epi.acc};
-  block_store_partials<kNP>(acc, d.part_p);
+  primal_phase<T, false>(d, make_view(ctl), sm, d.part_p);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_dual(DevLP<T> d) {
   Control* ctl = d.ctl;
+  pdl_enter();
+  if (ctl->done || ctl->k >= ctl->iter_limit) return;
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
-  DualEpi<T> epi;
-  const T* xn = nullptr;
-  auto prologue = [&]() -> bool {
-    pdl_enter();
-    if (ctl->done || ctl->k >= ctl->iter_limit) return false;
-    const SlotView v = make_view(ctl);
-    setup_dual(epi, d, v);
-    xn = d.X[v.nxt];
-    return true;
-  };
-  auto gat = [&](int j, T(&g)[1]) { g[0] = __ldg(xn + j); };
-  if (!spmv_tiles_pf<1, T, T>(d.a_tiles, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals, gat, epi,
-                              sm + (threadIdx.x >> 5) * kSmemPerWarp, prologue))
-    return;
-  const typename AccOf<T>::type acc[kND] = {epi.acc0, epi.acc1};
-  block_store_partials<kND>(acc, d.part_d);
+  dual_phase<T, false>(d, make_view(ctl), sm, d.part_d);
   if (!is_last_block(&ctl->cnt_dual)) return;
   __shared__ double red[kNP + kND];
   reduce_two<kNP, kND>(d.part_p, d.grid_p, d.part_d, d.grid_d, red);
