@@ -294,6 +294,33 @@ int scylla_batch_get_primal(const scylla_batch* h, int32_t b, double* x);
 /* cold restart of every LP (x = proj_[l,u](0), y = 0, initial step sizes) */
 int scylla_batch_reset_state(scylla_batch* h);
 
+/* ---- K-objective fan-out ---------------------------------------------------
+ * K pump objectives of one LP (Section 2.4: the objective update of round
+ * round_K around K different rounding targets) solved together as sparse-times-
+ * tall-skinny products, so A is read once per K objectives.  Every objective has
+ * its own step size, primal weight, restarts and termination and starts from the
+ * handle's current primal-dual pair (a warm start, Section 2.1). */
+typedef struct scylla_fanout scylla_fanout;
+
+/* lp: a handle without auxiliary columns (created with aux_general_integers = 0);
+ * it must outlive the fan-out, whose device data is its own except the shared
+ * matrices.  K: 1..64.  targets: host, K blocks of length n (targets[k*n + j]);
+ * integer entries integral within bounds.  Target k gives objective
+ * alpha^round_K s c + (1 - alpha^round_K) g_k with g_kj = +1 (target at l_j), -1
+ * (at u_j), 0 otherwise on integer columns.  Errors: INVALID_ARG, UNSUPPORTED
+ * (auxiliary columns present), OOM, CUDA. */
+int scylla_fanout_create(scylla_lp* lp, int32_t K, const double* targets, int32_t round_K, scylla_fanout** out);
+void scylla_fanout_destroy(scylla_fanout* f);
+/* PDHG for every objective until its relative KKT error is <= tol or it reaches
+ * iter_limit attempts.  results: host, K entries; seconds (may be NULL): device
+ * time of the whole fan-out. */
+int scylla_fanout_solve(scylla_fanout* f, double tol, int64_t iter_limit, scylla_pdhg_result* results,
+                        double* seconds);
+/* primal point of objective k, unscaled: host, length n */
+int scylla_fanout_get_primal(const scylla_fanout* f, int32_t k, double* x);
+/* every objective back to the handle's current pair, step size and primal weight */
+int scylla_fanout_reset_state(scylla_fanout* f);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* scylla_last_error(void);
 

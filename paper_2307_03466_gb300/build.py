@@ -26,13 +26,14 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["kernels.cu", "noalloc.cu"]
-CPP_SOURCES = ["lp.cpp", "fixprop.cpp", "pump.cpp", "batch.cpp"]
+CU_SOURCES = ["kernels.cu", "fanout.cu", "noalloc.cu"]
+CPP_SOURCES = ["lp.cpp", "fixprop.cpp", "pump.cpp", "batch.cpp", "fanout.cpp"]
 
 
 def _sources():
     return [os.path.join(CSRC, f) for f in CU_SOURCES + CPP_SOURCES] + \
-        [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "lp_handle.h"), os.path.join(INCLUDE, "scylla.h")]
+        [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "lp_handle.h"), os.path.join(CSRC, "device_common.cuh"),
+         os.path.join(INCLUDE, "scylla.h")]
 
 
 def _up_to_date() -> bool:

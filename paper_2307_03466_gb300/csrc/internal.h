@@ -121,6 +121,30 @@ struct DevBatch {
   int grid_p, grid_d, grid_c1, grid_c2, grid_ctl;
 };
 
+// K objectives of one LP solved together: K-wide vectors are row-major (n x K, m x K).
+template <typename T>
+struct DevFan {
+  DevLP<T> d;  // the base LP: matrices, bounds, scaling (its iterate pools unused)
+  int K;
+  T* X[3];
+  T* Y[3];
+  T* AX[3];
+  T* ATY[2];
+  T* XLR;
+  T* YLR;
+  const double* c_orig;                // unscaled base objective, n
+  const unsigned long long* lo_bits;   // bit k of column j: target k at l_j
+  const unsigned long long* up_bits;   // bit k of column j: target k at u_j
+  double t, om;                        // alpha^K s and 1 - alpha^K of the update
+  Control* ctl;                        // K control blocks
+  BatchSlot<T>* slot;                  // K
+  double *part_p, *part_d, *part_c1, *part_c2;  // [block][sum][objective]
+  int* n_done;
+  long long* kglob;
+  double exp_red, exp_grow;
+  int grid_p, grid_d, grid_c1, grid_c2;
+};
+
 // Buffers of the original (unaugmented) columns used by the objective update and
 // by setup; all device pointers.
 struct DevSetup {
@@ -250,6 +274,20 @@ struct Arena {
     return p;
   }
 };
+
+template <typename T>
+cudaError_t launch_fan_init(const DevFan<T>& F, double tol, long long iter_limit, int stall_checks, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fan_slot(const DevFan<T>& F, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fan_check(const DevFan<T>& F, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fan_seed(const DevFan<T>& F, const void* x0, const void* y0, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fan_get_x(const DevFan<T>& F, int k, double* out, cudaStream_t st);
+template <typename T>
+void fan_grids(DevFan<T>& F);
+constexpr int kFanMaxK = 64;
 
 // shared host helpers (lp.cpp)
 std::vector<int2> build_tiles_range(const std::vector<int>& rowptr, int r_begin, int r_end);

@@ -19,166 +19,10 @@
 #include <cmath>
 #include <cstdint>
 
+#include "device_common.cuh"
 #include "internal.h"
 
 namespace scylla {
-
-// ------------------------------------------------------------------ helpers ---
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ __forceinline__ void ld4(const int* p, int (&o)[4]) {
-  const int4 t = __ldg(reinterpret_cast<const int4*>(p));
-  o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
-}
-__device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
-  const float4 t = __ldg(reinterpret_cast<const float4*>(p));
-  o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
-}
-__device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
-  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
-  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
-}
-
-__device__ __forceinline__ int skew(int q) { return q + (q >> 5); }
-
-template <typename T>
-__device__ __forceinline__ T clampv(T v, T lo, T hi) {
-  v = v < lo ? lo : v;
-  return v > hi ? hi : v;
-}
-template <typename T>
-__device__ __forceinline__ T fma_t(T a, T b, T c);
-template <>
-__device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
-template <>
-__device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-
-// running average x_avg <- (1-w) x_avg + w x, in one fixed rounding sequence
-template <typename T>
-__device__ __forceinline__ T blend(T a, T x, T w1, T w) { return fma_t<T>(w1, a, w * x); }
-
-template <typename T>
-__device__ __forceinline__ T pos_inf();
-template <>
-__device__ __forceinline__ double pos_inf<double>() { return __longlong_as_double(0x7ff0000000000000ULL); }
-template <>
-__device__ __forceinline__ float pos_inf<float>() { return __int_as_float(0x7f800000); }
-
-// Dual step of Algorithm 1 for a row with bounds [lo, hi] (the proximal step of
-// the row-bound support function); lo = b, hi = +inf gives max(0, y + s (b - axt)).
-template <typename T>
-__device__ __forceinline__ T dual_prox(T y, T sigma, T axt, T lo, T hi) {
-  const T inf = pos_inf<T>();
-  if (lo > -inf) {
-    const T t = y + sigma * (lo - axt);
-    if (t > T(0)) return t;
-  }
-  if (hi < inf) {
-    const T t = y + sigma * (hi - axt);
-    if (t < T(0)) return t;
-  }
-  return T(0);
-}
-
-// lambda = projection of the reduced cost r onto the sign cone of the column bounds
-__device__ __forceinline__ double rc_proj(double r, double l, double u) {
-  const double inf = pos_inf<double>();
-  const bool lf = l > -inf, uf = u < inf;
-  if (lf && uf) return r;
-  if (lf) return r > 0.0 ? r : 0.0;
-  if (uf) return r < 0.0 ? r : 0.0;
-  return 0.0;
-}
-
-// SplitMix64 output function (Steele, Lea, Flood 2014)
-__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-  return z ^ (z >> 31);
-}
-__device__ __forceinline__ unsigned long long round_hash(long long j, double v) {
-  double r = floor(v + 0.5);
-  const double lim = 4611686018427387904.0;  // 2^62
-  r = r < -lim ? -lim : (r > lim ? lim : r);
-  const unsigned long long key =
-      (unsigned long long)j * 0x9E3779B97F4A7C15ULL + (unsigned long long)(long long)r;
-  return mix64(key);
-}
-
-// per-block reduction of N partial sums into part[blockIdx.x * N + k], fixed order
-template <int N, typename A>
-__device__ __forceinline__ void block_store_partials(const A (&v)[N], double* __restrict__ part) {
-  __shared__ double sh[kMaxWarps][N];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    const A t = warp_sum(v[k]);
-    if (lane == 0) sh[w][k] = double(t);
-  }
-  __syncthreads();
-  if (threadIdx.x < N) {
-    double s = 0.0;
-    for (int i = 0; i < nw; ++i) s += sh[i][threadIdx.x];
-    part[blockIdx.x * N + threadIdx.x] = s;
-  }
-  __syncthreads();
-}
-
-__device__ __forceinline__ bool is_last_block(unsigned int* counter) {
-  __shared__ int last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (last) __threadfence();
-  return last != 0;
-}
-
-// sums of two partial arrays (NA values over na blocks, NB over nb) in one pass by
-// the whole (last) block: each thread accumulates a fixed strided subset, then one
-// fixed-order block reduction of all NA + NB values
-template <int NA, int NB>
-__device__ void reduce_two(const double* pa, int na, const double* pb, int nb, double* out_shared) {
-  constexpr int N = NA + NB;
-  __shared__ double sh[kMaxWarps][N];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double s[N];
-#pragma unroll
-  for (int k = 0; k < N; ++k) s[k] = 0.0;
-  for (int b = threadIdx.x; b < na; b += blockDim.x)
-#pragma unroll
-    for (int k = 0; k < NA; ++k) s[k] += __ldcg(pa + b * NA + k);
-  for (int b = threadIdx.x; b < nb; b += blockDim.x)
-#pragma unroll
-    for (int k = 0; k < NB; ++k) s[NA + k] += __ldcg(pb + b * NB + k);
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    const double t = warp_sum(s[k]);
-    if (lane == 0) sh[w][k] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x < N) {
-    double t = 0.0;
-    for (int i = 0; i < nw; ++i) t += sh[i][threadIdx.x];
-    out_shared[threadIdx.x] = t;
-  }
-  __syncthreads();
-}
 
 // --------------------------------------------------------------- the SpMV core ---
 // Warp-tile CSR gather.  Each warp takes tiles round-robin.  A multi-row tile (at
@@ -279,77 +123,6 @@ __device__ __forceinline__ void spmv_tiles(const int2* __restrict__ tiles, int n
   }
 }
 
-// ------------------------------------------------------------- step control ---
-// Adaptive step (PDLP): eta_max = (omega ||dx||^2 + ||dy||^2 / omega) / (2 |dy.A dx|);
-// eta' = min((1 - (k+1)^-0.3) eta_max, (1 + (k+1)^-0.6) eta), k the 1-based attempt
-// number; the attempt is accepted when eta <= eta_max.  The two powers come from
-// a table that the check kernel fills for the next n_check attempts (FP64
-// transcendentals are slow on this part; in the table they run in parallel).
-__device__ void step_control(Control* c, double dx2, double dy2, double inter, const double* fac, int n_check,
-                             double* trace, int cap) {
-  if (!isfinite(dx2) || !isfinite(dy2) || !isfinite(inter)) {
-    c->done = 1;
-    c->status = SCYLLA_NUMERICAL;
-    return;
-  }
-  const long long k1 = c->k + 1;
-  const double eta = c->eta, om = c->omega;
-  bool accept = true;
-  double eta_next = eta;
-  double eta_max = pos_inf<double>();
-  if (c->adaptive) {
-    const double mv = om * dx2 + dy2 / om;
-    eta_max = inter != 0.0 ? mv / (2.0 * fabs(inter)) : pos_inf<double>();
-    const long long idx = k1 - 1 - c->k_fac;
-    double fr, fg;
-    if (idx >= 0 && idx < n_check) {
-      fr = fac[2 * idx];
-      fg = fac[2 * idx + 1];
-    } else {
-      const double kk = double(k1 + 1);
-      fr = 1.0 - pow(kk, -c->exp_red);
-      fg = 1.0 + pow(kk, -c->exp_grow);
-    }
-    eta_next = fmin(fr * eta_max, fg * eta);
-    accept = eta <= eta_max;
-  }
-  if (trace && k1 <= cap) {
-    double* t = trace + 4 * (k1 - 1);
-    t[0] = eta;
-    t[1] = eta_max;
-    t[2] = accept ? 1.0 : 0.0;
-    t[3] = eta_next;
-  }
-  c->k = k1;
-  c->eta_used = eta;
-  c->eta = eta_next;
-  c->copy_lr = 0;
-  if (accept) {
-    const int t = c->ix_cur;
-    c->ix_cur = c->ix_next;
-    c->ix_next = t;
-    c->aty_valid = 0;
-    c->wsum += eta;
-    c->avg_w = eta / c->wsum;
-    c->accepted++;
-  } else {
-    c->aty_valid = 1;
-    c->avg_w = 0.0;
-    c->rejected++;
-  }
-}
-
-// step-size factor table for attempts k+1 .. k+n_check (by the whole last block)
-__device__ void fill_step_factors(Control* c, double* fac, int n_check) {
-  const long long k = c->k;
-  for (int i = threadIdx.x; i < n_check; i += blockDim.x) {
-    const double kk = double(k + 1 + i + 1);
-    fac[2 * i] = 1.0 - pow(kk, -c->exp_red);
-    fac[2 * i + 1] = 1.0 + pow(kk, -c->exp_grow);
-  }
-  if (threadIdx.x == 0) c->k_fac = k;
-}
-
 // Programmatic dependent launch: each per-attempt kernel is launched while its
 // predecessor still runs; it waits here for the predecessor's completion (and
 // memory) before touching any mutable data, then lets its own successor launch.
@@ -370,11 +143,6 @@ struct MinBlocks<double> {
   static constexpr int value = 2;
 };
 
-// per-thread accumulator type of the bulk kernels
-template <typename T>
-struct AccOf {
-  typedef T type;
-};
 
 // gathered vectors: read-only path within one launch; L2-coherent loads inside the
 // persistent kernel, where other SMs wrote them earlier in the same launch
@@ -583,133 +351,6 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_dual(DevLP<T>
     step_control(ctl, red[0], red[1], red[2], d.step_fac, d.n_check, d.trace_steps, d.trace_cap);
     ctl->cnt_dual = 0;
   }
-}
-
-// ------------------------------------------------------------------ checks ---
-struct Eval {
-  double rp_s2, rd_s2, rp2, rd2, pobj, dobj, dx2, dy2;
-  double eps_p, eps_d, eps_g, rel;
-};
-
-__device__ __forceinline__ double weighted_kkt(const Eval& e, double om) {
-  const double g = e.pobj - e.dobj;
-  return sqrt(om * om * e.rp_s2 + e.rd_s2 / (om * om) + g * g);
-}
-
-__device__ void finish(Control* c, int status, bool out_avg, const Eval& e) {
-  c->done = 1;
-  c->status = status;
-  c->used_avg = out_avg ? 1 : 0;
-  c->eps_p = e.eps_p;
-  c->eps_d = e.eps_d;
-  c->eps_g = e.eps_g;
-  c->rel_kkt = e.rel;
-  c->pobj = e.pobj;
-  c->dobj = e.dobj;
-  if (out_avg) {
-    int t = c->ix_cur;
-    c->ix_cur = c->ix_avg;
-    c->ix_avg = t;
-    t = c->ia_cur;
-    c->ia_cur = c->ia_avg;
-    c->ia_avg = t;
-  }
-}
-
-// Termination (Section 2.2), stalling (Algorithm 1) and restarts (PDLP) from the
-// 18 reduced sums of the two check kernels.
-__device__ void check_control(Control* c, const double* r, double* trace, int cap) {
-  Eval e[2];
-  for (int q = 0; q < 2; ++q) {
-    const double* cs = r + 5 * q;
-    const double* rs = r + kNC1 + 4 * q;
-    e[q].rd_s2 = cs[0];
-    e[q].rd2 = cs[1];
-    e[q].pobj = cs[2] + c->offset;
-    e[q].dobj = (rs[2] + cs[3]) + c->offset;
-    e[q].dx2 = cs[4];
-    e[q].rp_s2 = rs[0];
-    e[q].rp2 = rs[1];
-    e[q].dy2 = rs[3];
-    e[q].eps_p = sqrt(e[q].rp2) / (1.0 + c->bnorm);
-    e[q].eps_d = sqrt(e[q].rd2) / (1.0 + c->cnorm);
-    e[q].eps_g = fabs(e[q].pobj - e[q].dobj) / (1.0 + fabs(e[q].pobj) + fabs(e[q].dobj));
-    e[q].rel = fmax(e[q].eps_p, fmax(e[q].eps_d, e[q].eps_g));
-  }
-  const unsigned long long h = c->hash_accum;
-  c->hash_accum = 0ULL;
-  c->aty_valid = 1;
-  if (c->initial) {
-    c->initial = 0;
-    c->avg_w = 0.0;
-    const double kc = weighted_kkt(e[0], c->omega);
-    c->kkt_lr = kc;
-    c->kkt_prev = kc;
-    c->k_lr = 0;
-    c->copy_lr = 1;
-    c->last_hash = h;
-    c->same_hash = 0;
-    c->eps_p = e[0].eps_p; c->eps_d = e[0].eps_d; c->eps_g = e[0].eps_g;
-    c->rel_kkt = e[0].rel; c->pobj = e[0].pobj; c->dobj = e[0].dobj;
-    if (isnan(e[0].rel)) finish(c, SCYLLA_NUMERICAL, false, e[0]);
-    else if (e[0].rel <= c->tol) finish(c, SCYLLA_CONVERGED, false, e[0]);
-    else if (c->iter_limit <= 0) finish(c, SCYLLA_ITER_LIMIT, false, e[0]);
-    return;
-  }
-  const bool has_avg = c->wsum > 0.0;
-  c->avg_w = 0.0;
-  const bool out_avg = has_avg && e[1].rel < e[0].rel;
-  const Eval& eo = out_avg ? e[1] : e[0];
-  c->eps_p = eo.eps_p; c->eps_d = eo.eps_d; c->eps_g = eo.eps_g;
-  c->rel_kkt = eo.rel; c->pobj = eo.pobj; c->dobj = eo.dobj;
-  if (isnan(e[0].rel)) { finish(c, SCYLLA_NUMERICAL, false, e[0]); return; }
-  if (eo.rel <= c->tol) { finish(c, SCYLLA_CONVERGED, out_avg, eo); return; }
-  if (c->k >= c->iter_limit) { finish(c, SCYLLA_ITER_LIMIT, out_avg, eo); return; }
-  c->same_hash = (h == c->last_hash) ? c->same_hash + 1 : 0;
-  c->last_hash = h;
-  if (c->stall_checks > 0 && c->same_hash >= c->stall_checks) { finish(c, SCYLLA_STALLED, out_avg, eo); return; }
-  if (!c->restarts_on) return;
-  const double om = c->omega;
-  const double kc_cur = weighted_kkt(e[0], om);
-  const bool cand_avg = has_avg && weighted_kkt(e[1], om) < kc_cur;
-  const Eval& ec = cand_avg ? e[1] : e[0];
-  const double kc = weighted_kkt(ec, om);
-  const bool restart = kc <= c->beta_s * c->kkt_lr || (kc <= c->beta_n * c->kkt_lr && kc > c->kkt_prev) ||
-                       double(c->k - c->k_lr) >= c->beta_a * double(c->k);
-  double* rec = nullptr;
-  if (trace && c->n_ctrace < cap) {
-    rec = trace + 5 * c->n_ctrace;
-    c->n_ctrace++;
-    rec[0] = double(c->k);
-    rec[1] = restart ? 1.0 : 0.0;
-    rec[2] = cand_avg ? 1.0 : 0.0;
-    rec[3] = c->omega;
-    rec[4] = kc;
-  }
-  if (!restart) {
-    c->kkt_prev = kc;
-    return;
-  }
-  c->restarts++;
-  if (c->pw_update) {
-    const double ddx = sqrt(ec.dx2), ddy = sqrt(ec.dy2);
-    if (ddx > 1e-10 && ddy > 1e-10)
-      c->omega = exp(c->theta * log(ddy / ddx) + (1.0 - c->theta) * log(om));
-  }
-  if (cand_avg) {
-    int t = c->ix_cur;
-    c->ix_cur = c->ix_avg;
-    c->ix_avg = t;
-    t = c->ia_cur;
-    c->ia_cur = c->ia_avg;
-    c->ia_avg = t;
-  }
-  c->k_lr = c->k;
-  c->wsum = 0.0;
-  c->copy_lr = 1;
-  c->kkt_lr = weighted_kkt(ec, c->omega);
-  c->kkt_prev = c->kkt_lr;
-  if (rec) rec[3] = c->omega;
 }
 
 template <typename T>
@@ -1314,29 +955,6 @@ __global__ void k_objective_rows(DevObjective o, double offset_base, int use_off
 // are finished (or waiting at their iteration limit) are skipped.  Sums are kept per
 // tile and reduced per LP, in a fixed order, by one warp per LP in the control
 // kernels, which then run the same step and check logic as the single-LP path.
-constexpr int kSlotActive = 1, kSlotCopyLr = 2, kSlotCached = 4, kSlotAvg = 8, kSlotCheck = 16;
-
-template <typename T>
-__device__ __forceinline__ void write_slot(BatchSlot<T>* s, const Control* c) {
-  BatchSlot<T> v;
-  v.tau = T(c->eta / c->omega);
-  v.sigma = T(c->eta * c->omega);
-  v.w = T(c->avg_w);
-  v.w1 = T(1.0 - c->avg_w);
-  v.cur = c->ix_cur;
-  v.nxt = c->ix_next;
-  v.avg = c->ix_avg;
-  v.ia_cur = c->ia_cur;
-  v.ia_avg = c->ia_avg;
-  int f = 0;
-  if (!c->done && c->k < c->iter_limit) f |= kSlotActive;
-  if (!c->done) f |= kSlotCheck;
-  if (c->copy_lr) f |= kSlotCopyLr;
-  if (c->aty_valid) f |= kSlotCached;
-  if (c->avg_w > 0.0) f |= kSlotAvg;
-  v.flags = f;
-  *s = v;
-}
 
 // warp-tile loop of the batched kernels: begin(lp, t) decides per tile (uniformly
 // over the warp) whether the tile's LP takes part, end(t) flushes the tile's sums

@@ -102,6 +102,11 @@ _SIGS = {
     "scylla_batch_solve": (C.c_int, [_P, C.c_double, C.c_int64, C.POINTER(PdhgResult), _D]),
     "scylla_batch_get_primal": (C.c_int, [_P, C.c_int32, _D]),
     "scylla_batch_reset_state": (C.c_int, [_P]),
+    "scylla_fanout_create": (C.c_int, [_P, C.c_int32, _D, C.c_int32, C.POINTER(_P)]),
+    "scylla_fanout_destroy": (None, [_P]),
+    "scylla_fanout_solve": (C.c_int, [_P, C.c_double, C.c_int64, C.POINTER(PdhgResult), _D]),
+    "scylla_fanout_get_primal": (C.c_int, [_P, C.c_int32, _D]),
+    "scylla_fanout_reset_state": (C.c_int, [_P]),
     "scylla_last_error": (C.c_char_p, []),
 }
 
@@ -361,3 +366,43 @@ class Batch:
 
     def reset_state(self):
         _check(lib().scylla_batch_reset_state(self.h))
+
+
+class Fanout:
+    """K pump objectives of one LP solved together (``scylla_fanout``).
+
+    targets: array (n, K) of rounding targets; objective k is the Section 2.4 update
+    of round ``round_K`` around column k.  The LP handle must outlive this object."""
+
+    def __init__(self, lp: "LP", targets, round_K: int = 1):
+        t = np.ascontiguousarray(np.asarray(targets, dtype=np.float64).T)  # K blocks of length n
+        self.K = t.shape[0]
+        self.lp = lp
+        h = _P()
+        _check(lib().scylla_fanout_create(lp.h, self.K, _dp(t), int(round_K), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().scylla_fanout_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, tol: float, iter_limit: int):
+        res = (PdhgResult * self.K)()
+        sec = C.c_double()
+        _check(lib().scylla_fanout_solve(self.h, float(tol), int(iter_limit), res, C.byref(sec)))
+        return list(res), sec.value
+
+    def primal(self, k: int) -> np.ndarray:
+        x = np.empty(self.lp.n)
+        _check(lib().scylla_fanout_get_primal(self.h, int(k), _dp(x)))
+        return x
+
+    def reset_state(self):
+        _check(lib().scylla_fanout_reset_state(self.h))
