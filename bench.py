@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dram", action="store_true", help="skip the DRAM-resident MCF section")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched section")
+    ap.add_argument("--no-fanout", action="store_true", help="skip the K-objective fan-out section")
     return ap.parse_args()
 
 
@@ -291,6 +292,9 @@ def run_ours(args):
     batched = None
     if rank == 0 and not args.no_batch:
         batched = batched_section(S, peak, peak_kind)
+    fanout = None
+    if rank == 0 and not args.no_fanout:
+        fanout = fanout_section(S)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -344,7 +348,54 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "dram_resident": dram,
         "batched": batched,
+        "fanout": fanout,
     }
+    return out
+
+
+FAN_WORKLOAD = "fan-out: m=200k, n=500k, 5M lognormal nnz, 40% binary, K=64 targets flipping 10% of binaries"
+
+
+def fanout_section(S):
+    """K = 64 pump objectives of one LP solved to rel-KKT 1e-4 as one FP32-mixed SpMM
+    fan-out, against 64 sequential plain FP64 solves of the same objectives from the
+    same warm start (device time of the solves)."""
+    import torch
+    from paper_2307_03466_gb300 import instances as I
+    inst = I.fanout_base()
+    base = S.LP.from_instance(inst, S.default_params(precision=S.PREC_MIXED, aux_general_integers=0))
+    base.pdhg_solve(1e-3, 20000)  # the shared warm start
+    x = base.primal()
+    target = x.copy()
+    ic = inst.is_int == 1
+    target[ic] = np.floor(x[ic] + 0.5)
+    targets = I.fanout_targets(inst, target, K=64, flip_frac=0.10)
+    state = base.get_state()
+    out = {"workload": FAN_WORKLOAD, "m": inst.m, "n": inst.n, "nnz": inst.nnz, "K": 64}
+    F = S.Fanout(base, targets, round_K=1)
+    F.solve(TOL, ITER_CAP)  # warm-up (graph capture)
+    F.reset_state()
+    res, sec = F.solve(TOL, ITER_CAP)
+    out["mixed_fanout"] = {"seconds": sec, "converged": sum(1 for r in res if r.status == S.CONVERGED),
+                           "max_attempts": max(r.iterations for r in res),
+                           "max_rel_kkt": max(r.rel_kkt for r in res)}
+    F.close()
+    seq = 0.0
+    seq_conv = 0
+    seq_att = 0
+    g = S.LP.from_instance(inst, S.default_params(precision=S.PREC_FP64, aux_general_integers=0))
+    for q in range(64):
+        g.set_state(*state)
+        g.set_objective(targets[:, q], 1)
+        r = g.pdhg_solve(TOL, ITER_CAP)
+        seq += r.seconds
+        seq_conv += int(r.status == S.CONVERGED)
+        seq_att += r.iterations
+    g.close()
+    base.close()
+    torch.cuda.synchronize()
+    out["fp64_sequential"] = {"seconds": seq, "converged": seq_conv, "sum_attempts": seq_att}
+    out["speedup_mixed_fanout_vs_fp64_sequential"] = seq / sec
     return out
 
 
