@@ -74,7 +74,10 @@ __device__ __forceinline__ double fan_g(const unsigned long long* lo_bits, const
 }
 
 // sum over the row's nonzeros of a_rp * src[col][k] for the lane's two objectives;
-// the (index, value) pairs are loaded 32 at a time and broadcast by shuffles
+// the (index, value) pairs are loaded 32 at a time and broadcast by shuffles, four
+// nonzeros per step so eight gathers per lane are in flight.  Lanes past the row end
+// carry (column 0, value 0), which adds exactly zero, so the four-wide steps need
+// no bounds test and the summation order stays the CSR order.
 template <typename Acc, typename V, typename Src>
 __device__ __forceinline__ void row_gather(int p0, int p1, const int* __restrict__ cols, const V* __restrict__ vals,
                                            Src src, Acc (&s)[2]) {
@@ -90,13 +93,22 @@ __device__ __forceinline__ void row_gather(int p0, int p1, const int* __restrict
       vl = __ldg(vals + p);
     }
     const int cnt = p1 - b < 32 ? p1 - b : 32;
-    for (int e = 0; e < cnt; ++e) {
-      const int c = __shfl_sync(0xffffffffu, cl, e);
-      const Acc a = Acc(__shfl_sync(0xffffffffu, vl, e));
-      Acc g[2];
-      src(c, g);
-      s[0] = fma_t<Acc>(a, g[0], s[0]);
-      s[1] = fma_t<Acc>(a, g[1], s[1]);
+    for (int e = 0; e < cnt; e += 4) {
+      int c[4];
+      Acc a[4];
+      Acc g[4][2];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        c[u] = __shfl_sync(0xffffffffu, cl, e + u);
+        a[u] = Acc(__shfl_sync(0xffffffffu, vl, e + u));
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) src(c[u], g[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        s[0] = fma_t<Acc>(a[u], g[u][0], s[0]);
+        s[1] = fma_t<Acc>(a[u], g[u][1], s[1]);
+      }
     }
   }
 }
