@@ -8,6 +8,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -110,19 +111,20 @@ __device__ __forceinline__ unsigned long long round_hash(long long j, double v) 
   return mix64(key);
 }
 
-// per-block reduction of N partial sums into part[blockIdx.x * N + k], fixed order
+// per-block reduction of N partial sums into part[blockIdx.x * N + k], fixed order,
+// in the accumulator type A (FP32 sums of the FP32 bulk stay on the FP32 pipe)
 template <int N, typename A>
-__device__ __forceinline__ void block_store_partials(const A (&v)[N], double* __restrict__ part) {
-  __shared__ double sh[kMaxWarps][N];
+__device__ __forceinline__ void block_store_partials(const A (&v)[N], A* __restrict__ part) {
+  __shared__ A sh[kMaxWarps][N];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     const A t = warp_sum(v[k]);
-    if (lane == 0) sh[w][k] = double(t);
+    if (lane == 0) sh[w][k] = t;
   }
   __syncthreads();
   if (threadIdx.x < N) {
-    double s = 0.0;
+    A s = A(0);
     for (int i = 0; i < nw; ++i) s += sh[i][threadIdx.x];
     part[blockIdx.x * N + threadIdx.x] = s;
   }
@@ -131,11 +133,13 @@ __device__ __forceinline__ void block_store_partials(const A (&v)[N], double* __
 
 __device__ __forceinline__ bool is_last_block(unsigned int* counter) {
   __shared__ int last;
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    if (last) __threadfence();
+  }
   __syncthreads();
-  if (last) __threadfence();
   return last != 0;
 }
 
@@ -170,49 +174,198 @@ static __device__ void reduce_two(const double* pa, int na, const double* pb, in
   __syncthreads();
 }
 
+__device__ __forceinline__ float ldcg_t(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ double ldcg_t(const double* p) { return __ldcg(p); }
+
+// The three sums of an attempt (||dx||^2 from na primal-block partials; ||dy||^2 and
+// the interaction from nb dual-block partials) by warps 1.. of the block, in a fixed
+// order: strided per-thread sums to scratch (3 * (blockDim.x - 32) values), then
+// warp 1 + k sums column k and reduces it across its lanes.  Warp 0 is left free for
+// the caller (it prefetches the decision's inputs meanwhile); every thread leaves
+// with out[0..2] valid.
+template <typename A>
+static __device__ void reduce_step(const A* pa, int na, const A* pb, int nb, A* scratch, A* out) {
+  const int nt = blockDim.x - 32, t = threadIdx.x - 32;
+  if (t >= 0) {
+    // the first kR values of each thread are loaded before any is summed
+    constexpr int kR = 6;
+    A va[kR], vb[kR], vc[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+      const int ba = t + r * nt, bb = t + r * nt;
+      va[r] = ba < na ? ldcg_t(pa + ba) : A(0);
+      vb[r] = bb < nb ? ldcg_t(pb + 2 * bb) : A(0);
+      vc[r] = bb < nb ? ldcg_t(pb + 2 * bb + 1) : A(0);
+    }
+    A s0 = A(0), s1 = A(0), s2 = A(0);
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+      s0 += va[r];
+      s1 += vb[r];
+      s2 += vc[r];
+    }
+    for (int b = t + kR * nt; b < na; b += nt) s0 += ldcg_t(pa + b);
+    for (int b = t + kR * nt; b < nb; b += nt) {
+      s1 += ldcg_t(pb + 2 * b);
+      s2 += ldcg_t(pb + 2 * b + 1);
+    }
+    scratch[t] = s0;
+    scratch[nt + t] = s1;
+    scratch[2 * nt + t] = s2;
+    asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
+    const int w = t >> 5, lane = t & 31;
+    if (w < 3) {
+      A v = A(0);
+      for (int i = lane; i < nt; i += 32) v += scratch[w * nt + i];
+      v = warp_sum(v);
+      if (lane == 0) out[w] = v;
+    }
+  }
+  __syncthreads();
+}
+
 // ------------------------------------------------------------- step control ---
 // Adaptive step (PDLP): eta_max = (omega ||dx||^2 + ||dy||^2 / omega) / (2 |dy.A dx|);
 // eta' = min((1 - (k+1)^-0.3) eta_max, (1 + (k+1)^-0.6) eta), k the 1-based attempt
 // number; the attempt is accepted when eta <= eta_max.  The two powers come from
 // a table that the check kernel fills for the next n_check attempts (FP64
 // transcendentals are slow on this part; in the table they run in parallel).
-static __device__ void step_control(Control* c, double dx2, double dy2, double inter, const double* fac, int n_check,
-                             double* trace, int cap) {
+//
+// The decision is split in two: step_pre gathers and prepares everything that
+// does not depend on the attempt's sums (it runs while they are being reduced),
+// step_control finishes once they are known.  C is the type of the decision
+// arithmetic: double in the FP64 mode; float in the FP32-mixed mode, whose sums
+// are FP32 already (every FP64 instruction is a long serial step on this part).
+
+// tau, sigma and the averaging weights of the next attempt from eta, omega, avg_w
+__device__ __forceinline__ void derive_steps(Control* c) {
+  const double eta = c->eta, om = c->omega, w = c->avg_w;
+  c->inv_omega = 1.0 / om;
+  c->tau_d = eta * c->inv_omega;
+  c->sigma_d = eta * om;
+  c->w_d = w;
+  c->w1_d = 1.0 - w;
+  c->tau_f = float(c->tau_d);
+  c->sigma_f = float(c->sigma_d);
+  c->w_f = float(w);
+  c->w1_f = float(c->w1_d);
+  c->avg_on = w > 0.0 ? 1 : 0;
+  c->eta_f = float(eta);
+  c->om_f = float(om);
+  c->iom_f = float(c->inv_omega);
+  c->wsum_f = float(c->wsum);
+}
+
+// FP32-mixed mode, before a check: the FP64 step-size state from its FP32 copies
+__device__ __forceinline__ void sync_step_state(Control* c) {
+  c->eta = double(c->eta_f);
+  c->wsum = double(c->wsum_f);
+}
+
+struct StepPre {
+  long long k1;
+  double eta, om, inv_om, fr, fg, wsum_new, w_acc;  // FP64 mode
+  float eta_f, om_f, iom_f, fr_f, fg_f, wsum_new_f, w_acc_f, fr_next, fg_next;  // FP32 mode
+  int adaptive;
+};
+
+// FP64 mode: this attempt's factors from the table
+static __device__ void step_factors(const Control* c, const double* fac, int n_check, long long k1, double& fr,
+                                    double& fg) {
+  const long long idx = k1 - 1 - c->k_fac;
+  if (idx >= 0 && idx < n_check) {
+    fr = fac[2 * idx];
+    fg = fac[2 * idx + 1];
+  } else {
+    const double kk = double(k1 + 1);
+    fr = 1.0 - pow(kk, -c->exp_red);
+    fg = 1.0 + pow(kk, -c->exp_grow);
+  }
+}
+
+template <typename C>
+static __device__ StepPre step_pre(const Control* c, const double* fac, int n_check);
+
+template <>
+__device__ StepPre step_pre<double>(const Control* c, const double* fac, int n_check) {
+  StepPre p;
+  p.k1 = c->k + 1;
+  p.eta = c->eta;
+  p.om = c->omega;
+  p.inv_om = c->inv_omega;
+  p.adaptive = c->adaptive;
+  p.wsum_new = c->wsum + p.eta;
+  p.w_acc = p.eta / p.wsum_new;  // the averaging weight if the attempt is accepted
+  p.fr = 1.0;
+  p.fg = 1.0;
+  if (p.adaptive) step_factors(c, fac, n_check, p.k1, p.fr, p.fg);
+  return p;
+}
+
+// FP32 mode: everything from the FP32 copies; this attempt's factors were stored by
+// the previous decision (or the check), the next attempt's come from the FP32 table
+template <>
+__device__ StepPre step_pre<float>(const Control* c, const double* fac, int n_check) {
+  StepPre p;
+  p.k1 = c->k + 1;
+  p.eta_f = c->eta_f;
+  p.om_f = c->om_f;
+  p.iom_f = c->iom_f;
+  p.adaptive = c->adaptive;
+  p.fr_f = c->fr_f;
+  p.fg_f = c->fg_f;
+  p.wsum_new_f = c->wsum_f + p.eta_f;
+  p.w_acc_f = p.eta_f / p.wsum_new_f;
+  const long long idx = p.k1 - c->k_fac;  // table index of attempt k1 + 1
+  if (idx >= 0 && idx < n_check) {
+    const float* facf = reinterpret_cast<const float*>(fac + 2 * n_check);
+    p.fr_next = facf[2 * idx];
+    p.fg_next = facf[2 * idx + 1];
+  } else {
+    double fr, fg;
+    step_factors(c, fac, n_check, p.k1 + 1, fr, fg);
+    p.fr_next = float(fr);
+    p.fg_next = float(fg);
+  }
+  return p;
+}
+
+template <typename C>
+static __device__ void step_control(Control* c, const StepPre& p, C dx2, C dy2, C inter, double* trace, int cap);
+
+// FP64 mode
+template <>
+__device__ void step_control<double>(Control* c, const StepPre& p, double dx2, double dy2, double inter,
+                                     double* trace, int cap) {
   if (!isfinite(dx2) || !isfinite(dy2) || !isfinite(inter)) {
     c->done = 1;
     c->status = SCYLLA_NUMERICAL;
     return;
   }
-  const long long k1 = c->k + 1;
-  const double eta = c->eta, om = c->omega;
   bool accept = true;
-  double eta_next = eta;
+  double eta_next = p.eta;
   double eta_max = pos_inf<double>();
-  if (c->adaptive) {
-    const double mv = om * dx2 + dy2 / om;
+  if (p.adaptive) {
+    const double mv = p.om * dx2 + dy2 * p.inv_om;
     eta_max = inter != 0.0 ? mv / (2.0 * fabs(inter)) : pos_inf<double>();
-    const long long idx = k1 - 1 - c->k_fac;
-    double fr, fg;
-    if (idx >= 0 && idx < n_check) {
-      fr = fac[2 * idx];
-      fg = fac[2 * idx + 1];
-    } else {
-      const double kk = double(k1 + 1);
-      fr = 1.0 - pow(kk, -c->exp_red);
-      fg = 1.0 + pow(kk, -c->exp_grow);
-    }
-    eta_next = fmin(fr * eta_max, fg * eta);
-    accept = eta <= eta_max;
+    eta_next = fmin(p.fr * eta_max, p.fg * p.eta);
+    accept = p.eta <= eta_max;
   }
+  const long long k1 = p.k1;
   if (trace && k1 <= cap) {
     double* t = trace + 4 * (k1 - 1);
-    t[0] = eta;
+    t[0] = p.eta;
     t[1] = eta_max;
     t[2] = accept ? 1.0 : 0.0;
     t[3] = eta_next;
   }
+  c->tau_d = eta_next * p.inv_om;
+  c->sigma_d = eta_next * p.om;
+  c->w_d = accept ? p.w_acc : 0.0;
+  c->w1_d = accept ? 1.0 - p.w_acc : 1.0;
+  c->avg_on = accept ? 1 : 0;
   c->k = k1;
-  c->eta_used = eta;
+  c->eta_used = p.eta;
   c->eta = eta_next;
   c->copy_lr = 0;
   if (accept) {
@@ -220,8 +373,8 @@ static __device__ void step_control(Control* c, double dx2, double dy2, double i
     c->ix_cur = c->ix_next;
     c->ix_next = t;
     c->aty_valid = 0;
-    c->wsum += eta;
-    c->avg_w = eta / c->wsum;
+    c->wsum = p.wsum_new;
+    c->avg_w = p.w_acc;
     c->accepted++;
   } else {
     c->aty_valid = 1;
@@ -230,13 +383,80 @@ static __device__ void step_control(Control* c, double dx2, double dy2, double i
   }
 }
 
+// FP32 mode: no FP64 instruction; eta and wsum live in their FP32 copies until
+// the next check
+template <>
+__device__ void step_control<float>(Control* c, const StepPre& p, float dx2, float dy2, float inter,
+                                    double* trace, int cap) {
+  if (!isfinite(dx2) || !isfinite(dy2) || !isfinite(inter)) {
+    c->done = 1;
+    c->status = SCYLLA_NUMERICAL;
+    sync_step_state(c);
+    return;
+  }
+  bool accept = true;
+  float eta_next = p.eta_f;
+  float eta_max = pos_inf<float>();
+  if (p.adaptive) {
+    const float mv = p.om_f * dx2 + dy2 * p.iom_f;
+    eta_max = inter != 0.0f ? mv / (2.0f * fabsf(inter)) : pos_inf<float>();
+    eta_next = fminf(p.fr_f * eta_max, p.fg_f * p.eta_f);
+    accept = p.eta_f <= eta_max;
+  }
+  const long long k1 = p.k1;
+  if (trace && k1 <= cap) {
+    double* t = trace + 4 * (k1 - 1);
+    t[0] = double(p.eta_f);
+    t[1] = double(eta_max);
+    t[2] = accept ? 1.0 : 0.0;
+    t[3] = double(eta_next);
+  }
+  c->tau_f = eta_next * p.iom_f;
+  c->sigma_f = eta_next * p.om_f;
+  c->w_f = accept ? p.w_acc_f : 0.0f;
+  c->w1_f = accept ? 1.0f - p.w_acc_f : 1.0f;
+  c->avg_on = accept ? 1 : 0;
+  c->eta_f = eta_next;
+  c->fr_f = p.fr_next;
+  c->fg_f = p.fg_next;
+  c->k = k1;
+  c->copy_lr = 0;
+  if (accept) {
+    const int t = c->ix_cur;
+    c->ix_cur = c->ix_next;
+    c->ix_next = t;
+    c->aty_valid = 0;
+    c->wsum_f = p.wsum_new_f;
+    c->accepted++;
+  } else {
+    c->aty_valid = 1;
+    c->rejected++;
+  }
+}
+
+// the whole decision at once (control kernels of the batched and fan-out solves)
+static __device__ void step_control(Control* c, double dx2, double dy2, double inter, const double* fac, int n_check,
+                                    double* trace, int cap) {
+  const StepPre p = step_pre<double>(c, fac, n_check);
+  step_control<double>(c, p, dx2, dy2, inter, trace, cap);
+}
+
 // step-size factor table for attempts k+1 .. k+n_check (by the whole last block)
+// (FP64 values, then FP32 copies); thread 0 also stores attempt k+1's FP32 factors
 static __device__ void fill_step_factors(Control* c, double* fac, int n_check) {
   const long long k = c->k;
+  float* facf = reinterpret_cast<float*>(fac + 2 * n_check);
   for (int i = threadIdx.x; i < n_check; i += blockDim.x) {
     const double kk = double(k + 1 + i + 1);
-    fac[2 * i] = 1.0 - pow(kk, -c->exp_red);
-    fac[2 * i + 1] = 1.0 + pow(kk, -c->exp_grow);
+    const double fr = 1.0 - pow(kk, -c->exp_red), fg = 1.0 + pow(kk, -c->exp_grow);
+    fac[2 * i] = fr;
+    fac[2 * i + 1] = fg;
+    facf[2 * i] = float(fr);
+    facf[2 * i + 1] = float(fg);
+    if (i == 0) {
+      c->fr_f = float(fr);
+      c->fg_f = float(fg);
+    }
   }
   if (threadIdx.x == 0) c->k_fac = k;
 }
@@ -274,7 +494,7 @@ static __device__ void finish(Control* c, int status, bool out_avg, const Eval& 
 
 // Termination (Section 2.2), stalling (Algorithm 1) and restarts (PDLP) from the
 // 18 reduced sums of the two check kernels.
-static __device__ void check_control(Control* c, const double* r, double* trace, int cap) {
+static __device__ void check_control_impl(Control* c, const double* r, double* trace, int cap) {
   Eval e[2];
   for (int q = 0; q < 2; ++q) {
     const double* cs = r + 5 * q;
@@ -366,6 +586,11 @@ static __device__ void check_control(Control* c, const double* r, double* trace,
   c->kkt_lr = weighted_kkt(ec, c->omega);
   c->kkt_prev = c->kkt_lr;
   if (rec) rec[3] = c->omega;
+}
+
+static __device__ void check_control(Control* c, const double* r, double* trace, int cap) {
+  check_control_impl(c, r, trace, cap);
+  derive_steps(c);
 }
 
 // per-thread accumulator type of the bulk kernels

@@ -436,6 +436,7 @@ __global__ void k_finit(DevFan<T> F, double tol, long long iter_limit, int stall
   c->copy_lr = 0;
   c->hash_accum = 0ULL;
   c->same_hash = 0;
+  derive_steps(c);
   write_fan_slot(&F.slot[k], c);
 }
 

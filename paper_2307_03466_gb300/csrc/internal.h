@@ -55,6 +55,18 @@ struct Control {
   int aty_valid, copy_lr, done, status, used_avg, initial;
   int adaptive, restarts_on, pw_update;
   unsigned int cnt_dual, cnt_c2, cnt_misc;
+  // Derived by the control logic whenever eta, omega or the averaging weight change,
+  // so the bulk kernels load them instead of recomputing them in every thread (FP64
+  // division and conversion are slow on this part): 1/omega, and the next attempt's
+  // tau = eta/omega, sigma = eta omega and averaging weights (w, 1 - w) in both types.
+  double inv_omega;
+  double tau_d, sigma_d, w_d, w1_d;
+  float tau_f, sigma_f, w_f, w1_f;
+  int avg_on;  // w > 0
+  // FP32-mixed mode: the step-size state between checks lives in FP32 copies (eta,
+  // omega, 1/omega, the step-weight sum and this attempt's two step-size factors);
+  // the FP64 fields eta and wsum are brought up to date from them before each check.
+  float eta_f, om_f, iom_f, wsum_f, fr_f, fg_f;
 };
 
 // Pointers of one LP, passed by value to every kernel.  T is the type of the bulk
@@ -86,7 +98,8 @@ struct DevLP {
   Control* ctl;
   double *part_p, *part_d, *part_c1, *part_c2;
   int grid_p, grid_d, grid_c1, grid_c2;
-  double* step_fac;      // 2 * n_check: (1 - kk^-a, 1 + kk^-b) of the next n_check attempts
+  double* step_fac;      // (1 - kk^-a, 1 + kk^-b) of the next n_check attempts: 2 n_check doubles,
+                         // then the same 2 n_check values as floats (3 n_check doubles in all)
   double* pp_part;       // persistent kernel: 24 partial sums per block
   unsigned long long* p_hash;  // persistent kernel: two rounding-hash slots
   int n_check;

@@ -152,22 +152,37 @@ __device__ __forceinline__ T gload(const T* p) {
   return __ldg(p);
 }
 
-// the control values one attempt or check needs, read once per phase
+// the control values one attempt or check needs, read once per phase; the step
+// sizes and averaging weights come already derived and converted to T
+template <typename T>
 struct SlotView {
   int cur, nxt, avg, ia_cur, ia_avg;
-  double eta, omega, avg_w;
+  T tau, sigma, w, w1;
+  bool do_avg;
   int copy_lr, aty_valid;
 };
-__device__ __forceinline__ SlotView make_view(const Control* c) {
-  SlotView v;
+__device__ __forceinline__ void view_steps(const Control* c, SlotView<float>& v) {
+  v.tau = c->tau_f;
+  v.sigma = c->sigma_f;
+  v.w = c->w_f;
+  v.w1 = c->w1_f;
+}
+__device__ __forceinline__ void view_steps(const Control* c, SlotView<double>& v) {
+  v.tau = c->tau_d;
+  v.sigma = c->sigma_d;
+  v.w = c->w_d;
+  v.w1 = c->w1_d;
+}
+template <typename T>
+__device__ __forceinline__ SlotView<T> make_view(const Control* c) {
+  SlotView<T> v;
   v.cur = c->ix_cur;
   v.nxt = c->ix_next;
   v.avg = c->ix_avg;
   v.ia_cur = c->ia_cur;
   v.ia_avg = c->ia_avg;
-  v.eta = c->eta;
-  v.omega = c->omega;
-  v.avg_w = c->avg_w;
+  view_steps(c, v);
+  v.do_avg = c->avg_on != 0;
   v.copy_lr = c->copy_lr;
   v.aty_valid = c->aty_valid;
   return v;
@@ -226,7 +241,7 @@ struct PrimalEpi {
 
 // primal step of Algorithm 1 over all columns; block partial of ||x' - x||^2 to part
 template <typename T>
-__device__ __forceinline__ void setup_primal(PrimalEpi<T>& epi, const DevLP<T>& d, const SlotView& v) {
+__device__ __forceinline__ void setup_primal(PrimalEpi<T>& epi, const DevLP<T>& d, const SlotView<T>& v) {
   epi.xc = d.X[v.cur];
   epi.xn = d.X[v.nxt];
   epi.xa = d.X[v.avg];
@@ -235,10 +250,10 @@ __device__ __forceinline__ void setup_primal(PrimalEpi<T>& epi, const DevLP<T>& 
   epi.cc = d.c;
   epi.ll = d.l;
   epi.uu = d.u;
-  epi.tau = T(v.eta / v.omega);
-  epi.w = T(v.avg_w);
-  epi.w1 = T(1.0 - v.avg_w);
-  epi.do_avg = v.avg_w > 0.0;
+  epi.tau = v.tau;
+  epi.w = v.w;
+  epi.w1 = v.w1;
+  epi.do_avg = v.do_avg;
   epi.copy_lr = v.copy_lr != 0;
   epi.store_aty = !v.aty_valid;
   epi.use_cached = false;
@@ -246,7 +261,8 @@ __device__ __forceinline__ void setup_primal(PrimalEpi<T>& epi, const DevLP<T>& 
 }
 
 template <typename T, bool Coh>
-__device__ __forceinline__ void primal_phase(const DevLP<T>& d, const SlotView& v, T* sm, double* part) {
+__device__ __forceinline__ void primal_phase(const DevLP<T>& d, const SlotView<T>& v, T* sm,
+                                             typename AccOf<T>::type* part) {
   PrimalEpi<T> epi;
   setup_primal(epi, d, v);
   if (v.aty_valid) {
@@ -296,7 +312,7 @@ struct DualEpi {
 // extrapolated dual step of Algorithm 1 over all rows; block partials of ||y' - y||^2
 // and (y' - y).(A x' - A x) to part
 template <typename T>
-__device__ __forceinline__ void setup_dual(DualEpi<T>& epi, const DevLP<T>& d, const SlotView& v) {
+__device__ __forceinline__ void setup_dual(DualEpi<T>& epi, const DevLP<T>& d, const SlotView<T>& v) {
   epi.axc = d.AX[v.cur];
   epi.axn = d.AX[v.nxt];
   epi.yc = d.Y[v.cur];
@@ -305,17 +321,18 @@ __device__ __forceinline__ void setup_dual(DualEpi<T>& epi, const DevLP<T>& d, c
   epi.ylr = d.YLR;
   epi.lo = d.lo;
   epi.hi = d.hi;
-  epi.sigma = T(v.eta * v.omega);
-  epi.w = T(v.avg_w);
-  epi.w1 = T(1.0 - v.avg_w);
-  epi.do_avg = v.avg_w > 0.0;
+  epi.sigma = v.sigma;
+  epi.w = v.w;
+  epi.w1 = v.w1;
+  epi.do_avg = v.do_avg;
   epi.copy_lr = v.copy_lr != 0;
   epi.acc0 = 0;
   epi.acc1 = 0;
 }
 
 template <typename T, bool Coh>
-__device__ __forceinline__ void dual_phase(const DevLP<T>& d, const SlotView& v, T* sm, double* part) {
+__device__ __forceinline__ void dual_phase(const DevLP<T>& d, const SlotView<T>& v, T* sm,
+                                           typename AccOf<T>::type* part) {
   DualEpi<T> epi;
   setup_dual(epi, d, v);
   const T* __restrict__ xn = d.X[v.nxt];
@@ -328,27 +345,39 @@ __device__ __forceinline__ void dual_phase(const DevLP<T>& d, const SlotView& v,
 
 // The per-attempt kernels: with programmatic dependent launch they are resident
 // while their predecessor drains, and wait for it before touching any data.
+// block partials of the per-attempt sums, in the bulk accumulator type
+template <typename T>
+__device__ __forceinline__ typename AccOf<T>::type* acc_part(double* p) {
+  return reinterpret_cast<typename AccOf<T>::type*>(p);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_primal(DevLP<T> d) {
   Control* ctl = d.ctl;
   pdl_enter();
   if (ctl->done || ctl->k >= ctl->iter_limit) return;
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
-  primal_phase<T, false>(d, make_view(ctl), sm, d.part_p);
+  primal_phase<T, false>(d, make_view<T>(ctl), sm, acc_part<T>(d.part_p));
 }
 
+// The last block to finish reduces all block partials (warps 1..) while thread 0
+// gathers the decision's other inputs, then takes the step-size decision.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_dual(DevLP<T> d) {
+  typedef typename AccOf<T>::type A;
   Control* ctl = d.ctl;
   pdl_enter();
   if (ctl->done || ctl->k >= ctl->iter_limit) return;
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
-  dual_phase<T, false>(d, make_view(ctl), sm, d.part_d);
+  dual_phase<T, false>(d, make_view<T>(ctl), sm, acc_part<T>(d.part_d));
   if (!is_last_block(&ctl->cnt_dual)) return;
-  __shared__ double red[kNP + kND];
-  reduce_two<kNP, kND>(d.part_p, d.grid_p, d.part_d, d.grid_d, red);
+  __shared__ StepPre pre;  // in shared memory: nothing stays live in registers across the reduction
+  if (threadIdx.x == 0) pre = step_pre<A>(ctl, d.step_fac, d.n_check);
+  __shared__ A red[kNP + kND];
+  static_assert(3 * (kThreads - 32) * sizeof(A) <= sizeof(sm), "reduction scratch");
+  reduce_step<A>(acc_part<T>(d.part_p), d.grid_p, acc_part<T>(d.part_d), d.grid_d, reinterpret_cast<A*>(sm), red);
   if (threadIdx.x == 0) {
-    step_control(ctl, red[0], red[1], red[2], d.step_fac, d.n_check, d.trace_steps, d.trace_cap);
+    step_control<A>(ctl, pre, red[0], red[1], red[2], d.trace_steps, d.trace_cap);
     ctl->cnt_dual = 0;
   }
 }
@@ -400,11 +429,10 @@ struct CheckColsEpi {
 // averaged dual from FP64 values, reduced costs, dual residuals, objectives, the
 // rounding hash; block partials to part, hash into *hash
 template <typename T, bool Coh>
-__device__ __forceinline__ void check_cols_phase(const DevLP<T>& d, const SlotView& v, double* sm, double* part,
+__device__ __forceinline__ void check_cols_phase(const DevLP<T>& d, const SlotView<T>& v, double* sm, double* part,
                                                  unsigned long long* hash) {
-  const double wd = v.avg_w;
-  const T w = T(wd), w1 = T(1.0 - wd);
-  const bool do_avg = wd > 0.0;
+  const T w = v.w, w1 = v.w1;
+  const bool do_avg = v.do_avg;
   const T* __restrict__ yc = d.Y[v.cur];
   const T* __restrict__ ya = d.Y[v.avg];
   CheckColsEpi<T> epi;
@@ -478,7 +506,7 @@ struct CheckRowsEpi {
 // FP64 row half of a check: A x of the current and averaged primal from FP64
 // values (refreshing the cached products), primal residuals, dual objective rows
 template <typename T, bool Coh>
-__device__ __forceinline__ void check_rows_phase(const DevLP<T>& d, const SlotView& v, double* sm, double* part) {
+__device__ __forceinline__ void check_rows_phase(const DevLP<T>& d, const SlotView<T>& v, double* sm, double* part) {
   const T* __restrict__ xc = d.X[v.cur];
   const T* __restrict__ xa = d.X[v.avg];
   CheckRowsEpi<T> epi;
@@ -490,9 +518,9 @@ __device__ __forceinline__ void check_rows_phase(const DevLP<T>& d, const SlotVi
   epi.R = d.R;
   epi.lo64 = d.lo64;
   epi.hi64 = d.hi64;
-  epi.w = T(v.avg_w);
-  epi.w1 = T(1.0 - v.avg_w);
-  epi.do_avg = v.avg_w > 0.0;
+  epi.w = v.w;
+  epi.w1 = v.w1;
+  epi.do_avg = v.do_avg;
 #pragma unroll
   for (int k = 0; k < kNC2; ++k) epi.acc[k] = 0.0;
   auto gat = [&](int j, double(&g)[2]) {
@@ -510,7 +538,7 @@ __global__ void __launch_bounds__(kThreads) k_check_cols(DevLP<T> d) {
   pdl_enter();
   if (ctl->done) return;
   __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];
-  check_cols_phase<T, false>(d, make_view(ctl), sm, d.part_c1, &ctl->hash_accum);
+  check_cols_phase<T, false>(d, make_view<T>(ctl), sm, d.part_c1, &ctl->hash_accum);
 }
 
 template <typename T>
@@ -519,12 +547,13 @@ __global__ void __launch_bounds__(kThreads) k_check_rows(DevLP<T> d) {
   pdl_enter();
   if (ctl->done) return;
   __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];
-  check_rows_phase<T, false>(d, make_view(ctl), sm, d.part_c2);
+  check_rows_phase<T, false>(d, make_view<T>(ctl), sm, d.part_c2);
   if (!is_last_block(&ctl->cnt_c2)) return;
   __shared__ double red[kNC1 + kNC2];
   reduce_two<kNC1, kNC2>(d.part_c1, d.grid_c1, d.part_c2, d.grid_c2, red);
   fill_step_factors(ctl, d.step_fac, d.n_check);
   if (threadIdx.x == 0) {
+    if (std::is_same<T, float>::value) sync_step_state(ctl);
     check_control(ctl, red, d.trace_checks, d.trace_cap);
     ctl->cnt_c2 = 0;
   }
@@ -592,8 +621,11 @@ __global__ void __launch_bounds__(kPThreads, 1) k_solve_persistent(DevLP<T> d, G
                                                                   unsigned long long limit_ns) {
   extern __shared__ double psm[];  // 2 * kPWarps * kSmemPerWarp doubles
   __shared__ Control sc;
-  __shared__ double fac[2 * kMaxNcheckPersistent];
+  __shared__ double fac[3 * kMaxNcheckPersistent];  // FP64 factors, then FP32 copies
   __shared__ double red[kNC1 + kNC2];
+  typedef typename AccOf<T>::type A;
+  __shared__ A sred[kNP + kND];
+  __shared__ StepPre spre;
   const int nb = gridDim.x;
   double* pp = d.pp_part;  // [2][nb] primal, [2][2nb] dual, [10 nb] cols, [8 nb] rows
   double* part_p[2] = {pp, pp + nb};
@@ -610,7 +642,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_solve_persistent(DevLP<T> d, G
   bool do_check = true;  // the start point is evaluated first
   while (ok) {
     if (do_check) {
-      const SlotView v = make_view(&sc);
+      const SlotView<T> v = make_view<T>(&sc);
       check_cols_phase<T, true>(d, v, psm, part_c1, &hash[hslot]);
       ok = grid_sync(bar, limit_ns);
       if (!ok) break;
@@ -621,6 +653,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_solve_persistent(DevLP<T> d, G
       fill_step_factors(&sc, fac, d.n_check);
       if (threadIdx.x == 0) {
         sc.hash_accum = __ldcg(&hash[hslot]);
+        if (std::is_same<T, float>::value) sync_step_state(&sc);
         if (lead) hash[hslot ^ 1] = 0ULL;  // the next check's slot; nobody reads it now
         check_control(&sc, red, lead ? d.trace_checks : nullptr, d.trace_cap);
       }
@@ -635,16 +668,17 @@ __global__ void __launch_bounds__(kPThreads, 1) k_solve_persistent(DevLP<T> d, G
       continue;
     }
     const int par = int(sc.k & 1);
-    const SlotView v = make_view(&sc);
-    primal_phase<T, true>(d, v, reinterpret_cast<T*>(psm), part_p[par]);
+    const SlotView<T> v = make_view<T>(&sc);
+    primal_phase<T, true>(d, v, reinterpret_cast<T*>(psm), acc_part<T>(part_p[par]));
     ok = grid_sync(bar, limit_ns);
     if (!ok) break;
-    dual_phase<T, true>(d, v, reinterpret_cast<T*>(psm), part_d[par]);
+    dual_phase<T, true>(d, v, reinterpret_cast<T*>(psm), acc_part<T>(part_d[par]));
     ok = grid_sync(bar, limit_ns);
     if (!ok) break;
-    reduce_two<kNP, kND>(part_p[par], nb, part_d[par], nb, red);
-    if (threadIdx.x == 0) step_control(&sc, red[0], red[1], red[2], fac, d.n_check, lead ? d.trace_steps : nullptr,
-                                       d.trace_cap);
+    if (threadIdx.x == 0) spre = step_pre<A>(&sc, fac, d.n_check);
+    reduce_step<A>(acc_part<T>(part_p[par]), nb, acc_part<T>(part_d[par]), nb, reinterpret_cast<A*>(psm), sred);
+    if (threadIdx.x == 0) step_control<A>(&sc, spre, sred[0], sred[1], sred[2], lead ? d.trace_steps : nullptr,
+                                          d.trace_cap);
     __syncthreads();
     ++since;
   }
@@ -689,6 +723,7 @@ __global__ void k_solve_init(Control* c, double tol, long long iter_limit, int s
   c->hash_accum = 0ULL;
   c->same_hash = 0;
   c->cnt_dual = c->cnt_c2 = c->cnt_misc = 0;
+  derive_steps(c);
 }
 
 // ------------------------------------------------------------ state access ---
@@ -1348,6 +1383,7 @@ __global__ void k_binit(DevBatch<T> B, double tol, long long iter_limit, int sta
   c->copy_lr = 0;
   c->hash_accum = 0ULL;
   c->same_hash = 0;
+  derive_steps(c);
   write_slot(&B.slot[b], c);
 }
 

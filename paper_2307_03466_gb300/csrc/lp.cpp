@@ -369,7 +369,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     lp->io_x = ar.take<double>(n);
     lp->io_y = ar.take<double>(m);
     lp->ctl = ar.take<Control>(1);
-    lp->step_fac = ar.take<double>(2 * size_t(lp->p.n_check));
+    lp->step_fac = ar.take<double>(3 * size_t(lp->p.n_check));  // FP64 factors, then FP32 copies
     lp->pp_part = ar.take<double>(size_t(kPersistentPartials) * std::max(lp->p_grid, 1));
     lp->p_hash = ar.take<unsigned long long>(2);
     lp->grid_bar = ar.take<char>(kGridBarBytes);
