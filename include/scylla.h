@@ -106,7 +106,8 @@ typedef struct {
   double device_wait_limit_s;   /* bound of every device-side barrier wait (5) */
   int32_t pdl;                  /* launch the per-attempt kernels with programmatic dependent launch, so
                                    each one is resident before its predecessor ends (1) */
-  int32_t reserved1;
+  int32_t prefetch;             /* 0: load each warp's first matrix tile before the wait on the preceding
+                                   kernel when A and A^T fit in half the L2 cache; 1: always; 2: never (0) */
 } scylla_params;
 
 typedef struct {

@@ -33,6 +33,7 @@ CPP_SOURCES = ["lp.cpp", "fixprop.cpp", "pump.cpp", "batch.cpp", "fanout.cpp"]
 def _sources():
     return [os.path.join(CSRC, f) for f in CU_SOURCES + CPP_SOURCES] + \
         [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "lp_handle.h"), os.path.join(CSRC, "device_common.cuh"),
+         os.path.join(CSRC, "host_par.h"),
          os.path.join(INCLUDE, "scylla.h")]
 
 
@@ -63,7 +64,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(BUILD, f + ".o")
         objs.append(o)
         cxx = shutil.which("g++") or "g++"
-        cmd = [cxx, "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall", "-Wno-unused-function",
+        cmd = [cxx, "-O2", "-std=c++17", "-fPIC", "-pthread", "-ffp-contract=off", "-Wall", "-Wno-unused-function",
                "-I", INCLUDE, "-I", CSRC, "-I", os.path.join(CUDA_HOME, "include"), "-c",
                os.path.join(CSRC, f), "-o", o]
         jobs.append(cmd)
@@ -79,7 +80,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         msg = "\n".join(" ".join(c) + "\n" + o for c, o in failed)
         raise RuntimeError("native build failed:\n" + msg)
     tmp = LIB + ".tmp"
-    link = [NVCC, "-shared", *ARCH, "-o", tmp, *objs, "-cudart", "static"]
+    link = [NVCC, "-shared", *ARCH, "-o", tmp, *objs, "-cudart", "static", "-lpthread"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + " ".join(link) + "\n" + r.stdout)

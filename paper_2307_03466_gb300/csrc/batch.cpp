@@ -234,7 +234,7 @@ int create_batch(int32_t count, const scylla_csr* A, const double* const* c, con
   int *a_rowptr, *a_cols, *t_rowptr, *t_cols, *a_tlp, *t_tlp, *a_beg, *t_beg, *n_done;
   int2 *a_tiles, *t_tiles;
   double *a_vals64, *t_vals64, *c_un, *l_un, *u_un, *lo_un, *hi_un, *c64, *l64, *u64, *lo64, *hi64;
-  double *R, *C, *R2, *C2, *red, *step_fac, *tp_p, *tp_d, *tp_c1, *tp_c2;
+  double *R, *C, *invR, *invC, *R2, *C2, *red, *step_fac, *tp_p, *tp_d, *tp_c1, *tp_c2;
   float *a_vals32 = nullptr, *t_vals32 = nullptr, *c32 = nullptr, *l32 = nullptr, *u32 = nullptr, *lo32 = nullptr,
         *hi32 = nullptr;
   uint8_t* int_mask;
@@ -281,6 +281,8 @@ int create_batch(int32_t count, const scylla_csr* A, const double* const* c, con
     hi64 = ar.take<double>(m);
     R = ar.take<double>(m);
     C = ar.take<double>(n);
+    invR = ar.take<double>(m);
+    invC = ar.take<double>(n);
     R2 = ar.take<double>(std::max(m, n));
     C2 = ar.take<double>(std::max(m, n));
     red = ar.take<double>(2 * size_t(red_blocks));
@@ -340,7 +342,7 @@ int create_batch(int32_t count, const scylla_csr* A, const double* const* c, con
   v.c = c_un; v.lo = lo_un; v.hi = hi_un; v.l = l_un; v.u = u_un;
   v.c64 = c64; v.lo64 = lo64; v.hi64 = hi64; v.l64 = l64; v.u64 = u64;
   v.c32 = c32; v.lo32 = lo32; v.hi32 = hi32; v.l32 = l32; v.u32 = u32;
-  v.R = R; v.C = C; v.m = m; v.n = n;
+  v.R = R; v.C = C; v.invR = invR; v.invC = invC; v.m = m; v.n = n;
   CKB(launch_scale_vectors(v, st));
   // per-LP initial step size and primal weight from the scaled data, and the norms
   // of the relative KKT error from the original data
@@ -395,7 +397,7 @@ int create_batch(int32_t count, const scylla_csr* A, const double* const* c, con
     d.a_rowptr = a_rowptr; d.a_cols = a_cols; d.a_tiles = a_tiles; d.a_ntiles = a_nt;
     d.t_rowptr = t_rowptr; d.t_cols = t_cols; d.t_tiles = t_tiles; d.t_ntiles = t_nt;
     d.a_vals64 = a_vals64; d.t_vals64 = t_vals64;
-    d.c64 = c64; d.l64 = l64; d.u64 = u64; d.lo64 = lo64; d.hi64 = hi64; d.R = R; d.C = C;
+    d.c64 = c64; d.l64 = l64; d.u64 = u64; d.lo64 = lo64; d.hi64 = hi64; d.R = R; d.C = C; d.invR = invR; d.invC = invC;
     d.int_mask = int_mask;
     d.step_fac = step_fac;
     d.n_check = h->p.n_check;

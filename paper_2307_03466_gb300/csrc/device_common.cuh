@@ -45,6 +45,21 @@ __device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
   o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
 }
 
+// float -> double without the FP64 pipe (where a conversion costs as much as an FP64
+// add): sign, exponent rebiased by 1023 - 127, mantissa shifted into place; exact for
+// zeros and normal numbers, which is all the iterates hold; subnormals, infinities and
+// NaNs take the hardware conversion
+__device__ __forceinline__ double to_f64(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int e = (b >> 23) & 0xffu, man = b & 0x7fffffu;
+  if (e == 0xffu || (e == 0u && man != 0u)) return double(f);
+  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+  const unsigned long long body =
+      e == 0u ? 0ULL : ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)man << 29);
+  return __longlong_as_double((long long)(sign | body));
+}
+__device__ __forceinline__ double to_f64(double d) { return d; }
+
 __device__ __forceinline__ int skew(int q) { return q + (q >> 5); }
 
 template <typename T>
@@ -143,33 +158,53 @@ __device__ __forceinline__ bool is_last_block(unsigned int* counter) {
   return last != 0;
 }
 
-// sums of two partial arrays (NA values over na blocks, NB over nb) in one pass by
-// the whole (last) block: each thread accumulates a fixed strided subset, then one
-// fixed-order block reduction of all NA + NB values
+// sums of two partial arrays (NA values over na blocks, NB over nb) by warps 1.. of
+// the (last) block, in a fixed order: each thread loads a strided subset (the first
+// two blocks' values before summing any), the per-thread sums go to scratch
+// (N * (blockDim.x - 32) doubles), then each warp reduces whole columns across its
+// lanes.  Warp 0 is left free; every thread leaves with out[0..N-1] valid.
 template <int NA, int NB>
-static __device__ void reduce_two(const double* pa, int na, const double* pb, int nb, double* out_shared) {
+static __device__ void reduce_two(const double* pa, int na, const double* pb, int nb, double* scratch,
+                                  double* out) {
   constexpr int N = NA + NB;
-  __shared__ double sh[kMaxWarps][N];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double s[N];
+  const int nt = blockDim.x - 32, t = threadIdx.x - 32;
+  if (t >= 0) {
+    double s[N];
 #pragma unroll
-  for (int k = 0; k < N; ++k) s[k] = 0.0;
-  for (int b = threadIdx.x; b < na; b += blockDim.x)
+    for (int k = 0; k < N; ++k) s[k] = 0.0;
+    constexpr int kR = 2;
+    double va[kR][NA], vb[kR][NB];
 #pragma unroll
-    for (int k = 0; k < NA; ++k) s[k] += __ldcg(pa + b * NA + k);
-  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+    for (int r = 0; r < kR; ++r) {
+      const int b = t + r * nt;
 #pragma unroll
-    for (int k = 0; k < NB; ++k) s[NA + k] += __ldcg(pb + b * NB + k);
+      for (int k = 0; k < NA; ++k) va[r][k] = b < na ? __ldcg(pa + b * NA + k) : 0.0;
 #pragma unroll
-  for (int k = 0; k < N; ++k) {
-    const double t = warp_sum(s[k]);
-    if (lane == 0) sh[w][k] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x < N) {
-    double t = 0.0;
-    for (int i = 0; i < nw; ++i) t += sh[i][threadIdx.x];
-    out_shared[threadIdx.x] = t;
+      for (int k = 0; k < NB; ++k) vb[r][k] = b < nb ? __ldcg(pb + b * NB + k) : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+#pragma unroll
+      for (int k = 0; k < NA; ++k) s[k] += va[r][k];
+#pragma unroll
+      for (int k = 0; k < NB; ++k) s[NA + k] += vb[r][k];
+    }
+    for (int b = t + kR * nt; b < na; b += nt)
+#pragma unroll
+      for (int k = 0; k < NA; ++k) s[k] += __ldcg(pa + b * NA + k);
+    for (int b = t + kR * nt; b < nb; b += nt)
+#pragma unroll
+      for (int k = 0; k < NB; ++k) s[NA + k] += __ldcg(pb + b * NB + k);
+#pragma unroll
+    for (int k = 0; k < N; ++k) scratch[k * nt + t] = s[k];
+    asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
+    const int w = t >> 5, lane = t & 31, nw = nt >> 5;
+    for (int k = w; k < N; k += nw) {
+      double v = 0.0;
+      for (int i = lane; i < nt; i += 32) v += scratch[k * nt + i];
+      v = warp_sum(v);
+      if (lane == 0) out[k] = v;
+    }
   }
   __syncthreads();
 }
@@ -441,22 +476,43 @@ static __device__ void step_control(Control* c, double dx2, double dy2, double i
   step_control<double>(c, p, dx2, dy2, inter, trace, cap);
 }
 
-// step-size factor table for attempts k+1 .. k+n_check (by the whole last block)
-// (FP64 values, then FP32 copies); thread 0 also stores attempt k+1's FP32 factors
-static __device__ void fill_step_factors(Control* c, double* fac, int n_check) {
+// step-size factor table for attempts k+1 .. k+n_check (by the whole last block):
+// 2 n_check FP64 values, then 2 n_check FP32 values; attempt k+1's FP32 factors also
+// go to the control block.  The FP32-mixed mode needs only the FP32 table, from
+// powf; the FP64 mode computes one FP64 power per thread (each is a long serial
+// chain on this part) and rounds it for the FP32 copy.
+template <typename T>
+static __device__ void fill_step_factors(Control* c, double* fac, int n_check);
+
+template <>
+__device__ void fill_step_factors<float>(Control* c, double* fac, int n_check) {
   const long long k = c->k;
+  const float er = float(c->exp_red), eg = float(c->exp_grow);
   float* facf = reinterpret_cast<float*>(fac + 2 * n_check);
   for (int i = threadIdx.x; i < n_check; i += blockDim.x) {
-    const double kk = double(k + 1 + i + 1);
-    const double fr = 1.0 - pow(kk, -c->exp_red), fg = 1.0 + pow(kk, -c->exp_grow);
-    fac[2 * i] = fr;
-    fac[2 * i + 1] = fg;
-    facf[2 * i] = float(fr);
-    facf[2 * i + 1] = float(fg);
+    const float kk = float(k + 1 + i + 1);
+    const float fr = 1.0f - powf(kk, -er), fg = 1.0f + powf(kk, -eg);
+    facf[2 * i] = fr;
+    facf[2 * i + 1] = fg;
     if (i == 0) {
-      c->fr_f = float(fr);
-      c->fg_f = float(fg);
+      c->fr_f = fr;
+      c->fg_f = fg;
     }
+  }
+  if (threadIdx.x == 0) c->k_fac = k;
+}
+
+template <>
+__device__ void fill_step_factors<double>(Control* c, double* fac, int n_check) {
+  const long long k = c->k;
+  float* facf = reinterpret_cast<float*>(fac + 2 * n_check);
+  for (int q = threadIdx.x; q < 2 * n_check; q += blockDim.x) {
+    const double kk = double(k + 1 + (q >> 1) + 1);
+    const double v = (q & 1) ? 1.0 + pow(kk, -c->exp_grow) : 1.0 - pow(kk, -c->exp_red);
+    fac[q] = v;
+    facf[q] = float(v);
+    if (q == 0) c->fr_f = float(v);
+    if (q == 1) c->fg_f = float(v);
   }
   if (threadIdx.x == 0) c->k_fac = k;
 }
@@ -492,33 +548,38 @@ static __device__ void finish(Control* c, int status, bool out_avg, const Eval& 
   }
 }
 
-// Termination (Section 2.2), stalling (Algorithm 1) and restarts (PDLP) from the
-// 18 reduced sums of the two check kernels.
-static __device__ void check_control_impl(Control* c, const double* r, double* trace, int cap) {
-  Eval e[2];
-  for (int q = 0; q < 2; ++q) {
-    const double* cs = r + 5 * q;
-    const double* rs = r + kNC1 + 4 * q;
-    e[q].rd_s2 = cs[0];
-    e[q].rd2 = cs[1];
-    e[q].pobj = cs[2] + c->offset;
-    e[q].dobj = (rs[2] + cs[3]) + c->offset;
-    e[q].dx2 = cs[4];
-    e[q].rp_s2 = rs[0];
-    e[q].rp2 = rs[1];
-    e[q].dy2 = rs[3];
-    e[q].eps_p = sqrt(e[q].rp2) / (1.0 + c->bnorm);
-    e[q].eps_d = sqrt(e[q].rd2) / (1.0 + c->cnorm);
-    e[q].eps_g = fabs(e[q].pobj - e[q].dobj) / (1.0 + fabs(e[q].pobj) + fabs(e[q].dobj));
-    e[q].rel = fmax(e[q].eps_p, fmax(e[q].eps_d, e[q].eps_g));
-  }
+// Evaluation q (0: current point, 1: averaged point) of a check from the 18 reduced
+// sums of the two check kernels: relative KKT parts (Section 2.2) and the quantities
+// the restart rule needs.
+__device__ __forceinline__ Eval make_eval(const Control* c, const double* r, int q) {
+  Eval e;
+  const double* cs = r + 5 * q;
+  const double* rs = r + kNC1 + 4 * q;
+  e.rd_s2 = cs[0];
+  e.rd2 = cs[1];
+  e.pobj = cs[2] + c->offset;
+  e.dobj = (rs[2] + cs[3]) + c->offset;
+  e.dx2 = cs[4];
+  e.rp_s2 = rs[0];
+  e.rp2 = rs[1];
+  e.dy2 = rs[3];
+  e.eps_p = sqrt(e.rp2) / (1.0 + c->bnorm);
+  e.eps_d = sqrt(e.rd2) / (1.0 + c->cnorm);
+  e.eps_g = fabs(e.pobj - e.dobj) / (1.0 + fabs(e.pobj) + fabs(e.dobj));
+  e.rel = fmax(e.eps_p, fmax(e.eps_d, e.eps_g));
+  return e;
+}
+
+// Termination (Section 2.2), stalling (Algorithm 1) and restarts (PDLP) from the two
+// evaluations and their weighted KKT errors wk[q] at the current primal weight.
+static __device__ void check_control_impl(Control* c, const Eval* e, const double* wk, double* trace, int cap) {
   const unsigned long long h = c->hash_accum;
   c->hash_accum = 0ULL;
   c->aty_valid = 1;
   if (c->initial) {
     c->initial = 0;
     c->avg_w = 0.0;
-    const double kc = weighted_kkt(e[0], c->omega);
+    const double kc = wk[0];
     c->kkt_lr = kc;
     c->kkt_prev = kc;
     c->k_lr = 0;
@@ -546,10 +607,10 @@ static __device__ void check_control_impl(Control* c, const double* r, double* t
   if (c->stall_checks > 0 && c->same_hash >= c->stall_checks) { finish(c, SCYLLA_STALLED, out_avg, eo); return; }
   if (!c->restarts_on) return;
   const double om = c->omega;
-  const double kc_cur = weighted_kkt(e[0], om);
-  const bool cand_avg = has_avg && weighted_kkt(e[1], om) < kc_cur;
+  const double kc_cur = wk[0];
+  const bool cand_avg = has_avg && wk[1] < kc_cur;
   const Eval& ec = cand_avg ? e[1] : e[0];
-  const double kc = weighted_kkt(ec, om);
+  const double kc = cand_avg ? wk[1] : wk[0];
   const bool restart = kc <= c->beta_s * c->kkt_lr || (kc <= c->beta_n * c->kkt_lr && kc > c->kkt_prev) ||
                        double(c->k - c->k_lr) >= c->beta_a * double(c->k);
   double* rec = nullptr;
@@ -568,9 +629,13 @@ static __device__ void check_control_impl(Control* c, const double* r, double* t
   }
   c->restarts++;
   if (c->pw_update) {
+    // omega' = exp(theta log(ddy / ddx) + (1 - theta) log omega); for theta = 1/2 this
+    // is sqrt((ddy / ddx) omega), without the slow FP64 logarithms and exponential
     const double ddx = sqrt(ec.dx2), ddy = sqrt(ec.dy2);
-    if (ddx > 1e-10 && ddy > 1e-10)
-      c->omega = exp(c->theta * log(ddy / ddx) + (1.0 - c->theta) * log(om));
+    if (ddx > 1e-10 && ddy > 1e-10) {
+      if (c->theta == 0.5) c->omega = sqrt((ddy / ddx) * om);
+      else c->omega = exp(c->theta * log(ddy / ddx) + (1.0 - c->theta) * log(om));
+    }
   }
   if (cand_avg) {
     int t = c->ix_cur;
@@ -583,14 +648,36 @@ static __device__ void check_control_impl(Control* c, const double* r, double* t
   c->k_lr = c->k;
   c->wsum = 0.0;
   c->copy_lr = 1;
-  c->kkt_lr = weighted_kkt(ec, c->omega);
+  c->kkt_lr = c->omega == om ? kc : weighted_kkt(ec, c->omega);
   c->kkt_prev = c->kkt_lr;
   if (rec) rec[3] = c->omega;
 }
 
+// single-thread form (control kernels of the batched and fan-out solves)
 static __device__ void check_control(Control* c, const double* r, double* trace, int cap) {
-  check_control_impl(c, r, trace, cap);
+  const Eval e[2] = {make_eval(c, r, 0), make_eval(c, r, 1)};
+  const double wk[2] = {weighted_kkt(e[0], c->omega), weighted_kkt(e[1], c->omega)};
+  check_control_impl(c, e, wk, trace, cap);
   derive_steps(c);
+}
+
+// warp form: lanes 0 and 1 evaluate the two points side by side (their square roots
+// and divisions are long FP64 chains), lane 0 decides.  Called by a whole warp.
+static __device__ void check_control_warp(Control* c, const double* r, double* trace, int cap) {
+  __shared__ Eval se[2];
+  __shared__ double swk[2];
+  const int lane = threadIdx.x & 31;
+  if (lane < 2) {
+    const Eval e = make_eval(c, r, lane);
+    se[lane] = e;
+    swk[lane] = weighted_kkt(e, c->omega);
+  }
+  __syncwarp();
+  if (lane == 0) {
+    check_control_impl(c, se, swk, trace, cap);
+    derive_steps(c);
+  }
+  __syncwarp();
 }
 
 // per-thread accumulator type of the bulk kernels

@@ -220,6 +220,7 @@ bool check_feasible_host(const scylla_lp& lp, const double* x) {
 
 int fix_and_propagate_host(const scylla_lp& lp, const double* xbar, double* xhat, double* dom_lo, double* dom_hi,
                            int32_t* fixed_cols, int64_t* n_fixed, uint8_t* ignored_rows) {
+  lp.ensure_columns();
   Propagator pr(lp);
   for (int32_t i = 0; i < lp.m0; ++i) pr.push(i);
   pr.run();

@@ -88,6 +88,7 @@ struct DevLP {
   const double* t_vals64;
   const T *c, *l, *u, *lo, *hi;
   const double *c64, *l64, *u64, *lo64, *hi64, *R, *C;
+  const double *invR, *invC;  // 1 / R, 1 / C (the checks multiply instead of dividing)
   const unsigned char* int_mask;
   T* X[3];
   T* Y[3];
@@ -104,6 +105,7 @@ struct DevLP {
   unsigned long long* p_hash;  // persistent kernel: two rounding-hash slots
   int n_check;
   int pdl;               // launch the per-attempt kernels with programmatic dependent launch
+  int prefetch;          // per-attempt kernels load their first tile before the dependency wait
   double* trace_steps;   // 4 doubles per attempt, or null
   double* trace_checks;  // 5 doubles per check, or null
   int trace_cap;
@@ -193,6 +195,7 @@ struct DevVecs {
   double *c64, *lo64, *hi64, *l64, *u64;
   float *c32, *lo32, *hi32, *l32, *u32;  // null in FP64 mode
   const double *R, *C;
+  double *invR, *invC;  // outputs: 1 / R, 1 / C (optional)
   int m, n;
 };
 cudaError_t launch_scale_vectors(const DevVecs& v, cudaStream_t st);

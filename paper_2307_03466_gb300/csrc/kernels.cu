@@ -32,38 +32,73 @@ namespace scylla {
 // up to 12 gathers per lane are in flight.  Products go to a skewed per-warp
 // shared buffer and lane r sums row r in CSR order.  A single long row is reduced
 // across the warp with shuffles.  The epilogue has two halves: load(row) is issued
-// at the start of the tile, before the gathers, and finish(row, sum, pre) runs once
-// the row sum is known, on the lane that owns the row.
-template <int NV, typename Acc, typename V, typename Gather, typename Epi>
-__device__ __forceinline__ void spmv_tiles(const int2* __restrict__ tiles, int ntiles,
+// before the gathers, and finish(row, sum, pre) runs once the row sum is known, on
+// the lane that owns the row.
+//
+// pro() runs once per thread before the first gather (it waits for the preceding
+// kernel and sets up the gather and the epilogue; false ends the launch).  With PF
+// the immutable part of the warp's first tile (bounds, row ranges, column indices,
+// values) is loaded before pro(), so those loads overlap the wait.
+template <int NV, bool PF, typename Acc, typename V, typename Gather, typename Epi, typename Pro>
+__device__ __forceinline__ bool spmv_tiles(const int2* __restrict__ tiles, int ntiles,
                                            const int* __restrict__ rowptr, const int* __restrict__ cols,
                                            const V* __restrict__ vals, Gather& gat, Epi& epi,
-                                           Acc* __restrict__ sm) {
+                                           Acc* __restrict__ sm, Pro&& pro) {
   const int lane = threadIdx.x & 31;
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int t = gwarp; t < ntiles; t += nwarps) {
+  int r0 = 0, r1 = 0, p0 = 0, p1 = 0, q0 = 0, q1 = 0;
+  bool longrow = false;
+  // p1 - base <= kTileNnz + kVec - 1 < 3 * 32 * kVec: three vector steps cover a tile
+  int c[3][4];
+  V v[3][4];
+  auto fetch = [&](int t) {
     const int2 ta = __ldg(tiles + t), tb = __ldg(tiles + t + 1);
-    const int r0 = ta.x, r1 = tb.x, p0 = ta.y, p1 = tb.y;
+    r0 = ta.x;
+    r1 = tb.x;
+    p0 = ta.y;
+    p1 = tb.y;
+    longrow = r1 - r0 == 1 && p1 - p0 > kTileNnz;
+    if (!longrow) {
+      q0 = q1 = 0;
+      if (lane < r1 - r0) {
+        q0 = __ldg(rowptr + r0 + lane) - p0;
+        q1 = __ldg(rowptr + r0 + lane + 1) - p0;
+      }
+      const int base = p0 & ~(kVec - 1);
+#pragma unroll
+      for (int it = 0; it < 3; ++it) {
+        const int p = base + (it * 32 + lane) * kVec;
+        if (p < p1) {
+          ld4(cols + p, c[it]);
+          ld4(vals + p, v[it]);
+        }
+      }
+    }
+  };
+  if (PF && gwarp < ntiles) fetch(gwarp);
+  if (!pro()) return false;
+  for (int t = gwarp; t < ntiles; t += nwarps) {
+    if (!PF || t != gwarp) fetch(t);
     const int base = p0 & ~(kVec - 1);
-    if (r1 - r0 == 1 && p1 - p0 > kTileNnz) {
+    if (longrow) {
       const typename Epi::Pre pre = epi.load(r0);
       Acc s[NV];
 #pragma unroll
       for (int k = 0; k < NV; ++k) s[k] = Acc(0);
       for (int p = base + lane * kVec; p < p1; p += 32 * kVec) {
-        int c[4];
-        V v[4];
-        ld4(cols + p, c);
-        ld4(vals + p, v);
+        int cc[4];
+        V vv[4];
+        ld4(cols + p, cc);
+        ld4(vals + p, vv);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int q = p + e;
           if (q >= p0 && q < p1) {
             Acc g[NV];
-            gat(c[e], g);
+            gat(cc[e], g);
 #pragma unroll
-            for (int k = 0; k < NV; ++k) s[k] = fma_t<Acc>(Acc(v[e]), g[k], s[k]);
+            for (int k = 0; k < NV; ++k) s[k] = fma_t<Acc>(Acc(vv[e]), g[k], s[k]);
           }
         }
       }
@@ -73,24 +108,8 @@ __device__ __forceinline__ void spmv_tiles(const int2* __restrict__ tiles, int n
     } else {
       const bool mine = lane < r1 - r0;
       const int row = r0 + lane;
-      int q0 = 0, q1 = 0;
       typename Epi::Pre pre{};
-      if (mine) {
-        q0 = __ldg(rowptr + row) - p0;
-        q1 = __ldg(rowptr + row + 1) - p0;
-        pre = epi.load(row);
-      }
-      // p1 - base <= kTileNnz + kVec - 1 < 3 * 32 * kVec: three vector steps cover the tile
-      int c[3][4];
-      V v[3][4];
-#pragma unroll
-      for (int it = 0; it < 3; ++it) {
-        const int p = base + (it * 32 + lane) * kVec;
-        if (p < p1) {
-          ld4(cols + p, c[it]);
-          ld4(vals + p, v[it]);
-        }
-      }
+      if (mine) pre = epi.load(row);
 #pragma unroll
       for (int it = 0; it < 3; ++it) {
         const int p = base + (it * 32 + lane) * kVec;
@@ -115,6 +134,107 @@ __device__ __forceinline__ void spmv_tiles(const int2* __restrict__ tiles, int n
           const int o = skew(q);
 #pragma unroll
           for (int k = 0; k < NV; ++k) s[k] += sm[k * kSmemPerWarp + o];
+        }
+        epi.finish(row, s, pre);
+      }
+      __syncwarp();
+    }
+  }
+  return true;
+}
+
+struct NoPro {
+  __device__ __forceinline__ bool operator()() const { return true; }
+};
+
+// Check form of the gather over FP32 iterates: the multi-row path stores each FP64
+// value and the gathered FP32 entries, and every row sum is a chain of FP64 fused
+// multiply-adds of a value and an exactly converted entry, in CSR order (one FP64
+// instruction per nonzero and vector instead of a conversion, a product and a sum).
+// smw holds kSmemPerWarp doubles, then NV * kSmemPerWarp floats.
+template <int NV, typename Gather, typename Epi>
+__device__ __forceinline__ void spmv_tiles_fma(const int2* __restrict__ tiles, int ntiles,
+                                               const int* __restrict__ rowptr, const int* __restrict__ cols,
+                                               const double* __restrict__ vals, Gather& gat, Epi& epi,
+                                               double* __restrict__ smw) {
+  float* __restrict__ sg = reinterpret_cast<float*>(smw + kSmemPerWarp);
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int t = gwarp; t < ntiles; t += nwarps) {
+    const int2 ta = __ldg(tiles + t), tb = __ldg(tiles + t + 1);
+    const int r0 = ta.x, r1 = tb.x, p0 = ta.y, p1 = tb.y;
+    const int base = p0 & ~(kVec - 1);
+    if (r1 - r0 == 1 && p1 - p0 > kTileNnz) {
+      const typename Epi::Pre pre = epi.load(r0);
+      double s[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) s[k] = 0.0;
+      for (int p = base + lane * kVec; p < p1; p += 32 * kVec) {
+        int cc[4];
+        double vv[4];
+        ld4(cols + p, cc);
+        ld4(vals + p, vv);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int q = p + e;
+          if (q >= p0 && q < p1) {
+            float g[NV];
+            gat(cc[e], g);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) s[k] = __fma_rn(vv[e], to_f64(g[k]), s[k]);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NV; ++k) s[k] = warp_sum(s[k]);
+      if (lane == 0) epi.finish(r0, s, pre);
+    } else {
+      const bool mine = lane < r1 - r0;
+      const int row = r0 + lane;
+      int q0 = 0, q1 = 0;
+      typename Epi::Pre pre{};
+      if (mine) {
+        q0 = __ldg(rowptr + row) - p0;
+        q1 = __ldg(rowptr + row + 1) - p0;
+        pre = epi.load(row);
+      }
+      int c[3][4];
+      double v[3][4];
+#pragma unroll
+      for (int it = 0; it < 3; ++it) {
+        const int p = base + (it * 32 + lane) * kVec;
+        if (p < p1) {
+          ld4(cols + p, c[it]);
+          ld4(vals + p, v[it]);
+        }
+      }
+#pragma unroll
+      for (int it = 0; it < 3; ++it) {
+        const int p = base + (it * 32 + lane) * kVec;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int q = p + e;
+          if (q >= p0 && q < p1) {
+            float g[NV];
+            gat(c[it][e], g);
+            const int o = skew(q - p0);
+            smw[o] = v[it][e];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) sg[k * kSmemPerWarp + o] = g[k];
+          }
+        }
+      }
+      __syncwarp();
+      if (mine) {
+        double s[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[k] = 0.0;
+        for (int q = q0; q < q1; ++q) {
+          const int o = skew(q);
+          const double a = smw[o];
+#pragma unroll
+          for (int k = 0; k < NV; ++k) s[k] = __fma_rn(a, to_f64(sg[k * kSmemPerWarp + o]), s[k]);
         }
         epi.finish(row, s, pre);
       }
@@ -213,7 +333,7 @@ template <typename T>
 struct PrimalEpi {
   typedef typename AccOf<T>::type A;
   struct Pre {
-    T x, c, l, u;
+    T x, c, l, u, xa;
   };
   const T* __restrict__ xc;
   T* __restrict__ xn;
@@ -226,11 +346,13 @@ struct PrimalEpi {
   T tau, w, w1;
   bool do_avg, copy_lr, store_aty, use_cached;
   A acc;
-  __device__ __forceinline__ Pre load(int j) const { return Pre{xc[j], cc[j], ll[j], uu[j]}; }
+  __device__ __forceinline__ Pre load(int j) const {
+    return Pre{xc[j], cc[j], ll[j], uu[j], do_avg ? xa[j] : T(0)};
+  }
   __device__ __forceinline__ void finish(int j, const T (&s)[1], const Pre& p) {
     const T aty_j = use_cached ? aty[j] : s[0];
     if (store_aty) aty[j] = aty_j;
-    if (do_avg) xa[j] = blend(xa[j], p.x, w1, w);
+    if (do_avg) xa[j] = blend(p.xa, p.x, w1, w);
     if (copy_lr) xlr[j] = p.x;
     const T v = clampv<T>(p.x + tau * (aty_j - p.c), p.l, p.u);
     xn[j] = v;
@@ -270,8 +392,8 @@ __device__ __forceinline__ void primal_phase(const DevLP<T>& d, const SlotView<T
   } else {
     const T* __restrict__ yc = d.Y[v.cur];
     auto gat = [&](int i, T(&g)[1]) { g[0] = gload<Coh>(yc + i); };
-    spmv_tiles<1, T, T>(d.t_tiles, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals, gat, epi,
-                        sm + (threadIdx.x >> 5) * kSmemPerWarp);
+    spmv_tiles<1, false, T, T>(d.t_tiles, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals, gat, epi,
+                               sm + (threadIdx.x >> 5) * kSmemPerWarp, NoPro());
   }
   const typename AccOf<T>::type acc[kNP] = {epi.acc};
   block_store_partials<kNP>(acc, part);
@@ -281,7 +403,7 @@ template <typename T>
 struct DualEpi {
   typedef typename AccOf<T>::type A;
   struct Pre {
-    T ax, y, lo, hi;
+    T ax, y, lo, hi, ya;
   };
   const T* __restrict__ axc;
   T* __restrict__ axn;
@@ -294,10 +416,12 @@ struct DualEpi {
   T sigma, w, w1;
   bool do_avg, copy_lr;
   A acc0, acc1;
-  __device__ __forceinline__ Pre load(int i) const { return Pre{axc[i], yc[i], lo[i], hi[i]}; }
+  __device__ __forceinline__ Pre load(int i) const {
+    return Pre{axc[i], yc[i], lo[i], hi[i], do_avg ? ya[i] : T(0)};
+  }
   __device__ __forceinline__ void finish(int i, const T (&s)[1], const Pre& p) {
     const T ax_new = s[0];
-    if (do_avg) ya[i] = blend(ya[i], p.y, w1, w);
+    if (do_avg) ya[i] = blend(p.ya, p.y, w1, w);
     if (copy_lr) ylr[i] = p.y;
     const T axt = T(2) * ax_new - p.ax;
     const T v = dual_prox<T>(p.y, sigma, axt, p.lo, p.hi);
@@ -337,8 +461,8 @@ __device__ __forceinline__ void dual_phase(const DevLP<T>& d, const SlotView<T>&
   setup_dual(epi, d, v);
   const T* __restrict__ xn = d.X[v.nxt];
   auto gat = [&](int j, T(&g)[1]) { g[0] = gload<Coh>(xn + j); };
-  spmv_tiles<1, T, T>(d.a_tiles, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals, gat, epi,
-                      sm + (threadIdx.x >> 5) * kSmemPerWarp);
+  spmv_tiles<1, false, T, T>(d.a_tiles, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals, gat, epi,
+                             sm + (threadIdx.x >> 5) * kSmemPerWarp, NoPro());
   const typename AccOf<T>::type acc[kND] = {epi.acc0, epi.acc1};
   block_store_partials<kND>(acc, part);
 }
@@ -351,25 +475,68 @@ __device__ __forceinline__ typename AccOf<T>::type* acc_part(double* p) {
   return reinterpret_cast<typename AccOf<T>::type*>(p);
 }
 
-template <typename T>
+template <typename T, bool PF>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_primal(DevLP<T> d) {
   Control* ctl = d.ctl;
-  pdl_enter();
-  if (ctl->done || ctl->k >= ctl->iter_limit) return;
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
-  primal_phase<T, false>(d, make_view<T>(ctl), sm, acc_part<T>(d.part_p));
+  if (!PF) {
+    pdl_enter();
+    if (ctl->done || ctl->k >= ctl->iter_limit) return;
+    primal_phase<T, false>(d, make_view<T>(ctl), sm, acc_part<T>(d.part_p));
+    return;
+  }
+  // prefetching form: the gather of A^T y is taken even when A^T y is cached (a
+  // retry), and its result is then ignored
+  PrimalEpi<T> epi;
+  const T* __restrict__ yc = nullptr;
+  bool cached = false;
+  auto gat = [&](int i, T(&g)[1]) { g[0] = cached ? T(0) : __ldg(yc + i); };
+  auto pro = [&]() -> bool {
+    pdl_enter();
+    if (ctl->done || ctl->k >= ctl->iter_limit) return false;
+    const SlotView<T> v = make_view<T>(ctl);
+    setup_primal(epi, d, v);
+    cached = v.aty_valid != 0;
+    epi.use_cached = cached;
+    yc = d.Y[v.cur];
+    return true;
+  };
+  if (!spmv_tiles<1, true, T, T>(d.t_tiles, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals, gat, epi,
+                                 sm + (threadIdx.x >> 5) * kSmemPerWarp, pro))
+    return;
+  const typename AccOf<T>::type acc[kNP] = {epi.acc};
+  block_store_partials<kNP>(acc, acc_part<T>(d.part_p));
 }
 
 // The last block to finish reduces all block partials (warps 1..) while thread 0
 // gathers the decision's other inputs, then takes the step-size decision.
-template <typename T>
+template <typename T, bool PF>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_dual(DevLP<T> d) {
   typedef typename AccOf<T>::type A;
   Control* ctl = d.ctl;
-  pdl_enter();
-  if (ctl->done || ctl->k >= ctl->iter_limit) return;
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
-  dual_phase<T, false>(d, make_view<T>(ctl), sm, acc_part<T>(d.part_d));
+  if (!PF) {
+    pdl_enter();
+    if (ctl->done || ctl->k >= ctl->iter_limit) return;
+    dual_phase<T, false>(d, make_view<T>(ctl), sm, acc_part<T>(d.part_d));
+  } else {
+    DualEpi<T> epi;
+    const T* __restrict__ xn = nullptr;
+    auto gat = [&](int j, T(&g)[1]) { g[0] = __ldg(xn + j); };
+    auto pro = [&]() -> bool {
+      pdl_enter();
+      if (ctl->done || ctl->k >= ctl->iter_limit) return false;
+      const SlotView<T> v = make_view<T>(ctl);
+      setup_dual(epi, d, v);
+      xn = d.X[v.nxt];
+      return true;
+    };
+    if (!spmv_tiles<1, true, T, T>(d.a_tiles, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals, gat, epi,
+                                   sm + (threadIdx.x >> 5) * kSmemPerWarp, pro))
+      return;
+    const A acc[kND] = {epi.acc0, epi.acc1};
+    block_store_partials<kND>(acc, acc_part<T>(d.part_d));
+  }
   if (!is_last_block(&ctl->cnt_dual)) return;
   __shared__ StepPre pre;  // in shared memory: nothing stays live in registers across the reduction
   if (threadIdx.x == 0) pre = step_pre<A>(ctl, d.step_fac, d.n_check);
@@ -382,6 +549,22 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_dual(DevLP<T>
   }
 }
 
+// the two-vector FP64 gather of a check: FP32 iterates take the fused form; FP64
+// iterates the product form (their gathered entries need no conversion)
+template <typename Gather, typename Epi>
+__device__ __forceinline__ void check_gather(const int2* tiles, int ntiles, const int* rowptr, const int* cols,
+                                             const double* vals, Gather& gat, Epi& epi, double* smw,
+                                             const float* /*tag*/) {
+  spmv_tiles_fma<2>(tiles, ntiles, rowptr, cols, vals, gat, epi, smw);
+}
+template <typename Gather, typename Epi>
+__device__ __forceinline__ void check_gather(const int2* tiles, int ntiles, const int* rowptr, const int* cols,
+                                             const double* vals, Gather& gat, Epi& epi, double* smw,
+                                             const double* /*tag*/) {
+  auto gat64 = [&](int i, double(&g)[2]) { gat(i, g); };
+  spmv_tiles<2, false, double, double>(tiles, ntiles, rowptr, cols, vals, gat64, epi, smw, NoPro());
+}
+
 template <typename T>
 struct CheckColsEpi {
   struct Pre {};
@@ -390,7 +573,7 @@ struct CheckColsEpi {
   T* __restrict__ aty_c;
   T* __restrict__ aty_a;
   const T* __restrict__ xlr;
-  const double *C, *c64, *l64, *u64;
+  const double *C, *invC, *c64, *l64, *u64;
   const unsigned char* int_mask;
   T w, w1;
   bool do_avg;
@@ -406,22 +589,22 @@ struct CheckColsEpi {
     }
     aty_c[j] = T(s[0]);
     aty_a[j] = T(s[1]);
-    const double Cj = C[j], cj = c64[j], lj = l64[j], uj = u64[j], xl = double(xlr[j]);
-    const double xs[2] = {double(x), double(xav)};
+    const double Cj = C[j], iCj = invC[j], cj = c64[j], lj = l64[j], uj = u64[j], xl = to_f64(xlr[j]);
+    const double xs[2] = {to_f64(x), to_f64(xav)};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const double r = cj - s[q];
       const double lam = rc_proj(r, lj, uj);
       const double rd = r - lam;
       acc[5 * q + 0] += rd * rd;
-      const double rdu = rd / Cj;
+      const double rdu = rd * iCj;
       acc[5 * q + 1] += rdu * rdu;
       acc[5 * q + 2] += cj * xs[q];
       acc[5 * q + 3] += (lam > 0.0 ? lj * lam : 0.0) - (lam < 0.0 ? uj * (-lam) : 0.0);
       const double dd = xs[q] - xl;
       acc[5 * q + 4] += dd * dd;
     }
-    if (int_mask[j]) h += round_hash(j, double(x) * Cj);
+    if (int_mask[j]) h += round_hash(j, xs[0] * Cj);
   }
 };
 
@@ -442,6 +625,7 @@ __device__ __forceinline__ void check_cols_phase(const DevLP<T>& d, const SlotVi
   epi.aty_a = d.ATY[v.ia_avg];
   epi.xlr = d.XLR;
   epi.C = d.C;
+  epi.invC = d.invC;
   epi.c64 = d.c64;
   epi.l64 = d.l64;
   epi.u64 = d.u64;
@@ -452,15 +636,15 @@ __device__ __forceinline__ void check_cols_phase(const DevLP<T>& d, const SlotVi
 #pragma unroll
   for (int k = 0; k < kNC1; ++k) epi.acc[k] = 0.0;
   epi.h = 0ULL;
-  auto gat = [&](int i, double(&g)[2]) {
+  auto gat = [&](int i, T(&g)[2]) {
     const T y = gload<Coh>(yc + i);
     T av = gload<Coh>(ya + i);
     if (do_avg) av = blend(av, y, w1, w);
-    g[0] = double(y);
-    g[1] = double(av);
+    g[0] = y;
+    g[1] = av;
   };
-  spmv_tiles<2, double, double>(d.t_tiles, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals64, gat, epi,
-                                sm + (threadIdx.x >> 5) * 2 * kSmemPerWarp);
+  check_gather(d.t_tiles, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals64, gat, epi,
+               sm + (threadIdx.x >> 5) * 2 * kSmemPerWarp, static_cast<const T*>(nullptr));
   block_store_partials<kNC1>(epi.acc, part);
   const unsigned long long h = warp_sum_u64(epi.h);
   if ((threadIdx.x & 31) == 0 && h != 0ULL) atomicAdd(hash, h);
@@ -474,7 +658,7 @@ struct CheckRowsEpi {
   T* __restrict__ ax_c;
   T* __restrict__ ax_a;
   const T* __restrict__ ylr;
-  const double *R, *lo64, *hi64;
+  const double *invR, *lo64, *hi64;
   T w, w1;
   bool do_avg;
   double acc[kNC2];
@@ -488,13 +672,13 @@ struct CheckRowsEpi {
     }
     ax_c[i] = T(s[0]);
     ax_a[i] = T(s[1]);
-    const double Ri = R[i], lo = lo64[i], hi = hi64[i], yl = double(ylr[i]);
-    const double ys[2] = {double(y), double(yav)};
+    const double iRi = invR[i], lo = lo64[i], hi = hi64[i], yl = to_f64(ylr[i]);
+    const double ys[2] = {to_f64(y), to_f64(yav)};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const double rps = s[q] - clampv<double>(s[q], lo, hi);
       acc[4 * q + 0] += rps * rps;
-      const double rp = rps / Ri;
+      const double rp = rps * iRi;
       acc[4 * q + 1] += rp * rp;
       acc[4 * q + 2] += (ys[q] > 0.0 ? lo * ys[q] : 0.0) - (ys[q] < 0.0 ? hi * (-ys[q]) : 0.0);
       const double dd = ys[q] - yl;
@@ -515,7 +699,7 @@ __device__ __forceinline__ void check_rows_phase(const DevLP<T>& d, const SlotVi
   epi.ax_c = d.AX[v.cur];
   epi.ax_a = d.AX[v.avg];
   epi.ylr = d.YLR;
-  epi.R = d.R;
+  epi.invR = d.invR;
   epi.lo64 = d.lo64;
   epi.hi64 = d.hi64;
   epi.w = v.w;
@@ -523,12 +707,12 @@ __device__ __forceinline__ void check_rows_phase(const DevLP<T>& d, const SlotVi
   epi.do_avg = v.do_avg;
 #pragma unroll
   for (int k = 0; k < kNC2; ++k) epi.acc[k] = 0.0;
-  auto gat = [&](int j, double(&g)[2]) {
-    g[0] = double(gload<Coh>(xc + j));
-    g[1] = double(gload<Coh>(xa + j));
+  auto gat = [&](int j, T(&g)[2]) {
+    g[0] = gload<Coh>(xc + j);
+    g[1] = gload<Coh>(xa + j);
   };
-  spmv_tiles<2, double, double>(d.a_tiles, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals64, gat, epi,
-                                sm + (threadIdx.x >> 5) * 2 * kSmemPerWarp);
+  check_gather(d.a_tiles, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals64, gat, epi,
+               sm + (threadIdx.x >> 5) * 2 * kSmemPerWarp, static_cast<const T*>(nullptr));
   block_store_partials<kNC2>(epi.acc, part);
 }
 
@@ -550,12 +734,14 @@ __global__ void __launch_bounds__(kThreads) k_check_rows(DevLP<T> d) {
   check_rows_phase<T, false>(d, make_view<T>(ctl), sm, d.part_c2);
   if (!is_last_block(&ctl->cnt_c2)) return;
   __shared__ double red[kNC1 + kNC2];
-  reduce_two<kNC1, kNC2>(d.part_c1, d.grid_c1, d.part_c2, d.grid_c2, red);
-  fill_step_factors(ctl, d.step_fac, d.n_check);
-  if (threadIdx.x == 0) {
-    if (std::is_same<T, float>::value) sync_step_state(ctl);
-    check_control(ctl, red, d.trace_checks, d.trace_cap);
-    ctl->cnt_c2 = 0;
+  static_assert((kNC1 + kNC2) * (kThreads - 32) <= 2 * kWarpsPerBlock * kSmemPerWarp, "reduction scratch");
+  reduce_two<kNC1, kNC2>(d.part_c1, d.grid_c1, d.part_c2, d.grid_c2, sm, red);
+  fill_step_factors<T>(ctl, d.step_fac, d.n_check);
+  if (threadIdx.x < 32) {
+    if (threadIdx.x == 0 && std::is_same<T, float>::value) sync_step_state(ctl);
+    __syncwarp();
+    check_control_warp(ctl, red, d.trace_checks, d.trace_cap);
+    if (threadIdx.x == 0) ctl->cnt_c2 = 0;
   }
 }
 
@@ -649,13 +835,17 @@ __global__ void __launch_bounds__(kPThreads, 1) k_solve_persistent(DevLP<T> d, G
       check_rows_phase<T, true>(d, v, psm, part_c2);
       ok = grid_sync(bar, limit_ns);
       if (!ok) break;
-      reduce_two<kNC1, kNC2>(part_c1, nb, part_c2, nb, red);
-      fill_step_factors(&sc, fac, d.n_check);
-      if (threadIdx.x == 0) {
-        sc.hash_accum = __ldcg(&hash[hslot]);
-        if (std::is_same<T, float>::value) sync_step_state(&sc);
-        if (lead) hash[hslot ^ 1] = 0ULL;  // the next check's slot; nobody reads it now
-        check_control(&sc, red, lead ? d.trace_checks : nullptr, d.trace_cap);
+      static_assert((kNC1 + kNC2) * (kPThreads - 32) <= 2 * kPWarps * kSmemPerWarp, "reduction scratch");
+      reduce_two<kNC1, kNC2>(part_c1, nb, part_c2, nb, psm, red);
+      fill_step_factors<T>(&sc, fac, d.n_check);
+      if (threadIdx.x < 32) {
+        if (threadIdx.x == 0) {
+          sc.hash_accum = __ldcg(&hash[hslot]);
+          if (std::is_same<T, float>::value) sync_step_state(&sc);
+          if (lead) hash[hslot ^ 1] = 0ULL;  // the next check's slot; nobody reads it now
+        }
+        __syncwarp();
+        check_control_warp(&sc, red, lead ? d.trace_checks : nullptr, d.trace_cap);
       }
       __syncthreads();
       hslot ^= 1;
@@ -851,6 +1041,7 @@ __global__ void k_scale_vectors(DevVecs v) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.n; j += stride) {
     const double cj = v.C[j];
     const double c = v.c[j] * cj, l = v.l[j] / cj, u = v.u[j] / cj;
+    if (v.invC) v.invC[j] = 1.0 / cj;
     v.c64[j] = c;
     v.l64[j] = l;
     v.u64[j] = u;
@@ -863,6 +1054,7 @@ __global__ void k_scale_vectors(DevVecs v) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.m; i += stride) {
     const double ri = v.R[i];
     const double lo = v.lo[i] * ri, hi = v.hi[i] * ri;
+    if (v.invR) v.invR[i] = 1.0 / ri;
     v.lo64[i] = lo;
     v.hi64[i] = hi;
     if (v.lo32) {
@@ -1251,6 +1443,7 @@ __global__ void __launch_bounds__(kThreads) k_bcheck_cols(DevBatch<T> B) {
   epi.B = &B;
   epi.xlr = d.XLR;
   epi.C = d.C;
+  epi.invC = d.invC;
   epi.c64 = d.c64;
   epi.l64 = d.l64;
   epi.u64 = d.u64;
@@ -1306,7 +1499,7 @@ __global__ void __launch_bounds__(kThreads) k_bcheck_rows(DevBatch<T> B) {
   BCheckRowsEpi<T> epi;
   epi.B = &B;
   epi.ylr = d.YLR;
-  epi.R = d.R;
+  epi.invR = d.invR;
   epi.lo64 = d.lo64;
   epi.hi64 = d.hi64;
 #pragma unroll
@@ -1520,19 +1713,19 @@ cudaError_t launch_check(const DevLP<T>& d, cudaStream_t st) {
 }
 
 template <typename T>
-cudaError_t launch_slot(const DevLP<T>& d, cudaStream_t st) {
-  cudaError_t e = launch_step_kernel<T>(k_primal<T>, d.grid_p, d, st);
-  if (e == cudaSuccess) e = launch_step_kernel<T>(k_dual<T>, d.grid_d, d, st);
-  return e;
-}
-
-template <typename T>
 cudaError_t launch_primal(const DevLP<T>& d, cudaStream_t st) {
-  return launch_step_kernel<T>(k_primal<T>, d.grid_p, d, st);
+  return launch_step_kernel<T>(d.prefetch ? k_primal<T, true> : k_primal<T, false>, d.grid_p, d, st);
 }
 template <typename T>
 cudaError_t launch_dual(const DevLP<T>& d, cudaStream_t st) {
-  return launch_step_kernel<T>(k_dual<T>, d.grid_d, d, st);
+  return launch_step_kernel<T>(d.prefetch ? k_dual<T, true> : k_dual<T, false>, d.grid_d, d, st);
+}
+
+template <typename T>
+cudaError_t launch_slot(const DevLP<T>& d, cudaStream_t st) {
+  cudaError_t e = launch_primal<T>(d, st);
+  if (e == cudaSuccess) e = launch_dual<T>(d, st);
+  return e;
 }
 template <typename T>
 cudaError_t launch_check_cols(const DevLP<T>& d, cudaStream_t st) {
@@ -1602,8 +1795,8 @@ int occupancy_grid(int kernel_id, int work_tiles) {
   int per_sm = 1;
   cudaError_t e = cudaSuccess;
   switch (kernel_id) {
-    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_primal<T>, kThreads, 0); break;
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dual<T>, kThreads, 0); break;
+    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_primal<T, false>, kThreads, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dual<T, false>, kThreads, 0); break;
     case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_check_cols<T>, kThreads, 0); break;
     default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_check_rows<T>, kThreads, 0); break;
   }

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "host_par.h"
 #include "lp_handle.h"
 
 namespace scylla {
@@ -78,6 +79,7 @@ extern "C" void scylla_default_params(scylla_params* p) {
   p->time_limit_s = 0.0;
   p->device_wait_limit_s = 5.0;
   p->pdl = 1;
+  p->prefetch = 0;
 }
 
 extern "C" const char* scylla_last_error(void) { return get_error(); }
@@ -133,6 +135,12 @@ void fill_dev(DevLP<T>& d, scylla_lp* lp);
 
 }  // namespace
 
+void scylla_lp::ensure_columns() const {
+  if (columns_ready) return;
+  scylla::transpose_csr(m0, n0, rowptr0.data(), cols0.data(), nullptr, colptr0, colrows0, nullptr);
+  columns_ready = true;
+}
+
 // --------------------------------------------------------------- validation ---
 int scylla::validate_lp(const scylla_csr* A, const double* c, const double* lo, const double* hi, const double* l,
                     const double* u, const uint8_t* is_int) {
@@ -143,15 +151,37 @@ int scylla::validate_lp(const scylla_csr* A, const double* c, const double* lo, 
     FAIL(SCYLLA_ERR_UNSUPPORTED, "dimensions or nnz beyond the 32-bit index range");
   if (!A->rowptr || (A->nnz > 0 && (!A->cols || !A->vals))) FAIL(SCYLLA_ERR_INVALID_ARG, "null CSR array");
   if (A->rowptr[0] != 0 || A->rowptr[A->m] != A->nnz) FAIL(SCYLLA_ERR_INVALID_ARG, "rowptr[0] != 0 or rowptr[m] != nnz");
-  for (int64_t i = 0; i < A->m; ++i) {
-    const int64_t p0 = A->rowptr[i], p1 = A->rowptr[i + 1];
-    if (p1 < p0) FAIL(SCYLLA_ERR_INVALID_ARG, "rowptr not non-decreasing at row " + std::to_string(i));
-    for (int64_t p = p0; p < p1; ++p) {
-      const int32_t j = A->cols[p];
-      if (j < 0 || j >= A->n) FAIL(SCYLLA_ERR_INVALID_ARG, "column index out of range in row " + std::to_string(i));
-      if (p > p0 && A->cols[p - 1] >= j)
-        FAIL(SCYLLA_ERR_INVALID_ARG, "column indices not strictly increasing in row " + std::to_string(i));
-      if (!std::isfinite(A->vals[p])) FAIL(SCYLLA_ERR_INVALID_ARG, "non-finite matrix value in row " + std::to_string(i));
+  for (int64_t i = 0; i < A->m; ++i)
+    if (A->rowptr[i + 1] < A->rowptr[i]) FAIL(SCYLLA_ERR_INVALID_ARG, "rowptr not non-decreasing at row " + std::to_string(i));
+  // rows in parallel slices; the first failing row is reported
+  {
+    const int64_t mm = A->m;
+    const int T = threads_for(A->nnz + mm);
+    std::vector<int64_t> bad(size_t(T), mm);
+    std::vector<int> why(size_t(T), 0);
+    fork_join(T, [&](int t) {
+      for (int64_t i = mm * t / T; i < mm * (t + 1) / T; ++i) {
+        const int64_t p0 = A->rowptr[i], p1 = A->rowptr[i + 1];
+        int w = 0;
+        for (int64_t p = p0; p < p1 && !w; ++p) {
+          const int32_t j = A->cols[p];
+          if (j < 0 || j >= A->n) w = 1;
+          else if (p > p0 && A->cols[p - 1] >= j) w = 2;
+          else if (!std::isfinite(A->vals[p])) w = 3;
+        }
+        if (w) {
+          bad[size_t(t)] = i;
+          why[size_t(t)] = w;
+          return;
+        }
+      }
+    });
+    for (int t = 0; t < T; ++t) {
+      if (!why[size_t(t)]) continue;
+      const std::string row = std::to_string(bad[size_t(t)]);
+      if (why[size_t(t)] == 1) FAIL(SCYLLA_ERR_INVALID_ARG, "column index out of range in row " + row);
+      if (why[size_t(t)] == 2) FAIL(SCYLLA_ERR_INVALID_ARG, "column indices not strictly increasing in row " + row);
+      FAIL(SCYLLA_ERR_INVALID_ARG, "non-finite matrix value in row " + row);
     }
   }
   for (int64_t i = 0; i < A->m; ++i) {
@@ -179,6 +209,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   if (lp->p.trace_capacity < 0) FAIL(SCYLLA_ERR_INVALID_ARG, "trace_capacity must be >= 0");
   if (lp->p.use_graph < 0 || lp->p.use_graph > 3) FAIL(SCYLLA_ERR_INVALID_ARG, "use_graph must be 0..3");
   if (!(lp->p.device_wait_limit_s > 0.0)) FAIL(SCYLLA_ERR_INVALID_ARG, "device_wait_limit_s must be > 0");
+  if (lp->p.prefetch < 0 || lp->p.prefetch > 2) FAIL(SCYLLA_ERR_INVALID_ARG, "prefetch must be 0..2");
   if (lp->p.precision != SCYLLA_PREC_FP64 && lp->p.precision != SCYLLA_PREC_MIXED)
     FAIL(SCYLLA_ERR_INVALID_ARG, "unknown precision");
   CK(cudaGetDevice(&lp->device));
@@ -202,16 +233,6 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   lp->l0.assign(l, l + n0);
   lp->u0.assign(u, u + n0);
   lp->int0.assign(is_int, is_int + n0);
-  // rows of each column, ascending (for propagation)
-  lp->colptr0.assign(n0 + 1, 0);
-  for (int64_t p = 0; p < nnz0; ++p) lp->colptr0[lp->cols0[p] + 1]++;
-  for (int64_t j = 0; j < n0; ++j) lp->colptr0[j + 1] += lp->colptr0[j];
-  lp->colrows0.assign(nnz0, 0);
-  {
-    std::vector<int64_t> cur(lp->colptr0.begin(), lp->colptr0.end() - 1);
-    for (int64_t i = 0; i < m0; ++i)
-      for (int64_t p = lp->rowptr0[i]; p < lp->rowptr0[i + 1]; ++p) lp->colrows0[cur[lp->cols0[p]]++] = int32_t(i);
-  }
   lp->c0norm = 0.0;
   for (int64_t j = 0; j < n0; ++j) lp->c0norm += c[j] * c[j];
   lp->c0norm = std::sqrt(lp->c0norm);
@@ -240,22 +261,30 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   lp->n = int(n);
   lp->nnz = int(nnz);
 
-  std::vector<int> rp(m + 1), ci(nnz);
-  std::vector<double> va(nnz);
+  // the iterated LP's CSR: the original rows (used in place when there are no
+  // auxiliary columns), then two rows per auxiliary column
+  std::vector<int> rp(m + 1), ci_aux;
+  std::vector<double> va_aux;
   for (int64_t i = 0; i <= m0; ++i) rp[i] = int(lp->rowptr0[i]);
-  for (int64_t p = 0; p < nnz0; ++p) {
-    ci[p] = lp->cols0[p];
-    va[p] = lp->vals0[p];
-  }
-  for (int64_t t = 0; t < na; ++t) {
-    const int j = lp->gen_int[t];
-    const int64_t r0 = m0 + 2 * t, p = nnz0 + 4 * t;
-    ci[p] = j; va[p] = -1.0;
-    ci[p + 1] = int(n0 + t); va[p + 1] = 1.0;
-    ci[p + 2] = j; va[p + 2] = 1.0;
-    ci[p + 3] = int(n0 + t); va[p + 3] = 1.0;
-    rp[r0 + 1] = int(p + 2);
-    rp[r0 + 2] = int(p + 4);
+  const int* ci = lp->cols0.data();
+  const double* va = lp->vals0.data();
+  if (na > 0) {
+    ci_aux.resize(nnz);
+    va_aux.resize(nnz);
+    std::copy(lp->cols0.begin(), lp->cols0.end(), ci_aux.begin());
+    std::copy(lp->vals0.begin(), lp->vals0.end(), va_aux.begin());
+    for (int64_t t = 0; t < na; ++t) {
+      const int j = lp->gen_int[t];
+      const int64_t r0 = m0 + 2 * t, p = nnz0 + 4 * t;
+      ci_aux[p] = j; va_aux[p] = -1.0;
+      ci_aux[p + 1] = int(n0 + t); va_aux[p + 1] = 1.0;
+      ci_aux[p + 2] = j; va_aux[p + 2] = 1.0;
+      ci_aux[p + 3] = int(n0 + t); va_aux[p + 3] = 1.0;
+      rp[r0 + 1] = int(p + 2);
+      rp[r0 + 2] = int(p + 4);
+    }
+    ci = ci_aux.data();
+    va = va_aux.data();
   }
   std::vector<double> cA(n), loA(m), hiA(m), lA(n), uA(n);
   for (int64_t j = 0; j < n0; ++j) { cA[j] = c[j]; lA[j] = l[j]; uA[j] = u[j]; }
@@ -270,20 +299,10 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   std::vector<uint8_t> imask(n, 0);
   for (int64_t j = 0; j < n0; ++j) imask[j] = is_int[j];
 
-  // ---- transpose (counting sort: rows ascending within each column)
-  std::vector<int> tp(n + 1, 0), tr(nnz);
-  std::vector<double> tv(nnz);
-  for (int64_t p = 0; p < nnz; ++p) tp[ci[p] + 1]++;
-  for (int64_t j = 0; j < n; ++j) tp[j + 1] += tp[j];
-  {
-    std::vector<int> cur(tp.begin(), tp.end() - 1);
-    for (int64_t i = 0; i < m; ++i)
-      for (int p = rp[i]; p < rp[i + 1]; ++p) {
-        const int q = cur[ci[p]]++;
-        tr[q] = int(i);
-        tv[q] = va[p];
-      }
-  }
+  // ---- stored transpose (rows ascending within each column)
+  std::vector<int> tp, tr;
+  std::vector<double> tv;
+  transpose_csr(m, n, rp.data(), ci, va, tp, tr, &tv);
   const std::vector<int2> at = build_tiles(rp), tt = build_tiles(tp);
   lp->a_ntiles = int(at.size()) - 1;
   lp->t_ntiles = int(tt.size()) - 1;
@@ -300,6 +319,16 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     lp->grid_d = occupancy_grid<double>(1, lp->a_ntiles);
     lp->grid_c1 = occupancy_grid<double>(2, lp->t_ntiles);
     lp->grid_c2 = occupancy_grid<double>(3, lp->a_ntiles);
+  }
+  // first-tile prefetch: pays when the per-attempt kernels' matrix data stay in L2
+  // between attempts (the kernels are then latency-bound); a DRAM-resident matrix
+  // keeps the lighter kernels
+  {
+    int l2 = 0;
+    CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, lp->device));
+    const double vb = mixed ? 4.0 : 8.0;
+    const double bytes = 2.0 * double(nnz) * (4.0 + vb) + 12.0 * double(m + n) * vb;
+    lp->prefetch = lp->p.prefetch == 1 || (lp->p.prefetch == 0 && bytes <= 0.5 * double(l2));
   }
   // persistent cooperative solve: one grid of co-resident blocks, if it fits
   {
@@ -344,6 +373,8 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     lp->hi32 = mixed ? ar.take<float>(m) : nullptr;
     lp->R = ar.take<double>(m);
     lp->C = ar.take<double>(n);
+    lp->invR = ar.take<double>(m);
+    lp->invC = ar.take<double>(n);
     lp->R2 = ar.take<double>(std::max(m, n));
     lp->C2 = ar.take<double>(std::max(m, n));
     lp->int_mask = ar.take<uint8_t>(n);
@@ -386,12 +417,12 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   CK(cudaEventCreateWithFlags(&lp->ev_chunk[1], cudaEventDisableTiming));
 
   CK(cudaMemcpyAsync(lp->a_rowptr, rp.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->a_cols, ci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->a_cols, ci, sizeof(int) * nnz, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->a_tiles, at.data(), sizeof(int2) * at.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->t_rowptr, tp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->t_cols, tr.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->t_tiles, tt.data(), sizeof(int2) * tt.size(), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->a_vals64, va.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->a_vals64, va, sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->t_vals64, tv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->c_un, cA.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->l_un, lA.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
@@ -420,7 +451,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     v.c = lp->c_un; v.lo = lp->lo_un; v.hi = lp->hi_un; v.l = lp->l_un; v.u = lp->u_un;
     v.c64 = lp->c64; v.lo64 = lp->lo64; v.hi64 = lp->hi64; v.l64 = lp->l64; v.u64 = lp->u64;
     v.c32 = lp->c32; v.lo32 = lp->lo32; v.hi32 = lp->hi32; v.l32 = lp->l32; v.u32 = lp->u32;
-    v.R = lp->R; v.C = lp->C; v.m = int(m); v.n = int(n);
+    v.R = lp->R; v.C = lp->C; v.invR = lp->invR; v.invC = lp->invC; v.m = int(m); v.n = int(n);
     CK(launch_scale_vectors(v, st));
     double amax = 0.0, fro2 = 0.0;
     CK(matrix_norms(s, st, &amax, &fro2));
@@ -503,6 +534,8 @@ void fill_dev(DevLP<T>& d, scylla_lp* lp) {
   d.c64 = lp->c64; d.l64 = lp->l64; d.u64 = lp->u64; d.lo64 = lp->lo64; d.hi64 = lp->hi64;
   d.R = lp->R;
   d.C = lp->C;
+  d.invR = lp->invR;
+  d.invC = lp->invC;
   d.int_mask = lp->int_mask;
   for (int k = 0; k < 3; ++k) {
     d.X[k] = reinterpret_cast<T*>(lp->X[k]);
@@ -520,6 +553,7 @@ void fill_dev(DevLP<T>& d, scylla_lp* lp) {
   d.p_hash = lp->p_hash;
   d.n_check = lp->p.n_check;
   d.pdl = lp->p.pdl ? 1 : 0;
+  d.prefetch = lp->prefetch ? 1 : 0;
   d.trace_steps = lp->trace_steps;
   d.trace_checks = lp->trace_checks;
   d.trace_cap = lp->p.trace_capacity;

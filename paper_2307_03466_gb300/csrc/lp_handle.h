@@ -22,8 +22,12 @@ struct scylla_lp {
   std::vector<double> vals0;
   std::vector<double> c0, lo0, hi0, l0, u0;
   std::vector<uint8_t> int0;
-  std::vector<int64_t> colptr0;  // transpose structure: rows of each column, ascending
-  std::vector<int32_t> colrows0;
+  // transpose structure of the original rows (rows of each column, ascending), for
+  // the host propagation; built on first use by ensure_columns()
+  mutable std::vector<int64_t> colptr0;
+  mutable std::vector<int32_t> colrows0;
+  mutable bool columns_ready = false;
+  void ensure_columns() const;
   double c0norm = 0.0;
   int64_t n_int = 0;
   std::vector<int> kind;     // 0 continuous, 1 integer with u - l = 1, 2 general integer
@@ -46,12 +50,14 @@ struct scylla_lp {
   unsigned long long* p_hash = nullptr;
   void* grid_bar = nullptr;
   int p_grid = 0;  // persistent grid (0: that mode is unavailable)
+  bool prefetch = false;  // per-attempt kernels prefetch their first tile (scylla_params.prefetch)
   double *a_vals64 = nullptr, *t_vals64 = nullptr;
   float *a_vals32 = nullptr, *t_vals32 = nullptr;
   double *c_un = nullptr, *l_un = nullptr, *u_un = nullptr, *lo_un = nullptr, *hi_un = nullptr;
   double *c64 = nullptr, *l64 = nullptr, *u64 = nullptr, *lo64 = nullptr, *hi64 = nullptr;
   float *c32 = nullptr, *l32 = nullptr, *u32 = nullptr, *lo32 = nullptr, *hi32 = nullptr;
   double *R = nullptr, *C = nullptr, *R2 = nullptr, *C2 = nullptr;
+  double *invR = nullptr, *invC = nullptr;
   uint8_t* int_mask = nullptr;
   double *c_orig = nullptr, *l_orig = nullptr, *u_orig = nullptr, *xhat_d = nullptr;
   int *kind_d = nullptr, *aux_of_d = nullptr;

@@ -46,7 +46,7 @@ class Params(C.Structure):
                 ("max_rounds", C.c_int64), ("iter_limit", C.c_int64), ("total_iter_cap", C.c_int64),
                 ("run_stall_checks", C.c_int32), ("trace_capacity", C.c_int32), ("seed", C.c_uint64),
                 ("time_limit_s", C.c_double), ("device_wait_limit_s", C.c_double), ("pdl", C.c_int32),
-                ("reserved1", C.c_int32)]
+                ("prefetch", C.c_int32)]
 
 
 class PdhgResult(C.Structure):

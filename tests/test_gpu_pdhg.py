@@ -229,6 +229,25 @@ def test_programmatic_launch_changes_nothing():
     g2.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["knapcover_700", "long_rows"])
+def test_prefetch_on_off_identical(name, precision):
+    """The per-attempt kernels with and without the first-tile prefetch compute the
+    same sums in the same order (a retry's wasted gather is ignored): identical
+    results, in both precisions, with retries and averaging on the way."""
+    inst = INSTANCES[name]
+    g1, _ = pair(inst, precision=precision, prefetch=1)
+    g2, _ = pair(inst, precision=precision, prefetch=2)
+    r1 = g1.pdhg_solve(1e-6, 20000)
+    r2 = g2.pdhg_solve(1e-6, 20000)
+    assert r1.iterations == r2.iterations and r1.status == r2.status
+    assert r1.rejected == r2.rejected
+    np.testing.assert_array_equal(g1.primal(), g2.primal())
+    np.testing.assert_array_equal(g1.dual(), g2.dual())
+    g1.close()
+    g2.close()
+
+
 @pytest.mark.parametrize("name", ["setcover_200x500", "packcover_2kx4k", "long_rows"])
 def test_persistent_kernel_matches_graph_path(name):
     """The persistent kernel sums block partials over a different grid, so its step
