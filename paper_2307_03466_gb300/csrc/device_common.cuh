@@ -209,6 +209,63 @@ static __device__ void reduce_two(const double* pa, int na, const double* pb, in
   __syncthreads();
 }
 
+// sums of one partial array (N values over np blocks) by warps 1.., like reduce_two
+template <int N>
+static __device__ void reduce_one(const double* p, int np, double* scratch, double* out) {
+  const int nt = blockDim.x - 32, t = threadIdx.x - 32;
+  if (t >= 0) {
+    double s[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) s[k] = 0.0;
+    constexpr int kR = 2;
+    double v[kR][N];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+      const int b = t + r * nt;
+#pragma unroll
+      for (int k = 0; k < N; ++k) v[r][k] = b < np ? __ldcg(p + b * N + k) : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < kR; ++r)
+#pragma unroll
+      for (int k = 0; k < N; ++k) s[k] += v[r][k];
+    for (int b = t + kR * nt; b < np; b += nt)
+#pragma unroll
+      for (int k = 0; k < N; ++k) s[k] += __ldcg(p + b * N + k);
+#pragma unroll
+    for (int k = 0; k < N; ++k) scratch[k * nt + t] = s[k];
+    asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
+    const int w = t >> 5, lane = t & 31, nw = nt >> 5;
+    for (int k = w; k < N; k += nw) {
+      double x = 0.0;
+      for (int i = lane; i < nt; i += 32) x += scratch[k * nt + i];
+      x = warp_sum(x);
+      if (lane == 0) out[k] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// column k of a partial array (N values over np blocks) by the whole block, in a
+// fixed order; thread 0 returns the sum
+template <int N>
+static __device__ double block_column_sum(const double* p, int np, int k) {
+  __shared__ double sh[kMaxWarps];
+  double x = 0.0;
+  for (int b = threadIdx.x; b < np; b += blockDim.x) x += __ldcg(p + b * N + k);
+  x = warp_sum(x);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) sh[w] = x;
+  __syncthreads();
+  double t = 0.0;
+  if (w == 0) {
+    t = lane < nw ? sh[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  __syncthreads();
+  return t;
+}
+
 __device__ __forceinline__ float ldcg_t(const float* p) { return __ldcg(p); }
 __device__ __forceinline__ double ldcg_t(const double* p) { return __ldcg(p); }
 
@@ -663,20 +720,30 @@ static __device__ void check_control(Control* c, const double* r, double* trace,
 
 // warp form: lanes 0 and 1 evaluate the two points side by side (their square roots
 // and divisions are long FP64 chains), lane 0 decides.  Called by a whole warp.
+// The control block is worked on in a shared-memory copy that the warp loads and
+// stores with coalesced word accesses (the decision logic's many field accesses
+// are then shared-memory ones).
 static __device__ void check_control_warp(Control* c, const double* r, double* trace, int cap) {
   __shared__ Eval se[2];
   __shared__ double swk[2];
+  __shared__ Control sc;
+  static_assert(sizeof(Control) % 4 == 0, "word copy");
   const int lane = threadIdx.x & 31;
+  constexpr int kWords = int(sizeof(Control) / 4);
+  for (int i = lane; i < kWords; i += 32) reinterpret_cast<int*>(&sc)[i] = reinterpret_cast<const int*>(c)[i];
+  __syncwarp();
   if (lane < 2) {
-    const Eval e = make_eval(c, r, lane);
+    const Eval e = make_eval(&sc, r, lane);
     se[lane] = e;
-    swk[lane] = weighted_kkt(e, c->omega);
+    swk[lane] = weighted_kkt(e, sc.omega);
   }
   __syncwarp();
   if (lane == 0) {
-    check_control_impl(c, se, swk, trace, cap);
-    derive_steps(c);
+    check_control_impl(&sc, se, swk, trace, cap);
+    derive_steps(&sc);
   }
+  __syncwarp();
+  for (int i = lane; i < kWords; i += 32) reinterpret_cast<int*>(c)[i] = reinterpret_cast<const int*>(&sc)[i];
   __syncwarp();
 }
 

@@ -98,6 +98,7 @@ struct DevLP {
   T* YLR;
   Control* ctl;
   double *part_p, *part_d, *part_c1, *part_c2;
+  double* red_c1;  // the column check's reduced sums (kNC1)
   int grid_p, grid_d, grid_c1, grid_c2;
   double* step_fac;      // (1 - kk^-a, 1 + kk^-b) of the next n_check attempts: 2 n_check doubles,
                          // then the same 2 n_check values as floats (3 n_check doubles in all)

@@ -24,6 +24,14 @@
 
 namespace scylla {
 
+// lanes that sum one row of a multi-row tile of nr rows: the largest power of two
+// L with L * nr <= 32 (a tile of up to 16 rows splits each row over 2+ lanes, whose
+// partial sums are combined by a shuffle tree, in a fixed order)
+__device__ __forceinline__ int row_lanes(int nr) {
+  const int l = 32 / (nr > 0 ? nr : 1);
+  return 1 << (31 - __clz(l));
+}
+
 // --------------------------------------------------------------- the SpMV core ---
 // Warp-tile CSR gather.  Each warp takes tiles round-robin.  A multi-row tile (at
 // most kTileNnz nonzeros and 32 rows) is read with 16-byte vector loads of column
@@ -61,9 +69,10 @@ __device__ __forceinline__ bool spmv_tiles(const int2* __restrict__ tiles, int n
     longrow = r1 - r0 == 1 && p1 - p0 > kTileNnz;
     if (!longrow) {
       q0 = q1 = 0;
-      if (lane < r1 - r0) {
-        q0 = __ldg(rowptr + r0 + lane) - p0;
-        q1 = __ldg(rowptr + r0 + lane + 1) - p0;
+      const int rl = lane / row_lanes(r1 - r0);
+      if (rl < r1 - r0) {
+        q0 = __ldg(rowptr + r0 + rl) - p0;
+        q1 = __ldg(rowptr + r0 + rl + 1) - p0;
       }
       const int base = p0 & ~(kVec - 1);
 #pragma unroll
@@ -106,10 +115,11 @@ __device__ __forceinline__ bool spmv_tiles(const int2* __restrict__ tiles, int n
       for (int k = 0; k < NV; ++k) s[k] = warp_sum(s[k]);
       if (lane == 0) epi.finish(r0, s, pre);
     } else {
-      const bool mine = lane < r1 - r0;
-      const int row = r0 + lane;
+      const int L = row_lanes(r1 - r0), rl = lane / L, sub = lane - rl * L;
+      const bool mine = rl < r1 - r0, lead = mine && sub == 0;
+      const int row = r0 + rl;
       typename Epi::Pre pre{};
-      if (mine) pre = epi.load(row);
+      if (lead) pre = epi.load(row);
 #pragma unroll
       for (int it = 0; it < 3; ++it) {
         const int p = base + (it * 32 + lane) * kVec;
@@ -126,17 +136,20 @@ __device__ __forceinline__ bool spmv_tiles(const int2* __restrict__ tiles, int n
         }
       }
       __syncwarp();
-      if (mine) {
-        Acc s[NV];
+      Acc s[NV];
 #pragma unroll
-        for (int k = 0; k < NV; ++k) s[k] = Acc(0);
-        for (int q = q0; q < q1; ++q) {
+      for (int k = 0; k < NV; ++k) s[k] = Acc(0);
+      if (mine) {
+        for (int q = q0 + sub; q < q1; q += L) {
           const int o = skew(q);
 #pragma unroll
           for (int k = 0; k < NV; ++k) s[k] += sm[k * kSmemPerWarp + o];
         }
-        epi.finish(row, s, pre);
       }
+      for (int o = L >> 1; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[k] += __shfl_down_sync(0xffffffffu, s[k], o);
+      if (lead) epi.finish(row, s, pre);
       __syncwarp();
     }
   }
@@ -190,15 +203,16 @@ __device__ __forceinline__ void spmv_tiles_fma(const int2* __restrict__ tiles, i
       for (int k = 0; k < NV; ++k) s[k] = warp_sum(s[k]);
       if (lane == 0) epi.finish(r0, s, pre);
     } else {
-      const bool mine = lane < r1 - r0;
-      const int row = r0 + lane;
+      const int L = row_lanes(r1 - r0), rl = lane / L, sub = lane - rl * L;
+      const bool mine = rl < r1 - r0, lead = mine && sub == 0;
+      const int row = r0 + rl;
       int q0 = 0, q1 = 0;
       typename Epi::Pre pre{};
       if (mine) {
         q0 = __ldg(rowptr + row) - p0;
         q1 = __ldg(rowptr + row + 1) - p0;
-        pre = epi.load(row);
       }
+      if (lead) pre = epi.load(row);
       int c[3][4];
       double v[3][4];
 #pragma unroll
@@ -226,18 +240,21 @@ __device__ __forceinline__ void spmv_tiles_fma(const int2* __restrict__ tiles, i
         }
       }
       __syncwarp();
-      if (mine) {
-        double s[NV];
+      double s[NV];
 #pragma unroll
-        for (int k = 0; k < NV; ++k) s[k] = 0.0;
-        for (int q = q0; q < q1; ++q) {
+      for (int k = 0; k < NV; ++k) s[k] = 0.0;
+      if (mine) {
+        for (int q = q0 + sub; q < q1; q += L) {
           const int o = skew(q);
           const double a = smw[o];
 #pragma unroll
           for (int k = 0; k < NV; ++k) s[k] = __fma_rn(a, to_f64(sg[k * kSmemPerWarp + o]), s[k]);
         }
-        epi.finish(row, s, pre);
       }
+      for (int o = L >> 1; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[k] += __shfl_down_sync(0xffffffffu, s[k], o);
+      if (lead) epi.finish(row, s, pre);
       __syncwarp();
     }
   }
@@ -730,12 +747,18 @@ __global__ void __launch_bounds__(kThreads) k_check_rows(DevLP<T> d) {
   Control* ctl = d.ctl;
   pdl_enter();
   if (ctl->done) return;
+  // the column check's block partials, one value per block, while the row blocks run
+  for (int k = blockIdx.x; k < kNC1; k += gridDim.x) {
+    const double v = block_column_sum<kNC1>(d.part_c1, d.grid_c1, k);
+    if (threadIdx.x == 0) d.red_c1[k] = v;
+  }
   __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];
   check_rows_phase<T, false>(d, make_view<T>(ctl), sm, d.part_c2);
   if (!is_last_block(&ctl->cnt_c2)) return;
   __shared__ double red[kNC1 + kNC2];
-  static_assert((kNC1 + kNC2) * (kThreads - 32) <= 2 * kWarpsPerBlock * kSmemPerWarp, "reduction scratch");
-  reduce_two<kNC1, kNC2>(d.part_c1, d.grid_c1, d.part_c2, d.grid_c2, sm, red);
+  static_assert(kNC2 * (kThreads - 32) <= 2 * kWarpsPerBlock * kSmemPerWarp, "reduction scratch");
+  if (threadIdx.x < kNC1) red[threadIdx.x] = __ldcg(d.red_c1 + threadIdx.x);
+  reduce_one<kNC2>(d.part_c2, d.grid_c2, sm, red + kNC1);
   fill_step_factors<T>(ctl, d.step_fac, d.n_check);
   if (threadIdx.x < 32) {
     if (threadIdx.x == 0 && std::is_same<T, float>::value) sync_step_state(ctl);

@@ -396,6 +396,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     lp->part_d = ar.take<double>(size_t(kND) * std::max(lp->grid_d, 1));
     lp->part_c1 = ar.take<double>(size_t(kNC1) * std::max(lp->grid_c1, 1));
     lp->part_c2 = ar.take<double>(size_t(kNC2) * std::max(lp->grid_c2, 1));
+    lp->red_c1 = ar.take<double>(kNC1);
     lp->red = ar.take<double>(2 * size_t(lp->red_blocks));
     lp->io_x = ar.take<double>(n);
     lp->io_y = ar.take<double>(m);
@@ -546,7 +547,7 @@ void fill_dev(DevLP<T>& d, scylla_lp* lp) {
   d.XLR = reinterpret_cast<T*>(lp->XLR);
   d.YLR = reinterpret_cast<T*>(lp->YLR);
   d.ctl = lp->ctl;
-  d.part_p = lp->part_p; d.part_d = lp->part_d; d.part_c1 = lp->part_c1; d.part_c2 = lp->part_c2;
+  d.part_p = lp->part_p; d.part_d = lp->part_d; d.part_c1 = lp->part_c1; d.part_c2 = lp->part_c2; d.red_c1 = lp->red_c1;
   d.grid_p = lp->grid_p; d.grid_d = lp->grid_d; d.grid_c1 = lp->grid_c1; d.grid_c2 = lp->grid_c2;
   d.step_fac = lp->step_fac;
   d.pp_part = lp->pp_part;

@@ -67,6 +67,7 @@ struct scylla_lp {
   char* ATY[2] = {nullptr, nullptr};
   char *XLR = nullptr, *YLR = nullptr;
   double *part_p = nullptr, *part_d = nullptr, *part_c1 = nullptr, *part_c2 = nullptr, *red = nullptr;
+  double* red_c1 = nullptr;
   double *io_x = nullptr, *io_y = nullptr;
   double *trace_steps = nullptr, *trace_checks = nullptr;
   scylla::Control* ctl = nullptr;
