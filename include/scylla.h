@@ -106,8 +106,11 @@ typedef struct {
   double device_wait_limit_s;   /* bound of every device-side barrier wait (5) */
   int32_t pdl;                  /* launch the per-attempt kernels with programmatic dependent launch, so
                                    each one is resident before its predecessor ends (1) */
-  int32_t prefetch;             /* 0: load each warp's first matrix tile before the wait on the preceding
-                                   kernel when A and A^T fit in half the L2 cache; 1: always; 2: never (0) */
+  int32_t prefetch;             /* form of the per-attempt kernels. 0: automatic (4 when A, A^T and the
+                                   vectors fit in half of the L2 cache, else 2); 1: 32-row tiles, each
+                                   warp loading its first tile before the wait on the preceding kernel;
+                                   2: wide tiles of up to 128 rows, plain loads; 3: wide tiles staged in
+                                   shared memory by bulk copies; 4: 32-row tiles, plain loads (0) */
 } scylla_params;
 
 typedef struct {

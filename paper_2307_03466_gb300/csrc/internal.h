@@ -30,6 +30,10 @@ constexpr int kPThreads = kPWarps * 32;
 constexpr int kMaxNcheckPersistent = 1024;
 constexpr int kTileNnz = 256;  // nonzeros per multi-row warp tile
 constexpr int kTileRows = 32;  // rows per multi-row warp tile (one lane per row)
+constexpr int kWideRows = 128;  // rows per wide tile (DRAM-resident form): rows lane, lane + 32, ...
+constexpr int kWideRPL = kWideRows / 32;
+// forms of the per-attempt kernels
+constexpr int kFormPlain = 0, kFormPrefetch = 1, kFormWide = 2, kFormStaged = 3;
 constexpr int kVec = 4;        // elements per lane per vector load
 constexpr int kSmemPerWarp = kTileNnz + kTileNnz / 32 + 8;  // skewed product buffer
 
@@ -84,6 +88,10 @@ struct DevLP {
   const int* t_cols;
   const int2* t_tiles;
   int t_ntiles;
+  const int2* a_tiles_w;  // wide tiles (up to kWideRows rows) of the plain-load per-attempt kernels
+  int a_ntiles_w;
+  const int2* t_tiles_w;
+  int t_ntiles_w;
   const T* t_vals;
   const double* t_vals64;
   const T *c, *l, *u, *lo, *hi;
@@ -106,7 +114,8 @@ struct DevLP {
   unsigned long long* p_hash;  // persistent kernel: two rounding-hash slots
   int n_check;
   int pdl;               // launch the per-attempt kernels with programmatic dependent launch
-  int prefetch;          // per-attempt kernels load their first tile before the dependency wait
+  int form_p, form_d;    // form of the primal and dual per-attempt kernels (kForm*)
+  unsigned long long wait_ns;  // bound of every device-side wait
   double* trace_steps;   // 4 doubles per attempt, or null
   double* trace_checks;  // 5 doubles per check, or null
   int trace_cap;
@@ -261,7 +270,7 @@ cudaError_t launch_set_xy(const DevLP<T>& d, const double* x, const double* y, c
 template <typename T>
 cudaError_t launch_init_point(const DevLP<T>& d, cudaStream_t st);
 template <typename T>
-int occupancy_grid(int kernel_id, int work_tiles);  // kernel_id: 0 primal, 1 dual, 2 c1, 3 c2
+int occupancy_grid(int side, int form, int work_tiles);  // side: 0 primal, 1 dual, 2 c1, 3 c2
 
 int device_sm_count();
 
@@ -307,7 +316,7 @@ void fan_grids(DevFan<T>& F);
 constexpr int kFanMaxK = 64;
 
 // shared host helpers (lp.cpp)
-std::vector<int2> build_tiles_range(const std::vector<int>& rowptr, int r_begin, int r_end);
+std::vector<int2> build_tiles_range(const std::vector<int>& rowptr, int r_begin, int r_end, int max_rows = kTileRows);
 int validate_lp(const scylla_csr* A, const double* c, const double* lo, const double* hi, const double* l,
                 const double* u, const uint8_t* is_int);
 size_t padded_len(size_t nnz);

@@ -26,8 +26,10 @@ namespace scylla {
 
 // lanes that sum one row of a multi-row tile of nr rows: the largest power of two
 // L with L * nr <= 32 (a tile of up to 16 rows splits each row over 2+ lanes, whose
-// partial sums are combined by a shuffle tree, in a fixed order)
+// partial sums are combined by a shuffle tree, in a fixed order); 1 from 32 rows on
+// (a wide tile of up to 32 * RPL rows gives each lane rows lane, lane + 32, ...)
 __device__ __forceinline__ int row_lanes(int nr) {
+  if (nr >= 32) return 1;
   const int l = 32 / (nr > 0 ? nr : 1);
   return 1 << (31 - __clz(l));
 }
@@ -47,7 +49,7 @@ __device__ __forceinline__ int row_lanes(int nr) {
 // kernel and sets up the gather and the epilogue; false ends the launch).  With PF
 // the immutable part of the warp's first tile (bounds, row ranges, column indices,
 // values) is loaded before pro(), so those loads overlap the wait.
-template <int NV, bool PF, typename Acc, typename V, typename Gather, typename Epi, typename Pro>
+template <int NV, bool PF, typename Acc, typename V, typename Gather, typename Epi, typename Pro, int RPL = 1>
 __device__ __forceinline__ bool spmv_tiles(const int2* __restrict__ tiles, int ntiles,
                                            const int* __restrict__ rowptr, const int* __restrict__ cols,
                                            const V* __restrict__ vals, Gather& gat, Epi& epi,
@@ -55,11 +57,15 @@ __device__ __forceinline__ bool spmv_tiles(const int2* __restrict__ tiles, int n
   const int lane = threadIdx.x & 31;
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  int r0 = 0, r1 = 0, p0 = 0, p1 = 0, q0 = 0, q1 = 0;
+  int r0 = 0, r1 = 0, p0 = 0, p1 = 0;
+  int q0[RPL], q1[RPL];
   bool longrow = false;
   // p1 - base <= kTileNnz + kVec - 1 < 3 * 32 * kVec: three vector steps cover a tile
   int c[3][4];
   V v[3][4];
+  // row of slot j of this lane in a multi-row tile of nr rows (nr when none): row
+  // lane / L when rows are split over L lanes, else rows lane, lane + 32, ...
+  auto slot_row = [&](int nr, int L, int j) { return L > 1 ? (j == 0 ? lane / L : nr) : lane + 32 * j; };
   auto fetch = [&](int t) {
     const int2 ta = __ldg(tiles + t), tb = __ldg(tiles + t + 1);
     r0 = ta.x;
@@ -68,11 +74,15 @@ __device__ __forceinline__ bool spmv_tiles(const int2* __restrict__ tiles, int n
     p1 = tb.y;
     longrow = r1 - r0 == 1 && p1 - p0 > kTileNnz;
     if (!longrow) {
-      q0 = q1 = 0;
-      const int rl = lane / row_lanes(r1 - r0);
-      if (rl < r1 - r0) {
-        q0 = __ldg(rowptr + r0 + rl) - p0;
-        q1 = __ldg(rowptr + r0 + rl + 1) - p0;
+      const int nr = r1 - r0, L = row_lanes(nr);
+#pragma unroll
+      for (int j = 0; j < RPL; ++j) {
+        q0[j] = q1[j] = 0;
+        const int rl = slot_row(nr, L, j);
+        if (rl < nr) {
+          q0[j] = __ldg(rowptr + r0 + rl) - p0;
+          q1[j] = __ldg(rowptr + r0 + rl + 1) - p0;
+        }
       }
       const int base = p0 & ~(kVec - 1);
 #pragma unroll
@@ -115,11 +125,14 @@ __device__ __forceinline__ bool spmv_tiles(const int2* __restrict__ tiles, int n
       for (int k = 0; k < NV; ++k) s[k] = warp_sum(s[k]);
       if (lane == 0) epi.finish(r0, s, pre);
     } else {
-      const int L = row_lanes(r1 - r0), rl = lane / L, sub = lane - rl * L;
-      const bool mine = rl < r1 - r0, lead = mine && sub == 0;
-      const int row = r0 + rl;
-      typename Epi::Pre pre{};
-      if (lead) pre = epi.load(row);
+      const int nr = r1 - r0, L = row_lanes(nr), sub = L > 1 ? lane % L : 0;
+      typename Epi::Pre pre[RPL];
+#pragma unroll
+      for (int j = 0; j < RPL; ++j) {
+        const int rl = slot_row(nr, L, j);
+        pre[j] = typename Epi::Pre{};
+        if (rl < nr && sub == 0) pre[j] = epi.load(r0 + rl);
+      }
 #pragma unroll
       for (int it = 0; it < 3; ++it) {
         const int p = base + (it * 32 + lane) * kVec;
@@ -136,20 +149,25 @@ __device__ __forceinline__ bool spmv_tiles(const int2* __restrict__ tiles, int n
         }
       }
       __syncwarp();
-      Acc s[NV];
 #pragma unroll
-      for (int k = 0; k < NV; ++k) s[k] = Acc(0);
-      if (mine) {
-        for (int q = q0 + sub; q < q1; q += L) {
-          const int o = skew(q);
+      for (int j = 0; j < RPL; ++j) {
+        const int rl = slot_row(nr, L, j);
+        Acc s[NV];
 #pragma unroll
-          for (int k = 0; k < NV; ++k) s[k] += sm[k * kSmemPerWarp + o];
+        for (int k = 0; k < NV; ++k) s[k] = Acc(0);
+        if (rl < nr) {
+          for (int q = q0[j] + sub; q < q1[j]; q += L) {
+            const int o = skew(q);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) s[k] += sm[k * kSmemPerWarp + o];
+          }
         }
-      }
-      for (int o = L >> 1; o > 0; o >>= 1)
+        if (j == 0)
+          for (int o = L >> 1; o > 0; o >>= 1)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) s[k] += __shfl_down_sync(0xffffffffu, s[k], o);
-      if (lead) epi.finish(row, s, pre);
+            for (int k = 0; k < NV; ++k) s[k] += __shfl_down_sync(0xffffffffu, s[k], o);
+        if (rl < nr && sub == 0) epi.finish(r0 + rl, s, pre[j]);
+      }
       __syncwarp();
     }
   }
@@ -279,6 +297,11 @@ template <>
 struct MinBlocks<double> {
   static constexpr int value = 2;
 };
+// the wide-tile form holds up to four rows' epilogue values per lane
+template <typename T, int F>
+struct MinBlocksOf {
+  static constexpr int value = (F == kFormWide && sizeof(T) == 4) ? 3 : MinBlocks<T>::value;
+};
 
 
 // gathered vectors: read-only path within one launch; L2-coherent loads inside the
@@ -325,8 +348,8 @@ __device__ __forceinline__ SlotView<T> make_view(const Control* c) {
   return v;
 }
 
-// rows of every tile owned by this warp, without a gather: lane r takes row r of a
-// multi-row tile, lane 0 a long row (the same row-to-warp map as spmv_tiles)
+// rows of every tile owned by this warp, without a gather: the same row-to-lane
+// map as spmv_tiles, so the epilogue sums accumulate in the same lanes and order
 template <typename T, typename Epi>
 __device__ __forceinline__ void tiles_rows(const int2* __restrict__ tiles, int ntiles, const T* __restrict__ src,
                                            Epi& epi) {
@@ -335,12 +358,19 @@ __device__ __forceinline__ void tiles_rows(const int2* __restrict__ tiles, int n
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int t = gwarp; t < ntiles; t += nwarps) {
     const int2 ta = __ldg(tiles + t), tb = __ldg(tiles + t + 1);
-    const int nr = tb.x - ta.x;
-    const bool mine = (nr == 1 && tb.y - ta.y > kTileNnz) ? lane == 0 : lane < nr;
-    if (mine) {
-      const int row = ta.x + lane;
-      const T s[1] = {src[row]};
-      epi.finish(row, s, epi.load(row));
+    const int nr = tb.x - ta.x, L = row_lanes(nr);
+    if (L > 1) {
+      if (lane % L == 0 && lane / L < nr) {
+        const int row = ta.x + lane / L;
+        const T s[1] = {src[row]};
+        epi.finish(row, s, epi.load(row));
+      }
+    } else {
+      for (int rl = lane; rl < nr; rl += 32) {
+        const int row = ta.x + rl;
+        const T s[1] = {src[row]};
+        epi.finish(row, s, epi.load(row));
+      }
     }
   }
 }
@@ -365,6 +395,13 @@ struct PrimalEpi {
   A acc;
   __device__ __forceinline__ Pre load(int j) const {
     return Pre{xc[j], cc[j], ll[j], uu[j], do_avg ? xa[j] : T(0)};
+  }
+  // staged form: the five vectors of load(), in its order, staged in shared memory
+  __device__ __forceinline__ const T* stage_vec(int k) const {
+    return k == 0 ? xc : k == 1 ? cc : k == 2 ? ll : k == 3 ? uu : xa;
+  }
+  __device__ __forceinline__ Pre stage_pre(const T* sv, int stride, int o) const {
+    return Pre{sv[o], sv[stride + o], sv[2 * stride + o], sv[3 * stride + o], do_avg ? sv[4 * stride + o] : T(0)};
   }
   __device__ __forceinline__ void finish(int j, const T (&s)[1], const Pre& p) {
     const T aty_j = use_cached ? aty[j] : s[0];
@@ -399,18 +436,21 @@ __device__ __forceinline__ void setup_primal(PrimalEpi<T>& epi, const DevLP<T>& 
   epi.acc = 0;
 }
 
-template <typename T, bool Coh>
+// RPL > 1: the wide tiles
+template <typename T, bool Coh, int RPL = 1>
 __device__ __forceinline__ void primal_phase(const DevLP<T>& d, const SlotView<T>& v, T* sm,
                                              typename AccOf<T>::type* part) {
   PrimalEpi<T> epi;
   setup_primal(epi, d, v);
+  const int2* tiles = RPL > 1 ? d.t_tiles_w : d.t_tiles;
+  const int ntiles = RPL > 1 ? d.t_ntiles_w : d.t_ntiles;
   if (v.aty_valid) {
-    tiles_rows<T>(d.t_tiles, d.t_ntiles, epi.aty, epi);  // retry: A^T y is cached
+    tiles_rows<T>(tiles, ntiles, epi.aty, epi);  // retry: A^T y is cached
   } else {
     const T* __restrict__ yc = d.Y[v.cur];
     auto gat = [&](int i, T(&g)[1]) { g[0] = gload<Coh>(yc + i); };
-    spmv_tiles<1, false, T, T>(d.t_tiles, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals, gat, epi,
-                               sm + (threadIdx.x >> 5) * kSmemPerWarp, NoPro());
+    spmv_tiles<1, false, T, T, decltype(gat), PrimalEpi<T>, NoPro, RPL>(
+        tiles, ntiles, d.t_rowptr, d.t_cols, d.t_vals, gat, epi, sm + (threadIdx.x >> 5) * kSmemPerWarp, NoPro());
   }
   const typename AccOf<T>::type acc[kNP] = {epi.acc};
   block_store_partials<kNP>(acc, part);
@@ -435,6 +475,12 @@ struct DualEpi {
   A acc0, acc1;
   __device__ __forceinline__ Pre load(int i) const {
     return Pre{axc[i], yc[i], lo[i], hi[i], do_avg ? ya[i] : T(0)};
+  }
+  __device__ __forceinline__ const T* stage_vec(int k) const {
+    return k == 0 ? axc : k == 1 ? yc : k == 2 ? lo : k == 3 ? hi : ya;
+  }
+  __device__ __forceinline__ Pre stage_pre(const T* sv, int stride, int o) const {
+    return Pre{sv[o], sv[stride + o], sv[2 * stride + o], sv[3 * stride + o], do_avg ? sv[4 * stride + o] : T(0)};
   }
   __device__ __forceinline__ void finish(int i, const T (&s)[1], const Pre& p) {
     const T ax_new = s[0];
@@ -471,15 +517,16 @@ __device__ __forceinline__ void setup_dual(DualEpi<T>& epi, const DevLP<T>& d, c
   epi.acc1 = 0;
 }
 
-template <typename T, bool Coh>
+template <typename T, bool Coh, int RPL = 1>
 __device__ __forceinline__ void dual_phase(const DevLP<T>& d, const SlotView<T>& v, T* sm,
                                            typename AccOf<T>::type* part) {
   DualEpi<T> epi;
   setup_dual(epi, d, v);
   const T* __restrict__ xn = d.X[v.nxt];
   auto gat = [&](int j, T(&g)[1]) { g[0] = gload<Coh>(xn + j); };
-  spmv_tiles<1, false, T, T>(d.a_tiles, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals, gat, epi,
-                             sm + (threadIdx.x >> 5) * kSmemPerWarp, NoPro());
+  spmv_tiles<1, false, T, T, decltype(gat), DualEpi<T>, NoPro, RPL>(
+      RPL > 1 ? d.a_tiles_w : d.a_tiles, RPL > 1 ? d.a_ntiles_w : d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals, gat,
+      epi, sm + (threadIdx.x >> 5) * kSmemPerWarp, NoPro());
   const typename AccOf<T>::type acc[kND] = {epi.acc0, epi.acc1};
   block_store_partials<kND>(acc, part);
 }
@@ -492,14 +539,17 @@ __device__ __forceinline__ typename AccOf<T>::type* acc_part(double* p) {
   return reinterpret_cast<typename AccOf<T>::type*>(p);
 }
 
-template <typename T, bool PF>
-__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_primal(DevLP<T> d) {
+// F: kFormPlain (32-row tiles), kFormPrefetch (32-row tiles, first tile loaded
+// before the dependency wait), kFormWide (wide tiles, plain loads)
+template <typename T, int F>
+__global__ void __launch_bounds__(kThreads, (MinBlocksOf<T, F>::value)) k_primal(DevLP<T> d) {
   Control* ctl = d.ctl;
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
-  if (!PF) {
+  if (F != kFormPrefetch) {
     pdl_enter();
     if (ctl->done || ctl->k >= ctl->iter_limit) return;
-    primal_phase<T, false>(d, make_view<T>(ctl), sm, acc_part<T>(d.part_p));
+    if (F == kFormWide) primal_phase<T, false, kWideRPL>(d, make_view<T>(ctl), sm, acc_part<T>(d.part_p));
+    else primal_phase<T, false, 1>(d, make_view<T>(ctl), sm, acc_part<T>(d.part_p));
     return;
   }
   // prefetching form: the gather of A^T y is taken even when A^T y is cached (a
@@ -527,15 +577,16 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_primal(DevLP<
 
 // The last block to finish reduces all block partials (warps 1..) while thread 0
 // gathers the decision's other inputs, then takes the step-size decision.
-template <typename T, bool PF>
-__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_dual(DevLP<T> d) {
+template <typename T, int F>
+__global__ void __launch_bounds__(kThreads, (MinBlocksOf<T, F>::value)) k_dual(DevLP<T> d) {
   typedef typename AccOf<T>::type A;
   Control* ctl = d.ctl;
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
-  if (!PF) {
+  if (F != kFormPrefetch) {
     pdl_enter();
     if (ctl->done || ctl->k >= ctl->iter_limit) return;
-    dual_phase<T, false>(d, make_view<T>(ctl), sm, acc_part<T>(d.part_d));
+    if (F == kFormWide) dual_phase<T, false, kWideRPL>(d, make_view<T>(ctl), sm, acc_part<T>(d.part_d));
+    else dual_phase<T, false, 1>(d, make_view<T>(ctl), sm, acc_part<T>(d.part_d));
   } else {
     DualEpi<T> epi;
     const T* __restrict__ xn = nullptr;
@@ -562,6 +613,305 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_dual(DevLP<T>
   reduce_step<A>(acc_part<T>(d.part_p), d.grid_p, acc_part<T>(d.part_d), d.grid_d, reinterpret_cast<A*>(sm), red);
   if (threadIdx.x == 0) {
     step_control<A>(ctl, pre, red[0], red[1], red[2], d.trace_steps, d.trace_cap);
+    ctl->cnt_dual = 0;
+  }
+}
+
+// ------------------------------------------------------------ staged SpMV ---
+// Form of the per-attempt kernels for matrices that do not stay in L2 between
+// attempts (the kernels are then bound by the bytes in flight, not by latency).
+// Each warp owns a ring of two shared-memory stages; a stage holds one wide
+// tile's column indices and values, its row pointers and the five epilogue
+// vectors of its rows, each brought in by one cp.async.bulk copy (16-byte aligned
+// ranges, rounded outwards) that completes on the stage's mbarrier.  The warp
+// processes tile i while the copies of tiles i+1 .. i+S-1 are in flight, then
+// re-arms the stage with tile i+S.  A single row longer than a tile is read from
+// global memory directly.  Products, row sums and epilogues are those of
+// spmv_tiles on the same wide tiles, in the same order, so the staged and the
+// plain-load forms give identical results.  Every
+// mbarrier wait is bounded; a wait that runs out stops the warp's work and
+// returns false (the caller then ends the solve with SCYLLA_DEVICE_TIMEOUT).
+template <typename T>
+struct Staged {
+  static constexpr int kStages = 2;
+  static constexpr int kNnz = kTileNnz + 8;   // a tile's nonzeros from its aligned start, rounded up
+  static constexpr int kRows = kWideRows + 8;  // row pointers / rows of a wide tile from the aligned start, rounded up
+  static constexpr int kVecs = 5;
+  static constexpr int kColsOff = 0;
+  static constexpr int kValsOff = kColsOff + kNnz * 4;
+  static constexpr int kRpOff = kValsOff + kNnz * int(sizeof(T));
+  static constexpr int kVecOff = kRpOff + kRows * 4;
+  static constexpr int kStageBytes = kVecOff + kVecs * kRows * int(sizeof(T));
+  static constexpr int kWarpBytes = kStages * kStageBytes + 64;  // + the stages' mbarriers
+  static constexpr int kBlockBytes = kWarpsPerBlock * kWarpBytes;
+  static_assert(kValsOff % 16 == 0 && kRpOff % 16 == 0 && kVecOff % 16 == 0 && kStageBytes % 16 == 0, "align");
+  static_assert((kRows * int(sizeof(T))) % 16 == 0, "vector slots");
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return unsigned(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arm(unsigned long long* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, unsigned long long* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(b))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long clock_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait for the phase of parity `parity` to complete
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity, unsigned long long limit_ns) {
+  if (mbar_test(b, parity)) return true;
+  const unsigned long long t0 = clock_ns();
+  while (!mbar_test(b, parity))
+    if (clock_ns() - t0 > limit_ns) return false;
+  return true;
+}
+
+struct TileBounds {
+  int r0, r1, p0, p1;
+  __device__ __forceinline__ bool longrow() const { return r1 - r0 == 1 && p1 - p0 > kTileNnz; }
+};
+
+// one staged tile: lane 0 arms the stage's mbarrier with the total byte count and
+// issues the copies; vec_mask selects the epilogue vectors to stage
+template <typename T, typename Epi>
+__device__ __forceinline__ void stage_issue(char* st, unsigned long long* bar, const TileBounds& tb,
+                                            const int* rowptr, const int* cols, const T* vals, const Epi& epi,
+                                            int vec_mask) {
+  typedef Staged<T> S;
+  const int base = tb.p0 & ~(kVec - 1);
+  const int ncv = (tb.p1 - base + kVec - 1) & ~(kVec - 1);
+  const int rb = tb.r0 & ~3;
+  const int nrp = (tb.r1 + 1 - rb + 3) & ~3;
+  const int nv = (tb.r1 - rb + 3) & ~3;
+  unsigned bytes = unsigned(nrp * 4);
+  if (ncv > 0) bytes += unsigned(ncv * (4 + int(sizeof(T))));
+#pragma unroll
+  for (int k = 0; k < S::kVecs; ++k)
+    if (vec_mask & (1 << k)) bytes += unsigned(nv * int(sizeof(T)));
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the warp's reads of this stage come first
+  mbar_arm(bar, bytes);
+  if (ncv > 0) {
+    bulk_copy(st + S::kColsOff, cols + base, unsigned(ncv * 4), bar);
+    bulk_copy(st + S::kValsOff, vals + base, unsigned(ncv * int(sizeof(T))), bar);
+  }
+  bulk_copy(st + S::kRpOff, rowptr + rb, unsigned(nrp * 4), bar);
+#pragma unroll
+  for (int k = 0; k < S::kVecs; ++k)
+    if (vec_mask & (1 << k))
+      bulk_copy(st + S::kVecOff + k * S::kRows * int(sizeof(T)), epi.stage_vec(k) + rb, unsigned(nv * int(sizeof(T))),
+                bar);
+}
+
+// the warp's tiles gwarp, gwarp + nwarps, ...; gather(c) returns the gathered entry
+// (skip_gather: the row sums are not needed, as for a primal retry)
+template <typename T, typename Gather, typename Epi>
+__device__ bool staged_tiles(const int2* __restrict__ tiles, int ntiles, const int* __restrict__ rowptr,
+                             const int* __restrict__ cols, const T* __restrict__ vals, Gather& gat, Epi& epi,
+                             int vec_mask, bool skip_gather, char* wsm, unsigned long long limit_ns) {
+  typedef Staged<T> S;
+  constexpr int NS = S::kStages;
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(wsm + NS * S::kStageBytes);
+  if (lane == 0) {
+    for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  auto bounds = [&](int t) {
+    const int2 ta = __ldg(tiles + t), tb2 = __ldg(tiles + t + 1);
+    return TileBounds{ta.x, tb2.x, ta.y, tb2.y};
+  };
+  // stage s holds tile gwarp + (i) * nwarps for i = s, s + NS, ...; `armed` marks
+  // stages with copies in flight, `par` their current phase parity
+  unsigned armed = 0, par = 0;
+  TileBounds tb[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int t = gwarp + s * nwarps;
+    if (t < ntiles) {
+      tb[s] = bounds(t);
+      if (!tb[s].longrow()) {
+        if (lane == 0) stage_issue<T>(wsm + s * S::kStageBytes, &bars[s], tb[s], rowptr, cols, vals, epi, vec_mask);
+        armed |= 1u << s;
+      }
+    }
+  }
+  bool ok = true;
+  int i = 0;
+  for (int t = gwarp; t < ntiles; t += nwarps, ++i) {
+    const int s = i % NS;
+    const TileBounds b = tb[s];
+    char* st = wsm + s * S::kStageBytes;
+    if (b.longrow()) {
+      // a single long row, straight from global memory
+      const int base = b.p0 & ~(kVec - 1);
+      const typename Epi::Pre pre = epi.load(b.r0);
+      T acc = T(0);
+      if (!skip_gather) {
+        for (int p = base + lane * kVec; p < b.p1; p += 32 * kVec) {
+          int cc[4];
+          T vv[4];
+          ld4(cols + p, cc);
+          ld4(vals + p, vv);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int q = p + e;
+            if (q >= b.p0 && q < b.p1) acc = fma_t<T>(vv[e], gat(cc[e]), acc);
+          }
+        }
+      }
+      acc = warp_sum(acc);
+      const T sv[1] = {acc};
+      if (lane == 0) epi.finish(b.r0, sv, pre);
+    } else {
+      if (!mbar_wait(&bars[s], (par >> s) & 1u, limit_ns)) {
+        ok = false;
+        break;
+      }
+      par ^= 1u << s;
+      armed &= ~(1u << s);
+      const int base = b.p0 & ~(kVec - 1), off = b.p0 - base, len = b.p1 - b.p0;
+      const int rb = b.r0 & ~3;
+      const int* scol = reinterpret_cast<const int*>(st + S::kColsOff);
+      T* sval = reinterpret_cast<T*>(st + S::kValsOff);
+      const int* srp = reinterpret_cast<const int*>(st + S::kRpOff);
+      const T* svec = reinterpret_cast<const T*>(st + S::kVecOff);
+      // rows as in spmv_tiles on wide tiles: slot j of a lane is row lane / L (rows
+      // split over L lanes) or row lane + 32 j
+      const int nr = b.r1 - b.r0, L = row_lanes(nr), sub = L > 1 ? lane % L : 0;
+      int q0[kWideRPL], q1[kWideRPL];
+      typename Epi::Pre pre[kWideRPL];
+#pragma unroll
+      for (int j = 0; j < kWideRPL; ++j) {
+        const int rl = L > 1 ? (j == 0 ? lane / L : nr) : lane + 32 * j;
+        q0[j] = q1[j] = 0;
+        pre[j] = typename Epi::Pre{};
+        if (rl < nr) {
+          q0[j] = srp[b.r0 + rl - rb] - b.p0;
+          q1[j] = srp[b.r0 + rl + 1 - rb] - b.p0;
+          if (sub == 0) pre[j] = epi.stage_pre(svec, S::kRows, b.r0 + rl - rb);
+        }
+      }
+      if (!skip_gather) {
+        // products in place of the values; up to eight gathers per lane in flight
+        T g[kTileNnz / 32];
+#pragma unroll
+        for (int j = 0; j < kTileNnz / 32; ++j) {
+          const int k = lane + 32 * j;
+          g[j] = k < len ? gat(scol[off + k]) : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < kTileNnz / 32; ++j) {
+          const int k = lane + 32 * j;
+          if (k < len) sval[off + k] = sval[off + k] * g[j];
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < kWideRPL; ++j) {
+        const int rl = L > 1 ? (j == 0 ? lane / L : nr) : lane + 32 * j;
+        T acc = T(0);
+        if (rl < nr && !skip_gather)
+          for (int q = q0[j] + sub; q < q1[j]; q += L) acc += sval[off + q];
+        if (j == 0)
+          for (int o = L >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        const T sv[1] = {acc};
+        if (rl < nr && sub == 0) epi.finish(b.r0 + rl, sv, pre[j]);
+      }
+      __syncwarp();
+    }
+    // re-arm this stage with the warp's tile NS steps ahead
+    const int tn = t + NS * nwarps;
+    if (tn < ntiles) {
+      tb[s] = bounds(tn);
+      if (!tb[s].longrow()) {
+        if (lane == 0) stage_issue<T>(st, &bars[s], tb[s], rowptr, cols, vals, epi, vec_mask);
+        armed |= 1u << s;
+      }
+    }
+  }
+  if (!ok) {
+    // let the copies in flight land (bounded) before the shared memory is released
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (armed & (1u << s)) mbar_wait(&bars[s], (par >> s) & 1u, limit_ns);
+  }
+  return ok;
+}
+
+template <typename T>
+__device__ __forceinline__ void staged_timeout(Control* ctl) {
+  ctl->status = SCYLLA_DEVICE_TIMEOUT;
+  ctl->done = 1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_primal_st(DevLP<T> d) {
+  extern __shared__ __align__(128) char dsm[];
+  Control* ctl = d.ctl;
+  pdl_enter();
+  if (ctl->done || ctl->k >= ctl->iter_limit) return;
+  const SlotView<T> v = make_view<T>(ctl);
+  PrimalEpi<T> epi;
+  setup_primal(epi, d, v);
+  const bool cached = v.aty_valid != 0;
+  epi.use_cached = cached;
+  const T* __restrict__ yc = d.Y[v.cur];
+  auto gat = [&](int i) { return __ldg(yc + i); };
+  char* wsm = dsm + (threadIdx.x >> 5) * Staged<T>::kWarpBytes;
+  const bool ok = staged_tiles<T>(d.t_tiles_w, d.t_ntiles_w, d.t_rowptr, d.t_cols, d.t_vals, gat, epi,
+                                  v.do_avg ? 31 : 15, cached, wsm, d.wait_ns);
+  if (!ok && (threadIdx.x & 31) == 0) staged_timeout<T>(ctl);
+  const typename AccOf<T>::type acc[kNP] = {epi.acc};
+  block_store_partials<kNP>(acc, acc_part<T>(d.part_p));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_dual_st(DevLP<T> d) {
+  typedef typename AccOf<T>::type A;
+  extern __shared__ __align__(128) char dsm[];
+  Control* ctl = d.ctl;
+  pdl_enter();
+  if (ctl->done || ctl->k >= ctl->iter_limit) return;
+  const SlotView<T> v = make_view<T>(ctl);
+  DualEpi<T> epi;
+  setup_dual(epi, d, v);
+  const T* __restrict__ xn = d.X[v.nxt];
+  auto gat = [&](int j) { return __ldg(xn + j); };
+  char* wsm = dsm + (threadIdx.x >> 5) * Staged<T>::kWarpBytes;
+  const bool ok = staged_tiles<T>(d.a_tiles_w, d.a_ntiles_w, d.a_rowptr, d.a_cols, d.a_vals, gat, epi,
+                                  v.do_avg ? 31 : 15, false, wsm, d.wait_ns);
+  if (!ok && (threadIdx.x & 31) == 0) staged_timeout<T>(ctl);
+  const A acc[kND] = {epi.acc0, epi.acc1};
+  block_store_partials<kND>(acc, acc_part<T>(d.part_d));
+  if (!is_last_block(&ctl->cnt_dual)) return;
+  __shared__ StepPre pre;
+  if (threadIdx.x == 0) pre = step_pre<A>(ctl, d.step_fac, d.n_check);
+  __shared__ A red[kNP + kND];
+  static_assert(3 * (kThreads - 32) * sizeof(A) <= Staged<T>::kBlockBytes, "reduction scratch");
+  reduce_step<A>(acc_part<T>(d.part_p), d.grid_p, acc_part<T>(d.part_d), d.grid_d, reinterpret_cast<A*>(dsm), red);
+  if (threadIdx.x == 0) {
+    if (!ctl->done) step_control<A>(ctl, pre, red[0], red[1], red[2], d.trace_steps, d.trace_cap);
     ctl->cnt_dual = 0;
   }
 }
@@ -1714,11 +2064,12 @@ cudaError_t launch_solve_init(const DevLP<T>& d, double tol, long long iter_limi
 // launch of a per-attempt kernel, with the programmatic-serialization attribute when
 // d.pdl is set (the kernel then overlaps its launch with its predecessor's tail)
 template <typename T>
-static cudaError_t launch_step_kernel(void (*kernel)(DevLP<T>), int grid, const DevLP<T>& d, cudaStream_t st) {
+static cudaError_t launch_step_kernel(void (*kernel)(DevLP<T>), int grid, const DevLP<T>& d, cudaStream_t st,
+                                      int smem = 0) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = size_t(smem);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1737,11 +2088,21 @@ cudaError_t launch_check(const DevLP<T>& d, cudaStream_t st) {
 
 template <typename T>
 cudaError_t launch_primal(const DevLP<T>& d, cudaStream_t st) {
-  return launch_step_kernel<T>(d.prefetch ? k_primal<T, true> : k_primal<T, false>, d.grid_p, d, st);
+  switch (d.form_p) {
+    case kFormStaged: return launch_step_kernel<T>(k_primal_st<T>, d.grid_p, d, st, Staged<T>::kBlockBytes);
+    case kFormPrefetch: return launch_step_kernel<T>(k_primal<T, kFormPrefetch>, d.grid_p, d, st);
+    case kFormWide: return launch_step_kernel<T>(k_primal<T, kFormWide>, d.grid_p, d, st);
+    default: return launch_step_kernel<T>(k_primal<T, kFormPlain>, d.grid_p, d, st);
+  }
 }
 template <typename T>
 cudaError_t launch_dual(const DevLP<T>& d, cudaStream_t st) {
-  return launch_step_kernel<T>(d.prefetch ? k_dual<T, true> : k_dual<T, false>, d.grid_d, d, st);
+  switch (d.form_d) {
+    case kFormStaged: return launch_step_kernel<T>(k_dual_st<T>, d.grid_d, d, st, Staged<T>::kBlockBytes);
+    case kFormPrefetch: return launch_step_kernel<T>(k_dual<T, kFormPrefetch>, d.grid_d, d, st);
+    case kFormWide: return launch_step_kernel<T>(k_dual<T, kFormWide>, d.grid_d, d, st);
+    default: return launch_step_kernel<T>(k_dual<T, kFormPlain>, d.grid_d, d, st);
+  }
 }
 
 template <typename T>
@@ -1813,17 +2174,29 @@ cudaError_t launch_persistent(const DevLP<T>& d, void* grid_bar, int grid, doubl
                                      kPersistentSmem, st);
 }
 
+// grid of a per-attempt kernel (side 0: primal, 1: dual) of form `form`, or of a
+// check kernel (side 2: columns, 3: rows): resident blocks per SM times the SMs,
+// at most one warp per tile
 template <typename T>
-int occupancy_grid(int kernel_id, int work_tiles) {
+int occupancy_grid(int side, int form, int work_tiles) {
   int per_sm = 1;
+  int smem = 0;
+  void (*k)(DevLP<T>) = nullptr;
+  if (side == 2) k = k_check_cols<T>;
+  else if (side == 3) k = k_check_rows<T>;
+  else if (form == kFormStaged) {
+    k = side == 0 ? k_primal_st<T> : k_dual_st<T>;
+    smem = Staged<T>::kBlockBytes;
+  } else if (form == kFormWide) k = side == 0 ? k_primal<T, kFormWide> : k_dual<T, kFormWide>;
+  else if (form == kFormPrefetch) k = side == 0 ? k_primal<T, kFormPrefetch> : k_dual<T, kFormPrefetch>;
+  else k = side == 0 ? k_primal<T, kFormPlain> : k_dual<T, kFormPlain>;
   cudaError_t e = cudaSuccess;
-  switch (kernel_id) {
-    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_primal<T, false>, kThreads, 0); break;
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dual<T, false>, kThreads, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_check_cols<T>, kThreads, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_check_rows<T>, kThreads, 0); break;
+  if (smem > 0) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
   }
-  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
   long long need = (work_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (need < 1) need = 1;
   const long long cap = (long long)per_sm * device_sm_count();
@@ -1842,7 +2215,7 @@ int occupancy_grid(int kernel_id, int work_tiles) {
   template cudaError_t launch_get_y<T>(const DevLP<T>&, double*, int, cudaStream_t);                      \
   template cudaError_t launch_set_xy<T>(const DevLP<T>&, const double*, const double*, cudaStream_t);     \
   template cudaError_t launch_init_point<T>(const DevLP<T>&, cudaStream_t);                               \
-  template int occupancy_grid<T>(int, int);                                                                \
+  template int occupancy_grid<T>(int, int, int);                                                           \
   template int persistent_blocks_per_sm<T>();                                                             \
   template cudaError_t launch_persistent<T>(const DevLP<T>&, void*, int, double, cudaStream_t);
 

@@ -88,8 +88,8 @@ namespace {
 
 size_t padded(size_t nnz) { return scylla::padded_len(nnz); }
 
-std::vector<int2> build_tiles(const std::vector<int>& rowptr) {
-  return scylla::build_tiles_range(rowptr, 0, int(rowptr.size()) - 1);
+std::vector<int2> build_tiles(const std::vector<int>& rowptr, int max_rows = scylla::kTileRows) {
+  return scylla::build_tiles_range(rowptr, 0, int(rowptr.size()) - 1, max_rows);
 }
 
 }  // namespace
@@ -99,9 +99,9 @@ namespace scylla {
 size_t padded_len(size_t nnz) { return ((nnz + 3) & ~size_t(3)) + 4; }
 
 // contiguous row ranges of [r_begin, r_end) with at most kTileNnz nonzeros and
-// kTileRows rows; a longer row is a tile of its own.  Each boundary is stored as
+// max_rows rows; a longer row is a tile of its own.  Each boundary is stored as
 // (row, rowptr[row]).
-std::vector<int2> build_tiles_range(const std::vector<int>& rowptr, int r_begin, int m) {
+std::vector<int2> build_tiles_range(const std::vector<int>& rowptr, int r_begin, int m, int max_rows) {
   std::vector<int2> t;
   t.reserve((m - r_begin) / 4 + 2);
   t.push_back(make_int2(r_begin, rowptr[r_begin]));
@@ -114,7 +114,7 @@ std::vector<int2> build_tiles_range(const std::vector<int>& rowptr, int r_begin,
       continue;
     }
     int cnt = 0, nz = 0;
-    while (r < m && cnt < kTileRows) {
+    while (r < m && cnt < max_rows) {
       const int l2 = rowptr[r + 1] - rowptr[r];
       if (nz + l2 > kTileNnz) break;
       nz += l2;
@@ -209,7 +209,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   if (lp->p.trace_capacity < 0) FAIL(SCYLLA_ERR_INVALID_ARG, "trace_capacity must be >= 0");
   if (lp->p.use_graph < 0 || lp->p.use_graph > 3) FAIL(SCYLLA_ERR_INVALID_ARG, "use_graph must be 0..3");
   if (!(lp->p.device_wait_limit_s > 0.0)) FAIL(SCYLLA_ERR_INVALID_ARG, "device_wait_limit_s must be > 0");
-  if (lp->p.prefetch < 0 || lp->p.prefetch > 2) FAIL(SCYLLA_ERR_INVALID_ARG, "prefetch must be 0..2");
+  if (lp->p.prefetch < 0 || lp->p.prefetch > 4) FAIL(SCYLLA_ERR_INVALID_ARG, "prefetch must be 0..4");
   if (lp->p.precision != SCYLLA_PREC_FP64 && lp->p.precision != SCYLLA_PREC_MIXED)
     FAIL(SCYLLA_ERR_INVALID_ARG, "unknown precision");
   CK(cudaGetDevice(&lp->device));
@@ -309,26 +309,45 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
 
   // ---- grid sizes and scratch
   const bool mixed = lp->p.precision == SCYLLA_PREC_MIXED;
-  if (mixed) {
-    lp->grid_p = occupancy_grid<float>(0, lp->t_ntiles);
-    lp->grid_d = occupancy_grid<float>(1, lp->a_ntiles);
-    lp->grid_c1 = occupancy_grid<float>(2, lp->t_ntiles);
-    lp->grid_c2 = occupancy_grid<float>(3, lp->a_ntiles);
-  } else {
-    lp->grid_p = occupancy_grid<double>(0, lp->t_ntiles);
-    lp->grid_d = occupancy_grid<double>(1, lp->a_ntiles);
-    lp->grid_c1 = occupancy_grid<double>(2, lp->t_ntiles);
-    lp->grid_c2 = occupancy_grid<double>(3, lp->a_ntiles);
-  }
-  // first-tile prefetch: pays when the per-attempt kernels' matrix data stay in L2
-  // between attempts (the kernels are then latency-bound); a DRAM-resident matrix
-  // keeps the lighter kernels
+  // form of the per-attempt kernels.  When A, A^T and the vectors fit in half of L2
+  // they stay there between attempts and the kernels are latency-bound: 32-row
+  // tiles, 64 registers, four blocks per SM (measured: loading the first tile before
+  // the dependency wait gains nothing there).  Otherwise they are bound by the bytes
+  // in flight: wide tiles (up to kWideRows rows, several per lane; several times the
+  // bytes of a 32-row tile on short rows) and 80 registers, which keep more loads in
+  // flight per warp.  prefetch = 1 .. 4 force a form.
+  std::vector<int2> atw, ttw;
   {
     int l2 = 0;
     CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, lp->device));
     const double vb = mixed ? 4.0 : 8.0;
     const double bytes = 2.0 * double(nnz) * (4.0 + vb) + 12.0 * double(m + n) * vb;
-    lp->prefetch = lp->p.prefetch == 1 || (lp->p.prefetch == 0 && bytes <= 0.5 * double(l2));
+    const bool fits = bytes <= 0.5 * double(l2);
+    const int pf = lp->p.prefetch;
+    int form = kFormPlain;
+    if (pf == 1) form = kFormPrefetch;
+    else if (pf == 2 || (pf == 0 && !fits)) form = kFormWide;
+    else if (pf == 3) form = kFormStaged;
+    lp->form_p = lp->form_d = form;
+    if (form == kFormWide || form == kFormStaged) {
+      atw = build_tiles(rp, kWideRows);
+      ttw = build_tiles(tp, kWideRows);
+    }
+  }
+  const bool wide_p = lp->form_p == kFormWide || lp->form_p == kFormStaged;
+  const bool wide_d = lp->form_d == kFormWide || lp->form_d == kFormStaged;
+  lp->t_ntiles_w = wide_p ? int(ttw.size()) - 1 : lp->t_ntiles;
+  lp->a_ntiles_w = wide_d ? int(atw.size()) - 1 : lp->a_ntiles;
+  if (mixed) {
+    lp->grid_p = occupancy_grid<float>(0, lp->form_p, lp->t_ntiles_w);
+    lp->grid_d = occupancy_grid<float>(1, lp->form_d, lp->a_ntiles_w);
+    lp->grid_c1 = occupancy_grid<float>(2, 0, lp->t_ntiles);
+    lp->grid_c2 = occupancy_grid<float>(3, 0, lp->a_ntiles);
+  } else {
+    lp->grid_p = occupancy_grid<double>(0, lp->form_p, lp->t_ntiles_w);
+    lp->grid_d = occupancy_grid<double>(1, lp->form_d, lp->a_ntiles_w);
+    lp->grid_c1 = occupancy_grid<double>(2, 0, lp->t_ntiles);
+    lp->grid_c2 = occupancy_grid<double>(3, 0, lp->a_ntiles);
   }
   // persistent cooperative solve: one grid of co-resident blocks, if it fits
   {
@@ -349,9 +368,11 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     lp->a_rowptr = ar.take<int>(m + 1);
     lp->a_cols = ar.take<int>(padded(nnz));
     lp->a_tiles = ar.take<int2>(at.size());
+    lp->a_tiles_w = wide_d ? ar.take<int2>(atw.size()) : lp->a_tiles;
     lp->t_rowptr = ar.take<int>(n + 1);
     lp->t_cols = ar.take<int>(padded(nnz));
     lp->t_tiles = ar.take<int2>(tt.size());
+    lp->t_tiles_w = wide_p ? ar.take<int2>(ttw.size()) : lp->t_tiles;
     lp->a_vals64 = ar.take<double>(padded(nnz));
     lp->t_vals64 = ar.take<double>(padded(nnz));
     lp->a_vals32 = mixed ? ar.take<float>(padded(nnz)) : nullptr;
@@ -423,6 +444,8 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   CK(cudaMemcpyAsync(lp->t_rowptr, tp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->t_cols, tr.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->t_tiles, tt.data(), sizeof(int2) * tt.size(), cudaMemcpyHostToDevice, st));
+  if (wide_d) CK(cudaMemcpyAsync(lp->a_tiles_w, atw.data(), sizeof(int2) * atw.size(), cudaMemcpyHostToDevice, st));
+  if (wide_p) CK(cudaMemcpyAsync(lp->t_tiles_w, ttw.data(), sizeof(int2) * ttw.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->a_vals64, va, sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->t_vals64, tv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->c_un, cA.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
@@ -513,6 +536,7 @@ void fill_dev(DevLP<T>& d, scylla_lp* lp) {
   d.n = lp->n;
   d.a_rowptr = lp->a_rowptr; d.a_cols = lp->a_cols; d.a_tiles = lp->a_tiles; d.a_ntiles = lp->a_ntiles;
   d.t_rowptr = lp->t_rowptr; d.t_cols = lp->t_cols; d.t_tiles = lp->t_tiles; d.t_ntiles = lp->t_ntiles;
+  d.a_tiles_w = lp->a_tiles_w; d.a_ntiles_w = lp->a_ntiles_w; d.t_tiles_w = lp->t_tiles_w; d.t_ntiles_w = lp->t_ntiles_w;
   d.a_vals64 = lp->a_vals64;
   d.t_vals64 = lp->t_vals64;
   if (mixed) {
@@ -554,7 +578,9 @@ void fill_dev(DevLP<T>& d, scylla_lp* lp) {
   d.p_hash = lp->p_hash;
   d.n_check = lp->p.n_check;
   d.pdl = lp->p.pdl ? 1 : 0;
-  d.prefetch = lp->prefetch ? 1 : 0;
+  d.form_p = lp->form_p;
+  d.form_d = lp->form_d;
+  d.wait_ns = (unsigned long long)(lp->p.device_wait_limit_s * 1e9);
   d.trace_steps = lp->trace_steps;
   d.trace_checks = lp->trace_checks;
   d.trace_cap = lp->p.trace_capacity;

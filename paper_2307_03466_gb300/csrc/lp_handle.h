@@ -38,19 +38,20 @@ struct scylla_lp {
   // LP iterated on the device (original + auxiliary)
   int m = 0, n = 0, nnz = 0;
   int a_ntiles = 0, t_ntiles = 0;
+  int a_ntiles_w = 0, t_ntiles_w = 0;  // wide tiles of the plain-load per-attempt kernels
   int grid_p = 1, grid_d = 1, grid_c1 = 1, grid_c2 = 1, red_blocks = 1;
 
   void* arena = nullptr;
   size_t arena_bytes = 0;
   int *a_rowptr = nullptr, *a_cols = nullptr;
   int *t_rowptr = nullptr, *t_cols = nullptr;
-  int2 *a_tiles = nullptr, *t_tiles = nullptr;
+  int2 *a_tiles = nullptr, *t_tiles = nullptr, *a_tiles_w = nullptr, *t_tiles_w = nullptr;
   double* step_fac = nullptr;
   double* pp_part = nullptr;
   unsigned long long* p_hash = nullptr;
   void* grid_bar = nullptr;
   int p_grid = 0;  // persistent grid (0: that mode is unavailable)
-  bool prefetch = false;  // per-attempt kernels prefetch their first tile (scylla_params.prefetch)
+  int form_p = 0, form_d = 0;  // forms of the primal / dual per-attempt kernels (kForm*)
   double *a_vals64 = nullptr, *t_vals64 = nullptr;
   float *a_vals32 = nullptr, *t_vals32 = nullptr;
   double *c_un = nullptr, *l_un = nullptr, *u_un = nullptr, *lo_un = nullptr, *hi_un = nullptr;
