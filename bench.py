@@ -121,7 +121,7 @@ def kernel_bytes(m, n, nnz, sv, sx):
     return primal, dual
 
 
-def traffic_for(kernel: str):
+def traffic_for(kernel: str, workload: str = WORKLOAD):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the
     current kernel source (else null)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -134,7 +134,7 @@ def traffic_for(kernel: str):
     src = os.path.join(ROOT, "paper_2307_03466_gb300", "csrc", "kernels.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     ent = d.get(kernel)
-    if not ent or ent.get("kernels_cu_sha256") != sha or ent.get("workload") != WORKLOAD:
+    if not ent or ent.get("kernels_cu_sha256") != sha or ent.get("workload") != workload:
         return None
     return ent.get("dram_bytes_per_launch")
 
@@ -472,7 +472,7 @@ def dram_resident(S, peak, peak_kind):
                      "gbs": {"primal": gp, "dual": gd},
                      "roofline": {"bound": "hbm", "kernel": kname, "achieved": kb / (kms * 1e6), "peak": peak,
                                   "unit": "GB/s", "frac": kb / (kms * 1e6) / peak, "peak_source": peak_kind,
-                                  "bytes_per_launch": kb}}
+                                  "bytes_per_launch": kb, "traffic": traffic_for(kname + "@mcf", DRAM_WORKLOAD)}}
         lp.close()
         torch.cuda.synchronize()
     return out
