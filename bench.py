@@ -53,6 +53,22 @@ def instance(rank: int):
     return I.packing_covering(m=50_000, n=100_000, per_col=10, seed=1002 + rank)
 
 
+# ------------------------------------------------------------ across ranks ---
+def combine_ranks(dist, times, counts, device):
+    """Whole-job figures over the ranks of a multi-GPU run: the slowest rank's time
+    for each timed region (MAX) and the total units of work (SUM).  Each rank solves
+    its own LP (weak scaling: no data-path collective), so these two reductions are
+    the only communication.  With dist = None (one process) the inputs come back."""
+    if dist is None:
+        return [float(t) for t in times], [float(c) for c in counts]
+    import torch
+    tt = torch.tensor([float(t) for t in times], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    cc = torch.tensor([float(c) for c in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(cc, op=dist.ReduceOp.SUM)
+    return tt.tolist(), cc.tolist()
+
+
 # ----------------------------------------------------------------- clocks ---
 class Clocks:
     """nvidia-smi samples (every 50 ms) during the timed region."""
@@ -249,13 +265,7 @@ def run_ours(args):
     it_d = sum(r.iterations for r in res_d)
     t_d = sum(r.seconds for r in res_d)
     n_launch = sum(launches(r) for r in res_m)
-    if dist is not None:
-        tt = torch.tensor([t_m, wall, t_d], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ii = torch.tensor([it_m, it_d, n_launch], dtype=torch.float64, device="cuda")
-        dist.all_reduce(ii, op=dist.ReduceOp.SUM)
-        t_m, wall, t_d = tt.tolist()
-        it_m, it_d, n_launch = ii.tolist()
+    (t_m, wall, t_d), (it_m, it_d, n_launch) = combine_ranks(dist, (t_m, wall, t_d), (it_m, it_d, n_launch), "cuda")
 
     last = res_m[-1]
     last_d = res_d[-1]
