@@ -1,0 +1,126 @@
+"""Parity at the benchmark sizes, in the launch configuration bench.py times.
+
+The packing/covering workload (m = 50k, n = 100k, 1M nonzeros; the bench step) and
+the MCF-shaped workload (n = 8.8M, m = 1.8M, 25.6M nonzeros; the DRAM-resident
+case, whose per-attempt kernels take the wide-tile form) are both small enough for
+the oracle to run a few attempts:
+
+- FP64: fixed-step attempts from the cold start against the oracle, every entry
+  (1e-9), and on the packing/covering workload 32 adaptive attempts replayed on
+  the device's decisions (the same check as the small parity instances).
+- FP32-mixed (the bench configuration): one attempt from a seeded state inside the
+  bounds against the oracle's FP64 attempt from the same state, every entry on the
+  packing/covering workload and sampled columns and rows (computed one by one by
+  the oracle) on the MCF workload, within FP32 rounding.
+- FP32-mixed solves to rel-KKT 1e-4, the bench's stopping rule, re-evaluated by the
+  oracle on the returned point.
+"""
+import numpy as np
+import pytest
+
+from oracle import pdhg as O
+from paper_2307_03466_gb300 import instances as I
+from tests.gpu_common import gpu_available, pair, rel_err
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
+
+MIXED_TOL = 2e-5  # FP32 iterates and products, FP32 row sums of ~10-20 terms, one attempt
+
+
+@pytest.fixture(scope="module")
+def packcover():
+    # the bench step's workload (bench.instance(0))
+    return I.packing_covering(m=50_000, n=100_000, per_col=10, seed=1002)
+
+
+@pytest.fixture(scope="module")
+def mcf():
+    return I.mcf()
+
+
+def seeded_state(inst, seed):
+    """A state inside the column bounds, and a small dual, from a seeded generator."""
+    rng = np.random.default_rng(seed)
+    x = np.clip(rng.uniform(-0.5, 1.5, inst.n) * np.where(np.isfinite(inst.u), np.maximum(inst.u, 1.0), 1.0),
+                inst.l, inst.u)
+    y = rng.normal(0.0, 0.1, inst.m)
+    return x, y
+
+
+def one_attempt(inst, precision, x0, y0, prefetch=0):
+    """Device: one fixed-step attempt from (x0, y0); oracle: the same attempt in FP64
+    (both take the oracle's own initial step size and primal weight)."""
+    g, o = pair(inst, precision=precision, adaptive_step=False, restarts=False, prefetch=prefetch)
+    eta, om = o.eta, o.omega
+    g.set_state(x0, y0, eta, om)
+    r = g.pdhg_solve(0.0, 1)
+    assert r.iterations == 1
+    x1, y1, _, _ = g.get_state()
+    g.close()
+    o.set_state(x0, y0)
+    return x1, y1, o, eta, om
+
+
+def test_packcover_fp64_fixed_step_from_cold_start(packcover):
+    g, o = pair(packcover, adaptive_step=False, restarts=False)
+    g.pdhg_solve(0.0, 32)
+    o.solve(0.0, 32)
+    xg, yg, _, _ = g.get_state()
+    assert rel_err(xg, o.primal()) <= 1e-9 and rel_err(yg, o.dual()) <= 1e-9
+    g.close()
+
+
+def test_packcover_fp64_adaptive_on_device_decisions(packcover):
+    """32 adaptive attempts (a check at the start and at the limit) replayed on the
+    device's step-size and restart decisions.  The two sides sum rows in different
+    orders; over longer runs at this size the rounding difference grows past 1e-9
+    (4e-8 after 100 attempts), as it does past 100 attempts on the small instances."""
+    from tests.test_gpu_pdhg import compare_after
+    compare_after(packcover, 32)
+
+
+def test_packcover_mixed_one_attempt_every_entry(packcover):
+    x0, y0 = seeded_state(packcover, 7)
+    x1, y1, o, eta, om = one_attempt(packcover, 1, x0, y0)
+    xs, ys = o.pdhg_step(o.x, o.y, eta, om)
+    assert rel_err(x1, o.primal(xs)) <= MIXED_TOL
+    assert rel_err(y1, o.dual(ys)) <= MIXED_TOL
+
+
+def test_packcover_mixed_solve_reaches_1e4_checked_by_oracle(packcover):
+    g, o = pair(packcover, precision=1)
+    r = g.pdhg_solve(1e-4, 100000)
+    assert r.status == O.CONVERGED and r.rel_kkt <= 1e-4
+    x, y, _, _ = g.get_state()
+    ev = o.evaluate(x / o.C, y / o.R)
+    assert ev.rel_kkt <= 1.2e-4, ev
+    g.close()
+
+
+def test_mcf_fp64_fixed_step_from_cold_start_wide_tiles(mcf):
+    g, o = pair(mcf, adaptive_step=False, restarts=False)
+    g.pdhg_solve(0.0, 4)
+    o.solve(0.0, 4)
+    xg, yg, _, _ = g.get_state()
+    assert rel_err(xg, o.primal()) <= 1e-9 and rel_err(yg, o.dual()) <= 1e-9
+    g.close()
+
+
+@pytest.mark.parametrize("prefetch", [0, 3])
+def test_mcf_mixed_one_attempt_sampled(mcf, prefetch):
+    """prefetch 0: the automatic form (wide tiles, plain loads); 3: wide tiles staged
+    in shared memory by bulk copies."""
+    x0, y0 = seeded_state(mcf, 11)
+    x1, y1, o, eta, om = one_attempt(mcf, 1, x0, y0, prefetch=prefetch)
+    rng = np.random.default_rng(5)
+    cols = np.sort(rng.choice(mcf.n, 4000, replace=False))
+    rows = np.sort(rng.choice(mcf.m, 4000, replace=False))
+    xs_c = o.primal_step_at(cols, o.x, o.y, eta, om)
+    assert rel_err(x1[cols], xs_c * o.C[cols]) <= MIXED_TOL
+    # the dual step of a row needs the oracle's whole new primal iterate
+    xs_all, ys_all = o.pdhg_step(o.x, o.y, eta, om)
+    ys_r = o.dual_step_at(rows, o.x, xs_all, o.y, eta, om)
+    np.testing.assert_allclose(ys_r, ys_all[rows], rtol=1e-13, atol=0)
+    assert rel_err(y1[rows], ys_r * o.R[rows]) <= MIXED_TOL
+    # and every entry, against the oracle's whole attempt
+    assert rel_err(x1, o.primal(xs_all)) <= MIXED_TOL and rel_err(y1, o.dual(ys_all)) <= MIXED_TOL
