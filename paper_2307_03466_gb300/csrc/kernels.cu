@@ -34,6 +34,20 @@ __device__ __forceinline__ int row_lanes(int nr) {
   return 1 << (31 - __clz(l));
 }
 
+// The tiles of a warp: tile t goes to block t mod G and, within the block, to warp
+// (t div G) mod 8, so every block holds the same number of tiles (within one) and
+// each SM the same share when the grid is a whole number of waves of resident
+// blocks; costly tiles (long rows, often stored together) spread over the blocks.
+// The gathers of a launch are bound by each SM's L1TEX throughput (and the checks
+// by its FP64 pipe), so the busiest SM sets the time.
+struct WarpTiles {
+  int first, end, step;
+};
+__device__ __forceinline__ WarpTiles warp_tiles(int ntiles) {
+  const int G = int(gridDim.x), wpb = int(blockDim.x >> 5);
+  return WarpTiles{int(blockIdx.x) + int(threadIdx.x >> 5) * G, ntiles, wpb * G};
+}
+
 // --------------------------------------------------------------- the SpMV core ---
 // Warp-tile CSR gather.  Each warp takes tiles round-robin.  A multi-row tile (at
 // most kTileNnz nonzeros and 32 rows) is read with 16-byte vector loads of column
@@ -55,8 +69,7 @@ __device__ __forceinline__ bool spmv_tiles(const int2* __restrict__ tiles, int n
                                            const V* __restrict__ vals, Gather& gat, Epi& epi,
                                            Acc* __restrict__ sm, Pro&& pro) {
   const int lane = threadIdx.x & 31;
-  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const WarpTiles wt = warp_tiles(ntiles);
   int r0 = 0, r1 = 0, p0 = 0, p1 = 0;
   int q0[RPL], q1[RPL];
   bool longrow = false;
@@ -95,10 +108,10 @@ __device__ __forceinline__ bool spmv_tiles(const int2* __restrict__ tiles, int n
       }
     }
   };
-  if (PF && gwarp < ntiles) fetch(gwarp);
+  if (PF && wt.first < wt.end) fetch(wt.first);
   if (!pro()) return false;
-  for (int t = gwarp; t < ntiles; t += nwarps) {
-    if (!PF || t != gwarp) fetch(t);
+  for (int t = wt.first; t < wt.end; t += wt.step) {
+    if (!PF || t != wt.first) fetch(t);
     const int base = p0 & ~(kVec - 1);
     if (longrow) {
       const typename Epi::Pre pre = epi.load(r0);
@@ -190,9 +203,8 @@ __device__ __forceinline__ void spmv_tiles_fma(const int2* __restrict__ tiles, i
                                                double* __restrict__ smw) {
   float* __restrict__ sg = reinterpret_cast<float*>(smw + kSmemPerWarp);
   const int lane = threadIdx.x & 31;
-  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int t = gwarp; t < ntiles; t += nwarps) {
+  const WarpTiles wt = warp_tiles(ntiles);
+  for (int t = wt.first; t < wt.end; t += wt.step) {
     const int2 ta = __ldg(tiles + t), tb = __ldg(tiles + t + 1);
     const int r0 = ta.x, r1 = tb.x, p0 = ta.y, p1 = tb.y;
     const int base = p0 & ~(kVec - 1);
@@ -354,9 +366,8 @@ template <typename T, typename Epi>
 __device__ __forceinline__ void tiles_rows(const int2* __restrict__ tiles, int ntiles, const T* __restrict__ src,
                                            Epi& epi) {
   const int lane = threadIdx.x & 31;
-  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int t = gwarp; t < ntiles; t += nwarps) {
+  const WarpTiles wt = warp_tiles(ntiles);
+  for (int t = wt.first; t < wt.end; t += wt.step) {
     const int2 ta = __ldg(tiles + t), tb = __ldg(tiles + t + 1);
     const int nr = tb.x - ta.x, L = row_lanes(nr);
     if (L > 1) {
@@ -720,7 +731,7 @@ __device__ __forceinline__ void stage_issue(char* st, unsigned long long* bar, c
                 bar);
 }
 
-// the warp's tiles gwarp, gwarp + nwarps, ...; gather(c) returns the gathered entry
+// the warp's tiles (warp_tiles); gather(c) returns the gathered entry
 // (skip_gather: the row sums are not needed, as for a primal retry)
 template <typename T, typename Gather, typename Epi>
 __device__ bool staged_tiles(const int2* __restrict__ tiles, int ntiles, const int* __restrict__ rowptr,
@@ -729,8 +740,7 @@ __device__ bool staged_tiles(const int2* __restrict__ tiles, int ntiles, const i
   typedef Staged<T> S;
   constexpr int NS = S::kStages;
   const int lane = threadIdx.x & 31;
-  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const WarpTiles wt = warp_tiles(ntiles);
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(wsm + NS * S::kStageBytes);
   if (lane == 0) {
     for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
@@ -741,14 +751,14 @@ __device__ bool staged_tiles(const int2* __restrict__ tiles, int ntiles, const i
     const int2 ta = __ldg(tiles + t), tb2 = __ldg(tiles + t + 1);
     return TileBounds{ta.x, tb2.x, ta.y, tb2.y};
   };
-  // stage s holds tile gwarp + (i) * nwarps for i = s, s + NS, ...; `armed` marks
+  // stage s holds the warp's tiles i = s, s + NS, ... (tile wt.first + i * wt.step); `armed` marks
   // stages with copies in flight, `par` their current phase parity
   unsigned armed = 0, par = 0;
   TileBounds tb[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    const int t = gwarp + s * nwarps;
-    if (t < ntiles) {
+    const int t = wt.first + s * wt.step;
+    if (t < wt.end) {
       tb[s] = bounds(t);
       if (!tb[s].longrow()) {
         if (lane == 0) stage_issue<T>(wsm + s * S::kStageBytes, &bars[s], tb[s], rowptr, cols, vals, epi, vec_mask);
@@ -758,7 +768,7 @@ __device__ bool staged_tiles(const int2* __restrict__ tiles, int ntiles, const i
   }
   bool ok = true;
   int i = 0;
-  for (int t = gwarp; t < ntiles; t += nwarps, ++i) {
+  for (int t = wt.first; t < wt.end; t += wt.step, ++i) {
     const int s = i % NS;
     const TileBounds b = tb[s];
     char* st = wsm + s * S::kStageBytes;
@@ -841,8 +851,8 @@ __device__ bool staged_tiles(const int2* __restrict__ tiles, int ntiles, const i
       __syncwarp();
     }
     // re-arm this stage with the warp's tile NS steps ahead
-    const int tn = t + NS * nwarps;
-    if (tn < ntiles) {
+    const int tn = t + NS * wt.step;
+    if (tn < wt.end) {
       tb[s] = bounds(tn);
       if (!tb[s].longrow()) {
         if (lane == 0) stage_issue<T>(st, &bars[s], tb[s], rowptr, cols, vals, epi, vec_mask);
@@ -1564,9 +1574,8 @@ __device__ __forceinline__ void spmv_tiles_batch(const int2* __restrict__ tiles,
                                                  const int* __restrict__ cols, const V* __restrict__ vals,
                                                  Gather& gat, Epi& epi, Acc* __restrict__ sm) {
   const int lane = threadIdx.x & 31;
-  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int t = gwarp; t < ntiles; t += nwarps) {
+  const WarpTiles wt = warp_tiles(ntiles);
+  for (int t = wt.first; t < wt.end; t += wt.step) {
     if (!epi.begin(__ldg(tile_lp + t), t)) continue;
     const int2 ta = __ldg(tiles + t), tb = __ldg(tiles + t + 1);
     const int r0 = ta.x, r1 = tb.x, p0 = ta.y, p1 = tb.y;
@@ -2197,7 +2206,9 @@ int occupancy_grid(int side, int form, int work_tiles) {
     cudaGetLastError();
     per_sm = 1;
   }
-  long long need = (work_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  // a whole wave of resident blocks (every SM the same number, and with warp_tiles
+  // the same share of the tiles), or one block per tile on small problems
+  long long need = work_tiles;
   if (need < 1) need = 1;
   const long long cap = (long long)per_sm * device_sm_count();
   return int(need < cap ? need : cap);
@@ -2259,7 +2270,7 @@ void batch_grids(DevBatch<T>& B) {
     int per_sm = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem) != cudaSuccess || per_sm < 1)
       per_sm = 1;
-    long long need = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    long long need = tiles;  // a whole wave, or one block per tile (as occupancy_grid)
     if (need < 1) need = 1;
     const long long cap = (long long)per_sm * device_sm_count();
     return int(need < cap ? need : cap);
