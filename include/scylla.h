@@ -111,6 +111,8 @@ typedef struct {
                                    warp loading its first tile before the wait on the preceding kernel;
                                    2: wide tiles of up to 128 rows, plain loads; 3: wide tiles staged in
                                    shared memory by bulk copies; 4: 32-row tiles, plain loads (0) */
+  int32_t host_transpose;       /* 1: build the stored transpose A^T on the host threads; 0: on the device,
+                                   a stable radix sort of the nonzeros by column (0) */
 } scylla_params;
 
 typedef struct {
@@ -214,6 +216,11 @@ int scylla_time_kernels(scylla_lp* lp, int32_t attempts, double* ms);
 /* Diagonal scaling A~ = diag(R) A diag(C) found at create: host, R length m_total,
  * C length n_total. */
 int scylla_get_scaling(const scylla_lp* lp, double* R, double* C);
+
+/* The stored transpose of the scaled matrix A~ that the primal step gathers over
+ * (Section 2.1): host arrays colptr (n_total + 1), rows (nnz_total, ascending within
+ * each column) and vals (nnz_total, FP64); any of the three may be null. */
+int scylla_get_transpose(const scylla_lp* lp, int64_t* colptr, int32_t* rows, double* vals);
 
 /* Fix-and-propagate (Section 2.3) on the original MIP, on the host.
  *   xbar: host, length n.  xhat, dom_lo, dom_hi: host outputs, length n.

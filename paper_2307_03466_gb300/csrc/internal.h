@@ -270,7 +270,12 @@ cudaError_t launch_set_xy(const DevLP<T>& d, const double* x, const double* y, c
 template <typename T>
 cudaError_t launch_init_point(const DevLP<T>& d, cudaStream_t st);
 template <typename T>
-int occupancy_grid(int side, int form, int work_tiles);  // side: 0 primal, 1 dual, 2 c1, 3 c2
+int occupancy_grid(int side, int form, int work_tiles);
+// stable device transpose of an m x n CSR matrix (rows ascending within each column);
+// scratch of transpose_scratch_bytes(n, nnz) bytes; colptr has n + 1 entries
+size_t transpose_scratch_bytes(int n, long long nnz);
+cudaError_t transpose_device(int m, int n, long long nnz, const int* rowptr, const int* cols, const double* vals,
+                             int* colptr, int* rows_out, double* vals_out, void* scratch, cudaStream_t st);  // side: 0 primal, 1 dual, 2 c1, 3 c2
 
 int device_sm_count();
 

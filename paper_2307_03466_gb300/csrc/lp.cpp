@@ -80,6 +80,7 @@ extern "C" void scylla_default_params(scylla_params* p) {
   p->device_wait_limit_s = 5.0;
   p->pdl = 1;
   p->prefetch = 0;
+  p->host_transpose = 0;
 }
 
 extern "C" const char* scylla_last_error(void) { return get_error(); }
@@ -210,6 +211,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   if (lp->p.use_graph < 0 || lp->p.use_graph > 3) FAIL(SCYLLA_ERR_INVALID_ARG, "use_graph must be 0..3");
   if (!(lp->p.device_wait_limit_s > 0.0)) FAIL(SCYLLA_ERR_INVALID_ARG, "device_wait_limit_s must be > 0");
   if (lp->p.prefetch < 0 || lp->p.prefetch > 4) FAIL(SCYLLA_ERR_INVALID_ARG, "prefetch must be 0..4");
+  if (lp->p.host_transpose < 0 || lp->p.host_transpose > 1) FAIL(SCYLLA_ERR_INVALID_ARG, "host_transpose must be 0 or 1");
   if (lp->p.precision != SCYLLA_PREC_FP64 && lp->p.precision != SCYLLA_PREC_MIXED)
     FAIL(SCYLLA_ERR_INVALID_ARG, "unknown precision");
   CK(cudaGetDevice(&lp->device));
@@ -299,13 +301,16 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   std::vector<uint8_t> imask(n, 0);
   for (int64_t j = 0; j < n0; ++j) imask[j] = is_int[j];
 
-  // ---- stored transpose (rows ascending within each column)
+  // ---- stored transpose (rows ascending within each column): a stable radix sort
+  // by column on the device after the upload of A, or a counting sort on the host
+  // threads (scylla_params.host_transpose); its tiles are built once the column
+  // pointers are known
+  const bool host_tp = lp->p.host_transpose != 0;
   std::vector<int> tp, tr;
   std::vector<double> tv;
-  transpose_csr(m, n, rp.data(), ci, va, tp, tr, &tv);
-  const std::vector<int2> at = build_tiles(rp), tt = build_tiles(tp);
+  if (host_tp) transpose_csr(m, n, rp.data(), ci, va, tp, tr, &tv);
+  const std::vector<int2> at = build_tiles(rp);
   lp->a_ntiles = int(at.size()) - 1;
-  lp->t_ntiles = int(tt.size()) - 1;
 
   // ---- grid sizes and scratch
   const bool mixed = lp->p.precision == SCYLLA_PREC_MIXED;
@@ -329,26 +334,19 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     else if (pf == 2 || (pf == 0 && !fits)) form = kFormWide;
     else if (pf == 3) form = kFormStaged;
     lp->form_p = lp->form_d = form;
-    if (form == kFormWide || form == kFormStaged) {
-      atw = build_tiles(rp, kWideRows);
-      ttw = build_tiles(tp, kWideRows);
-    }
+    if (form == kFormWide || form == kFormStaged) atw = build_tiles(rp, kWideRows);
   }
   const bool wide_p = lp->form_p == kFormWide || lp->form_p == kFormStaged;
   const bool wide_d = lp->form_d == kFormWide || lp->form_d == kFormStaged;
-  lp->t_ntiles_w = wide_p ? int(ttw.size()) - 1 : lp->t_ntiles;
   lp->a_ntiles_w = wide_d ? int(atw.size()) - 1 : lp->a_ntiles;
-  if (mixed) {
-    lp->grid_p = occupancy_grid<float>(0, lp->form_p, lp->t_ntiles_w);
-    lp->grid_d = occupancy_grid<float>(1, lp->form_d, lp->a_ntiles_w);
-    lp->grid_c1 = occupancy_grid<float>(2, 0, lp->t_ntiles);
-    lp->grid_c2 = occupancy_grid<float>(3, 0, lp->a_ntiles);
-  } else {
-    lp->grid_p = occupancy_grid<double>(0, lp->form_p, lp->t_ntiles_w);
-    lp->grid_d = occupancy_grid<double>(1, lp->form_d, lp->a_ntiles_w);
-    lp->grid_c1 = occupancy_grid<double>(2, 0, lp->t_ntiles);
-    lp->grid_c2 = occupancy_grid<double>(3, 0, lp->a_ntiles);
-  }
+  auto grid_of = [&](int side, int form, int tiles) {
+    return mixed ? occupancy_grid<float>(side, form, tiles) : occupancy_grid<double>(side, form, tiles);
+  };
+  // the block partials are sized for the largest grid (the transpose's tile counts
+  // come later)
+  const int cap_p = grid_of(0, lp->form_p, 1 << 30), cap_c1 = grid_of(2, 0, 1 << 30);
+  lp->grid_d = grid_of(1, lp->form_d, lp->a_ntiles_w);
+  lp->grid_c2 = grid_of(3, 0, lp->a_ntiles);
   // persistent cooperative solve: one grid of co-resident blocks, if it fits
   {
     const int per_sm = mixed ? persistent_blocks_per_sm<float>() : persistent_blocks_per_sm<double>();
@@ -371,8 +369,8 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     lp->a_tiles_w = wide_d ? ar.take<int2>(atw.size()) : lp->a_tiles;
     lp->t_rowptr = ar.take<int>(n + 1);
     lp->t_cols = ar.take<int>(padded(nnz));
-    lp->t_tiles = ar.take<int2>(tt.size());
-    lp->t_tiles_w = wide_p ? ar.take<int2>(ttw.size()) : lp->t_tiles;
+    lp->t_tiles = ar.take<int2>(size_t(n) + 2);  // at most one tile per column, plus the end
+    lp->t_tiles_w = wide_p ? ar.take<int2>(size_t(n) + 2) : lp->t_tiles;
     lp->a_vals64 = ar.take<double>(padded(nnz));
     lp->t_vals64 = ar.take<double>(padded(nnz));
     lp->a_vals32 = mixed ? ar.take<float>(padded(nnz)) : nullptr;
@@ -413,9 +411,9 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     for (int k = 0; k < 2; ++k) lp->ATY[k] = ar.take<char>(vs * n);
     lp->XLR = ar.take<char>(vs * n);
     lp->YLR = ar.take<char>(vs * m);
-    lp->part_p = ar.take<double>(size_t(kNP) * std::max(lp->grid_p, 1));
+    lp->part_p = ar.take<double>(size_t(kNP) * std::max(cap_p, 1));
     lp->part_d = ar.take<double>(size_t(kND) * std::max(lp->grid_d, 1));
-    lp->part_c1 = ar.take<double>(size_t(kNC1) * std::max(lp->grid_c1, 1));
+    lp->part_c1 = ar.take<double>(size_t(kNC1) * std::max(cap_c1, 1));
     lp->part_c2 = ar.take<double>(size_t(kNC2) * std::max(lp->grid_c2, 1));
     lp->red_c1 = ar.take<double>(kNC1);
     lp->red = ar.take<double>(2 * size_t(lp->red_blocks));
@@ -441,13 +439,38 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   CK(cudaMemcpyAsync(lp->a_rowptr, rp.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->a_cols, ci, sizeof(int) * nnz, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->a_tiles, at.data(), sizeof(int2) * at.size(), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->t_rowptr, tp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->t_cols, tr.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->t_tiles, tt.data(), sizeof(int2) * tt.size(), cudaMemcpyHostToDevice, st));
   if (wide_d) CK(cudaMemcpyAsync(lp->a_tiles_w, atw.data(), sizeof(int2) * atw.size(), cudaMemcpyHostToDevice, st));
-  if (wide_p) CK(cudaMemcpyAsync(lp->t_tiles_w, ttw.data(), sizeof(int2) * ttw.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->a_vals64, va, sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->t_vals64, tv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
+  if (host_tp) {
+    CK(cudaMemcpyAsync(lp->t_rowptr, tp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(lp->t_cols, tr.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(lp->t_vals64, tv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
+  } else {
+    void* scratch = nullptr;
+    CK(cudaMalloc(&scratch, transpose_scratch_bytes(int(n), nnz)));
+    cudaError_t te = transpose_device(int(m), int(n), nnz, lp->a_rowptr, lp->a_cols, lp->a_vals64, lp->t_rowptr,
+                                      lp->t_cols, lp->t_vals64, scratch, st);
+    tp.resize(size_t(n) + 1);
+    if (te == cudaSuccess) te = cudaMemcpyAsync(tp.data(), lp->t_rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, st);
+    if (te == cudaSuccess) te = cudaStreamSynchronize(st);
+    cudaFree(scratch);
+    CK(te);
+  }
+  // tiles of the transpose, and the grids that depend on their counts
+  {
+    const std::vector<int2> tt = build_tiles(tp);
+    lp->t_ntiles = int(tt.size()) - 1;
+    CK(cudaMemcpyAsync(lp->t_tiles, tt.data(), sizeof(int2) * tt.size(), cudaMemcpyHostToDevice, st));
+    std::vector<int2> ttw;
+    if (wide_p) {
+      ttw = build_tiles(tp, kWideRows);
+      CK(cudaMemcpyAsync(lp->t_tiles_w, ttw.data(), sizeof(int2) * ttw.size(), cudaMemcpyHostToDevice, st));
+    }
+    lp->t_ntiles_w = wide_p ? int(ttw.size()) - 1 : lp->t_ntiles;
+    lp->grid_p = grid_of(0, lp->form_p, lp->t_ntiles_w);
+    lp->grid_c1 = grid_of(2, 0, lp->t_ntiles);
+    CK(cudaStreamSynchronize(st));  // tt and ttw leave scope
+  }
   CK(cudaMemcpyAsync(lp->c_un, cA.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->l_un, lA.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->u_un, uA.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
@@ -944,6 +967,22 @@ extern "C" int scylla_get_scaling(const scylla_lp* lp, double* R, double* C) {
   if (!lp || !C || (!R && lp->m > 0)) FAIL(SCYLLA_ERR_INVALID_ARG, "null argument");
   if (lp->m > 0) CK(cudaMemcpyAsync(R, lp->R, sizeof(double) * lp->m, cudaMemcpyDeviceToHost, lp->st));
   CK(cudaMemcpyAsync(C, lp->C, sizeof(double) * lp->n, cudaMemcpyDeviceToHost, lp->st));
+  CK(cudaStreamSynchronize(lp->st));
+  return SCYLLA_OK;
+}
+
+extern "C" int scylla_get_transpose(const scylla_lp* lp, int64_t* colptr, int32_t* rows, double* vals) {
+  if (!lp) FAIL(SCYLLA_ERR_INVALID_ARG, "null handle");
+  if (colptr) {
+    std::vector<int> tp(size_t(lp->n) + 1);
+    CK(cudaMemcpyAsync(tp.data(), lp->t_rowptr, sizeof(int) * tp.size(), cudaMemcpyDeviceToHost, lp->st));
+    CK(cudaStreamSynchronize(lp->st));
+    for (size_t j = 0; j < tp.size(); ++j) colptr[j] = tp[j];
+  }
+  if (rows && lp->nnz > 0)
+    CK(cudaMemcpyAsync(rows, lp->t_cols, sizeof(int32_t) * lp->nnz, cudaMemcpyDeviceToHost, lp->st));
+  if (vals && lp->nnz > 0)
+    CK(cudaMemcpyAsync(vals, lp->t_vals64, sizeof(double) * lp->nnz, cudaMemcpyDeviceToHost, lp->st));
   CK(cudaStreamSynchronize(lp->st));
   return SCYLLA_OK;
 }

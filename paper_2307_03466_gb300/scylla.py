@@ -46,7 +46,7 @@ class Params(C.Structure):
                 ("max_rounds", C.c_int64), ("iter_limit", C.c_int64), ("total_iter_cap", C.c_int64),
                 ("run_stall_checks", C.c_int32), ("trace_capacity", C.c_int32), ("seed", C.c_uint64),
                 ("time_limit_s", C.c_double), ("device_wait_limit_s", C.c_double), ("pdl", C.c_int32),
-                ("prefetch", C.c_int32)]
+                ("prefetch", C.c_int32), ("host_transpose", C.c_int32)]
 
 
 class PdhgResult(C.Structure):
@@ -88,6 +88,7 @@ _SIGS = {
     "scylla_get_state": (C.c_int, [_P, _D, _D, _D, _D]),
     "scylla_set_state": (C.c_int, [_P, _D, _D, C.c_double, C.c_double]),
     "scylla_get_scaling": (C.c_int, [_P, _D, _D]),
+    "scylla_get_transpose": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), _D]),
     "scylla_fix_and_propagate": (C.c_int, [_P, _D, _D, _D, _D, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
                                            C.POINTER(C.c_uint8)]),
     "scylla_check_feasible": (C.c_int, [_P, _D, C.POINTER(C.c_int32)]),
@@ -267,6 +268,16 @@ class LP:
         Cc = np.empty(self.n_total)
         _check(lib().scylla_get_scaling(self.h, _dp(R) if self.m_total else None, _dp(Cc)))
         return R, Cc
+
+    def transpose(self):
+        """The stored transpose of the scaled matrix: (colptr, rows, vals)."""
+        colptr = np.empty(self.n_total + 1, dtype=np.int64)
+        _check(lib().scylla_get_transpose(self.h, colptr.ctypes.data_as(C.POINTER(C.c_int64)), None, None))
+        nnz = int(colptr[-1])
+        rows = np.empty(nnz, dtype=np.int32)
+        vals = np.empty(nnz)
+        _check(lib().scylla_get_transpose(self.h, None, rows.ctypes.data_as(C.POINTER(C.c_int32)), _dp(vals)))
+        return colptr, rows, vals
 
     def fix_and_propagate(self, xbar):
         xb = _f64(xbar, self.n)
