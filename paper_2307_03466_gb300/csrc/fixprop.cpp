@@ -220,6 +220,8 @@ bool check_feasible_host(const scylla_lp& lp, const double* x) {
 
 int fix_and_propagate_host(const scylla_lp& lp, const double* xbar, double* xhat, double* dom_lo, double* dom_hi,
                            int32_t* fixed_cols, int64_t* n_fixed, uint8_t* ignored_rows) {
+  const int rc = lp.ensure_host_matrix();
+  if (rc != SCYLLA_OK) return rc;
   lp.ensure_columns();
   Propagator pr(lp);
   for (int32_t i = 0; i < lp.m0; ++i) pr.push(i);
@@ -351,6 +353,8 @@ extern "C" int scylla_check_feasible(const scylla_lp* lp, const double* x, int32
     set_error("null argument");
     return SCYLLA_ERR_INVALID_ARG;
   }
+  const int rc = lp->ensure_host_matrix();
+  if (rc != SCYLLA_OK) return rc;
   *feasible = check_feasible_host(*lp, x) ? 1 : 0;
   return SCYLLA_OK;
 }

@@ -136,8 +136,25 @@ void fill_dev(DevLP<T>& d, scylla_lp* lp);
 
 }  // namespace
 
+int scylla_lp::ensure_host_matrix() const {
+  if (host_matrix_ready) return SCYLLA_OK;
+  std::vector<int> rp(size_t(m0) + 1);
+  cols0.resize(size_t(nnz0));
+  vals0.resize(size_t(nnz0));
+  CK(cudaMemcpyAsync(rp.data(), a_rowptr, sizeof(int) * rp.size(), cudaMemcpyDeviceToHost, st));
+  if (nnz0 > 0) {
+    CK(cudaMemcpyAsync(cols0.data(), a_cols, sizeof(int32_t) * nnz0, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(vals0.data(), a_vals0, sizeof(double) * nnz0, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  rowptr0.assign(rp.begin(), rp.end());
+  host_matrix_ready = true;
+  return SCYLLA_OK;
+}
+
 void scylla_lp::ensure_columns() const {
   if (columns_ready) return;
+  if (ensure_host_matrix() != SCYLLA_OK) return;
   scylla::transpose_csr(m0, n0, rowptr0.data(), cols0.data(), nullptr, colptr0, colrows0, nullptr);
   columns_ready = true;
 }
@@ -226,9 +243,6 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   lp->m0 = m0;
   lp->n0 = n0;
   lp->nnz0 = nnz0;
-  lp->rowptr0.assign(A->rowptr, A->rowptr + m0 + 1);
-  lp->cols0.assign(A->cols, A->cols + nnz0);
-  lp->vals0.assign(A->vals, A->vals + nnz0);
   lp->c0.assign(c, c + n0);
   lp->lo0.assign(lo, lo + m0);
   lp->hi0.assign(hi, hi + m0);
@@ -267,14 +281,14 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   // auxiliary columns), then two rows per auxiliary column
   std::vector<int> rp(m + 1), ci_aux;
   std::vector<double> va_aux;
-  for (int64_t i = 0; i <= m0; ++i) rp[i] = int(lp->rowptr0[i]);
-  const int* ci = lp->cols0.data();
-  const double* va = lp->vals0.data();
+  for (int64_t i = 0; i <= m0; ++i) rp[i] = int(A->rowptr[i]);
+  const int* ci = A->cols;
+  const double* va = A->vals;
   if (na > 0) {
     ci_aux.resize(nnz);
     va_aux.resize(nnz);
-    std::copy(lp->cols0.begin(), lp->cols0.end(), ci_aux.begin());
-    std::copy(lp->vals0.begin(), lp->vals0.end(), va_aux.begin());
+    std::copy(A->cols, A->cols + nnz0, ci_aux.begin());
+    std::copy(A->vals, A->vals + nnz0, va_aux.begin());
     for (int64_t t = 0; t < na; ++t) {
       const int j = lp->gen_int[t];
       const int64_t r0 = m0 + 2 * t, p = nnz0 + 4 * t;
@@ -372,6 +386,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     lp->t_tiles = ar.take<int2>(size_t(n) + 2);  // at most one tile per column, plus the end
     lp->t_tiles_w = wide_p ? ar.take<int2>(size_t(n) + 2) : lp->t_tiles;
     lp->a_vals64 = ar.take<double>(padded(nnz));
+    lp->a_vals0 = ar.take<double>(size_t(nnz));
     lp->t_vals64 = ar.take<double>(padded(nnz));
     lp->a_vals32 = mixed ? ar.take<float>(padded(nnz)) : nullptr;
     lp->t_vals32 = mixed ? ar.take<float>(padded(nnz)) : nullptr;
@@ -441,6 +456,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   CK(cudaMemcpyAsync(lp->a_tiles, at.data(), sizeof(int2) * at.size(), cudaMemcpyHostToDevice, st));
   if (wide_d) CK(cudaMemcpyAsync(lp->a_tiles_w, atw.data(), sizeof(int2) * atw.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->a_vals64, va, sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
+  if (nnz > 0) CK(cudaMemcpyAsync(lp->a_vals0, lp->a_vals64, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, st));
   if (host_tp) {
     CK(cudaMemcpyAsync(lp->t_rowptr, tp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(lp->t_cols, tr.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, st));

@@ -17,9 +17,14 @@ struct scylla_lp {
 
   // original MIP on the host (fix-and-propagate, feasibility test, run loop)
   int64_t m0 = 0, n0 = 0, nnz0 = 0;
-  std::vector<int64_t> rowptr0;
-  std::vector<int32_t> cols0;
-  std::vector<double> vals0;
+  // the original matrix on the host, for the propagation and the feasibility test;
+  // downloaded on first use by ensure_host_matrix() (the device keeps the unscaled
+  // values in a_vals0)
+  mutable std::vector<int64_t> rowptr0;
+  mutable std::vector<int32_t> cols0;
+  mutable std::vector<double> vals0;
+  mutable bool host_matrix_ready = false;
+  int ensure_host_matrix() const;
   std::vector<double> c0, lo0, hi0, l0, u0;
   std::vector<uint8_t> int0;
   // transpose structure of the original rows (rows of each column, ascending), for
@@ -58,6 +63,7 @@ struct scylla_lp {
   double *c64 = nullptr, *l64 = nullptr, *u64 = nullptr, *lo64 = nullptr, *hi64 = nullptr;
   float *c32 = nullptr, *l32 = nullptr, *u32 = nullptr, *lo32 = nullptr, *hi32 = nullptr;
   double *R = nullptr, *C = nullptr, *R2 = nullptr, *C2 = nullptr;
+  double* a_vals0 = nullptr;  // unscaled values of A (the original rows first)
   double *invR = nullptr, *invC = nullptr;
   uint8_t* int_mask = nullptr;
   double *c_orig = nullptr, *l_orig = nullptr, *u_orig = nullptr, *xhat_d = nullptr;

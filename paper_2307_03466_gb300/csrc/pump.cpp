@@ -36,6 +36,10 @@ extern "C" int scylla_run(scylla_lp* lp, double* x_out, scylla_run_result* out) 
   }
   std::memset(out, 0, sizeof(*out));
   out->status = SCYLLA_NOT_FOUND;
+  {
+    const int rc = lp->ensure_host_matrix();  // the propagation and the feasibility test read it
+    if (rc != SCYLLA_OK) return rc;
+  }
   const auto t0 = std::chrono::steady_clock::now();
   auto elapsed = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
   const scylla_params& p = lp->p;
