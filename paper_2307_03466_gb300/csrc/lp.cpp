@@ -302,18 +302,29 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     ci = ci_aux.data();
     va = va_aux.data();
   }
-  std::vector<double> cA(n), loA(m), hiA(m), lA(n), uA(n);
-  for (int64_t j = 0; j < n0; ++j) { cA[j] = c[j]; lA[j] = l[j]; uA[j] = u[j]; }
-  for (int64_t t = 0; t < na; ++t) {
-    const int j = lp->gen_int[t];
-    cA[n0 + t] = 0.0;
-    lA[n0 + t] = 0.0;
-    uA[n0 + t] = u[j] - l[j];
+  // the iterated LP's vectors: the caller's arrays, extended for auxiliary columns
+  std::vector<double> cA, loA, hiA, lA, uA;
+  std::vector<uint8_t> imask;
+  const double *cP = c, *loP = lo, *hiP = hi, *lP = l, *uP = u;
+  const uint8_t* imP = is_int;
+  if (na > 0) {
+    cA.assign(c, c + n0);
+    lA.assign(l, l + n0);
+    uA.assign(u, u + n0);
+    loA.assign(lo, lo + m0);
+    hiA.assign(hi, hi + m0);
+    imask.assign(is_int, is_int + n0);
+    for (int64_t t = 0; t < na; ++t) {
+      const int j = lp->gen_int[t];
+      cA.push_back(0.0);
+      lA.push_back(0.0);
+      uA.push_back(u[j] - l[j]);
+      imask.push_back(0);
+    }
+    loA.resize(size_t(m), -kInf);
+    hiA.resize(size_t(m), kInf);
+    cP = cA.data(); loP = loA.data(); hiP = hiA.data(); lP = lA.data(); uP = uA.data(); imP = imask.data();
   }
-  for (int64_t i = 0; i < m0; ++i) { loA[i] = lo[i]; hiA[i] = hi[i]; }
-  for (int64_t i = m0; i < m; ++i) { loA[i] = -kInf; hiA[i] = kInf; }
-  std::vector<uint8_t> imask(n, 0);
-  for (int64_t j = 0; j < n0; ++j) imask[j] = is_int[j];
 
   // ---- stored transpose (rows ascending within each column): a stable radix sort
   // by column on the device after the upload of A, or a counting sort on the host
@@ -487,12 +498,14 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     lp->grid_c1 = grid_of(2, 0, lp->t_ntiles);
     CK(cudaStreamSynchronize(st));  // tt and ttw leave scope
   }
-  CK(cudaMemcpyAsync(lp->c_un, cA.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->l_un, lA.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->u_un, uA.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->lo_un, loA.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->hi_un, hiA.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->int_mask, imask.data(), n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->c_un, cP, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->l_un, lP, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lp->u_un, uP, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  if (m > 0) {
+    CK(cudaMemcpyAsync(lp->lo_un, loP, sizeof(double) * m, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(lp->hi_un, hiP, sizeof(double) * m, cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaMemcpyAsync(lp->int_mask, imP, n, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->c_orig, c, sizeof(double) * n0, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->l_orig, l, sizeof(double) * n0, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lp->u_orig, u, sizeof(double) * n0, cudaMemcpyHostToDevice, st));
