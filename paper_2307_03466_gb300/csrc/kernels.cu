@@ -48,6 +48,52 @@ __device__ __forceinline__ WarpTiles warp_tiles(int ntiles) {
   return WarpTiles{int(blockIdx.x) + int(threadIdx.x >> 5) * G, ntiles, wpb * G};
 }
 
+// Sum of one long row (p1 - p0 > kTileNnz nonzeros) over a warp: lane l takes the
+// vectors base + (32 i + l) kVec, i = 0, 1, ...  The column indices and values of
+// step i + 1 are loaded before the gathers of step i are issued, so the loads of a
+// row overlap its gathers (a 500-entry row: five dependent latencies, not eight);
+// each lane accumulates its entries in the same order as an unpipelined loop.
+template <int NV, typename Acc, typename V, typename Gather>
+__device__ __forceinline__ void long_row_sum(int p0, int p1, const int* __restrict__ cols,
+                                             const V* __restrict__ vals, Gather& gat, Acc (&s)[NV]) {
+  constexpr int kStep = 32 * kVec;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) s[k] = Acc(0);
+  int p = (p0 & ~(kVec - 1)) + lane * kVec;
+  int cc[4] = {0, 0, 0, 0};
+  V vv[4] = {V(0), V(0), V(0), V(0)};
+  if (p < p1) {
+    ld4(cols + p, cc);
+    ld4(vals + p, vv);
+  }
+  for (; p < p1; p += kStep) {
+    int cn[4] = {0, 0, 0, 0};
+    V vn[4] = {V(0), V(0), V(0), V(0)};
+    if (p + kStep < p1) {
+      ld4(cols + p + kStep, cn);
+      ld4(vals + p + kStep, vn);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int q = p + e;
+      if (q >= p0 && q < p1) {
+        Acc g[NV];
+        gat(cc[e], g);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[k] = fma_t<Acc>(Acc(vv[e]), g[k], s[k]);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      cc[e] = cn[e];
+      vv[e] = vn[e];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) s[k] = warp_sum(s[k]);
+}
+
 // --------------------------------------------------------------- the SpMV core ---
 // Warp-tile CSR gather.  Each warp takes tiles round-robin.  A multi-row tile (at
 // most kTileNnz nonzeros and 32 rows) is read with 16-byte vector loads of column
@@ -116,26 +162,7 @@ __device__ __forceinline__ bool spmv_tiles(const int2* __restrict__ tiles, int n
     if (longrow) {
       const typename Epi::Pre pre = epi.load(r0);
       Acc s[NV];
-#pragma unroll
-      for (int k = 0; k < NV; ++k) s[k] = Acc(0);
-      for (int p = base + lane * kVec; p < p1; p += 32 * kVec) {
-        int cc[4];
-        V vv[4];
-        ld4(cols + p, cc);
-        ld4(vals + p, vv);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int q = p + e;
-          if (q >= p0 && q < p1) {
-            Acc g[NV];
-            gat(cc[e], g);
-#pragma unroll
-            for (int k = 0; k < NV; ++k) s[k] = fma_t<Acc>(Acc(vv[e]), g[k], s[k]);
-          }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < NV; ++k) s[k] = warp_sum(s[k]);
+      long_row_sum<NV>(p0, p1, cols, vals, gat, s);
       if (lane == 0) epi.finish(r0, s, pre);
     } else {
       const int nr = r1 - r0, L = row_lanes(nr), sub = L > 1 ? lane % L : 0;
@@ -1583,26 +1610,7 @@ __device__ __forceinline__ void spmv_tiles_batch(const int2* __restrict__ tiles,
     if (r1 - r0 == 1 && p1 - p0 > kTileNnz) {
       const typename Epi::Pre pre = epi.load(r0);
       Acc s[NV];
-#pragma unroll
-      for (int k = 0; k < NV; ++k) s[k] = Acc(0);
-      for (int p = base + lane * kVec; p < p1; p += 32 * kVec) {
-        int c[4];
-        V v[4];
-        ld4(cols + p, c);
-        ld4(vals + p, v);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int q = p + e;
-          if (q >= p0 && q < p1) {
-            Acc g[NV];
-            gat(c[e], g);
-#pragma unroll
-            for (int k = 0; k < NV; ++k) s[k] = fma_t<Acc>(Acc(v[e]), g[k], s[k]);
-          }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < NV; ++k) s[k] = warp_sum(s[k]);
+      long_row_sum<NV>(p0, p1, cols, vals, gat, s);
       if (lane == 0) epi.finish(r0, s, pre);
     } else {
       const bool mine = lane < r1 - r0;
