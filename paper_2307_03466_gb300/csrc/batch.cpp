@@ -327,13 +327,11 @@ int create_batch(int32_t count, const scylla_csr* A, const double* const* c, con
   CKB(cudaMemcpyAsync(u_un, uA.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
   CKB(cudaMemcpyAsync(lo_un, loA.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
   CKB(cudaMemcpyAsync(hi_un, hiA.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
-  const std::vector<double> ones(std::max(m, n), 1.0);
-  CKB(cudaMemcpyAsync(R, ones.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
-  CKB(cudaMemcpyAsync(C, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
   // preconditioning of the block-diagonal LP is preconditioning of every LP
   DevSetup s{};
   s.m = m; s.n = n; s.n_orig = n; s.m_orig = m; s.nnz = int(nnz);
   s.a_rowptr = a_rowptr; s.a_cols = a_cols; s.t_rowptr = t_rowptr; s.t_cols = t_cols;
+  s.a_tiles = a_tiles; s.a_ntiles = a_nt; s.t_tiles = t_tiles; s.t_ntiles = t_nt;
   s.a_vals64 = a_vals64; s.t_vals64 = t_vals64; s.a_vals32 = a_vals32; s.t_vals32 = t_vals32;
   s.R = R; s.C = C; s.R2 = R2; s.C2 = C2; s.red = red; s.red_blocks = red_blocks;
   CKB(launch_precondition(s, h->p.ruiz_iters, h->p.pock_chambolle != 0, st));

@@ -284,6 +284,8 @@ extern "C" int scylla_fanout_create(scylla_lp* lp, int32_t K, const double* targ
     set_error("the fan-out needs an LP without auxiliary distance columns (create it with aux_general_integers = 0)");
     return SCYLLA_ERR_UNSUPPORTED;
   }
+  const int rv = lp->ensure_host_vectors();
+  if (rv != SCYLLA_OK) return rv;
   for (int k = 0; k < K; ++k)
     for (int64_t j = 0; j < lp->n0; ++j) {
       const double v = targets[size_t(k) * lp->n0 + j];

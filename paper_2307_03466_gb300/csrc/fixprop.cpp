@@ -365,6 +365,8 @@ extern "C" int scylla_perturb(const scylla_lp* lp, double* xhat, const double* x
     set_error("invalid argument");
     return SCYLLA_ERR_INVALID_ARG;
   }
+  const int rv = lp->ensure_host_vectors();
+  if (rv != SCYLLA_OK) return rv;
   const int64_t f = perturb_host(*lp, xhat, xbar, kind, K, seed);
   if (flipped) *flipped = f;
   return SCYLLA_OK;

@@ -180,6 +180,9 @@ struct DevSetup {
   const int* a_cols;
   const int* t_rowptr;
   const int* t_cols;
+  const int2* a_tiles;  // warp tiles of A and of A^T (as in DevLP)
+  const int2* t_tiles;
+  int a_ntiles, t_ntiles;
   double* a_vals64;  // in: original values; out: scaled values
   double* t_vals64;
   float* a_vals32;   // may be null
@@ -192,11 +195,23 @@ struct DevSetup {
   int red_blocks;
 };
 
-// ---- kernel launchers (kernels.cu) -------------------------------------------
+// ---- set-up launchers (setup.cu) ---------------------------------------------
+// R = C = 1, ruiz_iters Ruiz iterations and the Pock-Chambolle step (R2, C2 scratch)
 cudaError_t launch_precondition(const DevSetup& s, int ruiz_iters, bool pock_chambolle, cudaStream_t st);
+// a~ = diag(R) A diag(C) in both CSR copies (and their FP32 shadows)
 cudaError_t launch_scale_values(const DevSetup& s, cudaStream_t st);
-// max |a~|, sum a~^2 over the scaled A values -> host
-cudaError_t matrix_norms(const DevSetup& s, cudaStream_t st, double* amax, double* fro2);
+cudaError_t fill_f64(double* p, long long count, double v, cudaStream_t st);
+// kind = is_int (0/1) and aux_of = -1 over n columns
+cudaError_t column_kinds(long long n, const uint8_t* is_int, int* kind, int* aux_of, cudaStream_t st);
+struct SetupNorms {
+  double amax, fro2;  // max |a~|, sum a~^2
+  double c2, q2;      // sum c~^2, sum over rows of max(|lo~|, |hi~|)^2 (finite bounds)
+};
+// one launch over the scaled values and vectors, 4 * red_blocks partials in s.red -> host
+cudaError_t setup_norms(const DevSetup& s, const double* c64, const double* lo64, const double* hi64, cudaStream_t st,
+                        SetupNorms* out);
+
+// ---- kernel launchers (kernels.cu) -------------------------------------------
 
 struct DevVecs {
   // unscaled originals (FP64), augmented sizes

@@ -1358,94 +1358,8 @@ __global__ void k_init_point(DevLP<T> d) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) yc[i] = T(0);
 }
 
-// ----------------------------------------------------------- preconditioning ---
-// Ruiz pass: R'_i = R_i / sqrt(max_j (R_i |a_ij|) C_j), C'_j likewise, both from the
-// same (R, C); a zero maximum leaves the multiplier unchanged.
-__global__ void k_ruiz_rows(int m, const int* rowptr, const int* cols, const double* vals, const double* R,
-                            const double* C, double* Rout) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-    double mx = 0.0;
-    const double ri = R[i];
-    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) mx = fmax(mx, (ri * fabs(vals[p])) * C[cols[p]]);
-    Rout[i] = mx > 0.0 ? ri / sqrt(mx) : ri;
-  }
-}
-__global__ void k_ruiz_cols(int n, const int* colptr, const int* rows, const double* vals, const double* R,
-                            const double* C, double* Cout) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    double mx = 0.0;
-    const double cj = C[j];
-    for (int p = colptr[j]; p < colptr[j + 1]; ++p) mx = fmax(mx, (R[rows[p]] * fabs(vals[p])) * cj);
-    Cout[j] = mx > 0.0 ? cj / sqrt(mx) : cj;
-  }
-}
-// Pock-Chambolle (alpha = 1): R'_i = R_i / sqrt(sum_j (R_i |a_ij|) C_j), C'_j likewise.
-__global__ void k_pc_rows(int m, const int* rowptr, const int* cols, const double* vals, const double* R,
-                          const double* C, double* Rout) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    const double ri = R[i];
-    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) s += (ri * fabs(vals[p])) * C[cols[p]];
-    Rout[i] = s > 0.0 ? ri / sqrt(s) : ri;
-  }
-}
-__global__ void k_pc_cols(int n, const int* colptr, const int* rows, const double* vals, const double* R,
-                          const double* C, double* Cout) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    const double cj = C[j];
-    for (int p = colptr[j]; p < colptr[j + 1]; ++p) s += (R[rows[p]] * fabs(vals[p])) * cj;
-    Cout[j] = s > 0.0 ? cj / sqrt(s) : cj;
-  }
-}
-// a~_ij = (a_ij R_i) C_j in both CSR copies, plus FP32 shadows
-__global__ void k_scale_rows(int m, const int* rowptr, const int* cols, double* vals, float* vals32,
-                             const double* R, const double* C) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-    const double ri = R[i];
-    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-      const double v = (vals[p] * ri) * C[cols[p]];
-      vals[p] = v;
-      if (vals32) vals32[p] = float(v);
-    }
-  }
-}
-__global__ void k_scale_cols(int n, const int* colptr, const int* rows, double* vals, float* vals32,
-                             const double* R, const double* C) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    const double cj = C[j];
-    for (int p = colptr[j]; p < colptr[j + 1]; ++p) {
-      const double v = (vals[p] * R[rows[p]]) * cj;
-      vals[p] = v;
-      if (vals32) vals32[p] = float(v);
-    }
-  }
-}
-
-// two-pass reductions for setup: part[b] = (max |v|, sum v^2) over a grid-stride slice
-__global__ void k_norms_partial(const double* v, long long count, double* part) {
-  double mx = 0.0, s = 0.0;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < count;
-       p += (long long)gridDim.x * blockDim.x) {
-    const double a = v[p];
-    mx = fmax(mx, fabs(a));
-    s += a * a;
-  }
-  __shared__ double smx[kThreads], ss[kThreads];
-  smx[threadIdx.x] = mx;
-  ss[threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int t = 0; t < blockDim.x; ++t) {
-      a = fmax(a, smx[t]);
-      b += ss[t];
-    }
-    part[2 * blockIdx.x] = a;
-    part[2 * blockIdx.x + 1] = b;
-  }
-}
-
+// ------------------------------------------------------------ scaled vectors ---
+// c~ = C c, [l~, u~] = [l, u] / C, [lo~, hi~] = R [lo, hi], and 1/R, 1/C when asked.
 __global__ void k_scale_vectors(DevVecs v) {
   const int stride = gridDim.x * blockDim.x;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.n; j += stride) {
@@ -2006,51 +1920,6 @@ static int ew_grid(long long count) {
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return int(g);
-}
-
-cudaError_t launch_precondition(const DevSetup& s, int ruiz_iters, bool pock_chambolle, cudaStream_t st) {
-  double* R = s.R;
-  double* C = s.C;
-  double* R2 = s.R2;
-  double* C2 = s.C2;
-  const int gr = ew_grid(s.m), gc = ew_grid(s.n);
-  for (int it = 0; it < ruiz_iters; ++it) {
-    k_ruiz_rows<<<gr, kThreads, 0, st>>>(s.m, s.a_rowptr, s.a_cols, s.a_vals64, R, C, R2);
-    k_ruiz_cols<<<gc, kThreads, 0, st>>>(s.n, s.t_rowptr, s.t_cols, s.t_vals64, R, C, C2);
-    cudaMemcpyAsync(R, R2, sizeof(double) * s.m, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(C, C2, sizeof(double) * s.n, cudaMemcpyDeviceToDevice, st);
-  }
-  if (pock_chambolle) {
-    k_pc_rows<<<gr, kThreads, 0, st>>>(s.m, s.a_rowptr, s.a_cols, s.a_vals64, R, C, R2);
-    k_pc_cols<<<gc, kThreads, 0, st>>>(s.n, s.t_rowptr, s.t_cols, s.t_vals64, R, C, C2);
-    cudaMemcpyAsync(R, R2, sizeof(double) * s.m, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(C, C2, sizeof(double) * s.n, cudaMemcpyDeviceToDevice, st);
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_scale_values(const DevSetup& s, cudaStream_t st) {
-  k_scale_rows<<<ew_grid(s.m), kThreads, 0, st>>>(s.m, s.a_rowptr, s.a_cols, s.a_vals64, s.a_vals32, s.R, s.C);
-  k_scale_cols<<<ew_grid(s.n), kThreads, 0, st>>>(s.n, s.t_rowptr, s.t_cols, s.t_vals64, s.t_vals32, s.R, s.C);
-  return cudaGetLastError();
-}
-
-cudaError_t matrix_norms(const DevSetup& s, cudaStream_t st, double* amax, double* fro2) {
-  const int g = s.red_blocks;
-  k_norms_partial<<<g, kThreads, 0, st>>>(s.a_vals64, s.nnz, s.red);
-  std::vector<double> h(2 * g);
-  cudaError_t e = cudaMemcpyAsync(h.data(), s.red, sizeof(double) * 2 * g, cudaMemcpyDeviceToHost, st);
-  if (e != cudaSuccess) return e;
-  e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return e;
-  double a = 0.0, b = 0.0;
-  for (int q = 0; q < g; ++q) {
-    a = fmax(a, h[2 * q]);
-    b += h[2 * q + 1];
-  }
-  *amax = a;
-  *fro2 = b;
-  return cudaGetLastError();
 }
 
 cudaError_t launch_scale_vectors(const DevVecs& v, cudaStream_t st) {

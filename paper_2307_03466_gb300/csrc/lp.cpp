@@ -89,8 +89,26 @@ namespace {
 
 size_t padded(size_t nnz) { return scylla::padded_len(nnz); }
 
+// Warp tiles of a CSR structure.  Above kTileSpan rows the rows are cut into spans
+// of kTileSpan rows, tiled independently on the host threads and concatenated: a
+// tile never crosses a span boundary, so the tiles depend on the structure alone.
+constexpr int kTileSpan = 1 << 17;
 std::vector<int2> build_tiles(const std::vector<int>& rowptr, int max_rows = scylla::kTileRows) {
-  return scylla::build_tiles_range(rowptr, 0, int(rowptr.size()) - 1, max_rows);
+  const int m = int(rowptr.size()) - 1;
+  if (m <= kTileSpan) return scylla::build_tiles_range(rowptr, 0, m, max_rows);
+  const int spans = (m + kTileSpan - 1) / kTileSpan;
+  std::vector<std::vector<int2>> part(static_cast<size_t>(spans));
+  scylla::fork_join(spans, [&](int k) {
+    const int b = k * kTileSpan, e = std::min(m, b + kTileSpan);
+    part[size_t(k)] = scylla::build_tiles_range(rowptr, b, e, max_rows);
+  });
+  size_t total = 1;
+  for (const auto& v : part) total += v.size() - 1;
+  std::vector<int2> t;
+  t.reserve(total);
+  for (int k = 0; k < spans; ++k) t.insert(t.end(), part[size_t(k)].begin(), part[size_t(k)].end() - 1);
+  t.push_back(part.back().back());
+  return t;
 }
 
 }  // namespace
@@ -136,8 +154,32 @@ void fill_dev(DevLP<T>& d, scylla_lp* lp);
 
 }  // namespace
 
+int scylla_lp::ensure_host_vectors() const {
+  if (host_vectors_ready) return SCYLLA_OK;
+  c0.resize(size_t(n0));
+  l0.resize(size_t(n0));
+  u0.resize(size_t(n0));
+  int0.resize(size_t(n0));
+  lo0.resize(size_t(m0));
+  hi0.resize(size_t(m0));
+  CK(cudaMemcpyAsync(c0.data(), c_orig, sizeof(double) * n0, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(l0.data(), l_orig, sizeof(double) * n0, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(u0.data(), u_orig, sizeof(double) * n0, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(int0.data(), int_mask, n0, cudaMemcpyDeviceToHost, st));
+  if (m0 > 0) {
+    // the original rows come first; only the auxiliary rows' bounds change later
+    CK(cudaMemcpyAsync(lo0.data(), lo_un, sizeof(double) * m0, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hi0.data(), hi_un, sizeof(double) * m0, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  host_vectors_ready = true;
+  return SCYLLA_OK;
+}
+
 int scylla_lp::ensure_host_matrix() const {
   if (host_matrix_ready) return SCYLLA_OK;
+  const int rv = ensure_host_vectors();
+  if (rv != SCYLLA_OK) return rv;
   std::vector<int> rp(size_t(m0) + 1);
   cols0.resize(size_t(nnz0));
   vals0.resize(size_t(nnz0));
@@ -202,18 +244,46 @@ int scylla::validate_lp(const scylla_csr* A, const double* c, const double* lo, 
       FAIL(SCYLLA_ERR_INVALID_ARG, "non-finite matrix value in row " + row);
     }
   }
-  for (int64_t i = 0; i < A->m; ++i) {
-    if (std::isnan(lo[i]) || std::isnan(hi[i]) || lo[i] > hi[i] || lo[i] == kInf || hi[i] == -kInf)
-      FAIL(SCYLLA_ERR_INVALID_ARG, "invalid row bounds at row " + std::to_string(i));
-  }
-  for (int64_t j = 0; j < A->n; ++j) {
-    if (!std::isfinite(c[j])) FAIL(SCYLLA_ERR_INVALID_ARG, "non-finite objective at column " + std::to_string(j));
-    if (std::isnan(l[j]) || std::isnan(u[j]) || l[j] > u[j] || l[j] == kInf || u[j] == -kInf)
-      FAIL(SCYLLA_ERR_INVALID_ARG, "invalid column bounds at column " + std::to_string(j));
-    if (is_int[j] > 1) FAIL(SCYLLA_ERR_INVALID_ARG, "is_integer must be 0 or 1");
-    if (is_int[j] && ((std::isfinite(l[j]) && l[j] != std::floor(l[j])) ||
-                      (std::isfinite(u[j]) && u[j] != std::floor(u[j]))))
-      FAIL(SCYLLA_ERR_INVALID_ARG, "integer column with a fractional bound: " + std::to_string(j));
+  // row bounds and columns in parallel slices; the first failing index is reported
+  {
+    const int64_t mm = A->m, nn = A->n;
+    const int T = threads_for(2 * (mm + nn));
+    std::vector<int64_t> bad_row(size_t(T), mm), bad_col(size_t(T), nn);
+    std::vector<int> why(size_t(T), 0);
+    fork_join(T, [&](int t) {
+      for (int64_t i = mm * t / T; i < mm * (t + 1) / T; ++i)
+        if (std::isnan(lo[i]) || std::isnan(hi[i]) || lo[i] > hi[i] || lo[i] == kInf || hi[i] == -kInf) {
+          bad_row[size_t(t)] = i;
+          break;
+        }
+      for (int64_t j = nn * t / T; j < nn * (t + 1) / T; ++j) {
+        int w = 0;
+        if (!std::isfinite(c[j])) w = 1;
+        else if (std::isnan(l[j]) || std::isnan(u[j]) || l[j] > u[j] || l[j] == kInf || u[j] == -kInf) w = 2;
+        else if (is_int[j] > 1) w = 3;
+        else if (is_int[j] && ((std::isfinite(l[j]) && l[j] != std::floor(l[j])) ||
+                               (std::isfinite(u[j]) && u[j] != std::floor(u[j]))))
+          w = 4;
+        if (w) {
+          bad_col[size_t(t)] = j;
+          why[size_t(t)] = w;
+          break;
+        }
+      }
+    });
+    for (int t = 0; t < T; ++t)
+      if (bad_row[size_t(t)] < mm)
+        FAIL(SCYLLA_ERR_INVALID_ARG, "invalid row bounds at row " + std::to_string(bad_row[size_t(t)]));
+    for (int t = 0; t < T; ++t) {
+      const std::string j = std::to_string(bad_col[size_t(t)]);
+      switch (why[size_t(t)]) {
+        case 1: FAIL(SCYLLA_ERR_INVALID_ARG, "non-finite objective at column " + j);
+        case 2: FAIL(SCYLLA_ERR_INVALID_ARG, "invalid column bounds at column " + j);
+        case 3: FAIL(SCYLLA_ERR_INVALID_ARG, "is_integer must be 0 or 1");
+        case 4: FAIL(SCYLLA_ERR_INVALID_ARG, "integer column with a fractional bound: " + j);
+        default: break;
+      }
+    }
   }
   return SCYLLA_OK;
 }
@@ -238,37 +308,41 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   CK(cudaEventCreate(&lp->ev0));
   CK(cudaEventCreate(&lp->ev1));
 
-  // ---- host copies of the original MIP
+  // ---- the original MIP: ||c||, the integer count and the general integers that
+  // get auxiliary columns, in one pass over the caller's arrays in a number of
+  // chunks fixed by n (so ||c|| does not depend on the host's thread count).  The
+  // host copies of the vectors are fetched from the device on first use.
   const int64_t m0 = A->m, n0 = A->n, nnz0 = A->nnz;
   lp->m0 = m0;
   lp->n0 = n0;
   lp->nnz0 = nnz0;
-  lp->c0.assign(c, c + n0);
-  lp->lo0.assign(lo, lo + m0);
-  lp->hi0.assign(hi, hi + m0);
-  lp->l0.assign(l, l + n0);
-  lp->u0.assign(u, u + n0);
-  lp->int0.assign(is_int, is_int + n0);
-  lp->c0norm = 0.0;
-  for (int64_t j = 0; j < n0; ++j) lp->c0norm += c[j] * c[j];
-  lp->c0norm = std::sqrt(lp->c0norm);
-  lp->n_int = 0;
-  for (int64_t j = 0; j < n0; ++j) lp->n_int += is_int[j] ? 1 : 0;
-
-  // ---- auxiliary distance columns for general integers
-  lp->kind.assign(n0, 0);
-  lp->aux_of.assign(n0, -1);
-  lp->gen_int.clear();
-  for (int64_t j = 0; j < n0; ++j) {
-    if (!is_int[j]) continue;
-    const bool unit = (u[j] - l[j] == 1.0);
-    if (unit || !lp->p.aux_general_integers) {
-      lp->kind[j] = 1;
-    } else {
-      lp->kind[j] = 2;
-      lp->aux_of[j] = int32_t(lp->gen_int.size());
-      lp->gen_int.push_back(int32_t(j));
+  const bool aux_on = lp->p.aux_general_integers != 0;
+  {
+    const int chunks = int(std::max<int64_t>(1, std::min<int64_t>(64, n0 / 65536)));
+    std::vector<double> c2(size_t(chunks), 0.0);
+    std::vector<int64_t> nint(size_t(chunks), 0);
+    std::vector<std::vector<int32_t>> gen(static_cast<size_t>(chunks));
+    fork_join(chunks, [&](int t) {
+      double s2 = 0.0;
+      int64_t k = 0;
+      for (int64_t j = n0 * t / chunks; j < n0 * (t + 1) / chunks; ++j) {
+        s2 += c[j] * c[j];
+        if (!is_int[j]) continue;
+        ++k;
+        if (aux_on && u[j] - l[j] != 1.0) gen[size_t(t)].push_back(int32_t(j));
+      }
+      c2[size_t(t)] = s2;
+      nint[size_t(t)] = k;
+    });
+    double s2 = 0.0;
+    lp->n_int = 0;
+    lp->gen_int.clear();
+    for (int t = 0; t < chunks; ++t) {
+      s2 += c2[size_t(t)];
+      lp->n_int += nint[size_t(t)];
+      lp->gen_int.insert(lp->gen_int.end(), gen[size_t(t)].begin(), gen[size_t(t)].end());
     }
+    lp->c0norm = std::sqrt(s2);
   }
   const int64_t na = int64_t(lp->gen_int.size());
   lp->n_aux = na;
@@ -442,7 +516,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     lp->part_c1 = ar.take<double>(size_t(kNC1) * std::max(cap_c1, 1));
     lp->part_c2 = ar.take<double>(size_t(kNC2) * std::max(lp->grid_c2, 1));
     lp->red_c1 = ar.take<double>(kNC1);
-    lp->red = ar.take<double>(2 * size_t(lp->red_blocks));
+    lp->red = ar.take<double>(4 * size_t(lp->red_blocks));
     lp->io_x = ar.take<double>(n);
     lp->io_y = ar.take<double>(m);
     lp->ctl = ar.take<Control>(1);
@@ -457,8 +531,13 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   }
   cudaStream_t st = lp->st;
   CK(cudaMemsetAsync(lp->arena, 0, lp->arena_bytes, st));
-  CK(cudaMallocHost(&lp->h_ctl, sizeof(Control)));
-  CK(cudaMallocHost(&lp->h_done, 2 * sizeof(int)));
+  {
+    // one pinned block: the control block's host copy, then the two done flags
+    void* pin = nullptr;
+    CK(cudaMallocHost(&pin, sizeof(Control) + 64));
+    lp->h_ctl = static_cast<Control*>(pin);
+    lp->h_done = reinterpret_cast<int*>(static_cast<char*>(pin) + sizeof(Control));
+  }
   CK(cudaEventCreateWithFlags(&lp->ev_chunk[0], cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&lp->ev_chunk[1], cudaEventDisableTiming));
 
@@ -506,19 +585,33 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     CK(cudaMemcpyAsync(lp->hi_un, hiP, sizeof(double) * m, cudaMemcpyHostToDevice, st));
   }
   CK(cudaMemcpyAsync(lp->int_mask, imP, n, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->c_orig, c, sizeof(double) * n0, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->l_orig, l, sizeof(double) * n0, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->u_orig, u, sizeof(double) * n0, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->kind_d, lp->kind.data(), sizeof(int) * n0, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lp->aux_of_d, lp->aux_of.data(), sizeof(int) * n0, cudaMemcpyHostToDevice, st));
+  // the original columns are the first n0 of the iterated LP's
+  CK(cudaMemcpyAsync(lp->c_orig, lp->c_un, sizeof(double) * n0, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(lp->l_orig, lp->l_un, sizeof(double) * n0, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(lp->u_orig, lp->u_un, sizeof(double) * n0, cudaMemcpyDeviceToDevice, st));
+  // column kinds (0 continuous, 1 integer, 2 general integer with an auxiliary
+  // column) and auxiliary indices: from the integrality mask when there are no
+  // auxiliary columns
+  std::vector<int> kind, aux_of;
+  if (na == 0) {
+    CK(column_kinds(n0, lp->int_mask, lp->kind_d, lp->aux_of_d, st));
+  } else {
+    kind.assign(size_t(n0), 0);
+    aux_of.assign(size_t(n0), -1);
+    for (int64_t j = 0; j < n0; ++j) kind[size_t(j)] = is_int[j] ? 1 : 0;
+    for (int64_t t = 0; t < na; ++t) {
+      kind[size_t(lp->gen_int[size_t(t)])] = 2;
+      aux_of[size_t(lp->gen_int[size_t(t)])] = int(t);
+    }
+    CK(cudaMemcpyAsync(lp->kind_d, kind.data(), sizeof(int) * n0, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(lp->aux_of_d, aux_of.data(), sizeof(int) * n0, cudaMemcpyHostToDevice, st));
+  }
   {
-    const std::vector<double> ones(std::max(m, n), 1.0);
-    CK(cudaMemcpyAsync(lp->R, ones.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(lp->C, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
     // preconditioning (Section 2.1, PDLP's diagonal scaling) and scaled copies
     DevSetup s{};
     s.m = int(m); s.n = int(n); s.n_orig = int(n0); s.m_orig = int(m0); s.nnz = int(nnz);
     s.a_rowptr = lp->a_rowptr; s.a_cols = lp->a_cols; s.t_rowptr = lp->t_rowptr; s.t_cols = lp->t_cols;
+    s.a_tiles = lp->a_tiles; s.a_ntiles = lp->a_ntiles; s.t_tiles = lp->t_tiles; s.t_ntiles = lp->t_ntiles;
     s.a_vals64 = lp->a_vals64; s.t_vals64 = lp->t_vals64; s.a_vals32 = lp->a_vals32; s.t_vals32 = lp->t_vals32;
     s.R = lp->R; s.C = lp->C; s.R2 = lp->R2; s.C2 = lp->C2; s.red = lp->red; s.red_blocks = lp->red_blocks;
     CK(launch_precondition(s, lp->p.ruiz_iters, lp->p.pock_chambolle != 0, st));
@@ -529,28 +622,15 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     v.c32 = lp->c32; v.lo32 = lp->lo32; v.hi32 = lp->hi32; v.l32 = lp->l32; v.u32 = lp->u32;
     v.R = lp->R; v.C = lp->C; v.invR = lp->invR; v.invC = lp->invC; v.m = int(m); v.n = int(n);
     CK(launch_scale_vectors(v, st));
-    double amax = 0.0, fro2 = 0.0;
-    CK(matrix_norms(s, st, &amax, &fro2));
+    SetupNorms nm{};
+    CK(setup_norms(s, lp->c64, lp->lo64, lp->hi64, st, &nm));
     // initial step size: 1/max|a~| (adaptive) or f/||A~||_F (fixed); primal weight
-    // ||c~|| / ||b~|| on the scaled LP (1 when either is zero)
+    // ||c~|| / ||q~|| on the scaled LP, q~_i the largest finite row bound magnitude
+    // (1 when either norm is zero)
     double eta = 1.0;
-    if (lp->p.adaptive_step) eta = amax > 0.0 ? 1.0 / amax : 1.0;
-    else eta = fro2 > 0.0 ? lp->p.fixed_step_factor / std::sqrt(fro2) : 1.0;
-    std::vector<double> hc(n), hlo(m), hhi(m);
-    CK(cudaMemcpyAsync(hc.data(), lp->c64, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(hlo.data(), lp->lo64, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(hhi.data(), lp->hi64, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    double cn = 0.0, qn = 0.0;
-    for (int64_t j = 0; j < n; ++j) cn += hc[j] * hc[j];
-    for (int64_t i = 0; i < m; ++i) {
-      const double a = std::isfinite(hlo[i]) ? std::fabs(hlo[i]) : 0.0;
-      const double b = std::isfinite(hhi[i]) ? std::fabs(hhi[i]) : 0.0;
-      const double q = std::max(a, b);
-      qn += q * q;
-    }
-    cn = std::sqrt(cn);
-    qn = std::sqrt(qn);
+    if (lp->p.adaptive_step) eta = nm.amax > 0.0 ? 1.0 / nm.amax : 1.0;
+    else eta = nm.fro2 > 0.0 ? lp->p.fixed_step_factor / std::sqrt(nm.fro2) : 1.0;
+    const double cn = std::sqrt(nm.c2), qn = std::sqrt(nm.q2);
     Control h{};
     h.eta = eta;
     h.omega = (cn > 0.0 && qn > 0.0) ? cn / qn : 1.0;
@@ -661,8 +741,7 @@ void scylla_lp::release() {
     if (e) cudaEventDestroy(e);
     e = nullptr;
   }
-  if (h_done) cudaFreeHost(h_done);
-  h_done = nullptr;
+  h_done = nullptr;  // inside the h_ctl block
   if (arena) cudaFree(arena);
   arena = nullptr;
   if (h_ctl) cudaFreeHost(h_ctl);
@@ -885,6 +964,8 @@ extern "C" int scylla_pdhg_solve(scylla_lp* lp, double tol, int64_t iter_limit, 
 int scylla_lp::set_objective(const double* xhat, int32_t K) {
   if (!xhat) FAIL(SCYLLA_ERR_INVALID_ARG, "xhat is null");
   if (K < 1) FAIL(SCYLLA_ERR_INVALID_ARG, "round K must be >= 1");
+  const int rv = ensure_host_vectors();
+  if (rv != SCYLLA_OK) return rv;
   for (int64_t j = 0; j < n0; ++j) {
     if (!std::isfinite(xhat[j])) FAIL(SCYLLA_ERR_INVALID_ARG, "xhat not finite at " + std::to_string(j));
     if (int0[j] && (xhat[j] != std::floor(xhat[j]) || xhat[j] < l0[j] || xhat[j] > u0[j]))

@@ -24,9 +24,13 @@ struct scylla_lp {
   mutable std::vector<int32_t> cols0;
   mutable std::vector<double> vals0;
   mutable bool host_matrix_ready = false;
-  int ensure_host_matrix() const;
-  std::vector<double> c0, lo0, hi0, l0, u0;
-  std::vector<uint8_t> int0;
+  int ensure_host_matrix() const;  // also fetches the vectors
+  // the original vectors on the host (objective, bounds, integrality), downloaded on
+  // first use by ensure_host_vectors() from the device's unscaled copies
+  mutable std::vector<double> c0, lo0, hi0, l0, u0;
+  mutable std::vector<uint8_t> int0;
+  mutable bool host_vectors_ready = false;
+  int ensure_host_vectors() const;
   // transpose structure of the original rows (rows of each column, ascending), for
   // the host propagation; built on first use by ensure_columns()
   mutable std::vector<int64_t> colptr0;
@@ -35,9 +39,7 @@ struct scylla_lp {
   void ensure_columns() const;
   double c0norm = 0.0;
   int64_t n_int = 0;
-  std::vector<int> kind;     // 0 continuous, 1 integer with u - l = 1, 2 general integer
-  std::vector<int> aux_of;   // auxiliary index of a general integer column, else -1
-  std::vector<int32_t> gen_int;
+  std::vector<int32_t> gen_int;  // the general integer columns given auxiliary columns, ascending
   int64_t n_aux = 0;
 
   // LP iterated on the device (original + auxiliary)

@@ -7,6 +7,8 @@
 // atomics are integer counts.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "internal.h"
 
 namespace scylla {
@@ -18,17 +20,11 @@ constexpr int kTpItems = 16;
 constexpr int kTpChunk = kTpThreads * kTpItems;  // keys per block and pass
 constexpr int kScanThreads = 1024;
 
-// row index of every nonzero (binary search in the row pointers: long rows cost the
-// same as short ones)
-__global__ void k_tp_rowof(int m, long long nnz, const int* __restrict__ rowptr, int* __restrict__ rowof) {
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nnz; p += (long long)gridDim.x * blockDim.x) {
-    int lo = 0, hi = m;  // the row i with rowptr[i] <= p < rowptr[i + 1]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (rowptr[mid] <= p) lo = mid;
-      else hi = mid;
-    }
-    rowof[p] = lo;
+// row index of every nonzero: a thread per row fills its entries
+__global__ void k_tp_rowof(int m, const int* __restrict__ rowptr, int* __restrict__ rowof) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const int p1 = rowptr[i + 1];
+    for (int p = rowptr[i]; p < p1; ++p) rowof[p] = i;
   }
 }
 
@@ -53,31 +49,86 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_hist(const int* __restrict__ 
   hist[threadIdx.x * gridDim.x + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// exclusive prefix sum of data[0, len) in place, one block: each thread scans a
-// contiguous segment; data[len] receives the total
-__global__ void __launch_bounds__(kScanThreads) k_tp_scan(int* __restrict__ data, long long len) {
-  __shared__ long long part[kScanThreads];
-  const long long seg = (len + kScanThreads - 1) / kScanThreads;
-  const long long b = threadIdx.x * seg, e = b + seg < len ? b + seg : len;
-  long long s = 0;
-  for (long long i = b; i < e; ++i) s += data[i];
-  part[threadIdx.x] = s;
+// Exclusive prefix sum of data[0, len) in place, data[len] = the total (integer
+// sums, so the grouping does not matter): block b owns the segment [b seg,
+// (b + 1) seg); pass 1 sums each segment, pass 2 scans the segment sums in one
+// block, pass 3 rescans each segment from its offset in chunks of
+// kScanThreads * kScanItems (each thread a run of kScanItems, then a block scan of
+// the run totals).
+constexpr int kScanItems = 8;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+constexpr int kScanMaxBlocks = 1024;
+
+// exclusive block-wide scan of one value per thread (kScanThreads threads);
+// returns the thread's offset and the block total in *total
+__device__ __forceinline__ long long block_exclusive_scan(long long v, long long* sh, long long* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  long long x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    long long run = 0;
-    for (int t = 0; t < kScanThreads; ++t) {
-      const long long v = part[t];
-      part[t] = run;
-      run += v;
+  if (w == 0) {
+    long long z = lane < kScanThreads / 32 ? sh[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, z, o);
+      if (lane >= o) z += y;
     }
-    data[len] = int(run);
+    if (lane < kScanThreads / 32) sh[32 + lane] = z;  // inclusive over warps
   }
   __syncthreads();
-  long long run = part[threadIdx.x];
-  for (long long i = b; i < e; ++i) {
-    const int v = data[i];
-    data[i] = int(run);
-    run += v;
+  const long long before = w > 0 ? sh[32 + w - 1] : 0;
+  *total = sh[32 + kScanThreads / 32 - 1];
+  __syncthreads();  // sh is reused by the next call
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int* __restrict__ data, long long len,
+                                                              long long seg, long long* __restrict__ bsum) {
+  __shared__ long long sh[64];
+  const long long b0 = blockIdx.x * seg, b1 = b0 + seg < len ? b0 + seg : len;
+  long long s = 0;
+  for (long long i = b0 + threadIdx.x; i < b1; i += kScanThreads) s += data[i];
+  long long total = 0;
+  block_exclusive_scan(s, sh, &total);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(long long* __restrict__ bsum, int nb,
+                                                           int* __restrict__ data, long long len) {
+  __shared__ long long sh[64];
+  const long long v = int(threadIdx.x) < nb ? bsum[threadIdx.x] : 0;
+  long long total = 0;
+  const long long ex = block_exclusive_scan(v, sh, &total);
+  if (int(threadIdx.x) < nb) bsum[threadIdx.x] = ex;
+  if (threadIdx.x == 0) data[len] = int(total);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(int* __restrict__ data, long long len, long long seg,
+                                                            const long long* __restrict__ bsum) {
+  __shared__ long long sh[64];
+  const long long b0 = blockIdx.x * seg, b1 = b0 + seg < len ? b0 + seg : len;
+  long long carry = bsum[blockIdx.x];
+  for (long long c0 = b0; c0 < b1; c0 += kScanChunk) {
+    const long long t0 = c0 + (long long)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    long long s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      v[k] = t0 + k < b1 ? data[t0 + k] : 0;
+      s += v[k];
+    }
+    long long total = 0;
+    long long run = carry + block_exclusive_scan(s, sh, &total);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+      if (t0 + k < b1) {
+        data[t0 + k] = int(run);
+        run += v[k];
+      }
+    carry += total;
   }
 }
 
@@ -132,6 +183,19 @@ __global__ void k_tp_gather(long long nnz, const int* __restrict__ order, const 
   }
 }
 
+// the scan of data[0, len) with data[len] = total; bsum holds kScanMaxBlocks entries
+void scan_exclusive(int* data, long long len, long long* bsum, cudaStream_t st) {
+  long long nb = (len + kScanChunk - 1) / kScanChunk;
+  if (nb > kScanMaxBlocks) nb = kScanMaxBlocks;
+  if (nb < 1) nb = 1;
+  long long seg = (len + nb - 1) / nb;
+  seg = (seg + kScanChunk - 1) / kScanChunk * kScanChunk;
+  nb = len > 0 ? (len + seg - 1) / seg : 1;
+  k_scan_reduce<<<int(nb), kScanThreads, 0, st>>>(data, len, seg, bsum);
+  k_scan_top<<<1, kScanThreads, 0, st>>>(bsum, int(nb), data, len);
+  k_scan_down<<<int(nb), kScanThreads, 0, st>>>(data, len, seg, bsum);
+}
+
 int grid_for(long long work) {
   const long long g = (work + 255) / 256;
   const long long cap = 8LL * device_sm_count();
@@ -143,7 +207,7 @@ int grid_for(long long work) {
 size_t transpose_scratch_bytes(int n, long long nnz) {
   const long long nb = (nnz + kTpChunk - 1) / kTpChunk;
   const size_t ints = size_t(5 * nnz) + size_t(256 * (nb > 0 ? nb : 1) + 1) + size_t(n) + 1 + 64;
-  return ints * sizeof(int);
+  return ints * sizeof(int) + 8 * sizeof(long long) * kScanMaxBlocks;
 }
 
 cudaError_t transpose_device(int m, int n, long long nnz, const int* rowptr, const int* cols, const double* vals,
@@ -159,11 +223,15 @@ cudaError_t transpose_device(int m, int n, long long nnz, const int* rowptr, con
   idx[1] = s + 3 * nnz;
   int* rowof = s + 4 * nnz;
   int* hist = s + 5 * nnz;
+  // the scan's segment sums after the histogram (8-byte aligned)
+  const size_t hist_ints = size_t(256 * ((nnz + kTpChunk - 1) / kTpChunk)) + 1;
+  long long* bsum = reinterpret_cast<long long*>(
+      (reinterpret_cast<uintptr_t>(hist + hist_ints) + 15) & ~uintptr_t(15));
   const long long nb = (nnz + kTpChunk - 1) / kTpChunk;
   // column counts -> column pointers
   k_tp_count<<<grid_for(nnz), 256, 0, st>>>(nnz, cols, colptr);
-  k_tp_scan<<<1, kScanThreads, 0, st>>>(colptr, n);
-  k_tp_rowof<<<grid_for(nnz), 256, 0, st>>>(m, nnz, rowptr, rowof);
+  scan_exclusive(colptr, n, bsum, st);
+  k_tp_rowof<<<grid_for(m), 256, 0, st>>>(m, rowptr, rowof);
   // radix passes over the column bits
   int bits = 0;
   while (bits < 31 && (1LL << bits) < n) ++bits;
@@ -175,7 +243,7 @@ cudaError_t transpose_device(int m, int n, long long nnz, const int* rowptr, con
     int* kout = keys[pass & 1];
     int* iout = idx[pass & 1];
     k_tp_hist<<<int(nb), kTpThreads, 0, st>>>(kin, nnz, shift, hist);
-    k_tp_scan<<<1, kScanThreads, 0, st>>>(hist, 256 * nb);
+    scan_exclusive(hist, 256 * nb, bsum, st);
     k_tp_scatter<<<int(nb), kTpThreads, 0, st>>>(kin, iin, kout, iout, nnz, shift, hist);
     kin = kout;
     iin = iout;

@@ -238,8 +238,15 @@ class LP:
         _check(lib().scylla_run(self.h, _dp(x), C.byref(r)))
         return r, x
 
-    def primal(self) -> np.ndarray:
-        x = np.empty(self.n)
+    def primal(self, out: "np.ndarray | None" = None) -> np.ndarray:
+        """The primal iterate in the original space; written into ``out`` (a
+        contiguous float64 array of length n) when given."""
+        if out is None:
+            x = np.empty(self.n)
+        else:
+            x = out
+            if x.dtype != np.float64 or x.shape != (self.n,) or not x.flags["C_CONTIGUOUS"]:
+                raise ValueError("out must be a contiguous float64 array of length n")
         _check(lib().scylla_get_primal(self.h, _dp(x)))
         return x
 

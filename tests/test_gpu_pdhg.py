@@ -327,6 +327,23 @@ def test_state_roundtrip_and_resume():
     h.close()
 
 
+def test_primal_into_caller_buffer():
+    """LP.primal(out=...) writes the same values as a fresh array and rejects a buffer
+    of the wrong type or length."""
+    inst = INSTANCES["packcover_2kx4k"]
+    g, _ = pair(inst, precision=1)
+    g.pdhg_solve(1e-4, 20000)
+    buf = np.full(inst.n, np.nan)
+    out = g.primal(out=buf)
+    assert out is buf
+    np.testing.assert_array_equal(buf, g.primal())
+    with pytest.raises(ValueError):
+        g.primal(out=np.zeros(inst.n, dtype=np.float32))
+    with pytest.raises(ValueError):
+        g.primal(out=np.zeros(inst.n + 1))
+    g.close()
+
+
 def test_stall_rule_matches_oracle():
     inst = INSTANCES["setcover_200x500"]
     g, o = pair(inst, stall_checks=2, trace_capacity=100000)
