@@ -1389,14 +1389,52 @@ __global__ void k_scale_vectors(DevVecs v) {
 }
 
 // ------------------------------------------------------- objective update ---
+// The end of both objective kernels: the block's partials (offset terms, sum
+// c_hat^2, sum of squared row-bound magnitudes) are summed in thread order into
+// o.red[3 b + k]; the last block to finish reduces them over the blocks in a fixed
+// order (reduce_one) and writes ||b|| (largest finite |lo|, |hi| per row), ||c_hat||
+// and the offset (the reduced offset terms, or offset_base) to the control block.
+__device__ void objective_finish(const DevObjective& o, double off, double c2, double b2, double offset_base,
+                                 bool use_offset_terms) {
+  __shared__ double sh[3][kThreads];
+  sh[0][threadIdx.x] = off;
+  sh[1][threadIdx.x] = c2;
+  sh[2][threadIdx.x] = b2;
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double a = 0.0;
+    for (int q = 0; q < int(blockDim.x); ++q) a += sh[threadIdx.x][q];
+    o.red[3 * blockIdx.x + threadIdx.x] = a;
+    __threadfence();  // each writer publishes its partial before the block's ticket
+  }
+  if (!is_last_block(&o.ctl->cnt_misc)) return;
+  __shared__ double scratch[3 * (kThreads - 32)];
+  __shared__ double out[3];
+  reduce_one<3>(o.red, int(gridDim.x), scratch, out);
+  if (threadIdx.x == 0) {
+    o.ctl->bnorm = sqrt(out[2]);
+    o.ctl->cnorm = sqrt(out[1]);
+    o.ctl->offset = use_offset_terms ? out[0] : offset_base;
+    o.ctl->cnt_misc = 0;
+  }
+}
+
+// squared magnitude of the largest finite bound of a row
+__device__ __forceinline__ double row_bound2(double lo, double hi) {
+  const double inf = pos_inf<double>();
+  const double a = lo > -inf ? fabs(lo) : 0.0, b = hi < inf ? fabs(hi) : 0.0;
+  const double v = fmax(a, b);
+  return v * v;
+}
+
 // c_hat_j = alpha^K s c_j + (1 - alpha^K) g_j (Algorithm 1, Section 2.4): g_j = +1
 // when xhat_j = l_j and -1 when xhat_j = u_j on integer columns with u - l = 1; a
 // general integer column keeps alpha^K s c_j and its auxiliary column gets cost
 // (1 - alpha^K) with auxiliary rows d - x >= -xhat_j, d + x >= xhat_j.
-// part[b] = (offset terms, sum c_hat^2) per block.
+// The squared row-bound magnitudes are summed over the original rows here and, for
+// the auxiliary rows (lo = -xhat_j, xhat_j; hi = +inf), where they are written.
 __global__ void k_objective_cols(DevObjective o, double t, double om) {
-  double off = 0.0, c2 = 0.0;
-  const double inf = pos_inf<double>();
+  double off = 0.0, c2 = 0.0, b2 = 0.0;
   const int stride = gridDim.x * blockDim.x;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < o.n; j += stride) {
     double ch;
@@ -1418,6 +1456,7 @@ __global__ void k_objective_cols(DevObjective o, double t, double om) {
         const int r0 = o.m_orig + 2 * tq;
         o.lo_unscaled[r0] = -xh;
         o.lo_unscaled[r0 + 1] = xh;
+        b2 += row_bound2(-xh, o.hi_unscaled[r0]) + row_bound2(xh, o.hi_unscaled[r0 + 1]);
         const double l0 = -xh * o.R[r0], l1 = xh * o.R[r0 + 1];
         o.lo64[r0] = l0;
         o.lo64[r0 + 1] = l1;
@@ -1436,66 +1475,23 @@ __global__ void k_objective_cols(DevObjective o, double t, double om) {
     if (o.c32) o.c32[j] = float(cs);
     c2 += ch * ch;
   }
-  (void)inf;
-  __shared__ double s0[kThreads], s1[kThreads];
-  s0[threadIdx.x] = off;
-  s1[threadIdx.x] = c2;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int q = 0; q < blockDim.x; ++q) {
-      a += s0[q];
-      b += s1[q];
-    }
-    o.red[2 * blockIdx.x] = a;
-    o.red[2 * blockIdx.x + 1] = b;
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < o.m_orig; i += stride)
+    b2 += row_bound2(o.lo_unscaled[i], o.hi_unscaled[i]);
+  objective_finish(o, off, c2, b2, 0.0, true);
 }
 
-// sum c_hat^2 only (no change of c_hat), for the norms at create time
-__global__ void k_cnorm_cols(DevObjective o) {
-  double c2 = 0.0;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < o.n; j += gridDim.x * blockDim.x) {
+// the norms at create time without a change of c_hat: ||c_hat|| and ||b|| over all
+// rows, offset = offset_base
+__global__ void k_cnorm_cols(DevObjective o, double offset_base) {
+  double c2 = 0.0, b2 = 0.0;
+  const int stride = gridDim.x * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < o.n; j += stride) {
     const double ch = o.chat[j];
     c2 += ch * ch;
   }
-  __shared__ double s1[kThreads];
-  s1[threadIdx.x] = c2;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double b = 0.0;
-    for (int q = 0; q < blockDim.x; ++q) b += s1[q];
-    o.red[2 * blockIdx.x] = 0.0;
-    o.red[2 * blockIdx.x + 1] = b;
-  }
-}
-
-// ||b||^2 over rows (largest finite |lo|, |hi| per row), then the final reduction of
-// both kernels into the control block (single block of this kernel reduces).
-__global__ void k_objective_rows(DevObjective o, double offset_base, int use_offset_terms) {
-  const double inf = pos_inf<double>();
-  double b2 = 0.0;
-  for (int i = threadIdx.x; i < o.m; i += blockDim.x) {
-    const double lo = o.lo_unscaled[i], hi = o.hi_unscaled[i];
-    const double a = lo > -inf ? fabs(lo) : 0.0;
-    const double b = hi < inf ? fabs(hi) : 0.0;
-    const double v = fmax(a, b);
-    b2 += v * v;
-  }
-  __shared__ double sb[kThreads];
-  sb[threadIdx.x] = b2;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double bb = 0.0, off = 0.0, cc = 0.0;
-    for (int q = 0; q < blockDim.x; ++q) bb += sb[q];
-    for (int q = 0; q < o.red_blocks; ++q) {
-      off += o.red[2 * q];
-      cc += o.red[2 * q + 1];
-    }
-    o.ctl->bnorm = sqrt(bb);
-    o.ctl->cnorm = sqrt(cc);
-    o.ctl->offset = use_offset_terms ? off : offset_base;
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < o.m; i += stride)
+    b2 += row_bound2(o.lo_unscaled[i], o.hi_unscaled[i]);
+  objective_finish(o, 0.0, c2, b2, offset_base, false);
 }
 
 // ------------------------------------------------------------ batched solve ---
@@ -1930,13 +1926,11 @@ cudaError_t launch_scale_vectors(const DevVecs& v, cudaStream_t st) {
 cudaError_t launch_objective_update(const DevObjective& o, double t_scale, double one_minus_aK,
                                     cudaStream_t st) {
   k_objective_cols<<<o.red_blocks, kThreads, 0, st>>>(o, t_scale, one_minus_aK);
-  k_objective_rows<<<1, kThreads, 0, st>>>(o, 0.0, 1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_objective_norms(const DevObjective& o, double offset, cudaStream_t st) {
-  k_cnorm_cols<<<o.red_blocks, kThreads, 0, st>>>(o);
-  k_objective_rows<<<1, kThreads, 0, st>>>(o, offset, 0);
+  k_cnorm_cols<<<o.red_blocks, kThreads, 0, st>>>(o, offset);
   return cudaGetLastError();
 }
 
