@@ -45,6 +45,28 @@ __device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
   o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
 }
 
+// The same loads with the streaming cache hint (ld.global.cs: lines allocated
+// evict-first in L1 and L2), for matrix data read once per launch while the gathered
+// vector should stay in L2.
+__device__ __forceinline__ void ld4s(const int* p, int (&o)[4]) {
+  const int4 t = __ldcs(reinterpret_cast<const int4*>(p));
+  o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void ld4s(const float* p, float (&o)[4]) {
+  const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+  o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void ld4s(const double* p, double (&o)[4]) {
+  const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+template <bool kStream, typename V>
+__device__ __forceinline__ void ld4_as(const V* p, V (&o)[4]) {
+  if constexpr (kStream) ld4s(p, o);
+  else ld4(p, o);
+}
+
 // float -> double without the FP64 pipe (where a conversion costs as much as an FP64
 // add): sign, exponent rebiased by 1023 - 127, mantissa shifted into place; exact for
 // zeros and normal numbers, which is all the iterates hold; subnormals, infinities and

@@ -53,7 +53,7 @@ __device__ __forceinline__ WarpTiles warp_tiles(int ntiles) {
 // step i + 1 are loaded before the gathers of step i are issued, so the loads of a
 // row overlap its gathers (a 500-entry row: five dependent latencies, not eight);
 // each lane accumulates its entries in the same order as an unpipelined loop.
-template <int NV, typename Acc, typename V, typename Gather>
+template <int NV, bool kStream, typename Acc, typename V, typename Gather>
 __device__ __forceinline__ void long_row_sum(int p0, int p1, const int* __restrict__ cols,
                                              const V* __restrict__ vals, Gather& gat, Acc (&s)[NV]) {
   constexpr int kStep = 32 * kVec;
@@ -64,15 +64,15 @@ __device__ __forceinline__ void long_row_sum(int p0, int p1, const int* __restri
   int cc[4] = {0, 0, 0, 0};
   V vv[4] = {V(0), V(0), V(0), V(0)};
   if (p < p1) {
-    ld4(cols + p, cc);
-    ld4(vals + p, vv);
+    ld4_as<kStream>(cols + p, cc);
+    ld4_as<kStream>(vals + p, vv);
   }
   for (; p < p1; p += kStep) {
     int cn[4] = {0, 0, 0, 0};
     V vn[4] = {V(0), V(0), V(0), V(0)};
     if (p + kStep < p1) {
-      ld4(cols + p + kStep, cn);
-      ld4(vals + p + kStep, vn);
+      ld4_as<kStream>(cols + p + kStep, cn);
+      ld4_as<kStream>(vals + p + kStep, vn);
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -116,6 +116,9 @@ __device__ __forceinline__ bool spmv_tiles(const int2* __restrict__ tiles, int n
                                            Acc* __restrict__ sm, Pro&& pro) {
   const int lane = threadIdx.x & 31;
   const WarpTiles wt = warp_tiles(ntiles);
+  // wide tiles serve DRAM-resident problems: stream the matrix past the caches so
+  // that the gathered vector stays in L2
+  constexpr bool kStream = RPL > 1;
   int r0 = 0, r1 = 0, p0 = 0, p1 = 0;
   int q0[RPL], q1[RPL];
   bool longrow = false;
@@ -148,8 +151,8 @@ __device__ __forceinline__ bool spmv_tiles(const int2* __restrict__ tiles, int n
       for (int it = 0; it < 3; ++it) {
         const int p = base + (it * 32 + lane) * kVec;
         if (p < p1) {
-          ld4(cols + p, c[it]);
-          ld4(vals + p, v[it]);
+          ld4_as<kStream>(cols + p, c[it]);
+          ld4_as<kStream>(vals + p, v[it]);
         }
       }
     }
@@ -162,7 +165,7 @@ __device__ __forceinline__ bool spmv_tiles(const int2* __restrict__ tiles, int n
     if (longrow) {
       const typename Epi::Pre pre = epi.load(r0);
       Acc s[NV];
-      long_row_sum<NV>(p0, p1, cols, vals, gat, s);
+      long_row_sum<NV, kStream>(p0, p1, cols, vals, gat, s);
       if (lane == 0) epi.finish(r0, s, pre);
     } else {
       const int nr = r1 - r0, L = row_lanes(nr), sub = L > 1 ? lane % L : 0;
@@ -1520,7 +1523,7 @@ __device__ __forceinline__ void spmv_tiles_batch(const int2* __restrict__ tiles,
     if (r1 - r0 == 1 && p1 - p0 > kTileNnz) {
       const typename Epi::Pre pre = epi.load(r0);
       Acc s[NV];
-      long_row_sum<NV>(p0, p1, cols, vals, gat, s);
+      long_row_sum<NV, false>(p0, p1, cols, vals, gat, s);
       if (lane == 0) epi.finish(r0, s, pre);
     } else {
       const bool mine = lane < r1 - r0;
