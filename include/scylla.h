@@ -113,6 +113,11 @@ typedef struct {
                                    shared memory by bulk copies; 4: 32-row tiles, plain loads (0) */
   int32_t host_transpose;       /* 1: build the stored transpose A^T on the host threads; 0: on the device,
                                    a stable radix sort of the nonzeros by column (0) */
+  /* continuous repair inside scylla_run (see scylla_repair; not part of the paper's
+     Algorithm 1, so off by default) */
+  int64_t repair_iters;         /* attempt limit of each repair (all its rounds); 0 = no repair (0) */
+  double repair_tol;            /* rel-KKT target of each repair solve (1e-7) */
+  int32_t repair_rounds;        /* solves of one repair, with the violated rows shifted in between (8) */
 } scylla_params;
 
 typedef struct {
@@ -129,13 +134,25 @@ typedef struct {
 
 typedef struct {
   int32_t status;           /* SCYLLA_FOUND / SCYLLA_NOT_FOUND */
-  int32_t found_by;         /* 1: rounded LP point (Algorithm 1 first test), 2: fix-and-propagate */
+  int32_t found_by;         /* 1: rounded LP point (Algorithm 1 first test), 2: fix-and-propagate,
+                               3: continuous repair of the fix-and-propagate point */
   int64_t rounds;           /* pump rounds K performed */
   int64_t total_iterations; /* PDHG attempts over all rounds */
   int64_t perturbations;    /* rounds in which cycling was detected */
   double objective;         /* c^T x of the returned point */
   double seconds, seconds_pdhg, seconds_fixprop;
 } scylla_run_result;
+
+typedef struct {
+  int32_t status;       /* SCYLLA_FOUND when the repaired point passes scylla_check_feasible */
+  int32_t pdhg_status;  /* status of the last repair solve (SCYLLA_CONVERGED / ITER_LIMIT / ...) */
+  int64_t iterations;   /* PDHG attempts of all rounds */
+  int32_t rounds;       /* solves performed */
+  int32_t shifted_rows; /* rows whose working bounds were moved, over all rounds */
+  double rel_kkt;       /* relative KKT error of the last solve's point (on its working bounds) */
+  double objective;     /* c^T x of the returned point */
+  double seconds;       /* device time of the solves */
+} scylla_repair_result;
 
 typedef struct scylla_lp scylla_lp; /* opaque; owns all device and host copies */
 
@@ -182,8 +199,10 @@ int scylla_get_objective(const scylla_lp* lp, double* c_hat, double* offset);
 
 /* The whole heuristic (Algorithm 1): PDHG -> MIP-feasibility test -> fix-and-
  * propagate -> feasibility test -> cycle handling -> objective update, with the
- * tolerance schedule of Section 2.2.  x_out (host, length n original) receives the
- * solution when out->status == SCYLLA_FOUND; every returned point passed
+ * tolerance schedule of Section 2.2.  With p.repair_iters > 0 a fix-and-propagate
+ * point that fails the test is given to scylla_repair (p.repair_tol, p.repair_iters)
+ * before the cycle handling.  x_out (host, length n original) receives the solution
+ * when out->status == SCYLLA_FOUND; every returned point passed
  * scylla_check_feasible.  Errors: INVALID_ARG, CUDA, TIMEOUT (time limit hit). */
 int scylla_run(scylla_lp* lp, double* x_out, scylla_run_result* out);
 
@@ -234,6 +253,47 @@ int scylla_fix_and_propagate(const scylla_lp* lp, const double* xbar, double* xh
 /* Exact MIP-feasibility test of x (host, length n) on the original MIP
  * (Algorithm 1, both "MIP-feasible" tests): *feasible = 1 or 0. */
 int scylla_check_feasible(const scylla_lp* lp, const double* x, int32_t* feasible);
+
+/* Replace the bounds of the original columns (host, length n each), keeping the
+ * matrix, its preconditioning, the objective and the iterate; the auxiliary columns
+ * keep theirs.  The next solve projects onto the new box (Algorithm 1, primal step);
+ * call scylla_reset_state for a cold start.  The host copies used by the propagation
+ * and the feasibility test see the new bounds too.
+ * Errors: INVALID_ARG (null, NaN, lo > hi, lo = +inf, hi = -inf, an integer column
+ * with a fractional finite bound), CUDA. */
+int scylla_set_col_bounds(scylla_lp* lp, const double* col_lo, const double* col_hi);
+
+/* Replace the bounds of the original rows (host, length m each), keeping the
+ * matrix, its preconditioning, the objective and the iterate; auxiliary rows keep
+ * theirs, and ||b|| of the relative KKT error follows the new bounds.
+ * Errors: INVALID_ARG (null, NaN, lo > hi, lo = +inf, hi = -inf), CUDA. */
+int scylla_set_row_bounds(scylla_lp* lp, const double* row_lo, const double* row_hi);
+
+/* Continuous repair of an integer assignment.  The paper keeps the continuous part
+ * of fix-and-propagate's point at the LP values (Section 2.3), which on mixed
+ * problems often leaves rows violated; this re-solves the LP with the integer
+ * columns fixed,
+ *     min c^T x  s.t.  lo <= A x <= hi,  x_j = xhat_j (j integer),
+ *                      l_j <= x_j <= u_j (j continuous),
+ * by the same PDHG path (preconditioning, adaptive steps, restarts, FP64 checks;
+ * Sections 2.1-2.2) on a second device copy of the original MIP that the handle
+ * builds on first use (original objective, no auxiliary columns, the handle's PDHG
+ * parameters, always FP64) and keeps until it is destroyed.  Up to
+ * p.repair_rounds solves to rel-KKT <= tol, the first from the cold start, the next
+ * ones warm: after each, the integer entries are set to xhat's exactly and the point
+ * is given scylla_check_feasible's test; if it fails, every row whose activity
+ * (FP64, in CSR order) exceeds an original bound has its working bound moved
+ * inward by the excess plus the test's tolerance 1e-6 max(1, |bound|) (a row whose
+ * working bounds would cross gets their midpoint), because a PDHG point at a
+ * relative KKT error far below 1e-6 can still miss single rows by more than that.
+ * iter_limit bounds the attempts of all rounds together.
+ *   xhat: host, length n (integer entries integral within [l, u]; the others are
+ *   ignored).  x_out: host, length n, receives the last point whatever the outcome.
+ *   out: the test's verdict and the solves' figures (attempts and seconds summed).
+ * Errors: INVALID_ARG (null, tol < 0, iter_limit < 0, xhat not integral within the
+ * bounds of an integer column), OOM and CUDA from building the copy. */
+int scylla_repair(scylla_lp* lp, const double* xhat, double tol, int64_t iter_limit, double* x_out,
+                  scylla_repair_result* out);
 
 /* Cycle handling of Section 2.3 on its own.  kind: 1 short cycle, 2 long cycle.
  * xhat: host in/out, length n; xbar: host, length n; K: round; seed: stream seed.

@@ -30,6 +30,19 @@ Readings of what the paper leaves open:
   one unit toward xbar_j, or away from it when xhat_j already is round(xbar_j),
   inside [l_j, u_j] (the other direction when the first one is blocked).  Random
   numbers: SplitMix64 seeded with ``seed XOR K``, uniforms ``(r >> 11) * 2^-53``.
+* Continuous repair (an extension; the paper keeps the continuous part of the
+  fix-and-propagate point at the LP values, Section 2.3): the LP of the original
+  MIP with every integer column fixed at xhat (l_j = u_j = xhat_j), original
+  objective and rows, solved by the oracle PDHG to the given rel-KKT in up to
+  ``rounds`` solves (the first from the cold start, the next ones warm) within one
+  attempt budget.  After each solve the integer entries are set to xhat's and the
+  point is given the feasibility check; when it fails, every row whose activity
+  (FP64, CSR order) exceeds an original bound gets its working bound moved inward
+  by the excess plus 1e-6 max(1, |bound|) (crossing working bounds meet at their
+  midpoint), since a PDHG point can miss single rows by more than the check's
+  tolerance long after its relative KKT error is small.  In the outer loop the
+  repair runs, when asked for, after a fix-and-propagate point fails the check and
+  before the cycle test.
 * Feasibility check: integrality exact; a row whose coefficients, bounds and
   column values are all integers (below 2^47) is checked in exact integer
   arithmetic; otherwise activities are summed in CSR order with Neumaier
@@ -239,6 +252,51 @@ def check_feasible(rowptr, cols, vals, lo, hi, l, u, is_int, x, tol=1e-6) -> boo
     return True
 
 
+def repair(inst, xhat, tol: float, iter_limit: int, params: PdhgParams | None = None, rounds: int = 8):
+    """Continuous repair of xhat's integer assignment (see the module notes).
+    Returns (status FOUND / NOT_FOUND, x, dict of iterations, rounds, shifted_rows,
+    rel_kkt and status of the last solve)."""
+    A = sp.csr_matrix((inst.vals, inst.cols, inst.rowptr), shape=(inst.m, inst.n))
+    is_int = np.asarray(inst.is_int) == 1
+    xh = np.asarray(xhat, dtype=np.float64)
+    l = np.asarray(inst.l, dtype=np.float64).copy()
+    u = np.asarray(inst.u, dtype=np.float64).copy()
+    l[is_int] = xh[is_int]
+    u[is_int] = xh[is_int]
+    lo = np.asarray(inst.lo, dtype=np.float64)
+    hi = np.asarray(inst.hi, dtype=np.float64)
+    lo_w, hi_w = lo.copy(), hi.copy()
+    lp = OracleLP(A, inst.c, lo_w, hi_w, l, u, params=params or PdhgParams())
+    info = {"iterations": 0, "rounds": 0, "shifted_rows": 0, "rel_kkt": math.inf, "status": None}
+    st = NOT_FOUND
+    x = None
+    for t in range(rounds):
+        res = lp.solve(tol, iter_limit - info["iterations"])
+        info["iterations"] += res.iterations
+        info["rounds"] = t + 1
+        info["rel_kkt"] = res.rel_kkt
+        info["status"] = res.status
+        x = lp.primal().copy()
+        x[is_int] = xh[is_int]
+        if check_feasible(inst.rowptr, inst.cols, inst.vals, lo, hi, inst.l, inst.u, inst.is_int, x):
+            st = FOUND
+            break
+        if t + 1 == rounds or info["iterations"] >= iter_limit:
+            break
+        act = A @ x
+        up = act > hi
+        dn = (act < lo) & ~up
+        hi_w[up] -= (act[up] - hi[up]) + 1e-6 * np.maximum(1.0, np.abs(hi[up]))
+        lo_w[dn] += (lo[dn] - act[dn]) + 1e-6 * np.maximum(1.0, np.abs(lo[dn]))
+        cross = (up | dn) & (lo_w > hi_w)
+        mid = 0.5 * (lo_w[cross] + hi_w[cross])
+        lo_w[cross] = mid
+        hi_w[cross] = mid
+        info["shifted_rows"] += int(np.count_nonzero(up | dn))
+        lp.set_row_bounds(lo_w, hi_w)
+    return st, x, info
+
+
 @dataclass
 class PumpParams:
     alpha: float = 0.9
@@ -250,6 +308,9 @@ class PumpParams:
     total_iter_cap: int = 10 ** 9
     stall_checks: int = 5
     seed: int = 0
+    repair_iters: int = 0  # attempt limit of each continuous repair; 0 = none
+    repair_tol: float = 1e-7
+    repair_rounds: int = 8
     pdhg: PdhgParams = field(default_factory=PdhgParams)
 
 
@@ -297,6 +358,12 @@ def pump(inst, params: PumpParams | None = None) -> PumpResult:
         if check_feasible(inst.rowptr, inst.cols, inst.vals, inst.lo, inst.hi, inst.l, inst.u,
                           inst.is_int, xhat):
             return PumpResult(FOUND, xhat, K, total, "fixprop", log)
+        if pp.repair_iters > 0:
+            st, xrep, rinfo = repair(inst, xhat, pp.repair_tol, min(pp.repair_iters, pp.total_iter_cap - total),
+                                     pp.pdhg, pp.repair_rounds)
+            total += rinfo["iterations"]
+            if st == FOUND:
+                return PumpResult(FOUND, xrep, K, total, "repair", log)
         xhat, kind = perturb(xhat, xbar, hist, K, pp.seed, int_cols, inst.l, inst.u)
         hist.append(tuple(float(xhat[j]) for j in int_cols))
         chat, aux_lo, offset = objective_update(inst.c, inst.is_int, inst.l, inst.u, xhat, K,

@@ -201,6 +201,12 @@ cudaError_t launch_precondition(const DevSetup& s, int ruiz_iters, bool pock_cha
 // a~ = diag(R) A diag(C) in both CSR copies (and their FP32 shadows)
 cudaError_t launch_scale_values(const DevSetup& s, cudaStream_t st);
 cudaError_t fill_f64(double* p, long long count, double v, cudaStream_t st);
+// l64 = l / C, u64 = u / C (and the FP32 shadows when given) over n columns
+cudaError_t scale_col_bounds(long long n, const double* l, const double* u, const double* C, double* l64,
+                             double* u64, float* l32, float* u32, cudaStream_t st);
+// lo64 = lo R, hi64 = hi R (and the FP32 shadows when given) over m rows
+cudaError_t scale_row_bounds(long long m, const double* lo, const double* hi, const double* R, double* lo64,
+                             double* hi64, float* lo32, float* hi32, cudaStream_t st);
 // kind = is_int (0/1) and aux_of = -1 over n columns
 cudaError_t column_kinds(long long n, const uint8_t* is_int, int* kind, int* aux_of, cudaStream_t st);
 struct SetupNorms {

@@ -81,6 +81,9 @@ extern "C" void scylla_default_params(scylla_params* p) {
   p->pdl = 1;
   p->prefetch = 0;
   p->host_transpose = 0;
+  p->repair_iters = 0;
+  p->repair_tol = 1e-7;
+  p->repair_rounds = 8;
 }
 
 extern "C" const char* scylla_last_error(void) { return get_error(); }
@@ -299,6 +302,8 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   if (!(lp->p.device_wait_limit_s > 0.0)) FAIL(SCYLLA_ERR_INVALID_ARG, "device_wait_limit_s must be > 0");
   if (lp->p.prefetch < 0 || lp->p.prefetch > 4) FAIL(SCYLLA_ERR_INVALID_ARG, "prefetch must be 0..4");
   if (lp->p.host_transpose < 0 || lp->p.host_transpose > 1) FAIL(SCYLLA_ERR_INVALID_ARG, "host_transpose must be 0 or 1");
+  if (lp->p.repair_iters < 0 || !(lp->p.repair_tol >= 0.0) || lp->p.repair_rounds < 1)
+    FAIL(SCYLLA_ERR_INVALID_ARG, "need repair_iters >= 0, repair_tol >= 0 and repair_rounds >= 1");
   if (lp->p.precision != SCYLLA_PREC_FP64 && lp->p.precision != SCYLLA_PREC_MIXED)
     FAIL(SCYLLA_ERR_INVALID_ARG, "unknown precision");
   CK(cudaGetDevice(&lp->device));
@@ -729,6 +734,12 @@ DevObjective scylla_lp::objective_desc() {
 }
 
 void scylla_lp::release() {
+  if (repair_lp) {
+    cudaStreamSynchronize(repair_lp->st);
+    repair_lp->release();
+    delete repair_lp;
+    repair_lp = nullptr;
+  }
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
   exec = nullptr;
@@ -1110,6 +1121,164 @@ extern "C" int scylla_get_trace(const scylla_lp* lp, double* steps, int64_t* n_s
   if (n_steps) *n_steps = ns;
   if (n_checks) *n_checks = nc;
   return SCYLLA_OK;
+}
+
+// ------------------------------------------------------ column bounds, repair ---
+int scylla_lp::set_col_bounds(const double* l, const double* u) {
+  int rc = order_after_user();
+  if (rc != SCYLLA_OK) return rc;
+  CK(cudaMemcpyAsync(l_un, l, sizeof(double) * n0, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(u_un, u, sizeof(double) * n0, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(l_orig, l_un, sizeof(double) * n0, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(u_orig, u_un, sizeof(double) * n0, cudaMemcpyDeviceToDevice, st));
+  CK(scale_col_bounds(n0, l_un, u_un, C, l64, u64, l32, u32, st));
+  if (host_vectors_ready) {
+    l0.assign(l, l + n0);
+    u0.assign(u, u + n0);
+  }
+  CK(cudaStreamSynchronize(st));
+  return SCYLLA_OK;
+}
+
+int scylla_lp::set_row_bounds(const double* lo, const double* hi) {
+  int rc = order_after_user();
+  if (rc != SCYLLA_OK) return rc;
+  if (m0 > 0) {
+    CK(cudaMemcpyAsync(lo_un, lo, sizeof(double) * m0, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(hi_un, hi, sizeof(double) * m0, cudaMemcpyHostToDevice, st));
+    CK(scale_row_bounds(m0, lo_un, hi_un, R, lo64, hi64, lo32, hi32, st));
+  }
+  // ||b|| from the new bounds; c_hat and the offset stay
+  CK(cudaMemcpyAsync(h_ctl, ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  CK(launch_objective_norms(objective_desc(), h_ctl->offset, st));
+  if (host_vectors_ready) {
+    lo0.assign(lo, lo + m0);
+    hi0.assign(hi, hi + m0);
+  }
+  CK(cudaStreamSynchronize(st));
+  return SCYLLA_OK;
+}
+
+extern "C" int scylla_set_row_bounds(scylla_lp* lp, const double* row_lo, const double* row_hi) {
+  if (!lp || ((!row_lo || !row_hi) && lp->m0 > 0)) FAIL(SCYLLA_ERR_INVALID_ARG, "null argument");
+  for (int64_t i = 0; i < lp->m0; ++i) {
+    const double a = row_lo[i], b = row_hi[i];
+    if (std::isnan(a) || std::isnan(b) || a > b || a == kInf || b == -kInf)
+      FAIL(SCYLLA_ERR_INVALID_ARG, "invalid row bounds at row " + std::to_string(i));
+  }
+  return lp->set_row_bounds(row_lo, row_hi);
+}
+
+extern "C" int scylla_set_col_bounds(scylla_lp* lp, const double* col_lo, const double* col_hi) {
+  if (!lp || !col_lo || !col_hi) FAIL(SCYLLA_ERR_INVALID_ARG, "null argument");
+  int rc = lp->ensure_host_vectors();
+  if (rc != SCYLLA_OK) return rc;
+  for (int64_t j = 0; j < lp->n0; ++j) {
+    const double a = col_lo[j], b = col_hi[j];
+    if (std::isnan(a) || std::isnan(b) || a > b || a == kInf || b == -kInf)
+      FAIL(SCYLLA_ERR_INVALID_ARG, "invalid column bounds at column " + std::to_string(j));
+    if (lp->int0[size_t(j)] && ((std::isfinite(a) && a != std::floor(a)) || (std::isfinite(b) && b != std::floor(b))))
+      FAIL(SCYLLA_ERR_INVALID_ARG, "integer column with a fractional bound: " + std::to_string(j));
+  }
+  return lp->set_col_bounds(col_lo, col_hi);
+}
+
+// The continuous repair: the original MIP's LP with the integer columns fixed at
+// xhat, solved on a second handle without auxiliary columns (built on first use
+// from the host copy of the original MIP) from its cold start.
+int scylla_lp::repair(const double* xhat, double tol, int64_t iter_limit, double* x_out,
+                      scylla_repair_result* out) {
+  int rc = ensure_host_matrix();
+  if (rc != SCYLLA_OK) return rc;
+  for (int64_t j = 0; j < n0; ++j)
+    if (int0[size_t(j)] && !(std::isfinite(xhat[j]) && xhat[j] == std::floor(xhat[j]) && xhat[j] >= l0[size_t(j)] &&
+                             xhat[j] <= u0[size_t(j)]))
+      FAIL(SCYLLA_ERR_INVALID_ARG, "xhat not integral within bounds at integer column " + std::to_string(j));
+  if (!repair_lp) {
+    scylla_csr A{m0, n0, nnz0, rowptr0.data(), cols0.data(), vals0.data()};
+    scylla_params q = p;
+    q.aux_general_integers = 0;
+    q.trace_capacity = 0;
+    q.repair_iters = 0;
+    q.precision = SCYLLA_PREC_FP64;
+    scylla_lp* r = new scylla_lp();
+    rc = create_impl(&A, c0.data(), lo0.data(), hi0.data(), l0.data(), u0.data(), int0.data(), &q, user_st, r);
+    if (rc != SCYLLA_OK) {
+      r->release();
+      delete r;
+      return rc;
+    }
+    repair_lp = r;
+  }
+  std::vector<double> lf(l0), uf(u0);
+  for (int64_t j = 0; j < n0; ++j)
+    if (int0[size_t(j)]) lf[size_t(j)] = uf[size_t(j)] = xhat[j];
+  rc = repair_lp->set_col_bounds(lf.data(), uf.data());
+  // working row bounds: the original ones for the first solve
+  std::vector<double> lo_w(lo0), hi_w(hi0);
+  if (rc == SCYLLA_OK) rc = repair_lp->set_row_bounds(lo_w.data(), hi_w.data());
+  if (rc == SCYLLA_OK) rc = scylla_reset_state(repair_lp);
+  if (rc != SCYLLA_OK) return rc;
+  out->status = SCYLLA_NOT_FOUND;
+  for (int t = 0; t < p.repair_rounds; ++t) {
+    scylla_pdhg_result res{};
+    rc = repair_lp->solve(tol, iter_limit - out->iterations, 0, &res);
+    if (rc == SCYLLA_OK) rc = repair_lp->fetch_x(x_out, int(n0));
+    if (rc != SCYLLA_OK) return rc;
+    out->rounds = t + 1;
+    out->iterations += res.iterations;
+    out->seconds += res.seconds;
+    out->pdhg_status = res.status;
+    out->rel_kkt = res.rel_kkt;
+    for (int64_t j = 0; j < n0; ++j)
+      if (int0[size_t(j)]) x_out[j] = xhat[j];
+    if (check_feasible_host(*this, x_out)) {
+      out->status = SCYLLA_FOUND;
+      break;
+    }
+    if (t + 1 == p.repair_rounds || out->iterations >= iter_limit) break;
+    // move the working bound of every row whose activity exceeds an original bound
+    int shifted = 0;
+    for (int64_t i = 0; i < m0; ++i) {
+      double a = 0.0;
+      for (int64_t q = rowptr0[size_t(i)]; q < rowptr0[size_t(i) + 1]; ++q) a += vals0[size_t(q)] * x_out[cols0[size_t(q)]];
+      const double lo = lo0[size_t(i)], hi = hi0[size_t(i)];
+      bool moved = false;
+      if (a > hi) {
+        hi_w[size_t(i)] -= (a - hi) + 1e-6 * std::max(1.0, std::fabs(hi));
+        moved = true;
+      } else if (a < lo) {
+        lo_w[size_t(i)] += (lo - a) + 1e-6 * std::max(1.0, std::fabs(lo));
+        moved = true;
+      }
+      if (moved) {
+        ++shifted;
+        if (lo_w[size_t(i)] > hi_w[size_t(i)]) lo_w[size_t(i)] = hi_w[size_t(i)] = 0.5 * (lo_w[size_t(i)] + hi_w[size_t(i)]);
+      }
+    }
+    out->shifted_rows += shifted;
+    rc = repair_lp->set_row_bounds(lo_w.data(), hi_w.data());
+    if (rc != SCYLLA_OK) return rc;
+  }
+  double obj = 0.0;
+  for (int64_t j = 0; j < n0; ++j) obj += c0[size_t(j)] * x_out[j];
+  out->objective = obj;
+  return SCYLLA_OK;
+}
+
+extern "C" int scylla_repair(scylla_lp* lp, const double* xhat, double tol, int64_t iter_limit, double* x_out,
+                             scylla_repair_result* out) {
+  if (!lp || !xhat || !x_out || !out) FAIL(SCYLLA_ERR_INVALID_ARG, "null argument");
+  if (!(tol >= 0.0) || iter_limit < 0) FAIL(SCYLLA_ERR_INVALID_ARG, "need tol >= 0 and iter_limit >= 0");
+  std::memset(out, 0, sizeof(*out));
+  out->status = SCYLLA_NOT_FOUND;
+  try {
+    return lp->repair(xhat, tol, iter_limit, x_out, out);
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return SCYLLA_ERR_OOM;
+  }
 }
 
 extern "C" int scylla_reset_state(scylla_lp* lp) {

@@ -95,11 +95,22 @@ struct scylla_lp {
   int* h_done = nullptr;             // pinned, two slots
   int64_t last_launches = 0;
 
+  // the continuous-repair copy of the original MIP (scylla_repair), built on first use
+  scylla_lp* repair_lp = nullptr;
+
   scylla::DevObjective objective_desc();
   void release();
   int order_after_user();
   int solve(double tol, int64_t iter_limit, int stall_checks, scylla_pdhg_result* out);
   int set_objective(const double* xhat, int32_t K);
+  int set_col_bounds(const double* l, const double* u);    // no validation
+  int set_row_bounds(const double* lo, const double* hi);  // no validation
+  int repair(const double* xhat, double tol, int64_t iter_limit, double* x_out, scylla_repair_result* out);
   int fetch_x(double* host, int count);
   int fetch_y(double* host, int count);
 };
+
+namespace scylla {
+// exact MIP-feasibility test of x (length n0) on the handle's original MIP (fixprop.cpp)
+bool check_feasible_host(const scylla_lp& lp, const double* x);
+}  // namespace scylla

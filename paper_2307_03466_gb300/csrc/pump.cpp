@@ -6,6 +6,8 @@
 //     if round(xbar) is MIP-feasible and xbar was within 1e-6 of it: return it
 //     xhat = fix-and-propagate(xbar)             (host, Section 2.3)
 //     if xhat is MIP-feasible: return it
+//     (optional) re-solve the continuous part with xhat's integers fixed; if
+//       that point is MIP-feasible: return it
 //     if xhat repeats an earlier rounding: perturb it (Section 2.3)
 //     objective update around xhat for round K   (GPU, Section 2.4)
 //     eps = max(beta eps, eps_floor); K = K + 1   (Section 2.2)
@@ -21,7 +23,6 @@
 #include "lp_handle.h"
 
 namespace scylla {
-bool check_feasible_host(const scylla_lp& lp, const double* x);
 int fix_and_propagate_host(const scylla_lp& lp, const double* xbar, double* xhat, double* dom_lo, double* dom_hi,
                            int32_t* fixed_cols, int64_t* n_fixed, uint8_t* ignored_rows);
 int64_t perturb_host(const scylla_lp& lp, double* x, const double* xbar, int kind, int64_t K, uint64_t seed);
@@ -76,7 +77,7 @@ extern "C" int scylla_run(scylla_lp* lp, double* x_out, scylla_run_result* out) 
     out->seconds_pdhg += res.seconds;
     rc = lp->fetch_x(xbar.data(), int(n));
     if (rc != SCYLLA_OK) break;
-    const auto tf = std::chrono::steady_clock::now();
+    auto tf = std::chrono::steady_clock::now();
     // Algorithm 1: is the PDHG point itself MIP-feasible (after rounding)?
     bool near = true;
     xr = xbar;
@@ -97,6 +98,23 @@ extern "C" int scylla_run(scylla_lp* lp, double* x_out, scylla_run_result* out) 
       finish(xhat, 2);
       out->rounds = K;
       break;
+    }
+    // continuous repair of the fix-and-propagate point (an extension; off by default)
+    if (p.repair_iters > 0) {
+      out->seconds_fixprop += std::chrono::duration<double>(std::chrono::steady_clock::now() - tf).count();
+      scylla_repair_result rr;
+      std::memset(&rr, 0, sizeof(rr));
+      rc = lp->repair(xhat.data(), p.repair_tol, std::min<int64_t>(p.repair_iters, p.total_iter_cap - total),
+                      xr.data(), &rr);
+      if (rc != SCYLLA_OK) break;
+      total += rr.iterations;
+      out->seconds_pdhg += rr.seconds;
+      if (rr.status == SCYLLA_FOUND) {
+        finish(xr, 3);
+        out->rounds = K;
+        break;
+      }
+      tf = std::chrono::steady_clock::now();  // the cycle handling's time follows
     }
     // cycle test on the integer part
     std::vector<double> key(int_cols.size());

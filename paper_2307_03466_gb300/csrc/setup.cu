@@ -43,6 +43,38 @@ __global__ void k_fill_f64(double* __restrict__ p, long long count, double v) {
     p[i] = v;
 }
 
+// new column bounds in the scaled space, with the rounding of the scaled vectors at
+// create: l~_j = l_j / C_j, u~_j = u_j / C_j
+__global__ void k_scale_col_bounds(long long n, const double* __restrict__ l, const double* __restrict__ u,
+                                   const double* __restrict__ C, double* __restrict__ l64, double* __restrict__ u64,
+                                   float* __restrict__ l32, float* __restrict__ u32) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    const double cj = C[j], lj = l[j] / cj, uj = u[j] / cj;
+    l64[j] = lj;
+    u64[j] = uj;
+    if (l32) {
+      l32[j] = float(lj);
+      u32[j] = float(uj);
+    }
+  }
+}
+
+// new row bounds in the scaled space, with the rounding of the scaled vectors at
+// create: lo~_i = lo_i R_i, hi~_i = hi_i R_i
+__global__ void k_scale_row_bounds(long long m, const double* __restrict__ lo, const double* __restrict__ hi,
+                                   const double* __restrict__ R, double* __restrict__ lo64,
+                                   double* __restrict__ hi64, float* __restrict__ lo32, float* __restrict__ hi32) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+    const double ri = R[i], a = lo[i] * ri, b = hi[i] * ri;
+    lo64[i] = a;
+    hi64[i] = b;
+    if (lo32) {
+      lo32[i] = float(a);
+      hi32[i] = float(b);
+    }
+  }
+}
+
 // kind_j = 1 for an integer column, 0 otherwise; aux_j = -1 (no auxiliary columns)
 __global__ void k_column_kinds(long long n, const uint8_t* __restrict__ is_int, int* __restrict__ kind,
                                int* __restrict__ aux_of) {
@@ -175,6 +207,20 @@ void side_factors(const DevSetup& s, double* r, double* c, double* r2, double* c
 
 cudaError_t fill_f64(double* p, long long count, double v, cudaStream_t st) {
   if (count > 0) k_fill_f64<<<setup_grid(count, kSetupThreads), kSetupThreads, 0, st>>>(p, count, v);
+  return cudaGetLastError();
+}
+
+cudaError_t scale_col_bounds(long long n, const double* l, const double* u, const double* C, double* l64,
+                             double* u64, float* l32, float* u32, cudaStream_t st) {
+  if (n > 0)
+    k_scale_col_bounds<<<setup_grid(n, kSetupThreads), kSetupThreads, 0, st>>>(n, l, u, C, l64, u64, l32, u32);
+  return cudaGetLastError();
+}
+
+cudaError_t scale_row_bounds(long long m, const double* lo, const double* hi, const double* R, double* lo64,
+                             double* hi64, float* lo32, float* hi32, cudaStream_t st) {
+  if (m > 0)
+    k_scale_row_bounds<<<setup_grid(m, kSetupThreads), kSetupThreads, 0, st>>>(m, lo, hi, R, lo64, hi64, lo32, hi32);
   return cudaGetLastError();
 }
 

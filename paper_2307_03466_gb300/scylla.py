@@ -46,7 +46,8 @@ class Params(C.Structure):
                 ("max_rounds", C.c_int64), ("iter_limit", C.c_int64), ("total_iter_cap", C.c_int64),
                 ("run_stall_checks", C.c_int32), ("trace_capacity", C.c_int32), ("seed", C.c_uint64),
                 ("time_limit_s", C.c_double), ("device_wait_limit_s", C.c_double), ("pdl", C.c_int32),
-                ("prefetch", C.c_int32), ("host_transpose", C.c_int32)]
+                ("prefetch", C.c_int32), ("host_transpose", C.c_int32),
+                ("repair_iters", C.c_int64), ("repair_tol", C.c_double), ("repair_rounds", C.c_int32)]
 
 
 class PdhgResult(C.Structure):
@@ -64,6 +65,15 @@ class RunResult(C.Structure):
     _fields_ = [("status", C.c_int32), ("found_by", C.c_int32), ("rounds", C.c_int64),
                 ("total_iterations", C.c_int64), ("perturbations", C.c_int64), ("objective", C.c_double),
                 ("seconds", C.c_double), ("seconds_pdhg", C.c_double), ("seconds_fixprop", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class RepairResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("pdhg_status", C.c_int32), ("iterations", C.c_int64),
+                ("rounds", C.c_int32), ("shifted_rows", C.c_int32),
+                ("rel_kkt", C.c_double), ("objective", C.c_double), ("seconds", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -92,6 +102,9 @@ _SIGS = {
     "scylla_fix_and_propagate": (C.c_int, [_P, _D, _D, _D, _D, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
                                            C.POINTER(C.c_uint8)]),
     "scylla_check_feasible": (C.c_int, [_P, _D, C.POINTER(C.c_int32)]),
+    "scylla_set_col_bounds": (C.c_int, [_P, _D, _D]),
+    "scylla_set_row_bounds": (C.c_int, [_P, _D, _D]),
+    "scylla_repair": (C.c_int, [_P, _D, C.c_double, C.c_int64, _D, C.POINTER(RepairResult)]),
     "scylla_perturb": (C.c_int, [_P, _D, _D, C.c_int32, C.c_int64, C.c_uint64, C.POINTER(C.c_int64)]),
     "scylla_get_trace": (C.c_int, [_P, _D, C.POINTER(C.c_int64), _D, C.POINTER(C.c_int64)]),
     "scylla_reset_state": (C.c_int, [_P]),
@@ -307,6 +320,27 @@ class LP:
 
     def reset_state(self):
         _check(lib().scylla_reset_state(self.h))
+
+    def set_col_bounds(self, col_lo, col_hi):
+        """New bounds of the original columns (scylla_set_col_bounds)."""
+        lo = _f64(col_lo, self.n)
+        hi = _f64(col_hi, self.n)
+        _check(lib().scylla_set_col_bounds(self.h, _dp(lo), _dp(hi)))
+
+    def set_row_bounds(self, row_lo, row_hi):
+        """New bounds of the original rows (scylla_set_row_bounds)."""
+        lo = _f64(row_lo, self.m)
+        hi = _f64(row_hi, self.m)
+        _check(lib().scylla_set_row_bounds(self.h, _dp(lo) if self.m else None, _dp(hi) if self.m else None))
+
+    def repair(self, xhat, tol: float, iter_limit: int):
+        """Continuous repair of xhat's integer assignment (scylla_repair): returns
+        (RepairResult, x)."""
+        xh = _f64(xhat, self.n)
+        x = np.empty(self.n)
+        r = RepairResult()
+        _check(lib().scylla_repair(self.h, _dp(xh), float(tol), int(iter_limit), _dp(x), C.byref(r)))
+        return r, x
 
     def time_kernels(self, attempts: int):
         """Mean device ms of (primal, dual, check-cols, check-rows) launches."""

@@ -47,10 +47,12 @@ def test_struct_layout_matches_c_compiler(L):
 #include <stddef.h>
 #include "scylla.h"
 int main(void) {
-  printf("%zu %zu %zu %zu\n", sizeof(scylla_csr), sizeof(scylla_params), sizeof(scylla_pdhg_result),
-         sizeof(scylla_run_result));
-  printf("%zu %zu %zu\n", offsetof(scylla_params, fixed_step_factor), offsetof(scylla_params, seed),
-         offsetof(scylla_params, time_limit_s));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(scylla_csr), sizeof(scylla_params), sizeof(scylla_pdhg_result),
+         sizeof(scylla_run_result), sizeof(scylla_repair_result));
+  printf("%zu %zu %zu %zu %zu\n", offsetof(scylla_params, fixed_step_factor), offsetof(scylla_params, seed),
+         offsetof(scylla_params, time_limit_s), offsetof(scylla_params, repair_iters),
+         offsetof(scylla_params, repair_tol));
+  printf("%zu %zu\n", offsetof(scylla_params, repair_rounds), offsetof(scylla_repair_result, rel_kkt));
   return 0;
 }
 '''
@@ -61,8 +63,11 @@ int main(void) {
         subprocess.run(["gcc", "-I", os.path.dirname(HEADER), p, "-o", exe], check=True)
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     sizes = [int(v) for v in out]
-    assert sizes[:4] == [C.sizeof(S.Csr), C.sizeof(S.Params), C.sizeof(S.PdhgResult), C.sizeof(S.RunResult)]
-    assert sizes[4:] == [S.Params.fixed_step_factor.offset, S.Params.seed.offset, S.Params.time_limit_s.offset]
+    assert sizes[:5] == [C.sizeof(S.Csr), C.sizeof(S.Params), C.sizeof(S.PdhgResult), C.sizeof(S.RunResult),
+                         C.sizeof(S.RepairResult)]
+    assert sizes[5:] == [S.Params.fixed_step_factor.offset, S.Params.seed.offset, S.Params.time_limit_s.offset,
+                         S.Params.repair_iters.offset, S.Params.repair_tol.offset,
+                         S.Params.repair_rounds.offset, S.RepairResult.rel_kkt.offset]
 
 
 def test_default_params_are_the_papers(L):
@@ -70,6 +75,8 @@ def test_default_params_are_the_papers(L):
     # Algorithm 1 (alpha) and Section 2.2 (eps1, beta, floor)
     assert (p.alpha, p.eps1, p.beta, p.eps_floor) == (0.9, 0.01, 0.98, 1e-8)
     assert p.n_check == 64 and p.precision == S.PREC_FP64
+    # the continuous repair is not part of Algorithm 1: off unless asked for
+    assert p.repair_iters == 0 and p.repair_tol == 1e-7 and p.repair_rounds == 8
 
 
 def _create(rowptr, cols, vals, m, n, lo=None, hi=None, l=None, u=None, c=None, ii=None):
@@ -102,6 +109,10 @@ def test_null_handle_calls_fail_cleanly(L):
     r = S.PdhgResult()
     assert L.scylla_pdhg_solve(None, 1e-4, 10, C.byref(r)) == S.ERR_INVALID_ARG
     assert L.scylla_set_objective(None, None, 1) == S.ERR_INVALID_ARG
+    assert L.scylla_set_col_bounds(None, None, None) == S.ERR_INVALID_ARG
+    assert L.scylla_set_row_bounds(None, None, None) == S.ERR_INVALID_ARG
+    rr = S.RepairResult()
+    assert L.scylla_repair(None, None, 1e-6, 10, None, C.byref(rr)) == S.ERR_INVALID_ARG
     L.scylla_lp_destroy(None)
     assert b"null" in L.scylla_last_error()
 

@@ -124,3 +124,23 @@ def test_mcf_mixed_one_attempt_sampled(mcf, prefetch):
     assert rel_err(y1[rows], ys_r * o.R[rows]) <= MIXED_TOL
     # and every entry, against the oracle's whole attempt
     assert rel_err(x1, o.primal(xs_all)) <= MIXED_TOL and rel_err(y1, o.dual(ys_all)) <= MIXED_TOL
+
+
+def test_packcover_repair_of_a_feasible_fixing(packcover):
+    """Continuous repair at the bench size: the integers fixed at those of the
+    generator's interior point x0 (so the fixed LP is feasible and x0 is one of its
+    points), solves to rel-KKT 1e-7 with the shift rounds (one solve leaves single
+    rows outside the check's tolerance at this size).  The repaired point passes the
+    oracle's exact feasibility test, keeps the fixed integers, and its objective is
+    no worse than x0's."""
+    from oracle import pump as P
+    g, _ = pair(packcover, precision=1)
+    x0 = packcover.meta["x0"]
+    r, x = g.repair(x0, 1e-7, 100000)
+    assert r.status == P.FOUND and r.rel_kkt <= 1e-7
+    isi = packcover.is_int == 1
+    assert np.array_equal(x[isi], x0[isi])
+    assert P.check_feasible(packcover.rowptr, packcover.cols, packcover.vals, packcover.lo, packcover.hi,
+                            packcover.l, packcover.u, packcover.is_int, x)
+    assert float(packcover.c @ x) <= float(packcover.c @ x0) + 1e-6 * abs(float(packcover.c @ x0))
+    g.close()
