@@ -20,6 +20,10 @@ Readings of what the paper leaves open:
   follow the original rows, both in ascending j; before the first update the
   auxiliary rows are free (lo = -inf) and cost 0.  Constants of Delta go into the
   objective offset.
+* l2 distance (``distance = 2``; the paper's conclusion proposes it for avoiding the
+  auxiliary variables): ``alpha^K s c^T x + (1 - alpha^K) 1/2 sum_I (x_j - xhat_j)^2``
+  on every integer column, solved as a diagonal-Hessian PDHG (``OracleLP``'s
+  quadratic mode); no auxiliary columns.
 * MIP-feasible xbar (Algorithm 1): round the integer entries to nearest; accept
   when every one was within 1e-6 and the rounded point passes ``check_feasible``.
 * Cycling (Section 2.3, following Fischetti-Glover-Lodi 2005): a short cycle
@@ -161,6 +165,34 @@ def objective_update(c, is_int, l, u, xhat, K, gen_int, alpha=0.9):
         aux_lo[2 * q] = -xhat[j]
         aux_lo[2 * q + 1] = xhat[j]
     return chat, aux_lo, offset
+
+
+def objective_update_l2(c, is_int, xhat, K, alpha=0.9):
+    """The l2-distance objective of round K >= 1 (the conclusion's alternative to the
+    l1 distance, which needs no auxiliary columns):
+        alpha^K s c^T x + (1 - alpha^K) 1/2 sum_{j in I} (x_j - xhat_j)^2
+      = c_hat^T x + 1/2 x^T diag(q) x + offset,
+    c_hat_j = alpha^K s c_j - (1 - alpha^K) xhat_j and q_j = 1 - alpha^K on I,
+    c_hat_j = alpha^K s c_j and q_j = 0 elsewhere, offset = (1 - alpha^K)/2 sum_I xhat_j^2,
+    with s = sqrt(|I|) / ||c||_2 (0 when c = 0) as in the l1 update."""
+    n = len(c)
+    aK = alpha ** K
+    om = 1.0 - aK
+    nI = int(sum(1 for j in range(n) if is_int[j]))
+    cn = math.sqrt(sum(float(v) * float(v) for v in c))
+    s = math.sqrt(nI) / cn if cn > 0 else 0.0
+    t = aK * s
+    chat = np.zeros(n)
+    q = np.zeros(n)
+    offset = 0.0
+    for j in range(n):
+        if is_int[j]:
+            chat[j] = t * c[j] - om * xhat[j]
+            q[j] = om
+            offset += 0.5 * om * xhat[j] * xhat[j]
+        else:
+            chat[j] = t * c[j]
+    return chat, q, offset
 
 
 def _flip(v, xb, lj, uj):
@@ -311,6 +343,7 @@ class PumpParams:
     repair_iters: int = 0  # attempt limit of each continuous repair; 0 = none
     repair_tol: float = 1e-7
     repair_rounds: int = 8
+    distance: int = 1  # 1: l1 distance (Algorithm 1, auxiliary columns on general integers); 2: l2
     pdhg: PdhgParams = field(default_factory=PdhgParams)
 
 
@@ -329,7 +362,12 @@ def pump(inst, params: PumpParams | None = None) -> PumpResult:
     c, lo, hi, l, u, is_int, m, n)."""
     pp = params or PumpParams()
     A = sp.csr_matrix((inst.vals, inst.cols, inst.rowptr), shape=(inst.m, inst.n))
-    aug = augment(A, inst.c, inst.lo, inst.hi, inst.l, inst.u, inst.is_int)
+    l2 = pp.distance == 2
+    if l2:  # no auxiliary columns: the LP as given
+        aug = Augmented(A, np.asarray(inst.c, float), np.asarray(inst.lo, float), np.asarray(inst.hi, float),
+                        np.asarray(inst.l, float), np.asarray(inst.u, float), inst.n, inst.m, [])
+    else:
+        aug = augment(A, inst.c, inst.lo, inst.hi, inst.l, inst.u, inst.is_int)
     int_cols = [j for j in range(inst.n) if inst.is_int[j]]
     pd = PdhgParams(**{**pp.pdhg.__dict__, "stall_checks": pp.stall_checks})
     lp = OracleLP(aug.A, aug.c, aug.lo, aug.hi, aug.l, aug.u, int_cols=int_cols, params=pd)
@@ -366,6 +404,14 @@ def pump(inst, params: PumpParams | None = None) -> PumpResult:
                 return PumpResult(FOUND, xrep, K, total, "repair", log)
         xhat, kind = perturb(xhat, xbar, hist, K, pp.seed, int_cols, inst.l, inst.u)
         hist.append(tuple(float(xhat[j]) for j in int_cols))
+        if l2:
+            chat, q, offset = objective_update_l2(inst.c, inst.is_int, xhat, K, pp.alpha)
+            lp.set_objective_vector(chat, offset)
+            lp.set_quadratic(q)
+            log.append((K, res.status, res.iterations, res.rel_kkt, kind))
+            eps = max(pp.beta * eps, pp.eps_floor)
+            K += 1
+            continue
         chat, aux_lo, offset = objective_update(inst.c, inst.is_int, inst.l, inst.u, xhat, K,
                                                 aug.gen_int, pp.alpha)
         lp.set_objective_vector(chat, offset)
