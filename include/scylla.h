@@ -118,6 +118,9 @@ typedef struct {
   int64_t repair_iters;         /* attempt limit of each repair (all its rounds); 0 = no repair (0) */
   double repair_tol;            /* rel-KKT target of each repair solve (1e-7) */
   int32_t repair_rounds;        /* solves of one repair, with the violated rows shifted in between (8) */
+  int32_t distance;             /* distance of the objective update: 1 = l1 (Algorithm 1; auxiliary columns
+                                   for general integers), 2 = l2 (the conclusion's alternative: a diagonal
+                                   quadratic objective, no auxiliary columns) (1) */
 } scylla_params;
 
 typedef struct {
@@ -193,6 +196,23 @@ int scylla_pdhg_solve(scylla_lp* lp, double tol, int64_t iter_limit, scylla_pdhg
  * integral and inside their bounds).  Keeps x, y, eta, omega (warm start).
  * Errors: INVALID_ARG, CUDA. */
 int scylla_set_objective(scylla_lp* lp, const double* xhat, int32_t K);
+/* (With p.distance = 2 the update is the l2 one instead: c_hat_j = alpha^K s c_j -
+ * (1 - alpha^K) xhat_j and q_j = 1 - alpha^K on the integer columns, c_hat_j =
+ * alpha^K s c_j and q_j = 0 elsewhere, offset (1 - alpha^K)/2 sum xhat_j^2 over the
+ * integer columns: alpha^K s c^T x + (1 - alpha^K)/2 ||x_I - xhat_I||^2 as a
+ * diagonal quadratic objective, see scylla_set_qp_objective.) */
+
+/* Diagonal quadratic objective on the original columns (the conclusion's remark that
+ * PDHG, as in PDLP, takes objectives with a diagonal Hessian):
+ *     min c^T x + 1/2 x^T diag(q) x + offset   over the same constraints.
+ * c, q: host, length n (q_j >= 0, finite).  The primal step becomes the closed-form
+ * prox x' = proj_[l,u]((x + tau (A^T y - c)) / (1 + tau q)) in the scaled space, and
+ * the KKT error uses the reduced cost c + q x - A^T y and the objectives
+ * +-1/2 x^T Q x; an all-zero q is the LP exactly.  Keeps the iterate (warm start).
+ * Auxiliary columns keep their cost and get q = 0.  The batched and fan-out solves
+ * take LPs only.  Errors: INVALID_ARG (null, non-finite c or offset, q < 0 or
+ * non-finite), CUDA. */
+int scylla_set_qp_objective(scylla_lp* lp, const double* c, const double* q, double offset);
 
 /* Current objective c_hat (host, length n_total) and offset, unscaled. */
 int scylla_get_objective(const scylla_lp* lp, double* c_hat, double* offset);

@@ -280,6 +280,10 @@ extern "C" int scylla_fanout_create(scylla_lp* lp, int32_t K, const double* targ
     set_error("need a handle, targets, 1 <= K <= 64 and round >= 1");
     return SCYLLA_ERR_INVALID_ARG;
   }
+  if (lp->qp_active || lp->p.distance == 2) {
+    set_error("the fan-out takes LP objectives (no quadratic objective, distance = 1)");
+    return SCYLLA_ERR_UNSUPPORTED;
+  }
   if (lp->n_aux != 0) {
     set_error("the fan-out needs an LP without auxiliary distance columns (create it with aux_general_integers = 0)");
     return SCYLLA_ERR_UNSUPPORTED;

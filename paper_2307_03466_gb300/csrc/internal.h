@@ -98,6 +98,10 @@ struct DevLP {
   const double *c64, *l64, *u64, *lo64, *hi64, *R, *C;
   const double *invR, *invC;  // 1 / R, 1 / C (the checks multiply instead of dividing)
   const unsigned char* int_mask;
+  // diagonal Hessian of a quadratic objective, scaled (q~ = q C^2): bulk type for the
+  // primal step, FP64 for the checks; both null for an LP
+  const T* q;
+  const double* q64;
   T* X[3];
   T* Y[3];
   T* AX[3];
@@ -204,6 +208,11 @@ cudaError_t fill_f64(double* p, long long count, double v, cudaStream_t st);
 // l64 = l / C, u64 = u / C (and the FP32 shadows when given) over n columns
 cudaError_t scale_col_bounds(long long n, const double* l, const double* u, const double* C, double* l64,
                              double* u64, float* l32, float* u32, cudaStream_t st);
+// c64 = c C and q64 = q C^2 (and the FP32 shadows when given) over n columns
+cudaError_t scale_objective(long long n, const double* c, const double* q, const double* C, double* c64,
+                            float* c32, double* q64, float* q32, cudaStream_t st);
+// q64 = q C^2 (and the FP32 shadow when given) over n columns
+cudaError_t scale_hessian(long long n, const double* q, const double* C, double* q64, float* q32, cudaStream_t st);
 // lo64 = lo R, hi64 = hi R (and the FP32 shadows when given) over m rows
 cudaError_t scale_row_bounds(long long m, const double* lo, const double* hi, const double* R, double* lo64,
                              double* hi64, float* lo32, float* hi32, cudaStream_t st);
@@ -234,6 +243,10 @@ cudaError_t launch_scale_vectors(const DevVecs& v, cudaStream_t st);
 // Objective update of round K (Section 2.4) on the device.
 struct DevObjective {
   int n_orig, m_orig, n, m;
+  int l2;                // l2 distance: q_j = 1 - alpha^K and c_hat_j -= (1 - alpha^K) xhat_j on I
+  double* q_un;          // unscaled Hessian diagonal (n), written in l2 mode
+  double* q64;           // scaled q C^2 (n), written in l2 mode
+  float* q32;            // its FP32 shadow (mixed precision), or null
   const double* c_orig;  // original c (n_orig)
   const double* l_orig;
   const double* u_orig;

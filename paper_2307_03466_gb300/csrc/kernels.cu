@@ -431,6 +431,7 @@ struct PrimalEpi {
   const T* __restrict__ cc;
   const T* __restrict__ ll;
   const T* __restrict__ uu;
+  const T* __restrict__ qq;  // scaled Hessian diagonal of a quadratic objective, or null
   T tau, w, w1;
   bool do_avg, copy_lr, store_aty, use_cached;
   A acc;
@@ -449,7 +450,10 @@ struct PrimalEpi {
     if (store_aty) aty[j] = aty_j;
     if (do_avg) xa[j] = blend(p.xa, p.x, w1, w);
     if (copy_lr) xlr[j] = p.x;
-    const T v = clampv<T>(p.x + tau * (aty_j - p.c), p.l, p.u);
+    T z = p.x + tau * (aty_j - p.c);
+    // quadratic objective: the prox of tau/2 q x^2 scales the step by 1 / (1 + tau q)
+    if (qq) z = z / (T(1) + tau * qq[j]);
+    const T v = clampv<T>(z, p.l, p.u);
     xn[j] = v;
     const A dx = A(v) - A(p.x);
     acc += dx * dx;
@@ -467,6 +471,7 @@ __device__ __forceinline__ void setup_primal(PrimalEpi<T>& epi, const DevLP<T>& 
   epi.cc = d.c;
   epi.ll = d.l;
   epi.uu = d.u;
+  epi.qq = d.q;
   epi.tau = v.tau;
   epi.w = v.w;
   epi.w1 = v.w1;
@@ -972,7 +977,9 @@ __device__ __forceinline__ void check_gather(const int2* tiles, int ntiles, cons
   spmv_tiles<2, false, double, double>(tiles, ntiles, rowptr, cols, vals, gat64, epi, smw, NoPro());
 }
 
-template <typename T>
+// QP: 0 an LP (no Hessian terms compiled in), 1 a quadratic objective (qq set), 2
+// either, decided per column from qq (the persistent kernel, to keep one body)
+template <typename T, int QP = 0>
 struct CheckColsEpi {
   struct Pre {};
   const T* __restrict__ xc;
@@ -981,6 +988,7 @@ struct CheckColsEpi {
   T* __restrict__ aty_a;
   const T* __restrict__ xlr;
   const double *C, *invC, *c64, *l64, *u64;
+  const double* qq;  // scaled Hessian diagonal of a quadratic objective, or null
   const unsigned char* int_mask;
   T w, w1;
   bool do_avg;
@@ -998,9 +1006,12 @@ struct CheckColsEpi {
     aty_a[j] = T(s[1]);
     const double Cj = C[j], iCj = invC[j], cj = c64[j], lj = l64[j], uj = u64[j], xl = to_f64(xlr[j]);
     const double xs[2] = {to_f64(x), to_f64(xav)};
+    const bool has_q = QP == 1 || (QP == 2 && qq != nullptr);
+    const double qj = has_q ? qq[j] : 0.0;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      const double r = cj - s[q];
+      // quadratic objective: reduced cost c + q x - A^T y; +-1/2 q x^2 in the objectives
+      const double r = has_q ? (cj + qj * xs[q]) - s[q] : cj - s[q];
       const double lam = rc_proj(r, lj, uj);
       const double rd = r - lam;
       acc[5 * q + 0] += rd * rd;
@@ -1008,6 +1019,11 @@ struct CheckColsEpi {
       acc[5 * q + 1] += rdu * rdu;
       acc[5 * q + 2] += cj * xs[q];
       acc[5 * q + 3] += (lam > 0.0 ? lj * lam : 0.0) - (lam < 0.0 ? uj * (-lam) : 0.0);
+      if (has_q) {
+        const double hq = 0.5 * (qj * xs[q]) * xs[q];
+        acc[5 * q + 2] += hq;
+        acc[5 * q + 3] -= hq;
+      }
       const double dd = xs[q] - xl;
       acc[5 * q + 4] += dd * dd;
     }
@@ -1018,14 +1034,14 @@ struct CheckColsEpi {
 // FP64 column half of a check (Section 2.2): A^T y of the current and of the
 // averaged dual from FP64 values, reduced costs, dual residuals, objectives, the
 // rounding hash; block partials to part, hash into *hash
-template <typename T, bool Coh>
+template <typename T, bool Coh, int QP = 0>
 __device__ __forceinline__ void check_cols_phase(const DevLP<T>& d, const SlotView<T>& v, double* sm, double* part,
                                                  unsigned long long* hash) {
   const T w = v.w, w1 = v.w1;
   const bool do_avg = v.do_avg;
   const T* __restrict__ yc = d.Y[v.cur];
   const T* __restrict__ ya = d.Y[v.avg];
-  CheckColsEpi<T> epi;
+  CheckColsEpi<T, QP> epi;
   epi.xc = d.X[v.cur];
   epi.xa = d.X[v.avg];
   epi.aty_c = d.ATY[v.ia_cur];
@@ -1036,6 +1052,7 @@ __device__ __forceinline__ void check_cols_phase(const DevLP<T>& d, const SlotVi
   epi.c64 = d.c64;
   epi.l64 = d.l64;
   epi.u64 = d.u64;
+  epi.qq = d.q64;
   epi.int_mask = d.int_mask;
   epi.w = w;
   epi.w1 = w1;
@@ -1123,13 +1140,15 @@ __device__ __forceinline__ void check_rows_phase(const DevLP<T>& d, const SlotVi
   block_store_partials<kNC2>(epi.acc, part);
 }
 
-template <typename T>
+// QP = 1: the objective has a Hessian (d.q64 set); the LP variant (0) carries none of
+// its terms
+template <typename T, int QP = 0>
 __global__ void __launch_bounds__(kThreads) k_check_cols(DevLP<T> d) {
   Control* ctl = d.ctl;
   pdl_enter();
   if (ctl->done) return;
   __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];
-  check_cols_phase<T, false>(d, make_view<T>(ctl), sm, d.part_c1, &ctl->hash_accum);
+  check_cols_phase<T, false, QP>(d, make_view<T>(ctl), sm, d.part_c1, &ctl->hash_accum);
 }
 
 template <typename T>
@@ -1242,7 +1261,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_solve_persistent(DevLP<T> d, G
   while (ok) {
     if (do_check) {
       const SlotView<T> v = make_view<T>(&sc);
-      check_cols_phase<T, true>(d, v, psm, part_c1, &hash[hslot]);
+      check_cols_phase<T, true, 2>(d, v, psm, part_c1, &hash[hslot]);
       ok = grid_sync(bar, limit_ns);
       if (!ok) break;
       check_rows_phase<T, true>(d, v, psm, part_c2);
@@ -1436,12 +1455,28 @@ __device__ __forceinline__ double row_bound2(double lo, double hi) {
 // (1 - alpha^K) with auxiliary rows d - x >= -xhat_j, d + x >= xhat_j.
 // The squared row-bound magnitudes are summed over the original rows here and, for
 // the auxiliary rows (lo = -xhat_j, xhat_j; hi = +inf), where they are written.
+// l2 mode (o.l2): c_hat_j = t c_j - om xhat_j, q_j = om on integer columns, c_hat_j =
+// t c_j, q_j = 0 elsewhere; offset terms om/2 xhat_j^2 (no auxiliary columns).
 __global__ void k_objective_cols(DevObjective o, double t, double om) {
   double off = 0.0, c2 = 0.0, b2 = 0.0;
   const int stride = gridDim.x * blockDim.x;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < o.n; j += stride) {
     double ch;
-    if (j < o.n_orig) {
+    if (o.l2) {
+      double qv = 0.0;
+      if (j < o.n_orig && o.kind[j] >= 1) {
+        const double xh = o.xhat[j];
+        ch = __dadd_rn(__dmul_rn(t, o.c_orig[j]), -__dmul_rn(om, xh));
+        qv = om;
+        off += 0.5 * om * xh * xh;
+      } else {
+        ch = j < o.n_orig ? __dmul_rn(t, o.c_orig[j]) : 0.0;
+      }
+      const double Cj = o.C[j], qs = (qv * Cj) * Cj;
+      o.q_un[j] = qv;
+      o.q64[j] = qs;
+      if (o.q32) o.q32[j] = float(qs);
+    } else if (j < o.n_orig) {
       double g = 0.0;
       const int kd = o.kind[j];
       if (kd == 1) {
@@ -1619,6 +1654,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_bprimal(DevBa
   epi.cc = d.c;
   epi.ll = d.l;
   epi.uu = d.u;
+  epi.qq = nullptr;  // the batched solve takes LPs only
   epi.acc = 0;
   auto gat = [&](int i, T(&g)[1]) { g[0] = epi.cached ? T(0) : __ldg(epi.ysrc + i); };
   spmv_tiles_batch<1, T, T>(d.t_tiles, B.t_tile_lp, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals, gat, epi,
@@ -1750,6 +1786,7 @@ __global__ void __launch_bounds__(kThreads) k_bcheck_cols(DevBatch<T> B) {
   epi.c64 = d.c64;
   epi.l64 = d.l64;
   epi.u64 = d.u64;
+  epi.qq = d.q64;
   epi.int_mask = d.int_mask;
 #pragma unroll
   for (int k = 0; k < kNC1; ++k) epi.acc[k] = 0.0;
@@ -1964,7 +2001,7 @@ static cudaError_t launch_step_kernel(void (*kernel)(DevLP<T>), int grid, const 
 
 template <typename T>
 cudaError_t launch_check(const DevLP<T>& d, cudaStream_t st) {
-  cudaError_t e = launch_step_kernel<T>(k_check_cols<T>, d.grid_c1, d, st);
+  cudaError_t e = launch_step_kernel<T>(d.q64 ? k_check_cols<T, 1> : k_check_cols<T, 0>, d.grid_c1, d, st);
   if (e == cudaSuccess) e = launch_step_kernel<T>(k_check_rows<T>, d.grid_c2, d, st);
   return e;
 }
@@ -1996,7 +2033,7 @@ cudaError_t launch_slot(const DevLP<T>& d, cudaStream_t st) {
 }
 template <typename T>
 cudaError_t launch_check_cols(const DevLP<T>& d, cudaStream_t st) {
-  return launch_step_kernel<T>(k_check_cols<T>, d.grid_c1, d, st);
+  return launch_step_kernel<T>(d.q64 ? k_check_cols<T, 1> : k_check_cols<T, 0>, d.grid_c1, d, st);
 }
 template <typename T>
 cudaError_t launch_check_rows(const DevLP<T>& d, cudaStream_t st) {
@@ -2065,7 +2102,7 @@ int occupancy_grid(int side, int form, int work_tiles) {
   int per_sm = 1;
   int smem = 0;
   void (*k)(DevLP<T>) = nullptr;
-  if (side == 2) k = k_check_cols<T>;
+  if (side == 2) k = k_check_cols<T, 0>;
   else if (side == 3) k = k_check_rows<T>;
   else if (form == kFormStaged) {
     k = side == 0 ? k_primal_st<T> : k_dual_st<T>;

@@ -84,6 +84,7 @@ extern "C" void scylla_default_params(scylla_params* p) {
   p->repair_iters = 0;
   p->repair_tol = 1e-7;
   p->repair_rounds = 8;
+  p->distance = 1;
 }
 
 extern "C" const char* scylla_last_error(void) { return get_error(); }
@@ -304,6 +305,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   if (lp->p.host_transpose < 0 || lp->p.host_transpose > 1) FAIL(SCYLLA_ERR_INVALID_ARG, "host_transpose must be 0 or 1");
   if (lp->p.repair_iters < 0 || !(lp->p.repair_tol >= 0.0) || lp->p.repair_rounds < 1)
     FAIL(SCYLLA_ERR_INVALID_ARG, "need repair_iters >= 0, repair_tol >= 0 and repair_rounds >= 1");
+  if (lp->p.distance != 1 && lp->p.distance != 2) FAIL(SCYLLA_ERR_INVALID_ARG, "distance must be 1 or 2");
   if (lp->p.precision != SCYLLA_PREC_FP64 && lp->p.precision != SCYLLA_PREC_MIXED)
     FAIL(SCYLLA_ERR_INVALID_ARG, "unknown precision");
   CK(cudaGetDevice(&lp->device));
@@ -321,7 +323,8 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   lp->m0 = m0;
   lp->n0 = n0;
   lp->nnz0 = nnz0;
-  const bool aux_on = lp->p.aux_general_integers != 0;
+  // the l2 distance needs no auxiliary columns
+  const bool aux_on = lp->p.aux_general_integers != 0 && lp->p.distance == 1;
   {
     const int chunks = int(std::max<int64_t>(1, std::min<int64_t>(64, n0 / 65536)));
     std::vector<double> c2(size_t(chunks), 0.0);
@@ -499,6 +502,9 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     lp->C = ar.take<double>(n);
     lp->invR = ar.take<double>(m);
     lp->invC = ar.take<double>(n);
+    lp->q_un = ar.take<double>(n);
+    lp->q64 = ar.take<double>(n);
+    lp->q32 = mixed ? ar.take<float>(n) : nullptr;
     lp->R2 = ar.take<double>(std::max(m, n));
     lp->C2 = ar.take<double>(std::max(m, n));
     lp->int_mask = ar.take<uint8_t>(n);
@@ -730,7 +736,30 @@ DevObjective scylla_lp::objective_desc() {
   o.c_orig = c_orig; o.l_orig = l_orig; o.u_orig = u_orig; o.kind = kind_d; o.aux_of = aux_of_d; o.xhat = xhat_d;
   o.chat = c_un; o.lo_unscaled = lo_un; o.hi_unscaled = hi_un; o.R = R; o.C = C;
   o.c64 = c64; o.lo64 = lo64; o.c32 = c32; o.lo32 = lo32; o.red = red; o.red_blocks = red_blocks; o.ctl = ctl;
+  o.l2 = p.distance == 2 ? 1 : 0;
+  o.q_un = q_un; o.q64 = q64; o.q32 = q32;
   return o;
+}
+
+void scylla_lp::drop_graphs() {
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  exec = nullptr;
+  graph = nullptr;
+  if (chunk_exec) cudaGraphExecDestroy(chunk_exec);
+  if (chunk_graph) cudaGraphDestroy(chunk_graph);
+  chunk_exec = nullptr;
+  chunk_graph = nullptr;
+}
+
+void scylla_lp::set_qp_active(bool on) {
+  if (on == qp_active) return;
+  qp_active = on;
+  d64.q = on ? q64 : nullptr;
+  d64.q64 = on ? q64 : nullptr;
+  d32.q = on ? q32 : nullptr;
+  d32.q64 = on ? q64 : nullptr;
+  drop_graphs();  // they captured the kernels' parameters
 }
 
 void scylla_lp::release() {
@@ -740,14 +769,7 @@ void scylla_lp::release() {
     delete repair_lp;
     repair_lp = nullptr;
   }
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
-  exec = nullptr;
-  graph = nullptr;
-  if (chunk_exec) cudaGraphExecDestroy(chunk_exec);
-  if (chunk_graph) cudaGraphDestroy(chunk_graph);
-  chunk_exec = nullptr;
-  chunk_graph = nullptr;
+  drop_graphs();
   for (auto& e : ev_chunk) {
     if (e) cudaEventDestroy(e);
     e = nullptr;
@@ -989,6 +1011,30 @@ int scylla_lp::set_objective(const double* xhat, int32_t K) {
   const double s = c0norm > 0.0 ? std::sqrt(double(n_int)) / c0norm : 0.0;
   CK(launch_objective_update(objective_desc(), aK * s, 1.0 - aK, st));
   CK(cudaStreamSynchronize(st));
+  if (p.distance == 2) set_qp_active(true);  // the l2 update writes a Hessian
+  return SCYLLA_OK;
+}
+
+extern "C" int scylla_set_qp_objective(scylla_lp* lp, const double* c, const double* q, double offset) {
+  if (!lp || !c || !q) FAIL(SCYLLA_ERR_INVALID_ARG, "null argument");
+  if (!std::isfinite(offset)) FAIL(SCYLLA_ERR_INVALID_ARG, "offset not finite");
+  bool any_q = false;
+  for (int64_t j = 0; j < lp->n0; ++j) {
+    if (!std::isfinite(c[j])) FAIL(SCYLLA_ERR_INVALID_ARG, "non-finite objective at column " + std::to_string(j));
+    if (!(std::isfinite(q[j]) && q[j] >= 0.0))
+      FAIL(SCYLLA_ERR_INVALID_ARG, "Hessian diagonal must be finite and >= 0 (column " + std::to_string(j) + ")");
+    any_q = any_q || q[j] > 0.0;
+  }
+  int rc = lp->order_after_user();
+  if (rc != SCYLLA_OK) return rc;
+  cudaStream_t st = lp->st;
+  CK(cudaMemcpyAsync(lp->c_un, c, sizeof(double) * lp->n0, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(lp->q_un, 0, sizeof(double) * lp->n, st));
+  CK(cudaMemcpyAsync(lp->q_un, q, sizeof(double) * lp->n0, cudaMemcpyHostToDevice, st));
+  CK(scale_objective(lp->n, lp->c_un, lp->q_un, lp->C, lp->c64, lp->c32, lp->q64, lp->q32, st));
+  CK(launch_objective_norms(lp->objective_desc(), offset, st));
+  CK(cudaStreamSynchronize(st));
+  lp->set_qp_active(any_q);
   return SCYLLA_OK;
 }
 

@@ -67,6 +67,11 @@ struct scylla_lp {
   double *R = nullptr, *C = nullptr, *R2 = nullptr, *C2 = nullptr;
   double* a_vals0 = nullptr;  // unscaled values of A (the original rows first)
   double *invR = nullptr, *invC = nullptr;
+  // diagonal Hessian of a quadratic objective (n): unscaled, scaled, FP32 shadow;
+  // qp_active when the kernels take it (see set_qp_active)
+  double *q_un = nullptr, *q64 = nullptr;
+  float* q32 = nullptr;
+  bool qp_active = false;
   uint8_t* int_mask = nullptr;
   double *c_orig = nullptr, *l_orig = nullptr, *u_orig = nullptr, *xhat_d = nullptr;
   int *kind_d = nullptr, *aux_of_d = nullptr;
@@ -103,6 +108,8 @@ struct scylla_lp {
   int order_after_user();
   int solve(double tol, int64_t iter_limit, int stall_checks, scylla_pdhg_result* out);
   int set_objective(const double* xhat, int32_t K);
+  void set_qp_active(bool on);  // point the kernels at the Hessian (or not); drops the captured graphs
+  void drop_graphs();
   int set_col_bounds(const double* l, const double* u);    // no validation
   int set_row_bounds(const double* lo, const double* hi);  // no validation
   int repair(const double* xhat, double tol, int64_t iter_limit, double* x_out, scylla_repair_result* out);

@@ -75,6 +75,29 @@ __global__ void k_scale_row_bounds(long long m, const double* __restrict__ lo, c
   }
 }
 
+// Hessian diagonal in the scaled space: q~_j = (q_j C_j) C_j
+__global__ void k_scale_hessian(long long n, const double* __restrict__ q, const double* __restrict__ C,
+                                double* __restrict__ q64, float* __restrict__ q32) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    const double cj = C[j], v = (q[j] * cj) * cj;
+    q64[j] = v;
+    if (q32) q32[j] = float(v);
+  }
+}
+
+// a new objective in the scaled space: c~_j = c_j C_j, q~_j = (q_j C_j) C_j
+__global__ void k_scale_objective(long long n, const double* __restrict__ c, const double* __restrict__ q,
+                                  const double* __restrict__ C, double* __restrict__ c64, float* __restrict__ c32,
+                                  double* __restrict__ q64, float* __restrict__ q32) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    const double cj = C[j], a = c[j] * cj, b = (q[j] * cj) * cj;
+    c64[j] = a;
+    q64[j] = b;
+    if (c32) c32[j] = float(a);
+    if (q32) q32[j] = float(b);
+  }
+}
+
 // kind_j = 1 for an integer column, 0 otherwise; aux_j = -1 (no auxiliary columns)
 __global__ void k_column_kinds(long long n, const uint8_t* __restrict__ is_int, int* __restrict__ kind,
                                int* __restrict__ aux_of) {
@@ -221,6 +244,17 @@ cudaError_t scale_row_bounds(long long m, const double* lo, const double* hi, co
                              double* hi64, float* lo32, float* hi32, cudaStream_t st) {
   if (m > 0)
     k_scale_row_bounds<<<setup_grid(m, kSetupThreads), kSetupThreads, 0, st>>>(m, lo, hi, R, lo64, hi64, lo32, hi32);
+  return cudaGetLastError();
+}
+
+cudaError_t scale_objective(long long n, const double* c, const double* q, const double* C, double* c64,
+                            float* c32, double* q64, float* q32, cudaStream_t st) {
+  if (n > 0) k_scale_objective<<<setup_grid(n, kSetupThreads), kSetupThreads, 0, st>>>(n, c, q, C, c64, c32, q64, q32);
+  return cudaGetLastError();
+}
+
+cudaError_t scale_hessian(long long n, const double* q, const double* C, double* q64, float* q32, cudaStream_t st) {
+  if (n > 0) k_scale_hessian<<<setup_grid(n, kSetupThreads), kSetupThreads, 0, st>>>(n, q, C, q64, q32);
   return cudaGetLastError();
 }
 

@@ -47,7 +47,8 @@ class Params(C.Structure):
                 ("run_stall_checks", C.c_int32), ("trace_capacity", C.c_int32), ("seed", C.c_uint64),
                 ("time_limit_s", C.c_double), ("device_wait_limit_s", C.c_double), ("pdl", C.c_int32),
                 ("prefetch", C.c_int32), ("host_transpose", C.c_int32),
-                ("repair_iters", C.c_int64), ("repair_tol", C.c_double), ("repair_rounds", C.c_int32)]
+                ("repair_iters", C.c_int64), ("repair_tol", C.c_double), ("repair_rounds", C.c_int32),
+                ("distance", C.c_int32)]
 
 
 class PdhgResult(C.Structure):
@@ -91,6 +92,7 @@ _SIGS = {
     "scylla_pdhg_solve": (C.c_int, [_P, C.c_double, C.c_int64, C.POINTER(PdhgResult)]),
     "scylla_set_objective": (C.c_int, [_P, _D, C.c_int32]),
     "scylla_get_objective": (C.c_int, [_P, _D, _D]),
+    "scylla_set_qp_objective": (C.c_int, [_P, _D, _D, C.c_double]),
     "scylla_run": (C.c_int, [_P, _D, C.POINTER(RunResult)]),
     "scylla_get_primal": (C.c_int, [_P, _D]),
     "scylla_get_dual": (C.c_int, [_P, _D]),
@@ -238,6 +240,13 @@ class LP:
     def set_objective(self, xhat, K: int):
         x = _f64(xhat, self.n)
         _check(lib().scylla_set_objective(self.h, _dp(x), int(K)))
+
+    def set_qp_objective(self, c, q, offset: float = 0.0):
+        """min c^T x + 1/2 x^T diag(q) x + offset over the same constraints
+        (scylla_set_qp_objective)."""
+        cc = _f64(c, self.n)
+        qq = _f64(q, self.n)
+        _check(lib().scylla_set_qp_objective(self.h, _dp(cc), _dp(qq), float(offset)))
 
     def get_objective(self):
         c = np.empty(self.n_total)

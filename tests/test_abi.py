@@ -52,7 +52,8 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu\n", offsetof(scylla_params, fixed_step_factor), offsetof(scylla_params, seed),
          offsetof(scylla_params, time_limit_s), offsetof(scylla_params, repair_iters),
          offsetof(scylla_params, repair_tol));
-  printf("%zu %zu\n", offsetof(scylla_params, repair_rounds), offsetof(scylla_repair_result, rel_kkt));
+  printf("%zu %zu %zu\n", offsetof(scylla_params, repair_rounds), offsetof(scylla_repair_result, rel_kkt),
+         offsetof(scylla_params, distance));
   return 0;
 }
 '''
@@ -67,7 +68,7 @@ int main(void) {
                          C.sizeof(S.RepairResult)]
     assert sizes[5:] == [S.Params.fixed_step_factor.offset, S.Params.seed.offset, S.Params.time_limit_s.offset,
                          S.Params.repair_iters.offset, S.Params.repair_tol.offset,
-                         S.Params.repair_rounds.offset, S.RepairResult.rel_kkt.offset]
+                         S.Params.repair_rounds.offset, S.RepairResult.rel_kkt.offset, S.Params.distance.offset]
 
 
 def test_default_params_are_the_papers(L):
@@ -77,6 +78,7 @@ def test_default_params_are_the_papers(L):
     assert p.n_check == 64 and p.precision == S.PREC_FP64
     # the continuous repair is not part of Algorithm 1: off unless asked for
     assert p.repair_iters == 0 and p.repair_tol == 1e-7 and p.repair_rounds == 8
+    assert p.distance == 1  # Algorithm 1's l1 distance
 
 
 def _create(rowptr, cols, vals, m, n, lo=None, hi=None, l=None, u=None, c=None, ii=None):
@@ -111,6 +113,7 @@ def test_null_handle_calls_fail_cleanly(L):
     assert L.scylla_set_objective(None, None, 1) == S.ERR_INVALID_ARG
     assert L.scylla_set_col_bounds(None, None, None) == S.ERR_INVALID_ARG
     assert L.scylla_set_row_bounds(None, None, None) == S.ERR_INVALID_ARG
+    assert L.scylla_set_qp_objective(None, None, None, 0.0) == S.ERR_INVALID_ARG
     rr = S.RepairResult()
     assert L.scylla_repair(None, None, 1e-6, 10, None, C.byref(rr)) == S.ERR_INVALID_ARG
     L.scylla_lp_destroy(None)
