@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched section")
     ap.add_argument("--no-fanout", action="store_true", help="skip the K-objective fan-out section")
     ap.add_argument("--no-repair", action="store_true", help="skip the continuous-repair section")
+    ap.add_argument("--no-l2", action="store_true", help="skip the l2-distance (diagonal QP) section")
     return ap.parse_args()
 
 
@@ -318,6 +319,9 @@ def run_ours(args):
     repair = None
     if rank == 0 and not args.no_repair:
         repair = repair_section(S, mixed, inst)
+    l2 = None
+    if rank == 0 and not args.no_l2:
+        l2 = l2_section(S, inst)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -373,6 +377,7 @@ def run_ours(args):
         "batched": batched,
         "fanout": fanout,
         "repair": repair,
+        "l2_objective": l2,
     }
     return out
 
@@ -401,6 +406,29 @@ def repair_section(S, mixed, inst):
             "seconds": r.seconds,
             "iter_per_s": r.iterations / r.seconds if r.seconds > 0 else None, "rel_kkt": r.rel_kkt,
             "objective": r.objective, "first_call_wall_s": first_wall}
+
+
+def l2_section(S, inst):
+    """One pump round with the l2 distance on the bench workload (FP32-mixed): the LP
+    solved to rel-KKT 1e-4, fix-and-propagate, the l2 objective update of round 1
+    (a diagonal quadratic objective, no auxiliary columns), and the warm solve of
+    that QP to rel-KKT 1e-4, timed on the device (the second of two identical
+    rounds, after the graphs of the quadratic mode are captured)."""
+    lp = S.LP.from_instance(inst, S.default_params(precision=S.PREC_MIXED, distance=2))
+    out = {"workload": WORKLOAD, "precision": "f32 (FP64 checks)", "tol_rel_kkt": TOL}
+    for _ in range(2):
+        lp.reset_state()
+        lp.set_qp_objective(inst.c, np.zeros(inst.n), 0.0)  # back to the LP
+        r0 = lp.pdhg_solve(TOL, ITER_CAP)
+        xhat = lp.fix_and_propagate(lp.primal())[0]
+        lp.set_objective(xhat, 1)
+        r1 = lp.pdhg_solve(TOL, ITER_CAP)
+    out["lp"] = {"attempts": int(r0.iterations), "seconds": r0.seconds, "iter_per_s": r0.iterations / r0.seconds}
+    out["l2_round"] = {"attempts": int(r1.iterations), "seconds": r1.seconds,
+                       "iter_per_s": r1.iterations / r1.seconds if r1.seconds > 0 else None,
+                       "status": int(r1.status), "rel_kkt": r1.rel_kkt}
+    lp.close()
+    return out
 
 
 def fanout_section(S):
