@@ -28,6 +28,8 @@ Readings of what Section 2.3 leaves open:
   applied, and for each changed column (in CSR order) its rows are queued in
   ascending order unless already queued or ignored.
 * A propagation call stops after ``visit_cap(m) = 20 m + 1000`` row visits.
+* ``propagate_rounds`` is the round-based (Jacobi) form of the same propagation that
+  the GPU runs; see its docstring for how rounds merge and when they stop.
 """
 from __future__ import annotations
 
@@ -72,9 +74,23 @@ class _FixProp:
             self.queue.append(i)
 
     def visit(self, i):
+        ign, changes = self.proposals(i)
+        if ign:
+            self.ignored[i] = True
+            return
+        for j, nl, nu in changes:
+            self.dl[j] = nl
+            self.du[j] = nu
+        for j, _, _ in changes:
+            for r in self.col_rows[j]:
+                self.enqueue(r)
+
+    def proposals(self, i):
+        """(ignore the row, [(j, new_lb, new_ub) for the columns it tightens]) from the
+        current domains, without changing them."""
         lo_i, hi_i = self.lo[i], self.hi[i]
         if lo_i == -INF and hi_i == INF:
-            return
+            return False, []
         dl, du, vals, cols = self.dl, self.du, self.vals, self.cols
         p0, p1 = self.rowptr[i], self.rowptr[i + 1]
         minf = 0.0
@@ -97,11 +113,9 @@ class _FixProp:
             else:
                 maxf += a * bmax
         if nmin == 0 and hi_i != INF and minf > hi_i + 1e-9:
-            self.ignored[i] = True
-            return
+            return True, []
         if nmax == 0 and lo_i != -INF and maxf < lo_i - 1e-9:
-            self.ignored[i] = True
-            return
+            return True, []
         changes = []
         for p in range(p0, p1):
             j = cols[p]
@@ -151,15 +165,9 @@ class _FixProp:
             if new_lb == old_lb and new_ub == old_ub:
                 continue
             if new_lb > new_ub + 1e-9:
-                self.ignored[i] = True
-                return
+                return True, []
             changes.append((j, new_lb, new_ub))
-        for j, nl, nu in changes:
-            dl[j] = nl
-            du[j] = nu
-        for j, _, _ in changes:
-            for r in self.col_rows[j]:
-                self.enqueue(r)
+        return False, changes
 
     def propagate(self):
         cap = visit_cap(self.m)
@@ -211,6 +219,54 @@ def fix_and_propagate(rowptr, cols, vals, lo, hi, l, u, is_int, xbar):
     xhat = np.array([min(max(float(xbar[j]), fp.dl[j]), fp.du[j]) for j in range(fp.n)])
     return (xhat, np.array(fp.dl), np.array(fp.du), np.array(fixed, dtype=np.int64),
             np.array(fp.ignored, dtype=bool))
+
+
+def propagate_rounds(rowptr, cols, vals, lo, hi, l, u, is_int, max_rounds: int = 100000):
+    """Propagation in rounds (the order-free form a GPU runs): in each round every
+    active row (all rows in the first) computes its proposals from the domains at
+    the start of the round, exactly as one FIFO visit does; a row that would empty a
+    domain is ignored from then on.  Each column then takes the largest proposed
+    lower and the smallest proposed upper bound; if those cross by more than 1e-9
+    the column keeps its domain and counts a conflict.  The rows of the columns
+    that changed are the next round's active rows.  Stops when no column changes or
+    after max_rounds rounds.  On integer data without ignored rows or conflicts this
+    is the fixpoint of the FIFO propagation (the greatest fixpoint of a monotone
+    tightening; Knaster-Tarski).  Returns (dom_lo, dom_hi, ignored, rounds,
+    conflicts)."""
+    fp = _FixProp(rowptr, cols, vals, lo, hi, l, u, is_int)
+    active = list(range(fp.m))
+    rounds = 0
+    conflicts = 0
+    while active and rounds < max_rounds:
+        rounds += 1
+        new_l = {}
+        new_u = {}
+        for i in active:
+            if fp.ignored[i]:
+                continue
+            ign, changes = fp.proposals(i)
+            if ign:
+                fp.ignored[i] = True
+                continue
+            for j, nl, nu in changes:
+                new_l[j] = max(new_l.get(j, -INF), nl)
+                new_u[j] = min(new_u.get(j, INF), nu)
+        changed = []
+        for j in sorted(set(new_l) | set(new_u)):
+            nl = max(fp.dl[j], new_l.get(j, -INF))
+            nu = min(fp.du[j], new_u.get(j, INF))
+            if nl > nu + 1e-9:
+                conflicts += 1
+                continue
+            if nl != fp.dl[j] or nu != fp.du[j]:
+                fp.dl[j] = nl
+                fp.du[j] = nu
+                changed.append(j)
+        nxt = set()
+        for j in changed:
+            nxt.update(fp.col_rows[j])
+        active = sorted(r for r in nxt if not fp.ignored[r])
+    return (np.array(fp.dl), np.array(fp.du), np.array(fp.ignored, dtype=bool), rounds, conflicts)
 
 
 def propagate_only(rowptr, cols, vals, lo, hi, l, u, is_int):
