@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-fanout", action="store_true", help="skip the K-objective fan-out section")
     ap.add_argument("--no-repair", action="store_true", help="skip the continuous-repair section")
     ap.add_argument("--no-l2", action="store_true", help="skip the l2-distance (diagonal QP) section")
+    ap.add_argument("--no-propagate", action="store_true", help="skip the bound-propagation section")
     return ap.parse_args()
 
 
@@ -322,6 +323,9 @@ def run_ours(args):
     l2 = None
     if rank == 0 and not args.no_l2:
         l2 = l2_section(S, inst)
+    prop = None
+    if rank == 0 and not args.no_propagate:
+        prop = propagate_section(mixed, inst)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -378,6 +382,7 @@ def run_ours(args):
         "fanout": fanout,
         "repair": repair,
         "l2_objective": l2,
+        "propagation": prop,
     }
     return out
 
@@ -406,6 +411,28 @@ def repair_section(S, mixed, inst):
             "seconds": r.seconds,
             "iter_per_s": r.iterations / r.seconds if r.seconds > 0 else None, "rel_kkt": r.rel_kkt,
             "objective": r.objective, "first_call_wall_s": first_wall}
+
+
+def propagate_section(mixed, inst):
+    """GPU bound propagation (scylla_propagate) on the bench workload: from the column
+    bounds, and after fixing every integer column at the generator's interior point
+    (wall time of the call, host loop and copies included; best of 3)."""
+    x0 = inst.meta["x0"]
+    ic = inst.is_int == 1
+    dl_fix, du_fix = inst.l.copy(), inst.u.copy()
+    dl_fix[ic] = x0[ic]
+    du_fix[ic] = x0[ic]
+    out = {"workload": WORKLOAD}
+    for name, (dl0, du0) in (("root", (inst.l, inst.u)), ("integers_fixed", (dl_fix, du_fix))):
+        best = None
+        for _ in range(3):
+            t0 = time.perf_counter()
+            dl, du, ign, rounds, conflicts = mixed.propagate(dl0, du0)
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        out[name] = {"ms": 1e3 * best, "rounds": int(rounds), "conflicts": int(conflicts),
+                     "ignored_rows": int(ign.sum()), "columns_tightened": int(np.sum((dl > dl0) | (du < du0)))}
+    return out
 
 
 def l2_section(S, inst):

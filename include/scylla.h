@@ -283,6 +283,24 @@ int scylla_check_feasible(const scylla_lp* lp, const double* x, int32_t* feasibl
  * with a fractional finite bound), CUDA. */
 int scylla_set_col_bounds(scylla_lp* lp, const double* col_lo, const double* col_hi);
 
+/* Bound propagation on the GPU: the activity-based tightening of fix-and-propagate
+ * (Section 2.3) over the original rows, in rounds.  In a round every active row
+ * (all rows in the first) derives, from the domains at the start of the round and
+ * with the arithmetic of one visit of the sequential propagation, the bounds it
+ * tightens; every column then takes the tightest of them.  A row whose activity
+ * bounds exclude [lo, hi] or that would empty a domain is ignored from then on; a
+ * column whose merged bounds cross by more than 1e-9 keeps its domain (a conflict).
+ * The rows of changed columns are the next round's; it stops when there are none or
+ * after max_rounds.  On integer data without ignored rows or conflicts the result is
+ * the sequential propagation's fixpoint bit for bit (scylla_fix_and_propagate's
+ * first step); on other data it can differ where the continuous thresholds make the
+ * order matter.
+ *   dom_lo, dom_hi: host, length n, the starting domains in, the propagated ones out.
+ *   ignored_rows: host, length m, or NULL.  rounds, conflicts: outputs, or NULL.
+ * Errors: INVALID_ARG (null, NaN, lo > hi, max_rounds < 1), OOM, CUDA. */
+int scylla_propagate(scylla_lp* lp, double* dom_lo, double* dom_hi, uint8_t* ignored_rows, int64_t max_rounds,
+                     int64_t* rounds, int64_t* conflicts);
+
 /* Replace the bounds of the original rows (host, length m each), keeping the
  * matrix, its preconditioning, the objective and the iterate; auxiliary rows keep
  * theirs, and ||b|| of the relative KKT error follows the new bounds.

@@ -199,6 +199,29 @@ struct DevSetup {
   int red_blocks;
 };
 
+// Device side of the round-based bound propagation (propagate.cu) on the original
+// rows and columns of a handle.
+struct PropDev {
+  int m, n;                            // original rows and columns
+  const int* rowptr;                   // A: original rows first, unscaled values
+  const int* cols;
+  const double* vals;
+  const int* t_rowptr;                 // A^T (rows ascending in each column)
+  const int* t_rows;
+  const int* perm;                     // position in A of each entry of A^T
+  const double *lo, *hi;               // row bounds (m)
+  const unsigned char* is_int;         // n
+  double *dl, *du;                     // domains (n), updated in place
+  double *plb, *pub;                   // one round's proposals at the rows' CSR positions
+  unsigned char* state;                // per row: 0 none, 1 proposals, 2 ignored
+  unsigned long long* count;           // columns changed, conflicts, rows marked
+};
+cudaError_t propagate_perm(int n, const int* t_rowptr, const int* t_rows, const int* a_rowptr, const int* a_cols,
+                           int* perm, cudaStream_t st);
+// one round: row visits from `active`, then the column merge marking `active_next`
+cudaError_t propagate_round(const PropDev& P, const unsigned char* active, unsigned char* active_next,
+                            cudaStream_t st);
+
 // ---- set-up launchers (setup.cu) ---------------------------------------------
 // R = C = 1, ruiz_iters Ruiz iterations and the Pock-Chambolle step (R2, C2 scratch)
 cudaError_t launch_precondition(const DevSetup& s, int ruiz_iters, bool pock_chambolle, cudaStream_t st);

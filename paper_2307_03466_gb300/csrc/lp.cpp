@@ -763,6 +763,10 @@ void scylla_lp::set_qp_active(bool on) {
 }
 
 void scylla_lp::release() {
+  if (prop_mem) cudaFree(prop_mem);
+  prop_mem = nullptr;
+  if (prop_count_h) cudaFreeHost(prop_count_h);
+  prop_count_h = nullptr;
   if (repair_lp) {
     cudaStreamSynchronize(repair_lp->st);
     repair_lp->release();
@@ -1204,6 +1208,98 @@ int scylla_lp::set_row_bounds(const double* lo, const double* hi) {
   }
   CK(cudaStreamSynchronize(st));
   return SCYLLA_OK;
+}
+
+// ------------------------------------------------------------ propagation ---
+static int propagate_impl(scylla_lp* lp, double* dl, double* du, uint8_t* ignored, int64_t max_rounds,
+                          int64_t* rounds_out, int64_t* conflicts_out) {
+  const int64_t m0 = lp->m0, n0 = lp->n0;
+  cudaStream_t st = lp->st;
+  int rc = lp->order_after_user();
+  if (rc != SCYLLA_OK) return rc;
+  PropDev& P = lp->prop;
+  if (!lp->prop_mem) {
+    // perm over the transpose's entries, proposals at A's positions, domains, row
+    // states, two active-row masks, three counters
+    const size_t nnz = size_t(lp->nnz);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+      const size_t o = off;
+      off += (bytes + 255) & ~size_t(255);
+      return o;
+    };
+    const size_t o_perm = take(sizeof(int) * (nnz + 1)), o_plb = take(sizeof(double) * (nnz + 1)),
+                 o_pub = take(sizeof(double) * (nnz + 1)), o_dl = take(sizeof(double) * size_t(n0 + 1)),
+                 o_du = take(sizeof(double) * size_t(n0 + 1)), o_st = take(size_t(m0 + 1)),
+                 o_a0 = take(size_t(m0 + 1)), o_a1 = take(size_t(m0 + 1)),
+                 o_cnt = take(3 * sizeof(unsigned long long));
+    CK(cudaMalloc(&lp->prop_mem, off));
+    CK(cudaMallocHost(&lp->prop_count_h, 3 * sizeof(unsigned long long)));
+    char* b = static_cast<char*>(lp->prop_mem);
+    int* perm = reinterpret_cast<int*>(b + o_perm);
+    P.m = int(m0);
+    P.n = int(n0);
+    P.rowptr = lp->a_rowptr;
+    P.cols = lp->a_cols;
+    P.vals = lp->a_vals0;
+    P.t_rowptr = lp->t_rowptr;
+    P.t_rows = lp->t_cols;
+    P.perm = perm;
+    P.is_int = lp->int_mask;
+    P.plb = reinterpret_cast<double*>(b + o_plb);
+    P.pub = reinterpret_cast<double*>(b + o_pub);
+    P.dl = reinterpret_cast<double*>(b + o_dl);
+    P.du = reinterpret_cast<double*>(b + o_du);
+    P.state = reinterpret_cast<unsigned char*>(b + o_st);
+    lp->prop_active[0] = reinterpret_cast<unsigned char*>(b + o_a0);
+    lp->prop_active[1] = reinterpret_cast<unsigned char*>(b + o_a1);
+    P.count = reinterpret_cast<unsigned long long*>(b + o_cnt);
+    CK(propagate_perm(int(n0), lp->t_rowptr, lp->t_cols, lp->a_rowptr, lp->a_cols, perm, st));
+  }
+  P.lo = lp->lo_un;  // the current original row bounds come first
+  P.hi = lp->hi_un;
+  CK(cudaMemcpyAsync(P.dl, dl, sizeof(double) * n0, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(P.du, du, sizeof(double) * n0, cudaMemcpyHostToDevice, st));
+  if (m0 > 0) {
+    CK(cudaMemsetAsync(P.state, 0, size_t(m0), st));
+    CK(cudaMemsetAsync(lp->prop_active[0], 1, size_t(m0), st));
+  }
+  int64_t rounds = 0, conflicts = 0;
+  int cur = 0;
+  while (m0 > 0 && rounds < max_rounds) {
+    ++rounds;
+    CK(propagate_round(P, lp->prop_active[cur], lp->prop_active[cur ^ 1], st));
+    CK(cudaMemcpyAsync(lp->prop_count_h, P.count, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    conflicts += int64_t(lp->prop_count_h[1]);
+    if (lp->prop_count_h[2] == 0) break;  // no row is active next
+    cur ^= 1;
+  }
+  CK(cudaMemcpyAsync(dl, P.dl, sizeof(double) * n0, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(du, P.du, sizeof(double) * n0, cudaMemcpyDeviceToHost, st));
+  std::vector<unsigned char> state(static_cast<size_t>(m0));
+  if (ignored && m0 > 0) CK(cudaMemcpyAsync(state.data(), P.state, size_t(m0), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (ignored)
+    for (int64_t i = 0; i < m0; ++i) ignored[i] = state[size_t(i)] == 2 ? 1 : 0;
+  if (rounds_out) *rounds_out = rounds;
+  if (conflicts_out) *conflicts_out = conflicts;
+  return SCYLLA_OK;
+}
+
+extern "C" int scylla_propagate(scylla_lp* lp, double* dom_lo, double* dom_hi, uint8_t* ignored_rows,
+                                int64_t max_rounds, int64_t* rounds, int64_t* conflicts) {
+  if (!lp || !dom_lo || !dom_hi) FAIL(SCYLLA_ERR_INVALID_ARG, "null argument");
+  if (max_rounds < 1) FAIL(SCYLLA_ERR_INVALID_ARG, "max_rounds must be >= 1");
+  for (int64_t j = 0; j < lp->n0; ++j)
+    if (std::isnan(dom_lo[j]) || std::isnan(dom_hi[j]) || dom_lo[j] > dom_hi[j])
+      FAIL(SCYLLA_ERR_INVALID_ARG, "invalid domain at column " + std::to_string(j));
+  try {
+    return propagate_impl(lp, dom_lo, dom_hi, ignored_rows, max_rounds, rounds, conflicts);
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return SCYLLA_ERR_OOM;
+  }
 }
 
 extern "C" int scylla_set_row_bounds(scylla_lp* lp, const double* row_lo, const double* row_hi) {

@@ -102,6 +102,11 @@ struct scylla_lp {
 
   // the continuous-repair copy of the original MIP (scylla_repair), built on first use
   scylla_lp* repair_lp = nullptr;
+  // buffers of the device bound propagation (scylla_propagate), allocated on first use
+  void* prop_mem = nullptr;
+  scylla::PropDev prop{};
+  unsigned char* prop_active[2] = {nullptr, nullptr};
+  unsigned long long* prop_count_h = nullptr;  // pinned copy of the three counters
 
   scylla::DevObjective objective_desc();
   void release();

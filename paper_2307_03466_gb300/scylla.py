@@ -106,6 +106,8 @@ _SIGS = {
     "scylla_check_feasible": (C.c_int, [_P, _D, C.POINTER(C.c_int32)]),
     "scylla_set_col_bounds": (C.c_int, [_P, _D, _D]),
     "scylla_set_row_bounds": (C.c_int, [_P, _D, _D]),
+    "scylla_propagate": (C.c_int, [_P, _D, _D, C.POINTER(C.c_uint8), C.c_int64, C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_int64)]),
     "scylla_repair": (C.c_int, [_P, _D, C.c_double, C.c_int64, _D, C.POINTER(RepairResult)]),
     "scylla_perturb": (C.c_int, [_P, _D, _D, C.c_int32, C.c_int64, C.c_uint64, C.POINTER(C.c_int64)]),
     "scylla_get_trace": (C.c_int, [_P, _D, C.POINTER(C.c_int64), _D, C.POINTER(C.c_int64)]),
@@ -335,6 +337,17 @@ class LP:
         lo = _f64(col_lo, self.n)
         hi = _f64(col_hi, self.n)
         _check(lib().scylla_set_col_bounds(self.h, _dp(lo), _dp(hi)))
+
+    def propagate(self, dom_lo, dom_hi, max_rounds: int = 100000):
+        """Bound propagation on the GPU (scylla_propagate): returns (dom_lo, dom_hi,
+        ignored rows, rounds, conflicts)."""
+        dl = _f64(dom_lo, self.n).copy()
+        du = _f64(dom_hi, self.n).copy()
+        ign = np.zeros(max(self.m, 1), dtype=np.uint8)
+        rounds, conflicts = C.c_int64(), C.c_int64()
+        _check(lib().scylla_propagate(self.h, _dp(dl), _dp(du), ign.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                      int(max_rounds), C.byref(rounds), C.byref(conflicts)))
+        return dl, du, ign[: self.m].astype(bool), rounds.value, conflicts.value
 
     def set_row_bounds(self, row_lo, row_hi):
         """New bounds of the original rows (scylla_set_row_bounds)."""

@@ -114,6 +114,7 @@ def test_null_handle_calls_fail_cleanly(L):
     assert L.scylla_set_col_bounds(None, None, None) == S.ERR_INVALID_ARG
     assert L.scylla_set_row_bounds(None, None, None) == S.ERR_INVALID_ARG
     assert L.scylla_set_qp_objective(None, None, None, 0.0) == S.ERR_INVALID_ARG
+    assert L.scylla_propagate(None, None, None, None, 10, None, None) == S.ERR_INVALID_ARG
     rr = S.RepairResult()
     assert L.scylla_repair(None, None, 1e-6, 10, None, C.byref(rr)) == S.ERR_INVALID_ARG
     L.scylla_lp_destroy(None)
