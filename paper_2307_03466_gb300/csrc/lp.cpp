@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -92,6 +93,57 @@ extern "C" const char* scylla_last_error(void) { return get_error(); }
 namespace {
 
 size_t padded(size_t nnz) { return scylla::padded_len(nnz); }
+
+// A stream-ordered memory pool per device for the handles' arenas and set-up
+// scratch.  It keeps the memory of destroyed handles for the next ones (release
+// threshold: all of it), so creating and destroying handles in a loop needs no
+// cudaMalloc or synchronizing cudaFree.
+cudaError_t handle_pool(int device, cudaMemPool_t* out) {
+  static std::mutex mu;
+  static std::vector<cudaMemPool_t> pools;
+  std::lock_guard<std::mutex> lk(mu);
+  if (device < 0) return cudaErrorInvalidDevice;
+  if (size_t(device) >= pools.size()) pools.resize(size_t(device) + 1, nullptr);
+  if (!pools[size_t(device)]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    unsigned long long keep = ~0ULL;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) return e;
+    pools[size_t(device)] = pool;
+  }
+  *out = pools[size_t(device)];
+  return cudaSuccess;
+}
+
+// Pinned host blocks of kPinnedBlock bytes (a handle's control-block mirror and
+// done flags), kept on a free list for reuse instead of cudaFreeHost.
+constexpr size_t kPinnedBlock = sizeof(scylla::Control) + 64;
+std::mutex g_pinned_mu;
+std::vector<void*> g_pinned_free;
+
+cudaError_t pinned_acquire(void** p) {
+  {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    if (!g_pinned_free.empty()) {
+      *p = g_pinned_free.back();
+      g_pinned_free.pop_back();
+      return cudaSuccess;
+    }
+  }
+  return cudaMallocHost(p, kPinnedBlock);
+}
+
+void pinned_release(void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  g_pinned_free.push_back(p);
+}
 
 // Warp tiles of a CSR structure.  Above kTileSpan rows the rows are cut into spans
 // of kTileSpan rows, tiled independently on the host threads and concatenated: a
@@ -467,7 +519,9 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   for (int pass = 0; pass < 2; ++pass) {
     Arena ar;
     if (pass == 1) {
-      CK(cudaMalloc(&lp->arena, lp->arena_bytes));
+      cudaMemPool_t pool = nullptr;
+      CK(handle_pool(lp->device, &pool));
+      CK(cudaMallocFromPoolAsync(&lp->arena, lp->arena_bytes, pool, lp->st));
       ar.base = static_cast<char*>(lp->arena);
     }
     lp->a_rowptr = ar.take<int>(m + 1);
@@ -545,7 +599,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   {
     // one pinned block: the control block's host copy, then the two done flags
     void* pin = nullptr;
-    CK(cudaMallocHost(&pin, sizeof(Control) + 64));
+    CK(pinned_acquire(&pin));
     lp->h_ctl = static_cast<Control*>(pin);
     lp->h_done = reinterpret_cast<int*>(static_cast<char*>(pin) + sizeof(Control));
   }
@@ -564,13 +618,15 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     CK(cudaMemcpyAsync(lp->t_vals64, tv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
   } else {
     void* scratch = nullptr;
-    CK(cudaMalloc(&scratch, transpose_scratch_bytes(int(n), nnz)));
+    cudaMemPool_t pool = nullptr;
+    CK(handle_pool(lp->device, &pool));
+    CK(cudaMallocFromPoolAsync(&scratch, transpose_scratch_bytes(int(n), nnz), pool, st));
     cudaError_t te = transpose_device(int(m), int(n), nnz, lp->a_rowptr, lp->a_cols, lp->a_vals64, lp->t_rowptr,
                                       lp->t_cols, lp->t_vals64, scratch, st);
+    cudaFreeAsync(scratch, st);  // back to the pool once the transpose is done
     tp.resize(size_t(n) + 1);
     if (te == cudaSuccess) te = cudaMemcpyAsync(tp.data(), lp->t_rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, st);
     if (te == cudaSuccess) te = cudaStreamSynchronize(st);
-    cudaFree(scratch);
     CK(te);
   }
   // tiles of the transpose, and the grids that depend on their counts
@@ -779,9 +835,9 @@ void scylla_lp::release() {
     e = nullptr;
   }
   h_done = nullptr;  // inside the h_ctl block
-  if (arena) cudaFree(arena);
+  if (arena) cudaFreeAsync(arena, st);  // to the pool, after the stream's work
   arena = nullptr;
-  if (h_ctl) cudaFreeHost(h_ctl);
+  pinned_release(h_ctl);
   h_ctl = nullptr;
   if (ev_user) cudaEventDestroy(ev_user);
   if (ev0) cudaEventDestroy(ev0);
