@@ -123,14 +123,35 @@ __device__ __forceinline__ T dual_prox(T y, T sigma, T axt, T lo, T hi) {
   return T(0);
 }
 
+// Sign and finiteness tests of non-NaN doubles on their bit patterns (integer
+// instructions; an FP64 comparison occupies the slow FP64 pipe of this part):
+// v > 0 iff the bits are positive as a signed integer; v < 0 iff they are negative
+// and v is not -0; v > -inf and v < +inf iff the bits differ from those of -inf, +inf.
+__device__ __forceinline__ bool pos_bits(double v) { return __double_as_longlong(v) > 0; }
+__device__ __forceinline__ bool neg_bits(double v) {
+  const long long b = __double_as_longlong(v);
+  return b < 0 && b != (long long)0x8000000000000000ULL;
+}
+__device__ __forceinline__ bool above_neg_inf(double v) {
+  return __double_as_longlong(v) != (long long)0xFFF0000000000000ULL;
+}
+__device__ __forceinline__ bool below_pos_inf(double v) { return __double_as_longlong(v) != 0x7FF0000000000000LL; }
+
 // lambda = projection of the reduced cost r onto the sign cone of the column bounds
 __device__ __forceinline__ double rc_proj(double r, double l, double u) {
-  const double inf = pos_inf<double>();
-  const bool lf = l > -inf, uf = u < inf;
+  const bool lf = above_neg_inf(l), uf = below_pos_inf(u);
   if (lf && uf) return r;
-  if (lf) return r > 0.0 ? r : 0.0;
-  if (uf) return r < 0.0 ? r : 0.0;
+  if (lf) return pos_bits(r) ? r : 0.0;
+  if (uf) return neg_bits(r) ? r : 0.0;
   return 0.0;
+}
+
+// The bound term of a multiplier v against a bound pair: a v when v > 0, b v when
+// v < 0, 0 otherwise; the same value as (v > 0 ? a v : 0) - (v < 0 ? b (-v) : 0) in
+// one product.
+__device__ __forceinline__ double bound_term(double v, double a, double b) {
+  const double s = pos_bits(v) ? a : (neg_bits(v) ? b : 0.0);
+  return s * v;
 }
 
 // SplitMix64 output function (Steele, Lea, Flood 2014)

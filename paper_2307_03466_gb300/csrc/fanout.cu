@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_cols(DevFan<T> F) {
         const double rdu = rd / Cj;
         a[1] += rdu * rdu;
         a[2] += cs * xs[c];
-        a[3] += (lam > 0.0 ? lj * lam : 0.0) - (lam < 0.0 ? uj * (-lam) : 0.0);
+        a[3] += bound_term(lam, lj, uj);
         const double dd = xs[c] - xl;
         a[4] += dd * dd;
       }
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_rows(DevFan<T> F) {
         a[0] += rps * rps;
         const double rp = rps / Ri;
         a[1] += rp * rp;
-        a[2] += (ys[c] > 0.0 ? lo * ys[c] : 0.0) - (ys[c] < 0.0 ? hi * (-ys[c]) : 0.0);
+        a[2] += bound_term(ys[c], lo, hi);
         const double dd = ys[c] - yl;
         a[3] += dd * dd;
       }

@@ -1018,7 +1018,7 @@ struct CheckColsEpi {
       const double rdu = rd * iCj;
       acc[5 * q + 1] += rdu * rdu;
       acc[5 * q + 2] += cj * xs[q];
-      acc[5 * q + 3] += (lam > 0.0 ? lj * lam : 0.0) - (lam < 0.0 ? uj * (-lam) : 0.0);
+      acc[5 * q + 3] += bound_term(lam, lj, uj);
       if (has_q) {
         const double hq = 0.5 * (qj * xs[q]) * xs[q];
         acc[5 * q + 2] += hq;
@@ -1104,7 +1104,7 @@ struct CheckRowsEpi {
       acc[4 * q + 0] += rps * rps;
       const double rp = rps * iRi;
       acc[4 * q + 1] += rp * rp;
-      acc[4 * q + 2] += (ys[q] > 0.0 ? lo * ys[q] : 0.0) - (ys[q] < 0.0 ? hi * (-ys[q]) : 0.0);
+      acc[4 * q + 2] += bound_term(ys[q], lo, hi);
       const double dd = ys[q] - yl;
       acc[4 * q + 3] += dd * dd;
     }
