@@ -316,7 +316,10 @@ int scylla_set_row_bounds(scylla_lp* lp, const double* row_lo, const double* row
  * by the same PDHG path (preconditioning, adaptive steps, restarts, FP64 checks;
  * Sections 2.1-2.2) on a second device copy of the original MIP that the handle
  * builds on first use (original objective, no auxiliary columns, the handle's PDHG
- * parameters, always FP64) and keeps until it is destroyed.  Up to
+ * parameters, always FP64) and keeps until it is destroyed.  First the fixing is
+ * propagated on the GPU (scylla_propagate, at most 1000 rounds): a row it ignores or
+ * a conflict proves the fixed LP infeasible, and then no solve runs (rounds = 0,
+ * x_out = xhat clamped to the bounds).  Otherwise up to
  * p.repair_rounds solves to rel-KKT <= tol, the first from the cold start, the next
  * ones warm: after each, the integer entries are set to xhat's exactly and the point
  * is given scylla_check_feasible's test; if it fails, every row whose activity

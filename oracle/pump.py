@@ -35,9 +35,12 @@ Readings of what the paper leaves open:
   inside [l_j, u_j] (the other direction when the first one is blocked).  Random
   numbers: SplitMix64 seeded with ``seed XOR K``, uniforms ``(r >> 11) * 2^-53``.
 * Continuous repair (an extension; the paper keeps the continuous part of the
-  fix-and-propagate point at the LP values, Section 2.3): the LP of the original
+  fix-and-propagate point at the LP values, Section 2.3): the fixing is first
+  propagated in rounds (``fixprop.propagate_rounds``, at most 1000); a row it
+  ignores or a conflict proves the fixed LP infeasible and ends the repair (no
+  solve; x = xhat clamped to the bounds).  Otherwise the LP of the original
   MIP with every integer column fixed at xhat (l_j = u_j = xhat_j), original
-  objective and rows, solved by the oracle PDHG to the given rel-KKT in up to
+  objective and rows, is solved by the oracle PDHG to the given rel-KKT in up to
   ``rounds`` solves (the first from the cold start, the next ones warm) within one
   attempt budget.  After each solve the integer entries are set to xhat's and the
   point is given the feasibility check; when it fails, every row whose activity
@@ -297,9 +300,13 @@ def repair(inst, xhat, tol: float, iter_limit: int, params: PdhgParams | None = 
     u[is_int] = xh[is_int]
     lo = np.asarray(inst.lo, dtype=np.float64)
     hi = np.asarray(inst.hi, dtype=np.float64)
+    info = {"iterations": 0, "rounds": 0, "shifted_rows": 0, "rel_kkt": math.inf, "status": None}
+    _, _, ign, _, conf = fixprop.propagate_rounds(inst.rowptr, inst.cols, inst.vals, lo, hi, l, u, inst.is_int,
+                                                  max_rounds=1000)
+    if ign.any() or conf > 0:
+        return NOT_FOUND, np.minimum(np.maximum(xh, l), u), info
     lo_w, hi_w = lo.copy(), hi.copy()
     lp = OracleLP(A, inst.c, lo_w, hi_w, l, u, params=params or PdhgParams())
-    info = {"iterations": 0, "rounds": 0, "shifted_rows": 0, "rel_kkt": math.inf, "status": None}
     st = NOT_FOUND
     x = None
     for t in range(rounds):

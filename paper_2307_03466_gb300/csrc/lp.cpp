@@ -1267,6 +1267,10 @@ int scylla_lp::set_row_bounds(const double* lo, const double* hi) {
 }
 
 // ------------------------------------------------------------ propagation ---
+// rounds of the propagation that screens a repair's fixing (its verdict of
+// infeasibility holds at any round)
+constexpr int64_t kRepairPropagationRounds = 1000;
+
 static int propagate_impl(scylla_lp* lp, double* dl, double* du, uint8_t* ignored, int64_t max_rounds,
                           int64_t* rounds_out, int64_t* conflicts_out) {
   const int64_t m0 = lp->m0, n0 = lp->n0;
@@ -1393,6 +1397,31 @@ int scylla_lp::repair(const double* xhat, double tol, int64_t iter_limit, double
     if (int0[size_t(j)] && !(std::isfinite(xhat[j]) && xhat[j] == std::floor(xhat[j]) && xhat[j] >= l0[size_t(j)] &&
                              xhat[j] <= u0[size_t(j)]))
       FAIL(SCYLLA_ERR_INVALID_ARG, "xhat not integral within bounds at integer column " + std::to_string(j));
+  std::vector<double> lf(l0), uf(u0);
+  for (int64_t j = 0; j < n0; ++j)
+    if (int0[size_t(j)]) lf[size_t(j)] = uf[size_t(j)] = xhat[j];
+  // Propagation of the fixing on the GPU: every bound it derives holds for every point
+  // of the fixed LP, so a row it has to ignore or a column whose bounds cross proves
+  // the fixed LP infeasible, and no solve runs.
+  {
+    std::vector<double> pl(lf), pu(uf);
+    std::vector<uint8_t> ign(static_cast<size_t>(m0 > 0 ? m0 : 1), 0);
+    int64_t prounds = 0, pconf = 0;
+    rc = propagate_impl(this, pl.data(), pu.data(), ign.data(), kRepairPropagationRounds, &prounds, &pconf);
+    if (rc != SCYLLA_OK) return rc;
+    bool infeasible = pconf > 0;
+    for (int64_t i = 0; i < m0 && !infeasible; ++i) infeasible = ign[size_t(i)] != 0;
+    if (infeasible) {
+      double obj = 0.0;
+      for (int64_t j = 0; j < n0; ++j) {
+        x_out[j] = std::min(std::max(xhat[j], lf[size_t(j)]), uf[size_t(j)]);
+        obj += c0[size_t(j)] * x_out[j];
+      }
+      out->status = SCYLLA_NOT_FOUND;
+      out->objective = obj;
+      return SCYLLA_OK;
+    }
+  }
   if (!repair_lp) {
     scylla_csr A{m0, n0, nnz0, rowptr0.data(), cols0.data(), vals0.data()};
     scylla_params q = p;
@@ -1409,9 +1438,6 @@ int scylla_lp::repair(const double* xhat, double tol, int64_t iter_limit, double
     }
     repair_lp = r;
   }
-  std::vector<double> lf(l0), uf(u0);
-  for (int64_t j = 0; j < n0; ++j)
-    if (int0[size_t(j)]) lf[size_t(j)] = uf[size_t(j)] = xhat[j];
   rc = repair_lp->set_col_bounds(lf.data(), uf.data());
   // working row bounds: the original ones for the first solve
   std::vector<double> lo_w(lo0), hi_w(hi0);

@@ -104,7 +104,7 @@ def test_repair_infeasible_fixing_and_bad_input():
                       np.zeros(2), np.array([3.0, 1.0]), np.array([1, 0], dtype=np.uint8))
     g = S.LP.from_instance(inst, S.default_params())
     r, x = g.repair(np.array([2.0, 0.0]), 1e-9, 20000)
-    assert r.status == P.NOT_FOUND and x[0] == 2.0
+    assert r.status == P.NOT_FOUND and x[0] == 2.0 and r.rounds == 0 and r.iterations == 0
     r, x = g.repair(np.array([1.0, 0.0]), 1e-9, 20000)
     assert r.status == P.FOUND and x[0] == 1.0 and abs(x[1]) <= 1e-7
     with pytest.raises(S.ScyllaError):
@@ -130,3 +130,18 @@ def test_run_with_repair_finds_mixed_solutions():
         assert P.check_feasible(inst.rowptr, inst.cols, inst.vals, inst.lo, inst.hi, inst.l, inst.u, inst.is_int, x)
         assert abs(r.objective - float(inst.c @ x)) <= 1e-9 * max(1.0, abs(r.objective))
         g.close()
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_pure_integer_run_with_repair_equals_run_without(seed):
+    """Every column integer: the propagation screen ends each repair without a solve,
+    so scylla_run with the repair gives the run without it, attempts included."""
+    S = lib()
+    inst = I.knapsack_cover(60, seed=900 + seed, per_col=4)
+    out = []
+    for rep in (0, 20000):
+        g = S.LP.from_instance(inst, S.default_params(max_rounds=8, iter_limit=3000, repair_iters=rep))
+        r, x = g.run()
+        out.append((r.status, r.rounds, r.total_iterations, r.found_by, x.tobytes()))
+        g.close()
+    assert out[0] == out[1]

@@ -6,7 +6,8 @@ fix-and-propagate point at the LP values, Section 2.3).
   independent solver (scipy's HiGHS), so a dropped fixing, a wrong bound or a
   wrong objective fails.
 - The integer entries come back exactly as xhat's.
-- A fixing that leaves the LP infeasible is reported as not found.
+- A fixing that leaves the LP infeasible is reported as not found, by the
+  propagation screen and without a solve.
 - Where one solve leaves single rows violated beyond the check's tolerance, the
   shift rounds (violated rows' working bounds moved inward, warm re-solve) end
   at points that pass the exact check, near the fixed LP's optimum.
@@ -67,8 +68,9 @@ def test_repair_infeasible_fixing_is_not_found():
     inst = I.Instance("fix", 2, 2, A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data,
                       np.array([1.0, 1.0]), np.array([-math.inf, 0.5]), np.array([1.5, math.inf]),
                       np.zeros(2), np.array([3.0, 1.0]), np.array([1, 0], dtype=np.uint8))
-    st, x, _ = P.repair(inst, np.array([2.0, 0.0]), 1e-9, 20000)  # 2 + x1 <= 1.5 is impossible
+    st, x, info = P.repair(inst, np.array([2.0, 0.0]), 1e-9, 20000)  # 2 + x1 <= 1.5 is impossible
     assert st == P.NOT_FOUND and x[0] == 2.0
+    assert info["rounds"] == 0 and info["iterations"] == 0  # the propagation proves it, no solve runs
     st, x, _ = P.repair(inst, np.array([1.0, 0.0]), 1e-9, 20000)  # x1 = 0 works (objective 1)
     assert st == P.FOUND and x[0] == 1.0 and abs(x[1]) <= 1e-7
 
@@ -102,3 +104,14 @@ def test_pump_with_repair_finds_mixed_solutions():
         assert P.check_feasible(inst.rowptr, inst.cols, inst.vals, inst.lo, inst.hi, inst.l, inst.u, inst.is_int,
                                 r1.x)
     assert found_on == 6 and found_off < found_on
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_pure_integer_repairs_end_at_the_propagation_screen(seed):
+    """With every column integer, a failed fixing leaves no continuous freedom: the
+    screen proves each fixed LP infeasible, so the loop with the repair takes the
+    same path, attempts included, as the loop without it."""
+    inst = I.knapsack_cover(40, seed=900 + seed, per_col=4)
+    r0 = P.pump(inst, P.PumpParams(max_rounds=8, iter_limit=3000))
+    r1 = P.pump(inst, P.PumpParams(max_rounds=8, iter_limit=3000, repair_iters=20000))
+    assert r0.status == r1.status and r0.rounds == r1.rounds and r0.total_iterations == r1.total_iterations
