@@ -293,15 +293,18 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_cols(DevFan<T> F) {
       const double xl = double(F.XLR[o]);
       const double xs[2] = {double(x), double(xav)};
       const double ss[2] = {sc[q], sa[q]};
+      const bool boxed = above_neg_inf(lj) && below_pos_inf(uj);  // then r - lambda = 0 exactly
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const double r = cs - ss[c];
         const double lam = rc_proj(r, lj, uj);
-        const double rd = r - lam;
         double* a = acc + q * kNC1 + 5 * c;
-        a[0] += rd * rd;
-        const double rdu = rd / Cj;
-        a[1] += rdu * rdu;
+        if (!boxed) {
+          const double rd = r - lam;
+          a[0] += rd * rd;
+          const double rdu = rd / Cj;
+          a[1] += rdu * rdu;
+        }
         a[2] += cs * xs[c];
         a[3] += bound_term(lam, lj, uj);
         const double dd = xs[c] - xl;

@@ -1008,15 +1008,21 @@ struct CheckColsEpi {
     const double xs[2] = {to_f64(x), to_f64(xav)};
     const bool has_q = QP == 1 || (QP == 2 && qq != nullptr);
     const double qj = has_q ? qq[j] : 0.0;
+    // with both bounds finite the projection returns r itself, the dual residual
+    // r - lambda is exactly 0 and its two squared norms are left as they are (the
+    // same sums, without four FP64 instructions per iterate)
+    const bool boxed = above_neg_inf(lj) && below_pos_inf(uj);
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       // quadratic objective: reduced cost c + q x - A^T y; +-1/2 q x^2 in the objectives
       const double r = has_q ? (cj + qj * xs[q]) - s[q] : cj - s[q];
       const double lam = rc_proj(r, lj, uj);
-      const double rd = r - lam;
-      acc[5 * q + 0] += rd * rd;
-      const double rdu = rd * iCj;
-      acc[5 * q + 1] += rdu * rdu;
+      if (!boxed) {
+        const double rd = r - lam;
+        acc[5 * q + 0] += rd * rd;
+        const double rdu = rd * iCj;
+        acc[5 * q + 1] += rdu * rdu;
+      }
       acc[5 * q + 2] += cj * xs[q];
       acc[5 * q + 3] += bound_term(lam, lj, uj);
       if (has_q) {
