@@ -14,11 +14,17 @@ the oracle to run a few attempts:
   the oracle) on the MCF workload, within FP32 rounding.
 - FP32-mixed solves to rel-KKT 1e-4, the bench's stopping rule, re-evaluated by the
   oracle on the returned point.
+- The batched workload (256 power-law LPs, 17.2M nonzeros) and the fan-out workload
+  (m = 200k, n = 500k, 5M nonzeros, K = 64): fixed-step FP64 attempts of sampled LPs
+  and objectives against the oracle within 1e-9, and the FP32-mixed bench
+  configuration converging for every LP and objective, with the oracle's primal
+  residual of sampled points.
 """
 import numpy as np
 import pytest
 
 from oracle import pdhg as O
+from oracle import pump as P
 from paper_2307_03466_gb300 import instances as I
 from tests.gpu_common import gpu_available, pair, rel_err
 
@@ -144,3 +150,98 @@ def test_packcover_repair_of_a_feasible_fixing(packcover):
                             packcover.l, packcover.u, packcover.is_int, x)
     assert float(packcover.c @ x) <= float(packcover.c @ x0) + 1e-6 * abs(float(packcover.c @ x0))
     g.close()
+
+
+# ---- the batched and fan-out workloads of bench.py, at their full sizes ----------
+
+def sampled(insts):
+    """The smallest, a middle and the largest LP of a batch."""
+    order = sorted(range(len(insts)), key=lambda b: insts[b].nnz)
+    return [order[0], order[len(order) // 2], order[-1]]
+
+
+def test_batch_bench_size_fixed_step_sampled_lps_match_oracle():
+    """The 256 power-law LPs (17.2M nonzeros) as one batch: 8 fixed-step FP64 attempts;
+    the smallest, a middle and the largest LP equal the oracle's PDHG within 1e-9."""
+    from paper_2307_03466_gb300 import scylla as S
+    insts = I.batch()
+    assert len(insts) == 256
+    B = S.Batch(insts, S.default_params(adaptive_step=0, restarts=0))
+    res, _ = B.solve(0.0, 8)
+    assert all(r.iterations == 8 for r in res)
+    for b in sampled(insts):
+        inst = insts[b]
+        o = O.OracleLP(inst.csr(), inst.c, inst.lo, inst.hi, inst.l, inst.u,
+                       params=O.PdhgParams(adaptive_step=False, restarts=False))
+        o.solve(0.0, 8)
+        assert rel_err(B.primal(b), o.primal()) <= 1e-9, b
+    B.close()
+
+
+def test_batch_bench_size_mixed_all_converge_primal_checked_by_oracle():
+    """The bench configuration (FP32-mixed, rel-KKT 1e-4): every LP converges, and the
+    oracle's primal residual of the sampled LPs' points agrees."""
+    from paper_2307_03466_gb300 import scylla as S
+    insts = I.batch()
+    B = S.Batch(insts, S.default_params(precision=S.PREC_MIXED))
+    res, _ = B.solve(1e-4, 200000)
+    assert all(r.status == O.CONVERGED and r.rel_kkt <= 1e-4 for r in res)
+    for b in sampled(insts):
+        inst = insts[b]
+        o = O.OracleLP(inst.csr(), inst.c, inst.lo, inst.hi, inst.l, inst.u)
+        ev = o.evaluate(B.primal(b) / o.C, np.zeros(inst.m))
+        assert ev.eps_p <= 1.2e-4, (b, ev.eps_p)
+    B.close()
+
+
+@pytest.fixture(scope="module")
+def fan():
+    """The fan-out workload of bench.py: m = 200k, n = 500k, 5M nonzeros, K = 64 targets
+    around the rounded warm start (FP64 fixed-step base for the parity case)."""
+    from paper_2307_03466_gb300 import scylla as S
+    inst = I.fanout_base()
+    return S, inst
+
+
+def fan_targets(S, inst, base):
+    base.pdhg_solve(1e-3, 20000)
+    x = base.primal()
+    target = x.copy()
+    ic = inst.is_int == 1
+    target[ic] = np.floor(x[ic] + 0.5)
+    return I.fanout_targets(inst, target, K=64, flip_frac=0.10), base.get_state()
+
+
+def test_fanout_bench_size_fixed_step_sampled_objectives_match_oracle(fan):
+    S, inst = fan
+    base = S.LP.from_instance(inst, S.default_params(aux_general_integers=0, adaptive_step=0, restarts=0))
+    targets, state = fan_targets(S, inst, base)
+    F = S.Fanout(base, targets, round_K=1)
+    res, _ = F.solve(0.0, 4)
+    assert all(r.iterations == 4 for r in res)
+    o = O.OracleLP(inst.csr(), inst.c, inst.lo, inst.hi, inst.l, inst.u,
+                   params=O.PdhgParams(adaptive_step=False, restarts=False))
+    for q in (0, 31, 63):
+        chat, _, off = P.objective_update(inst.c, inst.is_int, inst.l, inst.u, targets[:, q], 1, [])
+        o.set_objective_vector(chat, off)
+        o.set_state(state[0], state[1])
+        o.eta, o.omega = state[2], state[3]
+        o.solve(0.0, 4)
+        assert rel_err(F.primal(q), o.primal()) <= 1e-9, q
+    F.close()
+    base.close()
+
+
+def test_fanout_bench_size_mixed_all_converge_primal_checked_by_oracle(fan):
+    S, inst = fan
+    base = S.LP.from_instance(inst, S.default_params(precision=S.PREC_MIXED, aux_general_integers=0))
+    targets, _ = fan_targets(S, inst, base)
+    F = S.Fanout(base, targets, round_K=1)
+    res, _ = F.solve(1e-4, 200000)
+    assert all(r.status == O.CONVERGED and r.rel_kkt <= 1e-4 for r in res)
+    o = O.OracleLP(inst.csr(), inst.c, inst.lo, inst.hi, inst.l, inst.u)
+    for q in (0, 63):
+        ev = o.evaluate(F.primal(q) / o.C, np.zeros(inst.m))
+        assert ev.eps_p <= 1.2e-4, (q, ev.eps_p)
+    F.close()
+    base.close()
