@@ -63,12 +63,14 @@ struct Propagator {
     int64_t j;
     double lb, ub;
   };
+  std::vector<Change> changes;  // of the row being visited (kept to reuse its storage)
 
   void visit(int32_t i) {
     const double lo = lp.lo0[i], hi = lp.hi0[i];
     if (lo == -kInf && hi == kInf) return;
     const int64_t p0 = lp.rowptr0[i], p1 = lp.rowptr0[i + 1];
     double minf = 0.0, maxf = 0.0;
+    double span = 0.0;  // largest |a_j| (u_j - l_j) of the row (+inf with an unbounded domain)
     int nmin = 0, nmax = 0;
     for (int64_t p = p0; p < p1; ++p) {
       const int64_t j = lp.cols0[p];
@@ -79,6 +81,7 @@ struct Propagator {
       else minf += a * bmin;
       if (std::isinf(bmax)) nmax++;
       else maxf += a * bmax;
+      span = std::max(span, std::fabs(a) * (du[j] - dl[j]));
     }
     if (nmin == 0 && hi != kInf && minf > hi + 1e-9) {
       ignored[i] = 1;
@@ -88,7 +91,24 @@ struct Propagator {
       ignored[i] = 1;
       return;
     }
-    std::vector<Change> changes;
+    // A side can tighten a bound only with exactly one unbounded contribution, or when
+    // its slack (hi - minact, maxact - lo) is within the largest single-column span:
+    // column j's candidate lies (slack - |a_j| (u_j - l_j)) / |a_j| beyond its own
+    // bound.  When both sides' slacks exceed the span by a relative margin of 1e-6
+    // (far above the rounding of the candidate arithmetic, which the integer rounding
+    // slack of 1e-6 and the continuous threshold of 1e-3 cover again) no candidate can
+    // change a domain, and the visit ends here with the same result.
+    {
+      constexpr double kMarg = 1e-6;
+      const bool hi_side =
+          hi != kInf && (nmin == 1 || (nmin == 0 && !((hi - minf) > span * (1.0 + kMarg) +
+                                                                     kMarg * (1.0 + std::fabs(hi) + std::fabs(minf)))));
+      const bool lo_side =
+          lo != -kInf && (nmax == 1 || (nmax == 0 && !((maxf - lo) > span * (1.0 + kMarg) +
+                                                                       kMarg * (1.0 + std::fabs(lo) + std::fabs(maxf)))));
+      if (!hi_side && !lo_side) return;
+    }
+    changes.clear();
     for (int64_t p = p0; p < p1; ++p) {
       const int64_t j = lp.cols0[p];
       const double a = lp.vals0[p];
