@@ -45,8 +45,69 @@ struct Propagator {
   std::vector<uint8_t> ignored, inq;
   std::deque<int32_t> queue;
 
+  // Per row, the activity data of its last full visit (finite parts of the minimum and
+  // maximum activity, counts of unbounded contributions, largest column span), kept
+  // current by every later bound change of its columns (upd counts those updates).
+  // It only decides whether a visit can end early; a visit that goes on recomputes
+  // everything from scratch in CSR order.
+  struct RowCache {
+    double minf, maxf, span;
+    int nmin, nmax, upd;
+    bool valid;
+  };
+  std::vector<RowCache> cache;
+
   explicit Propagator(const scylla_lp& h)
-      : lp(h), dl(h.l0), du(h.u0), ignored(h.m0, 0), inq(h.m0, 0) {}
+      : lp(h), dl(h.l0), du(h.u0), ignored(h.m0, 0), inq(h.m0, 0),
+        cache(size_t(h.m0), RowCache{0.0, 0.0, 0.0, 0, 0, 0, false}) {}
+
+  // column j's domain moved from (ol, ou) to (dl[j], du[j]) (tightened): update the
+  // cached activity data of its rows; the span is left as an upper bound
+  void bounds_changed(int64_t j, double ol, double ou) {
+    const double nl = dl[j], nu = du[j];
+    for (int64_t q = lp.colptr0[j]; q < lp.colptr0[j + 1]; ++q) {
+      RowCache& c = cache[size_t(lp.colrows0[q])];
+      if (!c.valid) continue;
+      const double a = lp.colvals0[q];
+      const double bo = a > 0 ? ol : ou, bn = a > 0 ? nl : nu;
+      const double co = a > 0 ? ou : ol, cn = a > 0 ? nu : nl;
+      if (bo != bn) {
+        if (std::isinf(bo)) {
+          c.nmin--;
+          c.minf += a * bn;
+        } else {
+          c.minf += a * (bn - bo);
+        }
+      }
+      if (co != cn) {
+        if (std::isinf(co)) {
+          c.nmax--;
+          c.maxf += a * cn;
+        } else {
+          c.maxf += a * (cn - co);
+        }
+      }
+      c.upd++;
+    }
+  }
+
+  // A side can tighten a bound only with exactly one unbounded contribution, or when
+  // its slack (hi - minact, maxact - lo) is within the largest single-column span:
+  // column j's candidate lies (slack - |a_j| (u_j - l_j)) / |a_j| beyond its own
+  // bound.  True when both sides' slacks exceed the span by a relative margin of
+  // 1e-6 (far above the rounding of the candidate arithmetic and of the cached sums,
+  // which the integer rounding slack of 1e-6 and the continuous threshold of 1e-3
+  // cover again): then no candidate can change a domain.
+  static bool screened(double lo, double hi, double minf, double maxf, int nmin, int nmax, double span) {
+    constexpr double kMarg = 1e-6;
+    const bool hi_side =
+        hi != kInf && (nmin == 1 || (nmin == 0 && !((hi - minf) > span * (1.0 + kMarg) +
+                                                                   kMarg * (1.0 + std::fabs(hi) + std::fabs(minf)))));
+    const bool lo_side =
+        lo != -kInf && (nmax == 1 || (nmax == 0 && !((maxf - lo) > span * (1.0 + kMarg) +
+                                                                     kMarg * (1.0 + std::fabs(lo) + std::fabs(maxf)))));
+    return !hi_side && !lo_side;
+  }
 
   void push(int32_t i) {
     if (!inq[i] && !ignored[i]) {
@@ -68,6 +129,12 @@ struct Propagator {
   void visit(int32_t i) {
     const double lo = lp.lo0[i], hi = lp.hi0[i];
     if (lo == -kInf && hi == kInf) return;
+    {
+      // the cached data, at most 64 updates old (their rounding stays far below the
+      // screen's margin), can end the visit without reading the row
+      const RowCache& c = cache[size_t(i)];
+      if (c.valid && c.upd < 64 && screened(lo, hi, c.minf, c.maxf, c.nmin, c.nmax, c.span)) return;
+    }
     const int64_t p0 = lp.rowptr0[i], p1 = lp.rowptr0[i + 1];
     double minf = 0.0, maxf = 0.0;
     double span = 0.0;  // largest |a_j| (u_j - l_j) of the row (+inf with an unbounded domain)
@@ -91,23 +158,8 @@ struct Propagator {
       ignored[i] = 1;
       return;
     }
-    // A side can tighten a bound only with exactly one unbounded contribution, or when
-    // its slack (hi - minact, maxact - lo) is within the largest single-column span:
-    // column j's candidate lies (slack - |a_j| (u_j - l_j)) / |a_j| beyond its own
-    // bound.  When both sides' slacks exceed the span by a relative margin of 1e-6
-    // (far above the rounding of the candidate arithmetic, which the integer rounding
-    // slack of 1e-6 and the continuous threshold of 1e-3 cover again) no candidate can
-    // change a domain, and the visit ends here with the same result.
-    {
-      constexpr double kMarg = 1e-6;
-      const bool hi_side =
-          hi != kInf && (nmin == 1 || (nmin == 0 && !((hi - minf) > span * (1.0 + kMarg) +
-                                                                     kMarg * (1.0 + std::fabs(hi) + std::fabs(minf)))));
-      const bool lo_side =
-          lo != -kInf && (nmax == 1 || (nmax == 0 && !((maxf - lo) > span * (1.0 + kMarg) +
-                                                                       kMarg * (1.0 + std::fabs(lo) + std::fabs(maxf)))));
-      if (!hi_side && !lo_side) return;
-    }
+    cache[size_t(i)] = RowCache{minf, maxf, span, nmin, nmax, 0, true};
+    if (screened(lo, hi, minf, maxf, nmin, nmax, span)) return;  // no candidate can change a domain
     changes.clear();
     for (int64_t p = p0; p < p1; ++p) {
       const int64_t j = lp.cols0[p];
@@ -155,8 +207,10 @@ struct Propagator {
       changes.push_back({j, nlb, nub});
     }
     for (const Change& c : changes) {
+      const double ol = dl[c.j], ou = du[c.j];
       dl[c.j] = c.lb;
       du[c.j] = c.ub;
+      bounds_changed(c.j, ol, ou);
     }
     for (const Change& c : changes) push_rows_of(c.j);
   }
@@ -263,8 +317,10 @@ int fix_and_propagate_host(const scylla_lp& lp, const double* xbar, double* xhat
     if (pr.dl[j] == pr.du[j]) continue;
     double v = round_half_up(xbar[j]);
     v = std::min(std::max(v, pr.dl[j]), pr.du[j]);
+    const double ol = pr.dl[j], ou = pr.du[j];
     pr.dl[j] = v;
     pr.du[j] = v;
+    pr.bounds_changed(j, ol, ou);
     if (fixed_cols) fixed_cols[nf] = int32_t(j);
     ++nf;
     pr.push_rows_of(j);

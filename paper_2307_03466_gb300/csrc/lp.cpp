@@ -253,7 +253,7 @@ int scylla_lp::ensure_host_matrix() const {
 void scylla_lp::ensure_columns() const {
   if (columns_ready) return;
   if (ensure_host_matrix() != SCYLLA_OK) return;
-  scylla::transpose_csr(m0, n0, rowptr0.data(), cols0.data(), nullptr, colptr0, colrows0, nullptr);
+  scylla::transpose_csr(m0, n0, rowptr0.data(), cols0.data(), vals0.data(), colptr0, colrows0, &colvals0);
   columns_ready = true;
 }
 

@@ -35,6 +35,7 @@ struct scylla_lp {
   // the host propagation; built on first use by ensure_columns()
   mutable std::vector<int64_t> colptr0;
   mutable std::vector<int32_t> colrows0;
+  mutable std::vector<double> colvals0;  // the values in the same order
   mutable bool columns_ready = false;
   void ensure_columns() const;
   double c0norm = 0.0;
