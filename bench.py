@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-repair", action="store_true", help="skip the continuous-repair section")
     ap.add_argument("--no-l2", action="store_true", help="skip the l2-distance (diagonal QP) section")
     ap.add_argument("--no-propagate", action="store_true", help="skip the bound-propagation section")
+    ap.add_argument("--no-heuristic", action="store_true", help="skip the whole-heuristic section")
     return ap.parse_args()
 
 
@@ -326,6 +327,9 @@ def run_ours(args):
     prop = None
     if rank == 0 and not args.no_propagate:
         prop = propagate_section(mixed, inst)
+    heur = None
+    if rank == 0 and not args.no_heuristic:
+        heur = heuristic_section(S, inst, ref)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -383,6 +387,7 @@ def run_ours(args):
         "repair": repair,
         "l2_objective": l2,
         "propagation": prop,
+        "heuristic": heur,
     }
     return out
 
@@ -411,6 +416,30 @@ def repair_section(S, mixed, inst):
             "seconds": r.seconds,
             "iter_per_s": r.iterations / r.seconds if r.seconds > 0 else None, "rel_kkt": r.rel_kkt,
             "objective": r.objective, "first_call_wall_s": first_wall}
+
+
+def heuristic_section(S, inst, ref_obj):
+    """The whole heuristic (scylla_run, Algorithm 1) on the bench workload, FP32-mixed
+    PDHG: as the paper describes it, and with the continuous repair; wall time of the
+    call (handle creation excluded), rounds, and the found objective against the
+    LP relaxation's optimum."""
+    out = {"workload": WORKLOAD, "lp_optimum": ref_obj}
+    for name, extra in (("paper", {}), ("with_repair", {"repair_iters": 100000})):
+        lp = S.LP.from_instance(inst, S.default_params(precision=S.PREC_MIXED, max_rounds=20, iter_limit=20000,
+                                                       **extra))
+        t0 = time.perf_counter()
+        r, x = lp.run()
+        wall = time.perf_counter() - t0
+        d = {"found": r.status == 0, "found_by": int(r.found_by), "rounds": int(r.rounds),
+             "pdhg_attempts": int(r.total_iterations), "wall_s": wall, "seconds_pdhg": r.seconds_pdhg,
+             "seconds_fixprop": r.seconds_fixprop}
+        if r.status == 0:
+            d["objective"] = r.objective
+            if ref_obj:
+                d["gap_to_lp_bound"] = abs(r.objective - ref_obj) / max(1.0, abs(ref_obj))
+        out[name] = d
+        lp.close()
+    return out
 
 
 def propagate_section(mixed, inst):
