@@ -1,0 +1,128 @@
+"""The library's host fix-and-propagate (Section 2.3), run on the CPU through the
+built library on a handle whose host copies are filled directly (no device work is
+involved), against the oracle bit for bit: the rounded point, the final domains,
+the fixed columns in fixing order and the ignored rows.  The instances include rows
+long enough, and slack enough, for the propagation's slack screen and row-activity
+caches to end most visits early, so these check that the shortcuts change nothing."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import fixprop as F
+from paper_2307_03466_gb300 import build as B
+from paper_2307_03466_gb300 import instances as I
+from tests.gpu_common import long_row_instance
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_2307_03466_gb300", "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+CUDA_INC = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+
+HARNESS = r"""
+#include <cstdio>
+#include <vector>
+#include "lp_handle.h"
+namespace scylla {
+int fix_and_propagate_host(const scylla_lp& lp, const double* xbar, double* xhat, double* dom_lo, double* dom_hi,
+                           int32_t* fixed_cols, int64_t* n_fixed, uint8_t* ignored_rows);
+}
+template <typename T> static std::vector<T> rd(const char* dir, const char* name, size_t n) {
+  char f[1024]; snprintf(f, sizeof f, "%s/%s", dir, name);
+  std::vector<T> v(n); FILE* fp = fopen(f, "rb");
+  if (!fp || fread(v.data(), sizeof(T), n, fp) != n) { fprintf(stderr, "read %s\n", f); exit(2); }
+  fclose(fp); return v;
+}
+template <typename T> static void wr(const char* dir, const char* name, const T* p, size_t n) {
+  char f[1024]; snprintf(f, sizeof f, "%s/%s", dir, name);
+  FILE* fp = fopen(f, "wb"); fwrite(p, sizeof(T), n, fp); fclose(fp);
+}
+int main(int argc, char** argv) {
+  const char* d = argv[1];
+  auto dims = rd<int64_t>(d, "dims", 3);
+  scylla_lp lp;
+  lp.m0 = dims[0]; lp.n0 = dims[1]; lp.nnz0 = dims[2];
+  lp.rowptr0 = rd<int64_t>(d, "rowptr", size_t(lp.m0 + 1));
+  lp.cols0 = rd<int32_t>(d, "cols", size_t(lp.nnz0));
+  lp.vals0 = rd<double>(d, "vals", size_t(lp.nnz0));
+  lp.host_matrix_ready = true;
+  lp.c0.assign(size_t(lp.n0), 0.0);
+  lp.lo0 = rd<double>(d, "lo", size_t(lp.m0)); lp.hi0 = rd<double>(d, "hi", size_t(lp.m0));
+  lp.l0 = rd<double>(d, "l", size_t(lp.n0)); lp.u0 = rd<double>(d, "u", size_t(lp.n0));
+  lp.int0 = rd<uint8_t>(d, "int", size_t(lp.n0));
+  lp.host_vectors_ready = true;
+  lp.n_int = 0; for (auto v : lp.int0) lp.n_int += v;
+  auto xbar = rd<double>(d, "xbar", size_t(lp.n0));
+  std::vector<double> xhat(lp.n0), dl(lp.n0), du(lp.n0);
+  std::vector<int32_t> fixed(lp.n0);
+  std::vector<uint8_t> ign(lp.m0 > 0 ? lp.m0 : 1);
+  int64_t nf = 0;
+  const int rc = scylla::fix_and_propagate_host(lp, xbar.data(), xhat.data(), dl.data(), du.data(), fixed.data(), &nf,
+                                                ign.data());
+  if (rc != 0) { fprintf(stderr, "rc %d\n", rc); return 3; }
+  wr(d, "o_xhat", xhat.data(), xhat.size()); wr(d, "o_dl", dl.data(), dl.size()); wr(d, "o_du", du.data(), du.size());
+  wr(d, "o_fixed", fixed.data(), size_t(nf)); wr(d, "o_ign", ign.data(), size_t(lp.m0));
+  wr(d, "o_nf", &nf, 1);
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    cxx = shutil.which("g++")
+    if cxx is None or not os.path.isdir(CUDA_INC):
+        pytest.skip("needs g++ and the CUDA headers")
+    lib = B.build()
+    d = tmp_path_factory.mktemp("fp")
+    src = d / "h.cpp"
+    exe = d / "h"
+    src.write_text(HARNESS)
+    subprocess.run([cxx, "-O2", "-std=c++17", "-I", CSRC, "-I", INCLUDE, "-I", CUDA_INC, str(src), "-o", str(exe),
+                    lib, "-Wl,-rpath," + os.path.dirname(lib)], check=True)
+    return str(exe)
+
+
+def run_harness(exe, inst, xbar, d):
+    os.makedirs(d, exist_ok=True)
+    np.asarray([inst.m, inst.n, len(inst.vals)], np.int64).tofile(os.path.join(d, "dims"))
+    np.asarray(inst.rowptr, np.int64).tofile(os.path.join(d, "rowptr"))
+    np.asarray(inst.cols, np.int32).tofile(os.path.join(d, "cols"))
+    np.asarray(inst.vals, np.float64).tofile(os.path.join(d, "vals"))
+    for k in ("lo", "hi", "l", "u"):
+        np.asarray(getattr(inst, k), np.float64).tofile(os.path.join(d, k))
+    np.asarray(inst.is_int, np.uint8).tofile(os.path.join(d, "int"))
+    np.asarray(xbar, np.float64).tofile(os.path.join(d, "xbar"))
+    r = subprocess.run([exe, d], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    nf = int(np.fromfile(os.path.join(d, "o_nf"), np.int64)[0])
+    return (np.fromfile(os.path.join(d, "o_xhat")), np.fromfile(os.path.join(d, "o_dl")),
+            np.fromfile(os.path.join(d, "o_du")), np.fromfile(os.path.join(d, "o_fixed"), np.int32)[:nf],
+            np.fromfile(os.path.join(d, "o_ign"), np.uint8).astype(bool))
+
+
+INSTANCES = {
+    "setcover": lambda: I.set_cover(),
+    "knapcover": lambda: I.knapsack_cover(300, seed=8),
+    "packcover_gen_int": lambda: I.packing_covering(m=300, n=600, per_col=4, seed=21),
+    "packcover_2kx4k": lambda: I.packing_covering(m=2000, n=4000, per_col=10, seed=11),
+    "mcf_small": lambda: I.mcf(nodes=20, avg_degree=4, commodities=6, seed=2),
+    "long_rows": lambda: long_row_instance(),
+}
+
+
+@pytest.mark.parametrize("name", list(INSTANCES))
+def test_host_fix_and_propagate_equals_oracle(harness, tmp_path, name):
+    inst = INSTANCES[name]()
+    rng = np.random.default_rng(17)
+    lo_b = np.where(np.isfinite(inst.l), inst.l, -5.0)
+    hi_b = np.where(np.isfinite(inst.u), inst.u, lo_b + 10.0)
+    xbar = rng.uniform(lo_b, hi_b)
+    xhat, dl, du, fixed, ign = run_harness(harness, inst, xbar, str(tmp_path / name))
+    oxhat, odl, odu, ofixed, oign = F.fix_and_propagate(inst.rowptr, inst.cols, inst.vals, inst.lo, inst.hi,
+                                                        inst.l, inst.u, inst.is_int, xbar)
+    assert np.array_equal(xhat, oxhat) and np.array_equal(dl, odl) and np.array_equal(du, odu)
+    assert np.array_equal(fixed, ofixed) and np.array_equal(ign, oign)
