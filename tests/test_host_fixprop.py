@@ -1,7 +1,8 @@
-"""The library's host fix-and-propagate (Section 2.3), run on the CPU through the
-built library on a handle whose host copies are filled directly (no device work is
-involved), against the oracle bit for bit: the rounded point, the final domains,
-the fixed columns in fixing order and the ignored rows.  The instances include rows
+"""The library's host rounding steps, run on the CPU through the built library on a
+handle whose host copies are filled directly (no device work is involved), against
+the oracle: fix-and-propagate (Section 2.3) bit for bit (the rounded point, the
+final domains, the fixed columns in fixing order and the ignored rows), the exact
+MIP-feasibility test and the cycle perturbation.  The instances include rows
 long enough, and slack enough, for the propagation's slack screen and row-activity
 caches to end most visits early, so these check that the shortcuts change nothing."""
 import os
@@ -24,11 +25,13 @@ CUDA_INC = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include
 
 HARNESS = r"""
 #include <cstdio>
+#include <string>
 #include <vector>
 #include "lp_handle.h"
 namespace scylla {
 int fix_and_propagate_host(const scylla_lp& lp, const double* xbar, double* xhat, double* dom_lo, double* dom_hi,
                            int32_t* fixed_cols, int64_t* n_fixed, uint8_t* ignored_rows);
+int64_t perturb_host(const scylla_lp& lp, double* x, const double* xbar, int kind, int64_t K, uint64_t seed);
 }
 template <typename T> static std::vector<T> rd(const char* dir, const char* name, size_t n) {
   char f[1024]; snprintf(f, sizeof f, "%s/%s", dir, name);
@@ -56,6 +59,24 @@ int main(int argc, char** argv) {
   lp.host_vectors_ready = true;
   lp.n_int = 0; for (auto v : lp.int0) lp.n_int += v;
   auto xbar = rd<double>(d, "xbar", size_t(lp.n0));
+  const std::string mode = argc > 2 ? argv[2] : "fixprop";
+  if (mode == "check") {
+    // points in "pts" (npts x n): one verdict byte each
+    auto np_ = rd<int64_t>(d, "npts", 1);
+    auto pts = rd<double>(d, "pts", size_t(np_[0] * lp.n0));
+    std::vector<uint8_t> v(static_cast<size_t>(np_[0]));
+    for (int64_t k = 0; k < np_[0]; ++k) v[size_t(k)] = scylla::check_feasible_host(lp, pts.data() + k * lp.n0) ? 1 : 0;
+    wr(d, "o_check", v.data(), v.size());
+    return 0;
+  }
+  if (mode == "perturb") {
+    auto args = rd<int64_t>(d, "pargs", 3);  // kind, K, seed
+    auto x = rd<double>(d, "xhat", size_t(lp.n0));
+    const int64_t fl = scylla::perturb_host(lp, x.data(), xbar.data(), int(args[0]), args[1], uint64_t(args[2]));
+    wr(d, "o_pert", x.data(), x.size());
+    wr(d, "o_flipped", &fl, 1);
+    return 0;
+  }
   std::vector<double> xhat(lp.n0), dl(lp.n0), du(lp.n0);
   std::vector<int32_t> fixed(lp.n0);
   std::vector<uint8_t> ign(lp.m0 > 0 ? lp.m0 : 1);
@@ -86,7 +107,7 @@ def harness(tmp_path_factory):
     return str(exe)
 
 
-def run_harness(exe, inst, xbar, d):
+def write_instance(inst, xbar, d):
     os.makedirs(d, exist_ok=True)
     np.asarray([inst.m, inst.n, len(inst.vals)], np.int64).tofile(os.path.join(d, "dims"))
     np.asarray(inst.rowptr, np.int64).tofile(os.path.join(d, "rowptr"))
@@ -96,6 +117,10 @@ def run_harness(exe, inst, xbar, d):
         np.asarray(getattr(inst, k), np.float64).tofile(os.path.join(d, k))
     np.asarray(inst.is_int, np.uint8).tofile(os.path.join(d, "int"))
     np.asarray(xbar, np.float64).tofile(os.path.join(d, "xbar"))
+
+
+def run_harness(exe, inst, xbar, d):
+    write_instance(inst, xbar, d)
     r = subprocess.run([exe, d], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr
     nf = int(np.fromfile(os.path.join(d, "o_nf"), np.int64)[0])
@@ -126,3 +151,56 @@ def test_host_fix_and_propagate_equals_oracle(harness, tmp_path, name):
                                                         inst.l, inst.u, inst.is_int, xbar)
     assert np.array_equal(xhat, oxhat) and np.array_equal(dl, odl) and np.array_equal(du, odu)
     assert np.array_equal(fixed, ofixed) and np.array_equal(ign, oign)
+
+
+@pytest.mark.parametrize("name", ["setcover", "knapcover", "packcover_gen_int", "mcf_small", "long_rows"])
+def test_host_feasibility_check_equals_oracle(harness, tmp_path, name):
+    """The exact MIP-feasibility test (Algorithm 1's two tests) on random integral
+    points, the all-zero and all-one points and the generator's interior point."""
+    from oracle import pump as P
+    inst = INSTANCES[name]()
+    rng = np.random.default_rng(1)
+    hi_b = np.where(np.isfinite(inst.u), inst.u, inst.l + 10)
+    pts = [np.ones(inst.n), np.zeros(inst.n)]
+    for _ in range(20):
+        x = rng.uniform(inst.l, np.minimum(hi_b, inst.l + 10))
+        x[inst.is_int == 1] = np.round(x[inst.is_int == 1])
+        pts.append(x)
+    if "x0" in inst.meta:
+        pts.append(inst.meta["x0"])
+    d = str(tmp_path / name)
+    write_instance(inst, np.zeros(inst.n), d)
+    np.asarray([len(pts)], np.int64).tofile(os.path.join(d, "npts"))
+    np.asarray(pts, np.float64).tofile(os.path.join(d, "pts"))
+    r = subprocess.run([harness, d, "check"], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    got = np.fromfile(os.path.join(d, "o_check"), np.uint8).astype(bool)
+    want = [P.check_feasible(inst.rowptr, inst.cols, inst.vals, inst.lo, inst.hi, inst.l, inst.u, inst.is_int, x)
+            for x in pts]
+    assert list(got) == want
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+@pytest.mark.parametrize("K", [1, 2, 17])
+def test_host_perturbation_equals_oracle(harness, tmp_path, kind, K):
+    """Cycle handling (Section 2.3): the short- and long-cycle flips with the
+    SplitMix64 stream of the round."""
+    from oracle import pump as P
+    inst = I.packing_covering(m=200, n=400, per_col=3, seed=4)
+    rng = np.random.default_rng(K)
+    xbar = rng.uniform(inst.l, np.minimum(inst.u, 10))
+    xhat = xbar.copy()
+    ic = np.nonzero(inst.is_int)[0]
+    xhat[ic] = np.floor(xbar[ic] + 0.5)
+    key = tuple(float(xhat[j]) for j in ic)
+    hist = [key] if kind == 1 else [key, tuple(v + 1 for v in key)]
+    xo, _ = P.perturb(xhat, xbar, hist, K, 12345, list(ic), inst.l, inst.u)
+    d = str(tmp_path / f"p{kind}_{K}")
+    write_instance(inst, xbar, d)
+    np.asarray(xhat, np.float64).tofile(os.path.join(d, "xhat"))
+    np.asarray([kind, K, 12345], np.int64).tofile(os.path.join(d, "pargs"))
+    r = subprocess.run([harness, d, "perturb"], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    xg = np.fromfile(os.path.join(d, "o_pert"))
+    assert np.array_equal(xg, xo)
+    assert int(np.fromfile(os.path.join(d, "o_flipped"), np.int64)[0]) == int(np.sum(xg != xhat))
