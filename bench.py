@@ -462,11 +462,24 @@ def propagate_section(mixed, inst):
         out[name] = {"ms": 1e3 * best, "rounds": int(rounds), "conflicts": int(conflicts),
                      "ignored_rows": int(ign.sum()), "columns_tightened": int(np.sum((dl > dl0) | (du < du0)))}
     # for context: the host's sequential fix-and-propagate of the LP point (Section 2.3:
-    # every integer column fixed in turn, each fix propagated by the FIFO queue)
+    # every integer column fixed in turn, each fix propagated by the FIFO queue).  The
+    # handle keeps the end state of the first propagation (bounds alone) until its
+    # bounds change, so a pump's first round pays it and later rounds do not: setting
+    # the same column bounds drops it, the next call is timed as a first round, and the
+    # best of 3 further calls as a later round.
     xbar = mixed.primal()
+    mixed.set_col_bounds(inst.l, inst.u)
     t0 = time.perf_counter()
     _, _, _, fixed, _ = mixed.fix_and_propagate(xbar)
-    out["host_fix_and_propagate"] = {"ms": 1e3 * (time.perf_counter() - t0), "columns_fixed": int(len(fixed))}
+    first = time.perf_counter() - t0
+    later = None
+    for _ in range(3):
+        t0 = time.perf_counter()
+        mixed.fix_and_propagate(xbar)
+        dt = time.perf_counter() - t0
+        later = dt if later is None else min(later, dt)
+    out["host_fix_and_propagate"] = {"ms": 1e3 * later, "ms_first_call": 1e3 * first,
+                                     "columns_fixed": int(len(fixed))}
     return out
 
 

@@ -223,7 +223,7 @@ int scylla_get_objective(const scylla_lp* lp, double* c_hat, double* offset);
  * point that fails the test is given to scylla_repair (p.repair_tol, p.repair_iters)
  * before the cycle handling.  x_out (host, length n original) receives the solution
  * when out->status == SCYLLA_FOUND; every returned point passed
- * scylla_check_feasible.  Errors: INVALID_ARG, CUDA, TIMEOUT (time limit hit). */
+ * scylla_check_feasible.  Errors: INVALID_ARG, OOM (host), CUDA, TIMEOUT (time limit hit). */
 int scylla_run(scylla_lp* lp, double* x_out, scylla_run_result* out);
 
 /* Current primal point, unscaled: host length n (original columns). */
@@ -266,12 +266,18 @@ int scylla_get_transpose(const scylla_lp* lp, int64_t* colptr, int32_t* rows, do
  *   fixed_cols: host output, length n (may be NULL), receives the columns fixed
  *   by rounding in fixing order; *n_fixed their count (may be NULL).
  *   ignored_rows: host output, length m (may be NULL), 1 for rows ignored after
- *   emptying a domain. */
+ *   emptying a domain.
+ * The first call keeps, in the handle, the end state of the propagation of the
+ * bounds alone (it depends only on the MIP); later calls start from it, with the
+ * same results, until scylla_set_col_bounds or scylla_set_row_bounds drops it.
+ * Errors: INVALID_ARG (null lp, xbar or xhat; NaN in xbar), OOM (host), CUDA (first
+ * download of the host copies). */
 int scylla_fix_and_propagate(const scylla_lp* lp, const double* xbar, double* xhat, double* dom_lo,
                              double* dom_hi, int32_t* fixed_cols, int64_t* n_fixed, uint8_t* ignored_rows);
 
 /* Exact MIP-feasibility test of x (host, length n) on the original MIP
- * (Algorithm 1, both "MIP-feasible" tests): *feasible = 1 or 0. */
+ * (Algorithm 1, both "MIP-feasible" tests): *feasible = 1 or 0.
+ * Errors: INVALID_ARG (null), OOM (host), CUDA (first download of the host copies). */
 int scylla_check_feasible(const scylla_lp* lp, const double* x, int32_t* feasible);
 
 /* Replace the bounds of the original columns (host, length n each), keeping the
@@ -338,7 +344,9 @@ int scylla_repair(scylla_lp* lp, const double* xhat, double tol, int64_t iter_li
 
 /* Cycle handling of Section 2.3 on its own.  kind: 1 short cycle, 2 long cycle.
  * xhat: host in/out, length n; xbar: host, length n; K: round; seed: stream seed.
- * *flipped (may be NULL) receives the number of changed entries. */
+ * *flipped (may be NULL) receives the number of changed entries.
+ * Errors: INVALID_ARG (null, kind not 1 or 2), OOM (host), CUDA (first download of
+ * the host copies). */
 int scylla_perturb(const scylla_lp* lp, double* xhat, const double* xbar, int32_t kind, int64_t K,
                    uint64_t seed, int64_t* flipped);
 

@@ -21,12 +21,17 @@
 // rows of each changed column are queued (ascending, unless queued or ignored).  One
 // propagation stops after 20 m + 1000 row visits.  Finally every column takes its
 // reference value projected onto its domain.
+//
+// The first propagation (every row queued once, before any fixing) depends only on
+// the MIP, so its end state is kept in the handle and reused by later calls until the
+// handle's bounds change.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
-#include <deque>
 #include <limits>
+#include <memory>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -41,53 +46,95 @@ const double kInf = std::numeric_limits<double>::infinity();
 
 struct Propagator {
   const scylla_lp& lp;
-  std::vector<double> dl, du;
-  std::vector<uint8_t> ignored, inq;
-  std::deque<int32_t> queue;
 
-  // Per row, the activity data of its last full visit (finite parts of the minimum and
-  // maximum activity, counts of unbounded contributions, largest column span), kept
-  // current by every later bound change of its columns (upd counts those updates).
-  // It only decides whether a visit can end early; a visit that goes on recomputes
-  // everything from scratch in CSR order.
-  struct RowCache {
-    double minf, maxf, span;
-    int nmin, nmax, upd;
-    bool valid;
+  // a column's domain, both bounds on one line
+  struct Dom {
+    double lb, ub;
   };
-  std::vector<RowCache> cache;
+  std::vector<Dom> dom;
 
-  explicit Propagator(const scylla_lp& h)
-      : lp(h), dl(h.l0), du(h.u0), ignored(h.m0, 0), inq(h.m0, 0),
-        cache(size_t(h.m0), RowCache{0.0, 0.0, 0.0, 0, 0, 0, false}) {}
+  // Everything a visit or a queue operation touches for row i, on one 64-byte line:
+  // its bounds, its queue and ignored flags, and the activity data of its last full
+  // visit (finite parts of the minimum and maximum activity, counts of unbounded
+  // contributions, largest column span), kept current by every later bound change of
+  // its columns (upd counts those updates).  The activity data only decides whether a
+  // visit can end early; a visit that goes on recomputes everything from scratch in
+  // CSR order.
+  struct alignas(64) Row {
+    double lo, hi;
+    double minf, maxf, span;
+    int32_t nmin, nmax, upd;
+    uint8_t valid, inq, ignored;
+  };
+  std::vector<Row> rows;
 
-  // column j's domain moved from (ol, ou) to (dl[j], du[j]) (tightened): update the
-  // cached activity data of its rows; the span is left as an upper bound
-  void bounds_changed(int64_t j, double ol, double ou) {
-    const double nl = dl[j], nu = du[j];
+  // FIFO of rows; a row is queued at most once (inq), so m slots suffice
+  std::vector<int32_t> ring;
+  int64_t head = 0, count = 0;
+
+  explicit Propagator(const scylla_lp& h) : lp(h), dom(size_t(h.n0)), rows(size_t(h.m0)), ring(size_t(h.m0 > 0 ? h.m0 : 1)) {
+    for (int64_t j = 0; j < h.n0; ++j) dom[size_t(j)] = Dom{h.l0[size_t(j)], h.u0[size_t(j)]};
+    for (int64_t i = 0; i < h.m0; ++i) {
+      Row& r = rows[size_t(i)];
+      r = Row{};
+      r.lo = h.lo0[size_t(i)];
+      r.hi = h.hi0[size_t(i)];
+    }
+  }
+
+  // continue from the end state of an earlier propagation (queue empty)
+  Propagator(const scylla_lp& h, const std::vector<Dom>& d, const std::vector<Row>& r)
+      : lp(h), dom(d), rows(r), ring(size_t(h.m0 > 0 ? h.m0 : 1)) {}
+
+  void push(int32_t i) {
+    Row& r = rows[size_t(i)];
+    if (!r.inq && !r.ignored) {
+      r.inq = 1;
+      int64_t t = head + count;
+      if (t >= lp.m0) t -= lp.m0;
+      ring[size_t(t)] = i;
+      ++count;
+    }
+  }
+
+  int32_t pop() {
+    const int32_t i = ring[size_t(head)];
+    if (++head == lp.m0) head = 0;
+    --count;
+    return i;
+  }
+
+  // column j's domain moved from (ol, ou) to its current (tightened) one: update the
+  // cached activity data of its rows (the span is left as an upper bound) and queue
+  // them, in column order
+  void tightened(int64_t j, double ol, double ou) {
+    const double nl = dom[size_t(j)].lb, nu = dom[size_t(j)].ub;
     for (int64_t q = lp.colptr0[j]; q < lp.colptr0[j + 1]; ++q) {
-      RowCache& c = cache[size_t(lp.colrows0[q])];
-      if (!c.valid) continue;
-      const double a = lp.colvals0[q];
-      const double bo = a > 0 ? ol : ou, bn = a > 0 ? nl : nu;
-      const double co = a > 0 ? ou : ol, cn = a > 0 ? nu : nl;
-      if (bo != bn) {
-        if (std::isinf(bo)) {
-          c.nmin--;
-          c.minf += a * bn;
-        } else {
-          c.minf += a * (bn - bo);
+      const int32_t i = lp.colrows0[q];
+      Row& c = rows[size_t(i)];
+      if (c.valid) {
+        const double a = lp.colvals0[q];
+        const double bo = a > 0 ? ol : ou, bn = a > 0 ? nl : nu;
+        const double co = a > 0 ? ou : ol, cn = a > 0 ? nu : nl;
+        if (bo != bn) {
+          if (std::isinf(bo)) {
+            c.nmin--;
+            c.minf += a * bn;
+          } else {
+            c.minf += a * (bn - bo);
+          }
         }
-      }
-      if (co != cn) {
-        if (std::isinf(co)) {
-          c.nmax--;
-          c.maxf += a * cn;
-        } else {
-          c.maxf += a * (cn - co);
+        if (co != cn) {
+          if (std::isinf(co)) {
+            c.nmax--;
+            c.maxf += a * cn;
+          } else {
+            c.maxf += a * (cn - co);
+          }
         }
+        c.upd++;
       }
-      c.upd++;
+      push(i);
     }
   }
 
@@ -109,32 +156,20 @@ struct Propagator {
     return !hi_side && !lo_side;
   }
 
-  void push(int32_t i) {
-    if (!inq[i] && !ignored[i]) {
-      inq[i] = 1;
-      queue.push_back(i);
-    }
-  }
-
-  void push_rows_of(int64_t j) {
-    for (int64_t q = lp.colptr0[j]; q < lp.colptr0[j + 1]; ++q) push(lp.colrows0[q]);
-  }
-
   struct Change {
     int64_t j;
     double lb, ub;
   };
   std::vector<Change> changes;  // of the row being visited (kept to reuse its storage)
+  std::vector<Change> c_old;    // the same columns with their previous domains
 
   void visit(int32_t i) {
-    const double lo = lp.lo0[i], hi = lp.hi0[i];
+    Row& r = rows[size_t(i)];
+    const double lo = r.lo, hi = r.hi;
     if (lo == -kInf && hi == kInf) return;
-    {
-      // the cached data, at most 64 updates old (their rounding stays far below the
-      // screen's margin), can end the visit without reading the row
-      const RowCache& c = cache[size_t(i)];
-      if (c.valid && c.upd < 64 && screened(lo, hi, c.minf, c.maxf, c.nmin, c.nmax, c.span)) return;
-    }
+    // the cached data, at most 64 updates old (their rounding stays far below the
+    // screen's margin), can end the visit without reading the row
+    if (r.valid && r.upd < 64 && screened(lo, hi, r.minf, r.maxf, r.nmin, r.nmax, r.span)) return;
     const int64_t p0 = lp.rowptr0[i], p1 = lp.rowptr0[i + 1];
     double minf = 0.0, maxf = 0.0;
     double span = 0.0;  // largest |a_j| (u_j - l_j) of the row (+inf with an unbounded domain)
@@ -142,30 +177,38 @@ struct Propagator {
     for (int64_t p = p0; p < p1; ++p) {
       const int64_t j = lp.cols0[p];
       const double a = lp.vals0[p];
-      const double bmin = a > 0 ? dl[j] : du[j];
-      const double bmax = a > 0 ? du[j] : dl[j];
+      const Dom d = dom[size_t(j)];
+      const double bmin = a > 0 ? d.lb : d.ub;
+      const double bmax = a > 0 ? d.ub : d.lb;
       if (std::isinf(bmin)) nmin++;
       else minf += a * bmin;
       if (std::isinf(bmax)) nmax++;
       else maxf += a * bmax;
-      span = std::max(span, std::fabs(a) * (du[j] - dl[j]));
+      span = std::max(span, std::fabs(a) * (d.ub - d.lb));
     }
     if (nmin == 0 && hi != kInf && minf > hi + 1e-9) {
-      ignored[i] = 1;
+      r.ignored = 1;
       return;
     }
     if (nmax == 0 && lo != -kInf && maxf < lo - 1e-9) {
-      ignored[i] = 1;
+      r.ignored = 1;
       return;
     }
-    cache[size_t(i)] = RowCache{minf, maxf, span, nmin, nmax, 0, true};
+    r.minf = minf;
+    r.maxf = maxf;
+    r.span = span;
+    r.nmin = nmin;
+    r.nmax = nmax;
+    r.upd = 0;
+    r.valid = 1;
     if (screened(lo, hi, minf, maxf, nmin, nmax, span)) return;  // no candidate can change a domain
     changes.clear();
     for (int64_t p = p0; p < p1; ++p) {
       const int64_t j = lp.cols0[p];
       const double a = lp.vals0[p];
-      const double bmin = a > 0 ? dl[j] : du[j];
-      const double bmax = a > 0 ? du[j] : dl[j];
+      const Dom d = dom[size_t(j)];
+      const double bmin = a > 0 ? d.lb : d.ub;
+      const double bmax = a > 0 ? d.ub : d.lb;
       double rmin, rmax;
       if (std::isinf(bmin)) rmin = (nmin == 1) ? minf : -kInf;
       else rmin = (nmin == 0) ? (minf - a * bmin) : -kInf;
@@ -182,7 +225,7 @@ struct Propagator {
         if (a > 0) cand_lb = t;
         else cand_ub = t;
       }
-      const double old_lb = dl[j], old_ub = du[j];
+      const double old_lb = d.lb, old_ub = d.ub;
       double nlb = old_lb, nub = old_ub;
       if (lp.int0[j]) {
         if (cand_ub != kInf) {
@@ -201,31 +244,33 @@ struct Propagator {
       }
       if (nlb == old_lb && nub == old_ub) continue;
       if (nlb > nub + 1e-9) {
-        ignored[i] = 1;
+        r.ignored = 1;
         return;
       }
       changes.push_back({j, nlb, nub});
     }
+    // all changes are applied before any row is queued or its cache updated; both only
+    // read the new domains, so doing them column by column keeps the queue order
     for (const Change& c : changes) {
-      const double ol = dl[c.j], ou = du[c.j];
-      dl[c.j] = c.lb;
-      du[c.j] = c.ub;
-      bounds_changed(c.j, ol, ou);
+      Dom& d = dom[size_t(c.j)];
+      const double ol = d.lb, ou = d.ub;
+      d.lb = c.lb;
+      d.ub = c.ub;
+      c_old.push_back({c.j, ol, ou});
     }
-    for (const Change& c : changes) push_rows_of(c.j);
+    for (const Change& c : c_old) tightened(c.j, c.lb, c.ub);
+    c_old.clear();
   }
 
   void run() {
     const int64_t cap = 20 * lp.m0 + 1000;
     int64_t visits = 0;
-    while (!queue.empty()) {
-      const int32_t i = queue.front();
-      queue.pop_front();
-      inq[i] = 0;
-      if (ignored[i]) continue;
+    while (count > 0) {
+      const int32_t i = pop();
+      rows[size_t(i)].inq = 0;
+      if (rows[size_t(i)].ignored) continue;
       if (visits >= cap) {
-        for (int32_t r : queue) inq[r] = 0;
-        queue.clear();
+        while (count > 0) rows[size_t(pop())].inq = 0;
         break;
       }
       ++visits;
@@ -233,6 +278,25 @@ struct Propagator {
     }
   }
 };
+
+// the end state of the first propagation of the handle's MIP, computed on first use
+struct RootState {
+  std::vector<Propagator::Dom> dom;
+  std::vector<Propagator::Row> rows;
+};
+
+const RootState& root_state(const scylla_lp& lp) {
+  if (!lp.root_prop) {
+    Propagator pr(lp);
+    for (int32_t i = 0; i < lp.m0; ++i) pr.push(i);
+    pr.run();
+    auto st = std::make_shared<RootState>();
+    st->dom = std::move(pr.dom);
+    st->rows = std::move(pr.rows);
+    lp.root_prop = st;
+  }
+  return *std::static_pointer_cast<const RootState>(lp.root_prop);
+}
 
 inline double round_half_up(double v) { return std::floor(v + 0.5); }
 
@@ -297,9 +361,8 @@ int fix_and_propagate_host(const scylla_lp& lp, const double* xbar, double* xhat
   const int rc = lp.ensure_host_matrix();
   if (rc != SCYLLA_OK) return rc;
   lp.ensure_columns();
-  Propagator pr(lp);
-  for (int32_t i = 0; i < lp.m0; ++i) pr.push(i);
-  pr.run();
+  const RootState& root = root_state(lp);
+  Propagator pr(lp, root.dom, root.rows);
   std::vector<int64_t> order;
   order.reserve(lp.n_int);
   std::vector<double> dist(lp.n0, 0.0);
@@ -314,25 +377,27 @@ int fix_and_propagate_host(const scylla_lp& lp, const double* xbar, double* xhat
   });
   int64_t nf = 0;
   for (int64_t j : order) {
-    if (pr.dl[j] == pr.du[j]) continue;
+    Propagator::Dom& d = pr.dom[size_t(j)];
+    if (d.lb == d.ub) continue;
     double v = round_half_up(xbar[j]);
-    v = std::min(std::max(v, pr.dl[j]), pr.du[j]);
-    const double ol = pr.dl[j], ou = pr.du[j];
-    pr.dl[j] = v;
-    pr.du[j] = v;
-    pr.bounds_changed(j, ol, ou);
+    v = std::min(std::max(v, d.lb), d.ub);
+    const double ol = d.lb, ou = d.ub;
+    d.lb = v;
+    d.ub = v;
     if (fixed_cols) fixed_cols[nf] = int32_t(j);
     ++nf;
-    pr.push_rows_of(j);
+    pr.tightened(j, ol, ou);
     pr.run();
   }
   for (int64_t j = 0; j < lp.n0; ++j) {
-    xhat[j] = std::min(std::max(xbar[j], pr.dl[j]), pr.du[j]);
-    if (dom_lo) dom_lo[j] = pr.dl[j];
-    if (dom_hi) dom_hi[j] = pr.du[j];
+    const Propagator::Dom d = pr.dom[size_t(j)];
+    xhat[j] = std::min(std::max(xbar[j], d.lb), d.ub);
+    if (dom_lo) dom_lo[j] = d.lb;
+    if (dom_hi) dom_hi[j] = d.ub;
   }
   if (n_fixed) *n_fixed = nf;
-  if (ignored_rows) std::memcpy(ignored_rows, pr.ignored.data(), size_t(lp.m0));
+  if (ignored_rows)
+    for (int64_t i = 0; i < lp.m0; ++i) ignored_rows[i] = pr.rows[size_t(i)].ignored;
   return SCYLLA_OK;
 }
 
@@ -421,7 +486,12 @@ extern "C" int scylla_fix_and_propagate(const scylla_lp* lp, const double* xbar,
       set_error("xbar has NaN at " + std::to_string(j));
       return SCYLLA_ERR_INVALID_ARG;
     }
-  return fix_and_propagate_host(*lp, xbar, xhat, dom_lo, dom_hi, fixed_cols, n_fixed, ignored_rows);
+  try {
+    return fix_and_propagate_host(*lp, xbar, xhat, dom_lo, dom_hi, fixed_cols, n_fixed, ignored_rows);
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return SCYLLA_ERR_OOM;
+  }
 }
 
 extern "C" int scylla_check_feasible(const scylla_lp* lp, const double* x, int32_t* feasible) {
@@ -429,9 +499,14 @@ extern "C" int scylla_check_feasible(const scylla_lp* lp, const double* x, int32
     set_error("null argument");
     return SCYLLA_ERR_INVALID_ARG;
   }
-  const int rc = lp->ensure_host_matrix();
-  if (rc != SCYLLA_OK) return rc;
-  *feasible = check_feasible_host(*lp, x) ? 1 : 0;
+  try {
+    const int rc = lp->ensure_host_matrix();
+    if (rc != SCYLLA_OK) return rc;
+    *feasible = check_feasible_host(*lp, x) ? 1 : 0;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return SCYLLA_ERR_OOM;
+  }
   return SCYLLA_OK;
 }
 
@@ -441,9 +516,14 @@ extern "C" int scylla_perturb(const scylla_lp* lp, double* xhat, const double* x
     set_error("invalid argument");
     return SCYLLA_ERR_INVALID_ARG;
   }
-  const int rv = lp->ensure_host_vectors();
-  if (rv != SCYLLA_OK) return rv;
-  const int64_t f = perturb_host(*lp, xhat, xbar, kind, K, seed);
-  if (flipped) *flipped = f;
+  try {
+    const int rv = lp->ensure_host_vectors();
+    if (rv != SCYLLA_OK) return rv;
+    const int64_t f = perturb_host(*lp, xhat, xbar, kind, K, seed);
+    if (flipped) *flipped = f;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return SCYLLA_ERR_OOM;
+  }
   return SCYLLA_OK;
 }

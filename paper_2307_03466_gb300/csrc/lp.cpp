@@ -1231,6 +1231,7 @@ extern "C" int scylla_get_trace(const scylla_lp* lp, double* steps, int64_t* n_s
 
 // ------------------------------------------------------ column bounds, repair ---
 int scylla_lp::set_col_bounds(const double* l, const double* u) {
+  root_prop.reset();
   int rc = order_after_user();
   if (rc != SCYLLA_OK) return rc;
   CK(cudaMemcpyAsync(l_un, l, sizeof(double) * n0, cudaMemcpyHostToDevice, st));
@@ -1247,6 +1248,7 @@ int scylla_lp::set_col_bounds(const double* l, const double* u) {
 }
 
 int scylla_lp::set_row_bounds(const double* lo, const double* hi) {
+  root_prop.reset();
   int rc = order_after_user();
   if (rc != SCYLLA_OK) return rc;
   if (m0 > 0) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <vector>
 
 #include "internal.h"
@@ -38,6 +39,9 @@ struct scylla_lp {
   mutable std::vector<double> colvals0;  // the values in the same order
   mutable bool columns_ready = false;
   void ensure_columns() const;
+  // the host propagation's end state after propagating the bounds alone (fixprop.cpp),
+  // kept between fix-and-propagate calls; set_col_bounds and set_row_bounds drop it
+  mutable std::shared_ptr<const void> root_prop;
   double c0norm = 0.0;
   int64_t n_int = 0;
   std::vector<int32_t> gen_int;  // the general integer columns given auxiliary columns, ascending

@@ -15,6 +15,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <set>
 #include <string>
 #include <vector>
@@ -30,11 +31,22 @@ int64_t perturb_host(const scylla_lp& lp, double* x, const double* xbar, int kin
 
 using namespace scylla;
 
+static int run_impl(scylla_lp* lp, double* x_out, scylla_run_result* out);
+
 extern "C" int scylla_run(scylla_lp* lp, double* x_out, scylla_run_result* out) {
   if (!lp || !x_out || !out) {
     set_error("null argument");
     return SCYLLA_ERR_INVALID_ARG;
   }
+  try {
+    return run_impl(lp, x_out, out);
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return SCYLLA_ERR_OOM;
+  }
+}
+
+static int run_impl(scylla_lp* lp, double* x_out, scylla_run_result* out) {
   std::memset(out, 0, sizeof(*out));
   out->status = SCYLLA_NOT_FOUND;
   {

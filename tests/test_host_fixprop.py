@@ -87,6 +87,16 @@ int main(int argc, char** argv) {
   wr(d, "o_xhat", xhat.data(), xhat.size()); wr(d, "o_dl", dl.data(), dl.size()); wr(d, "o_du", du.data(), du.size());
   wr(d, "o_fixed", fixed.data(), size_t(nf)); wr(d, "o_ign", ign.data(), size_t(lp.m0));
   wr(d, "o_nf", &nf, 1);
+  if (mode == "twice") {
+    // a second call on the same handle (it reuses the first propagation's end state)
+    auto xbar2 = rd<double>(d, "xbar2", size_t(lp.n0));
+    const int rc2 = scylla::fix_and_propagate_host(lp, xbar2.data(), xhat.data(), dl.data(), du.data(), fixed.data(),
+                                                   &nf, ign.data());
+    if (rc2 != 0) { fprintf(stderr, "rc %d\n", rc2); return 3; }
+    wr(d, "o2_xhat", xhat.data(), xhat.size()); wr(d, "o2_dl", dl.data(), dl.size());
+    wr(d, "o2_du", du.data(), du.size()); wr(d, "o2_fixed", fixed.data(), size_t(nf));
+    wr(d, "o2_ign", ign.data(), size_t(lp.m0)); wr(d, "o2_nf", &nf, 1);
+  }
   return 0;
 }
 """
@@ -119,14 +129,18 @@ def write_instance(inst, xbar, d):
     np.asarray(xbar, np.float64).tofile(os.path.join(d, "xbar"))
 
 
+def read_outputs(d, prefix="o_"):
+    f = lambda k: os.path.join(d, prefix + k)
+    nf = int(np.fromfile(f("nf"), np.int64)[0])
+    return (np.fromfile(f("xhat")), np.fromfile(f("dl")), np.fromfile(f("du")),
+            np.fromfile(f("fixed"), np.int32)[:nf], np.fromfile(f("ign"), np.uint8).astype(bool))
+
+
 def run_harness(exe, inst, xbar, d):
     write_instance(inst, xbar, d)
     r = subprocess.run([exe, d], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr
-    nf = int(np.fromfile(os.path.join(d, "o_nf"), np.int64)[0])
-    return (np.fromfile(os.path.join(d, "o_xhat")), np.fromfile(os.path.join(d, "o_dl")),
-            np.fromfile(os.path.join(d, "o_du")), np.fromfile(os.path.join(d, "o_fixed"), np.int32)[:nf],
-            np.fromfile(os.path.join(d, "o_ign"), np.uint8).astype(bool))
+    return read_outputs(d)
 
 
 INSTANCES = {
@@ -151,6 +165,30 @@ def test_host_fix_and_propagate_equals_oracle(harness, tmp_path, name):
                                                         inst.l, inst.u, inst.is_int, xbar)
     assert np.array_equal(xhat, oxhat) and np.array_equal(dl, odl) and np.array_equal(du, odu)
     assert np.array_equal(fixed, ofixed) and np.array_equal(ign, oign)
+
+
+def assert_equals_oracle(inst, xbar, got):
+    want = F.fix_and_propagate(inst.rowptr, inst.cols, inst.vals, inst.lo, inst.hi, inst.l, inst.u, inst.is_int, xbar)
+    for g, w in zip(got, want):
+        assert np.array_equal(g, w)
+
+
+@pytest.mark.parametrize("name", ["setcover", "packcover_2kx4k", "long_rows"])
+def test_host_second_call_reuses_first_propagation(harness, tmp_path, name):
+    """The first propagation (bounds alone) is kept in the handle; a second call with
+    another point starts from it and still equals the oracle's fresh run."""
+    inst = INSTANCES[name]()
+    rng = np.random.default_rng(23)
+    lo_b = np.where(np.isfinite(inst.l), inst.l, -5.0)
+    hi_b = np.where(np.isfinite(inst.u), inst.u, lo_b + 10.0)
+    xbar, xbar2 = rng.uniform(lo_b, hi_b), rng.uniform(lo_b, hi_b)
+    d = str(tmp_path / name)
+    write_instance(inst, xbar, d)
+    np.asarray(xbar2, np.float64).tofile(os.path.join(d, "xbar2"))
+    r = subprocess.run([harness, d, "twice"], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    assert_equals_oracle(inst, xbar, read_outputs(d))
+    assert_equals_oracle(inst, xbar2, read_outputs(d, "o2_"))
 
 
 @pytest.mark.parametrize("name", ["setcover", "knapcover", "packcover_gen_int", "mcf_small", "long_rows"])
