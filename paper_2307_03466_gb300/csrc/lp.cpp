@@ -1273,32 +1273,32 @@ int scylla_lp::set_row_bounds(const double* lo, const double* hi) {
 // infeasibility holds at any round)
 constexpr int64_t kRepairPropagationRounds = 1000;
 
-static int propagate_impl(scylla_lp* lp, double* dl, double* du, uint8_t* ignored, int64_t max_rounds,
-                          int64_t* rounds_out, int64_t* conflicts_out) {
+// the buffers of the device propagation, allocated and filled on first use: perm over
+// the transpose's entries, proposals at A's positions, domains, row states, two
+// active-row masks, three counters.  The handle takes them only once every step has
+// succeeded, so a failed first call leaves nothing half set up.
+static int ensure_prop_buffers(scylla_lp* lp) {
+  if (lp->prop_mem) return SCYLLA_OK;
   const int64_t m0 = lp->m0, n0 = lp->n0;
-  cudaStream_t st = lp->st;
-  int rc = lp->order_after_user();
-  if (rc != SCYLLA_OK) return rc;
-  PropDev& P = lp->prop;
-  if (!lp->prop_mem) {
-    // perm over the transpose's entries, proposals at A's positions, domains, row
-    // states, two active-row masks, three counters
-    const size_t nnz = size_t(lp->nnz);
-    size_t off = 0;
-    auto take = [&](size_t bytes) {
-      const size_t o = off;
-      off += (bytes + 255) & ~size_t(255);
-      return o;
-    };
-    const size_t o_perm = take(sizeof(int) * (nnz + 1)), o_plb = take(sizeof(double) * (nnz + 1)),
-                 o_pub = take(sizeof(double) * (nnz + 1)), o_dl = take(sizeof(double) * size_t(n0 + 1)),
-                 o_du = take(sizeof(double) * size_t(n0 + 1)), o_st = take(size_t(m0 + 1)),
-                 o_a0 = take(size_t(m0 + 1)), o_a1 = take(size_t(m0 + 1)),
-                 o_cnt = take(3 * sizeof(unsigned long long));
-    CK(cudaMalloc(&lp->prop_mem, off));
-    CK(cudaMallocHost(&lp->prop_count_h, 3 * sizeof(unsigned long long)));
-    char* b = static_cast<char*>(lp->prop_mem);
-    int* perm = reinterpret_cast<int*>(b + o_perm);
+  const size_t nnz = size_t(lp->nnz);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t o_perm = take(sizeof(int) * (nnz + 1)), o_plb = take(sizeof(double) * (nnz + 1)),
+               o_pub = take(sizeof(double) * (nnz + 1)), o_dl = take(sizeof(double) * size_t(n0 + 1)),
+               o_du = take(sizeof(double) * size_t(n0 + 1)), o_st = take(size_t(m0 + 1)),
+               o_a0 = take(size_t(m0 + 1)), o_a1 = take(size_t(m0 + 1)),
+               o_cnt = take(3 * sizeof(unsigned long long));
+  void* mem = nullptr;
+  unsigned long long* count_h = nullptr;
+  cudaError_t e = cudaMalloc(&mem, off);
+  if (e == cudaSuccess) e = cudaMallocHost(&count_h, 3 * sizeof(unsigned long long));
+  PropDev P{};
+  if (e == cudaSuccess) {
+    char* b = static_cast<char*>(mem);
     P.m = int(m0);
     P.n = int(n0);
     P.rowptr = lp->a_rowptr;
@@ -1306,6 +1306,7 @@ static int propagate_impl(scylla_lp* lp, double* dl, double* du, uint8_t* ignore
     P.vals = lp->a_vals0;
     P.t_rowptr = lp->t_rowptr;
     P.t_rows = lp->t_cols;
+    int* perm = reinterpret_cast<int*>(b + o_perm);
     P.perm = perm;
     P.is_int = lp->int_mask;
     P.plb = reinterpret_cast<double*>(b + o_plb);
@@ -1313,11 +1314,34 @@ static int propagate_impl(scylla_lp* lp, double* dl, double* du, uint8_t* ignore
     P.dl = reinterpret_cast<double*>(b + o_dl);
     P.du = reinterpret_cast<double*>(b + o_du);
     P.state = reinterpret_cast<unsigned char*>(b + o_st);
-    lp->prop_active[0] = reinterpret_cast<unsigned char*>(b + o_a0);
-    lp->prop_active[1] = reinterpret_cast<unsigned char*>(b + o_a1);
     P.count = reinterpret_cast<unsigned long long*>(b + o_cnt);
-    CK(propagate_perm(int(n0), lp->t_rowptr, lp->t_cols, lp->a_rowptr, lp->a_cols, perm, st));
+    e = propagate_perm(int(n0), lp->t_rowptr, lp->t_cols, lp->a_rowptr, lp->a_cols, perm, lp->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lp->st);
   }
+  if (e != cudaSuccess) {
+    if (mem) cudaFree(mem);
+    if (count_h) cudaFreeHost(count_h);
+    set_error(std::string("device propagation buffers: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SCYLLA_ERR_OOM : SCYLLA_ERR_CUDA;
+  }
+  char* b = static_cast<char*>(mem);
+  lp->prop = P;
+  lp->prop_active[0] = reinterpret_cast<unsigned char*>(b + o_a0);
+  lp->prop_active[1] = reinterpret_cast<unsigned char*>(b + o_a1);
+  lp->prop_count_h = count_h;
+  lp->prop_mem = mem;
+  return SCYLLA_OK;
+}
+
+static int propagate_impl(scylla_lp* lp, double* dl, double* du, uint8_t* ignored, int64_t max_rounds,
+                          int64_t* rounds_out, int64_t* conflicts_out) {
+  const int64_t m0 = lp->m0, n0 = lp->n0;
+  cudaStream_t st = lp->st;
+  int rc = lp->order_after_user();
+  if (rc != SCYLLA_OK) return rc;
+  rc = ensure_prop_buffers(lp);
+  if (rc != SCYLLA_OK) return rc;
+  PropDev& P = lp->prop;
   P.lo = lp->lo_un;  // the current original row bounds come first
   P.hi = lp->hi_un;
   CK(cudaMemcpyAsync(P.dl, dl, sizeof(double) * n0, cudaMemcpyHostToDevice, st));
