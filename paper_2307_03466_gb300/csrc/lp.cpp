@@ -904,8 +904,11 @@ int scylla_lp::order_after_user() {
   return SCYLLA_OK;
 }
 
+// Both builders leave the handle without a graph of their kind when a step fails
+// (the caller's next solve builds it again): the executable is instantiated into a
+// local and stored only on success, and a failed build drops what was made.
 template <typename T>
-static int build_graph(scylla_lp* lp, const DevLP<T>& d) {
+static int build_graph_steps(scylla_lp* lp, const DevLP<T>& d) {
   cudaStream_t st = lp->st;
   CK(cudaGraphCreate(&lp->graph, 0));
   CK(cudaGraphConditionalHandleCreate(&lp->cond, lp->graph, 1, cudaGraphCondAssignDefault));
@@ -926,8 +929,21 @@ static int build_graph(scylla_lp* lp, const DevLP<T>& d) {
   const cudaError_t e2 = cudaStreamEndCapture(st, &captured);
   CK(e);
   CK(e2);
-  CK(cudaGraphInstantiate(&lp->exec, lp->graph, 0));
+  cudaGraphExec_t exec = nullptr;
+  CK(cudaGraphInstantiate(&exec, lp->graph, 0));
+  lp->exec = exec;
   return SCYLLA_OK;
+}
+
+template <typename T>
+static int build_graph(scylla_lp* lp, const DevLP<T>& d) {
+  const int rc = build_graph_steps<T>(lp, d);
+  if (rc != SCYLLA_OK) {
+    if (lp->graph) cudaGraphDestroy(lp->graph);
+    lp->graph = nullptr;
+    lp->exec = nullptr;
+  }
+  return rc;
 }
 
 template <typename T>
@@ -939,10 +955,19 @@ static int build_chunk_graph(scylla_lp* lp, const DevLP<T>& d) {
   if (e == cudaSuccess) e = launch_check<T>(d, st);
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(st, &g);
-  CK(e);
-  CK(e2);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    CK(e);
+    CK(e2);
+  }
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t e3 = cudaGraphInstantiate(&exec, g, 0);
+  if (e3 != cudaSuccess) {
+    cudaGraphDestroy(g);
+    CK(e3);
+  }
   lp->chunk_graph = g;
-  CK(cudaGraphInstantiate(&lp->chunk_exec, g, 0));
+  lp->chunk_exec = exec;
   return SCYLLA_OK;
 }
 
