@@ -143,6 +143,16 @@ def run_harness(exe, inst, xbar, d):
     return read_outputs(d)
 
 
+def ping_pong_instance():
+    """x - y >= 1 and y - x >= 1 over integers in [0, 1e9] plus a free integer column:
+    the first propagation stops at its visit cap (20 m + 1000) long before the domains
+    cross, and fixing x then sends the pair around again."""
+    inf = np.inf
+    return I.Instance("ping_pong", 2, 3, np.array([0, 2, 4], np.int64), np.array([0, 1, 0, 1], np.int32),
+                      np.array([1.0, -1.0, -1.0, 1.0]), np.zeros(3), np.array([1.0, 1.0]), np.array([inf, inf]),
+                      np.zeros(3), np.array([1e9, 1e9, 5.0]), np.ones(3, np.uint8))
+
+
 INSTANCES = {
     "setcover": lambda: I.set_cover(),
     "knapcover": lambda: I.knapsack_cover(300, seed=8),
@@ -150,6 +160,7 @@ INSTANCES = {
     "packcover_2kx4k": lambda: I.packing_covering(m=2000, n=4000, per_col=10, seed=11),
     "mcf_small": lambda: I.mcf(nodes=20, avg_degree=4, commodities=6, seed=2),
     "long_rows": lambda: long_row_instance(),
+    "ping_pong": lambda: ping_pong_instance(),
 }
 
 

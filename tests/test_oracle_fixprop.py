@@ -183,3 +183,19 @@ def test_exhaustive_tiny_binary_soundness():
             assert tuple(int(t) for t in xhat) in {tuple(f) for f in feas}
         if not feas:
             assert not brute_feasible(dense, lo, hi, xhat)
+
+
+def test_visit_cap_stops_a_ping_pong_in_closed_form():
+    """Rows x - y >= 1 and y - x >= 1 on integers in [0, U]: each visit moves one lower
+    and one upper bound by one unit past the other column's, and the FIFO alternates
+    the two rows, so visit k sets the bounds it touches to k and U - k.  With U = 1e9
+    the domains would take 5e8 visits to cross; the call stops after
+    visit_cap(2) = 20 * 2 + 1000 = 1040 visits with row 0's bounds from visit 1039
+    and row 1's from visit 1040, and no row ignored."""
+    U = 1e9
+    assert F.visit_cap(2) == 1040
+    dl, du, ign = F.propagate_only([0, 2, 4], [0, 1, 0, 1], [1.0, -1.0, -1.0, 1.0], [1.0, 1.0],
+                                   [math.inf, math.inf], [0.0, 0.0], [U, U], [1, 1])
+    assert list(dl) == [1039.0, 1040.0]
+    assert list(du) == [U - 1040.0, U - 1039.0]
+    assert not ign.any()
