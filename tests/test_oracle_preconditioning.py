@@ -62,9 +62,8 @@ def test_pock_chambolle_output_has_spectral_norm_at_most_one(seed, ruiz):
     A.data *= rng.choice([-1.0, 1.0], A.nnz)
     R, C = precondition(A, ruiz_iters=ruiz, pock_chambolle=True)
     S = scaled(A, R, C)
-    assert np.linalg.norm(S, 2) <= 1.0 + 1e-12
-    # and every nonzero row and column of |S| sums to at most 1 times its weight
     assert np.all(np.isfinite(S))
+    assert np.linalg.norm(S, 2) <= 1.0 + 1e-12
 
 
 def test_permuted_diagonal_becomes_signed_permutation():
@@ -86,3 +85,50 @@ def test_zero_rows_and_columns_keep_unit_multipliers():
     R, C = precondition(A, ruiz_iters=10, pock_chambolle=True)
     assert R[0] == 1.0 and R[2] == 1.0 and C[1] == 1.0
     assert np.all(R > 0) and np.all(C > 0)
+
+
+def _planted(mistake):
+    """The preconditioning with one plausible mistake planted."""
+    def pre(A, ruiz_iters, pock_chambolle):
+        m, n = A.shape
+        R, C = np.ones(m), np.ones(n)
+        absA = abs(A).tocsr()
+        root = (lambda x: x) if mistake == "no_sqrt" else np.sqrt
+        for _ in range(ruiz_iters):
+            S = sp.diags(R) @ absA @ sp.diags(C)
+            rmax = np.asarray(S.max(axis=1).todense()).ravel()
+            R = R / root(np.where(rmax > 0, rmax, 1.0))
+            if mistake == "rows_first":
+                S = sp.diags(R) @ absA @ sp.diags(C)
+            cmax = np.asarray(S.max(axis=0).todense()).ravel()
+            C = C / root(np.where(cmax > 0, cmax, 1.0))
+        if pock_chambolle:
+            S = sp.diags(R) @ absA @ sp.diags(C)
+            rsum = np.asarray(S.sum(axis=1)).ravel()
+            csum = np.asarray(S.sum(axis=0)).ravel()
+            if mistake == "sums_exchanged":
+                rsum, csum = np.resize(csum, m), np.resize(rsum, n)
+            R = R / np.sqrt(np.where(rsum > 0, rsum, 1.0))
+            C = C / np.sqrt(np.where(csum > 0, csum, 1.0))
+        return R, C
+    return pre
+
+
+@pytest.mark.parametrize("mistake", ["rows_first", "no_sqrt", "sums_exchanged"])
+def test_pins_reject_planted_mistakes(monkeypatch, mistake):
+    """Each planted mistake fails at least one of the pins above."""
+    import sys
+    mod = sys.modules[__name__]
+    monkeypatch.setattr(mod, "precondition", _planted(mistake))
+    pins = [lambda: test_ruiz_on_positive_rank_one_matches_closed_form(3),
+            test_ruiz_then_pock_chambolle_on_rank_one_matches_closed_form,
+            lambda: test_pock_chambolle_output_has_spectral_norm_at_most_one(1, 0),
+            lambda: test_pock_chambolle_output_has_spectral_norm_at_most_one(0, 10),
+            test_permuted_diagonal_becomes_signed_permutation]
+    failed = 0
+    for pin in pins:
+        try:
+            pin()
+        except AssertionError:
+            failed += 1
+    assert failed >= 1
