@@ -81,6 +81,22 @@ int main(int argc, char** argv) {
   std::vector<int32_t> fixed(lp.n0);
   std::vector<uint8_t> ign(lp.m0 > 0 ? lp.m0 : 1);
   int64_t nf = 0;
+  if (mode == "multi") {
+    // points in "pts" (npts x n), one call each on the same handle; outputs o<k>_*
+    auto np_ = rd<int64_t>(d, "npts", 1);
+    auto pts = rd<double>(d, "pts", size_t(np_[0] * lp.n0));
+    for (int64_t k = 0; k < np_[0]; ++k) {
+      const int rck = scylla::fix_and_propagate_host(lp, pts.data() + k * lp.n0, xhat.data(), dl.data(), du.data(),
+                                                     fixed.data(), &nf, ign.data());
+      if (rck != 0) { fprintf(stderr, "rc %d\n", rck); return 3; }
+      char pre[32];
+      auto name = [&](const char* s) { snprintf(pre, sizeof pre, "o%lld_%s", (long long)k, s); return pre; };
+      wr(d, name("xhat"), xhat.data(), xhat.size()); wr(d, name("dl"), dl.data(), dl.size());
+      wr(d, name("du"), du.data(), du.size()); wr(d, name("fixed"), fixed.data(), size_t(nf));
+      wr(d, name("ign"), ign.data(), size_t(lp.m0)); wr(d, name("nf"), &nf, 1);
+    }
+    return 0;
+  }
   const int rc = scylla::fix_and_propagate_host(lp, xbar.data(), xhat.data(), dl.data(), du.data(), fixed.data(), &nf,
                                                 ign.data());
   if (rc != 0) { fprintf(stderr, "rc %d\n", rc); return 3; }
@@ -200,6 +216,23 @@ def test_host_second_call_reuses_first_propagation(harness, tmp_path, name):
     assert r.returncode == 0, r.stderr
     assert_equals_oracle(inst, xbar, read_outputs(d))
     assert_equals_oracle(inst, xbar2, read_outputs(d, "o2_"))
+
+
+@pytest.mark.parametrize("name", ["setcover", "knapcover", "packcover_gen_int", "mcf_small", "long_rows"])
+def test_host_consecutive_calls_on_the_gpu_tests_points(harness, tmp_path, name):
+    """The points of the GPU rounding test (a random point, an oracle LP point, exact
+    halves), one call after another on one handle as that test makes them."""
+    from tests.test_gpu_rounding import xbar_points
+    inst = INSTANCES[name]()
+    pts = xbar_points(inst, 5)
+    d = str(tmp_path / name)
+    write_instance(inst, np.zeros(inst.n), d)
+    np.asarray([len(pts)], np.int64).tofile(os.path.join(d, "npts"))
+    np.asarray(pts, np.float64).tofile(os.path.join(d, "pts"))
+    r = subprocess.run([harness, d, "multi"], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    for k, xb in enumerate(pts):
+        assert_equals_oracle(inst, xb, read_outputs(d, f"o{k}_"))
 
 
 @pytest.mark.parametrize("name", ["setcover", "knapcover", "packcover_gen_int", "mcf_small", "long_rows"])
