@@ -183,18 +183,30 @@ def _f64(a, n):
     return a
 
 
+def _csr(rowptr, cols, vals, m: int):
+    """The CSR arrays as the C ABI reads them.  The library gets plain pointers, so the
+    lengths it cannot see are checked here: rowptr has m + 1 entries, and cols and vals
+    have the same length, which is passed as nnz (the library then checks rowptr[0] = 0,
+    rowptr[m] = nnz and the rest before it reads cols or vals)."""
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    if m >= 0 and rp.shape != (m + 1,):
+        raise ValueError(f"rowptr: expected length m + 1 = {m + 1}, got {rp.shape}")
+    ci = np.ascontiguousarray(cols, dtype=np.int32)
+    va = np.ascontiguousarray(vals, dtype=np.float64)
+    if ci.ndim != 1 or ci.shape != va.shape:
+        raise ValueError(f"cols and vals: expected two arrays of one length, got {ci.shape} and {va.shape}")
+    return rp, ci, va, int(ci.shape[0])
+
+
 class LP:
     """An LP handle (``scylla_lp``).  Inputs are host arrays, copied at create."""
 
     def __init__(self, rowptr, cols, vals, c, row_lo, row_hi, col_lo, col_hi, is_integer, m: int, n: int,
                  params: Params | None = None, stream=None):
         L = lib()
-        self._rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
-        self._cols = np.ascontiguousarray(cols, dtype=np.int32)
-        self._vals = np.ascontiguousarray(vals, dtype=np.float64)
         self.m, self.n = int(m), int(n)
-        csr = Csr(self.m, self.n, int(self._rowptr[-1]) if len(self._rowptr) else 0,
-                  self._rowptr.ctypes.data_as(C.POINTER(C.c_int64)),
+        self._rowptr, self._cols, self._vals, nnz = _csr(rowptr, cols, vals, self.m)
+        csr = Csr(self.m, self.n, nnz, self._rowptr.ctypes.data_as(C.POINTER(C.c_int64)),
                   self._cols.ctypes.data_as(C.POINTER(C.c_int32)), _dp(self._vals))
         c = _f64(c, n)
         lo = _f64(row_lo, m)
@@ -202,6 +214,8 @@ class LP:
         l = _f64(col_lo, n)
         u = _f64(col_hi, n)
         ii = np.ascontiguousarray(is_integer, dtype=np.uint8)
+        if ii.shape != (self.n,):
+            raise ValueError(f"is_integer: expected length {self.n}, got {ii.shape}")
         self.params = params if params is not None else default_params()
         h = _P()
         st = _P(stream) if stream is not None else None
@@ -398,11 +412,9 @@ class Batch:
         arrs = {k: (_D * self.count)() for k in ("c", "lo", "hi", "l", "u")}
         self.sizes = []
         for b, inst in enumerate(instances):
-            rp = np.ascontiguousarray(inst.rowptr, dtype=np.int64)
-            ci = np.ascontiguousarray(inst.cols, dtype=np.int32)
-            va = np.ascontiguousarray(inst.vals, dtype=np.float64)
+            rp, ci, va, nnz = _csr(inst.rowptr, inst.cols, inst.vals, int(inst.m))
             keep += [rp, ci, va]
-            csrs[b] = Csr(inst.m, inst.n, int(rp[-1]), rp.ctypes.data_as(C.POINTER(C.c_int64)),
+            csrs[b] = Csr(inst.m, inst.n, nnz, rp.ctypes.data_as(C.POINTER(C.c_int64)),
                           ci.ctypes.data_as(C.POINTER(C.c_int32)), _dp(va))
             for k, a, ln in (("c", inst.c, inst.n), ("lo", inst.lo, inst.m), ("hi", inst.hi, inst.m),
                              ("l", inst.l, inst.n), ("u", inst.u, inst.n)):
@@ -449,7 +461,10 @@ class Fanout:
     of round ``round_K`` around column k.  The LP handle must outlive this object."""
 
     def __init__(self, lp: "LP", targets, round_K: int = 1):
-        t = np.ascontiguousarray(np.asarray(targets, dtype=np.float64).T)  # K blocks of length n
+        tg = np.asarray(targets, dtype=np.float64)
+        if tg.ndim != 2 or tg.shape[0] != lp.n:
+            raise ValueError(f"targets: expected shape (n, K) with n = {lp.n}, got {tg.shape}")
+        t = np.ascontiguousarray(tg.T)  # K blocks of length n
         self.K = t.shape[0]
         self.lp = lp
         h = _P()

@@ -94,6 +94,9 @@ def _create(rowptr, cols, vals, m, n, lo=None, hi=None, l=None, u=None, c=None, 
     (dict(rowptr=[0, 1], cols=[5], vals=[1.0], m=1, n=2), "out of range"),
     (dict(rowptr=[0, 1], cols=[0], vals=[np.nan], m=1, n=2), "non-finite"),
     (dict(rowptr=[1, 1], cols=[], vals=[], m=1, n=2), "rowptr"),
+    # rowptr[m] beyond the arrays: the binding passes their length as nnz, so the
+    # library reports it instead of reading past them
+    (dict(rowptr=[0, 2], cols=[0], vals=[1.0], m=1, n=2), "rowptr"),
     (dict(rowptr=[0, 1], cols=[0], vals=[1.0], m=1, n=2, lo=[2.0], hi=[1.0]), "row bounds"),
     (dict(rowptr=[0, 1], cols=[0], vals=[1.0], m=1, n=2, l=[0.0, 2.0], u=[1.0, 1.0]), "column bounds"),
     (dict(rowptr=[0, 1], cols=[0], vals=[1.0], m=1, n=2, c=[np.inf, 0.0]), "objective"),
@@ -105,6 +108,27 @@ def test_invalid_input_rejected_without_gpu(L, case, needle):
         _create(**case)
     assert ei.value.code == S.ERR_INVALID_ARG
     assert needle in str(ei.value)
+
+
+@pytest.mark.parametrize("case,needle", [
+    (dict(rowptr=[0, 1], cols=[0], vals=[1.0], m=2, n=2, lo=[1.0, 1.0], hi=[2.0, 2.0]), "rowptr"),
+    (dict(rowptr=[0, 1, 2], cols=[0], vals=[1.0], m=1, n=2), "rowptr"),
+    (dict(rowptr=[0, 2], cols=[0, 1], vals=[1.0], m=1, n=2), "cols and vals"),
+    (dict(rowptr=[0, 1], cols=[0], vals=[1.0], m=1, n=2, ii=[0, 0, 0]), "is_integer"),
+])
+def test_binding_checks_array_lengths_before_the_library(L, case, needle):
+    """Lengths the C ABI cannot see (it takes plain pointers) are checked by the binding."""
+    with pytest.raises(ValueError) as ei:
+        _create(**case)
+    assert needle in str(ei.value)
+
+
+def test_fanout_targets_shape_checked_by_the_binding(L):
+    import types
+    with pytest.raises(ValueError):
+        S.Fanout(types.SimpleNamespace(n=5, h=None), np.zeros(5))
+    with pytest.raises(ValueError):
+        S.Fanout(types.SimpleNamespace(n=5, h=None), np.zeros((4, 3)))
 
 
 def test_null_handle_calls_fail_cleanly(L):
