@@ -14,6 +14,9 @@
  *   - Return value: SCYLLA_OK (0) or a negative SCYLLA_ERR_* code.  Solver
  *     outcomes (converged, iteration limit, found, ...) are reported in result
  *     structs, never as error codes.  Nothing aborts or throws across the ABI.
+ *   - A call whose comment lists no errors (the accessors and resets) returns
+ *     SCYLLA_ERR_INVALID_ARG for a null handle, a null required pointer or an
+ *     index out of range, and SCYLLA_ERR_CUDA when a CUDA call fails.
  *   - scylla_last_error() gives a message for the last failing call on the
  *     calling thread.
  *   - Host pointers are caller-owned, read during the call only, and copied.
