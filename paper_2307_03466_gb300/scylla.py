@@ -186,8 +186,10 @@ def _f64(a, n):
 def _csr(rowptr, cols, vals, m: int):
     """The CSR arrays as the C ABI reads them.  The library gets plain pointers, so the
     lengths it cannot see are checked here: rowptr has m + 1 entries, and cols and vals
-    have the same length, which is passed as nnz (the library then checks rowptr[0] = 0,
-    rowptr[m] = nnz and the rest before it reads cols or vals)."""
+    have one length.  nnz is rowptr[m] when the arrays hold that many entries (longer
+    arrays, such as scipy's with spare capacity, pass their first nnz entries), else the
+    arrays' length, which the library then reports as inconsistent with rowptr[m]
+    before it reads cols or vals."""
     rp = np.ascontiguousarray(rowptr, dtype=np.int64)
     if m >= 0 and rp.shape != (m + 1,):
         raise ValueError(f"rowptr: expected length m + 1 = {m + 1}, got {rp.shape}")
@@ -195,6 +197,9 @@ def _csr(rowptr, cols, vals, m: int):
     va = np.ascontiguousarray(vals, dtype=np.float64)
     if ci.ndim != 1 or ci.shape != va.shape:
         raise ValueError(f"cols and vals: expected two arrays of one length, got {ci.shape} and {va.shape}")
+    nnz = int(rp[-1]) if rp.size else 0
+    if 0 <= nnz <= ci.shape[0]:
+        return rp, ci[:nnz], va[:nnz], nnz
     return rp, ci, va, int(ci.shape[0])
 
 

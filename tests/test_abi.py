@@ -123,6 +123,16 @@ def test_binding_checks_array_lengths_before_the_library(L, case, needle):
     assert needle in str(ei.value)
 
 
+def test_binding_passes_the_first_nnz_entries_of_longer_arrays(L):
+    """scipy CSR arrays may hold spare capacity beyond rowptr[m]: only the first nnz
+    entries reach the library (here the spare entry would be out of range)."""
+    with pytest.raises(S.ScyllaError) as ei:
+        _create(rowptr=[0, 1], cols=[0, 9], vals=[1.0, 1.0], m=1, n=2, lo=[2.0], hi=[1.0])
+    assert "row bounds" in str(ei.value)  # got past the CSR checks to the bounds
+    rp, ci, va, nnz = S._csr([0, 1], [0, 9], [1.0, 1.0], 1)
+    assert nnz == 1 and list(ci) == [0] and list(va) == [1.0]
+
+
 def test_fanout_targets_shape_checked_by_the_binding(L):
     import types
     with pytest.raises(ValueError):
