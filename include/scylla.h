@@ -283,6 +283,20 @@ int scylla_fix_and_propagate(const scylla_lp* lp, const double* xbar, double* xh
  * Errors: INVALID_ARG (null), OOM (host), CUDA (first download of the host copies). */
 int scylla_check_feasible(const scylla_lp* lp, const double* x, int32_t* feasible);
 
+/* Test of a certificate that the original LP relaxation has no feasible point, by
+ * weak duality (the LP solves Section 2.1 hands to PDLP can end in such a report):
+ *     D(y) = sum_i min_{lo_i <= s_i <= hi_i} y_i s_i
+ *          - sum_j max_{l_j <= x_j <= u_j} (A^T y)_j x_j
+ * over the original rows and columns.  Every feasible x has
+ * (first sum) <= y^T A x <= (second sum), so D(y) > 0 proves that none exists.
+ *   y: host, length m (one multiplier per original row).
+ *   *gap receives D(y), or -INFINITY when a term needs an infinite bound (y_i > 0
+ *   with row_lo_i = -inf, (A^T y)_j > 0 with col_hi_j = +inf, or the mirror cases).
+ * FP64 with compensated sums in a fixed order, on the host.
+ * Errors: INVALID_ARG (null, a NaN or infinite entry of y), OOM (host), CUDA (first
+ * download of the host copies). */
+int scylla_farkas_gap(const scylla_lp* lp, const double* y, double* gap);
+
 /* Replace the bounds of the original columns (host, length n each), keeping the
  * matrix, its preconditioning, the objective and the iterate; the auxiliary columns
  * keep theirs.  The next solve projects onto the new box (Algorithm 1, primal step);

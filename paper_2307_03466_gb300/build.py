@@ -27,7 +27,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["kernels.cu", "fanout.cu", "noalloc.cu", "transpose.cu", "setup.cu", "propagate.cu"]
-CPP_SOURCES = ["lp.cpp", "fixprop.cpp", "pump.cpp", "batch.cpp", "fanout.cpp"]
+CPP_SOURCES = ["lp.cpp", "fixprop.cpp", "pump.cpp", "batch.cpp", "fanout.cpp", "certify.cpp"]
 
 
 def _sources():

@@ -104,6 +104,7 @@ _SIGS = {
     "scylla_fix_and_propagate": (C.c_int, [_P, _D, _D, _D, _D, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
                                            C.POINTER(C.c_uint8)]),
     "scylla_check_feasible": (C.c_int, [_P, _D, C.POINTER(C.c_int32)]),
+    "scylla_farkas_gap": (C.c_int, [_P, _D, _D]),
     "scylla_set_col_bounds": (C.c_int, [_P, _D, _D]),
     "scylla_set_row_bounds": (C.c_int, [_P, _D, _D]),
     "scylla_propagate": (C.c_int, [_P, _D, _D, C.POINTER(C.c_uint8), C.c_int64, C.POINTER(C.c_int64),
@@ -347,6 +348,13 @@ class LP:
         f = C.c_int32()
         _check(lib().scylla_check_feasible(self.h, _dp(xx), C.byref(f)))
         return bool(f.value)
+
+    def farkas_gap(self, y) -> float:
+        """D(y) of scylla_farkas_gap: > 0 proves the LP relaxation infeasible."""
+        yy = _f64(y, self.m)
+        g = C.c_double()
+        _check(lib().scylla_farkas_gap(self.h, _dp(yy) if self.m else None, C.byref(g)))
+        return g.value
 
     def reset_state(self):
         _check(lib().scylla_reset_state(self.h))

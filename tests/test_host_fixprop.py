@@ -2,7 +2,8 @@
 handle whose host copies are filled directly (no device work is involved), against
 the oracle: fix-and-propagate (Section 2.3) bit for bit (the rounded point, the
 final domains, the fixed columns in fixing order and the ignored rows), the exact
-MIP-feasibility test and the cycle perturbation.  The instances include rows
+MIP-feasibility test, the cycle perturbation and the test of an infeasibility
+certificate (scylla_farkas_gap, through its C entry point).  The instances include rows
 long enough, and slack enough, for the propagation's slack screen and row-activity
 caches to end most visits early, so these check that the shortcuts change nothing."""
 import os
@@ -11,6 +12,7 @@ import subprocess
 
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 from oracle import fixprop as F
 from paper_2307_03466_gb300 import build as B
@@ -67,6 +69,17 @@ int main(int argc, char** argv) {
     std::vector<uint8_t> v(static_cast<size_t>(np_[0]));
     for (int64_t k = 0; k < np_[0]; ++k) v[size_t(k)] = scylla::check_feasible_host(lp, pts.data() + k * lp.n0) ? 1 : 0;
     wr(d, "o_check", v.data(), v.size());
+    return 0;
+  }
+  if (mode == "farkas") {
+    // multipliers in "ys" (ny x m): D(y) of each
+    auto ny = rd<int64_t>(d, "ny", 1);
+    auto ys = rd<double>(d, "ys", size_t(ny[0] * lp.m0));
+    std::vector<double> g(static_cast<size_t>(ny[0]));
+    std::vector<int32_t> rcs(static_cast<size_t>(ny[0]));
+    for (int64_t k = 0; k < ny[0]; ++k) rcs[size_t(k)] = scylla_farkas_gap(&lp, ys.data() + k * lp.m0, &g[size_t(k)]);
+    wr(d, "o_gap", g.data(), g.size());
+    wr(d, "o_rc", rcs.data(), rcs.size());
     return 0;
   }
   if (mode == "perturb") {
@@ -286,3 +299,59 @@ def test_host_perturbation_equals_oracle(harness, tmp_path, kind, K):
     xg = np.fromfile(os.path.join(d, "o_pert"))
     assert np.array_equal(xg, xo)
     assert int(np.fromfile(os.path.join(d, "o_flipped"), np.int64)[0]) == int(np.sum(xg != xhat))
+
+
+def _farkas(harness, d, inst, ys):
+    write_instance(inst, np.zeros(inst.n), d)
+    np.asarray([len(ys)], np.int64).tofile(os.path.join(d, "ny"))
+    np.asarray(ys, np.float64).tofile(os.path.join(d, "ys"))
+    r = subprocess.run([harness, d, "farkas"], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    rc = np.fromfile(os.path.join(d, "o_rc"), np.int32)
+    g = np.fromfile(os.path.join(d, "o_gap"))
+    return np.where(rc == 0, g, np.nan) if np.any(rc != 0) else g
+
+
+def test_host_farkas_gap_equals_oracle(harness, tmp_path):
+    """The library's certificate test (scylla_farkas_gap) against oracle/infeas.py: the
+    same -inf verdicts, equal values on exactly representable cases, and values within
+    the rounding of the oracle's uncompensated A^T y elsewhere (LPs with a known
+    feasible point, and the same LPs with a row added that makes them infeasible)."""
+    from oracle import infeas as X
+    from tests.test_oracle_infeas import _admissible_y
+    inf = np.inf
+    # hand cases: x >= 1 and x <= 0 on a free x; a row against a box
+    two = I.Instance("two", 2, 1, np.array([0, 1, 2], np.int64), np.array([0, 0], np.int32), np.array([1.0, 1.0]),
+                     np.zeros(1), np.array([1.0, -inf]), np.array([inf, 0.0]), np.array([-inf]), np.array([inf]),
+                     np.zeros(1, np.uint8))
+    g = _farkas(harness, str(tmp_path / "two"), two, [[1.0, -1.0], [3.0, -3.0], [1.0, 0.0], [-1.0, 1.0], [0.0, 0.0]])
+    assert list(g) == [1.0, 3.0, -inf, -inf, 0.0]
+    # a NaN multiplier is rejected by the entry point (INVALID_ARG, no value)
+    assert np.isnan(_farkas(harness, str(tmp_path / "two_nan"), two, [[np.nan, 1.0]])[0])
+    for seed in range(3):
+        inst = I.packing_covering(m=50, n=100, per_col=4, seed=200 + seed)
+        rng = np.random.default_rng(seed)
+        ys = [_admissible_y(inst, rng) for _ in range(20)]
+        ys.append(rng.normal(size=inst.m))  # leans on infinite sides
+        got = _farkas(harness, str(tmp_path / f"pc{seed}"), inst, ys)
+        A = inst.csr()
+        for y, gl in zip(ys, got):
+            go = X.farkas_gap(A, inst.lo, inst.hi, inst.l, inst.u, y)
+            if go == -inf:
+                assert gl == -inf
+                continue
+            scale = 1.0 + float(np.abs(A).T @ np.abs(y) @ np.abs(inst.u)) + float(
+                np.abs(y) @ np.where(y > 0, np.abs(np.nan_to_num(inst.lo, neginf=0)), np.abs(np.nan_to_num(inst.hi, posinf=0))))
+            assert abs(gl - go) <= 1e-13 * scale
+            assert gl <= 1e-9 * scale  # weak duality on a feasible LP
+        # the infeasible extension of the oracle pins: D = 1 up to rounding
+        y0 = ys[0]
+        a = A.T @ y0
+        L = X._side_min(y0, inst.lo, inst.hi)
+        A2 = sp.vstack([A, sp.csr_matrix(a)]).tocsr()
+        inf_inst = I.Instance("ext", inst.m + 1, inst.n, A2.indptr.astype(np.int64), A2.indices.astype(np.int32),
+                              A2.data, inst.c, np.append(inst.lo, -inf), np.append(inst.hi, L - 1.0), inst.l, inst.u,
+                              inst.is_int)
+        y2 = np.append(y0, -1.0)
+        g2 = _farkas(harness, str(tmp_path / f"ext{seed}"), inf_inst, [y2])[0]
+        assert abs(g2 - 1.0) <= 1e-9 * (1.0 + abs(L))
