@@ -6,7 +6,8 @@ Only tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
 may use this module.  Scylla hands its LP solves to PDLP (Section 2.1), whose solver
 also reports infeasible relaxations; these functions state what such a report
 rests on, in plain FP64 (``math.fsum``), so that a detector can be checked against
-them.  Both are weak duality written out, not the detector itself.
+them.  Both are weak duality written out; the detector that proposes the rays is
+``PdhgParams.infeasibility_checks`` in oracle/pdhg.py.
 
 * Primal infeasibility (a dual ray y).  For every feasible x,
       sum_i min_{lo_i <= s_i <= hi_i} y_i s_i  <=  y^T A x  =  (A^T y)^T x
@@ -69,6 +70,30 @@ def farkas_gap(A, lo, hi, l, u, y) -> float:
     if left == -math.inf or right == math.inf:
         return -math.inf
     return left - right
+
+
+def farkas_gap_scale(A, lo, hi, l, u, y):
+    """(D(y), S(y)): D as farkas_gap, and S the sum of the absolute values of D's
+    terms, the scale against which D's FP64 rounding is small."""
+    A = sp.csr_matrix(A)
+    y = np.asarray(y, dtype=np.float64)
+    lo, hi, l, u = (np.asarray(v, float) for v in (lo, hi, l, u))
+    g = farkas_gap(A, lo, hi, l, u, y)
+    if g == -math.inf:
+        return g, math.inf
+    r = A.T @ y
+    side = np.where(y > 0, y * np.where(np.isfinite(lo), lo, 0.0), np.where(y < 0, y * np.where(np.isfinite(hi), hi, 0.0), 0.0))
+    box = np.where(r > 0, r * np.where(np.isfinite(u), u, 0.0), np.where(r < 0, r * np.where(np.isfinite(l), l, 0.0), 0.0))
+    return g, math.fsum(np.abs(side)) + math.fsum(np.abs(box))
+
+
+def sign_projection(y, lo, hi) -> np.ndarray:
+    """y with every entry set to 0 whose sign would need an infinite row side
+    (y_i > 0 with lo_i = -inf, y_i < 0 with hi_i = +inf)."""
+    y = np.asarray(y, dtype=np.float64)
+    lo, hi = np.asarray(lo, float), np.asarray(hi, float)
+    keep = ((y > 0) & np.isfinite(lo)) | ((y < 0) & np.isfinite(hi))
+    return np.where(keep, y, 0.0)
 
 
 def recession_violation(A, lo, hi, l, u, d) -> float:

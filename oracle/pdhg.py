@@ -45,9 +45,11 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.sparse as sp
 
+from oracle import infeas
+
 INF = math.inf
 
-CONVERGED, ITER_LIMIT, STALLED = 0, 1, 2
+CONVERGED, ITER_LIMIT, STALLED, INFEASIBLE = 0, 1, 2, 3
 
 MASK64 = (1 << 64) - 1
 
@@ -68,6 +70,13 @@ class PdhgParams:
     step_reduction_exp: float = 0.3
     step_growth_exp: float = 0.6
     stall_checks: int = 0
+    # infeasibility detection (a reading; PDLP-style, the paper delegates the LP solve):
+    # at each check the candidate ray is the unscaled y minus y at the last check whose
+    # index is a power of two, with the entries that would need an infinite row side
+    # set to 0; the solve ends INFEASIBLE when D(candidate) > infeas_margin * S
+    # (oracle/infeas.py), which weak duality rules out on a feasible LP
+    infeasibility_checks: bool = False
+    infeas_margin: float = 1e-9
 
 
 def precondition(A: sp.csr_matrix, ruiz_iters: int, pock_chambolle: bool):
@@ -181,6 +190,7 @@ class SolveResult:
     dobj: float
     used_average: bool
     trace: list = field(default_factory=list)
+    certificate: "np.ndarray | None" = None  # the dual ray when status is INFEASIBLE
 
 
 class OracleLP:
@@ -361,6 +371,8 @@ class OracleLP:
         kkt_prev = kkt_lr
         last_hash = self.stall_hash(x)
         same_hash = 0
+        y_anchor = None
+        certificate = None
         status = None
         out = (x, y, ev_c, False)
         if ev_c.rel_kkt <= tol:
@@ -429,6 +441,18 @@ class OracleLP:
             if p.stall_checks > 0 and same_hash >= p.stall_checks:
                 status = STALLED
                 break
+            if p.infeasibility_checks:
+                n_chk = k // p.n_check
+                yu = self.dual(y)
+                if y_anchor is not None:
+                    cand = infeas.sign_projection(yu - y_anchor, self.lo, self.hi)
+                    g, sc = infeas.farkas_gap_scale(self.A, self.lo, self.hi, self.l, self.u, cand)
+                    if g > p.infeas_margin * sc:
+                        certificate = cand
+                        status = INFEASIBLE
+                        break
+                if n_chk & (n_chk - 1) == 0:
+                    y_anchor = yu
             if not p.restarts:
                 continue
             kc_cur = ev_c.weighted_kkt(omega)
@@ -479,4 +503,4 @@ class OracleLP:
         self.x, self.y = xo, yo
         self.eta, self.omega = eta, omega
         return SolveResult(status, k, accepted, rejected, restarts, evo.eps_p, evo.eps_d, evo.eps_g,
-                           evo.rel_kkt, evo.pobj, evo.dobj, used_avg, tr)
+                           evo.rel_kkt, evo.pobj, evo.dobj, used_avg, tr, certificate)

@@ -135,3 +135,58 @@ def test_planted_sign_mistake_fails_the_built_certificate():
     right = X._box_max(A2.T @ y2, inst.l, inst.u)
     assert abs((X._side_min(y2, lo2, hi2) - right) - 1.0) <= 1e-9 * (1.0 + abs(L))
     assert not abs((wrong_side_min(y2, lo2, hi2) - right) - 1.0) <= 1e-9 * (1.0 + abs(L))
+
+
+def _built_infeasible(seed, m=40, n=80):
+    inst = I.packing_covering(m=m, n=n, per_col=4, seed=100 + seed)
+    rng = np.random.default_rng(seed)
+    A = inst.csr()
+    ys = _admissible_y(inst, rng)
+    L = X._side_min(ys, inst.lo, inst.hi)
+    A2 = sp.vstack([A, sp.csr_matrix(A.T @ ys)]).tocsr()
+    return inst, A2, np.append(inst.lo, -INF), np.append(inst.hi, L - 1.0)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_detector_certifies_built_infeasible_lps(seed):
+    """With infeasibility checks on, the default adaptive solve of each built infeasible
+    LP ends INFEASIBLE within a few thousand attempts, with a ray that the independent
+    test confirms (D > 0), on an LP that HiGHS reports infeasible."""
+    from oracle import pdhg as O
+    inst, A2, lo2, hi2 = _built_infeasible(seed, *((40, 80) if seed < 6 else (120, 240)))
+    lp = O.OracleLP(A2, inst.c, lo2, hi2, inst.l, inst.u, params=O.PdhgParams(infeasibility_checks=True))
+    r = lp.solve(1e-8, 5000)
+    assert r.status == O.INFEASIBLE
+    assert X.farkas_gap(A2, lo2, hi2, inst.l, inst.u, r.certificate) > 0
+    assert _highs_status(A2, inst.c, lo2, hi2, inst.l, inst.u) == 2
+
+
+def test_detector_certifies_a_row_against_its_box():
+    from oracle import pdhg as O
+    A = sp.csr_matrix(np.array([[1.0, 1.0], [1.0, -1.0]]))
+    lo, hi = np.array([3.0, -1.0]), np.array([INF, 1.0])
+    lp = O.OracleLP(A, np.array([1.0, 2.0]), lo, hi, np.zeros(2), np.ones(2),
+                    params=O.PdhgParams(infeasibility_checks=True))
+    r = lp.solve(1e-8, 5000)
+    assert r.status == O.INFEASIBLE
+    assert X.farkas_gap(A, lo, hi, np.zeros(2), np.ones(2), r.certificate) > 0
+
+
+@pytest.mark.parametrize("name", ["setcover", "packcover", "knapcover", "mcf"])
+def test_detector_never_fires_on_feasible_lps_and_changes_nothing(name):
+    """On feasible LPs the checks cannot fire (weak duality; the margin is far above
+    the rounding) and leave the trajectory bit for bit as it is without them."""
+    from oracle import pdhg as O
+    inst = {"setcover": lambda: I.set_cover(m=60, n=150, seed=3),
+            "packcover": lambda: I.packing_covering(m=80, n=160, per_col=4, seed=5),
+            "knapcover": lambda: I.knapsack_cover(80, seed=2),
+            "mcf": lambda: I.mcf(nodes=12, avg_degree=4, commodities=4, seed=1)}[name]()
+    res = []
+    for on in (False, True):
+        lp = O.OracleLP(inst.csr(), inst.c, inst.lo, inst.hi, inst.l, inst.u,
+                        params=O.PdhgParams(infeasibility_checks=on))
+        r = lp.solve(1e-7, 6000)
+        res.append((r.status, r.iterations, lp.primal().copy(), lp.dual().copy()))
+    assert res[1][0] != O.INFEASIBLE
+    assert res[0][:2] == res[1][:2]
+    assert np.array_equal(res[0][2], res[1][2]) and np.array_equal(res[0][3], res[1][3])
