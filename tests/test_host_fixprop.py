@@ -190,6 +190,13 @@ INSTANCES = {
     "mcf_small": lambda: I.mcf(nodes=20, avg_degree=4, commodities=6, seed=2),
     "long_rows": lambda: long_row_instance(),
     "ping_pong": lambda: ping_pong_instance(),
+    "no_rows": lambda: I.Instance("no_rows", 0, 4, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0),
+                                  np.zeros(4), np.zeros(0), np.zeros(0), np.array([0.0, -3.0, 0.0, -np.inf]),
+                                  np.array([1.0, 3.0, 2.5, np.inf]), np.array([1, 1, 0, 1], np.uint8)),
+    "no_integers": lambda: I.Instance("no_integers", 2, 3, np.array([0, 2, 3], np.int64),
+                                      np.array([0, 2, 1], np.int32), np.array([1.0, 2.0, -1.0]), np.zeros(3),
+                                      np.array([1.0, -np.inf]), np.array([np.inf, 0.5]), np.zeros(3),
+                                      np.full(3, 4.0), np.zeros(3, np.uint8)),
 }
 
 
