@@ -278,6 +278,18 @@ int scylla_get_transpose(const scylla_lp* lp, int64_t* colptr, int32_t* rows, do
 int scylla_fix_and_propagate(const scylla_lp* lp, const double* xbar, double* xhat, double* dom_lo,
                              double* dom_hi, int32_t* fixed_cols, int64_t* n_fixed, uint8_t* ignored_rows);
 
+/* Fix-and-propagate of K points at once (Section 2.3), e.g. the K LP points of a
+ * fan-out solve, on the host threads.  Point k gives exactly what
+ * scylla_fix_and_propagate gives for it; every point starts from the handle's kept
+ * first propagation (computed first, on the calling thread).
+ *   K >= 0.  xbar: host, K blocks of length n (point k at xbar + k n).
+ *   xhat: host output, K blocks of length n.  dom_lo, dom_hi: host outputs, K blocks
+ *   of length n, or NULL.  n_fixed: host output, K entries, or NULL.
+ * Errors: INVALID_ARG (null lp, K < 0, null xbar or xhat with K > 0, NaN in xbar),
+ * OOM (host), CUDA (first download of the host copies). */
+int scylla_fix_and_propagate_many(const scylla_lp* lp, int32_t K, const double* xbar, double* xhat,
+                                  double* dom_lo, double* dom_hi, int64_t* n_fixed);
+
 /* Exact MIP-feasibility test of x (host, length n) on the original MIP
  * (Algorithm 1, both "MIP-feasible" tests): *feasible = 1 or 0.
  * Errors: INVALID_ARG (null), OOM (host), CUDA (first download of the host copies). */

@@ -26,6 +26,7 @@
 // the MIP, so its end state is kept in the handle and reused by later calls until the
 // handle's bounds change.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -35,6 +36,7 @@
 #include <string>
 #include <vector>
 
+#include "host_par.h"
 #include "internal.h"
 #include "lp_handle.h"
 
@@ -356,16 +358,18 @@ bool check_feasible_host(const scylla_lp& lp, const double* x) {
   return true;
 }
 
-int fix_and_propagate_host(const scylla_lp& lp, const double* xbar, double* xhat, double* dom_lo, double* dom_hi,
-                           int32_t* fixed_cols, int64_t* n_fixed, uint8_t* ignored_rows) {
-  const int rc = lp.ensure_host_matrix();
-  if (rc != SCYLLA_OK) return rc;
-  lp.ensure_columns();
-  const RootState& root = root_state(lp);
+}  // namespace scylla
+
+namespace {
+
+// the fixing loop for one point, from the kept first propagation (read only, so that
+// several points can run at once)
+void fix_one(const scylla_lp& lp, const RootState& root, const double* xbar, double* xhat, double* dom_lo,
+             double* dom_hi, int32_t* fixed_cols, int64_t* n_fixed, uint8_t* ignored_rows) {
   Propagator pr(lp, root.dom, root.rows);
   std::vector<int64_t> order;
-  order.reserve(lp.n_int);
-  std::vector<double> dist(lp.n0, 0.0);
+  order.reserve(size_t(lp.n_int));
+  std::vector<double> dist(size_t(lp.n0), 0.0);
   for (int64_t j = 0; j < lp.n0; ++j) {
     if (!lp.int0[j]) continue;
     order.push_back(j);
@@ -398,6 +402,43 @@ int fix_and_propagate_host(const scylla_lp& lp, const double* xbar, double* xhat
   if (n_fixed) *n_fixed = nf;
   if (ignored_rows)
     for (int64_t i = 0; i < lp.m0; ++i) ignored_rows[i] = pr.rows[size_t(i)].ignored;
+}
+
+}  // namespace
+
+namespace scylla {
+
+int fix_and_propagate_host(const scylla_lp& lp, const double* xbar, double* xhat, double* dom_lo, double* dom_hi,
+                           int32_t* fixed_cols, int64_t* n_fixed, uint8_t* ignored_rows) {
+  const int rc = lp.ensure_host_matrix();
+  if (rc != SCYLLA_OK) return rc;
+  lp.ensure_columns();
+  fix_one(lp, root_state(lp), xbar, xhat, dom_lo, dom_hi, fixed_cols, n_fixed, ignored_rows);
+  return SCYLLA_OK;
+}
+
+// K points at once: the set-up (host copies, transpose, first propagation) on the
+// calling thread, then the points dealt round-robin to the host threads, each with a
+// private copy of the kept state; point k gives what fix_and_propagate_host gives
+int fix_and_propagate_many_host(const scylla_lp& lp, int64_t K, const double* xbar, double* xhat, double* dom_lo,
+                                double* dom_hi, int64_t* n_fixed) {
+  const int rc = lp.ensure_host_matrix();
+  if (rc != SCYLLA_OK) return rc;
+  lp.ensure_columns();
+  const RootState& root = root_state(lp);
+  const int T = int(std::max<int64_t>(1, std::min<int64_t>(K, host_threads())));
+  const size_t n = size_t(lp.n0);
+  std::atomic<bool> oom{false};
+  fork_join(T, [&](int t) {
+    try {
+      for (int64_t k = t; k < K && !oom.load(); k += T)
+        fix_one(lp, root, xbar + size_t(k) * n, xhat + size_t(k) * n, dom_lo ? dom_lo + size_t(k) * n : nullptr,
+                dom_hi ? dom_hi + size_t(k) * n : nullptr, nullptr, n_fixed ? n_fixed + k : nullptr, nullptr);
+    } catch (const std::bad_alloc&) {
+      oom = true;
+    }
+  });
+  if (oom) throw std::bad_alloc();
   return SCYLLA_OK;
 }
 
@@ -488,6 +529,26 @@ extern "C" int scylla_fix_and_propagate(const scylla_lp* lp, const double* xbar,
     }
   try {
     return fix_and_propagate_host(*lp, xbar, xhat, dom_lo, dom_hi, fixed_cols, n_fixed, ignored_rows);
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return SCYLLA_ERR_OOM;
+  }
+}
+
+extern "C" int scylla_fix_and_propagate_many(const scylla_lp* lp, int32_t K, const double* xbar, double* xhat,
+                                             double* dom_lo, double* dom_hi, int64_t* n_fixed) {
+  if (!lp || K < 0 || (K > 0 && (!xbar || !xhat))) {
+    set_error("invalid argument");
+    return SCYLLA_ERR_INVALID_ARG;
+  }
+  const int64_t total = int64_t(K) * lp->n0;
+  for (int64_t q = 0; q < total; ++q)
+    if (std::isnan(xbar[q])) {
+      set_error("xbar has NaN at point " + std::to_string(q / lp->n0) + ", column " + std::to_string(q % lp->n0));
+      return SCYLLA_ERR_INVALID_ARG;
+    }
+  try {
+    return fix_and_propagate_many_host(*lp, K, xbar, xhat, dom_lo, dom_hi, n_fixed);
   } catch (const std::bad_alloc&) {
     set_error("host allocation failed");
     return SCYLLA_ERR_OOM;

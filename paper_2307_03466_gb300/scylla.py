@@ -105,6 +105,7 @@ _SIGS = {
                                            C.POINTER(C.c_uint8)]),
     "scylla_check_feasible": (C.c_int, [_P, _D, C.POINTER(C.c_int32)]),
     "scylla_farkas_gap": (C.c_int, [_P, _D, _D]),
+    "scylla_fix_and_propagate_many": (C.c_int, [_P, C.c_int32, _D, _D, _D, _D, C.POINTER(C.c_int64)]),
     "scylla_set_col_bounds": (C.c_int, [_P, _D, _D]),
     "scylla_set_row_bounds": (C.c_int, [_P, _D, _D]),
     "scylla_propagate": (C.c_int, [_P, _D, _D, C.POINTER(C.c_uint8), C.c_int64, C.POINTER(C.c_int64),
@@ -342,6 +343,20 @@ class LP:
                                               fixed.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(nf),
                                               ign.ctypes.data_as(C.POINTER(C.c_uint8))))
         return xhat, dl, du, fixed[: nf.value].astype(np.int64), ign[: self.m].astype(bool)
+
+    def fix_and_propagate_many(self, xbars):
+        """Fix-and-propagate of K points at once on the host threads
+        (scylla_fix_and_propagate_many): xbars of shape (K, n); returns xhat (K, n) and
+        the number of columns fixed by rounding per point (K,)."""
+        xb = np.ascontiguousarray(xbars, dtype=np.float64)
+        if xb.ndim != 2 or xb.shape[1] != self.n:
+            raise ValueError(f"xbars: expected shape (K, {self.n}), got {xb.shape}")
+        K = xb.shape[0]
+        xhat = np.empty((K, self.n))
+        nf = np.zeros(K, dtype=np.int64)
+        _check(lib().scylla_fix_and_propagate_many(self.h, int(K), _dp(xb), _dp(xhat), None, None,
+                                                   nf.ctypes.data_as(C.POINTER(C.c_int64))))
+        return xhat, nf
 
     def check_feasible(self, x) -> bool:
         xx = _f64(x, self.n)

@@ -141,6 +141,22 @@ def test_fanout_targets_shape_checked_by_the_binding(L):
         S.Fanout(types.SimpleNamespace(n=5, h=None), np.zeros((4, 3)))
 
 
+def test_new_binding_methods_marshal_through_ctypes(L):
+    """The batched fix-and-propagate and the certificate test: shapes checked in
+    Python, then a null handle comes back from the library as INVALID_ARG (so the
+    argument lists match the C signatures)."""
+    import types
+    fake = types.SimpleNamespace(n=5, m=3, h=None)
+    with pytest.raises(ValueError):
+        S.LP.fix_and_propagate_many(fake, np.zeros((2, 4)))
+    with pytest.raises(S.ScyllaError) as ei:
+        S.LP.fix_and_propagate_many(fake, np.zeros((2, 5)))
+    assert ei.value.code == S.ERR_INVALID_ARG
+    with pytest.raises(S.ScyllaError) as ei:
+        S.LP.farkas_gap(fake, np.zeros(3))
+    assert ei.value.code == S.ERR_INVALID_ARG
+
+
 def test_null_handle_calls_fail_cleanly(L):
     r = S.PdhgResult()
     assert L.scylla_pdhg_solve(None, 1e-4, 10, C.byref(r)) == S.ERR_INVALID_ARG

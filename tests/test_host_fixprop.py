@@ -71,6 +71,21 @@ int main(int argc, char** argv) {
     wr(d, "o_check", v.data(), v.size());
     return 0;
   }
+  if (mode == "many") {
+    // points in "pts" (npts x n) through scylla_fix_and_propagate_many: xhat, domains
+    // and fixed counts of all points
+    auto np_ = rd<int64_t>(d, "npts", 1);
+    const size_t K = size_t(np_[0]), n = size_t(lp.n0);
+    auto pts = rd<double>(d, "pts", K * n);
+    std::vector<double> xh(K * n), dlo(K * n), dhi(K * n);
+    std::vector<int64_t> nfs(K);
+    const int rc = scylla_fix_and_propagate_many(&lp, int32_t(K), pts.data(), xh.data(), dlo.data(), dhi.data(),
+                                                 nfs.data());
+    if (rc != 0) { fprintf(stderr, "rc %d\n", rc); return 3; }
+    wr(d, "m_xhat", xh.data(), xh.size()); wr(d, "m_dl", dlo.data(), dlo.size());
+    wr(d, "m_du", dhi.data(), dhi.size()); wr(d, "m_nf", nfs.data(), nfs.size());
+    return 0;
+  }
   if (mode == "farkas") {
     // multipliers in "ys" (ny x m): D(y) of each
     auto ny = rd<int64_t>(d, "ny", 1);
@@ -362,3 +377,47 @@ def test_host_farkas_gap_equals_oracle(harness, tmp_path):
         y2 = np.append(y0, -1.0)
         g2 = _farkas(harness, str(tmp_path / f"ext{seed}"), inf_inst, [y2])[0]
         assert abs(g2 - 1.0) <= 1e-9 * (1.0 + abs(L))
+
+
+@pytest.mark.parametrize("name", ["setcover", "packcover_2kx4k", "mcf_small", "long_rows", "ping_pong", "no_rows"])
+def test_host_many_points_at_once_equal_the_oracle(harness, tmp_path, name):
+    """scylla_fix_and_propagate_many (the points dealt to the host threads, each from
+    the kept first propagation) gives every point exactly the oracle's result."""
+    inst = INSTANCES[name]()
+    rng = np.random.default_rng(31)
+    lo_b = np.where(np.isfinite(inst.l), inst.l, -5.0)
+    hi_b = np.where(np.isfinite(inst.u), inst.u, lo_b + 10.0)
+    pts = [rng.uniform(lo_b, hi_b) for _ in range(11)]
+    pts.append(np.clip(np.floor(pts[0]) + 0.5, inst.l, inst.u))
+    d = str(tmp_path / name)
+    write_instance(inst, np.zeros(inst.n), d)
+    np.asarray([len(pts)], np.int64).tofile(os.path.join(d, "npts"))
+    np.asarray(pts, np.float64).tofile(os.path.join(d, "pts"))
+    r = subprocess.run([harness, d, "many"], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    K, n = len(pts), inst.n
+    xh = np.fromfile(os.path.join(d, "m_xhat")).reshape(K, n)
+    dl = np.fromfile(os.path.join(d, "m_dl")).reshape(K, n)
+    du = np.fromfile(os.path.join(d, "m_du")).reshape(K, n)
+    nf = np.fromfile(os.path.join(d, "m_nf"), np.int64)
+    for k, xb in enumerate(pts):
+        oxhat, odl, odu, ofixed, _ = F.fix_and_propagate(inst.rowptr, inst.cols, inst.vals, inst.lo, inst.hi,
+                                                         inst.l, inst.u, inst.is_int, xb)
+        assert np.array_equal(xh[k], oxhat) and np.array_equal(dl[k], odl) and np.array_equal(du[k], odu)
+        assert nf[k] == len(ofixed)
+
+
+def test_host_many_with_no_points_and_a_nan(harness, tmp_path):
+    inst = I.set_cover(m=20, n=30, seed=1)
+    d = str(tmp_path / "k0")
+    write_instance(inst, np.zeros(inst.n), d)
+    np.asarray([0], np.int64).tofile(os.path.join(d, "npts"))
+    np.zeros(0).tofile(os.path.join(d, "pts"))
+    r = subprocess.run([harness, d, "many"], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stderr
+    pts = np.zeros((2, inst.n))
+    pts[1, 3] = np.nan
+    np.asarray([2], np.int64).tofile(os.path.join(d, "npts"))
+    pts.tofile(os.path.join(d, "pts"))
+    r = subprocess.run([harness, d, "many"], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 3 and "rc -1" in r.stderr  # INVALID_ARG, nothing computed
