@@ -16,8 +16,8 @@
 // with a 1e-6 tolerance and kept when strictly tighter; continuous bounds are kept
 // when finite and tighter by more than 1e-3 max(1, |old|).  A row whose activity
 // range misses [lo, hi] by more than 1e-9, or whose bounds would empty a domain, is
-// ignored from then on (Section 2.3: constraints that would lead to empty domains are
-// ignored) and changes nothing; otherwise its changes are applied together and the
+// ignored from then on (Section 2.3 keeps rounding past such a row by disregarding it)
+// and changes nothing; otherwise its changes are applied together and the
 // rows of each changed column are queued (ascending, unless queued or ignored).  One
 // propagation stops after 20 m + 1000 row visits.  Finally every column takes its
 // reference value projected onto its domain.
