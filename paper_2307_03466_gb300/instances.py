@@ -1,8 +1,8 @@
 """Seeded synthetic MIP instances shaped like the workloads of Scylla's evaluation.
 
 The paper evaluates on MIPLIB 2017 and the FP-2.0 instances (Section 3), which are
-not available here; these generators stand in for "MIPs with difficult LP
-relaxations" (Section 3, Table 1 discussion).  Every instance is
+not available here; these generators stand in for the instances whose LP
+relaxations are hard to solve, where Section 3 finds the method most useful.  Every instance is
 ``min c^T x  s.t.  lo <= A x <= hi,  l <= x <= u,  x_j integer for is_int[j]``,
 the two-sided generalisation of the paper's ``A x >= b`` (Algorithm 1, input).
 
