@@ -64,6 +64,22 @@ def test_fix_and_propagate_bit_exact(name):
     g.close()
 
 
+@pytest.mark.parametrize("name", ["setcover_200x500", "packcover_gen_int", "long_rows"])
+def test_fix_and_propagate_many_points_bit_exact(name):
+    """scylla_fix_and_propagate_many on the handle's host copies: every point as the
+    oracle rounds it, and as a single call does."""
+    inst = ROUNDING_INSTANCES[name]()
+    g = handle(inst)
+    pts = xbar_points(inst, 7)
+    xh, nf = g.fix_and_propagate_many(np.stack(pts))
+    for k, xb in enumerate(pts):
+        xo, dlo, duo, fxo, igo = F.fix_and_propagate(inst.rowptr, inst.cols, inst.vals, inst.lo, inst.hi,
+                                                    inst.l, inst.u, inst.is_int, xb)
+        assert np.array_equal(xh[k], xo) and nf[k] == len(fxo)
+        assert np.array_equal(xh[k], g.fix_and_propagate(xb)[0])
+    g.close()
+
+
 @pytest.mark.parametrize("name", ["setcover_200x500", "knapcover_300", "packcover_gen_int"])
 def test_feasibility_check_matches_oracle(name):
     inst = ROUNDING_INSTANCES[name]()
