@@ -80,6 +80,34 @@ def test_fix_and_propagate_many_points_bit_exact(name):
     g.close()
 
 
+def test_farkas_gap_on_a_device_handle():
+    """scylla_farkas_gap through the binding, on a handle with auxiliary columns (its
+    rows and columns are the original MIP's): D = 1 on an LP built infeasible, and
+    the oracle's value on random multipliers of a feasible one."""
+    from oracle import infeas as X
+    from tests.test_oracle_infeas import _admissible_y
+    inst = I.packing_covering(m=40, n=80, per_col=4, seed=100)
+    rng = np.random.default_rng(0)
+    A = inst.csr()
+    ys = _admissible_y(inst, rng)
+    L = X._side_min(ys, inst.lo, inst.hi)
+    A2 = sp.vstack([A, sp.csr_matrix(A.T @ ys)]).tocsr()
+    bad = I.Instance("built_infeasible", inst.m + 1, inst.n, A2.indptr.astype(np.int64),
+                     A2.indices.astype(np.int32), A2.data, inst.c, np.append(inst.lo, -np.inf),
+                     np.append(inst.hi, L - 1.0), inst.l, inst.u, inst.is_int)
+    g = handle(bad)
+    assert g.n_aux > 0
+    assert abs(g.farkas_gap(np.append(ys, -1.0)) - 1.0) <= 1e-9 * (1.0 + abs(L))
+    g.close()
+    g = handle(inst)
+    for _ in range(5):
+        y = _admissible_y(inst, rng)
+        go = X.farkas_gap(A, inst.lo, inst.hi, inst.l, inst.u, y)
+        gl = g.farkas_gap(y)
+        assert gl <= 1e-9 * (1.0 + abs(go)) and abs(gl - go) <= 1e-9 * (1.0 + abs(go))
+    g.close()
+
+
 @pytest.mark.parametrize("name", ["setcover_200x500", "knapcover_300", "packcover_gen_int"])
 def test_feasibility_check_matches_oracle(name):
     inst = ROUNDING_INSTANCES[name]()
