@@ -37,7 +37,7 @@ def _rank_main(rank, world, port, out):
 def test_whole_job_reduction_over_two_gloo_ranks():
     world = 2
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:  # no fork of this (threaded) test process
         out = mgr.dict()
         mp.start_processes(_rank_main, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
         res = dict(out)
