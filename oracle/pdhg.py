@@ -71,8 +71,8 @@ class PdhgParams:
     step_growth_exp: float = 0.6
     stall_checks: int = 0
     # infeasibility detection (a reading; PDLP-style, the paper delegates the LP solve):
-    # at each check the candidate ray is the unscaled y minus y at the last check whose
-    # index is a power of two, with the entries that would need an infinite row side
+    # at each check the candidate ray is the unscaled y minus y at the last earlier check
+    # whose index is a power of two, with the entries that would need an infinite row side
     # set to 0; the solve ends INFEASIBLE when D(candidate) > infeas_margin * S
     # (oracle/infeas.py), which weak duality rules out on a feasible LP
     infeasibility_checks: bool = False
