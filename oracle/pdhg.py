@@ -270,7 +270,16 @@ class OracleLP:
 
     # -- Section 2.2: residuals and gap ----------------------------------------
     def evaluate(self, x, y) -> Evaluation:
-        """Relative KKT error of a scaled iterate, measured on the original LP."""
+        """Relative KKT error of a scaled iterate, measured on the original LP.
+
+        eps_p = ||Ax - proj_[lo,hi](Ax)||_2 / (1 + ||b||_2), b_i the largest finite
+        |lo_i|, |hi_i|; eps_d = ||r - lambda||_2 / (1 + ||c||_2) with r = c - A^T y
+        and lambda its projection onto the sign cone of the column bounds;
+        eps_g = |p - d| / (1 + |p| + |d|), where d takes lo_i y_i for y_i > 0, hi_i y_i
+        for y_i < 0 and the same with l, u and lambda.  A y_i whose sign needs an
+        infinite row side makes d = -inf; PDHG iterates never have one, because the
+        dual step keeps every y_i in the sign cone of its row's finite sides.
+        """
         Ax = self.As @ x
         ATy = self.AsT @ y
         rps = Ax - np.clip(Ax, self.lo_s, self.hi_s)
@@ -388,12 +397,14 @@ class OracleLP:
                 dx = x_new - x
                 dy = y_new - y
                 interaction = float(dy @ (self.As @ dx))
-                absA = abs(self.As)
-                scale = float(np.abs(dy) @ (absA @ (np.abs(x_new) + np.abs(x))))
-                cond = scale / abs(interaction) if interaction != 0.0 else INF
-                dz = math.sqrt(float(dx @ dx) + float(dy @ dy))
-                zn = math.sqrt(float(x @ x) + float(y @ y))
-                step_cond = zn / dz if dz > 0 else INF
+                if trace:
+                    # diagnostics of the trace only (no effect on the iterates)
+                    absA = abs(self.As)
+                    scale = float(np.abs(dy) @ (absA @ (np.abs(x_new) + np.abs(x))))
+                    cond = scale / abs(interaction) if interaction != 0.0 else INF
+                    dz = math.sqrt(float(dx @ dx) + float(dy @ dy))
+                    zn = math.sqrt(float(x @ x) + float(y @ y))
+                    step_cond = zn / dz if dz > 0 else INF
                 movement = omega * float(dx @ dx) + float(dy @ dy) / omega
                 eta_max = movement / (2.0 * abs(interaction)) if interaction != 0.0 else INF
                 kk = k + 2  # (k+1) with k the 1-based number of this attempt

@@ -51,8 +51,10 @@ Readings of what the paper leaves open:
   repair runs, when asked for, after a fix-and-propagate point fails the check and
   before the cycle test.
 * Feasibility check: integrality exact; a row whose coefficients, bounds and
-  column values are all integers (below 2^47) is checked in exact integer
-  arithmetic; otherwise activities are summed in CSR order with Neumaier
+  column values are all integers of magnitude below 2^47 is checked in exact
+  integer arithmetic (the library sums such rows in 128-bit integers: products stay
+  below 2^94 and a row of fewer than 2^31 of them below 2^125, so no sum can
+  overflow; this oracle uses the same limit so that both take the same branch); otherwise activities are summed in CSR order with Neumaier
   compensation and compared with tolerance 1e-6 * max(1, |bound|).  Continuous
   column bounds use the same tolerance, integer column bounds are exact.
 """

@@ -323,7 +323,8 @@ namespace scylla {
 
 // exact feasibility test (Algorithm 1, "MIP-feasible"): integrality exact; rows with
 // integer coefficients, bounds and column values (|v| < 2^47) in exact 128-bit
-// integer arithmetic; other rows by compensated FP64 sums with tolerance
+// integer arithmetic (each product is below 2^94 and a row has fewer than 2^31
+// entries, so a sum stays below 2^125 and cannot overflow); other rows by compensated FP64 sums with tolerance
 // 1e-6 max(1, |bound|); continuous column bounds with the same tolerance.
 bool check_feasible_host(const scylla_lp& lp, const double* x) {
   const double tol = 1e-6;

@@ -362,6 +362,124 @@ def tiny_lp(seed: int, m: int = 4, n: int = 5, density: float = 0.6, int_data: b
                     is_int=np.zeros(n, dtype=np.uint8), meta={"seed": seed, "dense": dense})
 
 
+# column kinds of open_bounds_lp: boxed [l, u], lower-bounded only [l, inf),
+# upper-bounded only (-inf, u], free, fixed (l = u)
+COL_KINDS = ("boxed", "lower", "upper", "free", "fixed")
+# row kinds: covering [lo, inf), packing (-inf, hi], ranged [lo, hi], equality, free
+ROW_KINDS = ("covering", "packing", "ranged", "equality", "free")
+
+
+def open_bounds_lp(m: int, n: int, per_col: int = 6, seed: int = 0, col_mix=None, row_mix=None,
+                   name: str = "open_bounds") -> Instance:
+    """LP with one-sided, free and fixed columns and every row kind, built around a
+    known optimal primal-dual pair so that its optimum is finite and known.
+
+    A has ``per_col`` nonzeros per column at distinct uniform rows with values
+    +-lognormal(0, 1).  Column kinds are drawn with the weights ``col_mix`` (a dict
+    over COL_KINDS) and row kinds with ``row_mix`` (over ROW_KINDS).  The pair is
+    drawn first: x* at a bound or strictly inside it, y* and the reduced costs
+    lambda* with the signs that make both complementary (y*_i > 0 only where lo_i is
+    finite and active, < 0 only where hi_i is, 0 on an inactive row; lambda*_j >= 0 at
+    an active lower bound, <= 0 at an active upper bound, 0 inside, either sign on a
+    fixed column).  Then lo, hi are set at or away from A x*, and c = A^T y* + lambda*.
+    (x*, y*) satisfies the optimality conditions of the LP, so f* = c^T x* is its
+    optimal value (meta "x_star", "y_star", "f_star").  Data only: no solver step.
+    """
+    rng = np.random.default_rng(seed)
+    cm = dict(boxed=0.3, lower=0.3, upper=0.1, free=0.2, fixed=0.1) if col_mix is None else dict(col_mix)
+    rm = dict(covering=0.3, packing=0.3, ranged=0.2, equality=0.15, free=0.05) if row_mix is None else dict(row_mix)
+    cw = np.array([cm.get(k, 0.0) for k in COL_KINDS], float)
+    rw = np.array([rm.get(k, 0.0) for k in ROW_KINDS], float)
+    ck = rng.choice(len(COL_KINDS), size=n, p=cw / cw.sum())
+    rk = rng.choice(len(ROW_KINDS), size=m, p=rw / rw.sum())
+    k = min(per_col, m)
+    rows = _distinct_rows_per_column(rng, m, n, k).ravel()
+    cols = np.repeat(np.arange(n), k)
+    vals = rng.lognormal(0.0, 1.0, size=n * k) * np.where(rng.random(n * k) < 0.5, -1.0, 1.0)
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(m, n))
+    A.sort_indices()
+    # columns: bounds, x*, lambda*
+    l = np.full(n, -INF)
+    u = np.full(n, INF)
+    x = np.zeros(n)
+    lam = np.zeros(n)
+    pos = rng.integers(0, 3, size=n)  # 0 at lower, 1 at upper, 2 inside
+    mag = rng.uniform(0.1, 2.0, size=n)
+    gap = rng.uniform(0.5, 5.0, size=n)
+    lb = rng.uniform(-3.0, 3.0, size=n)
+    for j in range(n):
+        kind = COL_KINDS[ck[j]]
+        if kind == "boxed":
+            l[j] = lb[j]
+            u[j] = lb[j] + 1.0 + gap[j]
+            x[j] = l[j] if pos[j] == 0 else (u[j] if pos[j] == 1 else l[j] + 0.5 * (u[j] - l[j]))
+            lam[j] = mag[j] if pos[j] == 0 else (-mag[j] if pos[j] == 1 else 0.0)
+        elif kind == "lower":
+            l[j] = lb[j]
+            at = pos[j] != 2
+            x[j] = l[j] if at else l[j] + gap[j]
+            lam[j] = mag[j] if at else 0.0
+        elif kind == "upper":
+            u[j] = lb[j]
+            at = pos[j] != 2
+            x[j] = u[j] if at else u[j] - gap[j]
+            lam[j] = -mag[j] if at else 0.0
+        elif kind == "free":
+            x[j] = rng.uniform(-5.0, 5.0)
+        else:  # fixed
+            l[j] = u[j] = x[j] = lb[j]
+            lam[j] = rng.normal()
+    # rows: bounds around r = A x*, y*
+    r = A @ x
+    lo = np.full(m, -INF)
+    hi = np.full(m, INF)
+    y = np.zeros(m)
+    act = rng.random(m) < 0.5
+    ym = rng.uniform(0.1, 2.0, size=m)
+    s = rng.uniform(0.1, 1.0, size=m) * (1.0 + np.abs(r))
+    side = rng.random(m) < 0.5
+    for i in range(m):
+        kind = ROW_KINDS[rk[i]]
+        if kind == "covering":
+            lo[i] = r[i] if act[i] else r[i] - s[i]
+            y[i] = ym[i] if act[i] else 0.0
+        elif kind == "packing":
+            hi[i] = r[i] if act[i] else r[i] + s[i]
+            y[i] = -ym[i] if act[i] else 0.0
+        elif kind == "ranged":
+            if act[i] and side[i]:
+                lo[i], hi[i], y[i] = r[i], r[i] + s[i], ym[i]
+            elif act[i]:
+                lo[i], hi[i], y[i] = r[i] - s[i], r[i], -ym[i]
+            else:
+                lo[i], hi[i] = r[i] - s[i], r[i] + 0.5 * s[i]
+        elif kind == "equality":
+            lo[i] = hi[i] = r[i]
+            y[i] = rng.normal()
+    c = A.T @ y + lam
+    return Instance(name=name, m=m, n=n, rowptr=A.indptr.astype(np.int64), cols=A.indices.astype(np.int32),
+                    vals=A.data.astype(np.float64), c=np.asarray(c, np.float64), lo=lo, hi=hi, l=l, u=u,
+                    is_int=np.zeros(n, dtype=np.uint8),
+                    meta={"seed": seed, "x_star": x, "y_star": y, "f_star": float(np.dot(c, x)),
+                          "col_kind": ck, "row_kind": rk})
+
+
+def standard_form_lp(m: int, n: int, per_col: int = 6, seed: int = 0) -> Instance:
+    """open_bounds_lp in standard form: every column x_j >= 0 (u = +inf, l = 0 after
+    the shift below) and every row an equality."""
+    inst = open_bounds_lp(m, n, per_col, seed, col_mix={"lower": 1.0}, row_mix={"equality": 1.0},
+                          name="standard_form")
+    # shift x -> x - l so that every lower bound is 0: the rows move by A l
+    A = inst.csr()
+    shift = A @ inst.l
+    inst.lo = inst.lo - shift
+    inst.hi = inst.hi - shift
+    inst.meta["x_star"] = inst.meta["x_star"] - inst.l
+    inst.meta["f_star"] = float(np.dot(inst.c, inst.meta["x_star"]))
+    inst.l = np.zeros(n)
+    return inst
+
+
 CONFIGS = {
     "setcover_200x500": lambda: set_cover(),
     "packcover_50kx100k": lambda: packing_covering(),

@@ -111,3 +111,32 @@ def test_fanout_targets_flip_ten_percent_of_the_binaries():
         diff = T[:, k] != base
         assert not diff[~bins].any()
         assert diff.sum() == int(round(0.10 * bins.sum()))
+
+
+def test_open_bounds_lp_recipe():
+    """Every column and row kind occurs; the constructed pair is feasible and
+    complementary (y_i > 0 only on an active finite lower side, < 0 on an active
+    upper side; lambda_j >= 0 at an active lower bound, <= 0 at an upper one, 0
+    strictly inside), and c = A^T y* + lambda*."""
+    inst = I.open_bounds_lp(400, 800, per_col=6, seed=3)
+    x, y = inst.meta["x_star"], inst.meta["y_star"]
+    A = inst.csr()
+    assert np.all(np.diff(A.tocsc().indptr) == 6)
+    assert set(np.unique(inst.meta["col_kind"])) == set(range(len(I.COL_KINDS)))
+    assert set(np.unique(inst.meta["row_kind"])) == set(range(len(I.ROW_KINDS)))
+    lf, uf = np.isfinite(inst.l), np.isfinite(inst.u)
+    assert (lf & ~uf).any() and (~lf & uf).any() and (~lf & ~uf).any() and (inst.l == inst.u).any()
+    r = A @ x
+    assert np.all(r >= inst.lo - 1e-9) and np.all(r <= inst.hi + 1e-9)
+    assert np.all(x >= inst.l) and np.all(x <= inst.u)
+    assert np.all(np.isfinite(inst.lo[y > 0])) and np.all(np.isfinite(inst.hi[y < 0]))
+    assert np.all(np.abs(r - inst.lo)[y > 0] <= 1e-9 * (1 + np.abs(r[y > 0])))
+    assert np.all(np.abs(r - inst.hi)[y < 0] <= 1e-9 * (1 + np.abs(r[y < 0])))
+    lam = inst.c - A.T @ y
+    inside = (x > inst.l) & (x < inst.u)
+    assert np.all(np.abs(lam[inside]) <= 1e-9)
+    assert np.all(lam[(x == inst.l) & ~(x == inst.u)] >= -1e-9)
+    assert np.all(lam[(x == inst.u) & ~(x == inst.l)] <= 1e-9)
+    std = I.standard_form_lp(100, 200, seed=4)
+    assert np.all(std.l == 0) and np.all(np.isinf(std.u)) and np.all(std.lo == std.hi)
+    assert np.allclose(std.csr() @ std.meta["x_star"], std.lo)

@@ -318,3 +318,103 @@ def test_rounding_hash_is_order_independent_and_sensitive():
     assert O.rounding_hash(x[perm], cols[perm]) == h
     x2 = x.copy(); x2[17] = np.floor(x2[17] + 0.5) + 1.0
     assert O.rounding_hash(x2, cols) != h
+
+
+# --- the relative KKT error at a point that is not optimal (Section 2.2) -------
+def _golden_eval_lp(params):
+    d = json.load(open(os.path.join(GOLDEN, "evaluate_nonoptimal.json")))
+    f = lambda v: [float(t) for t in v]
+    A = sp.csr_matrix(np.array(d["A_dense"], float))
+    lp = O.OracleLP(A, f(d["c"]), f(d["row_lo"]), f(d["row_hi"]), f(d["col_lo"]), f(d["col_hi"]), params=params)
+    return d, lp, np.array(f(d["x"])), np.array(f(d["y"]))
+
+
+def test_evaluate_hand_example_at_a_nonoptimal_point():
+    """Hand-computed eps_p, eps_d, eps_g, p and d (tests/golden/evaluate_nonoptimal.json)
+    on an LP with covering, packing and two-sided rows and boxed, lower-only,
+    upper-only and free columns: pins the normalisations 1 + ||b||, 1 + ||c||,
+    1 + |p| + |d|, every branch of the reduced-cost projection and every bound
+    term of the dual objective away from the optimum."""
+    d, lp, x, y = _golden_eval_lp(raw_params())
+    ev = lp.evaluate(x, y)
+    e = d["expected"]
+    assert abs(ev.eps_p - math.sqrt(7.5) / (1 + math.sqrt(19))) <= 1e-15
+    assert abs(ev.eps_d - math.sqrt(11) / (1 + math.sqrt(32))) <= 1e-15
+    assert abs(ev.eps_g - 6.75 / 10.25) <= 1e-15
+    assert ev.pobj == e["pobj"] and ev.dobj == e["dobj"]
+    for k in ("eps_p", "eps_d", "eps_g"):
+        assert abs(getattr(ev, k) - e[k + "_value"]) <= 1e-15, k
+    assert ev.rel_kkt == max(ev.eps_p, ev.eps_d, ev.eps_g)
+    # with an objective offset of 1/2 both objectives move: 8.5, 1.75, eps_g = 0.6
+    lp.set_objective_vector(lp.c, 0.5)
+    ev = lp.evaluate(x, y)
+    assert ev.pobj == 8.5 and ev.dobj == 1.75 and abs(ev.eps_g - 0.6) <= 1e-15
+
+
+def test_evaluate_hand_example_through_the_preconditioned_lp():
+    """The same point given to the preconditioned LP (x / C, y / R): the residuals
+    are measured on the original LP, so the hand values stand."""
+    d, lp, x, y = _golden_eval_lp(O.PdhgParams())
+    assert not np.allclose(lp.R, 1.0) and not np.allclose(lp.C, 1.0)
+    lp.set_state(x, y)
+    ev = lp.evaluate(lp.x, lp.y)
+    e = d["expected"]
+    for k in ("eps_p", "eps_d", "eps_g"):
+        assert abs(getattr(ev, k) - e[k + "_value"]) <= 1e-14, k
+    assert abs(ev.pobj - 8.0) <= 1e-14 and abs(ev.dobj - 1.25) <= 1e-14
+
+
+@pytest.mark.parametrize("gen,seed", [("open", 0), ("open", 1), ("open", 2), ("std", 0), ("std", 1)])
+def test_open_bound_and_standard_form_lps_match_highs(gen, seed):
+    """LPs with one-sided, free and fixed columns (and standard-form LPs: x >= 0,
+    equality rows) built around a known optimal pair: HiGHS finds the constructed
+    optimum, and the oracle's PDHG converges to it with its relative KKT error
+    confirmed; the start proj_[l,u](0) has a nonzero dual residual, so the
+    Lambda = R+, R- and {0} branches carry weight on the way."""
+    inst = (I.open_bounds_lp(30, 60, seed=seed) if gen == "open" else I.standard_form_lp(30, 60, seed=seed))
+    assert np.isinf(inst.u).any()
+    if gen == "open":
+        assert np.isinf(inst.l).any() and (np.isinf(inst.l) & np.isinf(inst.u)).any()
+    _, _, fstar = highs(inst.csr(), inst.c, inst.lo, inst.hi, inst.l, inst.u)
+    assert abs(fstar - inst.meta["f_star"]) <= 1e-9 * (1 + abs(fstar))
+    lp = lp_of(inst)
+    ev0 = lp.evaluate(lp.x, lp.y)
+    assert ev0.eps_d > 1e-3
+    np.testing.assert_allclose(lp.primal(), np.clip(np.zeros(inst.n), inst.l, inst.u), rtol=1e-15, atol=0)
+    res = lp.solve(1e-8, 400000)
+    assert res.status == O.CONVERGED
+    assert abs(res.pobj - fstar) <= 1e-6 * (1 + abs(fstar))
+    assert abs(res.dobj - fstar) <= 1e-6 * (1 + abs(fstar))
+    # the constructed pair itself has zero KKT error
+    ev = lp_of(inst, raw_params()).evaluate(inst.meta["x_star"], inst.meta["y_star"])
+    assert ev.rel_kkt <= 1e-13
+
+
+def _planted_projection(mistake):
+    def proj(r, l, u):
+        lf, uf = np.isfinite(l), np.isfinite(u)
+        if mistake == "cones_swapped":
+            return np.where(lf & uf, r, np.where(lf, np.minimum(r, 0.0), np.where(uf, np.maximum(r, 0.0), 0.0)))
+        # "one_sided_as_boxed": Lambda = R whenever one bound is finite
+        return np.where(lf | uf, r, 0.0)
+    return proj
+
+
+def _planted_bound_norm(mistake):
+    def bn(lo, hi):
+        a = np.where(np.isfinite(lo), np.abs(lo), 0.0)
+        b = np.where(np.isfinite(hi), np.abs(hi), 0.0)
+        return a + b if mistake == "sum" else np.minimum(a, b)
+    return bn
+
+
+@pytest.mark.parametrize("mistake", ["cones_swapped", "one_sided_as_boxed", "sum", "min"])
+def test_evaluate_hand_example_rejects_planted_mistakes(monkeypatch, mistake):
+    """A wrong sign cone for one-sided columns, or a wrong bound norm, fails the
+    hand example."""
+    if mistake in ("cones_swapped", "one_sided_as_boxed"):
+        monkeypatch.setattr(O, "reduced_cost_projection", _planted_projection(mistake))
+    else:
+        monkeypatch.setattr(O, "bound_norm_vector", _planted_bound_norm(mistake))
+    with pytest.raises(AssertionError):
+        test_evaluate_hand_example_at_a_nonoptimal_point()

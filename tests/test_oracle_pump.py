@@ -92,17 +92,28 @@ def test_perturb_short_cycle_flips_largest_distances():
     assert set(flipped) == set(range(n - TT, n))  # the largest |xbar - xhat|
 
 
-def test_perturb_long_cycle_and_no_cycle():
+def test_perturb_long_cycle_hand_example():
+    """A long cycle worked by hand (tests/golden/long_cycle_example.json): the
+    uniforms of the round's stream are written out, and the flips follow from them
+    column by column, binaries and general integers, with a continuous column
+    between them that draws no uniform."""
+    g = json.load(open(os.path.join(GOLDEN, "long_cycle_example.json")))
+    r = P.SplitMix64(g["seed"] ^ g["K"])
+    assert [r.uniform() for _ in g["uniforms_of_stream_seed_14"]] == g["uniforms_of_stream_seed_14"]
+    hist = [tuple(float(v) for v in h) for h in g["history_int_keys"]]
+    x, kind = P.perturb(np.array(g["xhat"], float), np.array(g["xbar"], float), hist, g["K"], g["seed"],
+                        g["int_cols"], np.array(g["l"], float), np.array(g["u"], float))
+    assert kind == g["expected_kind"]
+    np.testing.assert_array_equal(x, np.array(g["expected_xhat"], float))
+
+
+def test_perturb_no_cycle():
     n = 30
-    rng = np.random.default_rng(1)
-    xbar = rng.random(n)
-    a = tuple(np.zeros(n)); b = tuple(np.ones(n))
-    x, kind = P.perturb(np.zeros(n), xbar, [a, b], 5, 11, list(range(n)), np.zeros(n), np.ones(n))
-    assert kind == "long"
-    r = P.SplitMix64(11 ^ 5)
-    expect = np.array([1.0 if xbar[j] + max(-0.3 + r.uniform(), 0.0) > 0.5 else 0.0 for j in range(n)])
-    np.testing.assert_array_equal(x, expect)
+    xbar = np.random.default_rng(1).random(n)
+    b = tuple(np.ones(n))
     x, kind = P.perturb(np.full(n, 0.0), xbar, [b], 5, 11, list(range(n)), np.zeros(n), np.ones(n))
+    assert kind == "none"
+    x, kind = P.perturb(np.full(n, 0.0), xbar, [], 5, 11, list(range(n)), np.zeros(n), np.ones(n))
     assert kind == "none"
 
 
