@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-l2", action="store_true", help="skip the l2-distance (diagonal QP) section")
     ap.add_argument("--no-propagate", action="store_true", help="skip the bound-propagation section")
     ap.add_argument("--no-heuristic", action="store_true", help="skip the whole-heuristic section")
+    ap.add_argument("--only", default=None,
+                    choices=["dram", "batched", "fanout", "repair", "l2", "propagation", "heuristic"],
+                    help="run one section alone and print its object (for profiler captures; no bench line)")
     return ap.parse_args()
 
 
@@ -670,9 +673,42 @@ def run_reference(args):
             "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_only(args):
+    """One section of the bench on its own, printed as {"section": name, ...}."""
+    import torch
+    from paper_2307_03466_gb300 import build as B
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    B.build()
+    from paper_2307_03466_gb300 import scylla as S
+    peak, peak_kind = peaks()
+    name = args.only
+    if name == "dram":
+        out = dram_resident(S, peak, peak_kind)
+    elif name == "batched":
+        out = batched_section(S, peak, peak_kind)
+    elif name == "fanout":
+        out = fanout_section(S)
+    else:
+        inst = instance(0)
+        if name == "heuristic":
+            out = heuristic_section(S, inst, reference_objective())
+        elif name == "l2":
+            out = l2_section(S, inst)
+        else:
+            mixed = S.LP.from_instance(inst, S.default_params(precision=S.PREC_MIXED, aux_general_integers=0))
+            mixed.pdhg_solve(TOL, ITER_CAP)
+            out = repair_section(S, mixed, inst) if name == "repair" else propagate_section(mixed, inst)
+            mixed.close()
+    torch.cuda.synchronize()
+    return {"section": name, **out}
+
+
 def main():
     args = parse()
-    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.only is not None and args.impl != "reference":
+        out = run_only(args)
+    else:
+        out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
         print(json.dumps(out))
 

@@ -86,7 +86,7 @@ typedef struct {
                                    barriers between phases; falls back to 1 where it cannot be
                                    co-resident); 1: one CUDA graph per n_check attempts, replayed by a
                                    pipelined host loop; 2: a single graph with a device-side while
-                                   loop; 0: direct launches (3) */
+                                   loop; 0: direct launches (1) */
   double fixed_step_factor;     /* f of the fixed-step mode (0.9) */
   double beta_sufficient;       /* restart if KKT <= 0.2 KKT_last_restart */
   double beta_necessary;        /* ... or <= 0.8 KKT_last_restart and KKT grew since the last check */
@@ -390,9 +390,11 @@ int scylla_perturb(const scylla_lp* lp, double* xhat, const double* xbar, int32_
 int scylla_get_trace(const scylla_lp* lp, double* steps, int64_t* n_steps, double* checks, int64_t* n_checks);
 
 /* Primal residual without any device allocation, for callers that cannot call
- * cudaMalloc (inside a CUDA-graph capture, in a plugin handed a fixed memory pool,
- * in a loop that forbids allocator calls).  The paper has no counterpart: this is
- * a service entry point over the same residual the solver's KKT check computes.
+ * cudaMalloc: plugins whose host application hands them a fixed memory pool,
+ * real-time loops that forbid allocator calls (cudaMalloc and cudaFree can block and
+ * synchronise the device), processes sharing a GPU under a memory budget set
+ * elsewhere.  The paper has no counterpart: this is a service entry point over the
+ * same residual the solver's KKT check computes.
  *
  * Computes, on the caller's stream, for the caller's LP rows and point x:
  *   out[0] = ||A x - proj_[row_lo,row_hi](A x)||_2
@@ -405,10 +407,14 @@ int scylla_get_trace(const scylla_lp* lp, double* steps, int64_t* n_steps, doubl
  *   cudaStream_t or NULL.  The call is asynchronous: out is ready when the stream
  *   reaches it.
  * Scratch: one file-scope __device__ array of 128 KiB per device, held by every GPU
- * that loads the library until the process exits.  The first call on a device
- * looks its address up and clears its counter (a synchronising step): make that
- * first call before any stream capture.  Every call shares the array, so calls
- * that overlap on the GPU race and must be serialised by the caller.  Nothing is
+ * that loads the library until the process exits.  The first call on a device looks
+ * the array's device address up (cudaGetSymbolAddress, with that device current)
+ * and keeps it for the life of the process, so make that first call before any
+ * stream capture, and do not use the entry point across a cudaDeviceReset (the kept
+ * address would be stale).  Every call clears the array's arrival counter on its
+ * stream (cudaMemsetAsync) before its kernel, so a call that failed part way leaves
+ * nothing behind for the next one.  Every call shares the array, so calls that
+ * overlap on the GPU race and must be serialised by the caller.  Nothing is
  * allocated, by this library or by any library it calls.
  * Errors: INVALID_ARG (sizes, null pointers), UNSUPPORTED (device ordinal >= 64),
  * CUDA. */

@@ -1,12 +1,13 @@
 // Primal residual of a caller-owned LP without any device allocation.
 //
-// Some callers cannot allocate device memory at all: code running inside a
-// CUDA-graph capture (where cudaMalloc is not allowed), plugins handed a fixed
-// memory pool by their host application, or real-time loops that forbid allocator
-// calls.  For them, scylla_primal_residual_noalloc evaluates the relative primal
-// residual eps_p = ||A x - proj_[lo,hi](A x)||_2 / (1 + ||b||_2) of a point x on an
-// LP the caller keeps in its own device memory.  The per-block partial sums that
-// the residual kernel of the solver keeps in its handle's scratch live here in one
+// Some callers cannot allocate device memory at all: plugins that their host
+// application hands a fixed memory pool, real-time loops that forbid allocator calls
+// (cudaMalloc and cudaFree can block and synchronise the device), and processes that
+// share a GPU under a fixed memory budget set elsewhere.  For them,
+// scylla_primal_residual_noalloc evaluates the relative primal residual
+// eps_p = ||A x - proj_[lo,hi](A x)||_2 / (1 + ||b||_2) of a point x on an LP the
+// caller keeps in its own device memory.  The per-block partial sums that the
+// residual kernel of the solver keeps in its handle's scratch live here in one
 // file-scope __device__ array instead, so the call allocates nothing.
 //
 // That array is shared by every call on a device and keeps the last call's
@@ -105,14 +106,17 @@ __global__ void __launch_bounds__(kNaThreads) k_primal_residual_noalloc(
   }
 }
 
-// Device address of the scratch array, looked up once per device.  In host code the
-// name g_noalloc_scratch is only a host-side stand-in, so a kernel must be given
-// the address that cudaGetSymbolAddress returns while that device is current.
+// Device address of the scratch array, looked up by the first call on each device
+// and kept for the life of the process.  In host code the name g_noalloc_scratch is
+// only a host-side stand-in, so a kernel must be given the address that
+// cudaGetSymbolAddress returns while that device is current.  After a
+// cudaDeviceReset the module is loaded again and the kept address is stale: the
+// entry point is not for use across a device reset.
 constexpr int kMaxDevices = 64;
 std::mutex g_na_mutex;
 NoAllocScratch* g_na_ptr[kMaxDevices] = {};
 
-int scratch_for_current_device(NoAllocScratch** out, cudaStream_t st) {
+int scratch_for_current_device(NoAllocScratch** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) {
@@ -129,13 +133,6 @@ int scratch_for_current_device(NoAllocScratch** out, cudaStream_t st) {
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
       scylla::set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      return SCYLLA_ERR_CUDA;
-    }
-    // the counter must start at zero; kernels leave it at zero after every call
-    e = cudaMemsetAsync(&static_cast<NoAllocScratch*>(p)->blocks_done, 0, sizeof(unsigned int), st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) {
-      scylla::set_error(std::string("clearing the scratch counter: ") + cudaGetErrorString(e));
       return SCYLLA_ERR_CUDA;
     }
     g_na_ptr[dev] = static_cast<NoAllocScratch*>(p);
@@ -162,12 +159,21 @@ extern "C" int scylla_primal_residual_noalloc(int64_t m, const int64_t* rowptr, 
   }
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   NoAllocScratch* sc = nullptr;
-  const int rc = scratch_for_current_device(&sc, st);
+  const int rc = scratch_for_current_device(&sc);
   if (rc != SCYLLA_OK) return rc;
+  // every call clears the arrival counter on its own stream before its kernel: a
+  // finished kernel leaves it at zero, but one that failed part way (or a launch
+  // that was cancelled) would leave a count that the next call must not inherit
+  cudaError_t e = cudaMemsetAsync(&sc->blocks_done, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) {
+    scylla::set_error(std::string("scylla_primal_residual_noalloc: clearing the scratch counter: ") +
+                      cudaGetErrorString(e));
+    return SCYLLA_ERR_CUDA;
+  }
   const int blocks = int((m + kNaThreads - 1) / kNaThreads);
   k_primal_residual_noalloc<<<blocks, kNaThreads, 0, st>>>(sc, (long long)m, (const long long*)rowptr, cols, vals,
                                                             x, row_lo, row_hi, out);
-  const cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) {
     scylla::set_error(std::string("scylla_primal_residual_noalloc launch: ") + cudaGetErrorString(e));
     return SCYLLA_ERR_CUDA;

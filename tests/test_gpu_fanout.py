@@ -91,7 +91,7 @@ def test_mixed_fanout_reaches_1e4():
         chat, _, off = P.objective_update(inst.c, inst.is_int, inst.l, inst.u, targets[:, q], 2, [])
         o.set_objective_vector(chat, off)
         ref = o.solve(1e-8, 400000)
-        assert abs(res[q].pobj - ref.pobj) <= 1e-2 * (1 + abs(ref.pobj)), q
+        assert abs(res[q].pobj - ref.pobj) <= 1e-3 * (1 + abs(ref.pobj)), q  # oracle at 1e-4: <= 8e-5
     F.close()
     base.close()
 

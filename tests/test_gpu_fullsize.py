@@ -245,3 +245,44 @@ def test_fanout_bench_size_mixed_all_converge_primal_checked_by_oracle(fan):
         assert ev.eps_p <= 1.2e-4, (q, ev.eps_p)
     F.close()
     base.close()
+
+
+@pytest.fixture(scope="module")
+def open_bounds_1m():
+    # the packing/covering workload's size (m = 50k, n = 100k, 1M nonzeros) with
+    # lower-only, upper-only, free and fixed columns and every row kind
+    return I.open_bounds_lp(50_000, 100_000, per_col=10, seed=1012)
+
+
+@pytest.mark.parametrize("prefetch", [0, 2])
+def test_open_bounds_1m_fp64_fixed_step_both_forms(open_bounds_1m, prefetch):
+    """100 fixed-step FP64 attempts from the cold start (checks at 64 and 100, so the
+    column check's one-sided and free branches run) against the oracle, every entry
+    within 1e-9: the automatic form (32-row tiles at this size, as in the bench) and
+    the wide-tile form."""
+    inst = open_bounds_1m
+    g, o = pair(inst, adaptive_step=False, restarts=False, prefetch=prefetch)
+    rg = g.pdhg_solve(0.0, 100)
+    ro = o.solve(0.0, 100)
+    xg, yg, _, _ = g.get_state()
+    assert rel_err(xg, o.primal()) <= 1e-9 and rel_err(yg, o.dual()) <= 1e-9
+    assert abs(rg.eps_d - ro.eps_d) <= 1e-9 * max(1.0, ro.eps_d) and ro.eps_d > 0
+    assert abs(rg.eps_p - ro.eps_p) <= 1e-9 * max(1.0, ro.eps_p)
+    assert abs(rg.eps_g - ro.eps_g) <= 1e-9 * max(1.0, ro.eps_g)
+    g.close()
+
+
+def test_open_bounds_1m_mixed_solve_reaches_1e4(open_bounds_1m):
+    """The bench configuration (FP32-mixed, automatic form) on the same LP: rel-KKT
+    <= 1e-4 confirmed by the oracle's FP64 evaluation, objective within 1e-3 of the
+    constructed optimum."""
+    inst = open_bounds_1m
+    g, o = pair(inst, precision=1)
+    r = g.pdhg_solve(1e-4, 200000)
+    assert r.status == O.CONVERGED and r.rel_kkt <= 1e-4
+    x, y, _, _ = g.get_state()
+    ev = o.evaluate(x / o.C, y / o.R)
+    assert ev.rel_kkt <= 1.2e-4, ev
+    fs = inst.meta["f_star"]
+    assert abs(ev.pobj - fs) / (1 + abs(fs)) <= 1e-3
+    g.close()

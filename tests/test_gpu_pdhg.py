@@ -14,7 +14,7 @@ Even along the same decision sequence the adaptive step sizes exceed the global
 stability bound of PDHG (they are accepted against the local interaction only),
 and directions of the dual that only touch columns held at a bound are not
 damped, so rounding differences grow: the replayed iterates agree within 1e-9 up
-to 100 attempts and within 1e-6 at 1000; the fixed-step mode holds 1e-9 at 1000.
+to 100 attempts and within 2e-6 at 1000; the fixed-step mode holds 1e-9 at 1000.
 """
 import math
 
@@ -22,88 +22,12 @@ import numpy as np
 import pytest
 
 from oracle import pdhg as O
-from tests.gpu_common import INF, gpu_available, long_row_instance, pair, parity_instances, rel_err
+from tests.gpu_common import INF, TOL, TOL_LONG, compare_after, gpu_available, long_row_instance, pair, \
+    parity_instances, rel_err
 
 pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
 
-TOL = 1e-9
-TOL_LONG = 1e-6  # adaptive runs of 1000 attempts (see module docstring)
 INSTANCES = parity_instances()
-
-
-EPS = 2.0 ** -52
-MARGIN = 1e-4  # relative closeness of a restart/candidate comparison that counts as a tie
-
-
-def check_decisions(steps, checks, trace, replayed, long_run=False):
-    """The oracle's own decisions, computed on the same trajectory, against the
-    device's: step sizes within a tolerance scaled by the condition number of the
-    interaction term, accept/restart/candidate choices equal unless the deciding
-    quantities are within their rounding margins."""
-    own_steps = [t for t in trace if t[0] == "step"]
-    own_checks = [t for t in trace if t[0] == "check"]
-    assert len(own_steps) == len(steps) and len(own_checks) == len(checks)
-    for (_, k, acc, eta_used, eta_max, eta_next, cond, step_cond), rec in zip(own_steps, steps):
-        if replayed:
-            assert eta_used == rec[0]
-        else:
-            assert abs(eta_used - rec[0]) <= 1e-12 * eta_used
-        # eta_max is a ratio of quadratic forms of the step: well conditioned when the
-        # interaction term does not cancel (cond) and the step is not tiny against the
-        # iterate (step_cond); otherwise only a sanity bound applies
-        well = cond <= 1e6 and step_cond <= 1e4
-        tol = 1e-6 if well else 1e-2
-        if long_run:
-            # after a few hundred attempts the replayed states differ in directions the
-            # step sizes see (dy in non-unique dual directions); decisions are replayed
-            # and the iterates compared, the step-size values are not
-            continue
-        if np.isfinite(eta_max) and np.isfinite(rec[1]):
-            assert abs(eta_max - rec[1]) <= tol * eta_max, (k, eta_max, rec[1], cond)
-            assert abs(eta_next - rec[3]) <= tol * eta_next, (k, eta_next, rec[3], cond)
-        else:
-            assert np.isinf(eta_max) == np.isinf(rec[1]) or cond > 1e12
-        tie = abs(eta_used - eta_max) <= tol * max(eta_max, 1e-300)
-        assert tie or acc == (rec[2] > 0.5), (k, eta_used, eta_max, rec)
-    for (_, k, restart, is_avg, omega_after, kc, rmargin, cmargin, wcond), rec in zip(own_checks, checks):
-        assert k == rec[0]
-        if long_run:
-            continue  # replayed; past convergence the weighted KKT values are rounding noise
-        assert abs(kc - rec[4]) <= MARGIN * kc, (k, kc, rec)
-        assert rmargin <= MARGIN or restart == (rec[1] > 0.5), (k, restart, rec)
-        assert cmargin <= MARGIN or is_avg == (rec[2] > 0.5), (k, is_avg, rec)
-        if restart == (rec[1] > 0.5) and is_avg == (rec[2] > 0.5) and not long_run:
-            assert abs(omega_after - rec[3]) <= (1e-9 + 1e-9 * wcond) * omega_after, (k, omega_after, rec, wcond)
-
-
-def compare_after(inst, k, replay=True, tol=TOL, **kw):
-    g, o = pair(inst, trace_capacity=k + 8, **kw)
-    rg = g.pdhg_solve(0.0, k)
-    steps, checks = g.trace()
-    assert len(steps) == k
-    ro = o.solve(0.0, k, trace=True, replay=(steps, checks) if replay else None)
-    xg, yg, eta_g, om_g = g.get_state()
-    assert rg.status == ro.status == O.ITER_LIMIT
-    assert rg.iterations == ro.iterations == k
-    assert (rg.accepted, rg.rejected, rg.restarts) == (ro.accepted, ro.rejected, ro.restarts)
-    ex = rel_err(xg, o.primal())
-    ey = rel_err(yg, o.dual())
-    if ey > tol:
-        # y is not unique where it only reaches columns held at a bound (and modulo
-        # the null space of A^T, e.g. the conservation rows of one commodity sum to
-        # zero): the part of y the primal step sees is A^T y on the columns strictly
-        # inside their bounds, so compare that
-        A = inst.csr()
-        xo = o.primal()
-        free = (xo > inst.l + 1e-7 * (1 + np.abs(inst.l))) & (xo < inst.u - 1e-7 * (1 + np.abs(inst.u)))
-        ey = min(ey, rel_err((A.T @ yg)[free], (A.T @ o.dual())[free]))
-    assert ex <= tol and ey <= tol, (ex, ey)
-    # which candidate is reported is a tie-break once both have converged to round-off
-    assert bool(rg.used_average) == ro.used_average or max(rg.rel_kkt, ro.rel_kkt) < 1e-10
-    check_decisions(steps, checks, ro.trace, replay, long_run=k > 100)
-    assert abs(eta_g - o.eta) <= 1e-9 * o.eta and abs(om_g - o.omega) <= 1e-9 * o.omega
-    assert abs(rg.rel_kkt - ro.rel_kkt) <= 1e-7 * max(1.0, ro.rel_kkt)
-    g.close()
 
 
 @pytest.mark.parametrize("name", list(INSTANCES))
@@ -371,5 +295,5 @@ def test_mixed_precision_reaches_1e4_checked_by_oracle(name):
     rr = ref.solve(1e-8, 400000)
     assert rr.status == O.CONVERGED
     obj_err = abs(ev.pobj - rr.pobj) / (1 + abs(rr.pobj))
-    assert obj_err <= 1e-2
+    assert obj_err <= 1e-3  # the oracle's own error at rel-KKT 1e-4 here is <= 6e-6
     g.close()

@@ -1,8 +1,8 @@
 """The allocation-free primal residual entry point against the solver's own.
 
 scylla_primal_residual_noalloc serves callers that cannot allocate device memory
-(inside a graph capture, in plugins with a fixed pool): it keeps its reduction
-scratch in a fixed device array.  Its eps_p must equal the one scylla_pdhg_solve
+(plugins handed a fixed memory pool, loops that forbid allocator calls): it keeps its
+reduction scratch in a fixed device array.  Its eps_p must equal the one scylla_pdhg_solve
 reports for the same point (a zero-iteration solve evaluates the current point),
 within the tolerance of the parity tests, on two calls in a row (the second call
 reuses the scratch the first one left behind).  This file is collected last.
