@@ -144,6 +144,18 @@ def kernel_bytes(m, n, nnz, sv, sx):
     return primal, dual
 
 
+def fanout_bytes(m, n, nnz, K, sv, sx):
+    """Algorithmic bytes of one launch of each fan-out SpMM (K objectives at once):
+    the matrix once (values, indices, row pointers), the gathered K-wide vector
+    once, and the K-wide epilogue vectors -- primal: x read, average read and
+    written, x' written; dual: y and the cached A x read, average read and written,
+    y' and A x' written -- plus the per-column data (objective bit planes, the
+    objective pair, bounds) or per-row bounds."""
+    primal = nnz * (sv + 4) + 4 * (n + 1) + m * K * sx + 4 * n * K * sx + n * (24 + 2 * sx)
+    dual = nnz * (sv + 4) + 4 * (m + 1) + n * K * sx + 6 * m * K * sx + 2 * m * sx
+    return primal, dual
+
+
 def traffic_for(kernel: str, workload: str = WORKLOAD):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the
     current kernel source (else null)."""
@@ -155,16 +167,22 @@ def traffic_for(kernel: str, workload: str = WORKLOAD):
     except (OSError, ValueError):
         return None
     ent = d.get(kernel)
-    if not ent or ent.get("kernel_sources_sha256") != kernel_sources_sha256() or ent.get("workload") != workload:
+    if not ent or ent.get("workload") != workload:
+        return None
+    srcs = ent.get("sources", list(KERNEL_SOURCES))
+    if ent.get("kernel_sources_sha256") != kernel_sources_sha256(srcs):
         return None
     return ent.get("dram_bytes_per_launch")
 
 
-def kernel_sources_sha256() -> str:
-    """sha256 over the sources the per-attempt kernels are compiled from
-    (kernels.cu and the headers it includes), in that order."""
+KERNEL_SOURCES = ("kernels.cu", "device_common.cuh", "internal.h")
+
+
+def kernel_sources_sha256(sources=KERNEL_SOURCES) -> str:
+    """sha256 over the sources a kernel is compiled from (by default the per-attempt
+    kernels': kernels.cu and the headers it includes), in the order given."""
     h = hashlib.sha256()
-    for f in ("kernels.cu", "device_common.cuh", "internal.h"):
+    for f in sources:
         with open(os.path.join(ROOT, "paper_2307_03466_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -534,7 +552,28 @@ def fanout_section(S):
     res, sec = F.solve(TOL, ITER_CAP)
     out["mixed_fanout"] = {"seconds": sec, "converged": sum(1 for r in res if r.status == S.CONVERGED),
                            "max_attempts": max(r.iterations for r in res),
-                           "max_rel_kkt": max(r.rel_kkt for r in res)}
+                           "max_rel_kkt": max(r.rel_kkt for r in res),
+                           "ms_per_attempt": 1e3 * sec / max(1, max(r.iterations for r in res))}
+    # per-kernel device time (CUDA events around separate launches) and the roofline of
+    # the dominant SpMM
+    F.reset_state()
+    ms = F.time_kernels(2 * 64)
+    bp, bd = fanout_bytes(inst.m, inst.n, inst.nnz, 64, 4, 4)
+    peak, peak_kind = peaks()
+    kname, kb, kms = ("k_fdual<float>", bd, ms[1]) if ms[1] >= ms[0] else ("k_fprimal<float>", bp, ms[0])
+    out["kernel_ms"] = {"primal": ms[0], "dual": ms[1], "step_control": ms[2], "check_cols": ms[3],
+                        "check_rows": ms[4], "check_control": ms[5]}
+    sp, sd, tune_ms = F.info()
+    shapes = {1: "4 objectives/lane, 64 slots/sweep (2 rows/warp)", 2: "2 objectives/lane, 64 slots/sweep (1 row/warp)",
+              3: "4 objectives/lane, 32 slots/sweep (4 rows/warp, 2 sweeps)",
+              4: "2 objectives/lane, 32 slots/sweep (2 rows/warp, 2 sweeps)"}
+    out["autotuner"] = {"tile_shape": {"primal": shapes[sp], "dual": shapes[sd]},
+                        "ms_per_launch": {f"{side}_shape{q + 1}": tune_ms[4 * i + q]
+                                          for i, side in enumerate(("primal", "dual")) for q in range(4)}}
+    out["gbs"] = {"primal": bp / (ms[0] * 1e6), "dual": bd / (ms[1] * 1e6)}
+    out["roofline"] = {"bound": "hbm", "kernel": kname, "achieved": kb / (kms * 1e6), "peak": peak, "unit": "GB/s",
+                       "frac": kb / (kms * 1e6) / peak, "peak_source": peak_kind, "bytes_per_launch": kb,
+                       "traffic": traffic_for(kname + "@fanout", FAN_WORKLOAD)}
     # the rounding step of the 64 LP points (Section 2.3): all at once on the host
     # threads (scylla_fix_and_propagate_many) against the first four one after another
     # (wall time; the handle's first propagation is kept before either is timed)

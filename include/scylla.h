@@ -475,6 +475,29 @@ int scylla_fanout_solve(scylla_fanout* f, double tol, int64_t iter_limit, scylla
 int scylla_fanout_get_primal(const scylla_fanout* f, int32_t k, double* x);
 /* every objective back to the handle's current pair, step size and primal weight */
 int scylla_fanout_reset_state(scylla_fanout* f);
+/* Tile-shape autotuner of the fan-out (run once by scylla_fanout_create).  Every
+ * K-wide vector row has 64 slots; a tile shape sets how the SpMMs (primal over A^T,
+ * dual over A) cover them: VEC consecutive objectives per lane and CHUNK slots per
+ * sweep, so CHUNK / VEC lanes per row, 32 VEC / CHUNK rows per warp and 64 / CHUNK
+ * sweeps over the matrix (two sweeps halve the part of the gathered vector in use
+ * at a time).  Shapes: 1 = (4, 64), 2 = (2, 64), 3 = (4, 32), 4 = (2, 32); the
+ * FP64 mode takes 2 and 4.  shape_primal, shape_dual: 0 times every valid shape on
+ * this fan-out's own matrix and keeps the fastest, 1..4 forces one.  Every shape
+ * gives identical results.  The objectives go back to the handle's pair (as
+ * scylla_fanout_reset_state).  Errors: INVALID_ARG (an invalid shape), CUDA. */
+int scylla_fanout_tune(scylla_fanout* f, int32_t shape_primal, int32_t shape_dual);
+/* The tile shapes in use and the tuner's times: tune_ms (may be NULL) receives 8
+ * values, ms per launch of the primal SpMM in shapes 1..4, then of the dual SpMM
+ * (0 where a shape was not timed). */
+int scylla_fanout_info(const scylla_fanout* f, int32_t* shape_primal, int32_t* shape_dual, double* tune_ms);
+/* Measurement: `attempts` attempts of every objective from the current pairs (no
+ * tolerance test; the checks run every n_check attempts as in a solve) as separate
+ * launches with CUDA events around each, on the base handle's stream; ms[0..5]
+ * receive the mean device time in milliseconds of the primal SpMM, the dual SpMM,
+ * the step control, the column check, the row check and the check control (0 where
+ * a kernel did not run).  The pairs move on by those attempts.
+ * Errors: INVALID_ARG (null, attempts < 1), CUDA. */
+int scylla_fanout_time_kernels(scylla_fanout* f, int32_t attempts, double* ms);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* scylla_last_error(void);

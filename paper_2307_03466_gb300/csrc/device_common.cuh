@@ -821,9 +821,5 @@ __device__ __forceinline__ void write_slot(BatchSlot<T>* s, const Control* c) {
   *s = v;
 }
 
-template <typename T>
-__device__ __forceinline__ void write_fan_slot(BatchSlot<T>* s, const Control* c) {
-  write_slot(s, c);
-}
 
 }  // namespace scylla

@@ -40,6 +40,11 @@ struct scylla_fanout {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   float last_ms = 0.f;
+  // the autotuner's measurements: ms per launch of the primal SpMM in tile shapes
+  // 1..4, then of the dual SpMM (0 where a shape was not timed)
+  double tune_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  void* pools = nullptr;  // the iterate pools (X, Y, AX, ATY, XLR, YLR), contiguous in the arena
+  size_t pools_bytes = 0;
 
   void release() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -123,6 +128,58 @@ int fan_solve_impl(scylla_fanout* f, DevFan<T>& F, double tol, int64_t iter_limi
   return SCYLLA_OK;
 }
 
+// Tile-shape autotuner of the fan-out: for each SpMM (primal, dual) every valid tile
+// shape (objectives per lane VEC, slots per sweep CHUNK; so 32 VEC / CHUNK rows per
+// warp and 64 / CHUNK sweeps over the matrix) is timed on this fan-out's own matrix
+// and the fastest kept; shape 1..4 forces one instead (0: time them all).  Every
+// shape gives identical results (the same per-objective sums in the same order).
+// The timed launches run from the seeded state, which is zeroed and seeded again
+// afterwards.
+template <typename T>
+int fan_tune(scylla_fanout* f, DevFan<T>& F, int shape_p, int shape_d) {
+  cudaStream_t st = f->lp->st;
+  for (int side = 0; side < 2; ++side) {
+    const int forced = side == 0 ? shape_p : shape_d;
+    for (int q = 0; q < 4; ++q) f->tune_ms[4 * side + q] = 0.0;
+    if (forced != 0) {
+      (side == 0 ? F.shape_p : F.shape_d) = forced;
+      continue;
+    }
+    CKF(launch_fan_init<T>(F, 0.0, 1LL << 40, 0, st));
+    CKF(launch_fan_check<T>(F, st));
+    double best = 0.0;
+    int best_shape = 0;
+    for (int shape = 1; shape <= 4; ++shape) {
+      if (!fan_shape_valid<T>(shape)) continue;
+      (side == 0 ? F.shape_p : F.shape_d) = shape;
+      fan_grids<T>(F);
+      CKF(launch_fan_part<T>(F, side, st));  // warm-up
+      CKF(cudaEventRecord(f->ev0, st));
+      for (int r = 0; r < 3; ++r) CKF(launch_fan_part<T>(F, side, st));
+      CKF(cudaEventRecord(f->ev1, st));
+      CKF(cudaEventSynchronize(f->ev1));
+      float ms = 0.f;
+      CKF(cudaEventElapsedTime(&ms, f->ev0, f->ev1));
+      const double per = double(ms) / 3.0;
+      f->tune_ms[4 * side + shape - 1] = per;
+      if (best_shape == 0 || per < best) {
+        best = per;
+        best_shape = shape;
+      }
+    }
+    (side == 0 ? F.shape_p : F.shape_d) = best_shape;
+  }
+  fan_grids<T>(F);
+  if (f->exec) {  // the captured graph holds the old launch configuration
+    cudaGraphExecDestroy(f->exec);
+    cudaGraphDestroy(f->graph);
+    f->exec = nullptr;
+    f->graph = nullptr;
+  }
+  CKF(cudaMemsetAsync(f->pools, 0, f->pools_bytes, st));
+  return seed_state<T>(f, F);
+}
+
 int create_fan(scylla_lp* lp, int K, const double* targets, int round_K, scylla_fanout* f) {
   f->lp = lp;
   f->K = K;
@@ -162,8 +219,10 @@ int create_fan(scylla_lp* lp, int K, const double* targets, int round_K, scylla_
   const size_t vs = mixed ? sizeof(float) : sizeof(double);
   char *X[3], *Y[3], *AX[3], *ATY[2], *XLR, *YLR;
   unsigned long long *lob, *upb;
+  float2* cw;
   Control* ctl;
   void* slot;
+  FanState* state;
   double *pp, *pd, *pc1, *pc2, *fac;
   int* n_done;
   long long* kglob;
@@ -172,13 +231,31 @@ int create_fan(scylla_lp* lp, int K, const double* targets, int round_K, scylla_
   if (mixed) {
     g32.d = lp->d32;
     g32.K = K;
+    g32.shape_p = g32.shape_d = 1;
     fan_grids<float>(g32);
   } else {
     g64.d = lp->d64;
     g64.K = K;
+    g64.shape_p = g64.shape_d = 2;
     fan_grids<double>(g64);
   }
-  const int gp = mixed ? g32.grid_p : g64.grid_p, gd = mixed ? g32.grid_d : g64.grid_d;
+  // the block partial arrays hold the largest grid of any tile shape
+  int gp = mixed ? g32.grid_p : g64.grid_p, gd = mixed ? g32.grid_d : g64.grid_d;
+  for (int shape = 1; shape <= 4; ++shape) {
+    if (mixed) {
+      DevFan<float> t = g32;
+      t.shape_p = t.shape_d = shape;
+      fan_grids<float>(t);
+      gp = std::max(gp, t.grid_p);
+      gd = std::max(gd, t.grid_d);
+    } else if (fan_shape_valid<double>(shape)) {
+      DevFan<double> t = g64;
+      t.shape_p = t.shape_d = shape;
+      fan_grids<double>(t);
+      gp = std::max(gp, t.grid_p);
+      gd = std::max(gd, t.grid_d);
+    }
+  }
   const int gc1 = mixed ? g32.grid_c1 : g64.grid_c1, gc2 = mixed ? g32.grid_c2 : g64.grid_c2;
   const size_t nk = size_t(n) * kFanMaxK, mk = size_t(m) * kFanMaxK;
   for (int pass = 0; pass < 2; ++pass) {
@@ -195,10 +272,12 @@ int create_fan(scylla_lp* lp, int K, const double* targets, int round_K, scylla_
     for (int q = 0; q < 2; ++q) ATY[q] = ar.take<char>(vs * nk);
     XLR = ar.take<char>(vs * nk);
     YLR = ar.take<char>(vs * mk);
+    cw = ar.take<float2>(n);
     lob = ar.take<unsigned long long>(n);
     upb = ar.take<unsigned long long>(n);
     ctl = ar.take<Control>(K);
-    slot = ar.take<char>(sizeof(BatchSlot<double>) * K);
+    slot = ar.take<char>(sizeof(FanSlot<double>) * K);
+    state = ar.take<FanState>(1);
     pp = ar.take<double>(size_t(gp) * 1 * kFanMaxK);
     pd = ar.take<double>(size_t(gd) * 2 * kFanMaxK);
     pc1 = ar.take<double>(size_t(gc1) * kNC1 * kFanMaxK);
@@ -243,10 +322,12 @@ int create_fan(scylla_lp* lp, int K, const double* targets, int round_K, scylla_
     F.c_orig = lp->c_orig;
     F.lo_bits = lob;
     F.up_bits = upb;
+    F.cw = cw;
     F.t = t;
     F.om = om;
     F.ctl = ctl;
-    F.slot = static_cast<BatchSlot<TT>*>(slot);
+    F.slot = static_cast<FanSlot<TT>*>(slot);
+    F.state = state;
     F.part_p = pp;
     F.part_d = pd;
     F.part_c1 = pc1;
@@ -257,14 +338,19 @@ int create_fan(scylla_lp* lp, int K, const double* targets, int round_K, scylla_
     F.exp_grow = lp->p.step_growth_exp;
     F.d.step_fac = fac;  // the fan-out's own factor table
   };
+  f->pools = X[0];
+  f->pools_bytes = size_t(YLR + vs * mk - X[0]);
   if (mixed) {
     fill(g32, float{});
     f->f32 = g32;
-    return seed_state<float>(f, f->f32);
+    CKF(launch_fan_cw<float>(f->f32, cw, st));
+    const int rc = seed_state<float>(f, f->f32);
+    return rc != SCYLLA_OK ? rc : fan_tune<float>(f, f->f32, 0, 0);
   }
   fill(g64, double{});
   f->f64 = g64;
-  return seed_state<double>(f, f->f64);
+  const int rc = seed_state<double>(f, f->f64);
+  return rc != SCYLLA_OK ? rc : fan_tune<double>(f, f->f64, 0, 0);
 }
 
 }  // namespace
@@ -356,6 +442,91 @@ extern "C" int scylla_fanout_solve(scylla_fanout* f, double tol, int64_t iter_li
     r.seconds = f->last_ms * 1e-3;
   }
   if (seconds) *seconds = f->last_ms * 1e-3;
+  return SCYLLA_OK;
+}
+
+namespace {
+// the fan-out's kernels as separate launches with CUDA events around each (see
+// scylla_fanout_time_kernels)
+template <typename T>
+int fan_time_impl(scylla_fanout* f, DevFan<T>& F, int attempts, double* ms) {
+  scylla_lp* lp = f->lp;
+  cudaStream_t st = lp->st;
+  const int nchk = lp->p.n_check;
+  std::vector<std::pair<int, cudaEvent_t>> marks;  // (part, start); its end is the next entry's event
+  std::vector<cudaEvent_t> evs;
+  auto mark = [&](int part) -> cudaError_t {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return e;
+    evs.push_back(e0);
+    evs.push_back(e1);
+    e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) e = launch_fan_part<T>(F, part, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    marks.push_back({part, e0});
+    return e;
+  };
+  cudaError_t e = launch_fan_init<T>(F, 0.0, (long long)attempts + 1, 0, st);
+  if (e == cudaSuccess) e = launch_fan_check<T>(F, st);
+  for (int a = 0; a < attempts && e == cudaSuccess; ++a) {
+    for (int part = 0; part < 3 && e == cudaSuccess; ++part) e = mark(part);
+    if ((a + 1) % nchk == 0)
+      for (int part = 3; part < 6 && e == cudaSuccess; ++part) e = mark(part);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  double sum[6] = {0, 0, 0, 0, 0, 0};
+  int cnt[6] = {0, 0, 0, 0, 0, 0};
+  if (e == cudaSuccess)
+    for (size_t i = 0; i < marks.size(); ++i) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, evs[2 * i], evs[2 * i + 1]);
+      sum[marks[i].first] += t;
+      cnt[marks[i].first]++;
+    }
+  for (cudaEvent_t x : evs) cudaEventDestroy(x);
+  CKF(e);
+  for (int k = 0; k < 6; ++k) ms[k] = cnt[k] ? sum[k] / cnt[k] : 0.0;
+  return SCYLLA_OK;
+}
+}  // namespace
+
+extern "C" int scylla_fanout_time_kernels(scylla_fanout* f, int32_t attempts, double* ms) {
+  if (!f || !ms || attempts < 1) {
+    set_error("need a fan-out, ms[6] and attempts >= 1");
+    return SCYLLA_ERR_INVALID_ARG;
+  }
+  return f->lp->p.precision == SCYLLA_PREC_MIXED ? fan_time_impl<float>(f, f->f32, attempts, ms)
+                                                 : fan_time_impl<double>(f, f->f64, attempts, ms);
+}
+
+extern "C" int scylla_fanout_tune(scylla_fanout* f, int32_t shape_primal, int32_t shape_dual) {
+  if (!f) {
+    set_error("null fan-out");
+    return SCYLLA_ERR_INVALID_ARG;
+  }
+  const bool mixed = f->lp->p.precision == SCYLLA_PREC_MIXED;
+  for (const int s : {shape_primal, shape_dual})
+    if (s != 0 && !(mixed ? fan_shape_valid<float>(s) : fan_shape_valid<double>(s))) {
+      set_error("tile shape must be 0 (time all) or 1..4 (FP64: 2 or 4)");
+      return SCYLLA_ERR_INVALID_ARG;
+    }
+  return mixed ? fan_tune<float>(f, f->f32, shape_primal, shape_dual)
+               : fan_tune<double>(f, f->f64, shape_primal, shape_dual);
+}
+
+extern "C" int scylla_fanout_info(const scylla_fanout* f, int32_t* shape_primal, int32_t* shape_dual,
+                                  double* tune_ms) {
+  if (!f) {
+    set_error("null fan-out");
+    return SCYLLA_ERR_INVALID_ARG;
+  }
+  const bool mixed = f->lp->p.precision == SCYLLA_PREC_MIXED;
+  if (shape_primal) *shape_primal = mixed ? f->f32.shape_p : f->f64.shape_p;
+  if (shape_dual) *shape_dual = mixed ? f->f32.shape_d : f->f64.shape_d;
+  if (tune_ms)
+    for (int q = 0; q < 8; ++q) tune_ms[q] = f->tune_ms[q];
   return SCYLLA_OK;
 }
 

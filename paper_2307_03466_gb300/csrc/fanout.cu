@@ -3,19 +3,29 @@
 // bounds and differ only in the objective, done as sparse-times-tall-skinny
 // products so A is read once per K objectives.
 //
-// Layout: every K-wide vector is row-major (row j holds its K values contiguously),
-// so a nonzero a_ij gathers one contiguous K-wide row.  A warp owns a row of A (or
-// A^T); lane q owns objectives q and q + 32, so each lane keeps the step sizes and
-// flags of its objectives in registers.  The warp streams the row's (index, value)
-// pairs with one coalesced load per 32 nonzeros and broadcasts them with shuffles.
-// The objective of column k is generated on the fly from the base c and two bit
-// planes (target at the lower / upper bound) instead of being stored K times:
-// c_hat_jk = alpha^K s c_j + (1 - alpha^K) g_jk (Section 2.4).
+// Layout: every K-wide vector is row-major with 64 slots per row (row j holds the
+// values of objectives 0..63 contiguously, 256 bytes in FP32), so a nonzero a_ij
+// gathers one contiguous K-wide row.  The objective of column k is generated on the
+// fly from the base c and two bit planes (target at the lower / upper bound) instead
+// of being stored K times: c_hat_jk = alpha^K s c_j + (1 - alpha^K) g_jk
+// (Section 2.4).
+//
+// Pool roles are shared by every objective: X[cur], Y[cur], AX[cur] hold the
+// current points, [1 - cur] the next ones, [2] the running averages, ATY[0] and
+// ATY[1] the check's A^T y of the current and averaged points.  Every attempt
+// writes the next point of every slot and swaps cur.  An objective whose attempt was
+// rejected, or that restarts to (or finishes with) its average, has its slices
+// copied back into the current pool by k_fcopy before the next attempt (rare events,
+// a few scattered 4-byte columns); a finished objective is carried along unchanged
+// by zero step sizes.  So the SpMMs treat all 64 slots of a row alike and move them
+// with vector loads: a lane holds VEC consecutive objectives, CHUNK / VEC lanes
+// cover a row's CHUNK slots, and a warp works on 32 VEC / CHUNK rows at once
+// (64 / CHUNK sweeps over the matrix).  (VEC, CHUNK) is the tile shape the
+// create-time autotuner picks per SpMM.
 //
 // Every objective has its own control block (step size, primal weight, restarts,
-// termination) and pool roles; sums are per block and per objective, reduced per
-// objective by one warp in the control kernels, which apply the same logic as the
-// single-LP path.
+// termination); sums are per block and per objective, reduced per objective by one
+// warp in the control kernels, which apply the same logic as the single-LP path.
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -23,55 +33,11 @@
 
 namespace scylla {
 
-constexpr int kFK = 64;       // objectives per fan-out (two per lane)
+constexpr int kFK = 64;  // slots of a K-wide row
 constexpr int kFThreads = 256;
 constexpr int kFWarps = kFThreads / 32;
 
 __device__ __forceinline__ double fwarp_sum(double v) { return warp_sum(v); }
-
-template <typename T>
-struct FanLane {  // the per-objective values of one lane's two objectives
-  T tau[2], sigma[2], w[2], w1[2];
-  int cur[2], nxt[2], avg[2], ia_cur[2], ia_avg[2], flags[2];
-  bool on[2];
-};
-
-template <typename T>
-__device__ __forceinline__ void load_lane(const DevFan<T>& F, FanLane<T>& L, bool check) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int k = lane + 32 * q;
-    if (k < F.K) {
-      const BatchSlot<T> s = F.slot[k];
-      L.tau[q] = s.tau;
-      L.sigma[q] = s.sigma;
-      L.w[q] = s.w;
-      L.w1[q] = s.w1;
-      L.cur[q] = s.cur;
-      L.nxt[q] = s.nxt;
-      L.avg[q] = s.avg;
-      L.ia_cur[q] = s.ia_cur;
-      L.ia_avg[q] = s.ia_avg;
-      L.flags[q] = s.flags;
-      L.on[q] = (s.flags & (check ? 16 : 1)) != 0;
-    } else {
-      L.on[q] = false;
-      L.flags[q] = 0;
-      L.cur[q] = L.nxt[q] = L.avg[q] = L.ia_cur[q] = L.ia_avg[q] = 0;
-      L.tau[q] = L.sigma[q] = L.w[q] = L.w1[q] = T(0);
-    }
-  }
-}
-
-// g_jk of the l1 distance: +1 target at l_j, -1 target at u_j, 0 otherwise
-__device__ __forceinline__ double fan_g(const unsigned long long* lo_bits, const unsigned long long* up_bits, int j,
-                                        int k) {
-  const unsigned long long b = 1ULL << k;
-  if (lo_bits[j] & b) return 1.0;
-  if (up_bits[j] & b) return -1.0;
-  return 0.0;
-}
 
 // sum over the row's nonzeros of a_rp * src[col][k] for the lane's two objectives;
 // the (index, value) pairs are loaded 32 at a time and broadcast by shuffles, four
@@ -128,97 +94,498 @@ __device__ __forceinline__ void store_block_sums(const typename AccOf<T>::type* 
   }
 }
 
+// pool of the current points (the next points are in the other of pools 0 and 1)
 template <typename T>
-__global__ void __launch_bounds__(kFThreads) k_fprimal(DevFan<T> F) {
+__device__ __forceinline__ int fan_cur(const DevFan<T>& F) {
+  return int(F.state->att & 1ULL);
+}
+
+// ---------------------------------------------------------------- vectors ---
+template <typename T, int N>
+struct FVec;
+template <>
+struct FVec<float, 4> {
+  typedef float4 V;
+};
+template <>
+struct FVec<float, 2> {
+  typedef float2 V;
+};
+template <>
+struct FVec<double, 2> {
+  typedef double2 V;
+};
+
+template <typename T, int N>
+union VecU {
+  typename FVec<T, N>::V v;
+  T e[N];
+};
+
+template <typename T, int N>
+__device__ __forceinline__ void vld_nc(const T* p, T (&o)[N]) {
+  VecU<T, N> u;
+  u.v = __ldg(reinterpret_cast<const typename FVec<T, N>::V*>(p));
+#pragma unroll
+  for (int i = 0; i < N; ++i) o[i] = u.e[i];
+}
+// streaming accesses (read or written once per attempt and not gathered by the next
+// kernel): evict-first in L2, so the vector the next kernel gathers (x' written by
+// the primal, y' by the dual) and the one this kernel gathers keep their lines
+template <typename T, int N>
+__device__ __forceinline__ void vld_cs(const T* p, T (&o)[N]) {
+  VecU<T, N> u;
+  u.v = __ldcs(reinterpret_cast<const typename FVec<T, N>::V*>(p));
+#pragma unroll
+  for (int i = 0; i < N; ++i) o[i] = u.e[i];
+}
+template <typename T, int N>
+__device__ __forceinline__ void vst_cs(T* p, const T (&o)[N]) {
+  VecU<T, N> u;
+#pragma unroll
+  for (int i = 0; i < N; ++i) u.e[i] = o[i];
+  __stcs(reinterpret_cast<typename FVec<T, N>::V*>(p), u.v);
+}
+template <typename T, int N>
+__device__ __forceinline__ void vst(T* p, const T (&o)[N]) {
+  VecU<T, N> u;
+#pragma unroll
+  for (int i = 0; i < N; ++i) u.e[i] = o[i];
+  *reinterpret_cast<typename FVec<T, N>::V*>(p) = u.v;
+}
+
+// the tile shapes by number: (objectives per lane, slots per sweep) = 1: (4, 64),
+// 2: (2, 64), 3: (4, 32), 4: (2, 32)
+__host__ __device__ constexpr int fan_shape_vec(int s) { return (s == 1 || s == 3) ? 4 : 2; }
+__host__ __device__ constexpr int fan_shape_chunk(int s) { return (s == 3 || s == 4) ? 32 : 64; }
+
+// ---------------------------------------------------------- per-objective ---
+// The per-objective values of one attempt, copied to shared memory by every block
+// (structure of arrays, so a lane reads its VEC objectives from consecutive words).
+template <typename T>
+struct FanShared {
+  T tau[kFK], sigma[kFK], w[kFK], w1[kFK];
+  int flags[kFK];
+};
+
+template <typename T>
+__device__ __forceinline__ void load_fan_shared(const DevFan<T>& F, FanShared<T>& S) {
+  for (int k = threadIdx.x; k < kFK; k += blockDim.x) {
+    FanSlot<T> s;
+    if (k < F.K) {
+      s = F.slot[k];
+    } else {  // unused slots are carried like finished objectives
+      s.tau = s.sigma = s.w = T(0);
+      s.w1 = T(1);
+      s.flags = 0;
+    }
+    S.tau[k] = s.tau;
+    S.sigma[k] = s.sigma;
+    S.w[k] = s.w;
+    S.w1[k] = s.w1;
+    S.flags[k] = s.flags;
+  }
+  __syncthreads();
+}
+
+// c_hat_jk in the scaled space, C_j (t c_j + om g_jk): FP32 from the per-column pair
+// (t c_j C_j, om C_j) prepared at create; FP64 from the FP64 data as written
+template <typename T>
+__device__ __forceinline__ T fan_cost(const DevFan<T>& F, int j, int gi);
+template <>
+__device__ __forceinline__ float fan_cost<float>(const DevFan<float>& F, int j, int gi) {
+  const float2 w = __ldg(F.cw + j);
+  return fmaf(float(gi), w.y, w.x);
+}
+template <>
+__device__ __forceinline__ double fan_cost<double>(const DevFan<double>& F, int j, int gi) {
+  return (F.t * __ldg(F.c_orig + j) + F.om * double(gi)) * __ldg(F.d.C + j);
+}
+
+// ------------------------------------------------------------ SpMM sweeps ---
+// Geometry of a tile shape: LPR lanes per row, RPW rows per warp, NSW sweeps.
+template <int VEC, int CHUNK>
+struct FanGeo {
+  static constexpr int LPR = CHUNK / VEC;
+  static constexpr int RPW = 32 / LPR;
+  static constexpr int NSW = kFK / CHUNK;
+  static constexpr int NOBJ = NSW * VEC;  // objectives per lane over all sweeps
+};
+
+// One row's sum s[v] = sum_p a_p src(col_p)[v] in CSR order for the lane's VEC
+// objectives.  The segment's lanes hold the row's (index, value) pairs LPR at a time
+// (the first LPR loaded ahead in cl, vl) and broadcast them by shuffles within the
+// segment, four nonzeros per step so four vector gathers per lane are in flight.
+// The warp loops to the longest of its rows; a segment past its row's end issues no
+// load and adds nothing.
+template <typename T, int VEC, int LPR, typename Src>
+__device__ __forceinline__ void fan_vgather(int p0, int p1, int cl, T vl, const int* __restrict__ cols,
+                                            const T* __restrict__ vals, Src src, T (&s)[VEC]) {
+  const int sl = threadIdx.x & (LPR - 1);
+  constexpr int U = 4;
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) s[v] = T(0);
+  const int cnt = p1 - p0;
+  int maxcnt = cnt;
+#pragma unroll
+  for (int o = LPR; o < 32; o <<= 1) maxcnt = max(maxcnt, __shfl_xor_sync(0xffffffffu, maxcnt, o));
+  for (int b = 0; b < maxcnt; b += LPR) {
+    if (b != 0) {
+      cl = 0;
+      vl = T(0);
+      if (b + sl < cnt) {
+        cl = __ldg(cols + p0 + b + sl);
+        vl = __ldg(vals + p0 + b + sl);
+      }
+    }
+    const int lim = min(LPR, maxcnt - b);
+    for (int e = 0; e < lim; e += U) {
+      int c[U];
+      T a[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        c[u] = __shfl_sync(0xffffffffu, cl, (e + u) & (LPR - 1), LPR);
+        a[u] = __shfl_sync(0xffffffffu, vl, (e + u) & (LPR - 1), LPR);
+      }
+      T g[U][VEC];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (b + e + u < cnt) {
+          src(c[u], g[u]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) g[u][v] = T(0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (b + e + u < cnt)
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) s[v] = fma_t<T>(a[u], g[u][v], s[v]);
+    }
+  }
+}
+
+// per-block sums of the per-lane accumulators acc[t][o] (sum t; the lane's o-th
+// objective is slot (o / VEC) CHUNK + sl VEC + o % VEC) into
+// part[block][t][objective]; the segments of a warp hold the same objectives
+template <typename A, int VEC, int CHUNK, int NSUM>
+__device__ __forceinline__ void fan_block_sums(A (&acc)[NSUM][FanGeo<VEC, CHUNK>::NOBJ], double* part,
+                                               double* sh /*[kFWarps][NSUM][kFK]*/) {
+  typedef FanGeo<VEC, CHUNK> G;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, sl = lane & (G::LPR - 1);
+#pragma unroll
+  for (int t = 0; t < NSUM; ++t)
+#pragma unroll
+    for (int o = 0; o < G::NOBJ; ++o) {
+      A v = acc[t][o];
+#pragma unroll
+      for (int off = G::LPR; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      acc[t][o] = v;
+    }
+  if (lane < G::LPR)
+#pragma unroll
+    for (int t = 0; t < NSUM; ++t)
+#pragma unroll
+      for (int o = 0; o < G::NOBJ; ++o)
+        sh[(w * NSUM + t) * kFK + (o / VEC) * CHUNK + sl * VEC + (o % VEC)] = double(acc[t][o]);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < NSUM * kFK; idx += blockDim.x) {
+    double s = 0.0;
+    for (int v = 0; v < kFWarps; ++v) s += sh[v * NSUM * kFK + idx];
+    part[blockIdx.x * NSUM * kFK + idx] = s;
+  }
+}
+
+// Primal SpMM of one attempt for every objective (Algorithm 1, primal step):
+// x'_jk = proj_[l_j,u_j](x_jk + tau_k ((A^T Y)_jk - c_hat_jk)), the running average
+// and ||x' - x||^2 per objective.  Row groups are dealt gw, gw + nw, ...; while a
+// warp works on one group it has the row pointers of the group after the next and
+// the first (index, value) pairs of the next group in flight, and it loads the
+// group's epilogue operands before its gathers.
+template <typename T, int VEC, int CHUNK>
+__global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3) k_fprimal(DevFan<T> F) {
   typedef typename AccOf<T>::type A;
+  typedef FanGeo<VEC, CHUNK> G;
   __shared__ double sh[kFWarps * 1 * kFK];
-  FanLane<T> L;
-  load_lane(F, L, false);
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  __shared__ __align__(16) FanShared<T> S;
+  load_fan_shared(F, S);
   const DevLP<T>& d = F.d;
-  const int K = F.K;
-  A acc[2] = {A(0), A(0)};
-  const T* ysrc[2] = {F.Y[L.cur[0]], F.Y[L.cur[1]]};
-  auto src = [&](int i, T(&g)[2]) {
-    g[0] = L.on[0] ? __ldg(ysrc[0] + size_t(i) * K + lane) : T(0);
-    g[1] = L.on[1] ? __ldg(ysrc[1] + size_t(i) * K + lane + 32) : T(0);
-  };
-  for (int j = gw; j < d.n; j += nw) {
-    T s[2];
-    row_gather<T, T>(d.t_rowptr[j], d.t_rowptr[j + 1], d.t_cols, d.t_vals, src, s);
-    const double Cj = d.C[j], cj = F.c_orig[j];
-    const T lj = d.l[j], uj = d.u[j];
+  const int lane = threadIdx.x & 31, seg = lane / G::LPR, sl = lane & (G::LPR - 1);
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int n = d.n, cur = fan_cur(F);
+  const T* __restrict__ Xc = F.X[cur];
+  T* __restrict__ Xn = F.X[1 - cur];
+  T* __restrict__ Xa = F.X[2];
+  const T* __restrict__ Yc = F.Y[cur];
+  const T* __restrict__ At = F.ATY[0];
+  A acc[1][G::NOBJ];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      if (!L.on[q]) continue;
-      const int k = lane + 32 * q;
-      const size_t o = size_t(j) * K + k;
-      const bool cached = (L.flags[q] & 4) != 0;
-      T* aty = F.ATY[L.ia_cur[q]];
-      const T a = cached ? aty[o] : s[q];
-      if (!cached) aty[o] = a;
-      const T x = F.X[L.cur[q]][o];
-      if (L.flags[q] & 8) F.X[L.avg[q]][o] = blend(F.X[L.avg[q]][o], x, L.w1[q], L.w[q]);
-      if (L.flags[q] & 2) F.XLR[o] = x;
-      const T cs = T((F.t * cj + F.om * fan_g(F.lo_bits, F.up_bits, j, k)) * Cj);
-      const T v = clampv<T>(x + L.tau[q] * (a - cs), lj, uj);
-      F.X[L.nxt[q]][o] = v;
-      const A dx = A(v) - A(x);
-      acc[q] += dx * dx;
+  for (int o = 0; o < G::NOBJ; ++o) acc[0][o] = A(0);
+  const int ngroups = (n + G::RPW - 1) / G::RPW;
+#pragma unroll
+  for (int sw = 0; sw < G::NSW; ++sw) {
+    const int k0 = sw * CHUNK + sl * VEC;  // the lane's first objective in this sweep
+    T tau[VEC], w[VEC], w1[VEC];
+    int fl[VEC];
+    bool cached = false, avg = false, lr = false;
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+      tau[v] = S.tau[k0 + v];
+      w[v] = S.w[k0 + v];
+      w1[v] = S.w1[k0 + v];
+      fl[v] = S.flags[k0 + v];
+      cached |= (fl[v] & kSlotCached) != 0;
+      avg |= (fl[v] & kSlotAvg) != 0;
+      lr |= (fl[v] & kSlotCopyLr) != 0;
+    }
+    const T* ysrc = Yc + k0;
+    auto src = [&](int i, T(&g)[VEC]) { vld_nc<T, VEC>(ysrc + size_t(i) * kFK, g); };
+    auto rowp = [&](int gidx, int& a, int& b) {
+      const int j = gidx * G::RPW + seg;
+      a = b = 0;
+      if (gidx < ngroups && j < n) {
+        a = __ldg(d.t_rowptr + j);
+        b = __ldg(d.t_rowptr + j + 1);
+      }
+    };
+    int g = gw;
+    int p0, p1, pn0, pn1, cl = 0;
+    T vl = T(0);
+    rowp(g, p0, p1);
+    if (p0 + sl < p1) {
+      cl = __ldg(d.t_cols + p0 + sl);
+      vl = __ldg(d.t_vals + p0 + sl);
+    }
+    rowp(g + nw, pn0, pn1);
+    while (g < ngroups) {
+      int pnn0, pnn1, cln = 0;
+      T vln = T(0);
+      rowp(g + 2 * nw, pnn0, pnn1);
+      if (pn0 + sl < pn1) {
+        cln = __ldg(d.t_cols + pn0 + sl);
+        vln = __ldg(d.t_vals + pn0 + sl);
+      }
+      const int j = g * G::RPW + seg;
+      const bool live = j < n;
+      const size_t o = size_t(live ? j : 0) * kFK + k0;
+      T x[VEC], xa[VEC], at[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) x[v] = xa[v] = at[v] = T(0);
+      if (live) {
+        vld_cs<T, VEC>(Xc + o, x);
+        if (avg) vld_cs<T, VEC>(Xa + o, xa);
+        if (cached) vld_cs<T, VEC>(At + o, at);
+      }
+      T s[VEC];
+      fan_vgather<T, VEC, G::LPR>(p0, p1, cl, vl, d.t_cols, d.t_vals, src, s);
+      if (live) {
+        const unsigned long long lob = __ldg(F.lo_bits + j) >> k0, upb = __ldg(F.up_bits + j) >> k0;
+        const T lj = __ldg(d.l + j), uj = __ldg(d.u + j);
+        T xn[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+          // A^T y: the gathered sum, or the check's FP64 refresh of it (the checks of
+          // Section 2.2 recompute the products; the next attempt starts from them)
+          const T a = (fl[v] & kSlotCached) ? at[v] : s[v];
+          const int gi = int((lob >> v) & 1ULL) - int((upb >> v) & 1ULL);
+          const T cs = fan_cost<T>(F, j, gi);
+          xn[v] = clampv<T>(x[v] + tau[v] * (a - cs), lj, uj);
+          const A dx = A(xn[v]) - A(x[v]);
+          acc[0][sw * VEC + v] += dx * dx;
+          if (avg) xa[v] = blend(xa[v], x[v], w1[v], w[v]);
+        }
+        vst<T, VEC>(Xn + o, xn);
+        if (avg) vst_cs<T, VEC>(Xa + o, xa);
+        if (lr)
+#pragma unroll
+          for (int v = 0; v < VEC; ++v)
+            if (fl[v] & kSlotCopyLr) __stcs(F.XLR + o + v, x[v]);
+      }
+      g += nw;
+      p0 = pn0;
+      p1 = pn1;
+      pn0 = pnn0;
+      pn1 = pnn1;
+      cl = cln;
+      vl = vln;
     }
   }
-  store_block_sums<T>(acc, 1, F.part_p, sh);
+  fan_block_sums<A, VEC, CHUNK, 1>(acc, F.part_p, sh);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kFThreads) k_fdual(DevFan<T> F) {
+// Dual SpMM of one attempt for every objective (Algorithm 1, dual step with the
+// extrapolation A(2x' - x) = 2 A x' - A x from the cached A x): y', A x', the
+// running average, ||y' - y||^2 and (y' - y).(A x' - A x) per objective, with the
+// same look-ahead as the primal SpMM.
+template <typename T, int VEC, int CHUNK>
+__global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3) k_fdual(DevFan<T> F) {
   typedef typename AccOf<T>::type A;
+  typedef FanGeo<VEC, CHUNK> G;
   __shared__ double sh[kFWarps * 2 * kFK];
-  FanLane<T> L;
-  load_lane(F, L, false);
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  __shared__ __align__(16) FanShared<T> S;
+  load_fan_shared(F, S);
   const DevLP<T>& d = F.d;
-  const int K = F.K;
-  A acc[4] = {A(0), A(0), A(0), A(0)};  // [q][dy2, inter]
-  const T* xsrc[2] = {F.X[L.nxt[0]], F.X[L.nxt[1]]};
-  auto src = [&](int j, T(&g)[2]) {
-    g[0] = L.on[0] ? __ldg(xsrc[0] + size_t(j) * K + lane) : T(0);
-    g[1] = L.on[1] ? __ldg(xsrc[1] + size_t(j) * K + lane + 32) : T(0);
-  };
-  for (int i = gw; i < d.m; i += nw) {
-    T s[2];
-    row_gather<T, T>(d.a_rowptr[i], d.a_rowptr[i + 1], d.a_cols, d.a_vals, src, s);
-    const T lo = d.lo[i], hi = d.hi[i];
+  const int lane = threadIdx.x & 31, seg = lane / G::LPR, sl = lane & (G::LPR - 1);
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int m = d.m, cur = fan_cur(F);
+  const T* __restrict__ Xn = F.X[1 - cur];
+  const T* __restrict__ Yc = F.Y[cur];
+  T* __restrict__ Yn = F.Y[1 - cur];
+  T* __restrict__ Ya = F.Y[2];
+  const T* __restrict__ AXc = F.AX[cur];
+  T* __restrict__ AXn = F.AX[1 - cur];
+  A acc[2][G::NOBJ];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      if (!L.on[q]) continue;
-      const int k = lane + 32 * q;
-      const size_t o = size_t(i) * K + k;
-      const T ax = F.AX[L.cur[q]][o];
-      const T y = F.Y[L.cur[q]][o];
-      if (L.flags[q] & 8) F.Y[L.avg[q]][o] = blend(F.Y[L.avg[q]][o], y, L.w1[q], L.w[q]);
-      if (L.flags[q] & 2) F.YLR[o] = y;
-      const T axt = T(2) * s[q] - ax;
-      const T v = dual_prox<T>(y, L.sigma[q], axt, lo, hi);
-      F.Y[L.nxt[q]][o] = v;
-      F.AX[L.nxt[q]][o] = s[q];
-      const A dy = A(v) - A(y);
-      acc[2 * q] += dy * dy;
-      acc[2 * q + 1] += dy * (A(s[q]) - A(ax));
+  for (int o = 0; o < G::NOBJ; ++o) acc[0][o] = acc[1][o] = A(0);
+  const int ngroups = (m + G::RPW - 1) / G::RPW;
+#pragma unroll
+  for (int sw = 0; sw < G::NSW; ++sw) {
+    const int k0 = sw * CHUNK + sl * VEC;
+    T sig[VEC], w[VEC], w1[VEC];
+    int fl[VEC];
+    bool avg = false, lr = false;
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+      sig[v] = S.sigma[k0 + v];
+      w[v] = S.w[k0 + v];
+      w1[v] = S.w1[k0 + v];
+      fl[v] = S.flags[k0 + v];
+      avg |= (fl[v] & kSlotAvg) != 0;
+      lr |= (fl[v] & kSlotCopyLr) != 0;
+    }
+    const T* xsrc = Xn + k0;
+    auto src = [&](int jc, T(&g)[VEC]) { vld_nc<T, VEC>(xsrc + size_t(jc) * kFK, g); };
+    auto rowp = [&](int gidx, int& a, int& b) {
+      const int i = gidx * G::RPW + seg;
+      a = b = 0;
+      if (gidx < ngroups && i < m) {
+        a = __ldg(d.a_rowptr + i);
+        b = __ldg(d.a_rowptr + i + 1);
+      }
+    };
+    int g = gw;
+    int p0, p1, pn0, pn1, cl = 0;
+    T vl = T(0);
+    rowp(g, p0, p1);
+    if (p0 + sl < p1) {
+      cl = __ldg(d.a_cols + p0 + sl);
+      vl = __ldg(d.a_vals + p0 + sl);
+    }
+    rowp(g + nw, pn0, pn1);
+    while (g < ngroups) {
+      int pnn0, pnn1, cln = 0;
+      T vln = T(0);
+      rowp(g + 2 * nw, pnn0, pnn1);
+      if (pn0 + sl < pn1) {
+        cln = __ldg(d.a_cols + pn0 + sl);
+        vln = __ldg(d.a_vals + pn0 + sl);
+      }
+      const int i = g * G::RPW + seg;
+      const bool live = i < m;
+      const size_t o = size_t(live ? i : 0) * kFK + k0;
+      T ax[VEC], y[VEC], ya[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) ax[v] = y[v] = ya[v] = T(0);
+      if (live) {
+        vld_cs<T, VEC>(AXc + o, ax);
+        vld_cs<T, VEC>(Yc + o, y);
+        if (avg) vld_cs<T, VEC>(Ya + o, ya);
+      }
+      T s[VEC];
+      fan_vgather<T, VEC, G::LPR>(p0, p1, cl, vl, d.a_cols, d.a_vals, src, s);
+      if (live) {
+        const T lo = __ldg(d.lo + i), hi = __ldg(d.hi + i);
+        T yn[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+          const T axt = T(2) * s[v] - ax[v];
+          yn[v] = dual_prox<T>(y[v], sig[v], axt, lo, hi);
+          const A dy = A(yn[v]) - A(y[v]);
+          acc[0][sw * VEC + v] += dy * dy;
+          acc[1][sw * VEC + v] += dy * (A(s[v]) - A(ax[v]));
+          if (avg) ya[v] = blend(ya[v], y[v], w1[v], w[v]);
+        }
+        vst<T, VEC>(Yn + o, yn);
+        vst_cs<T, VEC>(AXn + o, s);
+        if (avg) vst_cs<T, VEC>(Ya + o, ya);
+        if (lr)
+#pragma unroll
+          for (int v = 0; v < VEC; ++v)
+            if (fl[v] & kSlotCopyLr) __stcs(F.YLR + o + v, y[v]);
+      }
+      g += nw;
+      p0 = pn0;
+      p1 = pn1;
+      pn0 = pnn0;
+      pn1 = pnn1;
+      cl = cln;
+      vl = vln;
     }
   }
-  store_block_sums<T>(acc, 2, F.part_d, sh);
+  // part_d is [block][sum][objective] with sum 0 = ||dy||^2, 1 = dy.(A x' - A x)
+  fan_block_sums<A, VEC, CHUNK, 2>(acc, F.part_d, sh);
 }
 
-// one warp per objective: block sums in a fixed order, then the step decision
+// ---------------------------------------------------------------- control ---
+// slot of one objective for the next attempt: an objective that does not attempt
+// (finished, or at its iteration limit until the next check ends it) is carried by
+// zero step sizes and no averaging, which leaves x, y and the average unchanged
 template <typename T>
-__global__ void k_fstep_control(DevFan<T> F) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) ++*F.kglob;
+__device__ __forceinline__ void write_fan_slot(FanSlot<T>* s, const Control* c) {
+  FanSlot<T> v;
+  const bool active = !c->done && c->k < c->iter_limit;
+  if (active) {
+    v.tau = T(c->eta / c->omega);
+    v.sigma = T(c->eta * c->omega);
+    v.w = T(c->avg_w);
+    v.w1 = T(1.0 - c->avg_w);
+    int f = kSlotActive | kSlotCheck;
+    if (c->copy_lr) f |= kSlotCopyLr;
+    if (c->aty_valid) f |= kSlotCached;
+    if (c->avg_w > 0.0) f |= kSlotAvg;
+    v.flags = f;
+  } else if (c->done) {
+    v.tau = v.sigma = v.w = T(0);
+    v.w1 = T(1);
+    v.flags = 0;
+  } else {
+    // at its iteration limit, waiting for the check that ends it: carried by zero
+    // step sizes, but the average still takes the last accepted point (the next
+    // attempt or the check blends it in; k_fstep_control then clears the weight)
+    v.tau = v.sigma = T(0);
+    v.w = T(c->avg_w);
+    v.w1 = T(1.0 - c->avg_w);
+    v.flags = kSlotCheck | (c->avg_w > 0.0 ? kSlotAvg : 0) | (c->copy_lr ? kSlotCopyLr : 0);
+  }
+  *s = v;
+}
+
+// One warp per objective: block sums in a fixed order, then the step decision;
+// rej[k] says whether objective k's attempt was rejected (k_fcopy_rej restores its
+// pair).  Block 0 counts the attempt, which swaps the pool roles of every objective.
+template <typename T>
+__global__ void __launch_bounds__(kFThreads) k_fstep_control(DevFan<T> F) {
+  FanState* st = F.state;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ++*F.kglob;
+    ++st->att;
+  }
   const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (k >= F.K) return;
-  if (!(F.slot[k].flags & 1)) return;
+  const int flags = F.slot[k].flags;
+  if (!(flags & kSlotActive)) {
+    if (lane == 0) {
+      st->rej[k] = 0;
+      if (flags & kSlotCheck) {  // carried: the pending average update is now applied
+        Control* c = &F.ctl[k];
+        c->avg_w = 0.0;
+        c->copy_lr = 0;
+        write_fan_slot(&F.slot[k], c);
+      }
+    }
+    return;
+  }
   const int G = F.grid_p, H = F.grid_d;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   for (int b = lane; b < G; b += 32) s0 += F.part_p[b * kFK + k];
@@ -231,65 +598,84 @@ __global__ void k_fstep_control(DevFan<T> F) {
   s2 = fwarp_sum(s2);
   if (lane == 0) {
     Control* c = &F.ctl[k];
+    const long long rej0 = c->rejected;
     step_control(c, s0, s1, s2, F.d.step_fac, F.d.n_check, nullptr, 0);
+    st->rej[k] = c->rejected != rej0 ? 1 : 0;
     if (c->done) atomicAdd(F.n_done, 1);
     write_fan_slot(&F.slot[k], c);
+    // the primal SpMM keeps no copy of A^T y: a retry after a rejected attempt (y
+    // restored by k_fcopy_rej) gathers it again
+    F.slot[k].flags &= ~kSlotCached;
   }
 }
 
 // FP64 column half of a check for every objective: A^T y of the current and the
-// averaged dual, reduced costs against c_hat_k, residuals, objectives, hash
+// averaged dual, reduced costs against c_hat_k, residuals, objectives, hash.  Lane
+// q of a warp works on objectives q and q + 32 of one column.
 template <typename T>
 __global__ void __launch_bounds__(kFThreads) k_fcheck_cols(DevFan<T> F) {
   __shared__ double sh[kFWarps * kNC1 * kFK];
-  FanLane<T> L;
-  load_lane(F, L, true);
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const DevLP<T>& d = F.d;
-  const int K = F.K;
+  const int cur = fan_cur(F);
+  bool on[2];
+  int fl[2];
+  T w[2], w1[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int k = lane + 32 * q;
+    fl[q] = k < F.K ? F.slot[k].flags : 0;
+    on[q] = (fl[q] & kSlotCheck) != 0;
+    w[q] = k < F.K ? F.slot[k].w : T(0);
+    w1[q] = k < F.K ? F.slot[k].w1 : T(1);
+  }
   double acc[2 * kNC1];
 #pragma unroll
   for (int q = 0; q < 2 * kNC1; ++q) acc[q] = 0.0;
   unsigned long long h[2] = {0ULL, 0ULL};
-  const T* yc[2] = {F.Y[L.cur[0]], F.Y[L.cur[1]]};
-  const T* ya[2] = {F.Y[L.avg[0]], F.Y[L.avg[1]]};
+  const T* yc = F.Y[cur];
+  const T* ya = F.Y[2];
+  T* Xc = F.X[cur];
+  T* Xa = F.X[2];
   for (int j = gw; j < d.n; j += nw) {
     double sc[2], sa[2];
     auto srcc = [&](int i, double(&g)[2]) {
-      g[0] = L.on[0] ? double(yc[0][size_t(i) * K + lane]) : 0.0;
-      g[1] = L.on[1] ? double(yc[1][size_t(i) * K + lane + 32]) : 0.0;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) g[q] = on[q] ? double(yc[size_t(i) * kFK + lane + 32 * q]) : 0.0;
     };
     auto srca = [&](int i, double(&g)[2]) {
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        if (!L.on[q]) {
+        if (!on[q]) {
           g[q] = 0.0;
           continue;
         }
-        const size_t o = size_t(i) * K + lane + 32 * q;
-        T v = ya[q][o];
-        if (L.flags[q] & 8) v = blend(v, yc[q][o], L.w1[q], L.w[q]);
+        const size_t o = size_t(i) * kFK + lane + 32 * q;
+        T v = ya[o];
+        if (fl[q] & kSlotAvg) v = blend(v, yc[o], w1[q], w[q]);
         g[q] = double(v);
       }
     };
     row_gather<double, double>(d.t_rowptr[j], d.t_rowptr[j + 1], d.t_cols, d.t_vals64, srcc, sc);
     row_gather<double, double>(d.t_rowptr[j], d.t_rowptr[j + 1], d.t_cols, d.t_vals64, srca, sa);
-    const double Cj = d.C[j], cj = F.c_orig[j], lj = d.l64[j], uj = d.u64[j];
+    const double Cj = d.C[j], lj = d.l64[j], uj = d.u64[j];
+    const unsigned long long lob = F.lo_bits[j], upb = F.up_bits[j];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      if (!L.on[q]) continue;
+      if (!on[q]) continue;
       const int k = lane + 32 * q;
-      const size_t o = size_t(j) * K + k;
-      const T x = F.X[L.cur[q]][o];
-      T xav = F.X[L.avg[q]][o];
-      if (L.flags[q] & 8) {
-        xav = blend(xav, x, L.w1[q], L.w[q]);
-        F.X[L.avg[q]][o] = xav;
+      const size_t o = size_t(j) * kFK + k;
+      const T x = Xc[o];
+      T xav = Xa[o];
+      if (fl[q] & kSlotAvg) {
+        xav = blend(xav, x, w1[q], w[q]);
+        Xa[o] = xav;
       }
-      F.ATY[L.ia_cur[q]][o] = T(sc[q]);
-      F.ATY[L.ia_avg[q]][o] = T(sa[q]);
-      const double cs = (F.t * cj + F.om * fan_g(F.lo_bits, F.up_bits, j, k)) * Cj;
+      F.ATY[0][o] = T(sc[q]);
+      F.ATY[1][o] = T(sa[q]);
+      const int gi = int((lob >> k) & 1ULL) - int((upb >> k) & 1ULL);
+      const double cs = (F.t * F.c_orig[j] + F.om * double(gi)) * Cj;
       const double xl = double(F.XLR[o]);
       const double xs[2] = {double(x), double(xav)};
       const double ss[2] = {sc[q], sa[q]};
@@ -316,49 +702,60 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_cols(DevFan<T> F) {
   store_block_sums<double>(acc, kNC1, F.part_c1, sh);
 #pragma unroll
   for (int q = 0; q < 2; ++q)
-    if (L.on[q] && h[q]) atomicAdd(&F.ctl[lane + 32 * q].hash_accum, h[q]);
+    if (on[q] && h[q]) atomicAdd(&F.ctl[lane + 32 * q].hash_accum, h[q]);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kFThreads) k_fcheck_rows(DevFan<T> F) {
   __shared__ double sh[kFWarps * kNC2 * kFK];
-  FanLane<T> L;
-  load_lane(F, L, true);
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const DevLP<T>& d = F.d;
-  const int K = F.K;
+  const int cur = fan_cur(F);
+  bool on[2];
+  int fl[2];
+  T w[2], w1[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int k = lane + 32 * q;
+    fl[q] = k < F.K ? F.slot[k].flags : 0;
+    on[q] = (fl[q] & kSlotCheck) != 0;
+    w[q] = k < F.K ? F.slot[k].w : T(0);
+    w1[q] = k < F.K ? F.slot[k].w1 : T(1);
+  }
   double acc[2 * kNC2];
 #pragma unroll
   for (int q = 0; q < 2 * kNC2; ++q) acc[q] = 0.0;
-  const T* xc[2] = {F.X[L.cur[0]], F.X[L.cur[1]]};
-  const T* xa[2] = {F.X[L.avg[0]], F.X[L.avg[1]]};
+  const T* xc = F.X[cur];
+  const T* xa = F.X[2];
+  T* Yc = F.Y[cur];
+  T* Ya = F.Y[2];
   for (int i = gw; i < d.m; i += nw) {
     double sc[2], sa[2];
     auto srcc = [&](int j, double(&g)[2]) {
-      g[0] = L.on[0] ? double(xc[0][size_t(j) * K + lane]) : 0.0;
-      g[1] = L.on[1] ? double(xc[1][size_t(j) * K + lane + 32]) : 0.0;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) g[q] = on[q] ? double(xc[size_t(j) * kFK + lane + 32 * q]) : 0.0;
     };
     auto srca = [&](int j, double(&g)[2]) {
-      g[0] = L.on[0] ? double(xa[0][size_t(j) * K + lane]) : 0.0;
-      g[1] = L.on[1] ? double(xa[1][size_t(j) * K + lane + 32]) : 0.0;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) g[q] = on[q] ? double(xa[size_t(j) * kFK + lane + 32 * q]) : 0.0;
     };
     row_gather<double, double>(d.a_rowptr[i], d.a_rowptr[i + 1], d.a_cols, d.a_vals64, srcc, sc);
     row_gather<double, double>(d.a_rowptr[i], d.a_rowptr[i + 1], d.a_cols, d.a_vals64, srca, sa);
     const double Ri = d.R[i], lo = d.lo64[i], hi = d.hi64[i];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      if (!L.on[q]) continue;
+      if (!on[q]) continue;
       const int k = lane + 32 * q;
-      const size_t o = size_t(i) * K + k;
-      const T y = F.Y[L.cur[q]][o];
-      T yav = F.Y[L.avg[q]][o];
-      if (L.flags[q] & 8) {
-        yav = blend(yav, y, L.w1[q], L.w[q]);
-        F.Y[L.avg[q]][o] = yav;
+      const size_t o = size_t(i) * kFK + k;
+      const T y = Yc[o];
+      T yav = Ya[o];
+      if (fl[q] & kSlotAvg) {
+        yav = blend(yav, y, w1[q], w[q]);
+        Ya[o] = yav;
       }
-      F.AX[L.cur[q]][o] = T(sc[q]);
-      F.AX[L.avg[q]][o] = T(sa[q]);
+      F.AX[cur][o] = T(sc[q]);
+      F.AX[2][o] = T(sa[q]);
       const double yl = double(F.YLR[o]);
       const double ys[2] = {double(y), double(yav)};
       const double ss[2] = {sc[q], sa[q]};
@@ -378,21 +775,27 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_rows(DevFan<T> F) {
   store_block_sums<double>(acc, kNC2, F.part_c2, sh);
 }
 
-// one warp per objective: check sums in a fixed order, then check_control; block 0
-// refills the step-size factor table shared by the objectives still running
+// One warp per objective: check sums in a fixed order, then check_control.  An
+// objective that restarts to its average or finishes with it (the single-LP path
+// swaps its pool roles) gets rst[k] = 1 instead, and k_fcopy_rst copies the
+// average into the current pool.  Block 0 refills the step-size factor table
+// shared by the objectives still running.
 template <typename T>
-__global__ void k_fcheck_control(DevFan<T> F) {
-  if (blockIdx.x == 0) {
-    const long long k0 = *F.kglob;
+__global__ void __launch_bounds__(kFThreads) k_fcheck_control(DevFan<T> F) {
+  FanState* st = F.state;
+  const long long k0 = *F.kglob;
+  if (blockIdx.x == 0)
     for (int i = threadIdx.x; i < F.d.n_check; i += blockDim.x) {
       const double kk = double(k0 + 1 + i + 1);
       F.d.step_fac[2 * i] = 1.0 - pow(kk, -F.exp_red);
       F.d.step_fac[2 * i + 1] = 1.0 + pow(kk, -F.exp_grow);
     }
-  }
   const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (k >= F.K) return;
-  if (!(F.slot[k].flags & 16)) return;
+  if (!(F.slot[k].flags & kSlotCheck)) {
+    if (lane == 0) st->rst[k] = 0;
+    return;
+  }
   double r[kNC1 + kNC2];
 #pragma unroll
   for (int s = 0; s < kNC1 + kNC2; ++s) r[s] = 0.0;
@@ -406,10 +809,53 @@ __global__ void k_fcheck_control(DevFan<T> F) {
   for (int s = 0; s < kNC1 + kNC2; ++s) r[s] = fwarp_sum(r[s]);
   if (lane == 0) {
     Control* c = &F.ctl[k];
-    c->k_fac = *F.kglob;
+    const int ix0 = c->ix_cur, ia0 = c->ia_cur;
+    c->k_fac = k0;
     check_control(c, r, nullptr, 0);
+    st->rst[k] = 0;
+    if (c->ix_cur != ix0) {  // to the average: copy instead of swapping roles
+      st->rst[k] = 1;
+      c->ix_avg = c->ix_cur;
+      c->ix_cur = ix0;
+      c->ia_avg = c->ia_cur;
+      c->ia_cur = ia0;
+    }
     if (c->done) atomicAdd(F.n_done, 1);
     write_fan_slot(&F.slot[k], c);
+  }
+}
+
+// Copies into the current pool, after the control kernels: RST = false, the
+// objectives whose attempt was rejected get back the point they attempted from (now
+// in the next pool: x, y, A x); RST = true, the ones that restart to or finish
+// with their average get the average (x, y, A x and the check's A^T y).  Row per
+// warp, lane q on slots q and q + 32; nothing to do unless a flag is set.
+template <typename T, bool RST>
+__global__ void __launch_bounds__(kFThreads) k_fcopy(DevFan<T> F) {
+  const FanState* st = F.state;
+  const int lane = threadIdx.x & 31;
+  const unsigned char* flag = RST ? st->rst : st->rej;
+  bool mine[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) mine[q] = lane + 32 * q < F.K && flag[lane + 32 * q] != 0;
+  if (!__any_sync(0xffffffffu, mine[0] || mine[1])) return;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int cur = fan_cur(F), from = RST ? 2 : 1 - cur;
+  const int rows = max(F.d.n, F.d.m);
+  for (int r = gw; r < rows; r += nw) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (!mine[q]) continue;
+      const size_t o = size_t(r) * kFK + lane + 32 * q;
+      if (r < F.d.n) {
+        F.X[cur][o] = F.X[from][o];
+        if (RST) F.ATY[0][o] = F.ATY[1][o];
+      }
+      if (r < F.d.m) {
+        F.Y[cur][o] = F.Y[from][o];
+        F.AX[cur][o] = F.AX[from][o];
+      }
+    }
   }
 }
 
@@ -443,46 +889,111 @@ __global__ void k_finit(DevFan<T> F, double tol, long long iter_limit, int stall
   write_fan_slot(&F.slot[k], c);
 }
 
-// every objective starts from the same pair: x0, y0 (scaled, length n / m), roles 0
+// every slot starts from the same pair x0, y0 (scaled, length n / m) in pool 0
 template <typename T>
 __global__ void k_fseed(DevFan<T> F, const T* x0, const T* y0) {
-  const int K = F.K;
-  const size_t nk = size_t(F.d.n) * K, mk = size_t(F.d.m) * K;
+  const size_t nk = size_t(F.d.n) * kFK, mk = size_t(F.d.m) * kFK;
   const size_t stride = size_t(gridDim.x) * blockDim.x;
-  for (size_t o = size_t(blockIdx.x) * blockDim.x + threadIdx.x; o < nk; o += stride) F.X[0][o] = x0[o / K];
-  for (size_t o = size_t(blockIdx.x) * blockDim.x + threadIdx.x; o < mk; o += stride) F.Y[0][o] = y0[o / K];
+  const size_t t0 = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t0 < 64) {
+    if (t0 == 0) F.state->att = 0ULL;
+    F.state->rej[t0] = 0;
+    F.state->rst[t0] = 0;
+  }
+  for (size_t o = t0; o < nk; o += stride) F.X[0][o] = x0[o / kFK];
+  for (size_t o = t0; o < mk; o += stride) F.Y[0][o] = y0[o / kFK];
+}
+
+// FP32 objective pairs (t c_j C_j, om C_j) of the scaled space, one per column
+template <typename T>
+__global__ void k_fcw(DevFan<T> F, float2* cw) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < F.d.n; j += gridDim.x * blockDim.x) {
+    const double Cj = F.d.C[j];
+    cw[j] = make_float2(float(F.t * F.c_orig[j] * Cj), float(F.om * Cj));
+  }
 }
 
 template <typename T>
 __global__ void k_fget_x(DevFan<T> F, int k, double* out) {
-  const T* x = F.X[F.ctl[k].ix_cur];
+  const T* x = F.X[fan_cur(F)];
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < F.d.n; j += gridDim.x * blockDim.x)
-    out[j] = double(x[size_t(j) * F.K + k]) * F.d.C[j];
+    out[j] = double(x[size_t(j) * kFK + k]) * F.d.C[j];
 }
 
 // ----------------------------------------------------------------- launchers ---
+// kernel of a tile shape (see fan_shape_vec); FP64 takes shapes 2 and 4
+template <typename T>
+const void* fan_spmm_kernel(int side, int shape);
+template <>
+const void* fan_spmm_kernel<float>(int side, int shape) {
+  switch (shape) {
+    case 1: return side == 0 ? (const void*)k_fprimal<float, 4, 64> : (const void*)k_fdual<float, 4, 64>;
+    case 3: return side == 0 ? (const void*)k_fprimal<float, 4, 32> : (const void*)k_fdual<float, 4, 32>;
+    case 4: return side == 0 ? (const void*)k_fprimal<float, 2, 32> : (const void*)k_fdual<float, 2, 32>;
+    default: return side == 0 ? (const void*)k_fprimal<float, 2, 64> : (const void*)k_fdual<float, 2, 64>;
+  }
+}
+template <>
+const void* fan_spmm_kernel<double>(int side, int shape) {
+  if (shape == 4) return side == 0 ? (const void*)k_fprimal<double, 2, 32> : (const void*)k_fdual<double, 2, 32>;
+  return side == 0 ? (const void*)k_fprimal<double, 2, 64> : (const void*)k_fdual<double, 2, 64>;
+}
+
+template <typename T>
+cudaError_t launch_spmm(const DevFan<T>& F, int side, cudaStream_t st) {
+  DevFan<T> arg = F;
+  void* args[] = {&arg};
+  const int grid = side == 0 ? F.grid_p : F.grid_d;
+  return cudaLaunchKernel(fan_spmm_kernel<T>(side, side == 0 ? F.shape_p : F.shape_d), dim3(grid), dim3(kFThreads),
+                          args, 0, st);
+}
+
 template <typename T>
 cudaError_t launch_fan_init(const DevFan<T>& F, double tol, long long iter_limit, int stall_checks, cudaStream_t st) {
   k_finit<T><<<1, kFK, 0, st>>>(F, tol, iter_limit, stall_checks);
   return cudaGetLastError();
 }
+
+// one kernel of an attempt or a check on its own (measurement): 0 primal, 1 dual,
+// 2 step control, 3 column check, 4 row check, 5 check control, 6 copies after the
+// step control, 7 copies after the check control
 template <typename T>
-cudaError_t launch_fan_slot(const DevFan<T>& F, cudaStream_t st) {
-  k_fprimal<T><<<F.grid_p, kFThreads, 0, st>>>(F);
-  k_fdual<T><<<F.grid_d, kFThreads, 0, st>>>(F);
-  k_fstep_control<T><<<(F.K * 32 + kFThreads - 1) / kFThreads, kFThreads, 0, st>>>(F);
+cudaError_t launch_fan_part(const DevFan<T>& F, int part, cudaStream_t st) {
+  const int ctl_grid = (F.K * 32 + kFThreads - 1) / kFThreads;
+  switch (part) {
+    case 0: return launch_spmm<T>(F, 0, st);
+    case 1: return launch_spmm<T>(F, 1, st);
+    case 2: k_fstep_control<T><<<ctl_grid, kFThreads, 0, st>>>(F); break;
+    case 3: k_fcheck_cols<T><<<F.grid_c1, kFThreads, 0, st>>>(F); break;
+    case 4: k_fcheck_rows<T><<<F.grid_c2, kFThreads, 0, st>>>(F); break;
+    case 5: k_fcheck_control<T><<<ctl_grid, kFThreads, 0, st>>>(F); break;
+    case 6: k_fcopy<T, false><<<F.grid_copy, kFThreads, 0, st>>>(F); break;
+    default: k_fcopy<T, true><<<F.grid_copy, kFThreads, 0, st>>>(F); break;
+  }
   return cudaGetLastError();
 }
 template <typename T>
+cudaError_t launch_fan_slot(const DevFan<T>& F, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  for (int part : {0, 1, 2, 6})
+    if (e == cudaSuccess) e = launch_fan_part<T>(F, part, st);
+  return e;
+}
+template <typename T>
 cudaError_t launch_fan_check(const DevFan<T>& F, cudaStream_t st) {
-  k_fcheck_cols<T><<<F.grid_c1, kFThreads, 0, st>>>(F);
-  k_fcheck_rows<T><<<F.grid_c2, kFThreads, 0, st>>>(F);
-  k_fcheck_control<T><<<(F.K * 32 + kFThreads - 1) / kFThreads, kFThreads, 0, st>>>(F);
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  for (int part : {3, 4, 5, 7})
+    if (e == cudaSuccess) e = launch_fan_part<T>(F, part, st);
+  return e;
 }
 template <typename T>
 cudaError_t launch_fan_seed(const DevFan<T>& F, const void* x0, const void* y0, cudaStream_t st) {
   k_fseed<T><<<4 * device_sm_count(), kFThreads, 0, st>>>(F, static_cast<const T*>(x0), static_cast<const T*>(y0));
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_fan_cw(const DevFan<T>& F, float2* cw, cudaStream_t st) {
+  k_fcw<T><<<2 * device_sm_count(), kFThreads, 0, st>>>(F, cw);
   return cudaGetLastError();
 }
 template <typename T>
@@ -491,28 +1002,39 @@ cudaError_t launch_fan_get_x(const DevFan<T>& F, int k, double* out, cudaStream_
   return cudaGetLastError();
 }
 template <typename T>
+bool fan_shape_valid(int shape) {
+  return sizeof(T) == 4 ? (shape >= 1 && shape <= 4) : (shape == 2 || shape == 4);
+}
+template <typename T>
 void fan_grids(DevFan<T>& F) {
-  auto grid = [](const void* k, int rows) {
+  auto grid = [](const void* k, long long units) {
     int per_sm = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kFThreads, 0) != cudaSuccess || per_sm < 1)
       per_sm = 1;
-    long long need = (rows + kFWarps - 1) / kFWarps;
+    long long need = (units + kFWarps - 1) / kFWarps;
     if (need < 1) need = 1;
     const long long cap = (long long)per_sm * device_sm_count();
     return int(need < cap ? need : cap);
   };
-  F.grid_p = grid((const void*)k_fprimal<T>, F.d.n);
-  F.grid_d = grid((const void*)k_fdual<T>, F.d.m);
+  // rows per warp of a shape: 32 VEC / CHUNK
+  const int rpw_p = 32 * fan_shape_vec(F.shape_p) / fan_shape_chunk(F.shape_p);
+  const int rpw_d = 32 * fan_shape_vec(F.shape_d) / fan_shape_chunk(F.shape_d);
+  F.grid_p = grid(fan_spmm_kernel<T>(0, F.shape_p), (F.d.n + rpw_p - 1) / rpw_p);
+  F.grid_d = grid(fan_spmm_kernel<T>(1, F.shape_d), (F.d.m + rpw_d - 1) / rpw_d);
   F.grid_c1 = grid((const void*)k_fcheck_cols<T>, F.d.n);
   F.grid_c2 = grid((const void*)k_fcheck_rows<T>, F.d.m);
+  F.grid_copy = grid((const void*)k_fcopy<T, false>, F.d.n > F.d.m ? F.d.n : F.d.m);
 }
 
 #define SCYLLA_INSTANTIATE_FAN(T)                                                                      \
   template cudaError_t launch_fan_init<T>(const DevFan<T>&, double, long long, int, cudaStream_t);     \
   template cudaError_t launch_fan_slot<T>(const DevFan<T>&, cudaStream_t);                             \
   template cudaError_t launch_fan_check<T>(const DevFan<T>&, cudaStream_t);                            \
+  template cudaError_t launch_fan_part<T>(const DevFan<T>&, int, cudaStream_t);                        \
   template cudaError_t launch_fan_seed<T>(const DevFan<T>&, const void*, const void*, cudaStream_t);   \
   template cudaError_t launch_fan_get_x<T>(const DevFan<T>&, int, double*, cudaStream_t);              \
+  template cudaError_t launch_fan_cw<T>(const DevFan<T>&, float2*, cudaStream_t);                     \
+  template bool fan_shape_valid<T>(int);                                                               \
   template void fan_grids<T>(DevFan<T>&);
 
 SCYLLA_INSTANTIATE_FAN(double)

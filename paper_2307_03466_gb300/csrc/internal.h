@@ -150,15 +150,31 @@ struct DevBatch {
   int grid_p, grid_d, grid_c1, grid_c2, grid_ctl;
 };
 
-// K objectives of one LP solved together: K-wide vectors are row-major (n x K, m x K).
+// Per-objective values of one attempt of a fan-out, written by its control kernels.
+template <typename T>
+struct FanSlot {
+  T tau, sigma, w, w1;
+  int flags;
+};
+
+// Pool roles shared by every objective of a fan-out, and the objectives whose
+// slices the copy kernels move into the current pool before the next attempt.
+struct FanState {
+  unsigned long long att;     // attempts since seeding: X[att & 1], Y[.], AX[.] hold the current points
+  unsigned char rej[64];      // 1: rejected in the last attempt (next pool -> current), written every attempt
+  unsigned char rst[64];      // 1: restarted to or finished with the average (average -> current), every check
+};
+
+// K objectives of one LP solved together: K-wide vectors are row-major with 64
+// slots per row (n x 64, m x 64); objectives K..63 are carried unchanged.
 template <typename T>
 struct DevFan {
   DevLP<T> d;  // the base LP: matrices, bounds, scaling (its iterate pools unused)
   int K;
-  T* X[3];
+  T* X[3];     // [cur], [1 - cur] with cur = state->att & 1; [2] the running average
   T* Y[3];
   T* AX[3];
-  T* ATY[2];
+  T* ATY[2];   // the checks' A^T y of the current [0] and averaged [1] point
   T* XLR;
   T* YLR;
   const double* c_orig;                // unscaled base objective, n
@@ -166,12 +182,18 @@ struct DevFan {
   const unsigned long long* up_bits;   // bit k of column j: target k at u_j
   double t, om;                        // alpha^K s and 1 - alpha^K of the update
   Control* ctl;                        // K control blocks
-  BatchSlot<T>* slot;                  // K
+  FanSlot<T>* slot;                    // K
+  FanState* state;
   double *part_p, *part_d, *part_c1, *part_c2;  // [block][sum][objective]
   int* n_done;
   long long* kglob;
   double exp_red, exp_grow;
-  int grid_p, grid_d, grid_c1, grid_c2;
+  int grid_p, grid_d, grid_c1, grid_c2, grid_copy;
+  // FP32 objective of the scaled space per column: (t c_j C_j, om C_j)
+  const float2* cw;
+  // tile shape of the primal and dual SpMM (objectives per lane, slots per sweep):
+  // 1 = (4, 64), 2 = (2, 64), 3 = (4, 32), 4 = (2, 32); FP64 takes 2 and 4
+  int shape_p, shape_d;
 };
 
 // Buffers of the original (unaugmented) columns used by the objective update and
@@ -370,12 +392,19 @@ cudaError_t launch_fan_slot(const DevFan<T>& F, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fan_check(const DevFan<T>& F, cudaStream_t st);
 template <typename T>
+cudaError_t launch_fan_part(const DevFan<T>& F, int part, cudaStream_t st);
+template <typename T>
 cudaError_t launch_fan_seed(const DevFan<T>& F, const void* x0, const void* y0, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fan_cw(const DevFan<T>& F, float2* cw, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fan_get_x(const DevFan<T>& F, int k, double* out, cudaStream_t st);
 template <typename T>
 void fan_grids(DevFan<T>& F);
+template <typename T>
+bool fan_shape_valid(int shape);
 constexpr int kFanMaxK = 64;
+
 
 // shared host helpers (lp.cpp)
 std::vector<int2> build_tiles_range(const std::vector<int>& rowptr, int r_begin, int r_end, int max_rows = kTileRows);

@@ -127,6 +127,9 @@ _SIGS = {
     "scylla_fanout_solve": (C.c_int, [_P, C.c_double, C.c_int64, C.POINTER(PdhgResult), _D]),
     "scylla_fanout_get_primal": (C.c_int, [_P, C.c_int32, _D]),
     "scylla_fanout_reset_state": (C.c_int, [_P]),
+    "scylla_fanout_time_kernels": (C.c_int, [_P, C.c_int32, _D]),
+    "scylla_fanout_tune": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "scylla_fanout_info": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _D]),
     "scylla_last_error": (C.c_char_p, []),
 }
 
@@ -523,3 +526,22 @@ class Fanout:
 
     def reset_state(self):
         _check(lib().scylla_fanout_reset_state(self.h))
+
+    def tune(self, shape_primal: int = 0, shape_dual: int = 0):
+        """scylla_fanout_tune: 0 times every tile shape, 1..4 forces one."""
+        _check(lib().scylla_fanout_tune(self.h, int(shape_primal), int(shape_dual)))
+
+    def info(self):
+        """(tile shape of the primal and dual SpMM, the tuner's ms per launch: primal
+        shapes 1..4, then dual shapes 1..4)."""
+        a, b = C.c_int32(), C.c_int32()
+        ms = np.zeros(8)
+        _check(lib().scylla_fanout_info(self.h, C.byref(a), C.byref(b), _dp(ms)))
+        return a.value, b.value, ms
+
+    def time_kernels(self, attempts: int) -> np.ndarray:
+        """Mean device ms of the primal SpMM, dual SpMM, step control, column check,
+        row check and check control (scylla_fanout_time_kernels)."""
+        ms = np.zeros(6)
+        _check(lib().scylla_fanout_time_kernels(self.h, int(attempts), _dp(ms)))
+        return ms

@@ -105,3 +105,81 @@ def test_fanout_needs_lp_without_aux_columns():
         S.Fanout(lp, np.zeros((inst.n, 2)))
     assert ei.value.code == S.ERR_UNSUPPORTED
     lp.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tile_shapes_identical_in_fixed_step_and_tuner_reports(precision):
+    """The autotuner's tile shapes of the two SpMMs (objectives per lane, slots per
+    sweep) compute every entry of x', y' and A x' with the same sums in the same
+    order.  Only the order in which the per-objective step-size sums are reduced
+    depends on the shape (rows per warp), and the fixed-step mode takes no decision
+    from them: there every forced shape gives identical iterates.  The tuner reports
+    the shapes it chose and its timings."""
+    S, inst, base, targets, state, params = setup(K=40, precision=precision, adaptive_step=0, restarts=0)
+    F = S.Fanout(base, targets, round_K=1)
+    sp, sd, ms = F.info()
+    valid = (1, 2, 3, 4) if precision == 1 else (2, 4)
+    assert sp in valid and sd in valid
+    assert all(ms[s - 1] > 0 and ms[4 + s - 1] > 0 for s in valid)
+    xs = {}
+    for shapes in [(a, b) for a in valid for b in valid]:
+        F.tune(*shapes)
+        assert F.info()[:2] == shapes
+        F.solve(0.0, 150)
+        xs[shapes] = np.stack([F.primal(q) for q in range(targets.shape[1])])
+    ref = xs[(valid[0], valid[0])]
+    for shapes, v in xs.items():
+        np.testing.assert_array_equal(v, ref, err_msg=str(shapes))
+    with pytest.raises(S.ScyllaError):
+        F.tune(5, 0)
+    if precision == 0:
+        with pytest.raises(S.ScyllaError):
+            F.tune(1, 0)  # FP64 takes shapes 2 and 4
+    F.close()
+    base.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tile_shapes_converge_alike_with_rejections_and_restarts(precision):
+    """Adaptive solves in every shape (rejected attempts and restarts to the average
+    on the way, so the pool copies run) converge per objective to the single-LP
+    solve's objective."""
+    S, inst, base, targets, state, params = setup(K=40, precision=precision)
+    F = S.Fanout(base, targets, round_K=1)
+    valid = (1, 2, 3, 4) if precision == 1 else (2, 4)
+    tol = 1e-6 if precision == 0 else 1e-4
+    ref = {}
+    for q in range(0, targets.shape[1], 7):
+        g, r = single(S, inst, params, state, targets[:, q], 200000, tol=1e-8)
+        ref[q] = r.pobj
+        g.close()
+    rej = rst = 0
+    for shapes in [(s, s) for s in valid]:
+        F.tune(*shapes)
+        res, _ = F.solve(tol, 200000)
+        rej += sum(r.rejected for r in res)
+        rst += sum(r.restarts for r in res)
+        for q, pobj in ref.items():
+            assert res[q].status == O.CONVERGED, (shapes, q)
+            assert abs(res[q].pobj - pobj) <= 10 * tol * (1 + abs(pobj)), (shapes, q, res[q].pobj, pobj)
+    assert rej > 0 and rst > 0
+    F.close()
+    base.close()
+
+
+def test_second_solve_continues_from_the_first():
+    """A solve that stops at an iteration limit leaves every objective's pair in the
+    current pool (finished objectives carried, averages copied in): a second solve
+    continues from there, as one longer solve does, up to the restart schedule's
+    dependence on the attempt count (same objectives converged, same answers)."""
+    S, inst, base, targets, state, params = setup(K=8, precision=0)
+    F = S.Fanout(base, targets, round_K=1)
+    r1, _ = F.solve(1e-7, 128)
+    r2, _ = F.solve(1e-7, 200000)
+    for q in range(targets.shape[1]):
+        assert r2[q].status == O.CONVERGED, q
+        g, r = single(S, inst, params, state, targets[:, q], 200000, tol=1e-7)
+        assert abs(r2[q].pobj - r.pobj) <= 1e-5 * (1 + abs(r.pobj)), q
+        g.close()
+    F.close()
+    base.close()
