@@ -188,18 +188,31 @@ __device__ __forceinline__ void load_fan_shared(const DevFan<T>& F, FanShared<T>
   __syncthreads();
 }
 
-// c_hat_jk in the scaled space, C_j (t c_j + om g_jk): FP32 from the per-column pair
-// (t c_j C_j, om C_j) prepared at create; FP64 from the FP64 data as written
+// c_hat_jk in the scaled space, C_j (t c_j + om g_jk), g_jk in {-1, 0, 1}: the
+// column's three possible values are formed once per column and selected per
+// objective.  FP32 from the per-column pair (t c_j C_j, om C_j) prepared at create;
+// FP64 as (t c_j + om g) C_j, the same rounding for each g as written out.
 template <typename T>
-__device__ __forceinline__ T fan_cost(const DevFan<T>& F, int j, int gi);
+struct FanCostCol {
+  T c0, cp, cm;  // g = 0, +1, -1
+  __device__ __forceinline__ T at(int gi) const { return gi > 0 ? cp : (gi < 0 ? cm : c0); }
+};
+template <typename T>
+__device__ __forceinline__ FanCostCol<T> fan_cost_col(const DevFan<T>& F, int j);
 template <>
-__device__ __forceinline__ float fan_cost<float>(const DevFan<float>& F, int j, int gi) {
+__device__ __forceinline__ FanCostCol<float> fan_cost_col<float>(const DevFan<float>& F, int j) {
   const float2 w = __ldg(F.cw + j);
-  return fmaf(float(gi), w.y, w.x);
+  return FanCostCol<float>{w.x, w.x + w.y, w.x - w.y};
 }
 template <>
-__device__ __forceinline__ double fan_cost<double>(const DevFan<double>& F, int j, int gi) {
-  return (F.t * __ldg(F.c_orig + j) + F.om * double(gi)) * __ldg(F.d.C + j);
+__device__ __forceinline__ FanCostCol<double> fan_cost_col<double>(const DevFan<double>& F, int j) {
+  const double tc = F.t * __ldg(F.c_orig + j), Cj = __ldg(F.d.C + j);
+  return FanCostCol<double>{tc * Cj, (tc + F.om) * Cj, (tc - F.om) * Cj};
+}
+// the same three values in FP64 for the checks
+__device__ __forceinline__ FanCostCol<double> fan_cost_col64(double t, double om, double c, double Cj) {
+  const double tc = t * c;
+  return FanCostCol<double>{tc * Cj, (tc + om) * Cj, (tc - om) * Cj};
 }
 
 // ------------------------------------------------------------ SpMM sweeps ---
@@ -382,14 +395,14 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
       if (live) {
         const unsigned long long lob = __ldg(F.lo_bits + j) >> k0, upb = __ldg(F.up_bits + j) >> k0;
         const T lj = __ldg(d.l + j), uj = __ldg(d.u + j);
+        const FanCostCol<T> cc = fan_cost_col<T>(F, j);
         T xn[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
           // A^T y: the gathered sum, or the check's FP64 refresh of it (the checks of
           // Section 2.2 recompute the products; the next attempt starts from them)
           const T a = (fl[v] & kSlotCached) ? at[v] : s[v];
-          const int gi = int((lob >> v) & 1ULL) - int((upb >> v) & 1ULL);
-          const T cs = fan_cost<T>(F, j, gi);
+          const T cs = cc.at(int((lob >> v) & 1ULL) - int((upb >> v) & 1ULL));
           xn[v] = clampv<T>(x[v] + tau[v] * (a - cs), lj, uj);
           const A dx = A(xn[v]) - A(x[v]);
           acc[0][sw * VEC + v] += dx * dx;
@@ -611,7 +624,9 @@ __global__ void __launch_bounds__(kFThreads) k_fstep_control(DevFan<T> F) {
 
 // FP64 column half of a check for every objective: A^T y of the current and the
 // averaged dual, reduced costs against c_hat_k, residuals, objectives, hash.  Lane
-// q of a warp works on objectives q and q + 32 of one column.
+// q of a warp works on objectives q and q + 32 of one column.  FP32 entries widen
+// to FP64 by the exact bit-level conversion on the integer pipe (an FP32-to-FP64
+// conversion instruction would take the FP64 pipe these kernels are bound by).
 template <typename T>
 __global__ void __launch_bounds__(kFThreads) k_fcheck_cols(DevFan<T> F) {
   __shared__ double sh[kFWarps * kNC1 * kFK];
@@ -642,7 +657,7 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_cols(DevFan<T> F) {
     double sc[2], sa[2];
     auto srcc = [&](int i, double(&g)[2]) {
 #pragma unroll
-      for (int q = 0; q < 2; ++q) g[q] = on[q] ? double(yc[size_t(i) * kFK + lane + 32 * q]) : 0.0;
+      for (int q = 0; q < 2; ++q) g[q] = on[q] ? to_f64(yc[size_t(i) * kFK + lane + 32 * q]) : 0.0;
     };
     auto srca = [&](int i, double(&g)[2]) {
 #pragma unroll
@@ -654,13 +669,14 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_cols(DevFan<T> F) {
         const size_t o = size_t(i) * kFK + lane + 32 * q;
         T v = ya[o];
         if (fl[q] & kSlotAvg) v = blend(v, yc[o], w1[q], w[q]);
-        g[q] = double(v);
+        g[q] = to_f64(v);
       }
     };
     row_gather<double, double>(d.t_rowptr[j], d.t_rowptr[j + 1], d.t_cols, d.t_vals64, srcc, sc);
     row_gather<double, double>(d.t_rowptr[j], d.t_rowptr[j + 1], d.t_cols, d.t_vals64, srca, sa);
-    const double Cj = d.C[j], lj = d.l64[j], uj = d.u64[j];
+    const double Cj = d.C[j], iCj = d.invC[j], lj = d.l64[j], uj = d.u64[j];
     const unsigned long long lob = F.lo_bits[j], upb = F.up_bits[j];
+    const FanCostCol<double> cc = fan_cost_col64(F.t, F.om, F.c_orig[j], Cj);
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       if (!on[q]) continue;
@@ -674,10 +690,9 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_cols(DevFan<T> F) {
       }
       F.ATY[0][o] = T(sc[q]);
       F.ATY[1][o] = T(sa[q]);
-      const int gi = int((lob >> k) & 1ULL) - int((upb >> k) & 1ULL);
-      const double cs = (F.t * F.c_orig[j] + F.om * double(gi)) * Cj;
-      const double xl = double(F.XLR[o]);
-      const double xs[2] = {double(x), double(xav)};
+      const double cs = cc.at(int((lob >> k) & 1ULL) - int((upb >> k) & 1ULL));
+      const double xl = to_f64(F.XLR[o]);
+      const double xs[2] = {to_f64(x), to_f64(xav)};
       const double ss[2] = {sc[q], sa[q]};
       const bool boxed = above_neg_inf(lj) && below_pos_inf(uj);  // then r - lambda = 0 exactly
 #pragma unroll
@@ -688,7 +703,7 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_cols(DevFan<T> F) {
         if (!boxed) {
           const double rd = r - lam;
           a[0] += rd * rd;
-          const double rdu = rd / Cj;
+          const double rdu = rd * iCj;
           a[1] += rdu * rdu;
         }
         a[2] += cs * xs[c];
@@ -696,7 +711,7 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_cols(DevFan<T> F) {
         const double dd = xs[c] - xl;
         a[4] += dd * dd;
       }
-      if (d.int_mask[j]) h[q] += round_hash(j, double(x) * Cj);
+      if (d.int_mask[j]) h[q] += round_hash(j, xs[0] * Cj);
     }
   }
   store_block_sums<double>(acc, kNC1, F.part_c1, sh);
@@ -734,15 +749,15 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_rows(DevFan<T> F) {
     double sc[2], sa[2];
     auto srcc = [&](int j, double(&g)[2]) {
 #pragma unroll
-      for (int q = 0; q < 2; ++q) g[q] = on[q] ? double(xc[size_t(j) * kFK + lane + 32 * q]) : 0.0;
+      for (int q = 0; q < 2; ++q) g[q] = on[q] ? to_f64(xc[size_t(j) * kFK + lane + 32 * q]) : 0.0;
     };
     auto srca = [&](int j, double(&g)[2]) {
 #pragma unroll
-      for (int q = 0; q < 2; ++q) g[q] = on[q] ? double(xa[size_t(j) * kFK + lane + 32 * q]) : 0.0;
+      for (int q = 0; q < 2; ++q) g[q] = on[q] ? to_f64(xa[size_t(j) * kFK + lane + 32 * q]) : 0.0;
     };
     row_gather<double, double>(d.a_rowptr[i], d.a_rowptr[i + 1], d.a_cols, d.a_vals64, srcc, sc);
     row_gather<double, double>(d.a_rowptr[i], d.a_rowptr[i + 1], d.a_cols, d.a_vals64, srca, sa);
-    const double Ri = d.R[i], lo = d.lo64[i], hi = d.hi64[i];
+    const double iRi = d.invR[i], lo = d.lo64[i], hi = d.hi64[i];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       if (!on[q]) continue;
@@ -756,15 +771,15 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_rows(DevFan<T> F) {
       }
       F.AX[cur][o] = T(sc[q]);
       F.AX[2][o] = T(sa[q]);
-      const double yl = double(F.YLR[o]);
-      const double ys[2] = {double(y), double(yav)};
+      const double yl = to_f64(F.YLR[o]);
+      const double ys[2] = {to_f64(y), to_f64(yav)};
       const double ss[2] = {sc[q], sa[q]};
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const double rps = ss[c] - clampv<double>(ss[c], lo, hi);
         double* a = acc + q * kNC2 + 4 * c;
         a[0] += rps * rps;
-        const double rp = rps / Ri;
+        const double rp = rps * iRi;
         a[1] += rp * rp;
         a[2] += bound_term(ys[c], lo, hi);
         const double dd = ys[c] - yl;

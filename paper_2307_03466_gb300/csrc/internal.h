@@ -148,6 +148,16 @@ struct DevBatch {
   long long* kglob;           // attempts made by the LPs still running
   double exp_red, exp_grow;
   int grid_p, grid_d, grid_c1, grid_c2, grid_ctl;
+  // persistent solve over a shared work queue: the LPs still running (rebuilt at
+  // every check) and their tiles, as lists of indices, and the chunk counters that
+  // warps take tiles from
+  int* q_lps;                 // nlp slots; q_cnt[0] in use
+  int* q_a;                   // tiles of A of those LPs; q_cnt[1] in use
+  int* q_t;                   // tiles of A^T; q_cnt[2] in use
+  int* q_pre;                 // 2 (nlp + 1): prefix sums of their A and A^T tile counts
+  int* q_cnt;                 // [0] LPs, [1] A tiles, [2] A^T tiles
+  unsigned int* q_ctr;        // [4] chunk counters: primal, dual, column check, row check
+  int grid_q;                 // co-resident blocks of the persistent kernel (0: it cannot run)
 };
 
 // Per-objective values of one attempt of a fan-out, written by its control kernels.
@@ -371,6 +381,17 @@ template <typename T>
 cudaError_t launch_batch_init_point(const DevBatch<T>& B, cudaStream_t st);
 template <typename T>
 void batch_grids(DevBatch<T>& B);
+// the persistent batched solve (all attempts and checks in one cooperative launch
+// over the shared work queue); grid_bar: a zeroed barrier, wait_limit_s bounds
+// every barrier wait, iter_limit the attempts of the solve
+template <typename T>
+cudaError_t launch_batch_persistent(const DevBatch<T>& B, void* grid_bar, long long iter_limit, double wait_limit_s,
+                                    cudaStream_t st);
+// every LP and every tile in the work lists, counters zeroed (start of a solve)
+template <typename T>
+cudaError_t launch_batch_queue_reset(const DevBatch<T>& B, cudaStream_t st);
+template <typename T>
+int batch_persistent_blocks_per_sm();
 
 // bump allocator over one cudaMalloc: pass 1 with base == nullptr sizes, pass 2 carves
 struct Arena {

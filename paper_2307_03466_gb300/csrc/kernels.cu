@@ -353,6 +353,14 @@ __device__ __forceinline__ T gload(const T* p) {
   if (Coh) return __ldcg(p);
   return __ldg(p);
 }
+// load of a vector the same kernel writes elsewhere: L2 only when blocks of one
+// launch hand the data to one another (a persistent kernel whose work moves between
+// blocks), a plain load otherwise
+template <bool Coh, typename T>
+__device__ __forceinline__ T eload(const T* p) {
+  if (Coh) return __ldcg(p);
+  return *p;
+}
 
 // the control values one attempt or check needs, read once per phase; the step
 // sizes and averaging weights come already derived and converted to T
@@ -417,7 +425,7 @@ __device__ __forceinline__ void tiles_rows(const int2* __restrict__ tiles, int n
 }
 
 // ---------------------------------------------------------------- PDHG slot ---
-template <typename T>
+template <typename T, bool Coh = false>
 struct PrimalEpi {
   typedef typename AccOf<T>::type A;
   struct Pre {
@@ -436,7 +444,7 @@ struct PrimalEpi {
   bool do_avg, copy_lr, store_aty, use_cached;
   A acc;
   __device__ __forceinline__ Pre load(int j) const {
-    return Pre{xc[j], cc[j], ll[j], uu[j], do_avg ? xa[j] : T(0)};
+    return Pre{eload<Coh>(xc + j), cc[j], ll[j], uu[j], do_avg ? eload<Coh>(xa + j) : T(0)};
   }
   // staged form: the five vectors of load(), in its order, staged in shared memory
   __device__ __forceinline__ const T* stage_vec(int k) const {
@@ -446,7 +454,7 @@ struct PrimalEpi {
     return Pre{sv[o], sv[stride + o], sv[2 * stride + o], sv[3 * stride + o], do_avg ? sv[4 * stride + o] : T(0)};
   }
   __device__ __forceinline__ void finish(int j, const T (&s)[1], const Pre& p) {
-    const T aty_j = use_cached ? aty[j] : s[0];
+    const T aty_j = use_cached ? eload<Coh>(aty + j) : s[0];
     if (store_aty) aty[j] = aty_j;
     if (do_avg) xa[j] = blend(p.xa, p.x, w1, w);
     if (copy_lr) xlr[j] = p.x;
@@ -502,7 +510,7 @@ __device__ __forceinline__ void primal_phase(const DevLP<T>& d, const SlotView<T
   block_store_partials<kNP>(acc, part);
 }
 
-template <typename T>
+template <typename T, bool Coh = false>
 struct DualEpi {
   typedef typename AccOf<T>::type A;
   struct Pre {
@@ -520,7 +528,7 @@ struct DualEpi {
   bool do_avg, copy_lr;
   A acc0, acc1;
   __device__ __forceinline__ Pre load(int i) const {
-    return Pre{axc[i], yc[i], lo[i], hi[i], do_avg ? ya[i] : T(0)};
+    return Pre{eload<Coh>(axc + i), eload<Coh>(yc + i), lo[i], hi[i], do_avg ? eload<Coh>(ya + i) : T(0)};
   }
   __device__ __forceinline__ const T* stage_vec(int k) const {
     return k == 0 ? axc : k == 1 ? yc : k == 2 ? lo : k == 3 ? hi : ya;
@@ -979,7 +987,7 @@ __device__ __forceinline__ void check_gather(const int2* tiles, int ntiles, cons
 
 // QP: 0 an LP (no Hessian terms compiled in), 1 a quadratic objective (qq set), 2
 // either, decided per column from qq (the persistent kernel, to keep one body)
-template <typename T, int QP = 0>
+template <typename T, int QP = 0, bool Coh = false>
 struct CheckColsEpi {
   struct Pre {};
   const T* __restrict__ xc;
@@ -996,15 +1004,15 @@ struct CheckColsEpi {
   unsigned long long h;
   __device__ __forceinline__ Pre load(int) const { return Pre{}; }
   __device__ __forceinline__ void finish(int j, const double (&s)[2], const Pre&) {
-    const T x = xc[j];
-    T xav = xa[j];
+    const T x = eload<Coh>(xc + j);
+    T xav = eload<Coh>(xa + j);
     if (do_avg) {
       xav = blend(xav, x, w1, w);
       xa[j] = xav;
     }
     aty_c[j] = T(s[0]);
     aty_a[j] = T(s[1]);
-    const double Cj = C[j], iCj = invC[j], cj = c64[j], lj = l64[j], uj = u64[j], xl = to_f64(xlr[j]);
+    const double Cj = C[j], iCj = invC[j], cj = c64[j], lj = l64[j], uj = u64[j], xl = to_f64(eload<Coh>(xlr + j));
     const double xs[2] = {to_f64(x), to_f64(xav)};
     const bool has_q = QP == 1 || (QP == 2 && qq != nullptr);
     const double qj = has_q ? qq[j] : 0.0;
@@ -1080,7 +1088,7 @@ __device__ __forceinline__ void check_cols_phase(const DevLP<T>& d, const SlotVi
   if ((threadIdx.x & 31) == 0 && h != 0ULL) atomicAdd(hash, h);
 }
 
-template <typename T>
+template <typename T, bool Coh = false>
 struct CheckRowsEpi {
   struct Pre {};
   const T* __restrict__ yc;
@@ -1094,15 +1102,15 @@ struct CheckRowsEpi {
   double acc[kNC2];
   __device__ __forceinline__ Pre load(int) const { return Pre{}; }
   __device__ __forceinline__ void finish(int i, const double (&s)[2], const Pre&) {
-    const T y = yc[i];
-    T yav = ya[i];
+    const T y = eload<Coh>(yc + i);
+    T yav = eload<Coh>(ya + i);
     if (do_avg) {
       yav = blend(yav, y, w1, w);
       ya[i] = yav;
     }
     ax_c[i] = T(s[0]);
     ax_a[i] = T(s[1]);
-    const double iRi = invR[i], lo = lo64[i], hi = hi64[i], yl = to_f64(ylr[i]);
+    const double iRi = invR[i], lo = lo64[i], hi = hi64[i], yl = to_f64(eload<Coh>(ylr + i));
     const double ys[2] = {to_f64(y), to_f64(yav)};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -1547,85 +1555,115 @@ __global__ void k_cnorm_cols(DevObjective o, double offset_base) {
 // tile and reduced per LP, in a fixed order, by one warp per LP in the control
 // kernels, which then run the same step and check logic as the single-LP path.
 
-// warp-tile loop of the batched kernels: begin(lp, t) decides per tile (uniformly
-// over the warp) whether the tile's LP takes part, end(t) flushes the tile's sums
+// One warp tile of the batched kernels (a multi-row tile or one long row): the
+// products into the warp's skewed shared buffer, then each lane sums its row in CSR
+// order and hands it to the epilogue.
+template <int NV, typename Acc, typename V, typename Gather, typename Epi>
+__device__ __forceinline__ void batch_tile(int t, const int2* __restrict__ tiles, const int* __restrict__ rowptr,
+                                           const int* __restrict__ cols, const V* __restrict__ vals, Gather& gat,
+                                           Epi& epi, Acc* __restrict__ sm) {
+  const int lane = threadIdx.x & 31;
+  const int2 ta = __ldg(tiles + t), tb = __ldg(tiles + t + 1);
+  const int r0 = ta.x, r1 = tb.x, p0 = ta.y, p1 = tb.y;
+  const int base = p0 & ~(kVec - 1);
+  if (r1 - r0 == 1 && p1 - p0 > kTileNnz) {
+    const typename Epi::Pre pre = epi.load(r0);
+    Acc s[NV];
+    long_row_sum<NV, false>(p0, p1, cols, vals, gat, s);
+    if (lane == 0) epi.finish(r0, s, pre);
+  } else {
+    const bool mine = lane < r1 - r0;
+    const int row = r0 + lane;
+    int q0 = 0, q1 = 0;
+    typename Epi::Pre pre{};
+    if (mine) {
+      q0 = __ldg(rowptr + row) - p0;
+      q1 = __ldg(rowptr + row + 1) - p0;
+      pre = epi.load(row);
+    }
+    int c[3][4];
+    V v[3][4];
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+      const int p = base + (it * 32 + lane) * kVec;
+      if (p < p1) {
+        ld4(cols + p, c[it]);
+        ld4(vals + p, v[it]);
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+      const int p = base + (it * 32 + lane) * kVec;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int q = p + e;
+        if (q >= p0 && q < p1) {
+          Acc g[NV];
+          gat(c[it][e], g);
+          const int o = skew(q - p0);
+#pragma unroll
+          for (int k = 0; k < NV; ++k) sm[k * kSmemPerWarp + o] = Acc(v[it][e]) * g[k];
+        }
+      }
+    }
+    __syncwarp();
+    if (mine) {
+      Acc s[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) s[k] = Acc(0);
+      for (int q = q0; q < q1; ++q) {
+        const int o = skew(q);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[k] += sm[k * kSmemPerWarp + o];
+      }
+      epi.finish(row, s, pre);
+    }
+    __syncwarp();
+  }
+}
+
+// warp-tile loop of the batched kernels over a static deal of the tiles:
+// begin(lp, t) decides per tile (uniformly over the warp) whether the tile's LP
+// takes part, end(t) flushes the tile's sums
 template <int NV, typename Acc, typename V, typename Gather, typename Epi>
 __device__ __forceinline__ void spmv_tiles_batch(const int2* __restrict__ tiles, const int* __restrict__ tile_lp,
                                                  int ntiles, const int* __restrict__ rowptr,
                                                  const int* __restrict__ cols, const V* __restrict__ vals,
                                                  Gather& gat, Epi& epi, Acc* __restrict__ sm) {
-  const int lane = threadIdx.x & 31;
   const WarpTiles wt = warp_tiles(ntiles);
   for (int t = wt.first; t < wt.end; t += wt.step) {
     if (!epi.begin(__ldg(tile_lp + t), t)) continue;
-    const int2 ta = __ldg(tiles + t), tb = __ldg(tiles + t + 1);
-    const int r0 = ta.x, r1 = tb.x, p0 = ta.y, p1 = tb.y;
-    const int base = p0 & ~(kVec - 1);
-    if (r1 - r0 == 1 && p1 - p0 > kTileNnz) {
-      const typename Epi::Pre pre = epi.load(r0);
-      Acc s[NV];
-      long_row_sum<NV, false>(p0, p1, cols, vals, gat, s);
-      if (lane == 0) epi.finish(r0, s, pre);
-    } else {
-      const bool mine = lane < r1 - r0;
-      const int row = r0 + lane;
-      int q0 = 0, q1 = 0;
-      typename Epi::Pre pre{};
-      if (mine) {
-        q0 = __ldg(rowptr + row) - p0;
-        q1 = __ldg(rowptr + row + 1) - p0;
-        pre = epi.load(row);
-      }
-      int c[3][4];
-      V v[3][4];
-#pragma unroll
-      for (int it = 0; it < 3; ++it) {
-        const int p = base + (it * 32 + lane) * kVec;
-        if (p < p1) {
-          ld4(cols + p, c[it]);
-          ld4(vals + p, v[it]);
-        }
-      }
-#pragma unroll
-      for (int it = 0; it < 3; ++it) {
-        const int p = base + (it * 32 + lane) * kVec;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int q = p + e;
-          if (q >= p0 && q < p1) {
-            Acc g[NV];
-            gat(c[it][e], g);
-            const int o = skew(q - p0);
-#pragma unroll
-            for (int k = 0; k < NV; ++k) sm[k * kSmemPerWarp + o] = Acc(v[it][e]) * g[k];
-          }
-        }
-      }
-      __syncwarp();
-      if (mine) {
-        Acc s[NV];
-#pragma unroll
-        for (int k = 0; k < NV; ++k) s[k] = Acc(0);
-        for (int q = q0; q < q1; ++q) {
-          const int o = skew(q);
-#pragma unroll
-          for (int k = 0; k < NV; ++k) s[k] += sm[k * kSmemPerWarp + o];
-        }
-        epi.finish(row, s, pre);
-      }
-      __syncwarp();
-    }
+    batch_tile<NV, Acc, V>(t, tiles, rowptr, cols, vals, gat, epi, sm);
     epi.end(t);
   }
 }
 
-template <typename T>
-struct BPrimalEpi : PrimalEpi<T> {
+// per-LP values of one attempt: L2 loads when the writer may be another block of
+// the same launch (the persistent solve)
+template <bool Coh, typename T>
+__device__ __forceinline__ BatchSlot<T> read_slot(const BatchSlot<T>* p) {
+  if (!Coh) return *p;
+  BatchSlot<T> s;
+  s.tau = __ldcg(&p->tau);
+  s.sigma = __ldcg(&p->sigma);
+  s.w = __ldcg(&p->w);
+  s.w1 = __ldcg(&p->w1);
+  s.cur = __ldcg(&p->cur);
+  s.nxt = __ldcg(&p->nxt);
+  s.avg = __ldcg(&p->avg);
+  s.ia_cur = __ldcg(&p->ia_cur);
+  s.ia_avg = __ldcg(&p->ia_avg);
+  s.flags = __ldcg(&p->flags);
+  return s;
+}
+
+template <typename T, bool Coh = false>
+struct BPrimalEpi : PrimalEpi<T, Coh> {
   const DevBatch<T>* B;
   const T* ysrc;
   bool cached;
   __device__ __forceinline__ bool begin(int b, int) {
-    const BatchSlot<T> s = B->slot[b];
+    const BatchSlot<T> s = read_slot<Coh>(B->slot + b);
     if (!(s.flags & kSlotActive)) return false;
     const DevLP<T>& d = B->d;
     this->xc = d.X[s.cur];
@@ -1667,12 +1705,12 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_bprimal(DevBa
                             sm + (threadIdx.x >> 5) * kSmemPerWarp);
 }
 
-template <typename T>
-struct BDualEpi : DualEpi<T> {
+template <typename T, bool Coh = false>
+struct BDualEpi : DualEpi<T, Coh> {
   const DevBatch<T>* B;
   const T* xsrc;
   __device__ __forceinline__ bool begin(int b, int) {
-    const BatchSlot<T> s = B->slot[b];
+    const BatchSlot<T> s = read_slot<Coh>(B->slot + b);
     if (!(s.flags & kSlotActive)) return false;
     const DevLP<T>& d = B->d;
     this->axc = d.AX[s.cur];
@@ -1740,8 +1778,8 @@ __global__ void k_bstep_control(DevBatch<T> B) {
   }
 }
 
-template <typename T>
-struct BCheckColsEpi : CheckColsEpi<T> {
+template <typename T, bool Coh = false>
+struct BCheckColsEpi : CheckColsEpi<T, 0, Coh> {
   const DevBatch<T>* B;
   const T* ycur;
   const T* yavg;
@@ -1749,7 +1787,7 @@ struct BCheckColsEpi : CheckColsEpi<T> {
   bool bavg;
   int lp;
   __device__ __forceinline__ bool begin(int b, int) {
-    const BatchSlot<T> s = B->slot[b];
+    const BatchSlot<T> s = read_slot<Coh>(B->slot + b);
     if (!(s.flags & kSlotCheck)) return false;
     const DevLP<T>& d = B->d;
     this->xc = d.X[s.cur];
@@ -1808,13 +1846,13 @@ __global__ void __launch_bounds__(kThreads) k_bcheck_cols(DevBatch<T> B) {
                                       epi, sm + (threadIdx.x >> 5) * 2 * kSmemPerWarp);
 }
 
-template <typename T>
-struct BCheckRowsEpi : CheckRowsEpi<T> {
+template <typename T, bool Coh = false>
+struct BCheckRowsEpi : CheckRowsEpi<T, Coh> {
   const DevBatch<T>* B;
   const T* xcur;
   const T* xavg;
   __device__ __forceinline__ bool begin(int b, int) {
-    const BatchSlot<T> s = B->slot[b];
+    const BatchSlot<T> s = read_slot<Coh>(B->slot + b);
     if (!(s.flags & kSlotCheck)) return false;
     const DevLP<T>& d = B->d;
     this->yc = d.Y[s.cur];
@@ -1943,6 +1981,371 @@ __global__ void k_binit_point(DevBatch<T> B) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) d.Y[0][i] = T(0);
 }
 
+
+// ------------------------------------- persistent batched solve over a work queue ---
+// One cooperative launch runs a whole batched solve.  Every phase (primal, dual,
+// step control; at checks the two check halves, check control and the rebuild of
+// the work lists) is separated from the next by a bounded grid barrier.  In the
+// matrix phases warps take chunks of kQChunk tiles from a shared counter over the
+// list of tiles of the LPs still running, so the work is balanced over the grid
+// whatever the sizes of the LPs; at every check the LPs that finished are dropped
+// from the lists (compaction), so their tiles are not visited again.  The
+// arithmetic per tile and the per-LP reduction of the per-tile sums are those of
+// the launch-per-phase path (same functions, same order), so the two give
+// identical results.  Work moves between blocks from one phase to the next, so
+// every load of data written during the launch goes to L2 (ld.global.cg): the
+// vectors, slots, control blocks, per-tile sums, lists and the step-factor table.
+constexpr int kQChunk = 4;          // tiles a warp takes from a queue at once
+constexpr int kQMaxNcheck = 256;    // the step-factor table is held in shared memory
+
+template <int NV, typename Acc, typename V, typename Gather, typename Epi>
+__device__ __forceinline__ void queue_tiles(const int* list, int count, unsigned int* ctr, const int2* tiles,
+                                            const int* tile_lp, const int* rowptr, const int* cols, const V* vals,
+                                            Gather& gat, Epi& epi, Acc* sm) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int v0 = 0;
+    if (lane == 0) v0 = int(atomicAdd(ctr, unsigned(kQChunk)));
+    v0 = __shfl_sync(0xffffffffu, v0, 0);
+    if (v0 >= count) break;
+    const int v1 = min(count, v0 + kQChunk);
+    for (int v = v0; v < v1; ++v) {
+      const int t = __ldcg(list + v);
+      if (!epi.begin(__ldg(tile_lp + t), t)) continue;
+      batch_tile<NV, Acc, V>(t, tiles, rowptr, cols, vals, gat, epi, sm);
+      epi.end(t);
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void bq_primal(const DevBatch<T>& B, int count, T* sm) {
+  const DevLP<T>& d = B.d;
+  BPrimalEpi<T, true> epi;
+  epi.B = &B;
+  epi.xlr = d.XLR;
+  epi.cc = d.c;
+  epi.ll = d.l;
+  epi.uu = d.u;
+  epi.qq = nullptr;
+  epi.acc = 0;
+  auto gat = [&](int i, T(&g)[1]) { g[0] = epi.cached ? T(0) : __ldcg(epi.ysrc + i); };
+  queue_tiles<1, T, T>(B.q_t, count, B.q_ctr + 0, d.t_tiles, B.t_tile_lp, d.t_rowptr, d.t_cols, d.t_vals, gat, epi,
+                       sm);
+}
+
+template <typename T>
+__device__ __forceinline__ void bq_dual(const DevBatch<T>& B, int count, T* sm) {
+  const DevLP<T>& d = B.d;
+  BDualEpi<T, true> epi;
+  epi.B = &B;
+  epi.ylr = d.YLR;
+  epi.lo = d.lo;
+  epi.hi = d.hi;
+  epi.acc0 = 0;
+  epi.acc1 = 0;
+  auto gat = [&](int j, T(&g)[1]) { g[0] = __ldcg(epi.xsrc + j); };
+  queue_tiles<1, T, T>(B.q_a, count, B.q_ctr + 1, d.a_tiles, B.a_tile_lp, d.a_rowptr, d.a_cols, d.a_vals, gat, epi,
+                       sm);
+}
+
+template <typename T>
+__device__ __forceinline__ void bq_check_cols(const DevBatch<T>& B, int count, double* sm) {
+  const DevLP<T>& d = B.d;
+  BCheckColsEpi<T, true> epi;
+  epi.B = &B;
+  epi.xlr = d.XLR;
+  epi.C = d.C;
+  epi.invC = d.invC;
+  epi.c64 = d.c64;
+  epi.l64 = d.l64;
+  epi.u64 = d.u64;
+  epi.qq = nullptr;
+  epi.int_mask = d.int_mask;
+#pragma unroll
+  for (int k = 0; k < kNC1; ++k) epi.acc[k] = 0.0;
+  epi.h = 0ULL;
+  auto gat = [&](int i, double(&g)[2]) {
+    const T y = __ldcg(epi.ycur + i);
+    T av = __ldcg(epi.yavg + i);
+    if (epi.bavg) av = blend(av, y, epi.bw1, epi.bw);
+    g[0] = double(y);
+    g[1] = double(av);
+  };
+  queue_tiles<2, double, double>(B.q_t, count, B.q_ctr + 2, d.t_tiles, B.t_tile_lp, d.t_rowptr, d.t_cols, d.t_vals64,
+                                 gat, epi, sm);
+}
+
+template <typename T>
+__device__ __forceinline__ void bq_check_rows(const DevBatch<T>& B, int count, double* sm) {
+  const DevLP<T>& d = B.d;
+  BCheckRowsEpi<T, true> epi;
+  epi.B = &B;
+  epi.ylr = d.YLR;
+  epi.invR = d.invR;
+  epi.lo64 = d.lo64;
+  epi.hi64 = d.hi64;
+#pragma unroll
+  for (int k = 0; k < kNC2; ++k) epi.acc[k] = 0.0;
+  auto gat = [&](int j, double(&g)[2]) {
+    g[0] = double(__ldcg(epi.xcur + j));
+    g[1] = double(__ldcg(epi.xavg + j));
+  };
+  queue_tiles<2, double, double>(B.q_a, count, B.q_ctr + 3, d.a_tiles, B.a_tile_lp, d.a_rowptr, d.a_cols, d.a_vals64,
+                                 gat, epi, sm);
+}
+
+// a control block into a warp's shared copy (L2 loads) and back, word by word
+__device__ __forceinline__ void ctl_in(Control* dst, const Control* src) {
+  static_assert(sizeof(Control) % 4 == 0, "word copy");
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < int(sizeof(Control) / 4); i += 32)
+    reinterpret_cast<int*>(dst)[i] = __ldcg(reinterpret_cast<const int*>(src) + i);
+  __syncwarp();
+}
+__device__ __forceinline__ void ctl_out(Control* dst, const Control* src) {
+  __syncwarp();
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < int(sizeof(Control) / 4); i += 32)
+    reinterpret_cast<int*>(dst)[i] = reinterpret_cast<const int*>(src)[i];
+  __syncwarp();
+}
+
+// step decision of every running LP, one warp per LP over the LP list; block 0
+// counts the attempt and rearms the matrix phases' counters (every warp has
+// finished taking tiles from them)
+template <typename T>
+__device__ __forceinline__ void bq_step(const DevBatch<T>& B, int nl, Control* sc, const double* fac) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ++*B.kglob;
+    B.q_ctr[0] = 0u;
+    B.q_ctr[1] = 0u;
+  }
+  for (int q = gw; q < nl; q += nw) {
+    const int b = __ldcg(B.q_lps + q);
+    if (!(__ldcg(&B.slot[b].flags) & kSlotActive)) continue;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int t = __ldg(B.t_tile_beg + b) + lane; t < __ldg(B.t_tile_beg + b + 1); t += 32) s0 += __ldcg(B.tp_p + t);
+    for (int t = __ldg(B.a_tile_beg + b) + lane; t < __ldg(B.a_tile_beg + b + 1); t += 32) {
+      s1 += __ldcg(B.tp_d + 2 * t);
+      s2 += __ldcg(B.tp_d + 2 * t + 1);
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    ctl_in(sc, B.ctl + b);
+    if (lane == 0) {
+      step_control(sc, s0, s1, s2, fac, B.d.n_check, nullptr, 0);
+      if (sc->done) atomicAdd(B.n_done, 1);
+      write_slot(&B.slot[b], sc);
+    }
+    ctl_out(B.ctl + b, sc);
+  }
+}
+
+// termination, stalling and restarts of every LP in the list; block 0 refills the
+// shared step-size factor table for the next n_check attempts
+template <typename T>
+__device__ __forceinline__ void bq_check_control(const DevBatch<T>& B, int nl, Control* sc) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const long long k = __ldcg(B.kglob);
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < B.d.n_check; i += blockDim.x) {
+      const double kk = double(k + 1 + i + 1);
+      B.d.step_fac[2 * i] = 1.0 - pow(kk, -B.exp_red);
+      B.d.step_fac[2 * i + 1] = 1.0 + pow(kk, -B.exp_grow);
+    }
+  for (int q = gw; q < nl; q += nw) {
+    const int b = __ldcg(B.q_lps + q);
+    if (!(__ldcg(&B.slot[b].flags) & kSlotCheck)) continue;
+    double r[kNC1 + kNC2];
+#pragma unroll
+    for (int s = 0; s < kNC1 + kNC2; ++s) r[s] = 0.0;
+    for (int t = __ldg(B.t_tile_beg + b) + lane; t < __ldg(B.t_tile_beg + b + 1); t += 32)
+#pragma unroll
+      for (int s = 0; s < kNC1; ++s) r[s] += __ldcg(B.tp_c1 + kNC1 * t + s);
+    for (int t = __ldg(B.a_tile_beg + b) + lane; t < __ldg(B.a_tile_beg + b + 1); t += 32)
+#pragma unroll
+      for (int s = 0; s < kNC2; ++s) r[kNC1 + s] += __ldcg(B.tp_c2 + kNC2 * t + s);
+#pragma unroll
+    for (int s = 0; s < kNC1 + kNC2; ++s) r[s] = warp_sum(r[s]);
+    ctl_in(sc, B.ctl + b);
+    if (lane == 0) {
+      sc->k_fac = k;
+      check_control(sc, r, nullptr, 0);
+      if (sc->done) atomicAdd(B.n_done, 1);
+      write_slot(&B.slot[b], sc);
+    }
+    ctl_out(B.ctl + b, sc);
+  }
+}
+
+// block-wide exclusive prefix sums of three counts (blockDim.x threads); returns
+// the block totals
+__device__ __forceinline__ int3 block_scan3(int3 v, int3& excl) {
+  __shared__ int3 wsum[kWarpsPerBlock];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int3 inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int a = __shfl_up_sync(0xffffffffu, inc.x, o), b = __shfl_up_sync(0xffffffffu, inc.y, o),
+              c = __shfl_up_sync(0xffffffffu, inc.z, o);
+    if (lane >= o) {
+      inc.x += a;
+      inc.y += b;
+      inc.z += c;
+    }
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  int3 off = make_int3(0, 0, 0), tot = make_int3(0, 0, 0);
+  for (int q = 0; q < int(blockDim.x >> 5); ++q) {
+    if (q < w) {
+      off.x += wsum[q].x;
+      off.y += wsum[q].y;
+      off.z += wsum[q].z;
+    }
+    tot.x += wsum[q].x;
+    tot.y += wsum[q].y;
+    tot.z += wsum[q].z;
+  }
+  excl = make_int3(off.x + inc.x - v.x, off.y + inc.y - v.y, off.z + inc.z - v.z);
+  __syncthreads();
+  return tot;
+}
+
+// compaction (block 0): the LPs of the list that are not finished, in list order,
+// with prefix sums of their tile counts; the chunk counters rearmed
+template <typename T>
+__device__ __forceinline__ void bq_compact_lps(const DevBatch<T>& B, int nl) {
+  int kept = 0, na = 0, nt = 0;
+  int* pre_a = B.q_pre;
+  int* pre_t = B.q_pre + (B.nlp + 1);
+  for (int base = 0; base < nl; base += blockDim.x) {
+    const int q = base + threadIdx.x;
+    int b = -1;
+    int3 v = make_int3(0, 0, 0);
+    if (q < nl) {
+      b = __ldcg(B.q_lps + q);
+      if (__ldcg(&B.slot[b].flags) & kSlotCheck) {
+        v.x = 1;
+        v.y = __ldg(B.a_tile_beg + b + 1) - __ldg(B.a_tile_beg + b);
+        v.z = __ldg(B.t_tile_beg + b + 1) - __ldg(B.t_tile_beg + b);
+      }
+    }
+    int3 ex;
+    const int3 tot = block_scan3(v, ex);  // its barriers also order the reads above before the writes below
+    if (v.x) {
+      B.q_lps[kept + ex.x] = b;
+      pre_a[kept + ex.x] = na + ex.y;
+      pre_t[kept + ex.x] = nt + ex.z;
+    }
+    kept += tot.x;
+    na += tot.y;
+    nt += tot.z;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    pre_a[kept] = na;
+    pre_t[kept] = nt;
+    B.q_cnt[0] = kept;
+    B.q_cnt[1] = na;
+    B.q_cnt[2] = nt;
+    for (int c = 0; c < 4; ++c) B.q_ctr[c] = 0u;
+  }
+}
+
+// the tile lists of the compacted LP list: a warp per LP copies its tile ranges
+template <typename T>
+__device__ __forceinline__ void bq_fill_tiles(const DevBatch<T>& B, int nl) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int* pre_a = B.q_pre;
+  const int* pre_t = B.q_pre + (B.nlp + 1);
+  for (int q = gw; q < nl; q += nw) {
+    const int b = __ldcg(B.q_lps + q);
+    const int a0 = __ldg(B.a_tile_beg + b), a1 = __ldg(B.a_tile_beg + b + 1);
+    const int t0 = __ldg(B.t_tile_beg + b), t1 = __ldg(B.t_tile_beg + b + 1);
+    const int da = __ldcg(pre_a + q), dt = __ldcg(pre_t + q);
+    for (int i = lane; i < a1 - a0; i += 32) B.q_a[da + i] = a0 + i;
+    for (int i = lane; i < t1 - t0; i += 32) B.q_t[dt + i] = t0 + i;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 3) k_bsolve_persistent(DevBatch<T> B, GridBar* bar, long long iter_limit,
+                                                               unsigned long long limit_ns) {
+  __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];  // tile products, 2 vectors of FP64 at a check
+  __shared__ Control sctl[kWarpsPerBlock];
+  __shared__ double fac[2 * kQMaxNcheck];
+  const int w = threadIdx.x >> 5;
+  double* smw2 = sm + w * 2 * kSmemPerWarp;
+  T* smw1 = reinterpret_cast<T*>(sm) + w * kSmemPerWarp;
+  bool ok = true, do_check = true;
+  long long since = 0;
+  int nl = 0, na = 0, nt = 0;
+  while (ok) {
+    if (do_check) {
+      nl = __ldcg(B.q_cnt + 0);
+      na = __ldcg(B.q_cnt + 1);
+      nt = __ldcg(B.q_cnt + 2);
+      bq_check_cols<T>(B, nt, smw2);
+      if (!(ok = grid_sync(bar, limit_ns))) break;
+      bq_check_rows<T>(B, na, smw2);
+      if (!(ok = grid_sync(bar, limit_ns))) break;
+      bq_check_control<T>(B, nl, &sctl[w]);
+      if (!(ok = grid_sync(bar, limit_ns))) break;
+      if (blockIdx.x == 0) bq_compact_lps<T>(B, nl);
+      if (!(ok = grid_sync(bar, limit_ns))) break;
+      nl = __ldcg(B.q_cnt + 0);
+      na = __ldcg(B.q_cnt + 1);
+      nt = __ldcg(B.q_cnt + 2);
+      bq_fill_tiles<T>(B, nl);
+      if (!(ok = grid_sync(bar, limit_ns))) break;
+      for (int i = threadIdx.x; i < 2 * B.d.n_check; i += blockDim.x) fac[i] = __ldcg(B.d.step_fac + i);
+      __syncthreads();
+      since = 0;
+      do_check = false;
+      if (nl == 0) break;  // every LP has finished
+    }
+    if (since == B.d.n_check || __ldcg(B.kglob) >= iter_limit) {
+      do_check = true;
+      continue;
+    }
+    bq_primal<T>(B, nt, smw1);
+    if (!(ok = grid_sync(bar, limit_ns))) break;
+    bq_dual<T>(B, na, smw1);
+    if (!(ok = grid_sync(bar, limit_ns))) break;
+    bq_step<T>(B, nl, &sctl[w], fac);
+    if (!(ok = grid_sync(bar, limit_ns))) break;
+    ++since;
+  }
+}
+
+// every LP and every tile in the work lists (in order), counters zeroed
+template <typename T>
+__global__ void k_bqueue_reset(DevBatch<T> B) {
+  const int stride = gridDim.x * blockDim.x, t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int na = B.d.a_ntiles, nt = B.d.t_ntiles;
+  for (int i = t0; i < B.nlp; i += stride) {
+    B.q_lps[i] = i;
+    B.q_pre[i] = B.a_tile_beg[i];
+    B.q_pre[B.nlp + 1 + i] = B.t_tile_beg[i];
+  }
+  for (int i = t0; i < na; i += stride) B.q_a[i] = i;
+  for (int i = t0; i < nt; i += stride) B.q_t[i] = i;
+  if (t0 == 0) {
+    B.q_pre[B.nlp] = na;
+    B.q_pre[2 * B.nlp + 1] = nt;
+    B.q_cnt[0] = B.nlp;
+    B.q_cnt[1] = na;
+    B.q_cnt[2] = nt;
+    for (int c = 0; c < 4; ++c) B.q_ctr[c] = 0u;
+  }
+}
 
 // ----------------------------------------------------------------- launchers ---
 static int g_sms = 0;
@@ -2182,6 +2585,35 @@ cudaError_t launch_batch_init_point(const DevBatch<T>& B, cudaStream_t st) {
   return cudaGetLastError();
 }
 template <typename T>
+int batch_persistent_blocks_per_sm() {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bsolve_persistent<T>, kThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm;
+}
+
+template <typename T>
+cudaError_t launch_batch_queue_reset(const DevBatch<T>& B, cudaStream_t st) {
+  const int items = B.d.a_ntiles > B.d.t_ntiles ? B.d.a_ntiles : B.d.t_ntiles;
+  k_bqueue_reset<T><<<ew_grid(items > B.nlp ? items : B.nlp), kThreads, 0, st>>>(B);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_batch_persistent(const DevBatch<T>& B, void* grid_bar, long long iter_limit, double wait_limit_s,
+                                    cudaStream_t st) {
+  if (B.grid_q < 1 || B.d.n_check > kQMaxNcheck) return cudaErrorInvalidConfiguration;
+  GridBar* bar = static_cast<GridBar*>(grid_bar);
+  unsigned long long limit_ns = (unsigned long long)(wait_limit_s * 1e9);
+  DevBatch<T> bb = B;
+  void* args[] = {&bb, &bar, &iter_limit, &limit_ns};
+  return cudaLaunchCooperativeKernel((const void*)k_bsolve_persistent<T>, dim3(B.grid_q), dim3(kThreads), args, 0,
+                                     st);
+}
+
+template <typename T>
 void batch_grids(DevBatch<T>& B) {
   auto grid = [](const void* k, int tiles, size_t smem) {
     int per_sm = 1;
@@ -2206,7 +2638,10 @@ void batch_grids(DevBatch<T>& B) {
   template cudaError_t launch_batch_check<T>(const DevBatch<T>&, cudaStream_t);                        \
   template cudaError_t launch_batch_get_x<T>(const DevBatch<T>&, int, int, int, double*, cudaStream_t); \
   template cudaError_t launch_batch_init_point<T>(const DevBatch<T>&, cudaStream_t);                   \
-  template void batch_grids<T>(DevBatch<T>&);
+  template void batch_grids<T>(DevBatch<T>&);                                                            \
+  template int batch_persistent_blocks_per_sm<T>();                                                       \
+  template cudaError_t launch_batch_queue_reset<T>(const DevBatch<T>&, cudaStream_t);                     \
+  template cudaError_t launch_batch_persistent<T>(const DevBatch<T>&, void*, long long, double, cudaStream_t);
 
 SCYLLA_INSTANTIATE_BATCH(double)
 SCYLLA_INSTANTIATE_BATCH(float)
