@@ -773,9 +773,32 @@ def batched_section(S, peak, peak_kind):
     B.reset_state()
     res, sec = B.solve(TOL, ITER_CAP)
     conv = sum(1 for r in res if r.status == S.CONVERGED)
+    pers, tune_ms = B.info()
     out["mixed_batched"] = {"seconds": sec, "converged": conv, "max_attempts": max(r.iterations for r in res),
                             "sum_attempts": sum(r.iterations for r in res),
-                            "max_rel_kkt": max(r.rel_kkt for r in res)}
+                            "max_rel_kkt": max(r.rel_kkt for r in res),
+                            "launch_form": "persistent work queue" if pers else "graph per n_check attempts",
+                            "create_time_ms_per_64_attempts": {"graphs": tune_ms[0], "persistent": tune_ms[1]}}
+    # the other form for the record (the same solve; identical results)
+    Bo = S.Batch(insts, S.default_params(precision=S.PREC_MIXED, batch_launch=1 if pers else 2))
+    Bo.solve(TOL, ITER_CAP)
+    Bo.reset_state()
+    _, sec_o = Bo.solve(TOL, ITER_CAP)
+    out["mixed_batched"]["other_form_seconds"] = sec_o
+    Bo.close()
+    # per-kernel device time of the graph form's kernels with every LP taking part
+    # (as at the start of a solve): CUDA events around separate launches
+    B.reset_state()
+    ms = B.time_kernels(64)
+    m_tot, n_tot = tot_m, 2 * tot_m
+    bp, bd = kernel_bytes(m_tot, n_tot, tot_nnz, 4, 4)
+    kname, kb, kms = ("k_bdual<float>", bd, ms[1]) if ms[1] >= ms[0] else ("k_bprimal<float>", bp, ms[0])
+    out["kernel_ms"] = {"primal": ms[0], "dual": ms[1], "step_control": ms[2],
+                        "note": "isolated CUDA-event launches, every LP taking part (the start of a solve)"}
+    out["roofline"] = {"bound": "hbm", "kernel": kname, "achieved": kb / (kms * 1e6), "peak": peak, "unit": "GB/s",
+                       "frac": kb / (kms * 1e6) / peak, "peak_source": peak_kind, "bytes_per_launch": kb,
+                       "frac_other_kernel": (bp / (ms[0] * 1e6) if kname == "k_bdual<float>"
+                                             else bd / (ms[1] * 1e6)) / peak}
     B.close()
     B = S.Batch(insts, S.default_params(precision=S.PREC_FP64))
     B.solve(TOL, ITER_CAP)

@@ -48,6 +48,10 @@ struct scylla_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   float last_ms = 0.f;
+  bool persistent = false;   // attempts in persistent launches over the work queue (batch_launch)
+  double tune_ms[2] = {0.0, 0.0};  // automatic choice: ms of n_check attempts in each form (graphs, persistent)
+  void* grid_bar = nullptr;  // the persistent launches' barrier (device)
+  int* h_err = nullptr;      // pinned copy of its error flag
 
   void release() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -60,6 +64,8 @@ struct scylla_batch {
     h_ctl = nullptr;
     if (h_done) cudaFreeHost(h_done);
     h_done = nullptr;
+    if (h_err) cudaFreeHost(h_err);
+    h_err = nullptr;
     for (cudaEvent_t* e : {&ev_user, &ev0, &ev1, &ev_chunk[0], &ev_chunk[1]}) {
       if (*e) cudaEventDestroy(*e);
       *e = nullptr;
@@ -89,8 +95,61 @@ void fill_batch(DevBatch<T>& B, DevLP<T>& d, scylla_batch* h, char* X[3], char* 
   batch_grids<T>(B);
 }
 
+// The persistent form: the start point's check and the compaction of the work
+// lists, then per chunk one cooperative launch of the attempts up to the next check,
+// the check kernels and the compaction, replayed by a pipelined host loop until
+// every LP is done.  A barrier wait that runs out ends the solve with
+// SCYLLA_ERR_TIMEOUT and the LPs still running marked SCYLLA_DEVICE_TIMEOUT.
+template <typename T>
+int batch_solve_persistent(scylla_batch* h, DevBatch<T>& B, double tol, int64_t iter_limit) {
+  cudaStream_t st = h->st;
+  const long long nchk = h->p.n_check;
+  const long long max_chunks = (iter_limit + nchk - 1) / nchk + 2;
+  CKB(cudaEventRecord(h->ev0, st));
+  CKB(cudaMemsetAsync(h->grid_bar, 0, 16, st));
+  CKB(launch_batch_init<T>(B, tol, (long long)iter_limit, h->p.stall_checks, st));
+  CKB(launch_batch_queue_reset<T>(B, st));
+  CKB(launch_batch_check<T>(B, st));  // every LP's start point
+  CKB(launch_batch_compact<T>(B, st));
+  auto enqueue = [&](long long c) -> cudaError_t {
+    cudaError_t e = launch_batch_persistent<T>(B, h->grid_bar, (long long)iter_limit, h->p.device_wait_limit_s, st);
+    if (e == cudaSuccess) e = launch_batch_check<T>(B, st);
+    if (e == cudaSuccess) e = launch_batch_compact<T>(B, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h->h_done[c & 1], B.n_done, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_chunk[c & 1], st);
+    return e;
+  };
+  CKB(cudaMemcpyAsync(&h->h_done[1], B.n_done, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CKB(cudaStreamSynchronize(st));
+  if (h->h_done[1] < h->nlp) {
+    CKB(enqueue(0));
+    for (long long c = 0; c < max_chunks; ++c) {
+      if (c + 1 < max_chunks) CKB(enqueue(c + 1));
+      CKB(cudaEventSynchronize(h->ev_chunk[c & 1]));
+      if (h->h_done[c & 1] >= h->nlp) break;
+    }
+  }
+  CKB(cudaEventRecord(h->ev1, st));
+  CKB(cudaMemcpyAsync(h->h_ctl, B.ctl, sizeof(Control) * h->nlp, cudaMemcpyDeviceToHost, st));
+  // GridBar: {count, gen, err}
+  CKB(cudaMemcpyAsync(h->h_err, static_cast<char*>(h->grid_bar) + 8, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CKB(cudaStreamSynchronize(st));
+  cudaEventElapsedTime(&h->last_ms, h->ev0, h->ev1);
+  if (*h->h_err) {
+    for (int b = 0; b < h->nlp; ++b)
+      if (!h->h_ctl[b].done) {
+        h->h_ctl[b].done = 1;
+        h->h_ctl[b].status = SCYLLA_DEVICE_TIMEOUT;
+      }
+    set_error("a grid barrier wait of the persistent batched solve ran out (device_wait_limit_s)");
+    return SCYLLA_ERR_TIMEOUT;
+  }
+  return SCYLLA_OK;
+}
+
 template <typename T>
 int batch_solve_impl(scylla_batch* h, DevBatch<T>& B, double tol, int64_t iter_limit) {
+  if (h->persistent) return batch_solve_persistent<T>(h, B, tol, iter_limit);
   cudaStream_t st = h->st;
   const long long nchk = h->p.n_check;
   const long long max_chunks = (iter_limit + nchk - 1) / nchk + 2;
@@ -141,6 +200,10 @@ int create_batch(int32_t count, const scylla_csr* A, const double* const* c, con
     set_error("n_check must be >= 1");
     return SCYLLA_ERR_INVALID_ARG;
   }
+  if (h->p.batch_launch < 0 || h->p.batch_launch > 2) {
+    set_error("batch_launch must be 0..2");
+    return SCYLLA_ERR_INVALID_ARG;
+  }
   const bool mixed = h->p.precision == SCYLLA_PREC_MIXED;
   h->nlp = count;
   h->user_st = static_cast<cudaStream_t>(stream);
@@ -148,6 +211,7 @@ int create_batch(int32_t count, const scylla_csr* A, const double* const* c, con
   for (cudaEvent_t* e : {&h->ev_user, &h->ev0, &h->ev1}) CKB(cudaEventCreate(e));
   for (int k = 0; k < 2; ++k) CKB(cudaEventCreateWithFlags(&h->ev_chunk[k], cudaEventDisableTiming));
   CKB(cudaMallocHost(&h->h_done, 2 * sizeof(int)));
+  CKB(cudaMallocHost(&h->h_err, sizeof(int)));
 
   // ---- block-diagonal LP
   h->row_off.assign(count + 1, 0);
@@ -241,6 +305,9 @@ int create_batch(int32_t count, const scylla_csr* A, const double* const* c, con
   Control* ctl;
   void* slot;
   long long* kglob;
+  int *q_lps, *q_a, *q_t, *q_pre, *q_cnt;
+  unsigned int *q_ctr, *lp_cnt;
+  void* gbar;
   const int red_blocks = std::max(1, std::min(4 * device_sm_count(), (std::max(m, n) + kThreads - 1) / kThreads));
   for (int pass = 0; pass < 2; ++pass) {
     Arena ar;
@@ -304,6 +371,14 @@ int create_batch(int32_t count, const scylla_csr* A, const double* const* c, con
     slot = ar.take<char>(sizeof(BatchSlot<double>) * count);
     n_done = ar.take<int>(1);
     kglob = ar.take<long long>(1);
+    q_lps = ar.take<int>(count);
+    q_a = ar.take<int>(a_nt);
+    q_t = ar.take<int>(t_nt);
+    q_pre = ar.take<int>(2 * size_t(count + 1));
+    q_cnt = ar.take<int>(4);
+    q_ctr = ar.take<unsigned int>(4);
+    lp_cnt = ar.take<unsigned int>(count);
+    gbar = ar.take<char>(16);
     h->io = ar.take<double>(n);
     if (pass == 0) h->arena_bytes = ar.off + 256;
   }
@@ -406,6 +481,8 @@ int create_batch(int32_t count, const scylla_csr* A, const double* const* c, con
     B.tp_p = tp_p; B.tp_d = tp_d; B.tp_c1 = tp_c1; B.tp_c2 = tp_c2;
     B.n_done = n_done;
     B.kglob = kglob;
+    B.q_lps = q_lps; B.q_a = q_a; B.q_t = q_t; B.q_pre = q_pre; B.q_cnt = q_cnt; B.q_ctr = q_ctr;
+    B.lp_cnt = lp_cnt;
   };
   if (mixed) {
     fill_common(d32);
@@ -424,7 +501,39 @@ int create_batch(int32_t count, const scylla_csr* A, const double* const* c, con
     fill_batch<double>(h->b64, d64, h, X, Y, AX, ATY, XLR, YLR);
     CKB(launch_batch_init_point<double>(h->b64, st));
   }
+  // persistent form: one co-resident grid (cooperative launch) where it fits
+  h->grid_bar = gbar;
+  {
+    int coop = 0, dev = 0;
+    CKB(cudaGetDevice(&dev));
+    CKB(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    const int per_sm = mixed ? batch_persistent_blocks_per_sm<float>() : batch_persistent_blocks_per_sm<double>();
+    const int grid = (coop && per_sm > 0) ? per_sm * device_sm_count() : 0;
+    h->b32.grid_q = h->b64.grid_q = grid;
+    if (h->p.batch_launch == 2 && grid == 0) {
+      set_error("batch_launch = 2: the persistent batched kernel cannot be made co-resident here");
+      return SCYLLA_ERR_UNSUPPORTED;
+    }
+    h->persistent = grid > 0 && h->p.batch_launch == 2;
+  }
   CKB(cudaStreamSynchronize(st));
+  // automatic form: n_check attempts from the cold start in each form, timed on the
+  // device; the faster is kept (both give identical results) and the LPs go back to
+  // the cold start
+  if (h->p.batch_launch == 0 && (mixed ? h->b32.grid_q : h->b64.grid_q) > 0) {
+    for (int form = 0; form < 2; ++form) {
+      h->persistent = form == 1;
+      const int rc = mixed ? batch_solve_impl<float>(h, h->b32, 0.0, h->p.n_check)
+                           : batch_solve_impl<double>(h, h->b64, 0.0, h->p.n_check);
+      if (rc != SCYLLA_OK) return rc;
+      h->tune_ms[form] = h->last_ms;
+    }
+    h->persistent = h->tune_ms[1] < h->tune_ms[0];
+    CKB(cudaMemcpyAsync(ctl, h->ctl0.data(), sizeof(Control) * count, cudaMemcpyHostToDevice, st));
+    if (mixed) CKB(launch_batch_init_point<float>(h->b32, st));
+    else CKB(launch_batch_init_point<double>(h->b64, st));
+    CKB(cudaStreamSynchronize(st));
+  }
   return SCYLLA_OK;
 }
 
@@ -518,6 +627,68 @@ extern "C" int scylla_batch_solve(scylla_batch* h, double tol, int64_t iter_limi
     r.seconds = h->last_ms * 1e-3;
   }
   if (seconds) *seconds = h->last_ms * 1e-3;
+  return SCYLLA_OK;
+}
+
+namespace {
+// the graph form's per-attempt kernels as separate launches with CUDA events around
+// each, from the cold start, every LP taking part (see scylla_batch_time_kernels)
+template <typename T>
+int batch_time_impl(scylla_batch* h, DevBatch<T>& B, int attempts, double* ms) {
+  cudaStream_t st = h->st;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> which;
+  cudaError_t e = launch_batch_init<T>(B, 0.0, (long long)attempts + 1, 0, st);
+  if (e == cudaSuccess) e = launch_batch_check<T>(B, st);
+  for (int a = 0; a < attempts && e == cudaSuccess; ++a)
+    for (int part = 0; part < 3 && e == cudaSuccess; ++part) {
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      e = cudaEventCreate(&e0);
+      if (e == cudaSuccess) e = cudaEventCreate(&e1);
+      if (e != cudaSuccess) break;
+      ev.push_back(e0);
+      ev.push_back(e1);
+      which.push_back(part);
+      e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess) e = launch_batch_part<T>(B, part, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  double sum[3] = {0, 0, 0};
+  int cnt[3] = {0, 0, 0};
+  if (e == cudaSuccess)
+    for (size_t i = 0; i < which.size(); ++i) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]);
+      sum[which[i]] += t;
+      cnt[which[i]]++;
+    }
+  for (cudaEvent_t x : ev) cudaEventDestroy(x);
+  CKB(e);
+  for (int k = 0; k < 3; ++k) ms[k] = cnt[k] ? sum[k] / cnt[k] : 0.0;
+  return SCYLLA_OK;
+}
+}  // namespace
+
+extern "C" int scylla_batch_time_kernels(scylla_batch* h, int32_t attempts, double* ms) {
+  if (!h || !ms || attempts < 1) {
+    set_error("need a batch, ms[3] and attempts >= 1");
+    return SCYLLA_ERR_INVALID_ARG;
+  }
+  return h->p.precision == SCYLLA_PREC_MIXED ? batch_time_impl<float>(h, h->b32, attempts, ms)
+                                             : batch_time_impl<double>(h, h->b64, attempts, ms);
+}
+
+extern "C" int scylla_batch_info(const scylla_batch* h, int32_t* persistent, double* tune_ms) {
+  if (!h) {
+    set_error("null handle");
+    return SCYLLA_ERR_INVALID_ARG;
+  }
+  if (persistent) *persistent = h->persistent ? 1 : 0;
+  if (tune_ms) {
+    tune_ms[0] = h->tune_ms[0];
+    tune_ms[1] = h->tune_ms[1];
+  }
   return SCYLLA_OK;
 }
 

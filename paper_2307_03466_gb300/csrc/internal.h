@@ -145,6 +145,7 @@ struct DevBatch {
   BatchSlot<T>* slot;         // nlp
   double *tp_p, *tp_d, *tp_c1, *tp_c2;  // per-tile partial sums
   int* n_done;                // LPs finished in this solve
+  unsigned int* lp_cnt;       // per LP: tiles of A done in this attempt's dual step (the last one decides)
   long long* kglob;           // attempts made by the LPs still running
   double exp_red, exp_grow;
   int grid_p, grid_d, grid_c1, grid_c2, grid_ctl;
@@ -376,20 +377,25 @@ cudaError_t launch_batch_slot(const DevBatch<T>& B, cudaStream_t st);
 template <typename T>
 cudaError_t launch_batch_check(const DevBatch<T>& B, cudaStream_t st);
 template <typename T>
+cudaError_t launch_batch_part(const DevBatch<T>& B, int part, cudaStream_t st);
+template <typename T>
 cudaError_t launch_batch_get_x(const DevBatch<T>& B, int b, int col0, int count, double* out, cudaStream_t st);
 template <typename T>
 cudaError_t launch_batch_init_point(const DevBatch<T>& B, cudaStream_t st);
 template <typename T>
 void batch_grids(DevBatch<T>& B);
-// the persistent batched solve (all attempts and checks in one cooperative launch
-// over the shared work queue); grid_bar: a zeroed barrier, wait_limit_s bounds
-// every barrier wait, iter_limit the attempts of the solve
+// the attempts between two checks of the batched solve in one cooperative launch
+// over the shared work queue; grid_bar: a zeroed barrier, wait_limit_s bounds every
+// barrier wait, iter_limit the attempts of the solve
 template <typename T>
 cudaError_t launch_batch_persistent(const DevBatch<T>& B, void* grid_bar, long long iter_limit, double wait_limit_s,
                                     cudaStream_t st);
 // every LP and every tile in the work lists, counters zeroed (start of a solve)
 template <typename T>
 cudaError_t launch_batch_queue_reset(const DevBatch<T>& B, cudaStream_t st);
+// after a check: the work lists without the LPs that finished, counters rearmed
+template <typename T>
+cudaError_t launch_batch_compact(const DevBatch<T>& B, cudaStream_t st);
 template <typename T>
 int batch_persistent_blocks_per_sm();
 

@@ -1552,8 +1552,10 @@ __global__ void k_cnorm_cols(DevObjective o, double offset_base) {
 // boundary and carry their LP's index; every LP has its own control block, so its
 // step size, pool roles, restarts and termination are its own.  Tiles of LPs that
 // are finished (or waiting at their iteration limit) are skipped.  Sums are kept per
-// tile and reduced per LP, in a fixed order, by one warp per LP in the control
-// kernels, which then run the same step and check logic as the single-LP path.
+// tile and reduced per LP in a fixed order: for the step decision by the warp that
+// finishes the LP's last tile of the dual step, for the checks by one warp per LP in
+// the check control kernel; both run the same step and check logic as the single-LP
+// path.
 
 // One warp tile of the batched kernels (a multi-row tile or one long row): the
 // products into the warp's skewed shared buffer, then each lane sums its row in CSR
@@ -1692,6 +1694,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_bprimal(DevBatch<T> B) {
   __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
   const DevLP<T>& d = B.d;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ++*B.kglob;  // attempt counter of the LPs still running
   BPrimalEpi<T> epi;
   epi.B = &B;
   epi.xlr = d.XLR;
@@ -1705,12 +1708,92 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_bprimal(DevBa
                             sm + (threadIdx.x >> 5) * kSmemPerWarp);
 }
 
+// device-scope release increment and acquire fence (the per-LP completion counters
+// of the persistent batched kernel)
+__device__ __forceinline__ unsigned int atom_add_release_gpu(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// a control block into a warp's shared copy (L2 loads) and back, word by word
+__device__ __forceinline__ void ctl_in(Control* dst, const Control* src) {
+  static_assert(sizeof(Control) % 4 == 0, "word copy");
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < int(sizeof(Control) / 4); i += 32)
+    reinterpret_cast<int*>(dst)[i] = __ldcg(reinterpret_cast<const int*>(src) + i);
+  __syncwarp();
+}
+__device__ __forceinline__ void ctl_out(Control* dst, const Control* src) {
+  __syncwarp();
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < int(sizeof(Control) / 4); i += 32)
+    reinterpret_cast<int*>(dst)[i] = reinterpret_cast<const int*>(src)[i];
+  __syncwarp();
+}
+
+// the decision of one LP on its shared control copy: out of line, so that its
+// registers do not count against the matrix phases of the persistent kernel
+template <typename T>
+__device__ __noinline__ void bq_decide(Control* sc, double s0, double s1, double s2, const double* fac, int n_check,
+                                       BatchSlot<T>* slot, int* n_done) {
+  step_control(sc, s0, s1, s2, fac, n_check, nullptr, 0);
+  if (sc->done) atomicAdd(n_done, 1);
+  write_slot(slot, sc);
+}
+
+// Sum over an LP's tiles of one per-tile value (part[t * stride + off], t in
+// [beg, end)), by one warp: each lane keeps four running sums over its tiles
+// (t = beg + lane, + 32, ...), taken round-robin, so four loads per lane are in
+// flight; then the four in a fixed order and a fixed shuffle tree.  Per-tile sums are
+// written in the same launch, so they are read from L2.
+__device__ __forceinline__ double lp_tile_sum(const double* part, int stride, int off, int beg, int end) {
+  const int lane = threadIdx.x & 31;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  int t = beg + lane;
+  for (; t + 96 < end; t += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a[u] += __ldcg(part + size_t(t + 32 * u) * stride + off);
+  }
+  for (int u = 0; t < end; t += 32, ++u) a[u & 3] += __ldcg(part + size_t(t) * stride + off);
+  return warp_sum((a[0] + a[1]) + (a[2] + a[3]));
+}
+
+// The step decision of LP lp by one warp, from its per-tile sums of this attempt:
+// out of line, so its registers do not count against the dual step's tile loop.
+// sc: a shared-memory copy for the control block (the persistent kernel, where
+// another block may have written it), or null (read and written in place).
+template <typename T>
+__device__ __noinline__ void lp_step_decision(const DevBatch<T>* B, int lp, Control* sc) {
+  const int lane = threadIdx.x & 31;
+  const int tb = __ldg(B->t_tile_beg + lp), te = __ldg(B->t_tile_beg + lp + 1);
+  const int ab = __ldg(B->a_tile_beg + lp), ae = __ldg(B->a_tile_beg + lp + 1);
+  const double s0 = lp_tile_sum(B->tp_p, 1, 0, tb, te);
+  const double s1 = lp_tile_sum(B->tp_d, 2, 0, ab, ae);
+  const double s2 = lp_tile_sum(B->tp_d, 2, 1, ab, ae);
+  if (sc) {
+    ctl_in(sc, B->ctl + lp);
+    if (lane == 0) bq_decide<T>(sc, s0, s1, s2, B->d.step_fac, B->d.n_check, &B->slot[lp], B->n_done);
+    ctl_out(B->ctl + lp, sc);
+  } else if (lane == 0) {
+    Control* c = &B->ctl[lp];
+    step_control(c, s0, s1, s2, B->d.step_fac, B->d.n_check, nullptr, 0);
+    if (c->done) atomicAdd(B->n_done, 1);
+    write_slot(&B->slot[lp], c);
+  }
+  if (lane == 0) B->lp_cnt[lp] = 0u;
+}
+
 template <typename T, bool Coh = false>
 struct BDualEpi : DualEpi<T, Coh> {
   const DevBatch<T>* B;
   const T* xsrc;
+  int lp;
+  Control* sc;  // a shared-memory copy for the decision (the persistent kernel), or null
   __device__ __forceinline__ bool begin(int b, int) {
     const BatchSlot<T> s = read_slot<Coh>(B->slot + b);
+    lp = b;
     if (!(s.flags & kSlotActive)) return false;
     const DevLP<T>& d = B->d;
     this->axc = d.AX[s.cur];
@@ -1726,16 +1809,39 @@ struct BDualEpi : DualEpi<T, Coh> {
     xsrc = d.X[s.nxt];
     return true;
   }
+  // the tile's sums; in the persistent kernel (Coh) the warp that finishes the
+  // LP's last tile of this attempt takes the LP's step decision (its primal sums are
+  // complete since the primal step came before): the tile's sums are released to the
+  // LP's counter by its increment, and the last one acquires them all
   __device__ __forceinline__ void end(int t) {
     const typename AccOf<T>::type a0 = warp_sum(this->acc0), a1 = warp_sum(this->acc1);
-    if ((threadIdx.x & 31) == 0) {
+    const int lane = threadIdx.x & 31;
+    int last = 0;
+    if (lane == 0) {
       B->tp_d[2 * t] = double(a0);
       B->tp_d[2 * t + 1] = double(a1);
+      if (Coh) {
+        const unsigned int ntiles = unsigned(__ldg(B->a_tile_beg + lp + 1) - __ldg(B->a_tile_beg + lp));
+        last = atom_add_release_gpu(B->lp_cnt + lp, 1u) == ntiles - 1u;
+      }
     }
     this->acc0 = 0;
     this->acc1 = 0;
+    if (!Coh || !__shfl_sync(0xffffffffu, last, 0)) return;
+    fence_acquire_gpu();
+    lp_step_decision<T>(B, lp, sc);
   }
 };
+
+// one warp per LP: its tiles' sums in a fixed order, then the step decision (the
+// launch-per-phase path)
+template <typename T>
+__global__ void k_bstep_control(DevBatch<T> B) {
+  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (b >= B.nlp) return;
+  if (!(B.slot[b].flags & kSlotActive)) return;
+  lp_step_decision<T>(&B, b, nullptr);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_bdual(DevBatch<T> B) {
@@ -1743,6 +1849,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_bdual(DevBatc
   const DevLP<T>& d = B.d;
   BDualEpi<T> epi;
   epi.B = &B;
+  epi.sc = nullptr;
   epi.ylr = d.YLR;
   epi.lo = d.lo;
   epi.hi = d.hi;
@@ -1751,31 +1858,6 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_bdual(DevBatc
   auto gat = [&](int j, T(&g)[1]) { g[0] = __ldg(epi.xsrc + j); };
   spmv_tiles_batch<1, T, T>(d.a_tiles, B.a_tile_lp, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals, gat, epi,
                             sm + (threadIdx.x >> 5) * kSmemPerWarp);
-}
-
-// one warp per LP: its tiles' sums in a fixed order, then the step decision
-template <typename T>
-__global__ void k_bstep_control(DevBatch<T> B) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) ++*B.kglob;  // attempt counter of the LPs still running
-  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (b >= B.nlp) return;
-  if (!(B.slot[b].flags & kSlotActive)) return;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-  for (int t = B.t_tile_beg[b] + lane; t < B.t_tile_beg[b + 1]; t += 32) s0 += B.tp_p[t];
-  for (int t = B.a_tile_beg[b] + lane; t < B.a_tile_beg[b + 1]; t += 32) {
-    s1 += B.tp_d[2 * t];
-    s2 += B.tp_d[2 * t + 1];
-  }
-  s0 = warp_sum(s0);
-  s1 = warp_sum(s1);
-  s2 = warp_sum(s2);
-  if (lane == 0) {
-    Control* c = &B.ctl[b];
-    step_control(c, s0, s1, s2, B.d.step_fac, B.d.n_check, nullptr, 0);
-    if (c->done) atomicAdd(B.n_done, 1);
-    write_slot(&B.slot[b], c);
-  }
 }
 
 template <typename T, bool Coh = false>
@@ -1942,6 +2024,7 @@ __global__ void k_binit(DevBatch<T> B, double tol, long long iter_limit, int sta
     *B.n_done = 0;
   }
   if (b >= B.nlp) return;
+  B.lp_cnt[b] = 0u;
   Control* c = &B.ctl[b];
   c->tol = tol;
   c->iter_limit = iter_limit;
@@ -1983,38 +2066,46 @@ __global__ void k_binit_point(DevBatch<T> B) {
 
 
 // ------------------------------------- persistent batched solve over a work queue ---
-// One cooperative launch runs a whole batched solve.  Every phase (primal, dual,
-// step control; at checks the two check halves, check control and the rebuild of
-// the work lists) is separated from the next by a bounded grid barrier.  In the
-// matrix phases warps take chunks of kQChunk tiles from a shared counter over the
-// list of tiles of the LPs still running, so the work is balanced over the grid
-// whatever the sizes of the LPs; at every check the LPs that finished are dropped
-// from the lists (compaction), so their tiles are not visited again.  The
+// One cooperative launch runs the attempts between two checks.  The two phases of
+// an attempt (primal; dual with the step decisions) are separated by bounded grid
+// barriers.  In the matrix phases warps take the tiles of a list of the tiles of
+// the LPs still running: a contiguous share each, then the rest in chunks of
+// kQChunk from a shared counter, so the work is balanced over the grid whatever the
+// sizes of the LPs; after every check the LPs that finished are dropped from the
+// lists (compaction), so their tiles are not visited again.  The
 // arithmetic per tile and the per-LP reduction of the per-tile sums are those of
 // the launch-per-phase path (same functions, same order), so the two give
 // identical results.  Work moves between blocks from one phase to the next, so
 // every load of data written during the launch goes to L2 (ld.global.cg): the
-// vectors, slots, control blocks, per-tile sums, lists and the step-factor table.
+// vectors, slots, control blocks, per-tile sums and lists.
 constexpr int kQChunk = 4;          // tiles a warp takes from a queue at once
-constexpr int kQMaxNcheck = 256;    // the step-factor table is held in shared memory
 
+// The tiles of a work list for one phase: each warp first works through its own
+// contiguous share of the first three quarters of the list (no atomics), then the
+// warps take the last quarter kQChunk tiles at a time from the shared counter, which
+// evens out the finishing times whatever the tiles' costs.
 template <int NV, typename Acc, typename V, typename Gather, typename Epi>
 __device__ __forceinline__ void queue_tiles(const int* list, int count, unsigned int* ctr, const int2* tiles,
                                             const int* tile_lp, const int* rowptr, const int* cols, const V* vals,
                                             Gather& gat, Epi& epi, Acc* sm) {
   const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  auto one = [&](int v) {
+    const int t = __ldcg(list + v);
+    if (!epi.begin(__ldg(tile_lp + t), t)) return;
+    batch_tile<NV, Acc, V>(t, tiles, rowptr, cols, vals, gat, epi, sm);
+    epi.end(t);
+  };
+  const int per = int((3LL * count) / (4LL * nw));
+  for (int v = gw * per; v < (gw + 1) * per; ++v) one(v);
+  const int head = per * nw;
   for (;;) {
     int v0 = 0;
-    if (lane == 0) v0 = int(atomicAdd(ctr, unsigned(kQChunk)));
+    if (lane == 0) v0 = head + int(atomicAdd(ctr, unsigned(kQChunk)));
     v0 = __shfl_sync(0xffffffffu, v0, 0);
     if (v0 >= count) break;
     const int v1 = min(count, v0 + kQChunk);
-    for (int v = v0; v < v1; ++v) {
-      const int t = __ldcg(list + v);
-      if (!epi.begin(__ldg(tile_lp + t), t)) continue;
-      batch_tile<NV, Acc, V>(t, tiles, rowptr, cols, vals, gat, epi, sm);
-      epi.end(t);
-    }
+    for (int v = v0; v < v1; ++v) one(v);
   }
 }
 
@@ -2035,10 +2126,11 @@ __device__ __forceinline__ void bq_primal(const DevBatch<T>& B, int count, T* sm
 }
 
 template <typename T>
-__device__ __forceinline__ void bq_dual(const DevBatch<T>& B, int count, T* sm) {
+__device__ __forceinline__ void bq_dual(const DevBatch<T>& B, int count, T* sm, Control* sc) {
   const DevLP<T>& d = B.d;
   BDualEpi<T, true> epi;
   epi.B = &B;
+  epi.sc = sc;
   epi.ylr = d.YLR;
   epi.lo = d.lo;
   epi.hi = d.hi;
@@ -2093,56 +2185,6 @@ __device__ __forceinline__ void bq_check_rows(const DevBatch<T>& B, int count, d
   };
   queue_tiles<2, double, double>(B.q_a, count, B.q_ctr + 3, d.a_tiles, B.a_tile_lp, d.a_rowptr, d.a_cols, d.a_vals64,
                                  gat, epi, sm);
-}
-
-// a control block into a warp's shared copy (L2 loads) and back, word by word
-__device__ __forceinline__ void ctl_in(Control* dst, const Control* src) {
-  static_assert(sizeof(Control) % 4 == 0, "word copy");
-  const int lane = threadIdx.x & 31;
-  for (int i = lane; i < int(sizeof(Control) / 4); i += 32)
-    reinterpret_cast<int*>(dst)[i] = __ldcg(reinterpret_cast<const int*>(src) + i);
-  __syncwarp();
-}
-__device__ __forceinline__ void ctl_out(Control* dst, const Control* src) {
-  __syncwarp();
-  const int lane = threadIdx.x & 31;
-  for (int i = lane; i < int(sizeof(Control) / 4); i += 32)
-    reinterpret_cast<int*>(dst)[i] = reinterpret_cast<const int*>(src)[i];
-  __syncwarp();
-}
-
-// step decision of every running LP, one warp per LP over the LP list; block 0
-// counts the attempt and rearms the matrix phases' counters (every warp has
-// finished taking tiles from them)
-template <typename T>
-__device__ __forceinline__ void bq_step(const DevBatch<T>& B, int nl, Control* sc, const double* fac) {
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ++*B.kglob;
-    B.q_ctr[0] = 0u;
-    B.q_ctr[1] = 0u;
-  }
-  for (int q = gw; q < nl; q += nw) {
-    const int b = __ldcg(B.q_lps + q);
-    if (!(__ldcg(&B.slot[b].flags) & kSlotActive)) continue;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int t = __ldg(B.t_tile_beg + b) + lane; t < __ldg(B.t_tile_beg + b + 1); t += 32) s0 += __ldcg(B.tp_p + t);
-    for (int t = __ldg(B.a_tile_beg + b) + lane; t < __ldg(B.a_tile_beg + b + 1); t += 32) {
-      s1 += __ldcg(B.tp_d + 2 * t);
-      s2 += __ldcg(B.tp_d + 2 * t + 1);
-    }
-    s0 = warp_sum(s0);
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
-    ctl_in(sc, B.ctl + b);
-    if (lane == 0) {
-      step_control(sc, s0, s1, s2, fac, B.d.n_check, nullptr, 0);
-      if (sc->done) atomicAdd(B.n_done, 1);
-      write_slot(&B.slot[b], sc);
-    }
-    ctl_out(B.ctl + b, sc);
-  }
 }
 
 // termination, stalling and restarts of every LP in the list; block 0 refills the
@@ -2275,54 +2317,46 @@ __device__ __forceinline__ void bq_fill_tiles(const DevBatch<T>& B, int nl) {
   }
 }
 
+// The attempts between two checks in one cooperative launch: primal phase, dual
+// phase and step decisions per attempt, separated by bounded grid barriers, until
+// n_check attempts are made or the iteration limit is reached.  The checks, and the
+// compaction of the work lists after them, run as ordinary kernels between launches.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 3) k_bsolve_persistent(DevBatch<T> B, GridBar* bar, long long iter_limit,
-                                                               unsigned long long limit_ns) {
-  __shared__ double sm[2 * kWarpsPerBlock * kSmemPerWarp];  // tile products, 2 vectors of FP64 at a check
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value)
+    k_battempts_persistent(DevBatch<T> B, GridBar* bar, long long iter_limit, unsigned long long limit_ns) {
+  __shared__ T sm[kWarpsPerBlock * kSmemPerWarp];
   __shared__ Control sctl[kWarpsPerBlock];
-  __shared__ double fac[2 * kQMaxNcheck];
   const int w = threadIdx.x >> 5;
-  double* smw2 = sm + w * 2 * kSmemPerWarp;
-  T* smw1 = reinterpret_cast<T*>(sm) + w * kSmemPerWarp;
-  bool ok = true, do_check = true;
-  long long since = 0;
-  int nl = 0, na = 0, nt = 0;
-  while (ok) {
-    if (do_check) {
-      nl = __ldcg(B.q_cnt + 0);
-      na = __ldcg(B.q_cnt + 1);
-      nt = __ldcg(B.q_cnt + 2);
-      bq_check_cols<T>(B, nt, smw2);
-      if (!(ok = grid_sync(bar, limit_ns))) break;
-      bq_check_rows<T>(B, na, smw2);
-      if (!(ok = grid_sync(bar, limit_ns))) break;
-      bq_check_control<T>(B, nl, &sctl[w]);
-      if (!(ok = grid_sync(bar, limit_ns))) break;
-      if (blockIdx.x == 0) bq_compact_lps<T>(B, nl);
-      if (!(ok = grid_sync(bar, limit_ns))) break;
-      nl = __ldcg(B.q_cnt + 0);
-      na = __ldcg(B.q_cnt + 1);
-      nt = __ldcg(B.q_cnt + 2);
-      bq_fill_tiles<T>(B, nl);
-      if (!(ok = grid_sync(bar, limit_ns))) break;
-      for (int i = threadIdx.x; i < 2 * B.d.n_check; i += blockDim.x) fac[i] = __ldcg(B.d.step_fac + i);
-      __syncthreads();
-      since = 0;
-      do_check = false;
-      if (nl == 0) break;  // every LP has finished
+  T* smw = sm + w * kSmemPerWarp;
+  const int nl = __ldcg(B.q_cnt + 0), na = __ldcg(B.q_cnt + 1), nt = __ldcg(B.q_cnt + 2);
+  if (nl == 0) return;
+  const long long k0 = __ldcg(B.kglob);  // attempts before this launch (a previous launch wrote it)
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  for (int since = 0; since < B.d.n_check && k0 + since < iter_limit; ++since) {
+    // the primal step (block 0 counts the attempt and rearms the dual counter, which
+    // nobody takes from until after the next barrier)
+    if (lead) {
+      ++*B.kglob;
+      B.q_ctr[1] = 0u;
     }
-    if (since == B.d.n_check || __ldcg(B.kglob) >= iter_limit) {
-      do_check = true;
-      continue;
-    }
-    bq_primal<T>(B, nt, smw1);
-    if (!(ok = grid_sync(bar, limit_ns))) break;
-    bq_dual<T>(B, na, smw1);
-    if (!(ok = grid_sync(bar, limit_ns))) break;
-    bq_step<T>(B, nl, &sctl[w], fac);
-    if (!(ok = grid_sync(bar, limit_ns))) break;
-    ++since;
+    bq_primal<T>(B, nt, smw);
+    if (!grid_sync(bar, limit_ns)) return;
+    // the dual step, whose last tile of each LP takes that LP's step decision
+    if (lead) B.q_ctr[0] = 0u;
+    bq_dual<T>(B, na, smw, &sctl[w]);
+    if (!grid_sync(bar, limit_ns)) return;
   }
+}
+
+// after a check: the LP list without the LPs that finished (one block), then the
+// tile lists of the LPs kept (every block)
+template <typename T>
+__global__ void k_bcompact(DevBatch<T> B) {
+  bq_compact_lps<T>(B, B.q_cnt[0]);
+}
+template <typename T>
+__global__ void k_bfill_tiles(DevBatch<T> B) {
+  bq_fill_tiles<T>(B, B.q_cnt[0]);
 }
 
 // every LP and every tile in the work lists (in order), counters zeroed
@@ -2567,6 +2601,15 @@ cudaError_t launch_batch_slot(const DevBatch<T>& B, cudaStream_t st) {
   k_bstep_control<T><<<B.grid_ctl, kThreads, 0, st>>>(B);
   return cudaGetLastError();
 }
+// one kernel of an attempt on its own (measurement): 0 primal, 1 dual, 2 step control
+template <typename T>
+cudaError_t launch_batch_part(const DevBatch<T>& B, int part, cudaStream_t st) {
+  if (part == 0) k_bprimal<T><<<B.grid_p, kThreads, 0, st>>>(B);
+  else if (part == 1) k_bdual<T><<<B.grid_d, kThreads, 0, st>>>(B);
+  else k_bstep_control<T><<<B.grid_ctl, kThreads, 0, st>>>(B);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_batch_check(const DevBatch<T>& B, cudaStream_t st) {
   k_bcheck_cols<T><<<B.grid_c1, kThreads, 0, st>>>(B);
@@ -2587,7 +2630,8 @@ cudaError_t launch_batch_init_point(const DevBatch<T>& B, cudaStream_t st) {
 template <typename T>
 int batch_persistent_blocks_per_sm() {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bsolve_persistent<T>, kThreads, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_battempts_persistent<T>, kThreads, 0) !=
+      cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -2604,13 +2648,20 @@ cudaError_t launch_batch_queue_reset(const DevBatch<T>& B, cudaStream_t st) {
 template <typename T>
 cudaError_t launch_batch_persistent(const DevBatch<T>& B, void* grid_bar, long long iter_limit, double wait_limit_s,
                                     cudaStream_t st) {
-  if (B.grid_q < 1 || B.d.n_check > kQMaxNcheck) return cudaErrorInvalidConfiguration;
+  if (B.grid_q < 1) return cudaErrorInvalidConfiguration;
   GridBar* bar = static_cast<GridBar*>(grid_bar);
   unsigned long long limit_ns = (unsigned long long)(wait_limit_s * 1e9);
   DevBatch<T> bb = B;
   void* args[] = {&bb, &bar, &iter_limit, &limit_ns};
-  return cudaLaunchCooperativeKernel((const void*)k_bsolve_persistent<T>, dim3(B.grid_q), dim3(kThreads), args, 0,
+  return cudaLaunchCooperativeKernel((const void*)k_battempts_persistent<T>, dim3(B.grid_q), dim3(kThreads), args, 0,
                                      st);
+}
+
+template <typename T>
+cudaError_t launch_batch_compact(const DevBatch<T>& B, cudaStream_t st) {
+  k_bcompact<T><<<1, kThreads, 0, st>>>(B);
+  k_bfill_tiles<T><<<ew_grid(32LL * B.nlp), kThreads, 0, st>>>(B);
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -2636,12 +2687,14 @@ void batch_grids(DevBatch<T>& B) {
   template cudaError_t launch_batch_init<T>(const DevBatch<T>&, double, long long, int, cudaStream_t); \
   template cudaError_t launch_batch_slot<T>(const DevBatch<T>&, cudaStream_t);                         \
   template cudaError_t launch_batch_check<T>(const DevBatch<T>&, cudaStream_t);                        \
+  template cudaError_t launch_batch_part<T>(const DevBatch<T>&, int, cudaStream_t);                    \
   template cudaError_t launch_batch_get_x<T>(const DevBatch<T>&, int, int, int, double*, cudaStream_t); \
   template cudaError_t launch_batch_init_point<T>(const DevBatch<T>&, cudaStream_t);                   \
   template void batch_grids<T>(DevBatch<T>&);                                                            \
   template int batch_persistent_blocks_per_sm<T>();                                                       \
   template cudaError_t launch_batch_queue_reset<T>(const DevBatch<T>&, cudaStream_t);                     \
-  template cudaError_t launch_batch_persistent<T>(const DevBatch<T>&, void*, long long, double, cudaStream_t);
+  template cudaError_t launch_batch_persistent<T>(const DevBatch<T>&, void*, long long, double, cudaStream_t); \
+  template cudaError_t launch_batch_compact<T>(const DevBatch<T>&, cudaStream_t);
 
 SCYLLA_INSTANTIATE_BATCH(double)
 SCYLLA_INSTANTIATE_BATCH(float)

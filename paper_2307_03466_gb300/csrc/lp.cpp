@@ -86,6 +86,8 @@ extern "C" void scylla_default_params(scylla_params* p) {
   p->repair_tol = 1e-7;
   p->repair_rounds = 8;
   p->distance = 1;
+  p->batch_launch = 0;
+  p->autotune = 1;
 }
 
 extern "C" const char* scylla_last_error(void) { return get_error(); }

@@ -48,7 +48,7 @@ class Params(C.Structure):
                 ("time_limit_s", C.c_double), ("device_wait_limit_s", C.c_double), ("pdl", C.c_int32),
                 ("prefetch", C.c_int32), ("host_transpose", C.c_int32),
                 ("repair_iters", C.c_int64), ("repair_tol", C.c_double), ("repair_rounds", C.c_int32),
-                ("distance", C.c_int32)]
+                ("distance", C.c_int32), ("batch_launch", C.c_int32), ("autotune", C.c_int32)]
 
 
 class PdhgResult(C.Structure):
@@ -127,6 +127,8 @@ _SIGS = {
     "scylla_fanout_solve": (C.c_int, [_P, C.c_double, C.c_int64, C.POINTER(PdhgResult), _D]),
     "scylla_fanout_get_primal": (C.c_int, [_P, C.c_int32, _D]),
     "scylla_fanout_reset_state": (C.c_int, [_P]),
+    "scylla_batch_info": (C.c_int, [_P, C.POINTER(C.c_int32), _D]),
+    "scylla_batch_time_kernels": (C.c_int, [_P, C.c_int32, _D]),
     "scylla_fanout_time_kernels": (C.c_int, [_P, C.c_int32, _D]),
     "scylla_fanout_tune": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "scylla_fanout_info": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _D]),
@@ -483,6 +485,21 @@ class Batch:
 
     def reset_state(self):
         _check(lib().scylla_batch_reset_state(self.h))
+
+    def info(self):
+        """(1 if the persistent work-queue launch is in use else 0, the create-time
+        ms of n_check attempts in the graph and persistent forms)."""
+        p = C.c_int32()
+        ms = np.zeros(2)
+        _check(lib().scylla_batch_info(self.h, C.byref(p), _dp(ms)))
+        return p.value, ms
+
+    def time_kernels(self, attempts: int) -> np.ndarray:
+        """Mean device ms of the primal step, dual step and step control of the graph
+        form as separate launches (scylla_batch_time_kernels)."""
+        ms = np.zeros(3)
+        _check(lib().scylla_batch_time_kernels(self.h, int(attempts), _dp(ms)))
+        return ms
 
 
 class Fanout:

@@ -52,8 +52,8 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu\n", offsetof(scylla_params, fixed_step_factor), offsetof(scylla_params, seed),
          offsetof(scylla_params, time_limit_s), offsetof(scylla_params, repair_iters),
          offsetof(scylla_params, repair_tol));
-  printf("%zu %zu %zu\n", offsetof(scylla_params, repair_rounds), offsetof(scylla_repair_result, rel_kkt),
-         offsetof(scylla_params, distance));
+  printf("%zu %zu %zu %zu %zu\n", offsetof(scylla_params, repair_rounds), offsetof(scylla_repair_result, rel_kkt),
+         offsetof(scylla_params, distance), offsetof(scylla_params, batch_launch), offsetof(scylla_params, autotune));
   return 0;
 }
 '''
@@ -68,7 +68,8 @@ int main(void) {
                          C.sizeof(S.RepairResult)]
     assert sizes[5:] == [S.Params.fixed_step_factor.offset, S.Params.seed.offset, S.Params.time_limit_s.offset,
                          S.Params.repair_iters.offset, S.Params.repair_tol.offset,
-                         S.Params.repair_rounds.offset, S.RepairResult.rel_kkt.offset, S.Params.distance.offset]
+                         S.Params.repair_rounds.offset, S.RepairResult.rel_kkt.offset, S.Params.distance.offset,
+                         S.Params.batch_launch.offset, S.Params.autotune.offset]
 
 
 def test_default_params_are_the_papers(L):

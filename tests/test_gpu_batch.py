@@ -107,3 +107,48 @@ def test_batch_rejects_invalid_member():
     with pytest.raises(S.ScyllaError) as ei:
         S.Batch([I.set_cover(m=20, n=30, seed=2), bad])
     assert ei.value.code == S.ERR_INVALID_ARG and "LP 1" in str(ei.value)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("adaptive", [0, 1])
+def test_persistent_queue_and_graph_paths_identical(precision, adaptive):
+    """The persistent launch (warps take tiles from a shared queue over the LPs still
+    running, compacted at every check) and the launch-per-phase graphs over a static
+    deal of the tiles compute every tile with the same arithmetic and reduce each
+    LP's per-tile sums in the same order: identical points, attempt counts,
+    rejections and restarts, with LPs finishing at different checks on the way."""
+    S = lib()
+    insts = batch_instances()
+    kw = dict(precision=precision, adaptive_step=adaptive, restarts=adaptive)
+    tol = 1e-6 if precision == 0 else 1e-4
+    out = {}
+    for mode in (1, 2):
+        B = S.Batch(insts, S.default_params(batch_launch=mode, **kw))
+        res, _ = B.solve(tol, 20000 if adaptive else 700)
+        out[mode] = ([B.primal(b) for b in range(len(insts))],
+                     [(r.iterations, r.rejected, r.restarts, r.status) for r in res])
+        B.close()
+    for b in range(len(insts)):
+        np.testing.assert_array_equal(out[2][0][b], out[1][0][b], err_msg=str(b))
+    assert out[2][1] == out[1][1]
+    if adaptive:
+        assert len({t[0] for t in out[2][1]}) > 1  # LPs left the queue at different checks
+
+
+def test_persistent_queue_barrier_timeout_is_reported():
+    """Every grid-barrier wait of the persistent batched kernel is bounded: with a
+    limit far below any barrier's duration the first wait runs out, every block
+    leaves, and the solve returns SCYLLA_ERR_TIMEOUT with the LPs marked
+    DEVICE_TIMEOUT; the context stays usable and a batch with the normal limit then
+    solves to the tolerance."""
+    S = lib()
+    insts = batch_instances()[:3]
+    B = S.Batch(insts, S.default_params(batch_launch=2, device_wait_limit_s=1e-9))
+    with pytest.raises(S.ScyllaError) as ei:
+        B.solve(1e-6, 1000)
+    assert ei.value.code == S.ERR_TIMEOUT
+    B.close()
+    B = S.Batch(insts, S.default_params(batch_launch=2))
+    res, _ = B.solve(1e-6, 100000)
+    assert all(r.status == O.CONVERGED for r in res)
+    B.close()

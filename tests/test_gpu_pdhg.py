@@ -297,3 +297,23 @@ def test_mixed_precision_reaches_1e4_checked_by_oracle(name):
     obj_err = abs(ev.pobj - rr.pobj) / (1 + abs(rr.pobj))
     assert obj_err <= 1e-3  # the oracle's own error at rel-KKT 1e-4 here is <= 6e-6
     g.close()
+
+
+def test_persistent_kernel_barrier_timeout_is_reported():
+    """Every grid-barrier wait of the persistent solve kernel (use_graph = 3) is
+    bounded: with a limit far below a barrier's duration the first wait runs out,
+    every block leaves, and the solve returns SCYLLA_ERR_TIMEOUT.  The barrier is
+    cleared at the start of every solve, so the handle stays usable (a second solve
+    reports the same), and a handle with the normal limit converges."""
+    import paper_2307_03466_gb300.scylla as S
+    inst = INSTANCES["packcover_2kx4k"]
+    g, _ = pair(inst, use_graph=3)
+    g2 = S.LP.from_instance(inst, S.default_params(use_graph=3, aux_general_integers=0, device_wait_limit_s=1e-9))
+    for _ in range(2):
+        with pytest.raises(S.ScyllaError) as ei:
+            g2.pdhg_solve(1e-6, 5000)
+        assert ei.value.code == S.ERR_TIMEOUT
+    g2.close()
+    r = g.pdhg_solve(1e-6, 100000)
+    assert r.status == O.CONVERGED and r.launches == 2
+    g.close()
