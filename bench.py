@@ -476,6 +476,7 @@ def run_ours(args):
                      "obj_rel_err_vs_oracle": (abs(last_d.pobj - ref) / (1 + abs(ref))) if ref is not None else None},
             "oracle_objective": ref,
             "reference": "FP64 CPU oracle solved to rel-KKT 1e-8 (tests/golden/reference_objectives.json)"},
+        "autotuner": autotune_info(mixed, fp64),
         "kernel_ms": {"mixed": {"primal": ms[0], "dual": ms[1], "check_cols": ms[2], "check_rows": ms[3]},
                       "fp64": {"primal": ms64[0], "dual": ms64[1], "check_cols": ms64[2], "check_rows": ms64[3]},
                       "isolated_launches": {"mixed": list(ms_iso), "fp64": list(ms64_iso)}},
@@ -518,6 +519,22 @@ def run_ours(args):
         hbm["fanout"] = {k: fanout["roofline"][k] for k in ("kernel", "achieved", "frac")}
     out["roofline"]["hbm_bound_workloads"] = hbm
     out["summary"] = summary_of(out)
+    return out
+
+
+FORM_NAMES = {4: "32-row tiles", 1: "32-row tiles, first tile prefetched", 2: "wide tiles (<= 128 rows)",
+              3: "wide tiles staged in shared memory"}
+
+
+def autotune_info(*lps):
+    """The per-attempt kernels' form each handle runs, the L2-size rule's, and the
+    create-time autotuner's times per attempt of the two forms it compares."""
+    out = {}
+    for lp in lps:
+        f, r, ms = lp.kernel_form()
+        key = "mixed" if lp.params.precision == 1 else "fp64"
+        out[key] = {"form": FORM_NAMES.get(f, f), "l2_rule_form": FORM_NAMES.get(r, r),
+                    "tuned_ms_per_attempt": {"32-row": ms[0], "wide": ms[1]}}
     return out
 
 
@@ -853,7 +870,10 @@ def dram_resident(S, peak, peak_kind):
         gp, gd = bp / (ms[0] * 1e6), bd / (ms[1] * 1e6)
         kname, kb, kms = (f"k_dual<{'float' if sv == 4 else 'double'}>", bd, ms[1]) if ms[1] >= ms[0] else \
             (f"k_primal<{'float' if sv == 4 else 'double'}>", bp, ms[0])
+        f, rule, tms = lp.kernel_form()
         out[name] = {"iter_per_s": r.iterations / r.seconds, "attempts": r.iterations, "rel_kkt_after": r.rel_kkt,
+                     "kernel_form": FORM_NAMES.get(f, f), "l2_rule_form": FORM_NAMES.get(rule, rule),
+                     "tuned_ms_per_attempt": {"32-row": tms[0], "wide": tms[1]},
                      "time_to_kkt_1e4": {"converged": rt.status == S.CONVERGED, "ms": 1e3 * rt.seconds,
                                          "attempts": int(rt.iterations), "cap": DRAM_TTK_CAP,
                                          "eps_p": rt.eps_p, "eps_d": rt.eps_d, "eps_g": rt.eps_g,

@@ -146,6 +146,9 @@ typedef struct {
   double eta, omega;     /* step size and primal weight after the solve */
   double seconds;        /* device time of the solve (CUDA events) */
   int64_t launches;      /* kernel launches issued, including ones that returned early */
+  int32_t kernel_form;   /* form of the per-attempt kernels (scylla_params.prefetch's numbering: 4 32-row
+                            tiles, 1 32-row with prefetch, 2 wide tiles, 3 staged wide tiles); 0 for the
+                            batched and fan-out solves */
 } scylla_pdhg_result;
 
 typedef struct {
@@ -264,6 +267,14 @@ int scylla_reset_state(scylla_lp* lp);
  * dual step, column check, row check (0 where a kernel did not run).  The pair
  * moves on by those attempts. */
 int scylla_time_kernels(scylla_lp* lp, int32_t attempts, double* ms);
+
+/* Form of the per-attempt kernels in use (numbered as scylla_params.prefetch: 4
+ * 32-row tiles, 1 32-row with prefetch, 2 wide tiles, 3 staged), the form the
+ * L2-size rule gives, and the create-time autotuner's times per attempt (primal plus
+ * dual, ms) of the 32-row and the wide form (0 when it did not time them: a forced
+ * form, autotune = 0, or the choice kept from an earlier handle of the same shape).
+ * Any output may be NULL. */
+int scylla_kernel_form(const scylla_lp* lp, int32_t* form, int32_t* rule_form, double* tune_ms);
 
 /* Diagonal scaling A~ = diag(R) A diag(C) found at create: host, R length m_total,
  * C length n_total. */

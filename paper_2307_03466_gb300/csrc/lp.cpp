@@ -6,6 +6,11 @@
 // whose device-side while loop runs until the device control block says done.
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <type_traits>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -209,6 +214,8 @@ namespace {
 
 template <typename T>
 void fill_dev(DevLP<T>& d, scylla_lp* lp);
+template <typename T>
+int autotune_form(scylla_lp* lp);
 
 }  // namespace
 
@@ -495,18 +502,29 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     else if (pf == 2 || (pf == 0 && !fits)) form = kFormWide;
     else if (pf == 3) form = kFormStaged;
     lp->form_p = lp->form_d = form;
-    if (form == kFormWide || form == kFormStaged) atw = build_tiles(rp, kWideRows);
+    lp->form_rule = form;
+    lp->tune = pf == 0 && lp->p.autotune != 0;
+    if (form == kFormWide || form == kFormStaged || lp->tune) atw = build_tiles(rp, kWideRows);
   }
-  const bool wide_p = lp->form_p == kFormWide || lp->form_p == kFormStaged;
-  const bool wide_d = lp->form_d == kFormWide || lp->form_d == kFormStaged;
+  // wide tiles are built for the wide forms, and for the autotuner, which times both
+  const bool wide_p = lp->form_p == kFormWide || lp->form_p == kFormStaged || lp->tune;
+  const bool wide_d = lp->form_d == kFormWide || lp->form_d == kFormStaged || lp->tune;
   lp->a_ntiles_w = wide_d ? int(atw.size()) - 1 : lp->a_ntiles;
   auto grid_of = [&](int side, int form, int tiles) {
     return mixed ? occupancy_grid<float>(side, form, tiles) : occupancy_grid<double>(side, form, tiles);
   };
-  // the block partials are sized for the largest grid (the transpose's tile counts
-  // come later)
-  const int cap_p = grid_of(0, lp->form_p, 1 << 30), cap_c1 = grid_of(2, 0, 1 << 30);
-  lp->grid_d = grid_of(1, lp->form_d, lp->a_ntiles_w);
+  auto form_tiles_d = [&](int form) {
+    return (form == kFormWide || form == kFormStaged) ? lp->a_ntiles_w : lp->a_ntiles;
+  };
+  // the block partials are sized for the largest grid of the forms in play (the
+  // transpose's tile counts come later)
+  int cap_p = grid_of(0, lp->form_p, 1 << 30), cap_d = grid_of(1, lp->form_d, form_tiles_d(lp->form_d));
+  const int cap_c1 = grid_of(2, 0, 1 << 30);
+  if (lp->tune) {
+    cap_p = std::max(grid_of(0, kFormPlain, 1 << 30), grid_of(0, kFormWide, 1 << 30));
+    cap_d = std::max(grid_of(1, kFormPlain, lp->a_ntiles), grid_of(1, kFormWide, lp->a_ntiles_w));
+  }
+  lp->grid_d = grid_of(1, lp->form_d, form_tiles_d(lp->form_d));
   lp->grid_c2 = grid_of(3, 0, lp->a_ntiles);
   // persistent cooperative solve: one grid of co-resident blocks, if it fits
   {
@@ -579,7 +597,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     lp->XLR = ar.take<char>(vs * n);
     lp->YLR = ar.take<char>(vs * m);
     lp->part_p = ar.take<double>(size_t(kNP) * std::max(cap_p, 1));
-    lp->part_d = ar.take<double>(size_t(kND) * std::max(lp->grid_d, 1));
+    lp->part_d = ar.take<double>(size_t(kND) * std::max(cap_d, 1));
     lp->part_c1 = ar.take<double>(size_t(kNC1) * std::max(cap_c1, 1));
     lp->part_c2 = ar.take<double>(size_t(kNC2) * std::max(lp->grid_c2, 1));
     lp->red_c1 = ar.take<double>(kNC1);
@@ -642,7 +660,8 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
       CK(cudaMemcpyAsync(lp->t_tiles_w, ttw.data(), sizeof(int2) * ttw.size(), cudaMemcpyHostToDevice, st));
     }
     lp->t_ntiles_w = wide_p ? int(ttw.size()) - 1 : lp->t_ntiles;
-    lp->grid_p = grid_of(0, lp->form_p, lp->t_ntiles_w);
+    lp->grid_p = grid_of(0, lp->form_p,
+                         (lp->form_p == kFormWide || lp->form_p == kFormStaged) ? lp->t_ntiles_w : lp->t_ntiles);
     lp->grid_c1 = grid_of(2, 0, lp->t_ntiles);
     CK(cudaStreamSynchronize(st));  // tt and ttw leave scope
   }
@@ -726,6 +745,10 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     CK(launch_init_point<double>(lp->d64, st));
   }
   CK(cudaStreamSynchronize(st));
+  if (lp->tune) {
+    const int rc = mixed ? autotune_form<float>(lp) : autotune_form<double>(lp);
+    if (rc != SCYLLA_OK) return rc;
+  }
   return SCYLLA_OK;
 }
 
@@ -1069,6 +1092,7 @@ int scylla_lp::solve(double tol, int64_t iter_limit, int stall_checks, scylla_pd
     cudaEventElapsedTime(&ms, ev0, ev1);
     out->seconds = ms * 1e-3;
     out->launches = last_launches >= 0 ? last_launches : 3 + h.chunks * (2LL * p.n_check + 3);
+    out->kernel_form = form_p == kFormPlain ? 4 : form_p;
   }
   return SCYLLA_OK;
 }
@@ -1615,6 +1639,90 @@ static int time_kernels_impl(scylla_lp* lp, const DevLP<T>& d, int attempts, dou
   for (auto& x : ev) cudaEventDestroy(x);
   CK(e);
   for (int k = 0; k < 4; ++k) ms[k] = cnt[k] ? sum[k] / cnt[k] : 0.0;
+  return SCYLLA_OK;
+}
+
+namespace {
+
+template <typename T>
+const DevLP<T>& dev_of(const scylla_lp* lp) {
+  if constexpr (std::is_same<T, float>::value) return lp->d32;
+  else return lp->d64;
+}
+
+// The forms' grids: resident blocks per SM times the SMs, at most one warp per tile.
+template <typename T>
+void set_form(scylla_lp* lp, int form) {
+  const bool wide = form == kFormWide || form == kFormStaged;
+  lp->form_p = lp->form_d = form;
+  lp->grid_p = occupancy_grid<T>(0, form, wide ? lp->t_ntiles_w : lp->t_ntiles);
+  lp->grid_d = occupancy_grid<T>(1, form, wide ? lp->a_ntiles_w : lp->a_ntiles);
+  if (std::is_same<T, float>::value) fill_dev<float>(lp->d32, lp);
+  else fill_dev<double>(lp->d64, lp);
+}
+
+// Create-time autotuner of the per-attempt kernels' form: the 32-row tiles (plain
+// loads) and the wide tiles (up to 128 rows, streaming loads) are each timed for
+// kTuneAttempts attempts (CUDA events around separate launches, primal plus dual)
+// from the start point on the handle's own matrix.  The other form replaces the
+// L2-size rule's only when it is more than kTuneMargin faster, so that forms close in
+// time keep the rule's, reproducible choice.  The choice is kept per matrix shape
+// and precision for the process, and the handle goes back to its start point.
+constexpr int kTuneAttempts = 16;
+constexpr double kTuneMargin = 0.03;
+
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int, int>, int> g_tune_cache;
+
+template <typename T>
+int autotune_form(scylla_lp* lp) {
+  const auto key = std::make_tuple(lp->device, lp->m, lp->n, lp->nnz, int(sizeof(T)));
+  int chosen = -1;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) chosen = it->second;
+  }
+  cudaStream_t st = lp->st;
+  if (chosen < 0) {
+    // the start point's control block, restored after the timed attempts
+    CK(cudaMemcpyAsync(lp->h_ctl, lp->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const Control saved = *lp->h_ctl;
+    const int forms[2] = {kFormPlain, kFormWide};
+    for (int q = 0; q < 2; ++q) {
+      set_form<T>(lp, forms[q]);
+      double ms[4] = {0, 0, 0, 0};
+      const int rc = time_kernels_impl<T>(lp, dev_of<T>(lp), kTuneAttempts, ms);
+      if (rc != SCYLLA_OK) return rc;
+      lp->tune_ms[q] = ms[0] + ms[1];
+    }
+    const int rule = lp->form_rule == kFormWide ? 1 : 0, other = 1 - rule;
+    chosen = forms[lp->tune_ms[other] < (1.0 - kTuneMargin) * lp->tune_ms[rule] ? other : rule];
+    {
+      std::lock_guard<std::mutex> g(g_tune_mutex);
+      g_tune_cache.emplace(key, chosen);
+    }
+    *lp->h_ctl = saved;
+    CK(cudaMemcpyAsync(lp->ctl, lp->h_ctl, sizeof(Control), cudaMemcpyHostToDevice, st));
+  }
+  set_form<T>(lp, chosen);
+  if (std::is_same<T, float>::value) CK(launch_init_point<float>(lp->d32, st));
+  else CK(launch_init_point<double>(lp->d64, st));
+  CK(cudaStreamSynchronize(st));
+  return SCYLLA_OK;
+}
+
+}  // namespace
+
+extern "C" int scylla_kernel_form(const scylla_lp* lp, int32_t* form, int32_t* rule_form, double* tune_ms) {
+  if (!lp) FAIL(SCYLLA_ERR_INVALID_ARG, "null handle");
+  if (form) *form = lp->form_p == kFormPlain ? 4 : lp->form_p;
+  if (rule_form) *rule_form = lp->form_rule == kFormPlain ? 4 : lp->form_rule;
+  if (tune_ms) {
+    tune_ms[0] = lp->tune_ms[0];
+    tune_ms[1] = lp->tune_ms[1];
+  }
   return SCYLLA_OK;
 }
 

@@ -64,6 +64,9 @@ struct scylla_lp {
   void* grid_bar = nullptr;
   int p_grid = 0;  // persistent grid (0: that mode is unavailable)
   int form_p = 0, form_d = 0;  // forms of the primal / dual per-attempt kernels (kForm*)
+  int form_rule = 0;           // the form the L2-size rule gives
+  bool tune = false;           // the create-time autotuner chooses between the 32-row and wide forms
+  double tune_ms[2] = {0.0, 0.0};  // its times per attempt (primal + dual) of the 32-row and wide forms
   double *a_vals64 = nullptr, *t_vals64 = nullptr;
   float *a_vals32 = nullptr, *t_vals32 = nullptr;
   double *c_un = nullptr, *l_un = nullptr, *u_un = nullptr, *lo_un = nullptr, *hi_un = nullptr;

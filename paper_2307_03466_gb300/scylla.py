@@ -56,7 +56,7 @@ class PdhgResult(C.Structure):
                 ("accepted", C.c_int64), ("rejected", C.c_int64), ("restarts", C.c_int64),
                 ("eps_p", C.c_double), ("eps_d", C.c_double), ("eps_g", C.c_double), ("rel_kkt", C.c_double),
                 ("pobj", C.c_double), ("dobj", C.c_double), ("eta", C.c_double), ("omega", C.c_double),
-                ("seconds", C.c_double), ("launches", C.c_int64)]
+                ("seconds", C.c_double), ("launches", C.c_int64), ("kernel_form", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -115,6 +115,7 @@ _SIGS = {
     "scylla_get_trace": (C.c_int, [_P, _D, C.POINTER(C.c_int64), _D, C.POINTER(C.c_int64)]),
     "scylla_reset_state": (C.c_int, [_P]),
     "scylla_time_kernels": (C.c_int, [_P, C.c_int32, _D]),
+    "scylla_kernel_form": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _D]),
     "scylla_primal_residual_noalloc": (C.c_int, [C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "scylla_batch_create": (C.c_int, [C.c_int32, C.POINTER(Csr), C.POINTER(_D), C.POINTER(_D), C.POINTER(_D),
                                       C.POINTER(_D), C.POINTER(_D), C.POINTER(Params), _P, C.POINTER(_P)]),
@@ -410,6 +411,14 @@ class LP:
         r = RepairResult()
         _check(lib().scylla_repair(self.h, _dp(xh), float(tol), int(iter_limit), _dp(x), C.byref(r)))
         return r, x
+
+    def kernel_form(self):
+        """(form in use, the L2-size rule's form, the autotuner's ms per attempt of the
+        32-row and the wide form) -- scylla_kernel_form."""
+        f, r = C.c_int32(), C.c_int32()
+        ms = np.zeros(2)
+        _check(lib().scylla_kernel_form(self.h, C.byref(f), C.byref(r), _dp(ms)))
+        return f.value, r.value, ms
 
     def time_kernels(self, attempts: int):
         """Mean device ms of (primal, dual, check-cols, check-rows) launches."""

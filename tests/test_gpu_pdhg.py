@@ -317,3 +317,32 @@ def test_persistent_kernel_barrier_timeout_is_reported():
     r = g.pdhg_solve(1e-6, 100000)
     assert r.status == O.CONVERGED and r.launches == 2
     g.close()
+
+
+@pytest.mark.parametrize("name", ["packcover_2kx4k", "mcf_small"])
+def test_autotuned_form_is_reported_and_leaves_no_trace(name):
+    """The create-time autotuner times the 32-row and the wide-tile forms on the
+    handle's matrix and keeps one: the handle reports it (and the L2-size rule's),
+    a solve from the tuned handle is bit-identical to one from a handle created with
+    that form forced (the timed attempts leave nothing behind), and a second handle
+    of the same shape takes the kept choice without timing."""
+    import paper_2307_03466_gb300.scylla as S
+    inst = INSTANCES[name]
+    g = S.LP.from_instance(inst, S.default_params(aux_general_integers=0, autotune=1))
+    form, rule, ms = g.kernel_form()
+    assert form in (2, 4) and rule in (2, 4)
+    h = S.LP.from_instance(inst, S.default_params(aux_general_integers=0, prefetch=form))
+    assert h.kernel_form()[0] == form
+    r1 = g.pdhg_solve(1e-6, 20000)
+    r2 = h.pdhg_solve(1e-6, 20000)
+    assert r1.kernel_form == form
+    assert r1.iterations == r2.iterations and r1.status == r2.status
+    np.testing.assert_array_equal(g.primal(), h.primal())
+    np.testing.assert_array_equal(g.dual(), h.dual())
+    k = S.LP.from_instance(inst, S.default_params(aux_general_integers=0, autotune=1))
+    f2, _, ms2 = k.kernel_form()
+    assert f2 == form
+    n = S.LP.from_instance(inst, S.default_params(aux_general_integers=0, autotune=0))
+    assert n.kernel_form()[0] == rule and not np.any(n.kernel_form()[2])
+    for lp in (g, h, k, n):
+        lp.close()
