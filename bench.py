@@ -419,6 +419,9 @@ def run_ours(args):
         lp.close()
         e2e_t += time.perf_counter() - t0
         e2e_it += r.iterations
+    sharded = None
+    if dist is not None and not (args.no_batch and args.no_fanout):
+        sharded = sharded_sections(S, dist, world, args)
     dram = None
     if rank == 0 and not args.no_dram:
         dram = dram_resident(S, peak, peak_kind)
@@ -506,6 +509,7 @@ def run_ours(args):
         "l2_objective": l2,
         "propagation": prop,
         "heuristic": heur,
+        "sharded_over_ranks": sharded,
     }
     # the HBM-bound workloads' rooflines beside the headline's, and a compact summary
     # as the last key (the part of the line a truncated record keeps)
@@ -563,6 +567,52 @@ def summary_of(o):
         smm["fanout"] = {"s": r(f["mixed_fanout"]["seconds"]), "x_seq64": r(f["speedup_mixed_fanout_vs_fp64_sequential"]),
                          "hbm_frac": [r(f["roofline"]["frac"]), r(f["roofline"]["frac_other_kernel"])]}
     return smm
+
+
+def sharded_sections(S, dist, world, args):
+    """The two workloads made of independent units, split over the ranks
+    (paper_2307_03466_gb300.shard): the 256 batched LPs by cost, and the 64 fan-out
+    objectives evenly; every rank solves its share (FP32-mixed, to rel-KKT 1e-4) on
+    its own GPU, the whole job's time is the slowest rank's device time, and rank 0
+    gathers every unit's result (strong scaling: the total work is fixed)."""
+    import torch
+    from paper_2307_03466_gb300 import instances as I
+    from paper_2307_03466_gb300 import shard
+    out = {}
+    rank = dist.get_rank()
+    params = S.default_params(precision=S.PREC_MIXED, aux_general_integers=0)
+
+    def run(name, units, weights, solve):
+        seen = {}
+
+        def timed(idx):
+            r = solve(idx)
+            seen["s"] = r[0]["seconds"] if r else 0.0  # one batch or fan-out per share
+            return r
+        timed(shard.partition(weights, world)[rank])  # warm-up (graphs, autotuners)
+        res = shard.solve_sharded(weights, timed, dist)
+        t, _ = combine_ranks(dist, (seen.get("s", 0.0),), (0,), "cuda")
+        if rank == 0:
+            out[name] = {"units": units, "ranks": world, "seconds_slowest_rank": t[0],
+                         "converged": sum(1 for r in res if r["status"] == S.CONVERGED)}
+
+    if not args.no_batch:
+        insts = I.batch()
+        run("batched", len(insts), shard.batch_weights(insts), shard.batch_solver(S, insts, params, TOL, ITER_CAP))
+    if not args.no_fanout:
+        inst = I.fanout_base()
+        base = S.LP.from_instance(inst, params)
+        base.pdhg_solve(1e-3, 20000)
+        x = base.primal()
+        target = x.copy()
+        ic = inst.is_int == 1
+        target[ic] = np.floor(x[ic] + 0.5)
+        targets = I.fanout_targets(inst, target, K=64, flip_frac=0.10)
+        state = base.get_state()
+        base.close()
+        run("fanout", 64, [1.0] * 64, shard.fanout_solver(S, inst, state, targets, 1, params, TOL, ITER_CAP))
+    torch.cuda.synchronize()
+    return out if rank == 0 else None
 
 
 FAN_WORKLOAD = "fan-out: m=200k, n=500k, 5M lognormal nnz, 40% binary, K=64 targets flipping 10% of binaries"

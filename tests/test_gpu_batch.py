@@ -152,3 +152,20 @@ def test_persistent_queue_barrier_timeout_is_reported():
     res, _ = B.solve(1e-6, 100000)
     assert all(r.status == O.CONVERGED for r in res)
     B.close()
+
+
+def test_a_ranks_share_of_the_batch_solves_as_in_the_whole_batch():
+    """On several GPUs each rank solves its share of the LPs as one batch
+    (paper_2307_03466_gb300.shard): a share gives every one of its LPs exactly the
+    result the whole batch gives it (per-LP preconditioning, per-tile sums and per-LP
+    reductions in a fixed order do not depend on the other LPs)."""
+    from paper_2307_03466_gb300 import shard
+    S = lib()
+    insts = batch_instances()
+    params = S.default_params(batch_launch=1)
+    full = shard.batch_solver(S, insts, params, 1e-6, 20000)(list(range(len(insts))))
+    for share in shard.partition(shard.batch_weights(insts), 2):
+        part = shard.batch_solver(S, insts, params, 1e-6, 20000)(share)
+        for q, i in enumerate(share):
+            assert part[q]["iterations"] == full[i]["iterations"] and part[q]["status"] == full[i]["status"]
+            np.testing.assert_array_equal(part[q]["x"], full[i]["x"])

@@ -183,3 +183,28 @@ def test_second_solve_continues_from_the_first():
         g.close()
     F.close()
     base.close()
+
+
+def test_a_ranks_share_of_the_objectives_solves_as_in_the_whole_fanout():
+    """On several GPUs each rank solves its share of the K objectives as one
+    fan-out from the same warm start (paper_2307_03466_gb300.shard): in the
+    fixed-step mode, with the tile shapes forced alike, every objective of a share
+    ends exactly where it does in the whole fan-out."""
+    from paper_2307_03466_gb300 import shard
+    S, inst, base, targets, state, params = setup(K=12, adaptive_step=0, restarts=0)
+    F = S.Fanout(base, targets, round_K=1)
+    F.tune(2, 2)
+    F.solve(0.0, 150)
+    full = [F.primal(q) for q in range(targets.shape[1])]
+    F.close()
+    for share in shard.partition([1.0] * targets.shape[1], 3):
+        b2 = S.LP.from_instance(inst, params)
+        b2.set_state(*state)
+        G = S.Fanout(b2, targets[:, share], round_K=1)
+        G.tune(2, 2)
+        G.solve(0.0, 150)
+        for q, k in enumerate(share):
+            np.testing.assert_array_equal(G.primal(q), full[k])
+        G.close()
+        b2.close()
+    base.close()
