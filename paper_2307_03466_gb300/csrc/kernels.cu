@@ -2330,19 +2330,23 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value)
   T* smw = sm + w * kSmemPerWarp;
   const int nl = __ldcg(B.q_cnt + 0), na = __ldcg(B.q_cnt + 1), nt = __ldcg(B.q_cnt + 2);
   if (nl == 0) return;
-  const long long k0 = __ldcg(B.kglob);  // attempts before this launch (a previous launch wrote it)
+  // attempts before this launch (a previous launch wrote it).  Every block reads it
+  // before its first barrier and block 0 counts an attempt only after that barrier,
+  // so all blocks see the same value and make the same number of attempts.
+  const long long k0 = __ldcg(B.kglob);
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
   for (int since = 0; since < B.d.n_check && k0 + since < iter_limit; ++since) {
-    // the primal step (block 0 counts the attempt and rearms the dual counter, which
-    // nobody takes from until after the next barrier)
-    if (lead) {
-      ++*B.kglob;
-      B.q_ctr[1] = 0u;
-    }
+    // the primal step (block 0 rearms the dual counter, which nobody takes from
+    // until after the next barrier)
+    if (lead) B.q_ctr[1] = 0u;
     bq_primal<T>(B, nt, smw);
     if (!grid_sync(bar, limit_ns)) return;
-    // the dual step, whose last tile of each LP takes that LP's step decision
-    if (lead) B.q_ctr[0] = 0u;
+    // the dual step, whose last tile of each LP takes that LP's step decision; block
+    // 0 counts the attempt (read only by the check after this launch)
+    if (lead) {
+      B.q_ctr[0] = 0u;
+      ++*B.kglob;
+    }
     bq_dual<T>(B, na, smw, &sctl[w]);
     if (!grid_sync(bar, limit_ns)) return;
   }

@@ -135,6 +135,34 @@ def test_persistent_queue_and_graph_paths_identical(precision, adaptive):
         assert len({t[0] for t in out[2][1]}) > 1  # LPs left the queue at different checks
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_persistent_queue_iteration_limit_inside_a_launch(precision):
+    """An iteration limit that ends the attempts part way through a launch's n_check
+    attempts: every block of the persistent launch makes the same number of attempts
+    (the attempt counter is read before any block advances it), so no barrier waits
+    for a block that left, and the points equal those of the graph form.  Repeated,
+    because the order in which blocks start varies from launch to launch."""
+    S = lib()
+    insts = batch_instances()
+    kw = dict(precision=precision)
+    ref = {}
+    B = S.Batch(insts, S.default_params(batch_launch=1, **kw))
+    for limit in (1, 5, 63, 65, 130):
+        B.reset_state()
+        res, _ = B.solve(0.0, limit)
+        ref[limit] = [B.primal(b) for b in range(len(insts))]
+    B.close()
+    B = S.Batch(insts, S.default_params(batch_launch=2, **kw))
+    for rep in range(4):
+        for limit in (1, 5, 63, 65, 130):
+            B.reset_state()
+            res, _ = B.solve(0.0, limit)
+            assert all(r.status == O.ITER_LIMIT and r.iterations == limit for r in res), (rep, limit)
+            for b in range(len(insts)):
+                np.testing.assert_array_equal(B.primal(b), ref[limit][b], err_msg=f"{rep} {limit} {b}")
+    B.close()
+
+
 def test_persistent_queue_barrier_timeout_is_reported():
     """Every grid-barrier wait of the persistent batched kernel is bounded: with a
     limit far below any barrier's duration the first wait runs out, every block
