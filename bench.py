@@ -49,10 +49,23 @@ def parse():
     ap.add_argument("--no-l2", action="store_true", help="skip the l2-distance (diagonal QP) section")
     ap.add_argument("--no-propagate", action="store_true", help="skip the bound-propagation section")
     ap.add_argument("--no-heuristic", action="store_true", help="skip the whole-heuristic section")
+    ap.add_argument("--form", default="auto", choices=["auto", "rows32", "wide"],
+                    help="form of the single-LP per-attempt kernels of the headline and DRAM-resident solves: "
+                         "auto (the create-time autotuner), or forced (profiler captures, under which the "
+                         "autotuner's timings are distorted)")
     ap.add_argument("--only", default=None,
                     choices=["dram", "batched", "fanout", "repair", "l2", "propagation", "heuristic"],
                     help="run one section alone and print its object (for profiler captures; no bench line)")
     return ap.parse_args()
+
+
+# parameters that force the per-attempt kernels' form (--form); empty for the autotuner
+FORM_KW = {}
+
+
+def set_form(name: str):
+    FORM_KW.clear()
+    FORM_KW.update({"auto": {}, "rows32": {"prefetch": 4, "autotune": 0}, "wide": {"prefetch": 2, "autotune": 0}}[name])
 
 
 def instance(rank: int):
@@ -344,9 +357,9 @@ def run_ours(args):
     inst = instance(rank)
     stream = torch.cuda.Stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    mixed = S.LP.from_instance(inst, S.default_params(precision=S.PREC_MIXED, aux_general_integers=0),
+    mixed = S.LP.from_instance(inst, S.default_params(precision=S.PREC_MIXED, aux_general_integers=0, **FORM_KW),
                                stream=stream.cuda_stream)
-    fp64 = S.LP.from_instance(inst, S.default_params(precision=S.PREC_FP64, aux_general_integers=0),
+    fp64 = S.LP.from_instance(inst, S.default_params(precision=S.PREC_FP64, aux_general_integers=0, **FORM_KW),
                               stream=stream.cuda_stream)
     nchk = int(mixed.params.n_check)
 
@@ -413,7 +426,7 @@ def run_ours(args):
     for _ in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        lp = S.LP.from_instance(inst, S.default_params(precision=S.PREC_MIXED, aux_general_integers=0))
+        lp = S.LP.from_instance(inst, S.default_params(precision=S.PREC_MIXED, aux_general_integers=0, **FORM_KW))
         r = lp.pdhg_solve(TOL, ITER_CAP)
         lp.primal(out=x)
         lp.close()
@@ -907,7 +920,7 @@ def dram_resident(S, peak, peak_kind):
     m, n, nnz = inst.m, inst.n, inst.nnz
     out = {"workload": DRAM_WORKLOAD, "m": m, "n": n, "nnz": nnz}
     for name, prec, sv in (("mixed", S.PREC_MIXED, 4), ("fp64", S.PREC_FP64, 8)):
-        lp = S.LP.from_instance(inst, S.default_params(precision=prec, aux_general_integers=0))
+        lp = S.LP.from_instance(inst, S.default_params(precision=prec, aux_general_integers=0, **FORM_KW))
         lp.pdhg_solve(0.0, 64)  # warm-up
         lp.reset_state()
         r = lp.pdhg_solve(0.0, 640)
@@ -998,6 +1011,7 @@ def run_only(args):
 
 def main():
     args = parse()
+    set_form(args.form)
     if args.only is not None and args.impl != "reference":
         out = run_only(args)
     else:

@@ -49,6 +49,7 @@ extern "C" {
 #define SCYLLA_STALLED 2    /* rounding of x unchanged over stall_checks checks */
 #define SCYLLA_NUMERICAL 3  /* NaN/Inf met in a step-size or KKT reduction */
 #define SCYLLA_DEVICE_TIMEOUT 4 /* a bounded device-side wait ran out (the call returns SCYLLA_ERR_TIMEOUT) */
+#define SCYLLA_INFEASIBLE 5 /* a dual ray proved the LP infeasible (scylla_params.infeasibility_checks) */
 
 /* ---- run status (scylla_run_result.status) -------------------------------- */
 #define SCYLLA_FOUND 0
@@ -134,10 +135,15 @@ typedef struct {
                                    per-attempt kernels on the handle's own matrix at create and keeps the
                                    faster (the choice is kept per matrix shape for the process); 0 takes the
                                    L2-size rule (1) */
+  int32_t infeasibility_checks; /* 1: at every check of a single-LP solve, test a candidate dual ray (the
+                                   change of y since an earlier check) and end the solve SCYLLA_INFEASIBLE
+                                   when it proves the LP infeasible (scylla_get_certificate); the
+                                   persistent form (use_graph = 3) then runs as 1.  Batched solves reject
+                                   it; fan-outs do not test.  (0) */
 } scylla_params;
 
 typedef struct {
-  int32_t status;        /* SCYLLA_CONVERGED / ITER_LIMIT / STALLED / NUMERICAL */
+  int32_t status;        /* SCYLLA_CONVERGED / ITER_LIMIT / STALLED / NUMERICAL / INFEASIBLE */
   int32_t used_average;  /* 1 if the returned point is the averaged iterate */
   int64_t iterations;    /* step attempts k of this solve */
   int64_t accepted, rejected, restarts;
@@ -329,6 +335,28 @@ int scylla_check_feasible(const scylla_lp* lp, const double* x, int32_t* feasibl
  * Errors: INVALID_ARG (null, a NaN or infinite entry of y), OOM (host), CUDA (first
  * download of the host copies). */
 int scylla_farkas_gap(const scylla_lp* lp, const double* y, double* gap);
+
+/* The dual ray tested at the last check of the last solve of a handle created with
+ * scylla_params.infeasibility_checks = 1 (the solve's status is SCYLLA_INFEASIBLE when
+ * the test proved the LP infeasible).
+ * Detection (a reading of the LP solver Section 2.1 hands the relaxations to): at the
+ * check after k = q n_check attempts (q >= 2) the candidate is y_k - y_a, where y_a is
+ * the dual at the last earlier check whose q is a power of two, with every entry set
+ * to 0 whose sign would need an infinite row bound.  The device computes D of the
+ * ray (as in scylla_farkas_gap, over the rows and columns the solve iterates, in the
+ * scaled space, each (A^T y)_j a compensated sum) and S, the sum of the absolute
+ * values of D's terms; the solve ends SCYLLA_INFEASIBLE when D > 1e-9 S.  On a
+ * feasible LP D <= 0 (weak duality), and 1e-9 S is far above the rounding of D.
+ *   y: host, length m of the original rows (may be null): the ray, unscaled, zero when
+ *      no candidate was tested.  With auxiliary distance rows
+ *      (aux_general_integers) the ray may weigh them too; y holds the original rows'
+ *      entries only.  scylla_farkas_gap(lp, y) tests it on the original data.
+ *   gap, scale (may be null): D and S as the device computed them; -INFINITY and 0
+ *      when no candidate was tested, gap = -INFINITY when a term needed an infinite
+ *      bound.
+ * Errors: INVALID_ARG (null handle, or a handle created without
+ * infeasibility_checks), CUDA. */
+int scylla_get_certificate(const scylla_lp* lp, double* y, double* gap, double* scale);
 
 /* Replace the bounds of the original columns (host, length n each), keeping the
  * matrix, its preconditioning, the objective and the iterate; the auxiliary columns

@@ -26,7 +26,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["kernels.cu", "fanout.cu", "noalloc.cu", "transpose.cu", "setup.cu", "propagate.cu"]
+CU_SOURCES = ["kernels.cu", "fanout.cu", "noalloc.cu", "transpose.cu", "setup.cu", "propagate.cu", "infeas.cu"]
 CPP_SOURCES = ["lp.cpp", "fixprop.cpp", "pump.cpp", "batch.cpp", "fanout.cpp", "certify.cpp"]
 
 

@@ -204,6 +204,10 @@ int create_batch(int32_t count, const scylla_csr* A, const double* const* c, con
     set_error("batch_launch must be 0..2");
     return SCYLLA_ERR_INVALID_ARG;
   }
+  if (h->p.infeasibility_checks != 0) {
+    set_error("infeasibility_checks applies to single-LP solves; a batch does not test rays");
+    return SCYLLA_ERR_UNSUPPORTED;
+  }
   const bool mixed = h->p.precision == SCYLLA_PREC_MIXED;
   h->nlp = count;
   h->user_st = static_cast<cudaStream_t>(stream);

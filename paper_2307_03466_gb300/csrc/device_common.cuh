@@ -676,6 +676,8 @@ static __device__ void check_control_impl(Control* c, const Eval* e, const doubl
   const unsigned long long h = c->hash_accum;
   c->hash_accum = 0ULL;
   c->aty_valid = 1;
+  const bool inf_tested = c->inf_tested != 0;  // a candidate dual ray was tested at this check
+  c->inf_tested = 0;
   if (c->initial) {
     c->initial = 0;
     c->avg_w = 0.0;
@@ -705,6 +707,9 @@ static __device__ void check_control_impl(Control* c, const Eval* e, const doubl
   c->same_hash = (h == c->last_hash) ? c->same_hash + 1 : 0;
   c->last_hash = h;
   if (c->stall_checks > 0 && c->same_hash >= c->stall_checks) { finish(c, SCYLLA_STALLED, out_avg, eo); return; }
+  // the ray proves the LP infeasible (weak duality; the margin is far above the
+  // rounding of D, which is <= 0 on every feasible LP)
+  if (inf_tested && c->inf_gap > kInfeasMargin * c->inf_scale) { finish(c, SCYLLA_INFEASIBLE, out_avg, eo); return; }
   if (!c->restarts_on) return;
   const double om = c->omega;
   const double kc_cur = wk[0];

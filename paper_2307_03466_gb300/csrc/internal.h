@@ -42,6 +42,11 @@ constexpr int kNP = 1;    // primal: ||dx||^2
 constexpr int kND = 2;    // dual: ||dy||^2, dy.(A x' - A x)
 constexpr int kNC1 = 10;  // column check: 5 sums x {current, average}
 constexpr int kNC2 = 8;   // row check: 4 sums x {current, average}
+// infeasibility detection: a candidate dual ray proves the LP infeasible when
+// D > kInfeasMargin * S (D and S as in scylla_get_certificate)
+constexpr double kInfeasMargin = 1e-9;
+constexpr int kNIR = 2;  // detector row sums: sum of the row terms of D, of their absolute values
+constexpr int kNIC = 3;  // detector column sums: column terms, their absolute values, infinite terms
 
 // Device control block: every decision of the solve is taken on the device and
 // kept here, so the iteration loop needs no host round trip.
@@ -71,6 +76,11 @@ struct Control {
   // omega, 1/omega, the step-weight sum and this attempt's two step-size factors);
   // the FP64 fields eta and wsum are brought up to date from them before each check.
   float eta_f, om_f, iom_f, wsum_f, fr_f, fg_f;
+  // infeasibility detection: D and S of the candidate ray tested at this check, and
+  // whether one was tested (set by the detector kernels, read by the check decision)
+  double inf_gap, inf_scale;
+  int inf_tested;
+  unsigned int cnt_inf;
 };
 
 // Pointers of one LP, passed by value to every kernel.  T is the type of the bulk
@@ -123,6 +133,12 @@ struct DevLP {
   double* trace_steps;   // 4 doubles per attempt, or null
   double* trace_checks;  // 5 doubles per check, or null
   int trace_cap;
+  // infeasibility detection (null when off): y at the anchor check, the candidate ray
+  // (FP64, scaled), block partials (kNIR then kNIC per block of inf_grid)
+  T* inf_anchor;
+  double* inf_cand;
+  double* inf_part;
+  int inf_grid;
 };
 
 // Per-LP values of one attempt in a batched solve, written by its control kernels.
@@ -355,6 +371,13 @@ template <typename T>
 cudaError_t launch_get_x(const DevLP<T>& d, double* out, int count, cudaStream_t st);
 template <typename T>
 cudaError_t launch_get_y(const DevLP<T>& d, double* out, int count, cudaStream_t st);
+// infeasibility detection at a check (infeas.cu): the candidate ray and its row
+// terms, then its column terms and the decision's inputs in the control block
+template <typename T>
+cudaError_t launch_infeas(const DevLP<T>& d, cudaStream_t st);
+// the last tested ray, unscaled, into out (count rows)
+template <typename T>
+cudaError_t launch_get_cert(const DevLP<T>& d, double* out, int count, cudaStream_t st);
 template <typename T>
 cudaError_t launch_set_xy(const DevLP<T>& d, const double* x, const double* y, cudaStream_t st);
 template <typename T>

@@ -1358,7 +1358,10 @@ __global__ void k_solve_init(Control* c, double tol, long long iter_limit, int s
   c->copy_lr = 0;
   c->hash_accum = 0ULL;
   c->same_hash = 0;
-  c->cnt_dual = c->cnt_c2 = c->cnt_misc = 0;
+  c->cnt_dual = c->cnt_c2 = c->cnt_misc = c->cnt_inf = 0;
+  c->inf_tested = 0;
+  c->inf_gap = -INFINITY;
+  c->inf_scale = 0.0;
   derive_steps(c);
 }
 
@@ -2449,6 +2452,8 @@ static cudaError_t launch_step_kernel(void (*kernel)(DevLP<T>), int grid, const 
 template <typename T>
 cudaError_t launch_check(const DevLP<T>& d, cudaStream_t st) {
   cudaError_t e = launch_step_kernel<T>(d.q64 ? k_check_cols<T, 1> : k_check_cols<T, 0>, d.grid_c1, d, st);
+  // infeasibility detection: the ray's terms, before the row half takes the decision
+  if (e == cudaSuccess && d.inf_cand) e = launch_infeas<T>(d, st);
   if (e == cudaSuccess) e = launch_step_kernel<T>(k_check_rows<T>, d.grid_c2, d, st);
   return e;
 }

@@ -93,6 +93,7 @@ extern "C" void scylla_default_params(scylla_params* p) {
   p->distance = 1;
   p->batch_launch = 0;
   p->autotune = 1;
+  p->infeasibility_checks = 0;
 }
 
 extern "C" const char* scylla_last_error(void) { return get_error(); }
@@ -367,6 +368,8 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   if (lp->p.repair_iters < 0 || !(lp->p.repair_tol >= 0.0) || lp->p.repair_rounds < 1)
     FAIL(SCYLLA_ERR_INVALID_ARG, "need repair_iters >= 0, repair_tol >= 0 and repair_rounds >= 1");
   if (lp->p.distance != 1 && lp->p.distance != 2) FAIL(SCYLLA_ERR_INVALID_ARG, "distance must be 1 or 2");
+  if (lp->p.infeasibility_checks != 0 && lp->p.infeasibility_checks != 1)
+    FAIL(SCYLLA_ERR_INVALID_ARG, "infeasibility_checks must be 0 or 1");
   if (lp->p.precision != SCYLLA_PREC_FP64 && lp->p.precision != SCYLLA_PREC_MIXED)
     FAIL(SCYLLA_ERR_INVALID_ARG, "unknown precision");
   CK(cudaGetDevice(&lp->device));
@@ -612,6 +615,10 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     const size_t tc = size_t(lp->p.trace_capacity);
     lp->trace_steps = tc ? ar.take<double>(4 * tc) : nullptr;
     lp->trace_checks = tc ? ar.take<double>(5 * tc) : nullptr;
+    const bool inf = lp->p.infeasibility_checks != 0;
+    lp->inf_anchor = inf ? ar.take<char>(vs * size_t(std::max(m, int64_t(1)))) : nullptr;
+    lp->inf_cand = inf ? ar.take<double>(size_t(std::max(m, int64_t(1)))) : nullptr;
+    lp->inf_part = inf ? ar.take<double>(size_t(kNIR + kNIC) * size_t(lp->red_blocks)) : nullptr;
     if (pass == 0) lp->arena_bytes = ar.off + 256;
   }
   cudaStream_t st = lp->st;
@@ -731,6 +738,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     h.beta_s = lp->p.beta_sufficient; h.beta_n = lp->p.beta_necessary; h.beta_a = lp->p.beta_artificial;
     h.theta = lp->p.pw_smoothing; h.exp_red = lp->p.step_reduction_exp; h.exp_grow = lp->p.step_growth_exp;
     h.done = 1;
+    h.inf_gap = -kInf;  // no candidate ray tested yet
     *lp->h_ctl = h;
     CK(cudaMemcpyAsync(lp->ctl, lp->h_ctl, sizeof(Control), cudaMemcpyHostToDevice, st));
     // c_hat = c (already in c_un), offset 0; norms of c and of the row bounds
@@ -808,6 +816,10 @@ void fill_dev(DevLP<T>& d, scylla_lp* lp) {
   d.trace_steps = lp->trace_steps;
   d.trace_checks = lp->trace_checks;
   d.trace_cap = lp->p.trace_capacity;
+  d.inf_anchor = reinterpret_cast<T*>(lp->inf_anchor);
+  d.inf_cand = lp->inf_cand;
+  d.inf_part = lp->inf_part;
+  d.inf_grid = lp->red_blocks;
 }
 }  // namespace
 
@@ -1004,7 +1016,8 @@ static int solve_impl(scylla_lp* lp, const DevLP<T>& d, double tol, int64_t iter
   CK(cudaEventRecord(lp->ev0, st));
   CK(launch_solve_init<T>(d, tol, (long long)iter_limit, stall_checks, max_chunks, st));
   long long launches = 1;
-  if (lp->p.use_graph == 3 && lp->p_grid > 0) {
+  // the persistent kernel has no infeasibility detection: with it on, chunk graphs
+  if (lp->p.use_graph == 3 && lp->p_grid > 0 && !lp->inf_cand) {
     // one cooperative launch evaluates the start point and runs every attempt
     CK(cudaMemsetAsync(lp->grid_bar, 0, kGridBarBytes, st));
     CK(cudaMemsetAsync(lp->p_hash, 0, 2 * sizeof(unsigned long long), st));
@@ -1179,6 +1192,23 @@ int scylla_lp::fetch_y(double* host, int count) {
   else CK(launch_get_y<double>(d64, io_y, count, st));
   CK(cudaMemcpyAsync(host, io_y, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  return SCYLLA_OK;
+}
+
+extern "C" int scylla_get_certificate(const scylla_lp* lp, double* y, double* gap, double* scale) {
+  if (!lp) FAIL(SCYLLA_ERR_INVALID_ARG, "null handle");
+  if (!lp->inf_cand) FAIL(SCYLLA_ERR_INVALID_ARG, "the handle was created without infeasibility_checks");
+  scylla_lp* h = const_cast<scylla_lp*>(lp);
+  cudaStream_t st = h->st;
+  if (y && lp->m0 > 0) {
+    if (lp->p.precision == SCYLLA_PREC_MIXED) CK(launch_get_cert<float>(h->d32, h->io_y, int(lp->m0), st));
+    else CK(launch_get_cert<double>(h->d64, h->io_y, int(lp->m0), st));
+    CK(cudaMemcpyAsync(y, h->io_y, sizeof(double) * lp->m0, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (gap) *gap = h->h_ctl->inf_gap;
+  if (scale) *scale = h->h_ctl->inf_scale;
   return SCYLLA_OK;
 }
 
@@ -1506,6 +1536,7 @@ int scylla_lp::repair(const double* xhat, double tol, int64_t iter_limit, double
     q.trace_capacity = 0;
     q.repair_iters = 0;
     q.precision = SCYLLA_PREC_FP64;
+    q.infeasibility_checks = 0;  // the repair's screen proves infeasible fixings
     scylla_lp* r = new scylla_lp();
     rc = create_impl(&A, c0.data(), lo0.data(), hi0.data(), l0.data(), u0.data(), int0.data(), &q, user_st, r);
     if (rc != SCYLLA_OK) {

@@ -91,6 +91,11 @@ struct scylla_lp {
   double *part_p = nullptr, *part_d = nullptr, *part_c1 = nullptr, *part_c2 = nullptr, *red = nullptr;
   double* red_c1 = nullptr;
   double *io_x = nullptr, *io_y = nullptr;
+  // infeasibility detection (scylla_params.infeasibility_checks; null when off): the
+  // anchor dual (bulk type), the candidate ray (FP64), the detector's block partials
+  char* inf_anchor = nullptr;
+  double* inf_cand = nullptr;
+  double* inf_part = nullptr;
   double *trace_steps = nullptr, *trace_checks = nullptr;
   scylla::Control* ctl = nullptr;
   scylla::Control* h_ctl = nullptr;  // pinned host mirror

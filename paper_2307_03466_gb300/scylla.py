@@ -17,7 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "lib", "libscylla.so")
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -6
-CONVERGED, ITER_LIMIT, STALLED, NUMERICAL, DEVICE_TIMEOUT = 0, 1, 2, 3, 4
+CONVERGED, ITER_LIMIT, STALLED, NUMERICAL, DEVICE_TIMEOUT, INFEASIBLE = 0, 1, 2, 3, 4, 5
 FOUND, NOT_FOUND = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 
@@ -48,7 +48,8 @@ class Params(C.Structure):
                 ("time_limit_s", C.c_double), ("device_wait_limit_s", C.c_double), ("pdl", C.c_int32),
                 ("prefetch", C.c_int32), ("host_transpose", C.c_int32),
                 ("repair_iters", C.c_int64), ("repair_tol", C.c_double), ("repair_rounds", C.c_int32),
-                ("distance", C.c_int32), ("batch_launch", C.c_int32), ("autotune", C.c_int32)]
+                ("distance", C.c_int32), ("batch_launch", C.c_int32), ("autotune", C.c_int32),
+                ("infeasibility_checks", C.c_int32)]
 
 
 class PdhgResult(C.Structure):
@@ -105,6 +106,7 @@ _SIGS = {
                                            C.POINTER(C.c_uint8)]),
     "scylla_check_feasible": (C.c_int, [_P, _D, C.POINTER(C.c_int32)]),
     "scylla_farkas_gap": (C.c_int, [_P, _D, _D]),
+    "scylla_get_certificate": (C.c_int, [_P, _D, _D, _D]),
     "scylla_fix_and_propagate_many": (C.c_int, [_P, C.c_int32, _D, _D, _D, _D, C.POINTER(C.c_int64)]),
     "scylla_set_col_bounds": (C.c_int, [_P, _D, _D]),
     "scylla_set_row_bounds": (C.c_int, [_P, _D, _D]),
@@ -376,6 +378,15 @@ class LP:
         g = C.c_double()
         _check(lib().scylla_farkas_gap(self.h, _dp(yy) if self.m else None, C.byref(g)))
         return g.value
+
+    def certificate(self):
+        """(y, gap, scale) of scylla_get_certificate: the dual ray tested at the last
+        check of the last solve (unscaled, one entry per original row) and the D and S
+        the device computed for it."""
+        y = np.zeros(self.m)
+        g, sc = C.c_double(), C.c_double()
+        _check(lib().scylla_get_certificate(self.h, _dp(y) if self.m else None, C.byref(g), C.byref(sc)))
+        return y, g.value, sc.value
 
     def reset_state(self):
         _check(lib().scylla_reset_state(self.h))

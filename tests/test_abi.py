@@ -54,6 +54,7 @@ int main(void) {
          offsetof(scylla_params, repair_tol));
   printf("%zu %zu %zu %zu %zu\n", offsetof(scylla_params, repair_rounds), offsetof(scylla_repair_result, rel_kkt),
          offsetof(scylla_params, distance), offsetof(scylla_params, batch_launch), offsetof(scylla_params, autotune));
+  printf("%zu\n", offsetof(scylla_params, infeasibility_checks));
   return 0;
 }
 '''
@@ -69,7 +70,8 @@ int main(void) {
     assert sizes[5:] == [S.Params.fixed_step_factor.offset, S.Params.seed.offset, S.Params.time_limit_s.offset,
                          S.Params.repair_iters.offset, S.Params.repair_tol.offset,
                          S.Params.repair_rounds.offset, S.RepairResult.rel_kkt.offset, S.Params.distance.offset,
-                         S.Params.batch_launch.offset, S.Params.autotune.offset]
+                         S.Params.batch_launch.offset, S.Params.autotune.offset,
+                         S.Params.infeasibility_checks.offset]
 
 
 def test_default_params_are_the_papers(L):
@@ -80,6 +82,7 @@ def test_default_params_are_the_papers(L):
     # the continuous repair is not part of Algorithm 1: off unless asked for
     assert p.repair_iters == 0 and p.repair_tol == 1e-7 and p.repair_rounds == 8
     assert p.distance == 1  # Algorithm 1's l1 distance
+    assert p.infeasibility_checks == 0  # the detector is a reading of the LP solver's, off by default
 
 
 def _create(rowptr, cols, vals, m, n, lo=None, hi=None, l=None, u=None, c=None, ii=None):
