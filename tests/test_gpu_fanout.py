@@ -192,11 +192,16 @@ def test_a_ranks_share_of_the_objectives_solves_as_in_the_whole_fanout():
     ends exactly where it does in the whole fan-out."""
     from paper_2307_03466_gb300 import shard
     S, inst, base, targets, state, params = setup(K=12, adaptive_step=0, restarts=0)
-    F = S.Fanout(base, targets, round_K=1)
+    # the whole fan-out starts, like every share, from the warm start set through
+    # set_state (the unscaled state scaled again, as a rank receives it)
+    b1 = S.LP.from_instance(inst, params)
+    b1.set_state(*state)
+    F = S.Fanout(b1, targets, round_K=1)
     F.tune(2, 2)
     F.solve(0.0, 150)
     full = [F.primal(q) for q in range(targets.shape[1])]
     F.close()
+    b1.close()
     for share in shard.partition([1.0] * targets.shape[1], 3):
         b2 = S.LP.from_instance(inst, params)
         b2.set_state(*state)
