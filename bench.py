@@ -543,16 +543,19 @@ FORM_NAMES = {4: "32-row tiles", 1: "32-row tiles, first tile prefetched", 2: "w
               3: "wide tiles staged in shared memory"}
 
 
+def form_info(lp):
+    """The forms of the two per-attempt kernels a handle runs, the L2-size rule's, and
+    the create-time autotuner's ms per launch of each kernel in the two forms."""
+    (fp, fd), r, ms = lp.kernel_form()
+    return {"form": {"primal": FORM_NAMES.get(fp, fp), "dual": FORM_NAMES.get(fd, fd)},
+            "l2_rule_form": FORM_NAMES.get(r, r),
+            "tuned_ms_per_launch": {"primal": {"32-row": ms[0], "wide": ms[2]},
+                                    "dual": {"32-row": ms[1], "wide": ms[3]}}}
+
+
 def autotune_info(*lps):
-    """The per-attempt kernels' form each handle runs, the L2-size rule's, and the
-    create-time autotuner's times per attempt of the two forms it compares."""
-    out = {}
-    for lp in lps:
-        f, r, ms = lp.kernel_form()
-        key = "mixed" if lp.params.precision == 1 else "fp64"
-        out[key] = {"form": FORM_NAMES.get(f, f), "l2_rule_form": FORM_NAMES.get(r, r),
-                    "tuned_ms_per_attempt": {"32-row": ms[0], "wide": ms[1]}}
-    return out
+    """form_info of each precision's handle."""
+    return {("mixed" if lp.params.precision == 1 else "fp64"): form_info(lp) for lp in lps}
 
 
 def summary_of(o):
@@ -933,10 +936,8 @@ def dram_resident(S, peak, peak_kind):
         gp, gd = bp / (ms[0] * 1e6), bd / (ms[1] * 1e6)
         kname, kb, kms = (f"k_dual<{'float' if sv == 4 else 'double'}>", bd, ms[1]) if ms[1] >= ms[0] else \
             (f"k_primal<{'float' if sv == 4 else 'double'}>", bp, ms[0])
-        f, rule, tms = lp.kernel_form()
         out[name] = {"iter_per_s": r.iterations / r.seconds, "attempts": r.iterations, "rel_kkt_after": r.rel_kkt,
-                     "kernel_form": FORM_NAMES.get(f, f), "l2_rule_form": FORM_NAMES.get(rule, rule),
-                     "tuned_ms_per_attempt": {"32-row": tms[0], "wide": tms[1]},
+                     **form_info(lp),
                      "time_to_kkt_1e4": {"converged": rt.status == S.CONVERGED, "ms": 1e3 * rt.seconds,
                                          "attempts": int(rt.iterations), "cap": DRAM_TTK_CAP,
                                          "eps_p": rt.eps_p, "eps_d": rt.eps_d, "eps_g": rt.eps_g,

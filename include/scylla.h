@@ -133,13 +133,15 @@ typedef struct {
                                    queue compacted at every check (0) */
   int32_t autotune;             /* with prefetch = 0: 1 times the 32-row and the wide-tile forms of the
                                    per-attempt kernels on the handle's own matrix at create and keeps the
-                                   faster (the choice is kept per matrix shape for the process); 0 takes the
-                                   L2-size rule (1) */
+                                   faster for each of the two kernels (the choice is kept per matrix shape
+                                   for the process); 0 takes the L2-size rule (1) */
   int32_t infeasibility_checks; /* 1: at every check of a single-LP solve, test a candidate dual ray (the
                                    change of y since an earlier check) and end the solve SCYLLA_INFEASIBLE
                                    when it proves the LP infeasible (scylla_get_certificate); the
                                    persistent form (use_graph = 3) then runs as 1.  Batched solves reject
                                    it; fan-outs do not test.  (0) */
+  int32_t dual_form;            /* with prefetch = 1..4: the dual per-attempt kernel's form, numbered as
+                                   prefetch, when it differs from the primal's; 0 the same (0) */
 } scylla_params;
 
 typedef struct {
@@ -152,9 +154,10 @@ typedef struct {
   double eta, omega;     /* step size and primal weight after the solve */
   double seconds;        /* device time of the solve (CUDA events) */
   int64_t launches;      /* kernel launches issued, including ones that returned early */
-  int32_t kernel_form;   /* form of the per-attempt kernels (scylla_params.prefetch's numbering: 4 32-row
-                            tiles, 1 32-row with prefetch, 2 wide tiles, 3 staged wide tiles); 0 for the
-                            batched and fan-out solves */
+  int32_t kernel_form;   /* form of the primal per-attempt kernel (scylla_params.prefetch's numbering: 4
+                            32-row tiles, 1 32-row with prefetch, 2 wide tiles, 3 staged wide tiles); 0 for
+                            the batched and fan-out solves */
+  int32_t kernel_form_dual; /* form of the dual per-attempt kernel, numbered alike */
 } scylla_pdhg_result;
 
 typedef struct {
@@ -274,13 +277,15 @@ int scylla_reset_state(scylla_lp* lp);
  * moves on by those attempts. */
 int scylla_time_kernels(scylla_lp* lp, int32_t attempts, double* ms);
 
-/* Form of the per-attempt kernels in use (numbered as scylla_params.prefetch: 4
- * 32-row tiles, 1 32-row with prefetch, 2 wide tiles, 3 staged), the form the
- * L2-size rule gives, and the create-time autotuner's times per attempt (primal plus
- * dual, ms) of the 32-row and the wide form (0 when it did not time them: a forced
+/* Forms of the primal and the dual per-attempt kernels in use (numbered as
+ * scylla_params.prefetch: 4 32-row tiles, 1 32-row with prefetch, 2 wide tiles, 3
+ * staged), the form the L2-size rule gives both, and the create-time autotuner's
+ * device times per launch in ms, tune_ms[0..3] = primal and dual of the 32-row
+ * form, primal and dual of the wide form (0 when it did not time them: a forced
  * form, autotune = 0, or the choice kept from an earlier handle of the same shape).
- * Any output may be NULL. */
-int scylla_kernel_form(const scylla_lp* lp, int32_t* form, int32_t* rule_form, double* tune_ms);
+ * The autotuner picks each kernel's form on its own.  Any output may be NULL. */
+int scylla_kernel_form(const scylla_lp* lp, int32_t* form, int32_t* form_dual, int32_t* rule_form,
+                       double* tune_ms);
 
 /* Diagonal scaling A~ = diag(R) A diag(C) found at create: host, R length m_total,
  * C length n_total. */

@@ -128,8 +128,27 @@ __device__ __forceinline__ bool spmv_tiles(const int2* __restrict__ tiles, int n
   // row of slot j of this lane in a multi-row tile of nr rows (nr when none): row
   // lane / L when rows are split over L lanes, else rows lane, lane + 32, ...
   auto slot_row = [&](int nr, int L, int j) { return L > 1 ? (j == 0 ? lane / L : nr) : lane + 32 * j; };
+  // wide tiles (several per warp): the bounds of the warp's next tile are loaded one
+  // tile ahead, so that a tile's row pointers and vector loads wait for one latency,
+  // not two.  32-row tiles serve L2-resident problems with about one tile per warp.
+  constexpr bool kAhead = RPL > 1;
+  int2 nta = make_int2(0, 0), ntb = make_int2(0, 0);
+  auto load_bounds = [&](int t) {
+    if (t < wt.end) {
+      nta = __ldg(tiles + t);
+      ntb = __ldg(tiles + t + 1);
+    }
+  };
   auto fetch = [&](int t) {
-    const int2 ta = __ldg(tiles + t), tb = __ldg(tiles + t + 1);
+    int2 ta, tb;
+    if (kAhead) {
+      ta = nta;
+      tb = ntb;
+      load_bounds(t + wt.step);
+    } else {
+      ta = __ldg(tiles + t);
+      tb = __ldg(tiles + t + 1);
+    }
     r0 = ta.x;
     r1 = tb.x;
     p0 = ta.y;
@@ -157,6 +176,7 @@ __device__ __forceinline__ bool spmv_tiles(const int2* __restrict__ tiles, int n
       }
     }
   };
+  if (kAhead) load_bounds(wt.first);
   if (PF && wt.first < wt.end) fetch(wt.first);
   if (!pro()) return false;
   for (int t = wt.first; t < wt.end; t += wt.step) {

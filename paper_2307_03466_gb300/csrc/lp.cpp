@@ -94,6 +94,7 @@ extern "C" void scylla_default_params(scylla_params* p) {
   p->batch_launch = 0;
   p->autotune = 1;
   p->infeasibility_checks = 0;
+  p->dual_form = 0;
 }
 
 extern "C" const char* scylla_last_error(void) { return get_error(); }
@@ -370,6 +371,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   if (lp->p.distance != 1 && lp->p.distance != 2) FAIL(SCYLLA_ERR_INVALID_ARG, "distance must be 1 or 2");
   if (lp->p.infeasibility_checks != 0 && lp->p.infeasibility_checks != 1)
     FAIL(SCYLLA_ERR_INVALID_ARG, "infeasibility_checks must be 0 or 1");
+  if (lp->p.dual_form < 0 || lp->p.dual_form > 4) FAIL(SCYLLA_ERR_INVALID_ARG, "dual_form must be 0..4");
   if (lp->p.precision != SCYLLA_PREC_FP64 && lp->p.precision != SCYLLA_PREC_MIXED)
     FAIL(SCYLLA_ERR_INVALID_ARG, "unknown precision");
   CK(cudaGetDevice(&lp->device));
@@ -501,13 +503,17 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     const bool fits = bytes <= 0.5 * double(l2);
     const int pf = lp->p.prefetch;
     int form = kFormPlain;
-    if (pf == 1) form = kFormPrefetch;
-    else if (pf == 2 || (pf == 0 && !fits)) form = kFormWide;
-    else if (pf == 3) form = kFormStaged;
-    lp->form_p = lp->form_d = form;
-    lp->form_rule = form;
+    auto forced = [](int v) {
+      return v == 1 ? kFormPrefetch : v == 2 ? kFormWide : v == 3 ? kFormStaged : kFormPlain;
+    };
+    if (pf == 0) form = fits ? kFormPlain : kFormWide;
+    else form = forced(pf);
+    lp->form_p = form;
+    lp->form_d = (pf != 0 && lp->p.dual_form != 0) ? forced(lp->p.dual_form) : form;
+    lp->form_rule = pf == 0 ? form : (fits ? kFormPlain : kFormWide);
     lp->tune = pf == 0 && lp->p.autotune != 0;
-    if (form == kFormWide || form == kFormStaged || lp->tune) atw = build_tiles(rp, kWideRows);
+    auto wide_form = [](int f) { return f == kFormWide || f == kFormStaged; };
+    if (wide_form(lp->form_p) || wide_form(lp->form_d) || lp->tune) atw = build_tiles(rp, kWideRows);
   }
   // wide tiles are built for the wide forms, and for the autotuner, which times both
   const bool wide_p = lp->form_p == kFormWide || lp->form_p == kFormStaged || lp->tune;
@@ -1106,6 +1112,7 @@ int scylla_lp::solve(double tol, int64_t iter_limit, int stall_checks, scylla_pd
     out->seconds = ms * 1e-3;
     out->launches = last_launches >= 0 ? last_launches : 3 + h.chunks * (2LL * p.n_check + 3);
     out->kernel_form = form_p == kFormPlain ? 4 : form_p;
+    out->kernel_form_dual = form_d == kFormPlain ? 4 : form_d;
   }
   return SCYLLA_OK;
 }
@@ -1683,53 +1690,59 @@ const DevLP<T>& dev_of(const scylla_lp* lp) {
 
 // The forms' grids: resident blocks per SM times the SMs, at most one warp per tile.
 template <typename T>
-void set_form(scylla_lp* lp, int form) {
-  const bool wide = form == kFormWide || form == kFormStaged;
-  lp->form_p = lp->form_d = form;
-  lp->grid_p = occupancy_grid<T>(0, form, wide ? lp->t_ntiles_w : lp->t_ntiles);
-  lp->grid_d = occupancy_grid<T>(1, form, wide ? lp->a_ntiles_w : lp->a_ntiles);
+void set_forms(scylla_lp* lp, int form_p, int form_d) {
+  const bool wp = form_p == kFormWide || form_p == kFormStaged, wd = form_d == kFormWide || form_d == kFormStaged;
+  lp->form_p = form_p;
+  lp->form_d = form_d;
+  lp->grid_p = occupancy_grid<T>(0, form_p, wp ? lp->t_ntiles_w : lp->t_ntiles);
+  lp->grid_d = occupancy_grid<T>(1, form_d, wd ? lp->a_ntiles_w : lp->a_ntiles);
   if (std::is_same<T, float>::value) fill_dev<float>(lp->d32, lp);
   else fill_dev<double>(lp->d64, lp);
 }
 
-// Create-time autotuner of the per-attempt kernels' form: the 32-row tiles (plain
+// Create-time autotuner of the per-attempt kernels' forms: the 32-row tiles (plain
 // loads) and the wide tiles (up to 128 rows, streaming loads) are each timed for
-// kTuneAttempts attempts (CUDA events around separate launches, primal plus dual)
-// from the start point on the handle's own matrix.  The other form replaces the
-// L2-size rule's only when it is more than kTuneMargin faster, so that forms close in
-// time keep the rule's, reproducible choice.  The choice is kept per matrix shape
-// and precision for the process, and the handle goes back to its start point.
+// kTuneAttempts attempts (CUDA events around separate launches) from the start point
+// on the handle's own matrix, and each of the two kernels takes its own form.  The
+// other form replaces the L2-size rule's only when it is more than kTuneMargin
+// faster, so that forms close in time keep the rule's, reproducible choice.  The
+// choice is kept per matrix shape and precision for the process, and the handle goes
+// back to its start point.
 constexpr int kTuneAttempts = 16;
 constexpr double kTuneMargin = 0.03;
 
 std::mutex g_tune_mutex;
-std::map<std::tuple<int, int, int, int, int>, int> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
 
 template <typename T>
 int autotune_form(scylla_lp* lp) {
   const auto key = std::make_tuple(lp->device, lp->m, lp->n, lp->nnz, int(sizeof(T)));
-  int chosen = -1;
+  std::pair<int, int> chosen(-1, -1);
   {
     std::lock_guard<std::mutex> g(g_tune_mutex);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) chosen = it->second;
   }
   cudaStream_t st = lp->st;
-  if (chosen < 0) {
+  if (chosen.first < 0) {
     // the start point's control block, restored after the timed attempts
     CK(cudaMemcpyAsync(lp->h_ctl, lp->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     const Control saved = *lp->h_ctl;
     const int forms[2] = {kFormPlain, kFormWide};
     for (int q = 0; q < 2; ++q) {
-      set_form<T>(lp, forms[q]);
+      set_forms<T>(lp, forms[q], forms[q]);
       double ms[4] = {0, 0, 0, 0};
       const int rc = time_kernels_impl<T>(lp, dev_of<T>(lp), kTuneAttempts, ms);
       if (rc != SCYLLA_OK) return rc;
-      lp->tune_ms[q] = ms[0] + ms[1];
+      lp->tune_ms[2 * q] = ms[0];
+      lp->tune_ms[2 * q + 1] = ms[1];
     }
     const int rule = lp->form_rule == kFormWide ? 1 : 0, other = 1 - rule;
-    chosen = forms[lp->tune_ms[other] < (1.0 - kTuneMargin) * lp->tune_ms[rule] ? other : rule];
+    auto pick = [&](int side) {
+      return forms[lp->tune_ms[2 * other + side] < (1.0 - kTuneMargin) * lp->tune_ms[2 * rule + side] ? other : rule];
+    };
+    chosen = std::make_pair(pick(0), pick(1));
     {
       std::lock_guard<std::mutex> g(g_tune_mutex);
       g_tune_cache.emplace(key, chosen);
@@ -1737,7 +1750,7 @@ int autotune_form(scylla_lp* lp) {
     *lp->h_ctl = saved;
     CK(cudaMemcpyAsync(lp->ctl, lp->h_ctl, sizeof(Control), cudaMemcpyHostToDevice, st));
   }
-  set_form<T>(lp, chosen);
+  set_forms<T>(lp, chosen.first, chosen.second);
   if (std::is_same<T, float>::value) CK(launch_init_point<float>(lp->d32, st));
   else CK(launch_init_point<double>(lp->d64, st));
   CK(cudaStreamSynchronize(st));
@@ -1746,14 +1759,14 @@ int autotune_form(scylla_lp* lp) {
 
 }  // namespace
 
-extern "C" int scylla_kernel_form(const scylla_lp* lp, int32_t* form, int32_t* rule_form, double* tune_ms) {
+extern "C" int scylla_kernel_form(const scylla_lp* lp, int32_t* form, int32_t* form_dual, int32_t* rule_form,
+                                  double* tune_ms) {
   if (!lp) FAIL(SCYLLA_ERR_INVALID_ARG, "null handle");
   if (form) *form = lp->form_p == kFormPlain ? 4 : lp->form_p;
+  if (form_dual) *form_dual = lp->form_d == kFormPlain ? 4 : lp->form_d;
   if (rule_form) *rule_form = lp->form_rule == kFormPlain ? 4 : lp->form_rule;
-  if (tune_ms) {
-    tune_ms[0] = lp->tune_ms[0];
-    tune_ms[1] = lp->tune_ms[1];
-  }
+  if (tune_ms)
+    for (int q = 0; q < 4; ++q) tune_ms[q] = lp->tune_ms[q];
   return SCYLLA_OK;
 }
 

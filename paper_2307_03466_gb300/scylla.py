@@ -49,7 +49,7 @@ class Params(C.Structure):
                 ("prefetch", C.c_int32), ("host_transpose", C.c_int32),
                 ("repair_iters", C.c_int64), ("repair_tol", C.c_double), ("repair_rounds", C.c_int32),
                 ("distance", C.c_int32), ("batch_launch", C.c_int32), ("autotune", C.c_int32),
-                ("infeasibility_checks", C.c_int32)]
+                ("infeasibility_checks", C.c_int32), ("dual_form", C.c_int32)]
 
 
 class PdhgResult(C.Structure):
@@ -57,7 +57,8 @@ class PdhgResult(C.Structure):
                 ("accepted", C.c_int64), ("rejected", C.c_int64), ("restarts", C.c_int64),
                 ("eps_p", C.c_double), ("eps_d", C.c_double), ("eps_g", C.c_double), ("rel_kkt", C.c_double),
                 ("pobj", C.c_double), ("dobj", C.c_double), ("eta", C.c_double), ("omega", C.c_double),
-                ("seconds", C.c_double), ("launches", C.c_int64), ("kernel_form", C.c_int32)]
+                ("seconds", C.c_double), ("launches", C.c_int64), ("kernel_form", C.c_int32),
+                ("kernel_form_dual", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -117,7 +118,7 @@ _SIGS = {
     "scylla_get_trace": (C.c_int, [_P, _D, C.POINTER(C.c_int64), _D, C.POINTER(C.c_int64)]),
     "scylla_reset_state": (C.c_int, [_P]),
     "scylla_time_kernels": (C.c_int, [_P, C.c_int32, _D]),
-    "scylla_kernel_form": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _D]),
+    "scylla_kernel_form": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32), _D]),
     "scylla_primal_residual_noalloc": (C.c_int, [C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "scylla_batch_create": (C.c_int, [C.c_int32, C.POINTER(Csr), C.POINTER(_D), C.POINTER(_D), C.POINTER(_D),
                                       C.POINTER(_D), C.POINTER(_D), C.POINTER(Params), _P, C.POINTER(_P)]),
@@ -424,12 +425,13 @@ class LP:
         return r, x
 
     def kernel_form(self):
-        """(form in use, the L2-size rule's form, the autotuner's ms per attempt of the
-        32-row and the wide form) -- scylla_kernel_form."""
-        f, r = C.c_int32(), C.c_int32()
-        ms = np.zeros(2)
-        _check(lib().scylla_kernel_form(self.h, C.byref(f), C.byref(r), _dp(ms)))
-        return f.value, r.value, ms
+        """((primal form, dual form) in use, the L2-size rule's form, the autotuner's ms
+        per launch: primal and dual of the 32-row form, then of the wide form) --
+        scylla_kernel_form."""
+        f, fd, r = C.c_int32(), C.c_int32(), C.c_int32()
+        ms = np.zeros(4)
+        _check(lib().scylla_kernel_form(self.h, C.byref(f), C.byref(fd), C.byref(r), _dp(ms)))
+        return (f.value, fd.value), r.value, ms
 
     def time_kernels(self, attempts: int):
         """Mean device ms of (primal, dual, check-cols, check-rows) launches."""

@@ -54,7 +54,8 @@ int main(void) {
          offsetof(scylla_params, repair_tol));
   printf("%zu %zu %zu %zu %zu\n", offsetof(scylla_params, repair_rounds), offsetof(scylla_repair_result, rel_kkt),
          offsetof(scylla_params, distance), offsetof(scylla_params, batch_launch), offsetof(scylla_params, autotune));
-  printf("%zu\n", offsetof(scylla_params, infeasibility_checks));
+  printf("%zu %zu %zu\n", offsetof(scylla_params, infeasibility_checks), offsetof(scylla_params, dual_form),
+         offsetof(scylla_pdhg_result, kernel_form_dual));
   return 0;
 }
 '''
@@ -71,7 +72,8 @@ int main(void) {
                          S.Params.repair_iters.offset, S.Params.repair_tol.offset,
                          S.Params.repair_rounds.offset, S.RepairResult.rel_kkt.offset, S.Params.distance.offset,
                          S.Params.batch_launch.offset, S.Params.autotune.offset,
-                         S.Params.infeasibility_checks.offset]
+                         S.Params.infeasibility_checks.offset, S.Params.dual_form.offset,
+                         S.PdhgResult.kernel_form_dual.offset]
 
 
 def test_default_params_are_the_papers(L):

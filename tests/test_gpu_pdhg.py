@@ -193,6 +193,21 @@ def test_wide_and_staged_forms_match_oracle(name):
         g.close()
 
 
+@pytest.mark.parametrize("name", ["setcover_200x500", "long_rows", "mcf_small"])
+@pytest.mark.parametrize("forms", [(2, 4), (4, 2)])
+def test_primal_and_dual_in_different_forms_match_oracle(name, forms):
+    """Each per-attempt kernel in its own form (the autotuner picks them separately;
+    dual_form forces it): the primal's block partials feed the dual's step decision
+    whatever the two grids, and fixed-step FP64 iterates equal the oracle's (1e-9)."""
+    inst = INSTANCES[name]
+    g, o = pair(inst, prefetch=forms[0], dual_form=forms[1], adaptive_step=False, restarts=False)
+    r = g.pdhg_solve(0.0, 300)
+    assert (r.kernel_form, r.kernel_form_dual) == forms
+    o.solve(0.0, 300)
+    assert rel_err(g.primal(), o.primal()) <= TOL and rel_err(g.dual(), o.dual()) <= TOL
+    g.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_wide_form_converges_like_prefetch_form(precision):
     """Adaptive solves of the wide-tile form reach the tolerance with the prefetch
@@ -321,28 +336,36 @@ def test_persistent_kernel_barrier_timeout_is_reported():
 
 @pytest.mark.parametrize("name", ["packcover_2kx4k", "mcf_small"])
 def test_autotuned_form_is_reported_and_leaves_no_trace(name):
-    """The create-time autotuner times the 32-row and the wide-tile forms on the
-    handle's matrix and keeps one: the handle reports it (and the L2-size rule's),
-    a solve from the tuned handle is bit-identical to one from a handle created with
-    that form forced (the timed attempts leave nothing behind), and a second handle
-    of the same shape takes the kept choice without timing."""
+    """The create-time autotuner times the 32-row and the wide-tile forms of both
+    per-attempt kernels on the handle's matrix and keeps one form for each: the
+    handle reports them (and the L2-size rule's), a solve from the tuned handle is
+    bit-identical to one from a handle created with those forms forced (the timed
+    attempts leave nothing behind), and a second handle of the same shape takes the
+    kept choice without timing."""
     import paper_2307_03466_gb300.scylla as S
     inst = INSTANCES[name]
     g = S.LP.from_instance(inst, S.default_params(aux_general_integers=0, autotune=1))
-    form, rule, ms = g.kernel_form()
-    assert form in (2, 4) and rule in (2, 4)
-    h = S.LP.from_instance(inst, S.default_params(aux_general_integers=0, prefetch=form))
-    assert h.kernel_form()[0] == form
+    (fp, fd), rule, ms = g.kernel_form()
+    assert fp in (2, 4) and fd in (2, 4) and rule in (2, 4)
+    h = S.LP.from_instance(inst, S.default_params(aux_general_integers=0, prefetch=fp, dual_form=fd))
+    assert h.kernel_form()[0] == (fp, fd)
     r1 = g.pdhg_solve(1e-6, 20000)
     r2 = h.pdhg_solve(1e-6, 20000)
-    assert r1.kernel_form == form
+    assert (r1.kernel_form, r1.kernel_form_dual) == (fp, fd)
     assert r1.iterations == r2.iterations and r1.status == r2.status
     np.testing.assert_array_equal(g.primal(), h.primal())
     np.testing.assert_array_equal(g.dual(), h.dual())
+    # each kernel's form is the faster of its two timings, unless within the margin of
+    # the rule's
+    for side, f in ((0, fp), (1, fd)):
+        t_plain, t_wide = ms[side], ms[2 + side]
+        assert t_plain > 0 and t_wide > 0
+        r_t, o_t = (t_wide, t_plain) if rule == 2 else (t_plain, t_wide)
+        assert (f == rule) == (o_t >= 0.97 * r_t)
     k = S.LP.from_instance(inst, S.default_params(aux_general_integers=0, autotune=1))
     f2, _, ms2 = k.kernel_form()
-    assert f2 == form
+    assert f2 == (fp, fd)
     n = S.LP.from_instance(inst, S.default_params(aux_general_integers=0, autotune=0))
-    assert n.kernel_form()[0] == rule and not np.any(n.kernel_form()[2])
+    assert n.kernel_form()[0] == (rule, rule) and not np.any(n.kernel_form()[2])
     for lp in (g, h, k, n):
         lp.close()
