@@ -49,10 +49,11 @@ def parse():
     ap.add_argument("--no-l2", action="store_true", help="skip the l2-distance (diagonal QP) section")
     ap.add_argument("--no-propagate", action="store_true", help="skip the bound-propagation section")
     ap.add_argument("--no-heuristic", action="store_true", help="skip the whole-heuristic section")
-    ap.add_argument("--form", default="auto", choices=["auto", "rows32", "wide"],
-                    help="form of the single-LP per-attempt kernels of the headline and DRAM-resident solves: "
-                         "auto (the create-time autotuner), or forced (profiler captures, under which the "
-                         "autotuner's timings are distorted)")
+    ap.add_argument("--form", default="auto",
+                    choices=["auto", "rows32", "wide", "wide,rows32", "rows32,wide"],
+                    help="forms of the single-LP per-attempt kernels (primal[,dual]) of the headline and "
+                         "DRAM-resident solves: auto (the create-time autotuner), or forced (profiler captures, "
+                         "under which the autotuner's timings are distorted)")
     ap.add_argument("--only", default=None,
                     choices=["dram", "batched", "fanout", "repair", "l2", "propagation", "heuristic"],
                     help="run one section alone and print its object (for profiler captures; no bench line)")
@@ -65,7 +66,11 @@ FORM_KW = {}
 
 def set_form(name: str):
     FORM_KW.clear()
-    FORM_KW.update({"auto": {}, "rows32": {"prefetch": 4, "autotune": 0}, "wide": {"prefetch": 2, "autotune": 0}}[name])
+    if name == "auto":
+        return
+    code = {"rows32": 4, "wide": 2}
+    parts = name.split(",")
+    FORM_KW.update({"prefetch": code[parts[0]], "dual_form": code[parts[-1]], "autotune": 0})
 
 
 def instance(rank: int):
