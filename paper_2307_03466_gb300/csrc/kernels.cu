@@ -1584,11 +1584,10 @@ __global__ void k_cnorm_cols(DevObjective o, double offset_base) {
 // products into the warp's skewed shared buffer, then each lane sums its row in CSR
 // order and hands it to the epilogue.
 template <int NV, typename Acc, typename V, typename Gather, typename Epi>
-__device__ __forceinline__ void batch_tile(int t, const int2* __restrict__ tiles, const int* __restrict__ rowptr,
-                                           const int* __restrict__ cols, const V* __restrict__ vals, Gather& gat,
-                                           Epi& epi, Acc* __restrict__ sm) {
+__device__ __forceinline__ void batch_tile_at(int2 ta, int2 tb, const int* __restrict__ rowptr,
+                                              const int* __restrict__ cols, const V* __restrict__ vals, Gather& gat,
+                                              Epi& epi, Acc* __restrict__ sm) {
   const int lane = threadIdx.x & 31;
-  const int2 ta = __ldg(tiles + t), tb = __ldg(tiles + t + 1);
   const int r0 = ta.x, r1 = tb.x, p0 = ta.y, p1 = tb.y;
   const int base = p0 & ~(kVec - 1);
   if (r1 - r0 == 1 && p1 - p0 > kTileNnz) {
@@ -1647,18 +1646,41 @@ __device__ __forceinline__ void batch_tile(int t, const int2* __restrict__ tiles
   }
 }
 
+// tile t of a batch: its bounds, then batch_tile_at
+template <int NV, typename Acc, typename V, typename Gather, typename Epi>
+__device__ __forceinline__ void batch_tile(int t, const int2* __restrict__ tiles, const int* __restrict__ rowptr,
+                                           const int* __restrict__ cols, const V* __restrict__ vals, Gather& gat,
+                                           Epi& epi, Acc* __restrict__ sm) {
+  batch_tile_at<NV, Acc, V>(__ldg(tiles + t), __ldg(tiles + t + 1), rowptr, cols, vals, gat, epi, sm);
+}
+
 // warp-tile loop of the batched kernels over a static deal of the tiles:
 // begin(lp, t) decides per tile (uniformly over the warp) whether the tile's LP
-// takes part, end(t) flushes the tile's sums
+// takes part, end(t) flushes the tile's sums.  The LP index and the bounds of the
+// warp's next tile are loaded together, one tile ahead, so that neither waits on
+// the other nor on the current tile's work.
 template <int NV, typename Acc, typename V, typename Gather, typename Epi>
 __device__ __forceinline__ void spmv_tiles_batch(const int2* __restrict__ tiles, const int* __restrict__ tile_lp,
                                                  int ntiles, const int* __restrict__ rowptr,
                                                  const int* __restrict__ cols, const V* __restrict__ vals,
                                                  Gather& gat, Epi& epi, Acc* __restrict__ sm) {
   const WarpTiles wt = warp_tiles(ntiles);
+  int lp_n = 0;
+  int2 ta_n = make_int2(0, 0), tb_n = make_int2(0, 0);
+  auto ahead = [&](int t) {
+    if (t < wt.end) {
+      lp_n = __ldg(tile_lp + t);
+      ta_n = __ldg(tiles + t);
+      tb_n = __ldg(tiles + t + 1);
+    }
+  };
+  ahead(wt.first);
   for (int t = wt.first; t < wt.end; t += wt.step) {
-    if (!epi.begin(__ldg(tile_lp + t), t)) continue;
-    batch_tile<NV, Acc, V>(t, tiles, rowptr, cols, vals, gat, epi, sm);
+    const int lp = lp_n;
+    const int2 ta = ta_n, tb = tb_n;
+    ahead(t + wt.step);
+    if (!epi.begin(lp, t)) continue;
+    batch_tile_at<NV, Acc, V>(ta, tb, rowptr, cols, vals, gat, epi, sm);
     epi.end(t);
   }
 }

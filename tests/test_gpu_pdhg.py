@@ -356,12 +356,14 @@ def test_autotuned_form_is_reported_and_leaves_no_trace(name):
     np.testing.assert_array_equal(g.primal(), h.primal())
     np.testing.assert_array_equal(g.dual(), h.dual())
     # each kernel's form is the faster of its two timings, unless within the margin of
-    # the rule's
-    for side, f in ((0, fp), (1, fd)):
-        t_plain, t_wide = ms[side], ms[2 + side]
-        assert t_plain > 0 and t_wide > 0
-        r_t, o_t = (t_wide, t_plain) if rule == 2 else (t_plain, t_wide)
-        assert (f == rule) == (o_t >= 0.97 * r_t)
+    # the rule's (when this handle timed them: an earlier handle of the same shape in
+    # this process leaves the kept choice and no timings)
+    if np.any(ms):
+        for side, f in ((0, fp), (1, fd)):
+            t_plain, t_wide = ms[side], ms[2 + side]
+            assert t_plain > 0 and t_wide > 0
+            r_t, o_t = (t_wide, t_plain) if rule == 2 else (t_plain, t_wide)
+            assert (f == rule) == (o_t >= 0.97 * r_t)
     k = S.LP.from_instance(inst, S.default_params(aux_general_integers=0, autotune=1))
     f2, _, ms2 = k.kernel_form()
     assert f2 == (fp, fd)
