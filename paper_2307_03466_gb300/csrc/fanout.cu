@@ -15,8 +15,8 @@
 // ATY[1] the check's A^T y of the current and averaged points.  Every attempt
 // writes the next point of every slot and swaps cur.  An objective whose attempt was
 // rejected, or that restarts to (or finishes with) its average, has its slices
-// copied back into the current pool by k_fcopy before the next attempt (rare events,
-// a few scattered 4-byte columns); a finished objective is carried along unchanged
+// copied back into the current pool by k_fcopy before the next attempt (a few
+// scattered 4-byte columns); a finished objective is carried along unchanged
 // by zero step sizes.  So the SpMMs treat all 64 slots of a row alike and move them
 // with vector loads: a lane holds VEC consecutive objectives, CHUNK / VEC lanes
 // cover a row's CHUNK slots, and a warp works on 32 VEC / CHUNK rows at once
@@ -152,6 +152,38 @@ __device__ __forceinline__ void vst(T* p, const T (&o)[N]) {
 #pragma unroll
   for (int i = 0; i < N; ++i) u.e[i] = o[i];
   *reinterpret_cast<typename FVec<T, N>::V*>(p) = u.v;
+}
+
+// Asynchronous copies of a lane's VEC entries of an epilogue vector into shared
+// memory (zero-filled when off), so that the next row group's operands are in flight
+// while the warp gathers for the current one, without holding registers.  Each lane
+// reads back only the slots it copied, so a wait on its own copies is all the
+// synchronisation needed.  16-byte copies bypass L1.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_lane(void* dst, const void* src, bool on) {
+  const unsigned d = unsigned(__cvta_generic_to_shared(dst));
+  const int n = on ? BYTES : 0;
+  if (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(BYTES), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+// two stages of three epilogue vectors per lane, per warp of a block
+template <typename T, int VEC>
+struct FanStage {
+  typename FVec<T, VEC>::V v[kFWarps][2][3][32];
+};
+template <typename T, int VEC>
+__device__ __forceinline__ void stage_read(const FanStage<T, VEC>& S, int w, int st, int q, int lane, T (&o)[VEC]) {
+  VecU<T, VEC> u;
+  u.v = S.v[w][st][q][lane];
+#pragma unroll
+  for (int i = 0; i < VEC; ++i) o[i] = u.e[i];
 }
 
 // the tile shapes by number: (objectives per lane, slots per sweep) = 1: (4, 64),
@@ -322,9 +354,11 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
   typedef FanGeo<VEC, CHUNK> G;
   __shared__ double sh[kFWarps * 1 * kFK];
   __shared__ __align__(16) FanShared<T> S;
+  __shared__ __align__(16) FanStage<T, VEC> E;
+  constexpr int kB = VEC * int(sizeof(T));
   load_fan_shared(F, S);
   const DevLP<T>& d = F.d;
-  const int lane = threadIdx.x & 31, seg = lane / G::LPR, sl = lane & (G::LPR - 1);
+  const int lane = threadIdx.x & 31, seg = lane / G::LPR, sl = lane & (G::LPR - 1), wib = threadIdx.x >> 5;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const int n = d.n, cur = fan_cur(F);
   const T* __restrict__ Xc = F.X[cur];
@@ -362,7 +396,17 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
         b = __ldg(d.t_rowptr + j + 1);
       }
     };
-    int g = gw;
+    // the epilogue operands (x, the average, a cached A^T y) of row group gg into stage st
+    auto issue = [&](int gg, int st) {
+      const int jj = gg * G::RPW + seg;
+      const bool lv = gg < ngroups && jj < n;
+      const size_t oo = size_t(lv ? jj : 0) * kFK + k0;
+      cp_async_lane<kB>(&E.v[wib][st][0][lane], Xc + oo, lv);
+      if (avg) cp_async_lane<kB>(&E.v[wib][st][1][lane], Xa + oo, lv);
+      if (cached) cp_async_lane<kB>(&E.v[wib][st][2][lane], At + oo, lv);
+      cp_async_commit();
+    };
+    int g = gw, stg = 0;
     int p0, p1, pn0, pn1, cl = 0;
     T vl = T(0);
     rowp(g, p0, p1);
@@ -371,6 +415,7 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
       vl = __ldg(d.t_vals + p0 + sl);
     }
     rowp(g + nw, pn0, pn1);
+    issue(g, 0);
     while (g < ngroups) {
       int pnn0, pnn1, cln = 0;
       T vln = T(0);
@@ -379,19 +424,17 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
         cln = __ldg(d.t_cols + pn0 + sl);
         vln = __ldg(d.t_vals + pn0 + sl);
       }
+      issue(g + nw, stg ^ 1);
       const int j = g * G::RPW + seg;
       const bool live = j < n;
       const size_t o = size_t(live ? j : 0) * kFK + k0;
-      T x[VEC], xa[VEC], at[VEC];
-#pragma unroll
-      for (int v = 0; v < VEC; ++v) x[v] = xa[v] = at[v] = T(0);
-      if (live) {
-        vld_cs<T, VEC>(Xc + o, x);
-        if (avg) vld_cs<T, VEC>(Xa + o, xa);
-        if (cached) vld_cs<T, VEC>(At + o, at);
-      }
       T s[VEC];
       fan_vgather<T, VEC, G::LPR>(p0, p1, cl, vl, d.t_cols, d.t_vals, src, s);
+      cp_async_wait<1>();  // this group's operands (the next group's may still be in flight)
+      T x[VEC], xa[VEC], at[VEC];
+      stage_read<T, VEC>(E, wib, stg, 0, lane, x);
+      if (avg) stage_read<T, VEC>(E, wib, stg, 1, lane, xa);
+      if (cached) stage_read<T, VEC>(E, wib, stg, 2, lane, at);
       if (live) {
         const unsigned long long lob = __ldg(F.lo_bits + j) >> k0, upb = __ldg(F.up_bits + j) >> k0;
         const T lj = __ldg(d.l + j), uj = __ldg(d.u + j);
@@ -416,6 +459,7 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
             if (fl[v] & kSlotCopyLr) __stcs(F.XLR + o + v, x[v]);
       }
       g += nw;
+      stg ^= 1;
       p0 = pn0;
       p1 = pn1;
       pn0 = pnn0;
@@ -423,6 +467,7 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
       cl = cln;
       vl = vln;
     }
+    cp_async_wait<0>();  // the copies issued past the last group land before the stages are reused
   }
   fan_block_sums<A, VEC, CHUNK, 1>(acc, F.part_p, sh);
 }
@@ -437,9 +482,11 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
   typedef FanGeo<VEC, CHUNK> G;
   __shared__ double sh[kFWarps * 2 * kFK];
   __shared__ __align__(16) FanShared<T> S;
+  __shared__ __align__(16) FanStage<T, VEC> E;
+  constexpr int kB = VEC * int(sizeof(T));
   load_fan_shared(F, S);
   const DevLP<T>& d = F.d;
-  const int lane = threadIdx.x & 31, seg = lane / G::LPR, sl = lane & (G::LPR - 1);
+  const int lane = threadIdx.x & 31, seg = lane / G::LPR, sl = lane & (G::LPR - 1), wib = threadIdx.x >> 5;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const int m = d.m, cur = fan_cur(F);
   const T* __restrict__ Xn = F.X[1 - cur];
@@ -477,7 +524,17 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
         b = __ldg(d.a_rowptr + i + 1);
       }
     };
-    int g = gw;
+    // the epilogue operands (A x, y, the average) of row group gg into stage st
+    auto issue = [&](int gg, int st) {
+      const int ii = gg * G::RPW + seg;
+      const bool lv = gg < ngroups && ii < m;
+      const size_t oo = size_t(lv ? ii : 0) * kFK + k0;
+      cp_async_lane<kB>(&E.v[wib][st][0][lane], AXc + oo, lv);
+      cp_async_lane<kB>(&E.v[wib][st][1][lane], Yc + oo, lv);
+      if (avg) cp_async_lane<kB>(&E.v[wib][st][2][lane], Ya + oo, lv);
+      cp_async_commit();
+    };
+    int g = gw, stg = 0;
     int p0, p1, pn0, pn1, cl = 0;
     T vl = T(0);
     rowp(g, p0, p1);
@@ -486,6 +543,7 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
       vl = __ldg(d.a_vals + p0 + sl);
     }
     rowp(g + nw, pn0, pn1);
+    issue(g, 0);
     while (g < ngroups) {
       int pnn0, pnn1, cln = 0;
       T vln = T(0);
@@ -494,19 +552,17 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
         cln = __ldg(d.a_cols + pn0 + sl);
         vln = __ldg(d.a_vals + pn0 + sl);
       }
+      issue(g + nw, stg ^ 1);
       const int i = g * G::RPW + seg;
       const bool live = i < m;
       const size_t o = size_t(live ? i : 0) * kFK + k0;
-      T ax[VEC], y[VEC], ya[VEC];
-#pragma unroll
-      for (int v = 0; v < VEC; ++v) ax[v] = y[v] = ya[v] = T(0);
-      if (live) {
-        vld_cs<T, VEC>(AXc + o, ax);
-        vld_cs<T, VEC>(Yc + o, y);
-        if (avg) vld_cs<T, VEC>(Ya + o, ya);
-      }
       T s[VEC];
       fan_vgather<T, VEC, G::LPR>(p0, p1, cl, vl, d.a_cols, d.a_vals, src, s);
+      cp_async_wait<1>();  // this group's operands (the next group's may still be in flight)
+      T ax[VEC], y[VEC], ya[VEC];
+      stage_read<T, VEC>(E, wib, stg, 0, lane, ax);
+      stage_read<T, VEC>(E, wib, stg, 1, lane, y);
+      if (avg) stage_read<T, VEC>(E, wib, stg, 2, lane, ya);
       if (live) {
         const T lo = __ldg(d.lo + i), hi = __ldg(d.hi + i);
         T yn[VEC];
@@ -528,6 +584,7 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
             if (fl[v] & kSlotCopyLr) __stcs(F.YLR + o + v, y[v]);
       }
       g += nw;
+      stg ^= 1;
       p0 = pn0;
       p1 = pn1;
       pn0 = pnn0;
@@ -535,6 +592,7 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
       cl = cln;
       vl = vln;
     }
+    cp_async_wait<0>();  // the copies issued past the last group land before the stages are reused
   }
   // part_d is [block][sum][objective] with sum 0 = ||dy||^2, 1 = dy.(A x' - A x)
   fan_block_sums<A, VEC, CHUNK, 2>(acc, F.part_d, sh);
@@ -843,32 +901,71 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_control(DevFan<T> F) {
 // Copies into the current pool, after the control kernels: RST = false, the
 // objectives whose attempt was rejected get back the point they attempted from (now
 // in the next pool: x, y, A x); RST = true, the ones that restart to or finish
-// with their average get the average (x, y, A x and the check's A^T y).  Row per
-// warp, lane q on slots q and q + 32; nothing to do unless a flag is set.
+// with their average get the average (x, y, A x and the check's A^T y).  A thread
+// per (row, flagged objective) pair; nothing to do unless a flag is set.
 template <typename T, bool RST>
 __global__ void __launch_bounds__(kFThreads) k_fcopy(DevFan<T> F) {
   const FanState* st = F.state;
-  const int lane = threadIdx.x & 31;
   const unsigned char* flag = RST ? st->rst : st->rej;
-  bool mine[2];
-#pragma unroll
-  for (int q = 0; q < 2; ++q) mine[q] = lane + 32 * q < F.K && flag[lane + 32 * q] != 0;
-  if (!__any_sync(0xffffffffu, mine[0] || mine[1])) return;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  // the flagged objectives, ascending
+  __shared__ int list[kFK];
+  __shared__ int cnt;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const bool a = lane < F.K && flag[lane] != 0, b = lane + 32 < F.K && flag[lane + 32] != 0;
+    const unsigned ma = __ballot_sync(0xffffffffu, a), mb = __ballot_sync(0xffffffffu, b);
+    const unsigned below = (1u << lane) - 1u;
+    if (a) list[__popc(ma & below)] = lane;
+    if (b) list[__popc(ma) + __popc(mb & below)] = lane + 32;
+    if (lane == 0) cnt = __popc(ma) + __popc(mb);
+  }
+  __syncthreads();
+  const int R = cnt;
+  if (R == 0) return;
   const int cur = fan_cur(F), from = RST ? 2 : 1 - cur;
-  const int rows = max(F.d.n, F.d.m);
-  for (int r = gw; r < rows; r += nw) {
+  const int n = F.d.n, m = F.d.m;
+  const long long rows = n > m ? n : m, total = rows * R;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  T* __restrict__ xc = F.X[cur];
+  const T* __restrict__ xf = F.X[from];
+  T* __restrict__ yc = F.Y[cur];
+  const T* __restrict__ yf = F.Y[from];
+  T* __restrict__ axc = F.AX[cur];
+  const T* __restrict__ axf = F.AX[from];
+  T* __restrict__ atc = F.ATY[0];
+  const T* __restrict__ atf = F.ATY[1];
+  // (row, objective) pairs, four per thread and step: every load of a step is issued
+  // before its stores, so the copies are bound by bandwidth, not by latency
+  constexpr int U = 4;
+  for (long long base = (long long)blockIdx.x * blockDim.x + threadIdx.x; base < total; base += U * stride) {
+    T vx[U], vy[U], vax[U], vat[U];
+    size_t off[U];
+    bool rx[U], ry[U];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      if (!mine[q]) continue;
-      const size_t o = size_t(r) * kFK + lane + 32 * q;
-      if (r < F.d.n) {
-        F.X[cur][o] = F.X[from][o];
-        if (RST) F.ATY[0][o] = F.ATY[1][o];
+    for (int u = 0; u < U; ++u) {
+      const long long idx = base + u * stride;
+      const int r = int(idx / R), k = list[int(idx % R)];
+      off[u] = size_t(r) * kFK + k;
+      rx[u] = idx < total && r < n;
+      ry[u] = idx < total && r < m;
+      if (rx[u]) {
+        vx[u] = xf[off[u]];
+        if (RST) vat[u] = atf[off[u]];
       }
-      if (r < F.d.m) {
-        F.Y[cur][o] = F.Y[from][o];
-        F.AX[cur][o] = F.AX[from][o];
+      if (ry[u]) {
+        vy[u] = yf[off[u]];
+        vax[u] = axf[off[u]];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (rx[u]) {
+        xc[off[u]] = vx[u];
+        if (RST) atc[off[u]] = vat[u];
+      }
+      if (ry[u]) {
+        yc[off[u]] = vy[u];
+        axc[off[u]] = vax[u];
       }
     }
   }
