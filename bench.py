@@ -885,6 +885,7 @@ def batched_section(S, peak, peak_kind):
                         "note": "isolated CUDA-event launches, every LP taking part (the start of a solve)"}
     out["roofline"] = {"bound": "hbm", "kernel": kname, "achieved": kb / (kms * 1e6), "peak": peak, "unit": "GB/s",
                        "frac": kb / (kms * 1e6) / peak, "peak_source": peak_kind, "bytes_per_launch": kb,
+                       "traffic": traffic_for(kname + "@batched", BATCH_WORKLOAD),
                        "frac_other_kernel": (bp / (ms[0] * 1e6) if kname == "k_bdual<float>"
                                              else bd / (ms[1] * 1e6)) / peak}
     B.close()
