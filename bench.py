@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--no-propagate", action="store_true", help="skip the bound-propagation section")
     ap.add_argument("--no-heuristic", action="store_true", help="skip the whole-heuristic section")
     ap.add_argument("--form", default="auto",
-                    choices=["auto", "rows32", "wide", "wide,rows32", "rows32,wide"],
+                    choices=["auto"] + [f"{a},{b}" if a != b else a for a in ("rows32", "wide", "async")
+                                        for b in ("rows32", "wide", "async")],
                     help="forms of the single-LP per-attempt kernels (primal[,dual]) of the headline and "
                          "DRAM-resident solves: auto (the create-time autotuner), or forced (profiler captures, "
                          "under which the autotuner's timings are distorted)")
@@ -68,7 +69,7 @@ def set_form(name: str):
     FORM_KW.clear()
     if name == "auto":
         return
-    code = {"rows32": 4, "wide": 2}
+    code = {"rows32": 4, "wide": 2, "async": 5}
     parts = name.split(",")
     FORM_KW.update({"prefetch": code[parts[0]], "dual_form": code[parts[-1]], "autotune": 0})
 
@@ -545,7 +546,7 @@ def run_ours(args):
 
 
 FORM_NAMES = {4: "32-row tiles", 1: "32-row tiles, first tile prefetched", 2: "wide tiles (<= 128 rows)",
-              3: "wide tiles staged in shared memory"}
+              3: "wide tiles staged in shared memory", 5: "32-row tiles, next tile staged by asynchronous copies"}
 
 
 def form_info(lp):
@@ -554,8 +555,8 @@ def form_info(lp):
     (fp, fd), r, ms = lp.kernel_form()
     return {"form": {"primal": FORM_NAMES.get(fp, fp), "dual": FORM_NAMES.get(fd, fd)},
             "l2_rule_form": FORM_NAMES.get(r, r),
-            "tuned_ms_per_launch": {"primal": {"32-row": ms[0], "wide": ms[2]},
-                                    "dual": {"32-row": ms[1], "wide": ms[3]}}}
+            "tuned_ms_per_launch": {side: {"32-row": ms[i], "wide": ms[2 + i], "async-copy": ms[4 + i]}
+                                    for i, side in enumerate(("primal", "dual"))}}
 
 
 def autotune_info(*lps):

@@ -114,7 +114,9 @@ typedef struct {
                                    vectors fit in half of the L2 cache, else 2); 1: 32-row tiles, each
                                    warp loading its first tile before the wait on the preceding kernel;
                                    2: wide tiles of up to 128 rows, plain loads; 3: wide tiles staged in
-                                   shared memory by bulk copies; 4: 32-row tiles, plain loads (0) */
+                                   shared memory by bulk copies; 4: 32-row tiles, plain loads; 5 (FP32-mixed
+                                   only): 32-row tiles, the warp's next tile staged in shared memory by
+                                   asynchronous copies (0) */
   int32_t host_transpose;       /* 1: build the stored transpose A^T on the host threads; 0: on the device,
                                    a stable radix sort of the nonzeros by column (0) */
   /* continuous repair inside scylla_run (see scylla_repair; not part of the paper's
@@ -131,7 +133,7 @@ typedef struct {
                                    2 the attempts between checks in one persistent cooperative launch whose
                                    warps take tiles from a shared queue over the LPs still running, the
                                    queue compacted at every check (0) */
-  int32_t autotune;             /* with prefetch = 0: 1 times the 32-row and the wide-tile forms of the
+  int32_t autotune;             /* with prefetch = 0: 1 times the 32-row, wide-tile and (FP32) asynchronous-copy forms of the
                                    per-attempt kernels on the handle's own matrix at create and keeps the
                                    faster for each of the two kernels (the choice is kept per matrix shape
                                    for the process); 0 takes the L2-size rule (1) */
@@ -279,11 +281,12 @@ int scylla_time_kernels(scylla_lp* lp, int32_t attempts, double* ms);
 
 /* Forms of the primal and the dual per-attempt kernels in use (numbered as
  * scylla_params.prefetch: 4 32-row tiles, 1 32-row with prefetch, 2 wide tiles, 3
- * staged), the form the L2-size rule gives both, and the create-time autotuner's
- * device times per launch in ms, tune_ms[0..3] = primal and dual of the 32-row
- * form, primal and dual of the wide form (0 when it did not time them: a forced
- * form, autotune = 0, or the choice kept from an earlier handle of the same shape).
- * The autotuner picks each kernel's form on its own.  Any output may be NULL. */
+ * staged, 5 asynchronous copies), the form the L2-size rule gives both, and the
+ * create-time autotuner's device times per launch in ms, tune_ms[0..5] = primal and
+ * dual of the 32-row form, of the wide form, and of the asynchronous-copy form (0
+ * when it did not time them: a forced form, autotune = 0, FP64 for the last pair, or
+ * the choice kept from an earlier handle of the same shape).  The autotuner picks
+ * each kernel's form on its own.  Any output may be NULL. */
 int scylla_kernel_form(const scylla_lp* lp, int32_t* form, int32_t* form_dual, int32_t* rule_form,
                        double* tune_ms);
 

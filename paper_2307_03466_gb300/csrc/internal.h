@@ -34,6 +34,9 @@ constexpr int kWideRows = 128;  // rows per wide tile (DRAM-resident form): rows
 constexpr int kWideRPL = kWideRows / 32;
 // forms of the per-attempt kernels
 constexpr int kFormPlain = 0, kFormPrefetch = 1, kFormWide = 2, kFormStaged = 3;
+// 32-row tiles whose next tile (indices, values, row pointers, epilogue operands) is
+// staged in shared memory by asynchronous copies (FP32 only)
+constexpr int kFormAsync = 4;
 constexpr int kVec = 4;        // elements per lane per vector load
 constexpr int kSmemPerWarp = kTileNnz + kTileNnz / 32 + 8;  // skewed product buffer
 

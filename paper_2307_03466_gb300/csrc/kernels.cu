@@ -444,6 +444,156 @@ __device__ __forceinline__ void tiles_rows(const int2* __restrict__ tiles, int n
   }
 }
 
+// ------------------------------------------------- asynchronous tile staging ---
+// The 32-row tiles with the warp's next tile staged in shared memory by
+// asynchronous copies (cp.async) while the warp gathers for the current tile: the
+// column indices and values, the row pointers and the epilogue operands of the next
+// tile are in flight one tile ahead, and none of them holds a register until the
+// tile starts.  Products, row sums and epilogues are those of spmv_tiles on the same
+// tiles, in the same order, so the two forms give identical results.  A single row
+// longer than a tile reads global memory directly.
+__device__ __forceinline__ unsigned long long l2_policy_evict_first() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void cpa16(void* dst, const void* src, unsigned long long pol) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(
+                   unsigned(__cvta_generic_to_shared(dst))),
+               "l"(src), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void cpa4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(unsigned(__cvta_generic_to_shared(dst))), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// one warp's stage: a tile's indices and values (three vector steps of 32 lanes),
+// the row pointers of its rows and five epilogue vectors over its rows
+template <typename V>
+struct AsyncStage {
+  static constexpr int kN = 3 * 32 * kVec;
+  int col[kN];
+  V val[kN];
+  int rp[32];
+  V pre[5][32];
+};
+
+template <typename V, typename Gather, typename Epi>
+__device__ __forceinline__ void spmv_tiles_async(const int2* __restrict__ tiles, int ntiles,
+                                                 const int* __restrict__ rowptr, const int* __restrict__ cols,
+                                                 const V* __restrict__ vals, Gather& gat, Epi& epi,
+                                                 V* __restrict__ sm, AsyncStage<V>& S, int vec_mask) {
+  static_assert(sizeof(V) == 4, "the asynchronous-copy form stages FP32 values");
+  const int lane = threadIdx.x & 31;
+  const WarpTiles wt = warp_tiles(ntiles);
+  if (wt.first >= wt.end) return;
+  const unsigned long long pol = l2_policy_evict_first();
+  auto longrow_of = [](int2 a, int2 b) { return b.x - a.x == 1 && b.y - a.y > kTileNnz; };
+  // the copies of one tile into the stage (none for a long row), as one group
+  auto issue = [&](int2 ta, int2 tb) {
+    if (!longrow_of(ta, tb)) {
+      const int base = ta.y & ~(kVec - 1);
+#pragma unroll
+      for (int it = 0; it < 3; ++it) {
+        const int o = (it * 32 + lane) * kVec, p = base + o;
+        if (p < tb.y) {
+          cpa16(&S.col[o], cols + p, pol);
+          cpa16(&S.val[o], vals + p, pol);
+        }
+      }
+      if (lane < tb.x - ta.x) {
+        cpa4(&S.rp[lane], rowptr + ta.x + lane);
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+          if (vec_mask & (1 << k)) cpa4(&S.pre[k][lane], epi.stage_vec(k) + ta.x + lane);
+      }
+    }
+    cpa_commit();
+  };
+  int2 ca = __ldg(tiles + wt.first), cb = __ldg(tiles + wt.first + 1);
+  int2 na = make_int2(0, 0), nb = make_int2(0, 0), la = make_int2(0, 0), lb = make_int2(0, 0);
+  if (wt.first + wt.step < wt.end) {
+    na = __ldg(tiles + wt.first + wt.step);
+    nb = __ldg(tiles + wt.first + wt.step + 1);
+  }
+  issue(ca, cb);
+  for (int t = wt.first; t < wt.end; t += wt.step) {
+    const int t2 = t + 2 * wt.step;
+    if (t2 < wt.end) {  // bounds two tiles ahead, for the copies issued at the next tile
+      la = __ldg(tiles + t2);
+      lb = __ldg(tiles + t2 + 1);
+    }
+    const int r0 = ca.x, r1 = cb.x, p0 = ca.y, p1 = cb.y;
+    const int base = p0 & ~(kVec - 1);
+    cpa_wait_all();
+    __syncwarp();
+    if (longrow_of(ca, cb)) {
+      __syncwarp();
+      if (t + wt.step < wt.end) issue(na, nb);
+      const typename Epi::Pre pre = epi.load(r0);
+      V s[1];
+      long_row_sum<1, true>(p0, p1, cols, vals, gat, s);
+      if (lane == 0) epi.finish(r0, s, pre);
+    } else {
+      const int nr = r1 - r0, L = row_lanes(nr), sub = L > 1 ? lane % L : 0;
+      const int rl = L > 1 ? lane / L : lane;
+      int q0 = 0, q1 = 0;
+      typename Epi::Pre pre{};
+      if (rl < nr) {
+        q0 = S.rp[rl] - p0;
+        q1 = (rl + 1 < nr ? S.rp[rl + 1] : p1) - p0;
+        if (sub == 0) pre = epi.stage_pre(&S.pre[0][0], 32, rl);
+      }
+      // the gathers take their indices from the stage; the values wait in registers
+      // for the products, so the stage is free once every gather is issued
+      V v[3][4], g[3][4];
+#pragma unroll
+      for (int it = 0; it < 3; ++it) {
+        const int o = (it * 32 + lane) * kVec, p = base + o;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int q = p + e;
+          v[it][e] = V(0);
+          g[it][e] = V(0);
+          if (q >= p0 && q < p1) {
+            V gg[1];
+            gat(S.col[o + e], gg);
+            g[it][e] = gg[0];
+            v[it][e] = S.val[o + e];
+          }
+        }
+      }
+      __syncwarp();  // every lane has read the stage before it is refilled
+      if (t + wt.step < wt.end) issue(na, nb);
+#pragma unroll
+      for (int it = 0; it < 3; ++it) {
+        const int p = base + (it * 32 + lane) * kVec;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int q = p + e;
+          if (q >= p0 && q < p1) sm[skew(q - p0)] = v[it][e] * g[it][e];
+        }
+      }
+      __syncwarp();
+      V sum = V(0);
+      if (rl < nr)
+        for (int q = q0 + sub; q < q1; q += L) sum += sm[skew(q)];
+      for (int o = L >> 1; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+      const V sv[1] = {sum};
+      if (rl < nr && sub == 0) epi.finish(r0 + rl, sv, pre);
+      __syncwarp();
+    }
+    ca = na;
+    cb = nb;
+    na = la;
+    nb = lb;
+  }
+  cpa_wait_all();
+}
+
 // ---------------------------------------------------------------- PDHG slot ---
 template <typename T, bool Coh = false>
 struct PrimalEpi {
@@ -985,6 +1135,60 @@ __global__ void __launch_bounds__(kThreads) k_dual_st(DevLP<T> d) {
   reduce_step<A>(acc_part<T>(d.part_p), d.grid_p, acc_part<T>(d.part_d), d.grid_d, reinterpret_cast<A*>(dsm), red);
   if (threadIdx.x == 0) {
     if (!ctl->done) step_control<A>(ctl, pre, red[0], red[1], red[2], d.trace_steps, d.trace_cap);
+    ctl->cnt_dual = 0;
+  }
+}
+
+// The asynchronous-copy form (FP32): the per-attempt kernels over 32-row tiles with
+// the warp's next tile staged in shared memory (spmv_tiles_async); a primal retry
+// (A^T y cached) takes the rows without a gather, as the other forms do.
+__global__ void __launch_bounds__(kThreads, 3) k_primal_as(DevLP<float> d) {
+  Control* ctl = d.ctl;
+  __shared__ float sm[kWarpsPerBlock * kSmemPerWarp];
+  __shared__ __align__(16) AsyncStage<float> stg[kWarpsPerBlock];
+  pdl_enter();
+  if (ctl->done || ctl->k >= ctl->iter_limit) return;
+  const SlotView<float> v = make_view<float>(ctl);
+  PrimalEpi<float> epi;
+  setup_primal(epi, d, v);
+  if (v.aty_valid) {
+    tiles_rows<float>(d.t_tiles, d.t_ntiles, epi.aty, epi);
+  } else {
+    const float* __restrict__ yc = d.Y[v.cur];
+    auto gat = [&](int i, float(&g)[1]) { g[0] = __ldg(yc + i); };
+    const int w = threadIdx.x >> 5;
+    spmv_tiles_async<float>(d.t_tiles, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals, gat, epi, sm + w * kSmemPerWarp,
+                            stg[w], v.do_avg ? 31 : 15);
+  }
+  const float acc[kNP] = {epi.acc};
+  block_store_partials<kNP>(acc, acc_part<float>(d.part_p));
+}
+
+__global__ void __launch_bounds__(kThreads, 3) k_dual_as(DevLP<float> d) {
+  typedef AccOf<float>::type A;
+  Control* ctl = d.ctl;
+  __shared__ float sm[kWarpsPerBlock * kSmemPerWarp];
+  __shared__ __align__(16) AsyncStage<float> stg[kWarpsPerBlock];
+  pdl_enter();
+  if (ctl->done || ctl->k >= ctl->iter_limit) return;
+  const SlotView<float> v = make_view<float>(ctl);
+  DualEpi<float> epi;
+  setup_dual(epi, d, v);
+  const float* __restrict__ xn = d.X[v.nxt];
+  auto gat = [&](int j, float(&g)[1]) { g[0] = __ldg(xn + j); };
+  const int w = threadIdx.x >> 5;
+  spmv_tiles_async<float>(d.a_tiles, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals, gat, epi, sm + w * kSmemPerWarp,
+                          stg[w], v.do_avg ? 31 : 15);
+  const A acc[kND] = {epi.acc0, epi.acc1};
+  block_store_partials<kND>(acc, acc_part<float>(d.part_d));
+  if (!is_last_block(&ctl->cnt_dual)) return;
+  __shared__ StepPre pre;
+  if (threadIdx.x == 0) pre = step_pre<A>(ctl, d.step_fac, d.n_check);
+  __shared__ A red[kNP + kND];
+  static_assert(3 * (kThreads - 32) * sizeof(A) <= sizeof(sm), "reduction scratch");
+  reduce_step<A>(acc_part<float>(d.part_p), d.grid_p, acc_part<float>(d.part_d), d.grid_d, sm, red);
+  if (threadIdx.x == 0) {
+    step_control<A>(ctl, pre, red[0], red[1], red[2], d.trace_steps, d.trace_cap);
     ctl->cnt_dual = 0;
   }
 }
@@ -2504,6 +2708,9 @@ template <typename T>
 cudaError_t launch_primal(const DevLP<T>& d, cudaStream_t st) {
   switch (d.form_p) {
     case kFormStaged: return launch_step_kernel<T>(k_primal_st<T>, d.grid_p, d, st, Staged<T>::kBlockBytes);
+    case kFormAsync:
+      if constexpr (std::is_same<T, float>::value) return launch_step_kernel<float>(k_primal_as, d.grid_p, d, st);
+      return cudaErrorInvalidValue;
     case kFormPrefetch: return launch_step_kernel<T>(k_primal<T, kFormPrefetch>, d.grid_p, d, st);
     case kFormWide: return launch_step_kernel<T>(k_primal<T, kFormWide>, d.grid_p, d, st);
     default: return launch_step_kernel<T>(k_primal<T, kFormPlain>, d.grid_p, d, st);
@@ -2513,6 +2720,9 @@ template <typename T>
 cudaError_t launch_dual(const DevLP<T>& d, cudaStream_t st) {
   switch (d.form_d) {
     case kFormStaged: return launch_step_kernel<T>(k_dual_st<T>, d.grid_d, d, st, Staged<T>::kBlockBytes);
+    case kFormAsync:
+      if constexpr (std::is_same<T, float>::value) return launch_step_kernel<float>(k_dual_as, d.grid_d, d, st);
+      return cudaErrorInvalidValue;
     case kFormPrefetch: return launch_step_kernel<T>(k_dual<T, kFormPrefetch>, d.grid_d, d, st);
     case kFormWide: return launch_step_kernel<T>(k_dual<T, kFormWide>, d.grid_d, d, st);
     default: return launch_step_kernel<T>(k_dual<T, kFormPlain>, d.grid_d, d, st);
@@ -2601,6 +2811,9 @@ int occupancy_grid(int side, int form, int work_tiles) {
   else if (form == kFormStaged) {
     k = side == 0 ? k_primal_st<T> : k_dual_st<T>;
     smem = Staged<T>::kBlockBytes;
+  } else if (form == kFormAsync) {
+    if constexpr (std::is_same<T, float>::value) k = side == 0 ? k_primal_as : k_dual_as;
+    else k = side == 0 ? k_primal<T, kFormPlain> : k_dual<T, kFormPlain>;
   } else if (form == kFormWide) k = side == 0 ? k_primal<T, kFormWide> : k_dual<T, kFormWide>;
   else if (form == kFormPrefetch) k = side == 0 ? k_primal<T, kFormPrefetch> : k_dual<T, kFormPrefetch>;
   else k = side == 0 ? k_primal<T, kFormPlain> : k_dual<T, kFormPlain>;

@@ -52,6 +52,9 @@ using namespace scylla;
 
 static const double kInf = std::numeric_limits<double>::infinity();
 
+// a kernel form in scylla_params.prefetch's numbering
+static int api_form(int f) { return f == kFormPlain ? 4 : f == kFormAsync ? 5 : f; }
+
 extern "C" void scylla_default_params(scylla_params* p) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));
@@ -364,14 +367,16 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   if (lp->p.trace_capacity < 0) FAIL(SCYLLA_ERR_INVALID_ARG, "trace_capacity must be >= 0");
   if (lp->p.use_graph < 0 || lp->p.use_graph > 3) FAIL(SCYLLA_ERR_INVALID_ARG, "use_graph must be 0..3");
   if (!(lp->p.device_wait_limit_s > 0.0)) FAIL(SCYLLA_ERR_INVALID_ARG, "device_wait_limit_s must be > 0");
-  if (lp->p.prefetch < 0 || lp->p.prefetch > 4) FAIL(SCYLLA_ERR_INVALID_ARG, "prefetch must be 0..4");
+  if (lp->p.prefetch < 0 || lp->p.prefetch > 5) FAIL(SCYLLA_ERR_INVALID_ARG, "prefetch must be 0..5");
   if (lp->p.host_transpose < 0 || lp->p.host_transpose > 1) FAIL(SCYLLA_ERR_INVALID_ARG, "host_transpose must be 0 or 1");
   if (lp->p.repair_iters < 0 || !(lp->p.repair_tol >= 0.0) || lp->p.repair_rounds < 1)
     FAIL(SCYLLA_ERR_INVALID_ARG, "need repair_iters >= 0, repair_tol >= 0 and repair_rounds >= 1");
   if (lp->p.distance != 1 && lp->p.distance != 2) FAIL(SCYLLA_ERR_INVALID_ARG, "distance must be 1 or 2");
   if (lp->p.infeasibility_checks != 0 && lp->p.infeasibility_checks != 1)
     FAIL(SCYLLA_ERR_INVALID_ARG, "infeasibility_checks must be 0 or 1");
-  if (lp->p.dual_form < 0 || lp->p.dual_form > 4) FAIL(SCYLLA_ERR_INVALID_ARG, "dual_form must be 0..4");
+  if (lp->p.dual_form < 0 || lp->p.dual_form > 5) FAIL(SCYLLA_ERR_INVALID_ARG, "dual_form must be 0..5");
+  if (lp->p.precision != SCYLLA_PREC_MIXED && (lp->p.prefetch == 5 || lp->p.dual_form == 5))
+    FAIL(SCYLLA_ERR_INVALID_ARG, "the asynchronous-copy form (5) is for FP32-mixed precision");
   if (lp->p.precision != SCYLLA_PREC_FP64 && lp->p.precision != SCYLLA_PREC_MIXED)
     FAIL(SCYLLA_ERR_INVALID_ARG, "unknown precision");
   CK(cudaGetDevice(&lp->device));
@@ -504,7 +509,7 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
     const int pf = lp->p.prefetch;
     int form = kFormPlain;
     auto forced = [](int v) {
-      return v == 1 ? kFormPrefetch : v == 2 ? kFormWide : v == 3 ? kFormStaged : kFormPlain;
+      return v == 1 ? kFormPrefetch : v == 2 ? kFormWide : v == 3 ? kFormStaged : v == 5 ? kFormAsync : kFormPlain;
     };
     if (pf == 0) form = fits ? kFormPlain : kFormWide;
     else form = forced(pf);
@@ -532,6 +537,10 @@ static int create_impl(const scylla_csr* A, const double* c, const double* lo, c
   if (lp->tune) {
     cap_p = std::max(grid_of(0, kFormPlain, 1 << 30), grid_of(0, kFormWide, 1 << 30));
     cap_d = std::max(grid_of(1, kFormPlain, lp->a_ntiles), grid_of(1, kFormWide, lp->a_ntiles_w));
+    if (mixed) {
+      cap_p = std::max(cap_p, grid_of(0, kFormAsync, 1 << 30));
+      cap_d = std::max(cap_d, grid_of(1, kFormAsync, lp->a_ntiles));
+    }
   }
   lp->grid_d = grid_of(1, lp->form_d, form_tiles_d(lp->form_d));
   lp->grid_c2 = grid_of(3, 0, lp->a_ntiles);
@@ -1111,8 +1120,8 @@ int scylla_lp::solve(double tol, int64_t iter_limit, int stall_checks, scylla_pd
     cudaEventElapsedTime(&ms, ev0, ev1);
     out->seconds = ms * 1e-3;
     out->launches = last_launches >= 0 ? last_launches : 3 + h.chunks * (2LL * p.n_check + 3);
-    out->kernel_form = form_p == kFormPlain ? 4 : form_p;
-    out->kernel_form_dual = form_d == kFormPlain ? 4 : form_d;
+    out->kernel_form = api_form(form_p);
+    out->kernel_form_dual = api_form(form_d);
   }
   return SCYLLA_OK;
 }
@@ -1729,8 +1738,10 @@ int autotune_form(scylla_lp* lp) {
     CK(cudaMemcpyAsync(lp->h_ctl, lp->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     const Control saved = *lp->h_ctl;
-    const int forms[2] = {kFormPlain, kFormWide};
-    for (int q = 0; q < 2; ++q) {
+    // the 32-row, wide and (FP32) asynchronous-copy forms
+    const int forms[3] = {kFormPlain, kFormWide, kFormAsync};
+    const int nf = std::is_same<T, float>::value ? 3 : 2;
+    for (int q = 0; q < nf; ++q) {
       set_forms<T>(lp, forms[q], forms[q]);
       double ms[4] = {0, 0, 0, 0};
       const int rc = time_kernels_impl<T>(lp, dev_of<T>(lp), kTuneAttempts, ms);
@@ -1738,9 +1749,12 @@ int autotune_form(scylla_lp* lp) {
       lp->tune_ms[2 * q] = ms[0];
       lp->tune_ms[2 * q + 1] = ms[1];
     }
-    const int rule = lp->form_rule == kFormWide ? 1 : 0, other = 1 - rule;
+    const int rule = lp->form_rule == kFormWide ? 1 : 0;
     auto pick = [&](int side) {
-      return forms[lp->tune_ms[2 * other + side] < (1.0 - kTuneMargin) * lp->tune_ms[2 * rule + side] ? other : rule];
+      int best = rule;
+      for (int q = 0; q < nf; ++q)
+        if (lp->tune_ms[2 * q + side] < lp->tune_ms[2 * best + side]) best = q;
+      return forms[lp->tune_ms[2 * best + side] < (1.0 - kTuneMargin) * lp->tune_ms[2 * rule + side] ? best : rule];
     };
     chosen = std::make_pair(pick(0), pick(1));
     {
@@ -1762,11 +1776,11 @@ int autotune_form(scylla_lp* lp) {
 extern "C" int scylla_kernel_form(const scylla_lp* lp, int32_t* form, int32_t* form_dual, int32_t* rule_form,
                                   double* tune_ms) {
   if (!lp) FAIL(SCYLLA_ERR_INVALID_ARG, "null handle");
-  if (form) *form = lp->form_p == kFormPlain ? 4 : lp->form_p;
-  if (form_dual) *form_dual = lp->form_d == kFormPlain ? 4 : lp->form_d;
-  if (rule_form) *rule_form = lp->form_rule == kFormPlain ? 4 : lp->form_rule;
+  if (form) *form = api_form(lp->form_p);
+  if (form_dual) *form_dual = api_form(lp->form_d);
+  if (rule_form) *rule_form = api_form(lp->form_rule);
   if (tune_ms)
-    for (int q = 0; q < 4; ++q) tune_ms[q] = lp->tune_ms[q];
+    for (int q = 0; q < 6; ++q) tune_ms[q] = lp->tune_ms[q];
   return SCYLLA_OK;
 }
 

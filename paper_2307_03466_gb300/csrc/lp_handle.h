@@ -66,7 +66,8 @@ struct scylla_lp {
   int form_p = 0, form_d = 0;  // forms of the primal / dual per-attempt kernels (kForm*)
   int form_rule = 0;           // the form the L2-size rule gives
   bool tune = false;           // the create-time autotuner chooses between the 32-row and wide forms
-  double tune_ms[4] = {0.0, 0.0, 0.0, 0.0};  // its ms per launch: primal, dual of the 32-row form, then of the wide
+  double tune_ms[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // its ms per launch: primal, dual of the 32-row form,
+                                                       // then of the wide, then of the asynchronous-copy form
   double *a_vals64 = nullptr, *t_vals64 = nullptr;
   float *a_vals32 = nullptr, *t_vals32 = nullptr;
   double *c_un = nullptr, *l_un = nullptr, *u_un = nullptr, *lo_un = nullptr, *hi_un = nullptr;

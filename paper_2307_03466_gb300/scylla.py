@@ -426,10 +426,10 @@ class LP:
 
     def kernel_form(self):
         """((primal form, dual form) in use, the L2-size rule's form, the autotuner's ms
-        per launch: primal and dual of the 32-row form, then of the wide form) --
-        scylla_kernel_form."""
+        per launch: primal and dual of the 32-row form, of the wide form, of the
+        asynchronous-copy form) -- scylla_kernel_form."""
         f, fd, r = C.c_int32(), C.c_int32(), C.c_int32()
-        ms = np.zeros(4)
+        ms = np.zeros(6)
         _check(lib().scylla_kernel_form(self.h, C.byref(f), C.byref(fd), C.byref(r), _dp(ms)))
         return (f.value, fd.value), r.value, ms
 

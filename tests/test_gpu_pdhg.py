@@ -193,6 +193,34 @@ def test_wide_and_staged_forms_match_oracle(name):
         g.close()
 
 
+@pytest.mark.parametrize("name", ["knapcover_700", "long_rows", "packcover_2kx4k", "mcf_small"])
+@pytest.mark.parametrize("forms", [(4, 5), (5, 4), (5, 5)])
+def test_async_copy_form_identical_to_32_row_tiles(name, forms):
+    """FP32-mixed: the asynchronous-copy form stages the warp's next 32-row tile
+    (indices, values, row pointers, epilogue operands) in shared memory and computes
+    each tile's products, row sums and epilogue as the 32-row form does: identical
+    points, attempts, rejections and restarts, alone or paired with the 32-row form
+    in the other kernel.  The instances have fewer tiles than either form's resident
+    blocks, so the two take the same grid (tile deal and block partials)."""
+    inst = INSTANCES[name]
+    g0, _ = pair(inst, precision=1, prefetch=4)
+    g1, _ = pair(inst, precision=1, prefetch=forms[0], dual_form=forms[1])
+    r0, r1 = g0.pdhg_solve(1e-6, 20000), g1.pdhg_solve(1e-6, 20000)
+    assert (r1.kernel_form, r1.kernel_form_dual) == forms
+    assert (r1.iterations, r1.status, r1.rejected, r1.restarts) == (r0.iterations, r0.status, r0.rejected, r0.restarts)
+    np.testing.assert_array_equal(g1.primal(), g0.primal())
+    np.testing.assert_array_equal(g1.dual(), g0.dual())
+    g0.close()
+    g1.close()
+
+
+def test_async_copy_form_is_fp32_only():
+    import paper_2307_03466_gb300.scylla as S
+    with pytest.raises(S.ScyllaError) as ei:
+        S.LP.from_instance(INSTANCES["knapcover_700"], S.default_params(aux_general_integers=0, precision=0, prefetch=5))
+    assert ei.value.code == S.ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("name", ["setcover_200x500", "long_rows", "mcf_small"])
 @pytest.mark.parametrize("forms", [(2, 4), (4, 2)])
 def test_primal_and_dual_in_different_forms_match_oracle(name, forms):
@@ -346,7 +374,7 @@ def test_autotuned_form_is_reported_and_leaves_no_trace(name):
     inst = INSTANCES[name]
     g = S.LP.from_instance(inst, S.default_params(aux_general_integers=0, autotune=1))
     (fp, fd), rule, ms = g.kernel_form()
-    assert fp in (2, 4) and fd in (2, 4) and rule in (2, 4)
+    assert fp in (2, 4) and fd in (2, 4) and rule in (2, 4)  # FP64: the 32-row and wide forms
     h = S.LP.from_instance(inst, S.default_params(aux_general_integers=0, prefetch=fp, dual_form=fd))
     assert h.kernel_form()[0] == (fp, fd)
     r1 = g.pdhg_solve(1e-6, 20000)
