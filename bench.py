@@ -61,17 +61,26 @@ def parse():
     return ap.parse_args()
 
 
-# parameters that force the per-attempt kernels' form (--form); empty for the autotuner
+# parameters that force the per-attempt kernels' form (--form) of the FP32-mixed handles,
+# and of the FP64 ones (where the asynchronous-copy form, FP32 only, becomes the 32-row
+# form); empty for the autotuner
 FORM_KW = {}
+FORM_KW64 = {}
 
 
 def set_form(name: str):
     FORM_KW.clear()
+    FORM_KW64.clear()
     if name == "auto":
         return
     code = {"rows32": 4, "wide": 2, "async": 5}
     parts = name.split(",")
     FORM_KW.update({"prefetch": code[parts[0]], "dual_form": code[parts[-1]], "autotune": 0})
+    FORM_KW64.update({k: (4 if v == 5 else v) for k, v in FORM_KW.items()})
+
+
+def form_kw(precision) -> dict:
+    return FORM_KW if precision == 1 else FORM_KW64
 
 
 def instance(rank: int):
@@ -365,7 +374,7 @@ def run_ours(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     mixed = S.LP.from_instance(inst, S.default_params(precision=S.PREC_MIXED, aux_general_integers=0, **FORM_KW),
                                stream=stream.cuda_stream)
-    fp64 = S.LP.from_instance(inst, S.default_params(precision=S.PREC_FP64, aux_general_integers=0, **FORM_KW),
+    fp64 = S.LP.from_instance(inst, S.default_params(precision=S.PREC_FP64, aux_general_integers=0, **FORM_KW64),
                               stream=stream.cuda_stream)
     nchk = int(mixed.params.n_check)
 
@@ -424,15 +433,18 @@ def run_ours(args):
     ms64, _ = in_solve_ms(ms64_iso, t_d / max(1, world), it_d / max(1, world), nchk)
     b64_primal, b64_dual = kernel_bytes(m, n, nnz, 8, 8)
 
-    # end to end through the C ABI from host buffers: create (H2D + setup), solve, read x
+    # end to end through the C ABI from pinned host buffers: create (H2D + setup), solve, read x
     e2e_it = 0
     e2e_t = 0.0
     h2d = (8 * (m + 1) + 4 * nnz + 8 * nnz + 8 * 3 * n + 8 * 2 * m + n)
-    x = np.zeros(n)  # the caller's result buffer, reused across steps
+    hp = {k: torch.from_numpy(np.ascontiguousarray(getattr(inst, k))).pin_memory().numpy()
+          for k in ("rowptr", "cols", "vals", "c", "lo", "hi", "l", "u", "is_int")}
+    x = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()  # the caller's result buffer, reused
     for _ in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        lp = S.LP.from_instance(inst, S.default_params(precision=S.PREC_MIXED, aux_general_integers=0, **FORM_KW))
+        lp = S.LP(hp["rowptr"], hp["cols"], hp["vals"], hp["c"], hp["lo"], hp["hi"], hp["l"], hp["u"], hp["is_int"],
+                  m, n, S.default_params(precision=S.PREC_MIXED, aux_general_integers=0, **FORM_KW))
         r = lp.pdhg_solve(TOL, ITER_CAP)
         lp.primal(out=x)
         lp.close()
@@ -519,7 +531,7 @@ def run_ours(args):
         "gpu_launches": int(n_launch),
         "e2e": {"value": e2e_it / e2e_t, "unit": "iter/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(8 * n),
-                "path": "scylla_lp_create from host arrays + scylla_pdhg_solve + scylla_get_primal"},
+                "path": "scylla_lp_create from pinned host arrays + scylla_pdhg_solve + scylla_get_primal into a pinned buffer"},
         "cpu_baseline": cpu,
         "dram_resident": dram,
         "batched": batched,
@@ -930,7 +942,7 @@ def dram_resident(S, peak, peak_kind):
     m, n, nnz = inst.m, inst.n, inst.nnz
     out = {"workload": DRAM_WORKLOAD, "m": m, "n": n, "nnz": nnz}
     for name, prec, sv in (("mixed", S.PREC_MIXED, 4), ("fp64", S.PREC_FP64, 8)):
-        lp = S.LP.from_instance(inst, S.default_params(precision=prec, aux_general_integers=0, **FORM_KW))
+        lp = S.LP.from_instance(inst, S.default_params(precision=prec, aux_general_integers=0, **form_kw(prec)))
         lp.pdhg_solve(0.0, 64)  # warm-up
         lp.reset_state()
         r = lp.pdhg_solve(0.0, 640)
