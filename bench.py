@@ -874,19 +874,26 @@ def batched_section(S, peak, peak_kind):
     B.reset_state()
     res, sec = B.solve(TOL, ITER_CAP)
     conv = sum(1 for r in res if r.status == S.CONVERGED)
-    pers, tune_ms = B.info()
+    form, tune_ms = B.info()
+    names = {1: "graph per n_check attempts", 2: "persistent work queue",
+             3: "graph per n_check attempts, asynchronous-copy tiles"}
     out["mixed_batched"] = {"seconds": sec, "converged": conv, "max_attempts": max(r.iterations for r in res),
                             "sum_attempts": sum(r.iterations for r in res),
                             "max_rel_kkt": max(r.rel_kkt for r in res),
-                            "launch_form": "persistent work queue" if pers else "graph per n_check attempts",
-                            "create_time_ms_per_64_attempts": {"graphs": tune_ms[0], "persistent": tune_ms[1]}}
-    # the other form for the record (the same solve; identical results)
-    Bo = S.Batch(insts, S.default_params(precision=S.PREC_MIXED, batch_launch=1 if pers else 2))
-    Bo.solve(TOL, ITER_CAP)
-    Bo.reset_state()
-    _, sec_o = Bo.solve(TOL, ITER_CAP)
-    out["mixed_batched"]["other_form_seconds"] = sec_o
-    Bo.close()
+                            "launch_form": names.get(form, form),
+                            "create_time_ms_per_64_attempts": {"graphs": tune_ms[0], "persistent": tune_ms[1],
+                                                               "graphs, asynchronous-copy tiles": tune_ms[2]}}
+    # the other forms for the record (the same solve; identical results)
+    other = {}
+    for f in (1, 2, 3):
+        if f == form:
+            continue
+        Bo = S.Batch(insts, S.default_params(precision=S.PREC_MIXED, batch_launch=f))
+        Bo.solve(TOL, ITER_CAP)
+        Bo.reset_state()
+        _, other[names[f]] = Bo.solve(TOL, ITER_CAP)
+        Bo.close()
+    out["mixed_batched"]["other_forms_seconds"] = other
     # per-kernel device time of the graph form's kernels with every LP taking part
     # (as at the start of a solve): CUDA events around separate launches
     B.reset_state()

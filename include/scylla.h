@@ -127,12 +127,13 @@ typedef struct {
   int32_t distance;             /* distance of the objective update: 1 = l1 (Algorithm 1; auxiliary columns
                                    for general integers), 2 = l2 (the conclusion's alternative: a diagonal
                                    quadratic objective, no auxiliary columns) (1) */
-  int32_t batch_launch;         /* batched solve: 0 automatic (at create, n_check attempts in each of 1 and 2
-                                   are timed and the faster is kept); 1 one CUDA graph
+  int32_t batch_launch;         /* batched solve: 0 automatic (at create, n_check attempts in each of 1, 2 and,
+                                   FP32-mixed, 3 are timed and the fastest is kept); 1 one CUDA graph
                                    per n_check attempts, each phase a launch over a static deal of the tiles;
                                    2 the attempts between checks in one persistent cooperative launch whose
                                    warps take tiles from a shared queue over the LPs still running, the
-                                   queue compacted at every check (0) */
+                                   queue compacted at every check; 3 (FP32-mixed) as 1, each warp's next
+                                   tile staged in shared memory by asynchronous copies (0) */
   int32_t autotune;             /* with prefetch = 0: 1 times the 32-row, wide-tile and (FP32) asynchronous-copy forms of the
                                    per-attempt kernels on the handle's own matrix at create and keeps the
                                    faster for each of the two kernels (the choice is kept per matrix shape
@@ -503,12 +504,12 @@ int scylla_batch_solve(scylla_batch* h, double tol, int64_t iter_limit, scylla_p
                        double* seconds);
 /* primal point of LP b, unscaled: host, length A[b].n */
 int scylla_batch_get_primal(const scylla_batch* h, int32_t b, double* x);
-/* The launch form in use (*persistent = 1: the persistent work-queue launch, 0:
- * one graph per n_check attempts; see scylla_params.batch_launch) and, with
- * batch_launch = 0, the ms of the n_check attempts each form took at create
- * (tune_ms[0] graphs, tune_ms[1] persistent; 0 when not timed).  Either pointer
- * may be NULL. */
-int scylla_batch_info(const scylla_batch* h, int32_t* persistent, double* tune_ms);
+/* The launch form in use (*form, numbered as scylla_params.batch_launch: 1 graphs,
+ * 2 the persistent work-queue launch, 3 graphs over asynchronous-copy tiles) and,
+ * with batch_launch = 0, the ms of the n_check attempts each form took at create
+ * (tune_ms[0] graphs, tune_ms[1] persistent, tune_ms[2] asynchronous-copy graphs;
+ * 0 when not timed).  Either pointer may be NULL. */
+int scylla_batch_info(const scylla_batch* h, int32_t* form, double* tune_ms);
 /* Measurement: `attempts` attempts of every LP from its current pair (no tolerance
  * test) with the graph form's kernels as separate launches and CUDA events around
  * each; ms[0..2] receive the mean device time in milliseconds of the primal step,

@@ -49,7 +49,11 @@ struct scylla_batch {
   cudaGraphExec_t exec = nullptr;
   float last_ms = 0.f;
   bool persistent = false;   // attempts in persistent launches over the work queue (batch_launch)
-  double tune_ms[2] = {0.0, 0.0};  // automatic choice: ms of n_check attempts in each form (graphs, persistent)
+  // graphs whose primal / dual attempt kernels stage the next tile by asynchronous copies (FP32)
+  bool async_p = false, async_d = false;
+  double tune_kernel_ms[4] = {0.0, 0.0, 0.0, 0.0};  // ms per launch: primal, dual plain; primal, dual async
+  // automatic choice: ms of n_check attempts in each form (graphs, persistent, graphs with asynchronous copies)
+  double tune_ms[3] = {0.0, 0.0, 0.0};
   void* grid_bar = nullptr;  // the persistent launches' barrier (device)
   int* h_err = nullptr;      // pinned copy of its error flag
 
@@ -147,6 +151,36 @@ int batch_solve_persistent(scylla_batch* h, DevBatch<T>& B, double tol, int64_t 
   return SCYLLA_OK;
 }
 
+// the graph form's attempt kernels: asynchronous-copy tiles or not (FP32); the
+// captured graph holds the launches, so it is dropped when the form changes
+void set_async_tiles(scylla_batch* h, bool p, bool d) {
+  if (h->async_p == p && h->async_d == d) return;
+  h->async_p = p;
+  h->async_d = d;
+  h->b32.async_p = p ? 1 : 0;
+  h->b32.async_d = d ? 1 : 0;
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->exec = nullptr;
+  h->graph = nullptr;
+}
+
+// device ms per launch of one attempt kernel (part 0 primal, 1 dual) in the current
+// tile forms, over `reps` launches after one untimed
+template <typename T>
+int time_batch_part(scylla_batch* h, DevBatch<T>& B, int part, int reps, double* ms) {
+  cudaStream_t st = h->st;
+  CKB(launch_batch_part<T>(B, part, st));
+  CKB(cudaEventRecord(h->ev0, st));
+  for (int r = 0; r < reps; ++r) CKB(launch_batch_part<T>(B, part, st));
+  CKB(cudaEventRecord(h->ev1, st));
+  CKB(cudaEventSynchronize(h->ev1));
+  float t = 0.f;
+  CKB(cudaEventElapsedTime(&t, h->ev0, h->ev1));
+  *ms = double(t) / reps;
+  return SCYLLA_OK;
+}
+
 template <typename T>
 int batch_solve_impl(scylla_batch* h, DevBatch<T>& B, double tol, int64_t iter_limit) {
   if (h->persistent) return batch_solve_persistent<T>(h, B, tol, iter_limit);
@@ -200,8 +234,12 @@ int create_batch(int32_t count, const scylla_csr* A, const double* const* c, con
     set_error("n_check must be >= 1");
     return SCYLLA_ERR_INVALID_ARG;
   }
-  if (h->p.batch_launch < 0 || h->p.batch_launch > 2) {
-    set_error("batch_launch must be 0..2");
+  if (h->p.batch_launch < 0 || h->p.batch_launch > 3) {
+    set_error("batch_launch must be 0..3");
+    return SCYLLA_ERR_INVALID_ARG;
+  }
+  if (h->p.batch_launch == 3 && h->p.precision != SCYLLA_PREC_MIXED) {
+    set_error("batch_launch = 3 (asynchronous-copy tiles) is for FP32-mixed precision");
     return SCYLLA_ERR_INVALID_ARG;
   }
   if (h->p.infeasibility_checks != 0) {
@@ -520,19 +558,47 @@ int create_batch(int32_t count, const scylla_csr* A, const double* const* c, con
     }
     h->persistent = grid > 0 && h->p.batch_launch == 2;
   }
+  set_async_tiles(h, h->p.batch_launch == 3, h->p.batch_launch == 3);
   CKB(cudaStreamSynchronize(st));
   // automatic form: n_check attempts from the cold start in each form, timed on the
-  // device; the faster is kept (both give identical results) and the LPs go back to
-  // the cold start
-  if (h->p.batch_launch == 0 && (mixed ? h->b32.grid_q : h->b64.grid_q) > 0) {
-    for (int form = 0; form < 2; ++form) {
+  // device; the fastest is kept (all give identical results) and the LPs go back to
+  // the cold start.  The asynchronous-copy graphs take, for each of the two attempt
+  // kernels, the tile form with the shorter launch (timed separately).
+  if (h->p.batch_launch == 0) {
+    const bool can_persist = (mixed ? h->b32.grid_q : h->b64.grid_q) > 0;
+    bool ap = false, ad = false;
+    if (mixed) {
+      // every LP taking part, as at the start of a solve
+      CKB(launch_batch_init<float>(h->b32, 0.0, 1LL << 40, 0, st));
+      CKB(launch_batch_check<float>(h->b32, st));
+      for (int q = 0; q < 2; ++q) {
+        set_async_tiles(h, q == 1, q == 1);
+        for (int part = 0; part < 2; ++part) {
+          const int rc = time_batch_part<float>(h, h->b32, part, 8, &h->tune_kernel_ms[2 * q + part]);
+          if (rc != SCYLLA_OK) return rc;
+        }
+      }
+      ap = h->tune_kernel_ms[2] < h->tune_kernel_ms[0];
+      ad = h->tune_kernel_ms[3] < h->tune_kernel_ms[1];
+    }
+    int best = 0;
+    for (int form = 0; form < 3; ++form) {
+      if ((form == 1 && !can_persist) || (form == 2 && !(ap || ad))) continue;
       h->persistent = form == 1;
+      if (form == 2) set_async_tiles(h, ap, ad);
+      else set_async_tiles(h, false, false);
+      CKB(cudaMemcpyAsync(ctl, h->ctl0.data(), sizeof(Control) * count, cudaMemcpyHostToDevice, st));
+      if (mixed) CKB(launch_batch_init_point<float>(h->b32, st));
+      else CKB(launch_batch_init_point<double>(h->b64, st));
       const int rc = mixed ? batch_solve_impl<float>(h, h->b32, 0.0, h->p.n_check)
                            : batch_solve_impl<double>(h, h->b64, 0.0, h->p.n_check);
       if (rc != SCYLLA_OK) return rc;
       h->tune_ms[form] = h->last_ms;
+      if (h->tune_ms[form] < h->tune_ms[best]) best = form;
     }
-    h->persistent = h->tune_ms[1] < h->tune_ms[0];
+    h->persistent = best == 1;
+    if (best == 2) set_async_tiles(h, ap, ad);
+    else set_async_tiles(h, false, false);
     CKB(cudaMemcpyAsync(ctl, h->ctl0.data(), sizeof(Control) * count, cudaMemcpyHostToDevice, st));
     if (mixed) CKB(launch_batch_init_point<float>(h->b32, st));
     else CKB(launch_batch_init_point<double>(h->b64, st));
@@ -683,16 +749,14 @@ extern "C" int scylla_batch_time_kernels(scylla_batch* h, int32_t attempts, doub
                                              : batch_time_impl<double>(h, h->b64, attempts, ms);
 }
 
-extern "C" int scylla_batch_info(const scylla_batch* h, int32_t* persistent, double* tune_ms) {
+extern "C" int scylla_batch_info(const scylla_batch* h, int32_t* form, double* tune_ms) {
   if (!h) {
     set_error("null handle");
     return SCYLLA_ERR_INVALID_ARG;
   }
-  if (persistent) *persistent = h->persistent ? 1 : 0;
-  if (tune_ms) {
-    tune_ms[0] = h->tune_ms[0];
-    tune_ms[1] = h->tune_ms[1];
-  }
+  if (form) *form = h->persistent ? 2 : ((h->async_p || h->async_d) ? 3 : 1);
+  if (tune_ms)
+    for (int q = 0; q < 3; ++q) tune_ms[q] = h->tune_ms[q];
   return SCYLLA_OK;
 }
 

@@ -168,6 +168,9 @@ struct DevBatch {
   long long* kglob;           // attempts made by the LPs still running
   double exp_red, exp_grow;
   int grid_p, grid_d, grid_c1, grid_c2, grid_ctl;
+  int async_p, async_d;       // FP32: the primal / dual attempt kernel stages each warp's next tile by
+                              // asynchronous copies
+  int grid_pa, grid_da;       // their grids
   // persistent solve over a shared work queue: the LPs still running (rebuilt at
   // every check) and their tiles, as lists of indices, and the chunk counters that
   // warps take tiles from

@@ -1889,6 +1889,144 @@ __device__ __forceinline__ void spmv_tiles_batch(const int2* __restrict__ tiles,
   }
 }
 
+// The static deal of the batched kernels with the warp's next tile staged in shared
+// memory by asynchronous copies, as spmv_tiles_async does for one LP: the next
+// tile's LP index and bounds come a tile ahead, its LP's pool roles are read (an L2
+// load, in the shadow of the current tile's gathers) when its copies are issued, and
+// a tile of an LP that takes no part is neither staged nor computed.  Every tile's
+// products, row sums and epilogue are those of batch_tile_at.
+template <typename V, typename Gather, typename Epi>
+__device__ __forceinline__ void spmv_tiles_batch_async(const int2* __restrict__ tiles,
+                                                       const int* __restrict__ tile_lp, int ntiles,
+                                                       const int* __restrict__ rowptr, const int* __restrict__ cols,
+                                                       const V* __restrict__ vals, Gather& gat, Epi& epi,
+                                                       V* __restrict__ sm, AsyncStage<V>& S) {
+  static_assert(sizeof(V) == 4, "the asynchronous-copy form stages FP32 values");
+  const int lane = threadIdx.x & 31;
+  const WarpTiles wt = warp_tiles(ntiles);
+  if (wt.first >= wt.end) return;
+  const unsigned long long pol = l2_policy_evict_first();
+  auto longrow_of = [](int2 a, int2 b) { return b.x - a.x == 1 && b.y - a.y > kTileNnz; };
+  auto issue = [&](int lp, int2 ta, int2 tb) {
+    const V* pv[5];
+    const int mask = longrow_of(ta, tb) ? 0 : epi.stage_ptrs(lp, pv);
+    if (mask) {
+      const int base = ta.y & ~(kVec - 1);
+#pragma unroll
+      for (int it = 0; it < 3; ++it) {
+        const int o = (it * 32 + lane) * kVec, p = base + o;
+        if (p < tb.y) {
+          cpa16(&S.col[o], cols + p, pol);
+          cpa16(&S.val[o], vals + p, pol);
+        }
+      }
+      if (lane < tb.x - ta.x) {
+        cpa4(&S.rp[lane], rowptr + ta.x + lane);
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+          if (mask & (1 << k)) cpa4(&S.pre[k][lane], pv[k] + ta.x + lane);
+      }
+    }
+    cpa_commit();
+  };
+  int lc = __ldg(tile_lp + wt.first), ln = 0, ll = 0;
+  int2 ca = __ldg(tiles + wt.first), cb = __ldg(tiles + wt.first + 1);
+  int2 na = make_int2(0, 0), nb = make_int2(0, 0), la = make_int2(0, 0), lb = make_int2(0, 0);
+  if (wt.first + wt.step < wt.end) {
+    ln = __ldg(tile_lp + wt.first + wt.step);
+    na = __ldg(tiles + wt.first + wt.step);
+    nb = __ldg(tiles + wt.first + wt.step + 1);
+  }
+  issue(lc, ca, cb);
+  for (int t = wt.first; t < wt.end; t += wt.step) {
+    const int t2 = t + 2 * wt.step;
+    if (t2 < wt.end) {
+      ll = __ldg(tile_lp + t2);
+      la = __ldg(tiles + t2);
+      lb = __ldg(tiles + t2 + 1);
+    }
+    const int r0 = ca.x, r1 = cb.x, p0 = ca.y, p1 = cb.y;
+    const int base = p0 & ~(kVec - 1);
+    cpa_wait_all();
+    __syncwarp();
+    const bool on = epi.begin(lc, t);
+    if (!on) {
+      __syncwarp();
+      if (t + wt.step < wt.end) issue(ln, na, nb);
+    } else if (longrow_of(ca, cb)) {
+      __syncwarp();
+      if (t + wt.step < wt.end) issue(ln, na, nb);
+      const typename Epi::Pre pre = epi.load(r0);
+      V s[1];
+      long_row_sum<1, false>(p0, p1, cols, vals, gat, s);
+      if (lane == 0) epi.finish(r0, s, pre);
+      epi.end(t);
+    } else {
+      const int nr = r1 - r0;
+      const bool mine = lane < nr;
+      int q0 = 0, q1 = 0;
+      typename Epi::Pre pre{};
+      if (mine) {
+        q0 = S.rp[lane] - p0;
+        q1 = (lane + 1 < nr ? S.rp[lane + 1] : p1) - p0;
+        pre = epi.stage_pre(&S.pre[0][0], 32, lane);
+      }
+      V v[3][4], g[3][4];
+#pragma unroll
+      for (int it = 0; it < 3; ++it) {
+        const int o = (it * 32 + lane) * kVec, p = base + o;
+        int4 ci = make_int4(0, 0, 0, 0);
+        float4 vi = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (p < p1) {
+          ci = *reinterpret_cast<const int4*>(&S.col[o]);
+          vi = *reinterpret_cast<const float4*>(&S.val[o]);
+        }
+        const int cc[4] = {ci.x, ci.y, ci.z, ci.w};
+        const V vv[4] = {vi.x, vi.y, vi.z, vi.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int q = p + e;
+          v[it][e] = V(0);
+          g[it][e] = V(0);
+          if (q >= p0 && q < p1) {
+            V gg[1];
+            gat(cc[e], gg);
+            g[it][e] = gg[0];
+            v[it][e] = vv[e];
+          }
+        }
+      }
+      __syncwarp();  // every lane has read the stage before it is refilled
+      if (t + wt.step < wt.end) issue(ln, na, nb);
+#pragma unroll
+      for (int it = 0; it < 3; ++it) {
+        const int p = base + (it * 32 + lane) * kVec;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int q = p + e;
+          if (q >= p0 && q < p1) sm[skew(q - p0)] = v[it][e] * g[it][e];
+        }
+      }
+      __syncwarp();
+      if (mine) {
+        V sum = V(0);
+        for (int q = q0; q < q1; ++q) sum += sm[skew(q)];
+        const V sv[1] = {sum};
+        epi.finish(r0 + lane, sv, pre);
+      }
+      __syncwarp();
+      epi.end(t);
+    }
+    lc = ln;
+    ca = na;
+    cb = nb;
+    ln = ll;
+    na = la;
+    nb = lb;
+  }
+  cpa_wait_all();
+}
+
 // per-LP values of one attempt: L2 loads when the writer may be another block of
 // the same launch (the persistent solve)
 template <bool Coh, typename T>
@@ -1936,6 +2074,19 @@ struct BPrimalEpi : PrimalEpi<T, Coh> {
     const typename AccOf<T>::type a = warp_sum(this->acc);
     if ((threadIdx.x & 31) == 0) B->tp_p[t] = double(a);
     this->acc = 0;
+  }
+  // the epilogue vectors of LP b in stage_vec's order, and the mask of those to
+  // stage (0 when the LP takes no part)
+  __device__ __forceinline__ int stage_ptrs(int b, const T* (&p)[5]) const {
+    const BatchSlot<T> s = read_slot<Coh>(B->slot + b);
+    if (!(s.flags & kSlotActive)) return 0;
+    const DevLP<T>& d = B->d;
+    p[0] = d.X[s.cur];
+    p[1] = this->cc;
+    p[2] = this->ll;
+    p[3] = this->uu;
+    p[4] = d.X[s.avg];
+    return (s.flags & kSlotAvg) ? 31 : 15;
   }
 };
 
@@ -2080,6 +2231,17 @@ struct BDualEpi : DualEpi<T, Coh> {
     fence_acquire_gpu();
     lp_step_decision<T>(B, lp, sc);
   }
+  __device__ __forceinline__ int stage_ptrs(int b, const T* (&p)[5]) const {
+    const BatchSlot<T> s = read_slot<Coh>(B->slot + b);
+    if (!(s.flags & kSlotActive)) return 0;
+    const DevLP<T>& d = B->d;
+    p[0] = d.AX[s.cur];
+    p[1] = d.Y[s.cur];
+    p[2] = this->lo;
+    p[3] = this->hi;
+    p[4] = d.Y[s.avg];
+    return (s.flags & kSlotAvg) ? 31 : 15;
+  }
 };
 
 // one warp per LP: its tiles' sums in a fixed order, then the step decision (the
@@ -2107,6 +2269,44 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_bdual(DevBatc
   auto gat = [&](int j, T(&g)[1]) { g[0] = __ldg(epi.xsrc + j); };
   spmv_tiles_batch<1, T, T>(d.a_tiles, B.a_tile_lp, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals, gat, epi,
                             sm + (threadIdx.x >> 5) * kSmemPerWarp);
+}
+
+// the attempt kernels of the static deal with asynchronous-copy staging (FP32)
+__global__ void __launch_bounds__(kThreads, 3) k_bprimal_as(DevBatch<float> B) {
+  __shared__ float sm[kWarpsPerBlock * kSmemPerWarp];
+  __shared__ __align__(16) AsyncStage<float> stg[kWarpsPerBlock];
+  const DevLP<float>& d = B.d;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ++*B.kglob;  // attempt counter of the LPs still running
+  BPrimalEpi<float> epi;
+  epi.B = &B;
+  epi.xlr = d.XLR;
+  epi.cc = d.c;
+  epi.ll = d.l;
+  epi.uu = d.u;
+  epi.qq = nullptr;
+  epi.acc = 0;
+  auto gat = [&](int i, float(&g)[1]) { g[0] = epi.cached ? 0.f : __ldg(epi.ysrc + i); };
+  const int w = threadIdx.x >> 5;
+  spmv_tiles_batch_async<float>(d.t_tiles, B.t_tile_lp, d.t_ntiles, d.t_rowptr, d.t_cols, d.t_vals, gat, epi,
+                                sm + w * kSmemPerWarp, stg[w]);
+}
+
+__global__ void __launch_bounds__(kThreads, 3) k_bdual_as(DevBatch<float> B) {
+  __shared__ float sm[kWarpsPerBlock * kSmemPerWarp];
+  __shared__ __align__(16) AsyncStage<float> stg[kWarpsPerBlock];
+  const DevLP<float>& d = B.d;
+  BDualEpi<float> epi;
+  epi.B = &B;
+  epi.sc = nullptr;
+  epi.ylr = d.YLR;
+  epi.lo = d.lo;
+  epi.hi = d.hi;
+  epi.acc0 = 0;
+  epi.acc1 = 0;
+  auto gat = [&](int j, float(&g)[1]) { g[0] = __ldg(epi.xsrc + j); };
+  const int w = threadIdx.x >> 5;
+  spmv_tiles_batch_async<float>(d.a_tiles, B.a_tile_lp, d.a_ntiles, d.a_rowptr, d.a_cols, d.a_vals, gat, epi,
+                                sm + w * kSmemPerWarp, stg[w]);
 }
 
 template <typename T, bool Coh = false>
@@ -2858,18 +3058,30 @@ cudaError_t launch_batch_init(const DevBatch<T>& B, double tol, long long iter_l
   k_binit<T><<<(B.nlp + 127) / 128, 128, 0, st>>>(B, tol, iter_limit, stall_checks);
   return cudaGetLastError();
 }
+static void batch_attempt_kernels(const DevBatch<float>& B, cudaStream_t st, int part) {
+  if (part != 1) {
+    if (B.async_p) k_bprimal_as<<<B.grid_pa, kThreads, 0, st>>>(B);
+    else k_bprimal<float><<<B.grid_p, kThreads, 0, st>>>(B);
+  }
+  if (part != 0) {
+    if (B.async_d) k_bdual_as<<<B.grid_da, kThreads, 0, st>>>(B);
+    else k_bdual<float><<<B.grid_d, kThreads, 0, st>>>(B);
+  }
+}
+static void batch_attempt_kernels(const DevBatch<double>& B, cudaStream_t st, int part) {
+  if (part != 1) k_bprimal<double><<<B.grid_p, kThreads, 0, st>>>(B);
+  if (part != 0) k_bdual<double><<<B.grid_d, kThreads, 0, st>>>(B);
+}
 template <typename T>
 cudaError_t launch_batch_slot(const DevBatch<T>& B, cudaStream_t st) {
-  k_bprimal<T><<<B.grid_p, kThreads, 0, st>>>(B);
-  k_bdual<T><<<B.grid_d, kThreads, 0, st>>>(B);
+  batch_attempt_kernels(B, st, -1);
   k_bstep_control<T><<<B.grid_ctl, kThreads, 0, st>>>(B);
   return cudaGetLastError();
 }
 // one kernel of an attempt on its own (measurement): 0 primal, 1 dual, 2 step control
 template <typename T>
 cudaError_t launch_batch_part(const DevBatch<T>& B, int part, cudaStream_t st) {
-  if (part == 0) k_bprimal<T><<<B.grid_p, kThreads, 0, st>>>(B);
-  else if (part == 1) k_bdual<T><<<B.grid_d, kThreads, 0, st>>>(B);
+  if (part == 0 || part == 1) batch_attempt_kernels(B, st, part);
   else k_bstep_control<T><<<B.grid_ctl, kThreads, 0, st>>>(B);
   return cudaGetLastError();
 }
@@ -2941,6 +3153,13 @@ void batch_grids(DevBatch<T>& B) {
   };
   B.grid_p = grid((const void*)k_bprimal<T>, B.d.t_ntiles, 0);
   B.grid_d = grid((const void*)k_bdual<T>, B.d.a_ntiles, 0);
+  if constexpr (std::is_same<T, float>::value) {
+    B.grid_pa = grid((const void*)k_bprimal_as, B.d.t_ntiles, 0);
+    B.grid_da = grid((const void*)k_bdual_as, B.d.a_ntiles, 0);
+  } else {
+    B.grid_pa = B.grid_p;
+    B.grid_da = B.grid_d;
+  }
   B.grid_c1 = grid((const void*)k_bcheck_cols<T>, B.d.t_ntiles, 0);
   B.grid_c2 = grid((const void*)k_bcheck_rows<T>, B.d.a_ntiles, 0);
   B.grid_ctl = (B.nlp * 32 + kThreads - 1) / kThreads;

@@ -509,10 +509,10 @@ class Batch:
         _check(lib().scylla_batch_reset_state(self.h))
 
     def info(self):
-        """(1 if the persistent work-queue launch is in use else 0, the create-time
-        ms of n_check attempts in the graph and persistent forms)."""
+        """(the launch form in use: 1 graphs, 2 persistent work queue, 3 graphs over
+        asynchronous-copy tiles; the create-time ms of n_check attempts in each form)."""
         p = C.c_int32()
-        ms = np.zeros(2)
+        ms = np.zeros(3)
         _check(lib().scylla_batch_info(self.h, C.byref(p), _dp(ms)))
         return p.value, ms
 

@@ -113,24 +113,29 @@ def test_batch_rejects_invalid_member():
 @pytest.mark.parametrize("adaptive", [0, 1])
 def test_persistent_queue_and_graph_paths_identical(precision, adaptive):
     """The persistent launch (warps take tiles from a shared queue over the LPs still
-    running, compacted at every check) and the launch-per-phase graphs over a static
-    deal of the tiles compute every tile with the same arithmetic and reduce each
-    LP's per-tile sums in the same order: identical points, attempt counts,
-    rejections and restarts, with LPs finishing at different checks on the way."""
+    running, compacted at every check), the launch-per-phase graphs over a static
+    deal of the tiles and (FP32-mixed) the same graphs whose warps stage their next
+    tile by asynchronous copies compute every tile with the same arithmetic and
+    reduce each LP's per-tile sums in the same order: identical points, attempt
+    counts, rejections and restarts, with LPs finishing at different checks on the
+    way."""
     S = lib()
     insts = batch_instances()
     kw = dict(precision=precision, adaptive_step=adaptive, restarts=adaptive)
     tol = 1e-6 if precision == 0 else 1e-4
     out = {}
-    for mode in (1, 2):
+    modes = (1, 2, 3) if precision == 1 else (1, 2)
+    for mode in modes:
         B = S.Batch(insts, S.default_params(batch_launch=mode, **kw))
+        assert B.info()[0] == mode
         res, _ = B.solve(tol, 20000 if adaptive else 700)
         out[mode] = ([B.primal(b) for b in range(len(insts))],
                      [(r.iterations, r.rejected, r.restarts, r.status) for r in res])
         B.close()
-    for b in range(len(insts)):
-        np.testing.assert_array_equal(out[2][0][b], out[1][0][b], err_msg=str(b))
-    assert out[2][1] == out[1][1]
+    for mode in modes[1:]:
+        for b in range(len(insts)):
+            np.testing.assert_array_equal(out[mode][0][b], out[1][0][b], err_msg=f"{mode} {b}")
+        assert out[mode][1] == out[1][1]
     if adaptive:
         assert len({t[0] for t in out[2][1]}) > 1  # LPs left the queue at different checks
 
