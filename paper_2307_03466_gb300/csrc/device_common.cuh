@@ -137,6 +137,22 @@ __device__ __forceinline__ bool above_neg_inf(double v) {
 }
 __device__ __forceinline__ bool below_pos_inf(double v) { return __double_as_longlong(v) != 0x7FF0000000000000LL; }
 
+// FP64 dual step with the sign and finiteness tests on the integer pipe (the same
+// result as the generic form for every non-NaN value; a NaN t is passed on instead of
+// being replaced by 0, so the step-size reduction reports it)
+template <>
+__device__ __forceinline__ double dual_prox<double>(double y, double sigma, double axt, double lo, double hi) {
+  if (above_neg_inf(lo)) {
+    const double t = y + sigma * (lo - axt);
+    if (pos_bits(t)) return t;
+  }
+  if (below_pos_inf(hi)) {
+    const double t = y + sigma * (hi - axt);
+    if (neg_bits(t)) return t;
+  }
+  return 0.0;
+}
+
 // lambda = projection of the reduced cost r onto the sign cone of the column bounds
 __device__ __forceinline__ double rc_proj(double r, double l, double u) {
   const bool lf = above_neg_inf(l), uf = below_pos_inf(u);
