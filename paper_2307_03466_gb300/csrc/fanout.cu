@@ -273,14 +273,15 @@ struct FanGeo {
 // One row's sum s[v] = sum_p a_p src(col_p)[v] in CSR order for the lane's VEC
 // objectives.  The segment's lanes hold the row's (index, value) pairs LPR at a time
 // (the first LPR loaded ahead in cl, vl) and broadcast them by shuffles within the
-// segment, four nonzeros per step so four vector gathers per lane are in flight.
+// segment, 16 / VEC nonzeros per step so that many vector gathers per lane are in flight.
 // The warp loops to the longest of its rows; a segment past its row's end issues no
 // load and adds nothing.
 template <typename T, int VEC, int LPR, typename Src>
 __device__ __forceinline__ void fan_vgather(int p0, int p1, int cl, T vl, const int* __restrict__ cols,
                                             const T* __restrict__ vals, Src src, T (&s)[VEC]) {
   const int sl = threadIdx.x & (LPR - 1);
-  constexpr int U = 4;
+  // nonzeros per step: 16 entries of the gathered vector per lane in flight
+  constexpr int U = 16 / VEC;
 #pragma unroll
   for (int v = 0; v < VEC; ++v) s[v] = T(0);
   const int cnt = p1 - p0;
