@@ -354,8 +354,11 @@ int scylla_farkas_gap(const scylla_lp* lp, const double* y, double* gap);
  * to 0 whose sign would need an infinite row bound.  The device computes D of the
  * ray (as in scylla_farkas_gap, over the rows and columns the solve iterates, in the
  * scaled space, each (A^T y)_j a compensated sum) and S, the sum of the absolute
- * values of D's terms; the solve ends SCYLLA_INFEASIBLE when D > 1e-9 S.  On a
- * feasible LP D <= 0 (weak duality), and 1e-9 S is far above the rounding of D.
+ * values of D's terms; the solve ends SCYLLA_INFEASIBLE when D > 1e-9 S and (without
+ * auxiliary distance rows) the host's test of the ray on the original data,
+ * scylla_farkas_gap, gives D > 0; a ray that fails it ends the solve
+ * SCYLLA_NUMERICAL.  On a feasible LP D <= 0 (weak duality), and 1e-9 S is far
+ * above the rounding of D.
  *   y: host, length m of the original rows (may be null): the ray, unscaled, zero when
  *      no candidate was tested.  With auxiliary distance rows
  *      (aux_general_integers) the ray may weigh them too; y holds the original rows'

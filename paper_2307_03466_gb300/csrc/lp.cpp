@@ -1097,9 +1097,26 @@ int scylla_lp::solve(double tol, int64_t iter_limit, int stall_checks, scylla_pd
   rc = (p.precision == SCYLLA_PREC_MIXED) ? solve_impl<float>(this, d32, tol, iter_limit, stall_checks)
                                           : solve_impl<double>(this, d64, tol, iter_limit, stall_checks);
   if (rc != SCYLLA_OK) return rc;
-  const Control& h = *h_ctl;
+  Control& h = *h_ctl;
   if (!h.done) FAIL(SCYLLA_ERR_CUDA, "solve ended without a final check");
   if (h.status == SCYLLA_DEVICE_TIMEOUT) FAIL(SCYLLA_ERR_TIMEOUT, "a device-side barrier wait ran out of time");
+  // a ray the device found is accepted only when the host's compensated test on the
+  // original data confirms it (D > 0); with auxiliary distance rows the ray also weighs
+  // rows the host copy does not hold, and the device's test stands
+  if (h.status == SCYLLA_INFEASIBLE && n_aux == 0 && m0 > 0) {
+    const int rh = ensure_host_matrix();
+    if (rh != SCYLLA_OK) return rh;
+    ensure_columns();
+    std::vector<double> ray(static_cast<size_t>(m0));
+    if (p.precision == SCYLLA_PREC_MIXED) CK(launch_get_cert<float>(d32, io_y, int(m0), st));
+    else CK(launch_get_cert<double>(d64, io_y, int(m0), st));
+    CK(cudaMemcpyAsync(ray.data(), io_y, sizeof(double) * m0, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (!(scylla::farkas_gap_host(*this, ray.data()) > 0.0)) {
+      h.status = SCYLLA_NUMERICAL;
+      set_error("the device's dual ray failed the host test of a certificate");
+    }
+  }
   if (out) {
     std::memset(out, 0, sizeof(*out));
     out->status = h.status;

@@ -139,4 +139,6 @@ struct scylla_lp {
 namespace scylla {
 // exact MIP-feasibility test of x (length n0) on the handle's original MIP (fixprop.cpp)
 bool check_feasible_host(const scylla_lp& lp, const double* x);
+// D(y) of a dual ray y (length m0) on the original LP, compensated FP64 (certify.cpp)
+double farkas_gap_host(const scylla_lp& lp, const double* y);
 }  // namespace scylla
