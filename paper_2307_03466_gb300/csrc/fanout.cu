@@ -147,6 +147,13 @@ __device__ __forceinline__ void vst_cs(T* p, const T (&o)[N]) {
   __stcs(reinterpret_cast<typename FVec<T, N>::V*>(p), u.v);
 }
 template <typename T, int N>
+__device__ __forceinline__ void lds_vec(const T* p, T (&o)[N]) {
+  VecU<T, N> u;
+  u.v = *reinterpret_cast<const typename FVec<T, N>::V*>(p);
+#pragma unroll
+  for (int i = 0; i < N; ++i) o[i] = u.e[i];
+}
+template <typename T, int N>
 __device__ __forceinline__ void vst(T* p, const T (&o)[N]) {
   VecU<T, N> u;
 #pragma unroll
@@ -363,7 +370,7 @@ __device__ __forceinline__ void fan_block_sums(A (&acc)[NSUM][FanGeo<VEC, CHUNK>
 // the first (index, value) pairs of the next group in flight, and it loads the
 // group's epilogue operands before its gathers.
 template <typename T, int VEC, int CHUNK>
-__global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3) k_fprimal(DevFan<T> F) {
+__global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 ? 4 : 3) k_fprimal(DevFan<T> F) {
   typedef typename AccOf<T>::type A;
   typedef FanGeo<VEC, CHUNK> G;
   __shared__ double sh[kFWarps * 1 * kFK];
@@ -385,18 +392,13 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
 #pragma unroll
   for (int sw = 0; sw < G::NSW; ++sw) {
     const int k0 = sw * CHUNK + sl * VEC;  // the lane's first objective in this sweep
-    T tau[VEC], w[VEC], w1[VEC];
-    int fl[VEC];
     bool cached = false, avg = false, lr = false;
 #pragma unroll
     for (int v = 0; v < VEC; ++v) {
-      tau[v] = S.tau[k0 + v];
-      w[v] = S.w[k0 + v];
-      w1[v] = S.w1[k0 + v];
-      fl[v] = S.flags[k0 + v];
-      cached |= (fl[v] & kSlotCached) != 0;
-      avg |= (fl[v] & kSlotAvg) != 0;
-      lr |= (fl[v] & kSlotCopyLr) != 0;
+      const int f = S.flags[k0 + v];
+      cached |= (f & kSlotCached) != 0;
+      avg |= (f & kSlotAvg) != 0;
+      lr |= (f & kSlotCopyLr) != 0;
     }
     const T* ysrc = Yc + k0;
     auto src = [&](int i, T(&g)[VEC]) { vld_nc<T, VEC>(ysrc + size_t(i) * kFK, g); };
@@ -428,17 +430,28 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
       const int j = g * G::RPW + seg;
       const bool live = j < n;
       const size_t o = size_t(live ? j : 0) * kFK + k0;
-      T x[VEC], xa[VEC], at[VEC];
+      T x[VEC], xa[VEC];
 #pragma unroll
-      for (int v = 0; v < VEC; ++v) x[v] = xa[v] = at[v] = T(0);
+      for (int v = 0; v < VEC; ++v) x[v] = xa[v] = T(0);
       if (live) {
         vld_cs<T, VEC>(Xc + o, x);
         if (avg) vld_cs<T, VEC>(Xa + o, xa);
-        if (cached) vld_cs<T, VEC>(At + o, at);
       }
       T s[VEC];
       fan_vgather<T, VEC, G::LPR>(p0, p1, cl, vl, d.t_cols, d.t_vals, src, s);
       if (live) {
+        // the per-objective values from shared memory here rather than in registers
+        // across the gathers (fewer registers, one more resident block per SM)
+        T tau[VEC], w[VEC], w1[VEC], at[VEC];
+        int fl[VEC];
+        lds_vec<T, VEC>(S.tau + k0, tau);
+        lds_vec<T, VEC>(S.w + k0, w);
+        lds_vec<T, VEC>(S.w1 + k0, w1);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) fl[v] = S.flags[k0 + v];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) at[v] = T(0);
+        if (cached) vld_cs<T, VEC>(At + o, at);
         const unsigned long long lob = __ldg(F.lo_bits + j) >> k0, upb = __ldg(F.up_bits + j) >> k0;
         const T lj = __ldg(d.l + j), uj = __ldg(d.u + j);
         const FanCostCol<T> cc = fan_cost_col<T>(F, j);
@@ -481,7 +494,7 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
 // asynchronous copies while the warp gathers for the current group (measured: the
 // dual 5% faster; the same staging made the primal slower, so it loads directly).
 template <typename T, int VEC, int CHUNK>
-__global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3) k_fdual(DevFan<T> F) {
+__global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && !(VEC == 4 && CHUNK == 32) ? 4 : 3) k_fdual(DevFan<T> F) {
   typedef typename AccOf<T>::type A;
   typedef FanGeo<VEC, CHUNK> G;
   __shared__ double sh[kFWarps * 2 * kFK];
@@ -507,17 +520,12 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
 #pragma unroll
   for (int sw = 0; sw < G::NSW; ++sw) {
     const int k0 = sw * CHUNK + sl * VEC;
-    T sig[VEC], w[VEC], w1[VEC];
-    int fl[VEC];
     bool avg = false, lr = false;
 #pragma unroll
     for (int v = 0; v < VEC; ++v) {
-      sig[v] = S.sigma[k0 + v];
-      w[v] = S.w[k0 + v];
-      w1[v] = S.w1[k0 + v];
-      fl[v] = S.flags[k0 + v];
-      avg |= (fl[v] & kSlotAvg) != 0;
-      lr |= (fl[v] & kSlotCopyLr) != 0;
+      const int f = S.flags[k0 + v];
+      avg |= (f & kSlotAvg) != 0;
+      lr |= (f & kSlotCopyLr) != 0;
     }
     const T* xsrc = Xn + k0;
     auto src = [&](int jc, T(&g)[VEC]) { vld_nc<T, VEC>(xsrc + size_t(jc) * kFK, g); };
@@ -570,6 +578,13 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && VEC == 2 ? 4 : 3)
       if (avg) stage_read<T, VEC>(E, wib, stg, 2, lane, ya);
       if (live) {
         const T lo = __ldg(d.lo + i), hi = __ldg(d.hi + i);
+        T sig[VEC], w[VEC], w1[VEC];
+        int fl[VEC];
+        lds_vec<T, VEC>(S.sigma + k0, sig);
+        lds_vec<T, VEC>(S.w + k0, w);
+        lds_vec<T, VEC>(S.w1 + k0, w1);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) fl[v] = S.flags[k0 + v];
         T yn[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
