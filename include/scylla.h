@@ -545,6 +545,10 @@ int scylla_fanout_solve(scylla_fanout* f, double tol, int64_t iter_limit, scylla
                         double* seconds);
 /* primal point of objective k, unscaled: host, length n */
 int scylla_fanout_get_primal(const scylla_fanout* f, int32_t k, double* x);
+/* dual point of objective k, unscaled: host, length m (the rows of the LP; the
+ * fan-out's LP has no auxiliary rows).  With scylla_fanout_get_primal it is the pair
+ * whose errors the objective's last result reports.  Errors: INVALID_ARG, CUDA. */
+int scylla_fanout_get_dual(const scylla_fanout* f, int32_t k, double* y);
 /* every objective back to the handle's current pair, step size and primal weight */
 int scylla_fanout_reset_state(scylla_fanout* f);
 /* Tile-shape autotuner of the fan-out (run once by scylla_fanout_create).  Every

@@ -285,7 +285,7 @@ int create_fan(scylla_lp* lp, int K, const double* targets, int round_K, scylla_
     fac = ar.take<double>(2 * size_t(lp->p.n_check));
     n_done = ar.take<int>(1);
     kglob = ar.take<long long>(1);
-    f->io = ar.take<double>(n);
+    f->io = ar.take<double>(n > m ? n : m);
     if (pass == 0) f->arena_bytes = ar.off + 256;
   }
   cudaStream_t st = lp->st;
@@ -539,6 +539,19 @@ extern "C" int scylla_fanout_get_primal(const scylla_fanout* f, int32_t k, doubl
   if (f->lp->p.precision == SCYLLA_PREC_MIXED) CKF(launch_fan_get_x<float>(f->f32, k, f->io, st));
   else CKF(launch_fan_get_x<double>(f->f64, k, f->io, st));
   CKF(cudaMemcpyAsync(x, f->io, sizeof(double) * f->lp->n0, cudaMemcpyDeviceToHost, st));
+  CKF(cudaStreamSynchronize(st));
+  return SCYLLA_OK;
+}
+
+extern "C" int scylla_fanout_get_dual(const scylla_fanout* f, int32_t k, double* y) {
+  if (!f || !y || k < 0 || k >= f->K) {
+    set_error("invalid argument");
+    return SCYLLA_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = f->lp->st;
+  if (f->lp->p.precision == SCYLLA_PREC_MIXED) CKF(launch_fan_get_y<float>(f->f32, k, f->io, st));
+  else CKF(launch_fan_get_y<double>(f->f64, k, f->io, st));
+  CKF(cudaMemcpyAsync(y, f->io, sizeof(double) * f->lp->m0, cudaMemcpyDeviceToHost, st));
   CKF(cudaStreamSynchronize(st));
   return SCYLLA_OK;
 }

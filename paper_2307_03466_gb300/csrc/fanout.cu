@@ -79,6 +79,84 @@ __device__ __forceinline__ void row_gather(int p0, int p1, const int* __restrict
   }
 }
 
+// The FP32-mixed checks' form of row_gather: the same sums over the row in CSR order,
+// each an FP32 pair (s, c) with s + c the value, so that they take the FP32 pipe and
+// not the FP64 one (64 times slower on this part, and the bound of these kernels).
+// The FP64 entry a is split once per warp step into a_hi = fl32(a) and
+// a_lo = fl32(a - a_hi); per term, a_hi g is formed exactly as p + e (an FMA gives the
+// product's rounding error), a_lo g is added to e, and p joins s by Knuth's two-sum,
+// whose rounding error joins c with e.  The pair holds the FP64 sum to about 2^-44 of
+// the sum of the terms' magnitudes (the FP64 form: 2^-53).  Every operation is an
+// explicitly rounded intrinsic, so no multiply is contracted into a following add.
+template <typename Src>
+__device__ __forceinline__ void row_gather_pair(int p0, int p1, const int* __restrict__ cols,
+                                                const double* __restrict__ vals, Src src, float (&s)[2],
+                                                float (&c)[2]) {
+  const int lane = threadIdx.x & 31;
+  s[0] = s[1] = c[0] = c[1] = 0.0f;
+  for (int b = p0; b < p1; b += 32) {
+    const int p = b + lane;
+    int cl = 0;
+    float hl = 0.0f, ll = 0.0f;
+    if (p < p1) {
+      cl = __ldg(cols + p);
+      const double a = __ldg(vals + p);
+      hl = __double2float_rn(a);
+      ll = __double2float_rn(a - to_f64(hl));
+    }
+    const int cnt = p1 - b < 32 ? p1 - b : 32;
+    for (int e = 0; e < cnt; e += 4) {
+      int ci[4];
+      float ah[4], al[4], g[4][2];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        ci[u] = __shfl_sync(0xffffffffu, cl, e + u);
+        ah[u] = __shfl_sync(0xffffffffu, hl, e + u);
+        al[u] = __shfl_sync(0xffffffffu, ll, e + u);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) src(ci[u], g[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          // lanes past the row end carry (column 0, 0, 0): every term is an exact zero
+          const float pr = __fmul_rn(ah[u], g[u][q]);
+          float er = __fmaf_rn(ah[u], g[u][q], -pr);
+          er = __fmaf_rn(al[u], g[u][q], er);
+          const float t = __fadd_rn(s[q], pr);
+          const float z = __fsub_rn(t, s[q]);
+          const float ts = __fadd_rn(__fsub_rn(s[q], __fsub_rn(t, z)), __fsub_rn(pr, z));
+          c[q] = __fadd_rn(c[q], __fadd_rn(ts, er));
+          s[q] = t;
+        }
+    }
+  }
+}
+
+// A check's products of one row for the lane's two objectives: out in FP64 for the
+// check's sums, ref in the iterates' precision for the refresh of the cached products
+// (FP64: the FP64 sums; FP32-mixed: the FP32 pairs of row_gather_pair, ref their
+// rounded value).  src(col, g) gives the two gathered entries in T.
+template <typename T, typename Src>
+__device__ __forceinline__ void check_gather(int p0, int p1, const int* __restrict__ cols,
+                                             const double* __restrict__ vals, Src src, double (&out)[2],
+                                             T (&ref)[2]) {
+  if constexpr (sizeof(T) == 4) {
+    float s[2], c[2];
+    row_gather_pair(p0, p1, cols, vals, src, s, c);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      out[q] = to_f64(s[q]) + to_f64(c[q]);
+      ref[q] = __fadd_rn(s[q], c[q]);
+    }
+  } else {
+    row_gather<double, double>(p0, p1, cols, vals, src, out);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) ref[q] = out[q];
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void store_block_sums(const typename AccOf<T>::type* acc /*[2][N]*/, int N, double* part,
                                                  double* sh /*[kFWarps][N*kFK]*/) {
@@ -462,7 +540,10 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 ? 4 : 3) k_fprimal(D
           // Section 2.2 recompute the products; the next attempt starts from them)
           const T a = (fl[v] & kSlotCached) ? at[v] : s[v];
           const T cs = cc.at(int((lob >> v) & 1ULL) - int((upb >> v) & 1ULL));
-          xn[v] = clampv<T>(x[v] + tau[v] * (a - cs), lj, uj);
+          // one explicit fused multiply-add, so that every slot of the lane rounds
+          // alike; an objective that does not attempt has tau = 0 and keeps its point
+          // (the checks keep the average inside [l, u], so the clamp is exact too)
+          xn[v] = clampv<T>(fma_t<T>(tau[v], a - cs, x[v]), lj, uj);
           const A dx = A(xn[v]) - A(x[v]);
           acc[0][sw * VEC + v] += dx * dx;
           if (avg) xa[v] = blend(xa[v], x[v], w1[v], w[v]);
@@ -589,7 +670,7 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && !(VEC == 4 && CHU
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
           const T axt = T(2) * s[v] - ax[v];
-          yn[v] = dual_prox<T>(y[v], sig[v], axt, lo, hi);
+          yn[v] = dual_prox<T>(y[v], sig[v], axt, lo, hi);  // sig = 0 keeps y
           const A dy = A(yn[v]) - A(y[v]);
           acc[0][sw * VEC + v] += dy * dy;
           acc[1][sw * VEC + v] += dy * (A(s[v]) - A(ax[v]));
@@ -733,26 +814,28 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_cols(DevFan<T> F) {
   T* Xa = F.X[2];
   for (int j = gw; j < d.n; j += nw) {
     double sc[2], sa[2];
-    auto srcc = [&](int i, double(&g)[2]) {
+    T rc[2], ra[2];
+    auto srcc = [&](int i, T(&g)[2]) {
 #pragma unroll
-      for (int q = 0; q < 2; ++q) g[q] = on[q] ? to_f64(yc[size_t(i) * kFK + lane + 32 * q]) : 0.0;
+      for (int q = 0; q < 2; ++q) g[q] = on[q] ? yc[size_t(i) * kFK + lane + 32 * q] : T(0);
     };
-    auto srca = [&](int i, double(&g)[2]) {
+    auto srca = [&](int i, T(&g)[2]) {
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         if (!on[q]) {
-          g[q] = 0.0;
+          g[q] = T(0);
           continue;
         }
         const size_t o = size_t(i) * kFK + lane + 32 * q;
         T v = ya[o];
         if (fl[q] & kSlotAvg) v = blend(v, yc[o], w1[q], w[q]);
-        g[q] = to_f64(v);
+        g[q] = v;
       }
     };
-    row_gather<double, double>(d.t_rowptr[j], d.t_rowptr[j + 1], d.t_cols, d.t_vals64, srcc, sc);
-    row_gather<double, double>(d.t_rowptr[j], d.t_rowptr[j + 1], d.t_cols, d.t_vals64, srca, sa);
+    check_gather<T>(d.t_rowptr[j], d.t_rowptr[j + 1], d.t_cols, d.t_vals64, srcc, sc, rc);
+    check_gather<T>(d.t_rowptr[j], d.t_rowptr[j + 1], d.t_cols, d.t_vals64, srca, sa, ra);
     const double Cj = d.C[j], iCj = d.invC[j], lj = d.l64[j], uj = d.u64[j];
+    const T ljT = d.l[j], ujT = d.u[j];
     const unsigned long long lob = F.lo_bits[j], upb = F.up_bits[j];
     const FanCostCol<double> cc = fan_cost_col64(F.t, F.om, F.c_orig[j], Cj);
 #pragma unroll
@@ -761,13 +844,16 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_cols(DevFan<T> F) {
       const int k = lane + 32 * q;
       const size_t o = size_t(j) * kFK + k;
       const T x = Xc[o];
-      T xav = Xa[o];
-      if (fl[q] & kSlotAvg) {
-        xav = blend(xav, x, w1[q], w[q]);
-        Xa[o] = xav;
-      }
-      F.ATY[0][o] = T(sc[q]);
-      F.ATY[1][o] = T(sa[q]);
+      // the average of points in [l, u] can leave it by a rounding: it is kept in the
+      // box the iterates are clamped to, so that the point a check evaluates is the
+      // one an objective finishing with it keeps (and returns)
+      const T x0 = Xa[o];
+      T xav = x0;
+      if (fl[q] & kSlotAvg) xav = blend(xav, x, w1[q], w[q]);
+      xav = clampv<T>(xav, ljT, ujT);
+      if (xav != x0) Xa[o] = xav;
+      F.ATY[0][o] = rc[q];
+      F.ATY[1][o] = ra[q];
       const double cs = cc.at(int((lob >> k) & 1ULL) - int((upb >> k) & 1ULL));
       const double xl = to_f64(F.XLR[o]);
       const double xs[2] = {to_f64(x), to_f64(xav)};
@@ -825,16 +911,17 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_rows(DevFan<T> F) {
   T* Ya = F.Y[2];
   for (int i = gw; i < d.m; i += nw) {
     double sc[2], sa[2];
-    auto srcc = [&](int j, double(&g)[2]) {
+    T rc[2], ra[2];
+    auto srcc = [&](int j, T(&g)[2]) {
 #pragma unroll
-      for (int q = 0; q < 2; ++q) g[q] = on[q] ? to_f64(xc[size_t(j) * kFK + lane + 32 * q]) : 0.0;
+      for (int q = 0; q < 2; ++q) g[q] = on[q] ? xc[size_t(j) * kFK + lane + 32 * q] : T(0);
     };
-    auto srca = [&](int j, double(&g)[2]) {
+    auto srca = [&](int j, T(&g)[2]) {
 #pragma unroll
-      for (int q = 0; q < 2; ++q) g[q] = on[q] ? to_f64(xa[size_t(j) * kFK + lane + 32 * q]) : 0.0;
+      for (int q = 0; q < 2; ++q) g[q] = on[q] ? xa[size_t(j) * kFK + lane + 32 * q] : T(0);
     };
-    row_gather<double, double>(d.a_rowptr[i], d.a_rowptr[i + 1], d.a_cols, d.a_vals64, srcc, sc);
-    row_gather<double, double>(d.a_rowptr[i], d.a_rowptr[i + 1], d.a_cols, d.a_vals64, srca, sa);
+    check_gather<T>(d.a_rowptr[i], d.a_rowptr[i + 1], d.a_cols, d.a_vals64, srcc, sc, rc);
+    check_gather<T>(d.a_rowptr[i], d.a_rowptr[i + 1], d.a_cols, d.a_vals64, srca, sa, ra);
     const double iRi = d.invR[i], lo = d.lo64[i], hi = d.hi64[i];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -847,8 +934,8 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_rows(DevFan<T> F) {
         yav = blend(yav, y, w1[q], w[q]);
         Ya[o] = yav;
       }
-      F.AX[cur][o] = T(sc[q]);
-      F.AX[2][o] = T(sa[q]);
+      F.AX[cur][o] = rc[q];
+      F.AX[2][o] = ra[q];
       const double yl = to_f64(F.YLR[o]);
       const double ys[2] = {to_f64(y), to_f64(yav)};
       const double ss[2] = {sc[q], sa[q]};
@@ -1052,6 +1139,13 @@ __global__ void k_fget_x(DevFan<T> F, int k, double* out) {
     out[j] = double(x[size_t(j) * kFK + k]) * F.d.C[j];
 }
 
+template <typename T>
+__global__ void k_fget_y(DevFan<T> F, int k, double* out) {
+  const T* y = F.Y[fan_cur(F)];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F.d.m; i += gridDim.x * blockDim.x)
+    out[i] = double(y[size_t(i) * kFK + k]) * F.d.R[i];
+}
+
 // ----------------------------------------------------------------- launchers ---
 // kernel of a tile shape (see fan_shape_vec); FP64 takes shapes 2 and 4
 template <typename T>
@@ -1134,6 +1228,11 @@ cudaError_t launch_fan_get_x(const DevFan<T>& F, int k, double* out, cudaStream_
   return cudaGetLastError();
 }
 template <typename T>
+cudaError_t launch_fan_get_y(const DevFan<T>& F, int k, double* out, cudaStream_t st) {
+  k_fget_y<T><<<4 * device_sm_count(), kFThreads, 0, st>>>(F, k, out);
+  return cudaGetLastError();
+}
+template <typename T>
 bool fan_shape_valid(int shape) {
   return sizeof(T) == 4 ? (shape >= 1 && shape <= 4) : (shape == 2 || shape == 4);
 }
@@ -1165,6 +1264,7 @@ void fan_grids(DevFan<T>& F) {
   template cudaError_t launch_fan_part<T>(const DevFan<T>&, int, cudaStream_t);                        \
   template cudaError_t launch_fan_seed<T>(const DevFan<T>&, const void*, const void*, cudaStream_t);   \
   template cudaError_t launch_fan_get_x<T>(const DevFan<T>&, int, double*, cudaStream_t);              \
+  template cudaError_t launch_fan_get_y<T>(const DevFan<T>&, int, double*, cudaStream_t);              \
   template cudaError_t launch_fan_cw<T>(const DevFan<T>&, float2*, cudaStream_t);                     \
   template bool fan_shape_valid<T>(int);                                                               \
   template void fan_grids<T>(DevFan<T>&);

@@ -456,6 +456,8 @@ cudaError_t launch_fan_cw(const DevFan<T>& F, float2* cw, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fan_get_x(const DevFan<T>& F, int k, double* out, cudaStream_t st);
 template <typename T>
+cudaError_t launch_fan_get_y(const DevFan<T>& F, int k, double* out, cudaStream_t st);
+template <typename T>
 void fan_grids(DevFan<T>& F);
 template <typename T>
 bool fan_shape_valid(int shape);

@@ -130,6 +130,7 @@ _SIGS = {
     "scylla_fanout_destroy": (None, [_P]),
     "scylla_fanout_solve": (C.c_int, [_P, C.c_double, C.c_int64, C.POINTER(PdhgResult), _D]),
     "scylla_fanout_get_primal": (C.c_int, [_P, C.c_int32, _D]),
+    "scylla_fanout_get_dual": (C.c_int, [_P, C.c_int32, _D]),
     "scylla_fanout_reset_state": (C.c_int, [_P]),
     "scylla_batch_info": (C.c_int, [_P, C.POINTER(C.c_int32), _D]),
     "scylla_batch_time_kernels": (C.c_int, [_P, C.c_int32, _D]),
@@ -562,6 +563,11 @@ class Fanout:
         x = np.empty(self.lp.n)
         _check(lib().scylla_fanout_get_primal(self.h, int(k), _dp(x)))
         return x
+
+    def dual(self, k: int) -> np.ndarray:
+        y = np.empty(self.lp.m)
+        _check(lib().scylla_fanout_get_dual(self.h, int(k), _dp(y)))
+        return y
 
     def reset_state(self):
         _check(lib().scylla_fanout_reset_state(self.h))

@@ -96,6 +96,35 @@ def test_mixed_fanout_reaches_1e4():
     base.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_reported_errors_are_the_oracles_evaluation_of_the_returned_pair(precision):
+    """Each objective's result reports the errors its last check measured (FP64 sums;
+    in FP32-mixed, sums kept as FP32 pairs good to about 2^-44 of the terms): they
+    equal the oracle's FP64 evaluation (Section 2.2) of the returned pair (x, y)
+    under that objective within 1e-10 (1 + |value|).  A pair sum without the low
+    part of the FP64 entries (2^-24 per term) misses eps_p by about 1e-8 and the
+    dual objective by about 1e-3 here."""
+    S, inst, base, targets, state, params = setup(K=6, precision=precision)
+    F = S.Fanout(base, targets, round_K=1)
+    res, _ = F.solve(1e-6 if precision == 0 else 1e-4, 200000)
+    for q in range(targets.shape[1]):
+        assert res[q].status == O.CONVERGED, q
+        o = O.OracleLP(inst.csr(), inst.c, inst.lo, inst.hi, inst.l, inst.u)
+        chat, _, off = P.objective_update(inst.c, inst.is_int, inst.l, inst.u, targets[:, q], 1, [])
+        o.set_objective_vector(chat, off)
+        x, y = F.primal(q), F.dual(q)
+        assert x.shape == (inst.n,) and y.shape == (inst.m,)
+        ev = o.evaluate(x / o.C, y / o.R)
+        r = res[q]
+        for name, a, b in (("eps_p", r.eps_p, ev.eps_p), ("eps_d", r.eps_d, ev.eps_d), ("eps_g", r.eps_g, ev.eps_g),
+                           ("pobj", r.pobj, ev.pobj), ("dobj", r.dobj, ev.dobj)):
+            assert abs(a - b) <= 1e-10 * (1 + abs(b)), (q, name, a, b)
+    with pytest.raises(S.ScyllaError):
+        F.dual(targets.shape[1])
+    F.close()
+    base.close()
+
+
 def test_fanout_needs_lp_without_aux_columns():
     S = lib()
     inst = I.packing_covering(m=60, n=120, per_col=3, seed=3)  # general integers -> auxiliary columns

@@ -232,17 +232,21 @@ def test_fanout_bench_size_fixed_step_sampled_objectives_match_oracle(fan):
     base.close()
 
 
-def test_fanout_bench_size_mixed_all_converge_primal_checked_by_oracle(fan):
+def test_fanout_bench_size_mixed_all_converge_checked_by_oracle(fan):
     S, inst = fan
     base = S.LP.from_instance(inst, S.default_params(precision=S.PREC_MIXED, aux_general_integers=0))
     targets, _ = fan_targets(S, inst, base)
     F = S.Fanout(base, targets, round_K=1)
     res, _ = F.solve(1e-4, 200000)
     assert all(r.status == O.CONVERGED and r.rel_kkt <= 1e-4 for r in res)
-    o = O.OracleLP(inst.csr(), inst.c, inst.lo, inst.hi, inst.l, inst.u)
     for q in (0, 63):
-        ev = o.evaluate(F.primal(q) / o.C, np.zeros(inst.m))
-        assert ev.eps_p <= 1.2e-4, (q, ev.eps_p)
+        o = O.OracleLP(inst.csr(), inst.c, inst.lo, inst.hi, inst.l, inst.u)
+        chat, _, off = P.objective_update(inst.c, inst.is_int, inst.l, inst.u, targets[:, q], 1, [])
+        o.set_objective_vector(chat, off)
+        ev = o.evaluate(F.primal(q) / o.C, F.dual(q) / o.R)
+        assert ev.rel_kkt <= 1.2e-4, (q, ev)
+        for a, b in ((res[q].eps_p, ev.eps_p), (res[q].eps_d, ev.eps_d), (res[q].eps_g, ev.eps_g)):
+            assert abs(a - b) <= 1e-10 * (1 + b), (q, a, b)
     F.close()
     base.close()
 
