@@ -220,6 +220,7 @@ int create_fan(scylla_lp* lp, int K, const double* targets, int round_K, scylla_
   char *X[3], *Y[3], *AX[3], *ATY[2], *XLR, *YLR;
   unsigned long long *lob, *upb;
   float2* cw;
+  double* cc64;
   Control* ctl;
   void* slot;
   FanState* state;
@@ -273,6 +274,7 @@ int create_fan(scylla_lp* lp, int K, const double* targets, int round_K, scylla_
     XLR = ar.take<char>(vs * nk);
     YLR = ar.take<char>(vs * mk);
     cw = ar.take<float2>(n);
+    cc64 = ar.take<double>(3 * size_t(n));
     lob = ar.take<unsigned long long>(n);
     upb = ar.take<unsigned long long>(n);
     ctl = ar.take<Control>(K);
@@ -323,6 +325,7 @@ int create_fan(scylla_lp* lp, int K, const double* targets, int round_K, scylla_
     F.lo_bits = lob;
     F.up_bits = upb;
     F.cw = cw;
+    F.cc64 = cc64;
     F.t = t;
     F.om = om;
     F.ctl = ctl;
@@ -343,12 +346,13 @@ int create_fan(scylla_lp* lp, int K, const double* targets, int round_K, scylla_
   if (mixed) {
     fill(g32, float{});
     f->f32 = g32;
-    CKF(launch_fan_cw<float>(f->f32, cw, st));
+    CKF(launch_fan_cw<float>(f->f32, cw, cc64, st));
     const int rc = seed_state<float>(f, f->f32);
     return rc != SCYLLA_OK ? rc : fan_tune<float>(f, f->f32, 0, 0);
   }
   fill(g64, double{});
   f->f64 = g64;
+  CKF(launch_fan_cw<double>(f->f64, nullptr, cc64, st));
   const int rc = seed_state<double>(f, f->f64);
   return rc != SCYLLA_OK ? rc : fan_tune<double>(f, f->f64, 0, 0);
 }

@@ -793,7 +793,7 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_cols(DevFan<T> F) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const DevLP<T>& d = F.d;
   const int cur = fan_cur(F);
-  bool on[2];
+  bool on[2], hs[2];
   int fl[2];
   T w[2], w1[2];
 #pragma unroll
@@ -803,6 +803,8 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_cols(DevFan<T> F) {
     on[q] = (fl[q] & kSlotCheck) != 0;
     w[q] = k < F.K ? F.slot[k].w : T(0);
     w1[q] = k < F.K ? F.slot[k].w1 : T(1);
+    // the hash of the rounded point only feeds the stall test
+    hs[q] = k < F.K && F.ctl[k].stall_checks > 0;
   }
   double acc[2 * kNC1];
 #pragma unroll
@@ -837,7 +839,7 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_cols(DevFan<T> F) {
     const double Cj = d.C[j], iCj = d.invC[j], lj = d.l64[j], uj = d.u64[j];
     const T ljT = d.l[j], ujT = d.u[j];
     const unsigned long long lob = F.lo_bits[j], upb = F.up_bits[j];
-    const FanCostCol<double> cc = fan_cost_col64(F.t, F.om, F.c_orig[j], Cj);
+    const FanCostCol<double> cc{F.cc64[3 * size_t(j)], F.cc64[3 * size_t(j) + 1], F.cc64[3 * size_t(j) + 2]};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       if (!on[q]) continue;
@@ -875,7 +877,7 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_cols(DevFan<T> F) {
         const double dd = xs[c] - xl;
         a[4] += dd * dd;
       }
-      if (d.int_mask[j]) h[q] += round_hash(j, xs[0] * Cj);
+      if (hs[q] && d.int_mask[j]) h[q] += round_hash(j, xs[0] * Cj);
     }
   }
   store_block_sums<double>(acc, kNC1, F.part_c1, sh);
@@ -1124,11 +1126,16 @@ __global__ void k_fseed(DevFan<T> F, const T* x0, const T* y0) {
 }
 
 // FP32 objective pairs (t c_j C_j, om C_j) of the scaled space, one per column
+// and the checks' FP64 triples (cw null in FP64)
 template <typename T>
-__global__ void k_fcw(DevFan<T> F, float2* cw) {
+__global__ void k_fcw(DevFan<T> F, float2* cw, double* cc64) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < F.d.n; j += gridDim.x * blockDim.x) {
     const double Cj = F.d.C[j];
-    cw[j] = make_float2(float(F.t * F.c_orig[j] * Cj), float(F.om * Cj));
+    if (cw) cw[j] = make_float2(float(F.t * F.c_orig[j] * Cj), float(F.om * Cj));
+    const FanCostCol<double> cc = fan_cost_col64(F.t, F.om, F.c_orig[j], Cj);
+    cc64[3 * size_t(j)] = cc.c0;
+    cc64[3 * size_t(j) + 1] = cc.cp;
+    cc64[3 * size_t(j) + 2] = cc.cm;
   }
 }
 
@@ -1218,8 +1225,8 @@ cudaError_t launch_fan_seed(const DevFan<T>& F, const void* x0, const void* y0, 
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_fan_cw(const DevFan<T>& F, float2* cw, cudaStream_t st) {
-  k_fcw<T><<<2 * device_sm_count(), kFThreads, 0, st>>>(F, cw);
+cudaError_t launch_fan_cw(const DevFan<T>& F, float2* cw, double* cc64, cudaStream_t st) {
+  k_fcw<T><<<2 * device_sm_count(), kFThreads, 0, st>>>(F, cw, cc64);
   return cudaGetLastError();
 }
 template <typename T>
@@ -1265,7 +1272,7 @@ void fan_grids(DevFan<T>& F) {
   template cudaError_t launch_fan_seed<T>(const DevFan<T>&, const void*, const void*, cudaStream_t);   \
   template cudaError_t launch_fan_get_x<T>(const DevFan<T>&, int, double*, cudaStream_t);              \
   template cudaError_t launch_fan_get_y<T>(const DevFan<T>&, int, double*, cudaStream_t);              \
-  template cudaError_t launch_fan_cw<T>(const DevFan<T>&, float2*, cudaStream_t);                     \
+  template cudaError_t launch_fan_cw<T>(const DevFan<T>&, float2*, double*, cudaStream_t);            \
   template bool fan_shape_valid<T>(int);                                                               \
   template void fan_grids<T>(DevFan<T>&);
 

@@ -224,6 +224,9 @@ struct DevFan {
   int grid_p, grid_d, grid_c1, grid_c2, grid_copy;
   // FP32 objective of the scaled space per column: (t c_j C_j, om C_j)
   const float2* cw;
+  // the checks' FP64 objective values of the scaled space per column, for g = 0, +1
+  // and -1 (three per column, as fan_cost_col64 forms them)
+  const double* cc64;
   // tile shape of the primal and dual SpMM (objectives per lane, slots per sweep):
   // 1 = (4, 64), 2 = (2, 64), 3 = (4, 32), 4 = (2, 32); FP64 takes 2 and 4
   int shape_p, shape_d;
@@ -452,7 +455,7 @@ cudaError_t launch_fan_part(const DevFan<T>& F, int part, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fan_seed(const DevFan<T>& F, const void* x0, const void* y0, cudaStream_t st);
 template <typename T>
-cudaError_t launch_fan_cw(const DevFan<T>& F, float2* cw, cudaStream_t st);
+cudaError_t launch_fan_cw(const DevFan<T>& F, float2* cw, double* cc64, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fan_get_x(const DevFan<T>& F, int k, double* out, cudaStream_t st);
 template <typename T>
