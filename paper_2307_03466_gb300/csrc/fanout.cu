@@ -412,7 +412,7 @@ __device__ __forceinline__ void fan_vgather(int p0, int p1, int cl, T vl, const 
 
 // per-block sums of the per-lane accumulators acc[t][o] (sum t; the lane's o-th
 // objective is slot (o / VEC) CHUNK + sl VEC + o % VEC) into
-// part[block][t][objective]; the segments of a warp hold the same objectives
+// part[t][objective][block]; the segments of a warp hold the same objectives
 template <typename A, int VEC, int CHUNK, int NSUM>
 __device__ __forceinline__ void fan_block_sums(A (&acc)[NSUM][FanGeo<VEC, CHUNK>::NOBJ], double* part,
                                                double* sh /*[kFWarps][NSUM][kFK]*/) {
@@ -437,7 +437,7 @@ __device__ __forceinline__ void fan_block_sums(A (&acc)[NSUM][FanGeo<VEC, CHUNK>
   for (int idx = threadIdx.x; idx < NSUM * kFK; idx += blockDim.x) {
     double s = 0.0;
     for (int v = 0; v < kFWarps; ++v) s += sh[v * NSUM * kFK + idx];
-    part[blockIdx.x * NSUM * kFK + idx] = s;
+    part[idx * int(gridDim.x) + int(blockIdx.x)] = s;  // [sum][objective][block]
   }
 }
 
@@ -695,7 +695,7 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && !(VEC == 4 && CHU
     }
     cp_async_wait<0>();  // the copies issued past the last group land before the stages are reused
   }
-  // part_d is [block][sum][objective] with sum 0 = ||dy||^2, 1 = dy.(A x' - A x)
+  // part_d is [sum][objective][block] with sum 0 = ||dy||^2, 1 = dy.(A x' - A x)
   fan_block_sums<A, VEC, CHUNK, 2>(acc, F.part_d, sh);
 }
 
@@ -760,10 +760,14 @@ __global__ void __launch_bounds__(kFThreads) k_fstep_control(DevFan<T> F) {
   }
   const int G = F.grid_p, H = F.grid_d;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-  for (int b = lane; b < G; b += 32) s0 += F.part_p[b * kFK + k];
+  // the partials are [sum][objective][block]: a warp's loads are consecutive
+  const double* pp = F.part_p + size_t(k) * G;
+  const double* pd0 = F.part_d + size_t(k) * H;
+  const double* pd1 = F.part_d + size_t(kFK + k) * H;
+  for (int b = lane; b < G; b += 32) s0 += pp[b];
   for (int b = lane; b < H; b += 32) {
-    s1 += F.part_d[(b * 2 + 0) * kFK + k];
-    s2 += F.part_d[(b * 2 + 1) * kFK + k];
+    s1 += pd0[b];
+    s2 += pd1[b];
   }
   s0 = fwarp_sum(s0);
   s1 = fwarp_sum(s1);

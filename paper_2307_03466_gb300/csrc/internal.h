@@ -217,7 +217,9 @@ struct DevFan {
   Control* ctl;                        // K control blocks
   FanSlot<T>* slot;                    // K
   FanState* state;
-  double *part_p, *part_d, *part_c1, *part_c2;  // [block][sum][objective]
+  // block partials: part_p, part_d [sum][objective][block]; part_c1, part_c2
+  // [block][sum][objective]
+  double *part_p, *part_d, *part_c1, *part_c2;
   int* n_done;
   long long* kglob;
   double exp_red, exp_grow;
