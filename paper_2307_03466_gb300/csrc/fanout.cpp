@@ -284,7 +284,7 @@ int create_fan(scylla_lp* lp, int K, const double* targets, int round_K, scylla_
     pd = ar.take<double>(size_t(gd) * 2 * kFanMaxK);
     pc1 = ar.take<double>(size_t(gc1) * kNC1 * kFanMaxK);
     pc2 = ar.take<double>(size_t(gc2) * kNC2 * kFanMaxK);
-    fac = ar.take<double>(2 * size_t(lp->p.n_check));
+    fac = ar.take<double>(3 * size_t(lp->p.n_check));  // FP64 factor pairs, then FP32 pairs
     n_done = ar.take<int>(1);
     kglob = ar.take<long long>(1);
     f->io = ar.take<double>(n > m ? n : m);

@@ -705,17 +705,21 @@ __global__ void __launch_bounds__(kFThreads, sizeof(T) == 4 && !(VEC == 4 && CHU
 // zero step sizes and no averaging, which leaves x, y and the average unchanged
 template <typename T>
 __device__ __forceinline__ void write_fan_slot(FanSlot<T>* s, const Control* c) {
+  // FP32-mixed: the decision's FP32 copies (set by step_control<float>, or by
+  // derive_steps after a check); FP64: from the FP64 fields
+  constexpr bool f32 = sizeof(T) == 4;
+  const double aw = f32 ? double(c->w_f) : c->avg_w;
   FanSlot<T> v;
   const bool active = !c->done && c->k < c->iter_limit;
   if (active) {
-    v.tau = T(c->eta / c->omega);
-    v.sigma = T(c->eta * c->omega);
-    v.w = T(c->avg_w);
-    v.w1 = T(1.0 - c->avg_w);
+    v.tau = f32 ? T(c->tau_f) : T(c->eta / c->omega);
+    v.sigma = f32 ? T(c->sigma_f) : T(c->eta * c->omega);
+    v.w = f32 ? T(c->w_f) : T(c->avg_w);
+    v.w1 = f32 ? T(c->w1_f) : T(1.0 - c->avg_w);
     int f = kSlotActive | kSlotCheck;
     if (c->copy_lr) f |= kSlotCopyLr;
     if (c->aty_valid) f |= kSlotCached;
-    if (c->avg_w > 0.0) f |= kSlotAvg;
+    if (aw > 0.0) f |= kSlotAvg;
     v.flags = f;
   } else if (c->done) {
     v.tau = v.sigma = v.w = T(0);
@@ -726,9 +730,9 @@ __device__ __forceinline__ void write_fan_slot(FanSlot<T>* s, const Control* c) 
     // step sizes, but the average still takes the last accepted point (the next
     // attempt or the check blends it in; k_fstep_control then clears the weight)
     v.tau = v.sigma = T(0);
-    v.w = T(c->avg_w);
-    v.w1 = T(1.0 - c->avg_w);
-    v.flags = kSlotCheck | (c->avg_w > 0.0 ? kSlotAvg : 0) | (c->copy_lr ? kSlotCopyLr : 0);
+    v.w = f32 ? T(c->w_f) : T(c->avg_w);
+    v.w1 = f32 ? T(c->w1_f) : T(1.0 - c->avg_w);
+    v.flags = kSlotCheck | (aw > 0.0 ? kSlotAvg : 0) | (c->copy_lr ? kSlotCopyLr : 0);
   }
   *s = v;
 }
@@ -752,6 +756,9 @@ __global__ void __launch_bounds__(kFThreads) k_fstep_control(DevFan<T> F) {
       if (flags & kSlotCheck) {  // carried: the pending average update is now applied
         Control* c = &F.ctl[k];
         c->avg_w = 0.0;
+        c->w_f = 0.0f;
+        c->w1_f = 1.0f;
+        c->avg_on = 0;
         c->copy_lr = 0;
         write_fan_slot(&F.slot[k], c);
       }
@@ -775,7 +782,14 @@ __global__ void __launch_bounds__(kFThreads) k_fstep_control(DevFan<T> F) {
   if (lane == 0) {
     Control* c = &F.ctl[k];
     const long long rej0 = c->rejected;
-    step_control(c, s0, s1, s2, F.d.step_fac, F.d.n_check, nullptr, 0);
+    if constexpr (sizeof(T) == 4) {
+      // FP32-mixed: the single-LP path's FP32 decision (no FP64 division on the
+      // per-attempt path); the FP64 sums are rounded once
+      const StepPre p = step_pre<float>(c, F.d.step_fac, F.d.n_check);
+      step_control<float>(c, p, float(s0), float(s1), float(s2), nullptr, 0);
+    } else {
+      step_control(c, s0, s1, s2, F.d.step_fac, F.d.n_check, nullptr, 0);
+    }
     st->rej[k] = c->rejected != rej0 ? 1 : 0;
     if (c->done) atomicAdd(F.n_done, 1);
     write_fan_slot(&F.slot[k], c);
@@ -970,11 +984,22 @@ template <typename T>
 __global__ void __launch_bounds__(kFThreads) k_fcheck_control(DevFan<T> F) {
   FanState* st = F.state;
   const long long k0 = *F.kglob;
+  constexpr bool f32 = sizeof(T) == 4;
+  // the step-size factors of attempts k0 + 1 .. k0 + n_check (entry i: attempt
+  // k0 + 1 + i), shared by the objectives still running: FP64 for the FP64 decision,
+  // FP32 (after the FP64 entries) for the FP32-mixed one
   if (blockIdx.x == 0)
     for (int i = threadIdx.x; i < F.d.n_check; i += blockDim.x) {
-      const double kk = double(k0 + 1 + i + 1);
-      F.d.step_fac[2 * i] = 1.0 - pow(kk, -F.exp_red);
-      F.d.step_fac[2 * i + 1] = 1.0 + pow(kk, -F.exp_grow);
+      if (f32) {
+        float* facf = reinterpret_cast<float*>(F.d.step_fac + 2 * F.d.n_check);
+        const float kk = float(k0 + 1 + i + 1);
+        facf[2 * i] = 1.0f - powf(kk, -float(F.exp_red));
+        facf[2 * i + 1] = 1.0f + powf(kk, -float(F.exp_grow));
+      } else {
+        const double kk = double(k0 + 1 + i + 1);
+        F.d.step_fac[2 * i] = 1.0 - pow(kk, -F.exp_red);
+        F.d.step_fac[2 * i + 1] = 1.0 + pow(kk, -F.exp_grow);
+      }
     }
   const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (k >= F.K) return;
@@ -997,6 +1022,12 @@ __global__ void __launch_bounds__(kFThreads) k_fcheck_control(DevFan<T> F) {
     Control* c = &F.ctl[k];
     const int ix0 = c->ix_cur, ia0 = c->ia_cur;
     c->k_fac = k0;
+    if (f32) {
+      sync_step_state(c);  // eta and the weight sum from their FP32 copies
+      const float kk = float(k0 + 2);  // attempt k0 + 1's factors, as the table's entry 0
+      c->fr_f = 1.0f - powf(kk, -float(F.exp_red));
+      c->fg_f = 1.0f + powf(kk, -float(F.exp_grow));
+    }
     check_control(c, r, nullptr, 0);
     st->rst[k] = 0;
     if (c->ix_cur != ix0) {  // to the average: copy instead of swapping roles
