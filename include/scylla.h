@@ -526,7 +526,11 @@ int scylla_batch_reset_state(scylla_batch* h);
  * round_K around K different rounding targets) solved together as sparse-times-
  * tall-skinny products, so A is read once per K objectives.  Every objective has
  * its own step size, primal weight, restarts and termination and starts from the
- * handle's current primal-dual pair (a warm start, Section 2.1). */
+ * handle's current primal-dual pair (a warm start, Section 2.1).  The handle's
+ * precision applies; in SCYLLA_PREC_MIXED the per-attempt step decisions run in
+ * FP32 (as a single-LP solve's do) and the checks' sums over a row are compensated
+ * FP32 pairs (about 2^-44 of the terms' magnitudes; residuals, objectives and norms
+ * in FP64). */
 typedef struct scylla_fanout scylla_fanout;
 
 /* lp: a handle without auxiliary columns (created with aux_general_integers = 0);
