@@ -799,11 +799,12 @@ __global__ void __launch_bounds__(kFThreads) k_fstep_control(DevFan<T> F) {
   }
 }
 
-// FP64 column half of a check for every objective: A^T y of the current and the
-// averaged dual, reduced costs against c_hat_k, residuals, objectives, hash.  Lane
-// q of a warp works on objectives q and q + 32 of one column.  FP32 entries widen
-// to FP64 by the exact bit-level conversion on the integer pipe (an FP32-to-FP64
-// conversion instruction would take the FP64 pipe these kernels are bound by).
+// Column half of a check for every objective: A^T y of the current and the averaged
+// dual (FP64 sums, or in FP32-mixed the FP32 pairs of check_gather), reduced costs
+// against c_hat_k, residuals, objectives, hash, all in FP64.  Lane q of a warp works
+// on objectives q and q + 32 of one column.  FP32 entries widen to FP64 by the exact
+// bit-level conversion on the integer pipe (an FP32-to-FP64 conversion instruction
+// would take the FP64 pipe, the bound of these kernels on this part).
 template <typename T>
 __global__ void __launch_bounds__(kFThreads) k_fcheck_cols(DevFan<T> F) {
   __shared__ double sh[kFWarps * kNC1 * kFK];
