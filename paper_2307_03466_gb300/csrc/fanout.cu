@@ -334,15 +334,17 @@ __device__ __forceinline__ FanCostCol<float> fan_cost_col<float>(const DevFan<fl
   const float2 w = __ldg(F.cw + j);
   return FanCostCol<float>{w.x, w.x + w.y, w.x - w.y};
 }
+// FP64 (the FP64 SpMMs, and the checks' triples of every precision): every
+// operation explicitly rounded, so that no multiply is contracted into the following
+// add (a contraction the compiler may take in one kernel or tile shape and not in
+// another)
+__device__ __forceinline__ FanCostCol<double> fan_cost_col64(double t, double om, double c, double Cj) {
+  const double tc = __dmul_rn(t, c);
+  return FanCostCol<double>{__dmul_rn(tc, Cj), __dmul_rn(__dadd_rn(tc, om), Cj), __dmul_rn(__dsub_rn(tc, om), Cj)};
+}
 template <>
 __device__ __forceinline__ FanCostCol<double> fan_cost_col<double>(const DevFan<double>& F, int j) {
-  const double tc = F.t * __ldg(F.c_orig + j), Cj = __ldg(F.d.C + j);
-  return FanCostCol<double>{tc * Cj, (tc + F.om) * Cj, (tc - F.om) * Cj};
-}
-// the same three values in FP64 for the checks
-__device__ __forceinline__ FanCostCol<double> fan_cost_col64(double t, double om, double c, double Cj) {
-  const double tc = t * c;
-  return FanCostCol<double>{tc * Cj, (tc + om) * Cj, (tc - om) * Cj};
+  return fan_cost_col64(F.t, F.om, __ldg(F.c_orig + j), __ldg(F.d.C + j));
 }
 
 // ------------------------------------------------------------ SpMM sweeps ---
