@@ -125,6 +125,37 @@ def test_reported_errors_are_the_oracles_evaluation_of_the_returned_pair(precisi
     base.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_reported_errors_with_free_and_one_sided_columns(precision):
+    """The same on an LP with free, one-sided and fixed columns and every row kind
+    (no integer columns, so the objectives coincide): the dual residual, which is
+    exactly 0 where both bounds of a column are finite, is nonzero here and agrees with
+    the oracle's, as do the other errors and both objectives."""
+    S = lib()
+    inst = I.open_bounds_lp(300, 500, seed=4)
+    params = S.default_params(precision=precision, aux_general_integers=0)
+    base = S.LP.from_instance(inst, params)
+    base.pdhg_solve(1e-3, 20000)
+    targets = np.repeat(base.primal()[:, None], 3, axis=1)
+    F = S.Fanout(base, targets, round_K=1)
+    res, _ = F.solve(1e-6 if precision == 0 else 1e-4, 200000)
+    seen_eps_d = False
+    for q in range(targets.shape[1]):
+        assert res[q].status == O.CONVERGED, q
+        o = O.OracleLP(inst.csr(), inst.c, inst.lo, inst.hi, inst.l, inst.u)
+        chat, _, off = P.objective_update(inst.c, inst.is_int, inst.l, inst.u, targets[:, q], 1, [])
+        o.set_objective_vector(chat, off)
+        ev = o.evaluate(F.primal(q) / o.C, F.dual(q) / o.R)
+        r = res[q]
+        seen_eps_d |= ev.eps_d > 0.0
+        for name, a, b in (("eps_p", r.eps_p, ev.eps_p), ("eps_d", r.eps_d, ev.eps_d), ("eps_g", r.eps_g, ev.eps_g),
+                           ("pobj", r.pobj, ev.pobj), ("dobj", r.dobj, ev.dobj)):
+            assert abs(a - b) <= 1e-10 * (1 + abs(b)), (q, name, a, b)
+    assert seen_eps_d
+    F.close()
+    base.close()
+
+
 def test_fanout_needs_lp_without_aux_columns():
     S = lib()
     inst = I.packing_covering(m=60, n=120, per_col=3, seed=3)  # general integers -> auxiliary columns
