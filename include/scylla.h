@@ -507,6 +507,9 @@ int scylla_batch_solve(scylla_batch* h, double tol, int64_t iter_limit, scylla_p
                        double* seconds);
 /* primal point of LP b, unscaled: host, length A[b].n */
 int scylla_batch_get_primal(const scylla_batch* h, int32_t b, double* x);
+/* dual point of LP b, unscaled: host, length A[b].m.  With scylla_batch_get_primal it
+ * is the pair whose errors the LP's last result reports.  Errors: INVALID_ARG, CUDA. */
+int scylla_batch_get_dual(const scylla_batch* h, int32_t b, double* y);
 /* The launch form in use (*form, numbered as scylla_params.batch_launch: 1 graphs,
  * 2 the persistent work-queue launch, 3 graphs over asynchronous-copy tiles) and,
  * with batch_launch = 0, the ms of the n_check attempts each form took at create

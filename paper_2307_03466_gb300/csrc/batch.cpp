@@ -774,6 +774,42 @@ extern "C" int scylla_batch_get_primal(const scylla_batch* h, int32_t b, double*
   return SCYLLA_OK;
 }
 
+// y of LP b from its current pool (the pair a finished LP returns, whose errors its
+// result reports), unscaled on the host: y_i = y~_i R_i in FP64, as the primal's
+// getter does on the device
+extern "C" int scylla_batch_get_dual(const scylla_batch* h, int32_t b, double* y) {
+  if (!h || !y || b < 0 || b >= h->nlp) {
+    set_error("invalid argument");
+    return SCYLLA_ERR_INVALID_ARG;
+  }
+  const int r0 = h->row_off[b], cnt = h->row_off[b + 1] - h->row_off[b];
+  if (cnt == 0) return SCYLLA_OK;
+  cudaStream_t st = h->st;
+  const bool mixed = h->p.precision == SCYLLA_PREC_MIXED;
+  const Control* dctl = mixed ? h->b32.ctl : h->b64.ctl;
+  int cur = -1;
+  CKB(cudaMemcpyAsync(&cur, &dctl[b].ix_cur, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CKB(cudaStreamSynchronize(st));
+  if (cur < 0 || cur > 2) {
+    set_error("pool index out of range");
+    return SCYLLA_ERR_CUDA;
+  }
+  std::vector<double> R(static_cast<size_t>(cnt));
+  const double* Rd = mixed ? h->b32.d.R : h->b64.d.R;
+  CKB(cudaMemcpyAsync(R.data(), Rd + r0, sizeof(double) * size_t(cnt), cudaMemcpyDeviceToHost, st));
+  if (mixed) {
+    std::vector<float> v(static_cast<size_t>(cnt));
+    CKB(cudaMemcpyAsync(v.data(), h->b32.d.Y[cur] + r0, sizeof(float) * size_t(cnt), cudaMemcpyDeviceToHost, st));
+    CKB(cudaStreamSynchronize(st));
+    for (int i = 0; i < cnt; ++i) y[i] = double(v[size_t(i)]) * R[size_t(i)];
+  } else {
+    CKB(cudaMemcpyAsync(y, h->b64.d.Y[cur] + r0, sizeof(double) * size_t(cnt), cudaMemcpyDeviceToHost, st));
+    CKB(cudaStreamSynchronize(st));
+    for (int i = 0; i < cnt; ++i) y[i] *= R[size_t(i)];
+  }
+  return SCYLLA_OK;
+}
+
 extern "C" int scylla_batch_reset_state(scylla_batch* h) {
   if (!h) {
     set_error("null handle");

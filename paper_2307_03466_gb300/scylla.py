@@ -125,6 +125,7 @@ _SIGS = {
     "scylla_batch_destroy": (None, [_P]),
     "scylla_batch_solve": (C.c_int, [_P, C.c_double, C.c_int64, C.POINTER(PdhgResult), _D]),
     "scylla_batch_get_primal": (C.c_int, [_P, C.c_int32, _D]),
+    "scylla_batch_get_dual": (C.c_int, [_P, C.c_int32, _D]),
     "scylla_batch_reset_state": (C.c_int, [_P]),
     "scylla_fanout_create": (C.c_int, [_P, C.c_int32, _D, C.c_int32, C.POINTER(_P)]),
     "scylla_fanout_destroy": (None, [_P]),
@@ -505,6 +506,12 @@ class Batch:
         x = np.empty(self.sizes[b][1])
         _check(lib().scylla_batch_get_primal(self.h, int(b), _dp(x)))
         return x
+
+    def dual(self, b: int) -> np.ndarray:
+        # an index out of range is the C call's error (INVALID_ARG)
+        y = np.empty(self.sizes[b][0] if 0 <= b < len(self.sizes) else 1)
+        _check(lib().scylla_batch_get_dual(self.h, int(b), _dp(y)))
+        return y
 
     def reset_state(self):
         _check(lib().scylla_batch_reset_state(self.h))

@@ -73,6 +73,35 @@ def test_adaptive_batch_converges_like_single_solves():
     B.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_reported_errors_are_the_oracles_evaluation_of_the_returned_pair(precision):
+    """Each LP's result reports the errors its last check measured: they equal the
+    oracle's evaluation (Section 2.2) of the returned pair (x, y) within
+    1e-10 (1 + |value|), eps_p, eps_d, eps_g and both objectives, on LPs of every
+    kind in the batch (an LP with free, one-sided and fixed columns included, whose
+    dual residual is not zero)."""
+    S = lib()
+    insts = batch_instances()[:4] + [I.open_bounds_lp(300, 500, seed=4)]
+    B = S.Batch(insts, S.default_params(precision=precision))
+    res, _ = B.solve(1e-6 if precision == 0 else 1e-4, 200000)
+    seen_eps_d = False
+    for b, inst in enumerate(insts):
+        assert res[b].status == O.CONVERGED, b
+        x, y = B.primal(b), B.dual(b)
+        assert x.shape == (inst.n,) and y.shape == (inst.m,)
+        o = oracle_of(inst)
+        ev = o.evaluate(x / o.C, y / o.R)
+        r = res[b]
+        seen_eps_d |= ev.eps_d > 0.0
+        for name, a, c in (("eps_p", r.eps_p, ev.eps_p), ("eps_d", r.eps_d, ev.eps_d), ("eps_g", r.eps_g, ev.eps_g),
+                           ("pobj", r.pobj, ev.pobj), ("dobj", r.dobj, ev.dobj)):
+            assert abs(a - c) <= 1e-10 * (1 + abs(c)), (b, name, a, c)
+    assert seen_eps_d
+    with pytest.raises(S.ScyllaError):
+        B.dual(len(insts))
+    B.close()
+
+
 def test_mixed_batch_reaches_1e4_checked_by_oracle():
     S = lib()
     insts = batch_instances()
