@@ -191,3 +191,27 @@ def test_batched_and_single_solves_agree_on_open_bounds():
         fs = inst.meta["f_star"]
         assert r.status == O.CONVERGED and abs(r.pobj - fs) <= 1e-6 * (1 + abs(fs))
     B.close()
+
+
+@pytest.mark.parametrize("use_graph", [1, 3])
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["open_bounds", "packcover", "mcf"])
+def test_reported_errors_are_the_oracles_evaluation_of_the_returned_pair(name, precision, use_graph):
+    """A solve reports the errors its last check measured (Section 2.2): they equal the
+    oracle's FP64 evaluation of the pair the handle returns, within 1e-10 (1 + |value|),
+    for eps_p, eps_d, eps_g and both objectives, in both precisions, for the chunk
+    graphs and the persistent kernel, on LPs with and without free and one-sided
+    columns (a nonzero dual residual on the first)."""
+    inst = {"open_bounds": lambda: I.open_bounds_lp(300, 500, seed=4),
+            "packcover": lambda: I.packing_covering(m=2000, n=4000, per_col=6, seed=9),
+            "mcf": lambda: I.mcf(nodes=30, avg_degree=4, commodities=6, seed=2)}[name]()
+    g, o = pair(inst, precision=precision, use_graph=use_graph)
+    r = g.pdhg_solve(1e-6 if precision == 0 else 1e-4, 200000)
+    assert r.status == O.CONVERGED
+    ev = o.evaluate(g.primal() / o.C, g.dual() / o.R)
+    for key, a, b in (("eps_p", r.eps_p, ev.eps_p), ("eps_d", r.eps_d, ev.eps_d), ("eps_g", r.eps_g, ev.eps_g),
+                      ("pobj", r.pobj, ev.pobj), ("dobj", r.dobj, ev.dobj)):
+        assert abs(a - b) <= 1e-10 * (1 + abs(b)), (key, a, b)
+    if name == "open_bounds":
+        assert ev.eps_d > 0.0
+    g.close()
